@@ -1,0 +1,219 @@
+"""Seeded box meshes of linear hexahedra, prisms and tetrahedra.
+
+Vertex order conventions (the library's documented input format):
+
+* hex8: (0,0,0) (1,0,0) (1,1,0) (0,1,0) (0,0,1) (1,0,1) (1,1,1) (0,1,1)
+  in the cell's local (i,j,k) corners;
+* pri6: triangle (v0,v1,v2) at the bottom, (v3,v4,v5) above it;
+* tet4: any order with positive orientation.
+
+Boundary nodes of periodic directions are distinct nodes; periodic faces are
+paired by the translation vectors returned in ``periodic``.
+"""
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class MeshSpec:
+    nodes: np.ndarray
+    elements: dict
+    periodic: list = field(default_factory=list)
+    bfaces: list = field(default_factory=list)    # [(node ids, tag)]
+
+    def as_dict(self):
+        return {"nodes": self.nodes, "elements": self.elements,
+                "periodic": self.periodic, "bfaces": self.bfaces}
+
+    @property
+    def n_elements(self):
+        return sum(len(c) for c in self.elements.values())
+
+
+def _grid_nodes(n, lo, hi):
+    xs = [np.linspace(lo[d], hi[d], n[d] + 1) for d in range(3)]
+    Z, Y, X = np.meshgrid(xs[2], xs[1], xs[0], indexing="ij")
+    return np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+
+
+def _nid(n):
+    nx, ny, nz = n
+
+    def f(i, j, k):
+        return i + (nx + 1) * (j + (ny + 1) * k)
+    return f
+
+
+def _perturb(nodes, n, lo, hi, frac, seed):
+    """Move nodes strictly inside the box by U(-a, a) per component,
+    a = frac * h / sqrt(3), so that |displacement| <= frac * h."""
+    if frac <= 0:
+        return nodes
+    rng = np.random.Generator(np.random.PCG64(seed))
+    h = (np.asarray(hi, float) - np.asarray(lo, float)) / np.asarray(n)
+    d = rng.uniform(-1.0, 1.0, size=nodes.shape) * (frac * h / np.sqrt(3.0))
+    eps = 1e-12 * np.max(np.asarray(hi) - np.asarray(lo))
+    inside = np.all((nodes > np.asarray(lo) + eps)
+                    & (nodes < np.asarray(hi) - eps), axis=1)
+    out = nodes.copy()
+    out[inside] += d[inside]
+    return out
+
+
+def _hex_cells(n):
+    nx, ny, nz = n
+    I, J, K = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz),
+                          indexing="ij")
+    # element order: i fastest
+    I, J, K = (a.transpose(2, 1, 0).ravel() for a in (I, J, K))
+    return I, J, K
+
+
+def _boundary_faces(n, f, periodic_dirs, tags):
+    """Quad faces on non-periodic box sides: tags[(dir, side)]."""
+    out = []
+    nx, ny, nz = n
+    rng = {0: (ny, nz), 1: (nx, nz), 2: (nx, ny)}
+    for d in range(3):
+        if d in periodic_dirs:
+            continue
+        for side in (0, 1):
+            tag = tags[(d, side)]
+            fixed = 0 if side == 0 else n[d]
+            a_n, b_n = rng[d]
+            for b in range(b_n):
+                for a in range(a_n):
+                    if d == 0:
+                        ids = (f(fixed, a, b), f(fixed, a + 1, b),
+                               f(fixed, a + 1, b + 1), f(fixed, a, b + 1))
+                    elif d == 1:
+                        ids = (f(a, fixed, b), f(a + 1, fixed, b),
+                               f(a + 1, fixed, b + 1), f(a, fixed, b + 1))
+                    else:
+                        ids = (f(a, b, fixed), f(a + 1, b, fixed),
+                               f(a + 1, b + 1, fixed), f(a, b + 1, fixed))
+                    out.append((ids, tag))
+    return out
+
+
+def box_hex(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), periodic=(0, 1, 2),
+            perturb=0.0, seed=20240829, tags=None):
+    """Box of n[0] x n[1] x n[2] hexahedra.
+
+    periodic: directions with periodic faces; the others get boundary faces
+    tagged by ``tags[(dir, side)]`` (default tag = 2*dir + side).
+    perturb: fraction of the cell size by which interior nodes move.
+    """
+    n = tuple(int(v) for v in n)
+    nodes = _perturb(_grid_nodes(n, lo, hi), n, lo, hi, perturb, seed)
+    f = _nid(n)
+    I, J, K = _hex_cells(n)
+    conn = np.stack([f(I, J, K), f(I + 1, J, K), f(I + 1, J + 1, K),
+                     f(I, J + 1, K), f(I, J, K + 1), f(I + 1, J, K + 1),
+                     f(I + 1, J + 1, K + 1), f(I, J + 1, K + 1)], axis=1)
+    pv = []
+    for d in periodic:
+        T = np.zeros(3)
+        T[d] = hi[d] - lo[d]
+        pv.append(T)
+    if tags is None:
+        tags = {(d, s): 2 * d + s for d in range(3) for s in (0, 1)}
+    bf = _boundary_faces(n, f, set(periodic), tags)
+    return MeshSpec(nodes, {"hex": conn.astype(np.int64)}, pv, bf)
+
+
+def _orient(nodes, conn, kind):
+    """Swap two vertices of every negatively oriented prism/tet."""
+    x = nodes[conn]
+    if kind == "tet":
+        a = x[:, 1] - x[:, 0]
+        b = x[:, 2] - x[:, 0]
+        c = x[:, 3] - x[:, 0]
+        det = np.einsum("ij,ij->i", a, np.cross(b, c))
+        bad = det < 0
+        conn[bad, 1], conn[bad, 2] = conn[bad, 2].copy(), conn[bad, 1].copy()
+    else:
+        a = x[:, 1] - x[:, 0]
+        b = x[:, 2] - x[:, 0]
+        c = x[:, 3] - x[:, 0]
+        det = np.einsum("ij,ij->i", np.cross(a, b), c)
+        bad = det < 0
+        for lo_, hi_ in ((1, 2), (4, 5)):
+            conn[bad, lo_], conn[bad, hi_] = (conn[bad, hi_].copy(),
+                                              conn[bad, lo_].copy())
+    return conn
+
+
+# Kuhn (Freudenthal) split of the unit cube into six tetrahedra that share
+# the main diagonal; corner index = i + 2 j + 4 k.
+_KUHN = []
+for _perm in ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)):
+    _c = [0]
+    _acc = 0
+    for _ax in _perm:
+        _acc += (1, 2, 4)[_ax]
+        _c.append(_acc)
+    _KUHN.append(tuple(_c))
+
+
+def mixed_box(n=40, x_pri=0.5, x_tet=0.8, perturb=0.05, seed=20240829,
+              periodic_x=False):
+    """Unit box of n^3 cells: hexes for x < x_pri, two prisms (split along
+    the cell's xy diagonal, axis along z) for x_pri <= x < x_tet and six
+    Kuhn tetrahedra for x >= x_tet.  y and z are periodic.  Quad faces and
+    triangular tet faces cannot conform, so both sides of the plane
+    x = x_tet (when tets meet hexes or prisms there) are boundary faces:
+    tag 2 on the quad side, tag 3 on the tet side.  x = 0 and x = 1 are
+    boundary faces with tags 0 and 1, or periodic when ``periodic_x`` (valid
+    only when the faces at x = 0 and x = 1 are of the same kind)."""
+    N = (n, n, n)
+    lo, hi = (0.0, 0.0, 0.0), (1.0, 1.0, 1.0)
+    nodes = _grid_nodes(N, lo, hi)
+    f = _nid(N)
+    i_pri = int(round(x_pri * n))
+    i_tet = int(round(x_tet * n))
+    nodes = _perturb(nodes, N, lo, hi, perturb, seed)
+    I, J, K = _hex_cells(N)
+    corner = [f(I + (c & 1), J + ((c >> 1) & 1), K + ((c >> 2) & 1))
+              for c in range(8)]
+    c = np.stack(corner, axis=1)
+    hexes = c[I < i_pri][:, [0, 1, 3, 2, 4, 5, 7, 6]]
+    cp = c[(I >= i_pri) & (I < i_tet)]
+    pris = np.empty((2 * len(cp), 6), np.int64)
+    pris[0::2] = cp[:, [0, 1, 3, 4, 5, 7]]
+    pris[1::2] = cp[:, [0, 3, 2, 4, 7, 6]]
+    ct = c[I >= i_tet]
+    tets = np.empty((6 * len(ct), 4), np.int64)
+    for q, kt in enumerate(_KUHN):
+        tets[q::6] = ct[:, list(kt)]
+    pris = _orient(nodes, pris, "pri")
+    tets = _orient(nodes, tets, "tet")
+    elements = {"hex": hexes, "pri": pris, "tet": tets}
+    plane = {k: np.nonzero(np.abs(_grid_nodes(N, lo, hi)[:, 0] - k / n)
+                           < 1e-12)[0] for k in (0, n, i_tet)}
+    bf = []
+    pv = [np.array([0.0, 1.0, 0.0]), np.array([0.0, 0.0, 1.0])]
+    if periodic_x:
+        pv.append(np.array([1.0, 0.0, 0.0]))
+    else:
+        bf += _plane_faces(elements, plane[0], None, 0)
+        bf += _plane_faces(elements, plane[n], None, 1)
+    if 0 < i_tet < n and (i_pri > 0 or i_tet > i_pri):
+        bf += _plane_faces({"hex": hexes, "pri": pris}, plane[i_tet], None, 2)
+        bf += _plane_faces({"tet": tets}, plane[i_tet], None, 3)
+    return MeshSpec(nodes, elements, pv, bf)
+
+
+def _plane_faces(elements, plane_nodes, _unused, tag):
+    """Element faces whose vertices all lie in a plane given by its node
+    ids: 4 such vertices of a hex or prism, 3 of a tet."""
+    on = set(int(v) for v in plane_nodes)
+    out = []
+    for kind, conn in elements.items():
+        want = 3 if kind == "tet" else 4
+        for ev in conn:
+            vs = [int(v) for v in ev if int(v) in on]
+            if len(vs) == want:
+                out.append((tuple(vs), tag))
+    return out

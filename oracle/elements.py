@@ -1,0 +1,320 @@
+"""Reference element types and their FR operators (test infrastructure only).
+
+For each element type this builds, in FP64, from the definitions of
+Section 2 of the paper:
+
+* the vertex map x = M_n(x~) (trilinear hex, linear prism, affine tet) and
+  its derivatives, for the Jacobian J = dM/dx~ of Section 2;
+* solution points, flux points on every face, reference unit outward
+  normals at the flux points and each face's area scale;
+* ``M0[s, z] = l_z(x_s^(f))``  -- Eq. (disu), interpolation to flux points;
+* ``D[d][z, v] = d l_v / d x~_d (x_z)`` -- the grad l term of Eq. (FRfinal);
+* ``LIFT[z, s] = (div~ g_s)(x_z)`` -- the correction term of Eq. (FRfinal).
+  The paper names only "a flux correction function g".  Reading: the DG
+  choice (Huynh 2007).  For every type it is the DG lift: div~ g_s lies in
+  the solution space and satisfies, for every v in that space,
+  int_element v div~ g_s = int_face(s) v l_s^(f), where l_s^(f) is the face
+  Lagrange basis of the flux points.  Face integrals use exact Gauss rules.
+  Pin: on the hexahedron it equals the tensor-product right/left Radau form
+  g_R' = (P'_{p+1} + P'_p)/2 (tests/test_oracle_operators.py).
+* integration weights ``W[z] = int l_z`` for discrete conservation checks.
+"""
+import numpy as np
+
+from . import bases
+from .points import gl_points, tet_nodes, tri_face_points, tri_solution_points
+from .polys import gauss_jacobi, gauss_legendre
+
+SQ2 = np.sqrt(2.0)
+SQ3 = np.sqrt(3.0)
+
+
+def _quad_rule(n):
+    x, w = gauss_legendre(n)
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    W = np.outer(w, w)
+    return np.stack([X.ravel(), Y.ravel()], axis=1), W.ravel()
+
+
+def _tri_rule(n):
+    a, wa = gauss_legendre(n)
+    b, wb = gauss_jacobi(n, 1.0, 0.0)
+    A, B = np.meshgrid(a, b, indexing="ij")
+    r = 0.5 * (1 + A) * (1 - B) - 1
+    s = B
+    w = np.outer(wa, wb) / 2.0
+    return np.stack([r.ravel(), s.ravel()], axis=1), w.ravel()
+
+
+def tet_rule(n):
+    a, wa = gauss_legendre(n)
+    b, wb = gauss_jacobi(n, 1.0, 0.0)
+    c, wc = gauss_jacobi(n, 2.0, 0.0)
+    A, B, C = np.meshgrid(a, b, c, indexing="ij")
+    r = 0.25 * (1 + A) * (1 - B) * (1 - C) - 1
+    s = 0.5 * (1 + B) * (1 - C) - 1
+    w = (wa[:, None, None] * wb[None, :, None] * wc[None, None, :]) / 8.0
+    return np.stack([r.ravel(), s.ravel(), C.ravel()], axis=1), w.ravel()
+
+
+def hex_rule(n):
+    x, w = gauss_legendre(n)
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    W = w[:, None, None] * w[None, :, None] * w[None, None, :]
+    return np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1), W.ravel()
+
+
+def pri_rule(n):
+    t2, w2 = _tri_rule(n)
+    z, wz = gauss_legendre(n)
+    pts = np.concatenate([np.column_stack([t2, np.full(len(t2), zz)])
+                          for zz in z])
+    w = np.concatenate([w2 * wzz for wzz in wz])
+    return pts, w
+
+
+class Face:
+    """One face of a reference element: 2D parameterisation -> 3D."""
+
+    def __init__(self, kind, verts, origin, ds, dt, normal):
+        self.kind = kind            # 'quad' or 'tri'
+        self.verts = verts          # local vertex ids
+        self.origin = np.asarray(origin, float)
+        self.ds = np.asarray(ds, float)   # d x~ / d s
+        self.dt = np.asarray(dt, float)   # d x~ / d t
+        self.normal = np.asarray(normal, float)
+        self.scale = np.linalg.norm(np.cross(self.ds, self.dt))
+
+    def map(self, st):
+        return (self.origin[None, :] + st[:, :1] * self.ds[None, :]
+                + st[:, 1:2] * self.dt[None, :])
+
+
+class ElementType:
+    """Base class: subclasses fill the geometry tables and bases."""
+
+    name = None
+    nverts = 0
+
+    def __init__(self, p):
+        self.p = p
+        self.upts = self.solution_points()
+        self.nupts = len(self.upts)
+        fp, fidx, fnrm = [], [], []
+        self.face_fpts = []
+        for fi, face in enumerate(self.faces):
+            st = self.face_points(face)
+            x = face.map(st)
+            start = sum(len(a) for a in fp)
+            fp.append(x)
+            fidx += [fi] * len(x)
+            fnrm.append(np.tile(face.normal, (len(x), 1)))
+            self.face_fpts.append(np.arange(start, start + len(x)))
+        self.fpts = np.concatenate(fp)
+        self.fpts_face = np.array(fidx)
+        self.fpts_norm = np.concatenate(fnrm)
+        self.nfpts = len(self.fpts)
+        self._build_operators()
+
+    # face Lagrange basis and exact face quadrature ---------------------
+    def face_points(self, face):
+        p = self.p
+        if face.kind == "quad":
+            x = gl_points(p)
+            X, Y = np.meshgrid(x, x, indexing="xy")
+            return np.stack([X.ravel(), Y.ravel()], axis=1)
+        return tri_face_points(p)
+
+    def _face_basis(self, face, st):
+        if face.kind == "quad":
+            return bases.quad_basis(self.p, st)
+        return bases.tri_basis(self.p, st)
+
+    def _face_rule(self, face):
+        n = self.p + 2
+        return _quad_rule(n) if face.kind == "quad" else _tri_rule(n)
+
+    def _build_operators(self):
+        V = self.basis(self.upts)
+        Vi = np.linalg.inv(V)
+        self.vdm_inv = Vi
+        self.M0 = self.basis(self.fpts) @ Vi
+        G = self.grad(self.upts)
+        self.D = [g @ Vi for g in G]
+        # DG lift of every flux point (orthonormal basis => mass = I)
+        lift = np.zeros((self.nupts, self.nfpts))
+        for fi, face in enumerate(self.faces):
+            st_q, w_q = self._face_rule(face)
+            xq = face.map(st_q)
+            psi_q = self.basis(xq)                           # (nq, nmodes)
+            st_f = self.face_points(face)
+            Vf = self._face_basis(face, st_f)
+            lf = self._face_basis(face, st_q) @ np.linalg.inv(Vf)   # (nq, nf)
+            b = psi_q.T @ (w_q[:, None] * face.scale * lf)   # (nmodes, nf)
+            lift[:, self.face_fpts[fi]] = V @ b
+        self.LIFT = lift
+        # integration weights of the nodal basis
+        xq, wq = self.volume_rule(self.p + 2)
+        self.W = (self.basis(xq) @ Vi).T @ wq
+
+    # geometry of the vertex map ------------------------------------------
+    def map_points(self, verts, x):
+        """Physical coordinates of reference points x, verts (ne, nv, 3)."""
+        N = self.shape(x)                                    # (npts, nv)
+        return np.einsum("pv,evk->epk", N, verts)
+
+    def jacobian(self, verts, x):
+        """a[e, p, j, :] = d x / d x~_j at reference points x."""
+        dN = self.dshape(x)                                  # (3, npts, nv)
+        return np.einsum("jpv,evk->epjk", dN, verts)
+
+    def metrics(self, verts, x):
+        """Return (S, detJ): S = detJ * J^{-1}, f~ = S f, rows a_j x a_k."""
+        a = self.jacobian(verts, x)
+        S = np.stack([np.cross(a[:, :, 1], a[:, :, 2]),
+                      np.cross(a[:, :, 2], a[:, :, 0]),
+                      np.cross(a[:, :, 0], a[:, :, 1])], axis=2)
+        det = np.einsum("epk,epk->ep", a[:, :, 0], S[:, :, 0])
+        return S, det
+
+
+class Hex(ElementType):
+    name = "hex"
+    nverts = 8
+    signs = np.array([[-1, -1, -1], [1, -1, -1], [1, 1, -1], [-1, 1, -1],
+                      [-1, -1, 1], [1, -1, 1], [1, 1, 1], [-1, 1, 1]], float)
+    faces = [
+        Face("quad", (0, 3, 7, 4), (-1, 0, 0), (0, 1, 0), (0, 0, 1), (-1, 0, 0)),
+        Face("quad", (1, 2, 6, 5), (1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 0, 0)),
+        Face("quad", (0, 1, 5, 4), (0, -1, 0), (1, 0, 0), (0, 0, 1), (0, -1, 0)),
+        Face("quad", (3, 2, 6, 7), (0, 1, 0), (1, 0, 0), (0, 0, 1), (0, 1, 0)),
+        Face("quad", (0, 1, 2, 3), (0, 0, -1), (1, 0, 0), (0, 1, 0), (0, 0, -1)),
+        Face("quad", (4, 5, 6, 7), (0, 0, 1), (1, 0, 0), (0, 1, 0), (0, 0, 1)),
+    ]
+
+    def solution_points(self):
+        x = gl_points(self.p)
+        Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+        return np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+
+    def basis(self, x):
+        return bases.hex_basis(self.p, x)
+
+    def grad(self, x):
+        return bases.hex_grad(self.p, x)
+
+    def volume_rule(self, n):
+        return hex_rule(n)
+
+    def shape(self, x):
+        s = self.signs
+        return np.prod(1 + x[:, None, :] * s[None, :, :], axis=2) / 8.0
+
+    def dshape(self, x):
+        s = self.signs
+        f = 1 + x[:, None, :] * s[None, :, :]            # (npts, 8, 3)
+        out = []
+        for j in range(3):
+            d = s[None, :, j] / 8.0
+            for k in range(3):
+                if k != j:
+                    d = d * f[:, :, k]
+            out.append(d)
+        return np.stack(out)
+
+
+class Prism(ElementType):
+    name = "pri"
+    nverts = 6
+    faces = [
+        Face("tri", (0, 1, 2), (0, 0, -1), (1, 0, 0), (0, 1, 0), (0, 0, -1)),
+        Face("tri", (3, 4, 5), (0, 0, 1), (1, 0, 0), (0, 1, 0), (0, 0, 1)),
+        Face("quad", (0, 1, 4, 3), (0, -1, 0), (1, 0, 0), (0, 0, 1), (0, -1, 0)),
+        Face("quad", (1, 2, 5, 4), (0, 0, 0), (-1, 1, 0), (0, 0, 1),
+             (1 / SQ2, 1 / SQ2, 0)),
+        Face("quad", (0, 2, 5, 3), (-1, 0, 0), (0, 1, 0), (0, 0, 1), (-1, 0, 0)),
+    ]
+
+    def solution_points(self):
+        t = tri_solution_points(self.p)
+        z = gl_points(self.p)
+        return np.concatenate([np.column_stack([t, np.full(len(t), zz)])
+                               for zz in z])
+
+    def basis(self, x):
+        return bases.pri_basis(self.p, x)
+
+    def grad(self, x):
+        return bases.pri_grad(self.p, x)
+
+    def volume_rule(self, n):
+        return pri_rule(n)
+
+    @staticmethod
+    def _bary(x):
+        return np.stack([-(x[:, 0] + x[:, 1]) / 2, (1 + x[:, 0]) / 2,
+                         (1 + x[:, 1]) / 2], axis=1)
+
+    def shape(self, x):
+        lam = self._bary(x)
+        zl, zh = (1 - x[:, 2:3]) / 2, (1 + x[:, 2:3]) / 2
+        return np.concatenate([lam * zl, lam * zh], axis=1)
+
+    def dshape(self, x):
+        lam = self._bary(x)
+        zl, zh = (1 - x[:, 2:3]) / 2, (1 + x[:, 2:3]) / 2
+        dl = [np.tile([[-0.5, 0.5, 0.0]], (len(x), 1)),
+              np.tile([[-0.5, 0.0, 0.5]], (len(x), 1))]
+        d0 = np.concatenate([dl[0] * zl, dl[0] * zh], axis=1)
+        d1 = np.concatenate([dl[1] * zl, dl[1] * zh], axis=1)
+        d2 = np.concatenate([-0.5 * lam, 0.5 * lam], axis=1)
+        return np.stack([d0, d1, d2])
+
+
+class Tet(ElementType):
+    name = "tet"
+    nverts = 4
+    faces = [
+        Face("tri", (0, 1, 2), (0, 0, -1), (1, 0, 0), (0, 1, 0), (0, 0, -1)),
+        Face("tri", (0, 1, 3), (0, -1, 0), (1, 0, 0), (0, 0, 1), (0, -1, 0)),
+        Face("tri", (0, 2, 3), (-1, 0, 0), (0, 1, 0), (0, 0, 1), (-1, 0, 0)),
+        Face("tri", (1, 2, 3), (-1, 0, 0), (-1, 1, 0), (-1, 0, 1),
+             (1 / SQ3, 1 / SQ3, 1 / SQ3)),
+    ]
+
+    def solution_points(self):
+        if self.p == 0:
+            return np.array([[-0.5, -0.5, -0.5]])
+        return tet_nodes(self.p)
+
+    def basis(self, x):
+        return bases.tet_basis(self.p, x)
+
+    def grad(self, x):
+        return bases.tet_grad(self.p, x)
+
+    def volume_rule(self, n):
+        return tet_rule(n)
+
+    def shape(self, x):
+        return np.stack([-(1 + x[:, 0] + x[:, 1] + x[:, 2]) / 2,
+                         (1 + x[:, 0]) / 2, (1 + x[:, 1]) / 2,
+                         (1 + x[:, 2]) / 2], axis=1)
+
+    def dshape(self, x):
+        n = len(x)
+        base = np.array([[-0.5, 0.5, 0.0, 0.0], [-0.5, 0.0, 0.5, 0.0],
+                         [-0.5, 0.0, 0.0, 0.5]])
+        return np.stack([np.tile(base[j], (n, 1)) for j in range(3)])
+
+
+ETYPES = {"hex": Hex, "pri": Prism, "tet": Tet}
+
+_cache = {}
+
+
+def element(name, p):
+    key = (name, p)
+    if key not in _cache:
+        _cache[key] = ETYPES[name](p)
+    return _cache[key]
