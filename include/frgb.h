@@ -1,0 +1,186 @@
+/* frgb -- Flux Reconstruction right-hand side on one GB300 GPU.
+ *
+ * C ABI of the library.  It evaluates the right-hand side of the
+ * Flux Reconstruction (FR) discretisation of the compressible Euler and
+ * Navier-Stokes equations (PyFR v2.0.3, arXiv 2408.16509, Section 2) on
+ * meshes of linear hexahedra, prisms and tetrahedra, and advances it with
+ * explicit Runge-Kutta schemes.  Every step of the right-hand side runs in
+ * the library's CUDA kernels (sm_103a); there is no CPU fallback.
+ *
+ * Conventions shared by all calls
+ *   - Return value: FR_OK (0) on success, a negative FR_E* code otherwise;
+ *     fr_last_error() gives a message for the calling thread.
+ *   - The library copies every host input; the caller keeps ownership of
+ *     its buffers.  Handles are opaque and released by fr_mesh_destroy.
+ *   - Host solution layout: per element type, [n_elem][nupts][5], FP64,
+ *     variables (rho, rho u, rho v, rho w, E); point order as returned by
+ *     fr_get_points.
+ *   - Element vertex order (reference coordinates of each vertex):
+ *       FR_HEX8: (-1,-1,-1) (1,-1,-1) (1,1,-1) (-1,1,-1)
+ *                (-1,-1, 1) (1,-1, 1) (1,1, 1) (-1,1, 1)
+ *       FR_PRI6: (-1,-1,-1) (1,-1,-1) (-1,1,-1) (-1,-1,1) (1,-1,1) (-1,1,1)
+ *       FR_TET4: (-1,-1,-1) (1,-1,-1) (-1,1,-1) (-1,-1,1)
+ *     Elements must be positively oriented (det J > 0 everywhere).
+ *   - Calls on one handle are not thread-safe; kernels run on the handle's
+ *     stream (fr_set_stream).
+ */
+#ifndef FRGB_H
+#define FRGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  FR_OK = 0,
+  FR_EINVAL = -1,      /* bad argument */
+  FR_ENOMEM = -2,      /* device or host allocation failed */
+  FR_ECUDA = -3,       /* a CUDA call failed (message has the CUDA error) */
+  FR_EMESH = -4,       /* non-conforming mesh, unmatched face, bad Jacobian */
+  FR_ENONFINITE = -5,  /* a right-hand side produced NaN or Inf */
+  FR_EFILTER = -6,     /* entropy-filter root-find fell back to bisection */
+  FR_ETIMEOUT = -7     /* a bounded device wait expired */
+};
+
+enum { FR_HEX8 = 0, FR_PRI6 = 1, FR_TET4 = 2 };
+enum { FR_EULER = 0, FR_NAVIER_STOKES = 1 };
+enum { FR_FP64 = 0, FR_FP32 = 1 };
+enum { FR_BC_STATE = 0, FR_BC_EXTRAPOLATE = 1 };
+enum { FR_RK4 = 0, FR_RK45 = 1 };
+
+typedef struct fr_mesh fr_mesh;
+
+typedef struct {
+  int etype;            /* FR_HEX8, FR_PRI6 or FR_TET4 */
+  int64_t n_elem;
+  const int64_t* conn;  /* [n_elem][n_vertices] node ids */
+} fr_etype_desc;
+
+typedef struct {
+  int tag;              /* boundary-face tag this condition applies to */
+  int kind;             /* FR_BC_STATE: outside state = state (primitive
+                           rho, u, v, w, p); FR_BC_EXTRAPOLATE: outside
+                           state = inside state */
+  double state[5];
+} fr_bc_desc;
+
+typedef struct {
+  int64_t n_nodes;
+  const double* nodes;            /* [n_nodes][3] */
+  int n_etypes;
+  const fr_etype_desc* etypes;    /* at most one entry per element type */
+  int order;                      /* polynomial order p, 1..4 */
+  int physics;                    /* FR_EULER or FR_NAVIER_STOKES */
+  double gamma, mu, prandtl;      /* ratio of specific heats, dynamic
+                                     viscosity (constant), Prandtl number */
+  int n_periodic;                 /* 0..3 translation vectors */
+  double periodic[3][3];
+  int64_t n_bfaces;
+  const int64_t* bface_nodes;     /* [n_bfaces][4] node ids, -1 pads tris */
+  const int* bface_tags;          /* [n_bfaces] */
+  int n_bcs;                      /* <= 8 */
+  const fr_bc_desc* bcs;
+  int precision;                  /* FR_FP64 or FR_FP32 (storage + compute) */
+  int device;                     /* CUDA device ordinal; < 0 builds a
+                                     host-only handle (geometry, points and
+                                     operators; no GPU is touched and the
+                                     compute calls return FR_EINVAL) */
+} fr_mesh_desc;
+
+/* Build a discretisation (Section 2: conforming tessellation, reference
+ * mappings, solution and flux points).  Faces are paired by their vertex
+ * sets, then periodically by translated centroids; every remaining face
+ * must be listed in bface_nodes.  Flux points are paired by physical
+ * coordinates.  FR_EMESH: non-conforming or unmatched faces, det J <= 0.
+ * Allocates device memory (all state lives on device `device`). */
+int fr_mesh_create(const fr_mesh_desc* desc, fr_mesh** out);
+
+/* Release all host and device memory of the handle.  NULL is allowed. */
+int fr_mesh_destroy(fr_mesh* mesh);
+
+/* Element count, solution points and flux points per element of `etype`
+ * (zeros when the mesh has no element of that type). */
+int fr_get_info(const fr_mesh* mesh, int etype, int64_t* n_elem, int* nupts,
+                int* nfpts);
+
+/* Physical coordinates of the solution points: host [n_elem][nupts][3]. */
+int fr_get_points(const fr_mesh* mesh, int etype, double* xyz);
+
+/* Copy a solution in (host FP64 [n_elem][nupts][5]) / out. */
+int fr_set_solution(fr_mesh* mesh, int etype, const double* u);
+int fr_get_solution(const fr_mesh* mesh, int etype, double* u);
+
+/* Same from / to device memory in the host layout (FP64), on the handle's
+ * stream; the pointer must stay valid until the stream reaches the copy. */
+int fr_set_solution_device(fr_mesh* mesh, int etype, const void* dptr);
+int fr_get_solution_device(const fr_mesh* mesh, int etype, void* dptr);
+
+/* One evaluation of the right-hand side du/dt = -J^{-1} div~ f~ (Section 2,
+ * Eqs. disu, comm_flux, FRfinal) at the current solution.  The result stays
+ * on the device; fr_get_rhs copies it out in the host layout.
+ * FR_ENONFINITE when any entry is NaN or Inf. */
+int fr_rhs(fr_mesh* mesh);
+int fr_get_rhs(const fr_mesh* mesh, int etype, double* rhs);
+
+/* Advance the solution by `nsteps` explicit steps of size dt (Section 2,
+ * "a suitable explicit time integration scheme"; Section 3.5 low-storage
+ * pairs): FR_RK4 classical four-stage, FR_RK45 the two-register
+ * RK4(3)5[2R+]C of Kennedy, Carpenter & Lewis.  One step is replayed as one
+ * CUDA graph.  Returns FR_ENONFINITE if any stage produced NaN/Inf. */
+int fr_rk_step(fr_mesh* mesh, int scheme, double dt, int nsteps);
+
+/* Measurement aid: advances the solution by ONE step of `scheme` exactly
+ * as fr_rk_step does, but launches the kernels one by one (no graph) with
+ * CUDA events around every launch on the handle's stream.  On return
+ * ms[k] holds the summed device time (milliseconds) and launches[k] the
+ * launch count of kernel class k during that step, for k < FR_KC_COUNT. */
+enum { FR_KC_FACE_U = 0,  /* NS common solution at interior flux points */
+       FR_KC_BND_U = 1,   /* NS common solution at boundary flux points */
+       FR_KC_GRAD = 2,    /* NS corrected gradients (one launch per type) */
+       FR_KC_FACE_F = 3,  /* common normal flux, interior pairs */
+       FR_KC_BND_F = 4,   /* common normal flux, boundary points */
+       FR_KC_VOL = 5,     /* volume: flux, divergence, lift, RK update */
+       FR_KC_COUNT = 6 };
+int fr_profile_step(fr_mesh* mesh, int scheme, double dt, double* ms,
+                    int* launches);
+
+/* Kernels and copies of the handle run on this stream (cudaStream_t);
+ * NULL selects the handle's own stream. */
+int fr_set_stream(fr_mesh* mesh, void* cuda_stream);
+
+/* Synchronise the handle's stream. */
+int fr_sync(fr_mesh* mesh);
+
+/* Reference-element data of `etype`, FP64, host memory, as built by the
+ * library (Section 2):
+ *   FR_OP_M0      [nfpts][nupts]        l_z(x_f), Eq. (disu)
+ *   FR_OP_D       [3][nupts][nupts]     d l_v / d x~_d at x_z, Eq. (FRfinal)
+ *   FR_OP_LIFT    [nupts][nfpts]        div~ g_f at x_z (DG correction)
+ *   FR_OP_WEIGHTS [nupts]               int l_z over the reference element
+ *   FR_OP_UPTS    [nupts][3]            reference solution points
+ *   FR_OP_FPTS    [nfpts][3]            reference flux points
+ * Works on host-only handles too. */
+enum { FR_OP_M0 = 0, FR_OP_D = 1, FR_OP_LIFT = 2, FR_OP_WEIGHTS = 3,
+       FR_OP_UPTS = 4, FR_OP_FPTS = 5 };
+int fr_get_operator(const fr_mesh* mesh, int etype, int which, double* out);
+
+/* Metric terms at the solution points: smat [n_elem][9][nupts] holds
+ * S = det(J) J^{-1} (row-major 3x3 per point), rcpdjac [n_elem][nupts]
+ * holds 1/det J.  Either pointer may be NULL. */
+int fr_get_metrics(const fr_mesh* mesh, int etype, double* smat,
+                   double* rcpdjac);
+
+/* Number of interior flux-point pairs and boundary flux points. */
+int fr_get_pairs(const fr_mesh* mesh, int64_t* n_interior,
+                 int64_t* n_boundary);
+
+/* Message of the last failed call on this thread. */
+const char* fr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FRGB_H */

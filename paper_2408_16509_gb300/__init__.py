@@ -1,0 +1,8 @@
+"""GB300-native Flux Reconstruction right-hand side (PyFR v2.0.3 hot path).
+
+The compute path is the CUDA library ``lib/libfrgb.so`` (sources in
+``csrc/``, C ABI in ``include/frgb.h``); this package only marshals
+arguments to it.
+"""
+from ._binding import (ETYPES, FRError, FRMesh, load)  # noqa: F401
+from .build import build  # noqa: F401

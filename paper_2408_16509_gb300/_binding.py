@@ -1,0 +1,283 @@
+"""ctypes binding of ``libfrgb.so`` (the C ABI declared in include/frgb.h).
+
+Argument marshalling only: every step of the right-hand side and of the
+Runge-Kutta update runs in the library's CUDA kernels.  There is no CPU
+path; if the library has not been built, loading raises immediately.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import LIB
+
+FR_OK = 0
+ERRORS = {-1: "FR_EINVAL", -2: "FR_ENOMEM", -3: "FR_ECUDA", -4: "FR_EMESH",
+          -5: "FR_ENONFINITE", -6: "FR_EFILTER", -7: "FR_ETIMEOUT"}
+ETYPES = {"hex": 0, "pri": 1, "tet": 2}
+PHYSICS = {"euler": 0, "ns": 1}
+PRECISION = {"fp64": 0, "fp32": 1}
+SCHEMES = {"rk4": 0, "rk45": 1}
+BC_KIND = {"state": 0, "extrap": 1}
+
+
+class FRError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+        self.name = ERRORS.get(code, str(code))
+
+
+class EtypeDesc(C.Structure):
+    _fields_ = [("etype", C.c_int), ("n_elem", C.c_int64),
+                ("conn", C.POINTER(C.c_int64))]
+
+
+class BCDesc(C.Structure):
+    _fields_ = [("tag", C.c_int), ("kind", C.c_int),
+                ("state", C.c_double * 5)]
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("nodes", C.POINTER(C.c_double)),
+                ("n_etypes", C.c_int), ("etypes", C.POINTER(EtypeDesc)),
+                ("order", C.c_int), ("physics", C.c_int),
+                ("gamma", C.c_double), ("mu", C.c_double),
+                ("prandtl", C.c_double), ("n_periodic", C.c_int),
+                ("periodic", (C.c_double * 3) * 3),
+                ("n_bfaces", C.c_int64),
+                ("bface_nodes", C.POINTER(C.c_int64)),
+                ("bface_tags", C.POINTER(C.c_int)),
+                ("n_bcs", C.c_int), ("bcs", C.POINTER(BCDesc)),
+                ("precision", C.c_int), ("device", C.c_int)]
+
+
+_lib = None
+
+
+def load():
+    """Load the compiled library (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB):
+        raise RuntimeError(
+            f"CUDA library {LIB} is missing: build it with "
+            "paper_2408_16509_gb300.build.build() (nvcc for sm_103a)")
+    lib = C.CDLL(LIB)
+    P, I, D = C.c_void_p, C.c_int, C.c_double
+    sigs = {
+        "fr_mesh_create": (I, [C.POINTER(MeshDesc), C.POINTER(P)]),
+        "fr_mesh_destroy": (I, [P]),
+        "fr_get_info": (I, [P, I, C.POINTER(C.c_int64), C.POINTER(I),
+                            C.POINTER(I)]),
+        "fr_get_points": (I, [P, I, P]),
+        "fr_set_solution": (I, [P, I, P]),
+        "fr_get_solution": (I, [P, I, P]),
+        "fr_set_solution_device": (I, [P, I, P]),
+        "fr_get_solution_device": (I, [P, I, P]),
+        "fr_rhs": (I, [P]),
+        "fr_get_rhs": (I, [P, I, P]),
+        "fr_rk_step": (I, [P, I, D, I]),
+        "fr_set_stream": (I, [P, P]),
+        "fr_sync": (I, [P]),
+        "fr_last_error": (C.c_char_p, []),
+        "fr_get_operator": (I, [P, I, I, P]),
+        "fr_get_metrics": (I, [P, I, P, P]),
+        "fr_get_pairs": (I, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+        "fr_profile_step": (I, [P, I, D, P, P]),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != FR_OK:
+        raise FRError(rc, load().fr_last_error().decode())
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class FRMesh:
+    """A discretised mesh living on one GPU (see include/frgb.h).
+
+    spec: dict with ``nodes``, ``elements`` ({'hex'|'pri'|'tet': conn}),
+    ``periodic`` (translation vectors) and ``bfaces`` ([(node ids, tag)]).
+    bcs: {tag: ('state', rho, u, v, w, p) | ('extrap',)}.
+    """
+
+    def __init__(self, spec, order, physics="euler", gamma=1.4, mu=0.0,
+                 prandtl=0.72, bcs=None, precision="fp64", device=0):
+        lib = load()
+        if hasattr(spec, "as_dict"):
+            spec = spec.as_dict()
+        nodes = np.ascontiguousarray(spec["nodes"], np.float64)
+        self._keep = [nodes]
+        ets = []
+        for name, conn in spec["elements"].items():
+            conn = np.ascontiguousarray(conn, np.int64)
+            if len(conn) == 0:
+                continue
+            self._keep.append(conn)
+            ets.append(EtypeDesc(ETYPES[name], len(conn),
+                                 conn.ctypes.data_as(C.POINTER(C.c_int64))))
+        et_arr = (EtypeDesc * len(ets))(*ets)
+        bfl = spec.get("bfaces", [])
+        bnodes = np.full((max(len(bfl), 1), 4), -1, np.int64)
+        btags = np.zeros(max(len(bfl), 1), np.int32)
+        for i, (ids, tag) in enumerate(bfl):
+            bnodes[i, :len(ids)] = ids
+            btags[i] = tag
+        self._keep += [bnodes, btags]
+        bcs = bcs or {}
+        bc_list = []
+        for tag, bc in bcs.items():
+            st = (C.c_double * 5)(*(bc[1:6] if bc[0] == "state" else [0] * 5))
+            bc_list.append(BCDesc(int(tag), BC_KIND[bc[0]], st))
+        bc_arr = (BCDesc * max(len(bc_list), 1))(*bc_list)
+        per = ((C.c_double * 3) * 3)()
+        pv = spec.get("periodic", [])
+        for i, T in enumerate(pv):
+            for k in range(3):
+                per[i][k] = float(T[k])
+        d = MeshDesc()
+        d.n_nodes = len(nodes)
+        d.nodes = nodes.ctypes.data_as(C.POINTER(C.c_double))
+        d.n_etypes = len(ets)
+        d.etypes = et_arr
+        d.order = int(order)
+        d.physics = PHYSICS[physics]
+        d.gamma, d.mu, d.prandtl = float(gamma), float(mu), float(prandtl)
+        d.n_periodic = len(pv)
+        d.periodic = per
+        d.n_bfaces = len(bfl)
+        d.bface_nodes = bnodes.ctypes.data_as(C.POINTER(C.c_int64))
+        d.bface_tags = btags.ctypes.data_as(C.POINTER(C.c_int))
+        d.n_bcs = len(bc_list)
+        d.bcs = bc_arr
+        d.precision = PRECISION[precision]
+        d.device = int(device)
+        h = C.c_void_p()
+        _check(lib.fr_mesh_create(C.byref(d), C.byref(h)))
+        self._h = h
+        self._keep = None
+        self.precision = precision
+        self.types = [t for t in ("hex", "pri", "tet") if self.info(t)[0] > 0]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().fr_mesh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self, etype):
+        ne, nu, nf = C.c_int64(), C.c_int(), C.c_int()
+        _check(load().fr_get_info(self._h, ETYPES[etype], C.byref(ne),
+                                  C.byref(nu), C.byref(nf)))
+        return ne.value, nu.value, nf.value
+
+    def points(self, etype):
+        ne, nu, _ = self.info(etype)
+        out = np.empty((ne, nu, 3), np.float64)
+        _check(load().fr_get_points(self._h, ETYPES[etype], _ptr(out)))
+        return out
+
+    def set_solution(self, u):
+        """u: {etype: (n_elem, nupts, 5) float64 host array}."""
+        for t, a in u.items():
+            a = np.ascontiguousarray(a, np.float64)
+            _check(load().fr_set_solution(self._h, ETYPES[t], _ptr(a)))
+
+    def get_solution(self):
+        out = {}
+        for t in self.types:
+            ne, nu, _ = self.info(t)
+            a = np.empty((ne, nu, 5), np.float64)
+            _check(load().fr_get_solution(self._h, ETYPES[t], _ptr(a)))
+            out[t] = a
+        return out
+
+    def set_solution_device(self, etype, tensor):
+        """tensor: CUDA float64 contiguous (n_elem, nupts, 5)."""
+        _check(load().fr_set_solution_device(self._h, ETYPES[etype],
+                                             C.c_void_p(tensor.data_ptr())))
+
+    def get_solution_device(self, etype, tensor):
+        _check(load().fr_get_solution_device(self._h, ETYPES[etype],
+                                             C.c_void_p(tensor.data_ptr())))
+
+    def rhs(self):
+        """One right-hand-side evaluation at the current solution."""
+        _check(load().fr_rhs(self._h))
+        out = {}
+        for t in self.types:
+            ne, nu, _ = self.info(t)
+            a = np.empty((ne, nu, 5), np.float64)
+            _check(load().fr_get_rhs(self._h, ETYPES[t], _ptr(a)))
+            out[t] = a
+        return out
+
+    def rhs_device(self):
+        """Right-hand side left on the device (no copy back)."""
+        _check(load().fr_rhs(self._h))
+
+    def rk_step(self, scheme, dt, nsteps=1):
+        _check(load().fr_rk_step(self._h, SCHEMES[scheme], float(dt),
+                                 int(nsteps)))
+
+    KERNEL_CLASSES = ("face_ucommon", "bnd_ucommon", "grad", "face_flux",
+                      "bnd_flux", "volume")
+
+    def profile_step(self, scheme, dt):
+        """One RK step with per-launch CUDA events: returns
+        {kernel class: (summed ms, launches)}."""
+        ms = np.zeros(6, np.float64)
+        n = np.zeros(6, np.int32)
+        _check(load().fr_profile_step(self._h, SCHEMES[scheme], float(dt),
+                                      _ptr(ms), _ptr(n)))
+        return {k: (float(ms[i]), int(n[i]))
+                for i, k in enumerate(self.KERNEL_CLASSES)}
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, a raw cudaStream_t int, or None."""
+        ptr = getattr(stream, "cuda_stream", stream)
+        _check(load().fr_set_stream(self._h, C.c_void_p(ptr or 0)))
+
+    def sync(self):
+        _check(load().fr_sync(self._h))
+
+    OPS = {"M0": 0, "D": 1, "LIFT": 2, "W": 3, "upts": 4, "fpts": 5}
+
+    def operator(self, etype, which):
+        """Reference-element data built by the library (FR_OP_*)."""
+        ne, nu, nf = self.info(etype)
+        shape = {"M0": (nf, nu), "D": (3, nu, nu), "LIFT": (nu, nf),
+                 "W": (nu,), "upts": (nu, 3), "fpts": (nf, 3)}[which]
+        out = np.empty(shape, np.float64)
+        _check(load().fr_get_operator(self._h, ETYPES[etype],
+                                      self.OPS[which], _ptr(out)))
+        return out
+
+    def metrics(self, etype):
+        ne, nu, _ = self.info(etype)
+        S = np.empty((ne, 9, nu), np.float64)
+        rj = np.empty((ne, nu), np.float64)
+        _check(load().fr_get_metrics(self._h, ETYPES[etype], _ptr(S),
+                                     _ptr(rj)))
+        return S, rj
+
+    def pair_counts(self):
+        a, b = C.c_int64(), C.c_int64()
+        _check(load().fr_get_pairs(self._h, C.byref(a), C.byref(b)))
+        return a.value, b.value

@@ -1,0 +1,823 @@
+// C ABI of the FR library: mesh set-up, device memory, kernel launch
+// sequences and CUDA-graph replay of Runge-Kutta steps.  See include/frgb.h.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <memory>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/frgb.h"
+#include "fr_kernels.cuh"
+#include "fr_mesh.hpp"
+
+using namespace frgb;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define CK(call)                                                        \
+  do {                                                                  \
+    cudaError_t e_ = (call);                                            \
+    if (e_ != cudaSuccess)                                              \
+      return fail(FR_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// Compile-time (nupts, nfpts) for every supported (element kind, order).
+template <class F>
+bool dispatch(int kind, int p, F&& f) {
+  switch (kind * 16 + p) {
+#define FR_CASE(K, P, NU, NF)                                              \
+  case K * 16 + P:                                                         \
+    f(std::integral_constant<int, NU>{}, std::integral_constant<int, NF>{}); \
+    return true;
+    FR_CASE(0, 1, 8, 24)
+    FR_CASE(0, 2, 27, 54)
+    FR_CASE(0, 3, 64, 96)
+    FR_CASE(0, 4, 125, 150)
+    FR_CASE(1, 1, 6, 18)
+    FR_CASE(1, 2, 18, 39)
+    FR_CASE(1, 3, 40, 68)
+    FR_CASE(1, 4, 75, 105)
+    FR_CASE(2, 1, 4, 12)
+    FR_CASE(2, 2, 10, 24)
+    FR_CASE(2, 3, 20, 40)
+    FR_CASE(2, 4, 35, 60)
+#undef FR_CASE
+  }
+  return false;
+}
+
+template <int NU>
+constexpr int epb() {
+  return NU >= 128 ? 1 : 128 / NU;
+}
+
+struct DevType {
+  int kind = 0, nu = 0, nf = 0;
+  long long ne = 0;
+  long long off_f = 0;      // offset of this type in the flux-point buffers
+  void* X = nullptr;        // solution register        [ne][5][nu]
+  void* Y = nullptr;        // stage register
+  void* A = nullptr;        // RK4 accumulator
+  void* R = nullptr;        // right-hand side (fr_rhs)
+  void* smat = nullptr;     // [ne][9][nu]
+  void* rcpdjac = nullptr;  // [ne][nu]
+  void* grad = nullptr;     // [ne][15][nu] (NS)
+  void* M0T = nullptr;
+  void* DT = nullptr;
+  void* LIFTT = nullptr;
+  void* NREF = nullptr;
+};
+
+void free_all(std::vector<void*>& v) {
+  for (void* p : v)
+    if (p) cudaFree(p);
+  v.clear();
+}
+
+}  // namespace
+
+struct fr_mesh {
+  int device = 0, precision = FR_FP64, physics = FR_EULER, order = 0;
+  bool host_only = false;
+  size_t wsize = 8;
+  cudaStream_t stream = nullptr, own_stream = nullptr;
+  double gamma = 1.4, mu = 0.0, prandtl = 0.72;
+  std::vector<HostType> host;
+  HostConn conn;
+  std::vector<DevType> types;
+  int type_of_kind[3] = {-1, -1, -1};
+  TypeTab tt{};
+  BCTab<double> bc64{};
+  BCTab<float> bc32{};
+  long long nf_total = 0;
+  void* uf = nullptr;
+  void* fc = nullptr;
+  void* du = nullptr;
+  void* gradf = nullptr;
+  int32_t* pl = nullptr;
+  int32_t* pr = nullptr;
+  void* pn = nullptr;
+  void* pmr = nullptr;
+  int32_t* bidx = nullptr;
+  int32_t* bbc = nullptr;
+  void* bn = nullptr;
+  int np = 0, nb = 0;
+  double* d_dt = nullptr;
+  int* d_flag = nullptr;
+  double h_dt = 0.0;
+  bool uf_valid = false;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  cudaStream_t graph_stream[2] = {nullptr, nullptr};
+  std::vector<void*> allocs;
+  void* d_staging = nullptr;   // host-layout FP64 staging for set/get
+  size_t staging_bytes = 0;
+
+  ~fr_mesh() {
+    for (int i = 0; i < 2; ++i)
+      if (graph[i]) cudaGraphExecDestroy(graph[i]);
+    free_all(allocs);
+    if (d_staging) cudaFree(d_staging);
+    if (own_stream) cudaStreamDestroy(own_stream);
+  }
+};
+
+namespace {
+
+template <typename T>
+int dev_upload(fr_mesh* m, const std::vector<double>& h, void** out) {
+  *out = nullptr;
+  if (h.empty()) return FR_OK;
+  std::vector<T> t(h.begin(), h.end());
+  CK(cudaMalloc(out, t.size() * sizeof(T)));
+  m->allocs.push_back(*out);
+  CK(cudaMemcpy(*out, t.data(), t.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return FR_OK;
+}
+
+int dev_upload_i32(fr_mesh* m, const std::vector<int32_t>& h, int32_t** out) {
+  *out = nullptr;
+  if (h.empty()) return FR_OK;
+  CK(cudaMalloc((void**)out, h.size() * sizeof(int32_t)));
+  m->allocs.push_back(*out);
+  CK(cudaMemcpy(*out, h.data(), h.size() * 4, cudaMemcpyHostToDevice));
+  return FR_OK;
+}
+
+int dev_zeros(fr_mesh* m, size_t bytes, void** out) {
+  *out = nullptr;
+  if (!bytes) return FR_OK;
+  CK(cudaMalloc(out, bytes));
+  m->allocs.push_back(*out);
+  CK(cudaMemset(*out, 0, bytes));
+  return FR_OK;
+}
+
+template <typename T>
+int setup_device(fr_mesh* m) {
+  int rc;
+  long long off = 0;
+  for (size_t t = 0; t < m->host.size(); ++t) {
+    const HostType& H = m->host[t];
+    DevType D;
+    D.kind = H.kind;
+    D.nu = H.ref.nupts;
+    D.nf = H.ref.nfpts;
+    D.ne = H.ne;
+    D.off_f = off;
+    off += D.ne * 5 * D.nf;
+    m->tt.nf[t] = D.nf;
+    m->tt.off_f[t] = D.off_f;
+    m->type_of_kind[D.kind] = int(t);
+    size_t sol = size_t(D.ne) * 5 * D.nu * sizeof(T);
+    if ((rc = dev_zeros(m, sol, &D.X))) return rc;
+    if ((rc = dev_zeros(m, sol, &D.Y))) return rc;
+    if ((rc = dev_zeros(m, sol, &D.A))) return rc;
+    if ((rc = dev_zeros(m, sol, &D.R))) return rc;
+    if (m->physics == FR_NAVIER_STOKES &&
+        (rc = dev_zeros(m, 3 * sol, &D.grad)))
+      return rc;
+    if ((rc = dev_upload<T>(m, H.smat, &D.smat))) return rc;
+    if ((rc = dev_upload<T>(m, H.rcpdjac, &D.rcpdjac))) return rc;
+    const RefElement& R = H.ref;
+    std::vector<double> m0t(size_t(D.nu) * D.nf), dt(3 * size_t(D.nu) * D.nu),
+        lt(size_t(D.nf) * D.nu);
+    for (int f = 0; f < D.nf; ++f)
+      for (int z = 0; z < D.nu; ++z) {
+        m0t[size_t(z) * D.nf + f] = R.M0[size_t(f) * D.nu + z];
+        lt[size_t(f) * D.nu + z] = R.LIFT[size_t(z) * D.nf + f];
+      }
+    for (int d = 0; d < 3; ++d)
+      for (int z = 0; z < D.nu; ++z)
+        for (int v = 0; v < D.nu; ++v)
+          dt[(size_t(d) * D.nu + v) * D.nu + z] =
+              R.D[(size_t(d) * D.nu + z) * D.nu + v];
+    if ((rc = dev_upload<T>(m, m0t, &D.M0T))) return rc;
+    if ((rc = dev_upload<T>(m, dt, &D.DT))) return rc;
+    if ((rc = dev_upload<T>(m, lt, &D.LIFTT))) return rc;
+    if ((rc = dev_upload<T>(m, R.fnorm, &D.NREF))) return rc;
+    m->types.push_back(D);
+  }
+  m->nf_total = off;
+  size_t fb = size_t(off) * sizeof(T);
+  if ((rc = dev_zeros(m, fb, &m->uf))) return rc;
+  if ((rc = dev_zeros(m, fb, &m->fc))) return rc;
+  if (m->physics == FR_NAVIER_STOKES) {
+    if ((rc = dev_zeros(m, fb, &m->du))) return rc;
+    if ((rc = dev_zeros(m, 3 * fb, &m->gradf))) return rc;
+  }
+  const HostConn& C = m->conn;
+  m->np = int(C.pl.size());
+  m->nb = int(C.bidx.size());
+  if ((rc = dev_upload_i32(m, C.pl, &m->pl))) return rc;
+  if ((rc = dev_upload_i32(m, C.pr, &m->pr))) return rc;
+  if ((rc = dev_upload<T>(m, C.pn, &m->pn))) return rc;
+  if ((rc = dev_upload<T>(m, C.pmr, &m->pmr))) return rc;
+  if ((rc = dev_upload_i32(m, C.bidx, &m->bidx))) return rc;
+  if ((rc = dev_upload_i32(m, C.bbc, &m->bbc))) return rc;
+  if ((rc = dev_upload<T>(m, C.bn, &m->bn))) return rc;
+  CK(cudaMalloc((void**)&m->d_dt, sizeof(double)));
+  m->allocs.push_back(m->d_dt);
+  CK(cudaMalloc((void**)&m->d_flag, sizeof(int)));
+  m->allocs.push_back(m->d_flag);
+  CK(cudaMemset(m->d_flag, 0, sizeof(int)));
+  return FR_OK;
+}
+
+template <typename T>
+Phys<T> phys(const fr_mesh* m) {
+  Phys<T> p;
+  p.gamma = T(m->gamma);
+  p.gm1 = T(m->gamma - 1.0);
+  p.mu = T(m->mu);
+  p.kappa = T(m->mu * m->gamma / m->prandtl);
+  return p;
+}
+
+template <typename T>
+const BCTab<T>& bctab(const fr_mesh* m);
+template <>
+const BCTab<double>& bctab<double>(const fr_mesh* m) {
+  return m->bc64;
+}
+template <>
+const BCTab<float>& bctab<float>(const fr_mesh* m) {
+  return m->bc32;
+}
+
+template <typename T>
+DenseOps<T> ops_of(const DevType& D) {
+  return DenseOps<T>{(const T*)D.M0T, (const T*)D.DT, (const T*)D.LIFTT,
+                     (const T*)D.NREF};
+}
+
+inline unsigned nblk(long long n, int b) { return unsigned((n + b - 1) / b); }
+
+template <typename T>
+void launch_interp(fr_mesh* m, cudaStream_t s) {
+  for (auto& D : m->types) {
+    T* uf = (T*)m->uf + D.off_f;
+    dispatch(D.kind, m->order, [&](auto nu, auto nf) {
+      constexpr int NU = decltype(nu)::value, NF = decltype(nf)::value;
+      constexpr int E = epb<NU>();
+      k_interp_dense<T, NU, NF, E><<<nblk(D.ne, E), E * NU, 0, s>>>(
+          D.ne, (const T*)D.X, ops_of<T>(D), uf);
+    });
+  }
+}
+
+// Optional per-launch event recorder used by fr_profile_step.
+struct Prof {
+  std::vector<int> cls;
+  std::vector<cudaEvent_t> ev;  // pairs (start, end)
+  void mark(int c, cudaStream_t s, bool start) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, s);
+    ev.push_back(e);
+    if (start) cls.push_back(c);
+  }
+};
+
+#define PROF_BEGIN(c) \
+  if (prof) prof->mark(c, s, true)
+#define PROF_END(c) \
+  if (prof) prof->mark(c, s, false)
+
+// Launch one RK stage (or a bare right-hand side when mode == 0).
+template <typename T>
+void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
+                  Prof* prof = nullptr) {
+  const bool ns = m->physics == FR_NAVIER_STOKES;
+  const Phys<T> ph = phys<T>(m);
+  const BCTab<T>& bc = bctab<T>(m);
+  const int tb = 256;
+  auto input = [&](const DevType& D) -> const T* {
+    if (mode == 0 || stage == 0) return (const T*)D.X;
+    return (const T*)D.Y;
+  };
+  if (ns) {
+    if (m->np) {
+      PROF_BEGIN(FR_KC_FACE_U);
+      k_face_ucommon<T><<<nblk(m->np, tb), tb, 0, s>>>(
+          m->np, m->pl, m->pr, (const T*)m->uf, (T*)m->du, m->tt);
+      PROF_END(FR_KC_FACE_U);
+    }
+    if (m->nb) {
+      PROF_BEGIN(FR_KC_BND_U);
+      k_bnd_ucommon<T><<<nblk(m->nb, tb), tb, 0, s>>>(
+          m->nb, m->bidx, m->bbc, (const T*)m->uf, (T*)m->du, m->tt, bc);
+      PROF_END(FR_KC_BND_U);
+    }
+    for (auto& D : m->types) {
+      dispatch(D.kind, m->order, [&](auto nu, auto nf) {
+        constexpr int NU = decltype(nu)::value, NF = decltype(nf)::value;
+        constexpr int E = epb<NU>();
+        size_t sm = size_t(E) * (5 * NU + 5 * NF + 15 * NU) * sizeof(T);
+        PROF_BEGIN(FR_KC_GRAD);
+        k_grad_dense<T, NU, NF, E><<<nblk(D.ne, E), E * NU, sm, s>>>(
+            D.ne, input(D), (const T*)m->du + D.off_f, (const T*)D.smat,
+            (const T*)D.rcpdjac, ops_of<T>(D), (T*)D.grad,
+            (T*)m->gradf + D.off_f * 3);
+        PROF_END(FR_KC_GRAD);
+      });
+    }
+  }
+  if (m->np) {
+    PROF_BEGIN(FR_KC_FACE_F);
+    if (ns)
+      k_face_flux<T, true><<<nblk(m->np, tb), tb, 0, s>>>(
+          m->np, m->pl, m->pr, (const T*)m->pn, (const T*)m->pmr,
+          (const T*)m->uf, (const T*)m->gradf, (T*)m->fc, m->tt, ph);
+    else
+      k_face_flux<T, false><<<nblk(m->np, tb), tb, 0, s>>>(
+          m->np, m->pl, m->pr, (const T*)m->pn, (const T*)m->pmr,
+          (const T*)m->uf, nullptr, (T*)m->fc, m->tt, ph);
+    PROF_END(FR_KC_FACE_F);
+  }
+  if (m->nb) {
+    PROF_BEGIN(FR_KC_BND_F);
+    if (ns)
+      k_bnd_flux<T, true><<<nblk(m->nb, tb), tb, 0, s>>>(
+          m->nb, m->bidx, m->bbc, (const T*)m->bn, (const T*)m->uf,
+          (const T*)m->gradf, (T*)m->fc, m->tt, ph, bc);
+    else
+      k_bnd_flux<T, false><<<nblk(m->nb, tb), tb, 0, s>>>(
+          m->nb, m->bidx, m->bbc, (const T*)m->bn, (const T*)m->uf, nullptr,
+          (T*)m->fc, m->tt, ph, bc);
+    PROF_END(FR_KC_BND_F);
+  }
+  for (auto& D : m->types) {
+    StageArgs<T> sa;
+    sa.mode = mode;
+    sa.stage = stage;
+    sa.X = (T*)D.X;
+    sa.A = (T*)D.A;
+    sa.Y = (T*)D.Y;
+    sa.out = (T*)D.R;
+    sa.dt = m->d_dt;
+    sa.flag = m->d_flag;
+    sa.uf_next = mode == 0 ? nullptr : (T*)m->uf + D.off_f;
+    dispatch(D.kind, m->order, [&](auto nu, auto nf) {
+      constexpr int NU = decltype(nu)::value, NF = decltype(nf)::value;
+      constexpr int E = epb<NU>();
+      size_t sm = size_t(E) * (15 * NU + 5 * NF) * sizeof(T);
+      PROF_BEGIN(FR_KC_VOL);
+      if (ns)
+        k_vol_dense<T, NU, NF, E, true><<<nblk(D.ne, E), E * NU, sm, s>>>(
+            D.ne, input(D), (const T*)D.grad, (const T*)m->fc + D.off_f,
+            (const T*)D.smat, (const T*)D.rcpdjac, ops_of<T>(D), ph, sa);
+      else
+        k_vol_dense<T, NU, NF, E, false><<<nblk(D.ne, E), E * NU, sm, s>>>(
+            D.ne, input(D), nullptr, (const T*)m->fc + D.off_f,
+            (const T*)D.smat, (const T*)D.rcpdjac, ops_of<T>(D), ph, sa);
+      PROF_END(FR_KC_VOL);
+    });
+  }
+}
+
+// layout conversion kernels: host layout [ne][nu][5] FP64 <-> [ne][5][nu] T
+template <typename T>
+__global__ void k_layout_in(long long n, int nu, const double* __restrict__ src,
+                            T* __restrict__ dst) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  long long e = i / (5 * nu);
+  int r = int(i - e * 5 * nu);
+  int k = r / nu, z = r - k * nu;
+  dst[i] = T(src[(e * nu + z) * 5 + k]);
+}
+
+template <typename T>
+__global__ void k_layout_out(long long n, int nu, const T* __restrict__ src,
+                             double* __restrict__ dst) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  long long e = i / (5 * nu);
+  int r = int(i - e * 5 * nu);
+  int k = r / nu, z = r - k * nu;
+  dst[(e * nu + z) * 5 + k] = double(src[i]);
+}
+
+DevType* type_ptr(fr_mesh* m, int etype) {
+  if (m->host_only) return nullptr;
+  if (etype < 0 || etype > 2 || m->type_of_kind[etype] < 0) return nullptr;
+  return &m->types[m->type_of_kind[etype]];
+}
+
+const HostType* host_ptr(const fr_mesh* m, int etype) {
+  if (etype < 0 || etype > 2 || m->type_of_kind[etype] < 0) return nullptr;
+  return &m->host[m->type_of_kind[etype]];
+}
+
+template <typename T>
+int set_solution_dev(fr_mesh* m, DevType& D, const double* dsrc) {
+  long long n = D.ne * 5 * D.nu;
+  k_layout_in<T><<<nblk(n, 256), 256, 0, m->stream>>>(n, D.nu, dsrc, (T*)D.X);
+  CK(cudaGetLastError());
+  m->uf_valid = false;
+  return FR_OK;
+}
+
+template <typename T>
+int get_dev(fr_mesh* m, const DevType& D, const void* src, double* ddst) {
+  long long n = D.ne * 5 * D.nu;
+  k_layout_out<T><<<nblk(n, 256), 256, 0, m->stream>>>(n, D.nu, (const T*)src,
+                                                       ddst);
+  CK(cudaGetLastError());
+  return FR_OK;
+}
+
+template <typename T>
+int ensure_uf(fr_mesh* m) {
+  if (m->uf_valid) return FR_OK;
+  launch_interp<T>(m, m->stream);
+  CK(cudaGetLastError());
+  m->uf_valid = true;
+  return FR_OK;
+}
+
+template <typename T>
+int do_rhs(fr_mesh* m) {
+  int rc = ensure_uf<T>(m);
+  if (rc) return rc;
+  CK(cudaMemsetAsync(m->d_flag, 0, sizeof(int), m->stream));
+  launch_stage<T>(m, m->stream, 0, 0);
+  CK(cudaGetLastError());
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, m->d_flag, sizeof(int), cudaMemcpyDeviceToHost,
+                     m->stream));
+  CK(cudaStreamSynchronize(m->stream));
+  if (flag) return fail(FR_ENONFINITE, "right-hand side is not finite");
+  return FR_OK;
+}
+
+template <typename T>
+int build_graph(fr_mesh* m, int scheme) {
+  cudaStream_t s = m->stream;
+  CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  const int nst = scheme == FR_RK4 ? 4 : 5;
+  for (int st = 0; st < nst; ++st) launch_stage<T>(m, s, scheme == FR_RK4 ? 1 : 2, st);
+  cudaGraph_t g;
+  cudaError_t e = cudaStreamEndCapture(s, &g);
+  if (e != cudaSuccess) return fail(FR_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  if (m->graph[scheme]) cudaGraphExecDestroy(m->graph[scheme]);
+  e = cudaGraphInstantiate(&m->graph[scheme], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(FR_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  m->graph_stream[scheme] = s;
+  return FR_OK;
+}
+
+template <typename T>
+int do_rk(fr_mesh* m, int scheme, double dt, int nsteps) {
+  int rc = ensure_uf<T>(m);
+  if (rc) return rc;
+  if (!m->graph[scheme] || m->graph_stream[scheme] != m->stream) {
+    if ((rc = build_graph<T>(m, scheme))) return rc;
+  }
+  m->h_dt = dt;
+  CK(cudaMemcpyAsync(m->d_dt, &m->h_dt, sizeof(double), cudaMemcpyHostToDevice,
+                     m->stream));
+  CK(cudaMemsetAsync(m->d_flag, 0, sizeof(int), m->stream));
+  for (int i = 0; i < nsteps; ++i) CK(cudaGraphLaunch(m->graph[scheme], m->stream));
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, m->d_flag, sizeof(int), cudaMemcpyDeviceToHost,
+                     m->stream));
+  CK(cudaStreamSynchronize(m->stream));
+  if (flag) return fail(FR_ENONFINITE, "a Runge-Kutta stage is not finite");
+  return FR_OK;
+}
+
+template <typename T>
+int do_profile(fr_mesh* m, int scheme, double dt, double* ms, int* launches) {
+  int rc = ensure_uf<T>(m);
+  if (rc) return rc;
+  m->h_dt = dt;
+  CK(cudaMemcpyAsync(m->d_dt, &m->h_dt, sizeof(double), cudaMemcpyHostToDevice,
+                     m->stream));
+  Prof prof;
+  const int nst = scheme == FR_RK4 ? 4 : 5;
+  for (int st = 0; st < nst; ++st)
+    launch_stage<T>(m, m->stream, scheme == FR_RK4 ? 1 : 2, st, &prof);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(m->stream));
+  for (int k = 0; k < FR_KC_COUNT; ++k) {
+    ms[k] = 0.0;
+    launches[k] = 0;
+  }
+  for (size_t i = 0; i < prof.cls.size(); ++i) {
+    float t = 0.f;
+    cudaEventElapsedTime(&t, prof.ev[2 * i], prof.ev[2 * i + 1]);
+    ms[prof.cls[i]] += t;
+    launches[prof.cls[i]] += 1;
+  }
+  for (cudaEvent_t e : prof.ev) cudaEventDestroy(e);
+  return FR_OK;
+}
+
+}  // namespace
+
+// ===================================================================== ABI
+extern "C" {
+
+const char* fr_last_error(void) { return g_err.c_str(); }
+
+int fr_mesh_create(const fr_mesh_desc* d, fr_mesh** out) {
+  if (!d || !out) return fail(FR_EINVAL, "null argument");
+  *out = nullptr;
+  if (d->order < 1 || d->order > 4) return fail(FR_EINVAL, "order must be 1..4");
+  if (d->physics != FR_EULER && d->physics != FR_NAVIER_STOKES)
+    return fail(FR_EINVAL, "unknown physics");
+  if (d->precision != FR_FP64 && d->precision != FR_FP32)
+    return fail(FR_EINVAL, "unknown precision");
+  if (d->n_bcs < 0 || d->n_bcs > kMaxBC) return fail(FR_EINVAL, "too many boundary conditions");
+  if (d->n_periodic < 0 || d->n_periodic > 3) return fail(FR_EINVAL, "n_periodic must be 0..3");
+  if (d->n_nodes <= 0 || !d->nodes) return fail(FR_EINVAL, "no nodes");
+  if (d->gamma <= 1.0) return fail(FR_EINVAL, "gamma must exceed 1");
+  if (d->physics == FR_NAVIER_STOKES && (d->mu < 0 || d->prandtl <= 0))
+    return fail(FR_EINVAL, "bad viscosity or Prandtl number");
+  std::unique_ptr<fr_mesh> m(new fr_mesh());
+  m->device = d->device;
+  m->precision = d->precision;
+  m->physics = d->physics;
+  m->order = d->order;
+  m->gamma = d->gamma;
+  m->mu = d->mu;
+  m->prandtl = d->prandtl > 0 ? d->prandtl : 0.72;
+  m->wsize = d->precision == FR_FP64 ? 8 : 4;
+  MeshInput in;
+  in.n_nodes = d->n_nodes;
+  in.nodes = d->nodes;
+  in.order = d->order;
+  bool seen[3] = {false, false, false};
+  for (int i = 0; i < d->n_etypes; ++i) {
+    const fr_etype_desc& t = d->etypes[i];
+    if (t.etype < 0 || t.etype > 2 || seen[t.etype])
+      return fail(FR_EINVAL, "bad or repeated element type");
+    if (t.n_elem < 0 || (t.n_elem > 0 && !t.conn)) return fail(FR_EINVAL, "bad connectivity");
+    seen[t.etype] = true;
+  }
+  for (int k = 0; k < 3; ++k)  // canonical type order: hex, prism, tet
+    for (int i = 0; i < d->n_etypes; ++i)
+      if (d->etypes[i].etype == k)
+        in.types.push_back({k, {d->etypes[i].n_elem, d->etypes[i].conn}});
+  for (int i = 0; i < d->n_periodic; ++i)
+    in.periodic.push_back({d->periodic[i][0], d->periodic[i][1], d->periodic[i][2]});
+  in.n_bfaces = d->n_bfaces;
+  in.bface_nodes = d->bface_nodes;
+  in.bface_tags = d->bface_tags;
+  if (d->n_bfaces > 0 && (!d->bface_nodes || !d->bface_tags))
+    return fail(FR_EINVAL, "boundary faces without nodes or tags");
+  for (int i = 0; i < d->n_bcs; ++i) {
+    const fr_bc_desc& b = d->bcs[i];
+    if (b.kind != FR_BC_STATE && b.kind != FR_BC_EXTRAPOLATE)
+      return fail(FR_EINVAL, "unknown boundary condition");
+    in.bc_tags.push_back(b.tag);
+    double rho = b.state[0], u = b.state[1], v = b.state[2], w = b.state[3],
+           p = b.state[4];
+    double cons[5] = {rho, rho * u, rho * v, rho * w,
+                      p / (d->gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w)};
+    m->bc64.kind[i] = b.kind;
+    m->bc32.kind[i] = b.kind;
+    for (int k = 0; k < 5; ++k) {
+      m->bc64.state[i][k] = cons[k];
+      m->bc32.state[i][k] = float(cons[k]);
+    }
+  }
+  bool emesh = false;
+  std::string err;
+  try {
+    err = build_mesh(in, m->host, m->conn, &emesh);
+  } catch (const std::exception& ex) {
+    return fail(FR_EINVAL, ex.what());
+  }
+  if (!err.empty()) return fail(emesh ? FR_EMESH : FR_EINVAL, err);
+  if (d->device < 0) {  // host-only handle: geometry and operators, no GPU
+    m->host_only = true;
+    for (size_t t = 0; t < m->host.size(); ++t) m->type_of_kind[m->host[t].kind] = int(t);
+    *out = m.release();
+    return FR_OK;
+  }
+  CK(cudaSetDevice(d->device));
+  CK(cudaStreamCreateWithFlags(&m->own_stream, cudaStreamNonBlocking));
+  m->stream = m->own_stream;
+  static bool consts_done[64] = {false};
+  int dev = d->device;
+  if (dev >= 0 && dev < 64 && !consts_done[dev]) {
+    const double a[4] = {970286171893.0 / 4311952581923.0,
+                         6584761158862.0 / 12103376702013.0,
+                         2251764453980.0 / 15575788980749.0,
+                         26877169314380.0 / 34165994151039.0};
+    const double b[5] = {1153189308089.0 / 22510343858157.0,
+                         1772645290293.0 / 4653164025191.0,
+                         -1672844663538.0 / 4480602732383.0,
+                         2114624349019.0 / 3568978502595.0,
+                         5198255086312.0 / 14908931495163.0};
+    CK(cudaMemcpyToSymbol(c_rk45_a, a, sizeof(a)));
+    CK(cudaMemcpyToSymbol(c_rk45_b, b, sizeof(b)));
+    consts_done[dev] = true;
+  }
+  int rc = m->precision == FR_FP64 ? setup_device<double>(m.get())
+                                   : setup_device<float>(m.get());
+  if (rc) return rc;
+  *out = m.release();
+  return FR_OK;
+}
+
+int fr_mesh_destroy(fr_mesh* m) {
+  if (!m) return FR_OK;
+  if (!m->host_only) {
+    cudaSetDevice(m->device);
+    if (m->stream) cudaStreamSynchronize(m->stream);
+  }
+  delete m;
+  return FR_OK;
+}
+
+int fr_get_info(const fr_mesh* m, int etype, int64_t* ne, int* nu, int* nf) {
+  if (!m) return fail(FR_EINVAL, "null mesh");
+  const HostType* H = host_ptr(m, etype);
+  if (ne) *ne = H ? H->ne : 0;
+  if (nu) *nu = H ? H->ref.nupts : 0;
+  if (nf) *nf = H ? H->ref.nfpts : 0;
+  return FR_OK;
+}
+
+int fr_get_points(const fr_mesh* m, int etype, double* xyz) {
+  if (!m || !xyz) return fail(FR_EINVAL, "null argument");
+  const HostType* H = host_ptr(m, etype);
+  if (!H) return fail(FR_EINVAL, "mesh has no elements of this type");
+  std::memcpy(xyz, H->upts_x.data(), H->upts_x.size() * sizeof(double));
+  return FR_OK;
+}
+
+static int ensure_staging(fr_mesh* m, size_t bytes) {
+  if (m->staging_bytes >= bytes) return FR_OK;
+  if (m->d_staging) {
+    cudaStreamSynchronize(m->stream);
+    cudaFree(m->d_staging);
+    m->d_staging = nullptr;
+    m->staging_bytes = 0;
+  }
+  CK(cudaMalloc(&m->d_staging, bytes));
+  m->staging_bytes = bytes;
+  return FR_OK;
+}
+
+// Host solution in: one copy into a device staging buffer (host layout,
+// FP64), then the layout kernel writes the element-major device register.
+int fr_set_solution(fr_mesh* m, int etype, const double* u) {
+  if (!m || !u) return fail(FR_EINVAL, "null argument");
+  DevType* D = type_ptr(m, etype);
+  if (!D) return fail(FR_EINVAL, "mesh has no elements of this type");
+  CK(cudaSetDevice(m->device));
+  size_t bytes = size_t(D->ne) * 5 * D->nu * sizeof(double);
+  int rc = ensure_staging(m, bytes);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(m->d_staging, u, bytes, cudaMemcpyHostToDevice, m->stream));
+  rc = m->precision == FR_FP64
+           ? set_solution_dev<double>(m, *D, (const double*)m->d_staging)
+           : set_solution_dev<float>(m, *D, (const double*)m->d_staging);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(m->stream));
+  return FR_OK;
+}
+
+static int get_host(const fr_mesh* mc, int etype, double* out, bool rhs) {
+  fr_mesh* m = const_cast<fr_mesh*>(mc);
+  if (!m || !out) return fail(FR_EINVAL, "null argument");
+  DevType* D = type_ptr(m, etype);
+  if (!D) return fail(FR_EINVAL, "mesh has no elements of this type");
+  CK(cudaSetDevice(m->device));
+  size_t bytes = size_t(D->ne) * 5 * D->nu * sizeof(double);
+  int rc = ensure_staging(m, bytes);
+  if (rc) return rc;
+  const void* src = rhs ? D->R : D->X;
+  rc = m->precision == FR_FP64
+           ? get_dev<double>(m, *D, src, (double*)m->d_staging)
+           : get_dev<float>(m, *D, src, (double*)m->d_staging);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(out, m->d_staging, bytes, cudaMemcpyDeviceToHost, m->stream));
+  CK(cudaStreamSynchronize(m->stream));
+  return FR_OK;
+}
+
+int fr_get_solution(const fr_mesh* m, int etype, double* u) {
+  return get_host(m, etype, u, false);
+}
+
+int fr_get_rhs(const fr_mesh* m, int etype, double* r) {
+  return get_host(m, etype, r, true);
+}
+
+int fr_set_solution_device(fr_mesh* m, int etype, const void* dptr) {
+  if (!m || !dptr) return fail(FR_EINVAL, "null argument");
+  DevType* D = type_ptr(m, etype);
+  if (!D) return fail(FR_EINVAL, "mesh has no elements of this type");
+  CK(cudaSetDevice(m->device));
+  return m->precision == FR_FP64
+             ? set_solution_dev<double>(m, *D, (const double*)dptr)
+             : set_solution_dev<float>(m, *D, (const double*)dptr);
+}
+
+int fr_get_solution_device(const fr_mesh* mc, int etype, void* dptr) {
+  fr_mesh* m = const_cast<fr_mesh*>(mc);
+  if (!m || !dptr) return fail(FR_EINVAL, "null argument");
+  DevType* D = type_ptr(m, etype);
+  if (!D) return fail(FR_EINVAL, "mesh has no elements of this type");
+  CK(cudaSetDevice(m->device));
+  return m->precision == FR_FP64
+             ? get_dev<double>(m, *D, D->X, (double*)dptr)
+             : get_dev<float>(m, *D, D->X, (double*)dptr);
+}
+
+int fr_rhs(fr_mesh* m) {
+  if (!m) return fail(FR_EINVAL, "null mesh");
+  if (m->host_only) return fail(FR_EINVAL, "host-only handle (device < 0)");
+  CK(cudaSetDevice(m->device));
+  return m->precision == FR_FP64 ? do_rhs<double>(m) : do_rhs<float>(m);
+}
+
+int fr_rk_step(fr_mesh* m, int scheme, double dt, int nsteps) {
+  if (!m) return fail(FR_EINVAL, "null mesh");
+  if (m->host_only) return fail(FR_EINVAL, "host-only handle (device < 0)");
+  if (scheme != FR_RK4 && scheme != FR_RK45) return fail(FR_EINVAL, "unknown scheme");
+  if (nsteps < 0) return fail(FR_EINVAL, "negative step count");
+  if (nsteps == 0) return FR_OK;
+  CK(cudaSetDevice(m->device));
+  return m->precision == FR_FP64 ? do_rk<double>(m, scheme, dt, nsteps)
+                                 : do_rk<float>(m, scheme, dt, nsteps);
+}
+
+int fr_profile_step(fr_mesh* m, int scheme, double dt, double* ms,
+                    int* launches) {
+  if (!m || !ms || !launches) return fail(FR_EINVAL, "null argument");
+  if (m->host_only) return fail(FR_EINVAL, "host-only handle (device < 0)");
+  if (scheme != FR_RK4 && scheme != FR_RK45) return fail(FR_EINVAL, "unknown scheme");
+  CK(cudaSetDevice(m->device));
+  return m->precision == FR_FP64 ? do_profile<double>(m, scheme, dt, ms, launches)
+                                 : do_profile<float>(m, scheme, dt, ms, launches);
+}
+
+int fr_set_stream(fr_mesh* m, void* s) {
+  if (!m) return fail(FR_EINVAL, "null mesh");
+  if (m->host_only) return fail(FR_EINVAL, "host-only handle (device < 0)");
+  CK(cudaSetDevice(m->device));
+  CK(cudaStreamSynchronize(m->stream));
+  m->stream = s ? (cudaStream_t)s : m->own_stream;
+  return FR_OK;
+}
+
+int fr_sync(fr_mesh* m) {
+  if (!m) return fail(FR_EINVAL, "null mesh");
+  if (m->host_only) return fail(FR_EINVAL, "host-only handle (device < 0)");
+  CK(cudaSetDevice(m->device));
+  CK(cudaStreamSynchronize(m->stream));
+  return FR_OK;
+}
+
+int fr_get_operator(const fr_mesh* m, int etype, int which, double* out) {
+  if (!m || !out) return fail(FR_EINVAL, "null argument");
+  const HostType* H = host_ptr(m, etype);
+  if (!H) return fail(FR_EINVAL, "mesh has no elements of this type");
+  const RefElement& R = H->ref;
+  const std::vector<double>* v = nullptr;
+  switch (which) {
+    case FR_OP_M0: v = &R.M0; break;
+    case FR_OP_D: v = &R.D; break;
+    case FR_OP_LIFT: v = &R.LIFT; break;
+    case FR_OP_WEIGHTS: v = &R.W; break;
+    case FR_OP_UPTS: v = &R.upts; break;
+    case FR_OP_FPTS: v = &R.fpts; break;
+    default: return fail(FR_EINVAL, "unknown operator");
+  }
+  std::memcpy(out, v->data(), v->size() * sizeof(double));
+  return FR_OK;
+}
+
+int fr_get_metrics(const fr_mesh* m, int etype, double* smat, double* rcpdjac) {
+  if (!m) return fail(FR_EINVAL, "null argument");
+  const HostType* H = host_ptr(m, etype);
+  if (!H) return fail(FR_EINVAL, "mesh has no elements of this type");
+  if (smat) std::memcpy(smat, H->smat.data(), H->smat.size() * sizeof(double));
+  if (rcpdjac) std::memcpy(rcpdjac, H->rcpdjac.data(), H->rcpdjac.size() * sizeof(double));
+  return FR_OK;
+}
+
+int fr_get_pairs(const fr_mesh* m, int64_t* n_interior, int64_t* n_boundary) {
+  if (!m) return fail(FR_EINVAL, "null argument");
+  if (n_interior) *n_interior = int64_t(m->conn.pl.size());
+  if (n_boundary) *n_boundary = int64_t(m->conn.bidx.size());
+  return FR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,480 @@
+// FR right-hand-side kernels (PyFR v2.0.3, Section 2) -- generic dense form.
+//
+// Device layouts, per element type, element-major with the variable index
+// between the element and the point index so that one warp reads 32
+// consecutive points of one variable:
+//   solution / stage registers   [ne][5][nupts]
+//   flux-point traces            [ne][5][nfpts]   (one buffer for all types)
+//   gradients at solution pts    [ne][3*5][nupts]
+//   gradients at flux pts        [ne][3*5][nfpts]
+//   metric S = det J J^{-1}      [ne][9][nupts]  and 1/det J [ne][nupts]
+// Operators are stored transposed so that consecutive threads read
+// consecutive entries: M0T[nupts][nfpts], DT[3][nupts][nupts] (DT[d][v][z] =
+// d l_v/dx~_d at x_z), LIFTT[nfpts][nupts].
+#pragma once
+#include <cstdint>
+
+#include "fr_phys.cuh"
+
+namespace frgb {
+
+constexpr int kMaxBC = 8;
+
+// Per-type regions of the shared flux-point buffers.
+struct TypeTab {
+  int nf[3];
+  long long off_f[3];  // offset of the type's [ne][5][nf] region
+};
+
+template <typename T>
+struct BCTab {
+  int kind[kMaxBC];      // 0 = prescribed state, 1 = extrapolate
+  T state[kMaxBC][5];    // conserved ghost state
+};
+
+template <typename T>
+struct DenseOps {
+  const T* M0T;    // [nu][nf]
+  const T* DT;     // [3][nu][nu]
+  const T* LIFTT;  // [nf][nu]
+  const T* NREF;   // [nf][3]
+};
+
+// Time-integration epilogue of the volume kernel.
+//   mode 0: write R to out
+//   mode 1: classical RK4 stage `stage`  (registers X, A, Y)
+//   mode 2: RK4(3)5[2R+] stage `stage`   (registers X, Y)
+template <typename T>
+struct StageArgs {
+  int mode, stage;
+  T* X;
+  T* A;
+  T* Y;
+  T* out;
+  const double* dt;  // device scalar
+  int* flag;         // non-finite flag (bit 0)
+  T* uf_next;        // flux-point buffer for the next stage (or nullptr)
+};
+
+__constant__ double c_rk45_a[4];  // sub-diagonal a_{i+1,i}
+__constant__ double c_rk45_b[5];
+
+__device__ __forceinline__ void decode_fp(int32_t code, const TypeTab& tt,
+                                          int* t, long long* e, int* f) {
+  *t = code >> 29;
+  long long local = code & ((1 << 29) - 1);
+  int nf = tt.nf[*t];
+  *e = local / (5 * nf);
+  *f = int(local - *e * 5 * nf);
+}
+
+// index of variable v, point f, element e in a [ne][nv][nf] region of type t
+__device__ __forceinline__ long long fp_index(const TypeTab& tt, int t,
+                                              long long e, int f, int nv,
+                                              int v) {
+  long long base = tt.off_f[t] / 5 * nv;  // region scales with the var count
+  return base + (e * nv + v) * tt.nf[t] + f;
+}
+
+// RK epilogue for one point: R[5] -> registers; returns the next stage value
+template <typename T>
+__device__ __forceinline__ void stage_update(const StageArgs<T>& a,
+                                             long long idx0, long long vstr,
+                                             const T u[5], T R[5], T s[5]) {
+  bool bad = false;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) bad |= !isfinite(R[k]);
+  if (bad) atomicOr(a.flag, 1);
+  if (a.mode == 0) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      a.out[idx0 + k * vstr] = R[k];
+      s[k] = u[k];
+    }
+    return;
+  }
+  const T dt = T(*a.dt);
+  if (a.mode == 1) {
+    const int st = a.stage;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      long long i = idx0 + k * vstr;
+      if (st == 0) {
+        T x = u[k];
+        a.A[i] = x + dt * T(1.0 / 6.0) * R[k];
+        s[k] = x + dt * T(0.5) * R[k];
+        a.Y[i] = s[k];
+      } else if (st < 3) {
+        T x = a.X[i];
+        a.A[i] = a.A[i] + dt * T(1.0 / 3.0) * R[k];
+        s[k] = x + (st == 1 ? dt * T(0.5) : dt) * R[k];
+        a.Y[i] = s[k];
+      } else {
+        s[k] = a.A[i] + dt * T(1.0 / 6.0) * R[k];
+        a.X[i] = s[k];
+      }
+    }
+    return;
+  }
+  // mode 2: two-register RK4(3)5[2R+]
+  const int st = a.stage;
+  const T b = T(c_rk45_b[st]);
+  const T am = st < 4 ? T(c_rk45_a[st]) - b : T(0);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    long long i = idx0 + k * vstr;
+    T x = (st == 0 ? u[k] : a.X[i]) + b * dt * R[k];
+    a.X[i] = x;
+    if (st < 4) {
+      s[k] = x + am * dt * R[k];
+      a.Y[i] = s[k];
+    } else {
+      s[k] = x;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Eq. (disu): u_f = M0 u, one element per EPB group of threads.
+template <typename T, int NU, int NF, int EPB>
+__global__ void __launch_bounds__(EPB* NU)
+    k_interp_dense(long long ne, const T* __restrict__ u, DenseOps<T> ops,
+                   T* __restrict__ uf) {
+  __shared__ T us[EPB][5][NU];
+  const int le = threadIdx.x / NU, z = threadIdx.x % NU;
+  const long long e = (long long)blockIdx.x * EPB + le;
+  if (e < ne) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) us[le][k][z] = u[(e * 5 + k) * NU + z];
+  }
+  __syncthreads();
+  if (e >= ne) return;
+  for (int f = z; f < NF; f += NU) {
+    T acc[5] = {0, 0, 0, 0, 0};
+    for (int q = 0; q < NU; ++q) {
+      T m = ops.M0T[q * NF + f];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) acc[k] += m * us[le][k][q];
+    }
+#pragma unroll
+    for (int k = 0; k < 5; ++k) uf[(e * 5 + k) * NF + f] = acc[k];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Eq. (comm_flux) on interior pairs: transformed common normal flux written
+// to both sides (|S^T n~| F on L, -|S^T n~| F on R).  NS subtracts the BR1
+// average of both sides' viscous normal fluxes.
+template <typename T, bool NS>
+__global__ void k_face_flux(int np, const int32_t* __restrict__ pl,
+                            const int32_t* __restrict__ pr,
+                            const T* __restrict__ pn, const T* __restrict__ pmr,
+                            const T* __restrict__ uf, const T* __restrict__ gf,
+                            T* __restrict__ fc, TypeTab tt, Phys<T> ph) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  int tl, tr, fl, frr;
+  long long el, er;
+  decode_fp(pl[i], tt, &tl, &el, &fl);
+  decode_fp(pr[i], tt, &tr, &er, &frr);
+  T ul[5], ur[5], n[3];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    ul[k] = uf[fp_index(tt, tl, el, fl, 5, k)];
+    ur[k] = uf[fp_index(tt, tr, er, frr, 5, k)];
+  }
+  n[0] = pn[4 * i];
+  n[1] = pn[4 * i + 1];
+  n[2] = pn[4 * i + 2];
+  T ml = pn[4 * i + 3], mr = pmr[i];
+  T F[5];
+  rusanov(ul, ur, n, ph, F);
+  if (NS) {
+    T gl[3][5], gr[3][5];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        gl[j][k] = gf[fp_index(tt, tl, el, fl, 15, j * 5 + k)];
+        gr[j][k] = gf[fp_index(tt, tr, er, frr, 15, j * 5 + k)];
+      }
+    viscous_normal_acc(ul, gl, n, ph, T(-0.5), F);
+    viscous_normal_acc(ur, gr, n, ph, T(-0.5), F);
+  }
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    fc[fp_index(tt, tl, el, fl, 5, k)] = ml * F[k];
+    fc[fp_index(tt, tr, er, frr, 5, k)] = -mr * F[k];
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void ghost_state(const BCTab<T>& bc, int b,
+                                            const T ul[5], T ur[5]) {
+  if (bc.kind[b] == 0) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) ur[k] = bc.state[b][k];
+  } else {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) ur[k] = ul[k];
+  }
+}
+
+// Boundary flux points: outside state from the boundary condition, outside
+// gradient equal to the inside one.
+template <typename T, bool NS>
+__global__ void k_bnd_flux(int nb, const int32_t* __restrict__ bidx,
+                           const int32_t* __restrict__ bbc,
+                           const T* __restrict__ bn, const T* __restrict__ uf,
+                           const T* __restrict__ gf, T* __restrict__ fc,
+                           TypeTab tt, Phys<T> ph, BCTab<T> bc) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nb) return;
+  int t, f;
+  long long e;
+  decode_fp(bidx[i], tt, &t, &e, &f);
+  T ul[5], ur[5], n[3] = {bn[4 * i], bn[4 * i + 1], bn[4 * i + 2]};
+#pragma unroll
+  for (int k = 0; k < 5; ++k) ul[k] = uf[fp_index(tt, t, e, f, 5, k)];
+  ghost_state(bc, bbc[i], ul, ur);
+  T F[5];
+  rusanov(ul, ur, n, ph, F);
+  if (NS) {
+    T g[3][5];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int k = 0; k < 5; ++k) g[j][k] = gf[fp_index(tt, t, e, f, 15, j * 5 + k)];
+    viscous_normal_acc(ul, g, n, ph, T(-0.5), F);
+    viscous_normal_acc(ur, g, n, ph, T(-0.5), F);
+  }
+  T m = bn[4 * i + 3];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) fc[fp_index(tt, t, e, f, 5, k)] = m * F[k];
+}
+
+// NS: common solution u^C = (u- + u+)/2; stores u^C - u_f on both sides.
+template <typename T>
+__global__ void k_face_ucommon(int np, const int32_t* __restrict__ pl,
+                               const int32_t* __restrict__ pr,
+                               const T* __restrict__ uf, T* __restrict__ du,
+                               TypeTab tt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  int tl, tr, fl, frr;
+  long long el, er;
+  decode_fp(pl[i], tt, &tl, &el, &fl);
+  decode_fp(pr[i], tt, &tr, &er, &frr);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    long long il = fp_index(tt, tl, el, fl, 5, k);
+    long long ir = fp_index(tt, tr, er, frr, 5, k);
+    T a = uf[il], b = uf[ir];
+    T h = T(0.5) * (b - a);
+    du[il] = h;
+    du[ir] = -h;
+  }
+}
+
+template <typename T>
+__global__ void k_bnd_ucommon(int nb, const int32_t* __restrict__ bidx,
+                              const int32_t* __restrict__ bbc,
+                              const T* __restrict__ uf, T* __restrict__ du,
+                              TypeTab tt, BCTab<T> bc) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nb) return;
+  int t, f;
+  long long e;
+  decode_fp(bidx[i], tt, &t, &e, &f);
+  T ul[5], ur[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) ul[k] = uf[fp_index(tt, t, e, f, 5, k)];
+  ghost_state(bc, bbc[i], ul, ur);
+#pragma unroll
+  for (int k = 0; k < 5; ++k)
+    du[fp_index(tt, t, e, f, 5, k)] = T(0.5) * (ur[k] - ul[k]);
+}
+
+// ---------------------------------------------------------------------------
+// NS gradient path: corrected reference gradient D u + LIFT (n~ du), physical
+// gradient (1/J) S^T grad~ u at solution points, and its interpolation to
+// the flux points.
+template <typename T, int NU, int NF, int EPB>
+__global__ void __launch_bounds__(EPB* NU)
+    k_grad_dense(long long ne, const T* __restrict__ u,
+                 const T* __restrict__ du, const T* __restrict__ smat,
+                 const T* __restrict__ rcpdjac, DenseOps<T> ops,
+                 T* __restrict__ grad, T* __restrict__ gradf) {
+  extern __shared__ unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int le = threadIdx.x / NU, z = threadIdx.x % NU;
+  const long long e = (long long)blockIdx.x * EPB + le;
+  T* us = sm + le * (5 * NU + 5 * NF + 15 * NU);
+  T* ds = us + 5 * NU;
+  T* gs = ds + 5 * NF;
+  if (e < ne) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) us[k * NU + z] = u[(e * 5 + k) * NU + z];
+    for (int f = z; f < NF; f += NU)
+#pragma unroll
+      for (int k = 0; k < 5; ++k) ds[k * NF + f] = du[(e * 5 + k) * NF + f];
+  }
+  __syncthreads();
+  if (e < ne) {
+    T gref[3][5];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int k = 0; k < 5; ++k) gref[d][k] = T(0);
+    for (int q = 0; q < NU; ++q) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        T w = ops.DT[(d * NU + q) * NU + z];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) gref[d][k] += w * us[k * NU + q];
+      }
+    }
+    for (int f = 0; f < NF; ++f) {
+      T l = ops.LIFTT[f * NU + z];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        T w = l * ops.NREF[f * 3 + d];
+        if (w != T(0)) {
+#pragma unroll
+          for (int k = 0; k < 5; ++k) gref[d][k] += w * ds[k * NF + f];
+        }
+      }
+    }
+    T S[3][3];
+#pragma unroll
+    for (int r = 0; r < 9; ++r) S[r / 3][r % 3] = smat[(e * 9 + r) * NU + z];
+    T rj = rcpdjac[e * NU + z];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        T g = rj * (S[0][j] * gref[0][k] + S[1][j] * gref[1][k] +
+                    S[2][j] * gref[2][k]);
+        grad[(e * 15 + j * 5 + k) * NU + z] = g;
+        gs[(j * 5 + k) * NU + z] = g;
+      }
+  }
+  __syncthreads();
+  if (e >= ne) return;
+  for (int f = z; f < NF; f += NU) {
+    T acc[15];
+#pragma unroll
+    for (int c = 0; c < 15; ++c) acc[c] = T(0);
+    for (int q = 0; q < NU; ++q) {
+      T m = ops.M0T[q * NF + f];
+#pragma unroll
+      for (int c = 0; c < 15; ++c) acc[c] += m * gs[c * NU + q];
+    }
+#pragma unroll
+    for (int c = 0; c < 15; ++c) gradf[(e * 15 + c) * NF + f] = acc[c];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Volume kernel: transformed flux f~ = S F at solution points, Eq. (FRfinal)
+// divergence  sum_d D_d f~_d + LIFT (F^C - n~.M0 f~), negdivconf R = -div/J,
+// the RK epilogue, and the next stage's u_f = M0 u_next.
+template <typename T, int NU, int NF, int EPB, bool NS>
+__global__ void __launch_bounds__(EPB* NU)
+    k_vol_dense(long long ne, const T* __restrict__ u,
+                const T* __restrict__ grad, const T* __restrict__ fc,
+                const T* __restrict__ smat, const T* __restrict__ rcpdjac,
+                DenseOps<T> ops, Phys<T> ph, StageArgs<T> sa) {
+  extern __shared__ unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int le = threadIdx.x / NU, z = threadIdx.x % NU;
+  const long long e = (long long)blockIdx.x * EPB + le;
+  T* ft = sm + le * (15 * NU + 5 * NF);  // [3][5][NU]
+  T* jm = ft + 15 * NU;                  // [5][NF]
+  T uz[5];
+  if (e < ne) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) uz[k] = u[(e * 5 + k) * NU + z];
+    T F[3][5];
+    euler_flux(uz, ph, F);
+    if (NS) {
+      T g[3][5];
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) g[j][k] = grad[(e * 15 + j * 5 + k) * NU + z];
+      viscous_flux_acc(uz, g, ph, T(-1), F);
+    }
+    T S[3][3];
+#pragma unroll
+    for (int r = 0; r < 9; ++r) S[r / 3][r % 3] = smat[(e * 9 + r) * NU + z];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int k = 0; k < 5; ++k)
+        ft[(d * 5 + k) * NU + z] =
+            S[d][0] * F[0][k] + S[d][1] * F[1][k] + S[d][2] * F[2][k];
+  }
+  __syncthreads();
+  if (e < ne) {
+    for (int f = z; f < NF; f += NU) {
+      T fn[5] = {0, 0, 0, 0, 0};
+      T nr[3] = {ops.NREF[f * 3], ops.NREF[f * 3 + 1], ops.NREF[f * 3 + 2]};
+      for (int q = 0; q < NU; ++q) {
+        T m = ops.M0T[q * NF + f];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          if (nr[d] == T(0)) continue;
+          T w = m * nr[d];
+#pragma unroll
+          for (int k = 0; k < 5; ++k) fn[k] += w * ft[(d * 5 + k) * NU + q];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 5; ++k) jm[k * NF + f] = fc[(e * 5 + k) * NF + f] - fn[k];
+    }
+  }
+  __syncthreads();
+  T s[5];
+  if (e < ne) {
+    T div[5] = {0, 0, 0, 0, 0};
+    for (int q = 0; q < NU; ++q) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        T w = ops.DT[(d * NU + q) * NU + z];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) div[k] += w * ft[(d * 5 + k) * NU + q];
+      }
+    }
+    for (int f = 0; f < NF; ++f) {
+      T l = ops.LIFTT[f * NU + z];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) div[k] += l * jm[k * NF + f];
+    }
+    T rj = rcpdjac[e * NU + z];
+    T R[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) R[k] = -div[k] * rj;
+    stage_update(sa, e * 5 * NU + z, NU, uz, R, s);
+  }
+  if (sa.uf_next == nullptr) return;
+  __syncthreads();  // ft no longer read: reuse it for the next stage value
+  if (e < ne) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) ft[k * NU + z] = s[k];
+  }
+  __syncthreads();
+  if (e >= ne) return;
+  for (int f = z; f < NF; f += NU) {
+    T acc[5] = {0, 0, 0, 0, 0};
+    for (int q = 0; q < NU; ++q) {
+      T m = ops.M0T[q * NF + f];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) acc[k] += m * ft[k * NU + q];
+    }
+#pragma unroll
+    for (int k = 0; k < 5; ++k) sa.uf_next[(e * 5 + k) * NF + f] = acc[k];
+  }
+}
+
+}  // namespace frgb

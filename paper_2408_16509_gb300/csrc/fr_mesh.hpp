@@ -1,0 +1,62 @@
+// Host-side mesh geometry and interface pairing for the FR library.
+//
+// Section 2 of the paper: the domain is a conforming tessellation; each
+// element is the image of a reference element under x = M_n(x~) with
+// Jacobian J; the transformed flux is f~ = J J^{-1} f = S f.  Flux points of
+// adjoining elements conform.  Section 3.4: for linear elements the metric
+// terms follow from the vertices alone.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "fr_ref.hpp"
+
+namespace frgb {
+
+struct HostType {
+  int kind = 0;
+  int64_t ne = 0;
+  RefElement ref;
+  std::vector<int64_t> conn;     // [ne][nv]
+  std::vector<double> verts;     // [ne][nv][3]
+  std::vector<double> upts_x;    // [ne][nupts][3]
+  std::vector<double> smat;      // [ne][9][nupts]   S[i][j] = row i, col j
+  std::vector<double> rcpdjac;   // [ne][nupts]
+  std::vector<double> fpts_x;    // [ne][nfpts][3]
+  std::vector<double> fnvec;     // [ne][nfpts][3]  S^T n~ at flux points
+};
+
+// One side of a flux-point pair: element type in bits 29..30, offset of
+// variable 0 (e * 5 * nfpts + f) in the low 29 bits.
+inline int32_t encode_fp(int t, int64_t e, int nf, int f) {
+  return int32_t((int64_t(t) << 29) | (e * 5 * nf + f));
+}
+
+struct HostConn {
+  std::vector<int32_t> pl, pr;   // interior pairs (sorted by pl)
+  std::vector<double> pn;        // [np][4]  unit normal from L side, |S^T n~| L
+  std::vector<double> pmr;       // [np]     |S^T n~| on the R side
+  std::vector<int32_t> bidx;     // boundary flux points
+  std::vector<int32_t> bbc;      // boundary-condition index per point
+  std::vector<double> bn;        // [nb][4]
+};
+
+struct MeshInput {
+  int64_t n_nodes = 0;
+  const double* nodes = nullptr;
+  int order = 0;
+  std::vector<std::pair<int, std::pair<int64_t, const int64_t*>>> types;
+  std::vector<std::array<double, 3>> periodic;
+  int64_t n_bfaces = 0;
+  const int64_t* bface_nodes = nullptr;  // [n][4], -1 pads triangles
+  const int* bface_tags = nullptr;
+  std::vector<int> bc_tags;              // tag of bc index i
+};
+
+// Returns an empty string on success, else an error message.  ``err_mesh``
+// is set when the failure is a non-conforming / unmatched mesh.
+std::string build_mesh(const MeshInput& in, std::vector<HostType>& types,
+                       HostConn& conn, bool* err_mesh);
+
+}  // namespace frgb

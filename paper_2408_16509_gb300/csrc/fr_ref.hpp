@@ -1,0 +1,64 @@
+// Reference-element data for the FR library (host side, FP64).
+//
+// Builds, for each element type and order p, the point sets and operator
+// matrices of the Flux Reconstruction method (PyFR v2.0.3, Section 2):
+//   M0   [nfpts][nupts]   interpolation to flux points, Eq. (disu)
+//   D    [3][nupts][nupts] derivative of the nodal basis, Eq. (FRfinal)
+//   LIFT [nupts][nfpts]   divergence of the DG correction function g_s at
+//                         the solution points, Eq. (FRfinal)
+// and, for the hexahedron, the 1D factors used by the sum-factorised kernels.
+#pragma once
+#include <array>
+#include <cstdint>
+#include <vector>
+
+namespace frgb {
+
+enum ElemKind { EK_HEX = 0, EK_PRI = 1, EK_TET = 2 };
+
+struct RefFace {
+  bool tri;                    // triangle (else quadrilateral)
+  int nv;                      // 3 or 4 vertices
+  int verts[4];                // local vertex ids
+  double origin[3], ds[3], dt[3];  // x~ = origin + s ds + t dt
+  double normal[3];            // reference unit outward normal
+  double scale;                // |ds x dt|
+};
+
+struct RefElement {
+  int kind = 0, p = 0, nverts = 0, nupts = 0, nfpts = 0, nfaces = 0;
+  std::vector<RefFace> faces;
+  std::vector<double> upts;        // [nupts][3]
+  std::vector<double> fpts;        // [nfpts][3]
+  std::vector<int> fpts_face;      // [nfpts]
+  std::vector<int> face_start;     // [nfaces+1]
+  std::vector<double> fnorm;       // [nfpts][3]
+  std::vector<double> M0;          // [nfpts][nupts]
+  std::vector<double> D;           // [3][nupts][nupts]
+  std::vector<double> LIFT;        // [nupts][nfpts]
+  std::vector<double> W;           // [nupts]  integration weights
+  std::vector<double> vdm_inv;     // [nupts][nupts] nodal <- modal
+  // hexahedron only: 1D factors on the Gauss-Legendre points x1
+  std::vector<double> x1;          // [p+1]
+  std::vector<double> d1;          // [p+1][p+1]  l_m'(x_a)
+  std::vector<double> lm, lp;      // [p+1]  l_m(-1), l_m(+1)
+  std::vector<double> gl, gr;      // [p+1]  correction derivative weights:
+                                   //  -g_L'(x_a) on x=-1, g_R'(x_a) on x=+1
+  // vertex map of the element type
+  void shape(const double* x, double* N) const;            // N[nverts]
+  void dshape(const double* x, double* dN) const;          // dN[3][nverts]
+  // orthonormal basis (modal) at points
+  void basis(int npts, const double* x, double* out) const;           // [npts][nm]
+  void grad(int npts, const double* x, double* out) const;            // [3][npts][nm]
+};
+
+RefElement make_ref(int kind, int p);
+
+// 1D helpers (exposed for unit use)
+void gauss_legendre(int n, double* x, double* w);
+void gauss_lobatto(int n, double* x);
+double jacobi_p(int n, double a, double b, double x);
+double jacobi_dp(int n, double a, double b, double x);
+bool invert(int n, const double* A, double* Ainv);
+
+}  // namespace frgb

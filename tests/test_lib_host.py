@@ -1,0 +1,117 @@
+"""CPU tests of the C-ABI library: it loads, exports every declared symbol,
+and its host-side set-up (points, operators, metrics, interface pairing,
+mesh validation) agrees with the independently written oracle.  No GPU is
+touched: handles are created with device = -1 (host-only)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2408_16509_gb300 as fr
+from frinputs import box_hex, mixed_box
+from oracle.mesh import FRMesh as OracleMesh
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    fr.build()
+
+
+def _declared():
+    names = []
+    inc = os.path.join(ROOT, "include")
+    for f in sorted(os.listdir(inc)):
+        if f.endswith(".h"):
+            txt = open(os.path.join(inc, f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?\w+\s*\**\s+(fr_\w+)\s*\(",
+                                txt, flags=re.M)
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(fr.build())
+    names = _declared()
+    assert "fr_rhs" in names and "fr_rk_step" in names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_compute_calls_refuse_host_only_handles():
+    g = fr.FRMesh(box_hex((2, 2, 2)), 2, device=-1)
+    with pytest.raises(fr.FRError) as e:
+        g.rhs()
+    assert e.value.name == "FR_EINVAL"
+
+
+SPECS = {
+    "hex": lambda: box_hex((3, 2, 2), perturb=0.1),
+    "mixed": lambda: mixed_box(n=3, x_pri=0.34, x_tet=0.67, perturb=0.05),
+}
+
+
+@pytest.mark.parametrize("name", list(SPECS))
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_host_setup_matches_oracle(name, p):
+    spec = SPECS[name]()
+    bcs = {k: ("state", 1.0, 0.0, 0.0, 0.0, 1.0) for k in range(6)}
+    g = fr.FRMesh(spec, p, bcs=bcs, device=-1)
+    o = OracleMesh(spec.as_dict(), p)
+    assert g.types == o.types
+    for t in g.types:
+        el = o.el[t]
+        assert np.abs(g.operator(t, "upts") - el.upts).max() < 1e-15
+        assert np.abs(g.operator(t, "fpts") - el.fpts).max() < 1e-15
+        assert np.abs(g.operator(t, "M0") - el.M0).max() < 1e-13
+        for d in range(3):
+            assert np.abs(g.operator(t, "D")[d] - el.D[d]).max() < 1e-13
+        assert np.abs(g.operator(t, "LIFT") - el.LIFT).max() < 5e-13
+        assert np.abs(g.operator(t, "W") - el.W).max() < 1e-13
+        assert np.abs(g.points(t) - o.upts_x[t]).max() < 1e-14
+        S, rj = g.metrics(t)
+        So = o.S_u[t].reshape(o.ne[t], -1, 9).transpose(0, 2, 1)
+        assert np.abs(S - So).max() < 1e-14
+        assert np.abs(rj * o.detJ[t] - 1).max() < 1e-13
+    npair, nb = g.pair_counts()
+    assert npair == len(o.pair_l) and nb == len(o.bnd_g)
+
+
+def test_nonconforming_mesh_is_rejected():
+    spec = box_hex((2, 2, 2), periodic=(0, 1))
+    spec.bfaces = []
+    with pytest.raises(fr.FRError) as e:
+        fr.FRMesh(spec, 2, device=-1)
+    assert e.value.name == "FR_EMESH"
+
+
+def test_inverted_element_is_rejected():
+    spec = box_hex((2, 2, 2))
+    conn = spec.elements["hex"].copy()
+    conn[0] = conn[0][[4, 5, 6, 7, 0, 1, 2, 3]]     # mirrored: det J < 0
+    spec.elements = {"hex": conn}
+    with pytest.raises(fr.FRError) as e:
+        fr.FRMesh(spec, 2, device=-1)
+    assert e.value.name == "FR_EMESH"
+
+
+def test_bad_arguments():
+    spec = box_hex((2, 2, 2))
+    with pytest.raises(fr.FRError):
+        fr.FRMesh(spec, 9, device=-1)
+    with pytest.raises(fr.FRError):
+        fr.FRMesh(spec, 2, gamma=1.0, device=-1)
+    spec2 = box_hex((2, 2, 2), periodic=(0, 1))
+    # z faces listed with a tag that has no boundary condition
+    with pytest.raises(fr.FRError):
+        fr.FRMesh(spec2, 2, device=-1)
+
+
+def test_single_element_periodic_with_itself():
+    spec = box_hex((1, 1, 1))
+    g = fr.FRMesh(spec, 2, device=-1)
+    o = OracleMesh(spec.as_dict(), 2)
+    assert g.pair_counts() == (len(o.pair_l), 0)
