@@ -122,25 +122,114 @@ def config(precision):
 
 
 # ------------------------------------------------------ byte/flop models
-def kernel_models(nu, nf, ne, w, np_, nb):
-    """Compulsory DRAM bytes per launch of each kernel class (RK45 stage
-    i > 0, Navier-Stokes): see the design doc, kernel table."""
-    per_elem = {
-        "grad": w * (5 * nu + 5 * nf + 10 * nu + 15 * nu + 15 * nf),
-        "volume": w * (5 * nu + 15 * nu + 5 * nf + 10 * nu + 5 * nu
-                       + 10 * nu + 5 * nf),
+FP64_TFLOPS_PROBE = 1.058   # measured DFMA throughput on this GB300 pool
+FP32_TFLOPS_PROBE = 77.8    # measured FFMA throughput on this GB300 pool
+
+
+def kernel_models(nu, nf, ne, w, wr, npair):
+    """Algorithmic DRAM bytes and floating-point operations per launch of
+    each kernel class for an RK4(3)5[2R+] stage i > 0 of the Navier-Stokes
+    right-hand side on hexahedra (sum-factorised operators), N = p + 1.
+    w: bytes of a trace/stage value, wr: bytes of a solution register."""
+    n = round(nu ** (1.0 / 3.0))
+    bytes_ = {
+        # u(5) + metrics(10) + du(5 per flux pt) in, grad(15) + gradf(15) out
+        "grad": ne * (w * (5 * nu + 10 * nu + 5 * nf + 15 * nu + 15 * nf)),
+        # u(5) + grad(15) + metrics(10) + F^C(5/fpt) in; Y and u_f out;
+        # solution register X in and out
+        "volume": ne * (w * (5 * nu + 15 * nu + 10 * nu + 5 * nf + 5 * nu
+                             + 5 * nf) + wr * 10 * nu),
+        "face_ucommon": npair * (w * 20 + 8),
+        "face_flux": npair * (w * (2 * 20 + 5 + 10) + 8),
     }
-    per_pair = {
-        "face_ucommon": w * 20 + 8,
-        "face_flux": w * (2 * 20 + 5 + 10) + 8,
+    flops = {
+        "grad": ne * (2 * nu * (15 * n + 30 + 45) + 15 * nu
+                      + 2 * nf * 15 * n),
+        "volume": ne * (nu * (30 + 150 + 90 + 2 * 5 * (3 * n + 6) + 25)
+                        + 2 * nf * 5 * n + 5 * nf + 2 * nf * 5 * n),
+        "face_ucommon": npair * 10,
+        "face_flux": npair * 330,
     }
-    return {"grad": per_elem["grad"] * ne, "volume": per_elem["volume"] * ne,
-            "face_ucommon": per_pair["face_ucommon"] * np_,
-            "face_flux": per_pair["face_flux"] * np_}
+    return bytes_, flops
+
+
+def roofline(prof, models, peaks, src, precision):
+    """Roofline record of the dominant kernel class: the bound is whichever
+    of DRAM bytes / HBM peak and flops / arithmetic peak takes longer."""
+    bytes_, flops = models
+    dom = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
+    t = prof[dom][0] / prof[dom][1] * 1e-3
+    b, f = bytes_.get(dom), flops.get(dom)
+    bw = b / t / 1e9 if b else None
+    fl = f / t / 1e12 if f else None
+    if precision == "fp64":
+        fpeak, fsrc = FP64_TFLOPS_PROBE, "FP64 FMA probe on this pool"
+    else:
+        fpeak, fsrc = FP32_TFLOPS_PROBE, "FP32 FMA probe on this pool"
+    t_mem = b / (peaks["hbm_gbs"] * 1e9) if b else 0.0
+    t_alu = f / (fpeak * 1e12) if f else 0.0
+    if t_alu > t_mem:
+        out = {"kernel": dom, "bound": "alu", "achieved": fl, "peak": fpeak,
+               "unit": "TFLOP/s", "frac": fl / fpeak, "traffic": None,
+               "peak_source": fsrc}
+    else:
+        out = {"kernel": dom, "bound": "hbm", "achieved": bw,
+               "peak": peaks["hbm_gbs"], "unit": "GB/s",
+               "frac": bw / peaks["hbm_gbs"], "traffic": None,
+               "peak_source": src + " hbm_gbs (MEASURED_PEAKS.json)"}
+    out.update({"launches_per_step": prof[dom][1], "kernel_ms": t * 1e3,
+                "algorithmic_bytes": b, "algorithmic_flops": f,
+                "achieved_gbs": bw, "achieved_tflops": fl,
+                "attainable_ms": max(t_mem, t_alu) * 1e3})
+    return out
 
 
 # ------------------------------------------------------------ our arm
+def measure(fr, torch, precision, steps, warmup, device, dist):
+    spec = workload_spec(N_CELLS)
+    mesh = fr.FRMesh(spec, ORDER, physics="ns", gamma=1.4, mu=1.0 / RE,
+                     prandtl=PR, precision=precision, device=device)
+    stream = torch.cuda.Stream(device=device)
+    mesh.set_stream(stream)
+    x = mesh.points("hex")
+    ne, nu, nf = mesh.info("hex")
+    u0 = tgv(x.reshape(-1, 3)).reshape(ne, nu, 5)
+    mesh.set_solution({"hex": u0})
+    for _ in range(warmup):             # the first one builds the CUDA graph
+        mesh.rk_step("rk45", DT, 1)
+    mesh.set_solution({"hex": u0})
+    sampler = ClockSampler(device)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    mesh.rk_step("rk45", DT, steps)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = t0.elapsed_time(t1)
+    if dist:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+        dist.barrier()
+    final = mesh.get_solution()["hex"]
+    prof = {}
+    reps = 3
+    for _ in range(reps):
+        for k, (t, n) in mesh.profile_step("rk45", DT).items():
+            a = prof.setdefault(k, [0.0, 0])
+            a[0] += t / reps
+            a[1] = n
+    return mesh, u0, ms, clocks, prof, final
+
+
 def run_ours(args):
+    import ctypes
+
     import torch
 
     import paper_2408_16509_gb300 as fr
@@ -154,88 +243,48 @@ def run_ours(args):
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
     fr.build()
-    spec = workload_spec(N_CELLS)
-    mesh = fr.FRMesh(spec, ORDER, physics="ns", gamma=1.4, mu=1.0 / RE,
-                     prandtl=PR, precision=args.precision, device=local)
-    stream = torch.cuda.Stream(device=local)
-    mesh.set_stream(stream)
-    x = mesh.points("hex")
+    peaks, src = _peaks()
+    mesh, u0, ms, clocks, prof, final = measure(
+        fr, torch, args.precision, args.steps, args.warmup, local, dist)
     ne, nu, nf = mesh.info("hex")
-    u0 = tgv(x.reshape(-1, 3)).reshape(ne, nu, 5)
-    mesh.set_solution({"hex": u0})
-    npts = ne * nu
-    units_per_step = npts * 5 * STAGES
-    # warm-up (builds the CUDA graph)
-    for _ in range(args.warmup):
-        mesh.rk_step("rk45", DT, 1)
-    sampler = ClockSampler(local)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    sampler.start()
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    mesh.rk_step("rk45", DT, args.steps)
-    t1.record(stream)
-    torch.cuda.synchronize()
-    clocks = sampler.stop()
-    ms = t0.elapsed_time(t1)
-    if dist:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-        dist.barrier()
+    units_per_step = ne * nu * 5 * STAGES
     value = units_per_step * args.steps * world / (ms * 1e-3) / 1e9
-    # per-kernel device times of one step, launched one by one with events
-    prof = {}
-    reps = 3
-    for _ in range(reps):
-        for k, (t, n) in mesh.profile_step("rk45", DT).items():
-            a = prof.setdefault(k, [0.0, 0])
-            a[0] += t / reps
-            a[1] = n
     launches_per_step = sum(n for _, n in prof.values())
-    # end-to-end through the C ABI with pinned host buffers
+    # end-to-end through the C ABI with pinned host buffers: every step
+    # copies the state in, runs one RK step and copies the state out
+    lib = fr.load()
     host_in = torch.from_numpy(np.ascontiguousarray(u0)).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
-    hin = host_in.numpy()
-    hout = host_out.numpy()
-    e2e_steps = max(2, min(args.steps, 10))
+    hin, hout = host_in.numpy(), host_out.numpy()
+    e2e_steps = max(3, min(args.steps, 10))
     torch.cuda.synchronize()
     w0 = time.perf_counter()
-    import ctypes
-    lib = fr.load()
     for _ in range(e2e_steps):
         rc = lib.fr_set_solution(mesh._h, 0, hin.ctypes.data_as(ctypes.c_void_p))
         rc |= lib.fr_rk_step(mesh._h, 1, DT, 1)
-        rc |= lib.fr_get_solution(mesh._h, 0, hout.ctypes.data_as(ctypes.c_void_p))
+        rc |= lib.fr_get_solution(mesh._h, 0,
+                                  hout.ctypes.data_as(ctypes.c_void_p))
         if rc:
             raise RuntimeError(lib.fr_last_error().decode())
     e2e_s = time.perf_counter() - w0
+    if dist:
+        tt = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
     e2e = units_per_step * e2e_steps * world / e2e_s / 1e9
-    # roofline of the dominant kernel
-    peaks, src = _peaks()
+    npair, _ = mesh.pair_counts()
     w = 8 if args.precision == "fp64" else 4
-    npair, nb = mesh.pair_counts()
-    models = kernel_models(nu, nf, ne, w, npair, nb)
-    dom = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
-    dom_ms = prof[dom][0] / prof[dom][1]
-    bytes_per_launch = models.get(dom)
-    achieved = bytes_per_launch / (dom_ms * 1e-3) / 1e9 if bytes_per_launch else None
-    roof = {"kernel": dom, "bound": "hbm", "achieved": achieved,
-            "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"] if achieved else None,
-            "traffic": None, "peak_source": src,
-            "kernel_ms": dom_ms,
-            "algorithmic_bytes_per_launch": bytes_per_launch}
+    wr = 4 if args.precision == "fp32" else 8
+    roof = roofline(prof, kernel_models(nu, nf, ne, w, wr, npair), peaks,
+                    src, args.precision)
     line = {
         "metric": "GDOF-stage/s per GB300 (NS FR RHS + RK update)",
         "value": value, "unit": "GDOF-stage/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "f32",
+        "dtype": {"fp64": "f64", "fp32": "f32",
+                  "mixed": "f32 (f64 RK registers)"}[args.precision],
         "data": "synthetic (seeded perturbed mesh, analytic TGV state)",
         "config": config(args.precision),
         "clocks": clocks,
@@ -246,6 +295,35 @@ def run_ours(args):
         "kernel_ms_per_step": {k: v[0] for k, v in prof.items() if v[1]},
         "roofline": roof,
     }
+    mesh.close()
+    if args.variants and world == 1:
+        line["variants"] = {}
+        for prec in ("fp64", "fp32", "mixed"):
+            if prec == args.precision:
+                continue
+            m2, _, ms2, _, prof2, fin2 = measure(
+                fr, torch, prec, args.steps, args.warmup, local, None)
+            w2 = 8 if prec == "fp64" else 4
+            wr2 = 4 if prec == "fp32" else 8
+            if args.precision == "fp64":
+                ref, oth = final, fin2
+            else:
+                ref, oth = fin2, final
+            d = (oth - ref).reshape(-1, 5)
+            r = ref.reshape(-1, 5)
+            den = np.maximum(np.linalg.norm(r, axis=0),
+                             np.linalg.norm(r[:, 0]))
+            line["variants"][prec] = {
+                "value": units_per_step * args.steps / (ms2 * 1e-3) / 1e9,
+                "ms_per_step": ms2 / args.steps,
+                "rel_l2_vs_fp64_after_steps": (np.linalg.norm(d, axis=0)
+                                               / den).tolist(),
+                "roofline": roofline(
+                    prof2, kernel_models(nu, nf, ne, w2, wr2, npair), peaks,
+                    src, prec),
+                "kernel_ms_per_step": {k: v[0] for k, v in prof2.items()
+                                       if v[1]}}
+            m2.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if rank == 0:
@@ -325,7 +403,10 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="fp64",
+                    choices=["fp64", "fp32", "mixed"])
+    ap.add_argument("--variants", type=int, default=1,
+                    help="also time the other precision modes (N=1 only)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

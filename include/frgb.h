@@ -47,7 +47,10 @@ enum {
 
 enum { FR_HEX8 = 0, FR_PRI6 = 1, FR_TET4 = 2 };
 enum { FR_EULER = 0, FR_NAVIER_STOKES = 1 };
-enum { FR_FP64 = 0, FR_FP32 = 1 };
+/* FR_FP64: everything in FP64.  FR_FP32: everything in FP32.
+ * FR_MIXED: traces, fluxes, operators and stage values in FP32, the RK
+ * solution and accumulator registers in FP64 (hexahedral meshes). */
+enum { FR_FP64 = 0, FR_FP32 = 1, FR_MIXED = 2 };
 enum { FR_BC_STATE = 0, FR_BC_EXTRAPOLATE = 1 };
 enum { FR_RK4 = 0, FR_RK45 = 1 };
 
@@ -83,7 +86,7 @@ typedef struct {
   const int* bface_tags;          /* [n_bfaces] */
   int n_bcs;                      /* <= 8 */
   const fr_bc_desc* bcs;
-  int precision;                  /* FR_FP64 or FR_FP32 (storage + compute) */
+  int precision;                  /* FR_FP64, FR_FP32 or FR_MIXED */
   int device;                     /* CUDA device ordinal; < 0 builds a
                                      host-only handle (geometry, points and
                                      operators; no GPU is touched and the
@@ -146,6 +149,14 @@ enum { FR_KC_FACE_U = 0,  /* NS common solution at interior flux points */
        FR_KC_COUNT = 6 };
 int fr_profile_step(fr_mesh* mesh, int scheme, double dt, double* ms,
                     int* launches);
+
+/* Kernel family for hexahedra: FR_VARIANT_SUMFACT applies the operators
+ * line by line (1D factors of the tensor-product basis), FR_VARIANT_DENSE
+ * applies the full operator matrices as for prisms and tetrahedra;
+ * FR_VARIANT_AUTO (default) is the sum-factorised family.  Both give the
+ * same result up to rounding. */
+enum { FR_VARIANT_AUTO = 0, FR_VARIANT_DENSE = 1, FR_VARIANT_SUMFACT = 2 };
+int fr_set_kernel_variant(fr_mesh* mesh, int variant);
 
 /* Kernels and copies of the handle run on this stream (cudaStream_t);
  * NULL selects the handle's own stream. */

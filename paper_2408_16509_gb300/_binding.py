@@ -16,7 +16,8 @@ ERRORS = {-1: "FR_EINVAL", -2: "FR_ENOMEM", -3: "FR_ECUDA", -4: "FR_EMESH",
           -5: "FR_ENONFINITE", -6: "FR_EFILTER", -7: "FR_ETIMEOUT"}
 ETYPES = {"hex": 0, "pri": 1, "tet": 2}
 PHYSICS = {"euler": 0, "ns": 1}
-PRECISION = {"fp64": 0, "fp32": 1}
+PRECISION = {"fp64": 0, "fp32": 1, "mixed": 2}
+VARIANTS = {"auto": 0, "dense": 1, "sumfact": 2}
 SCHEMES = {"rk4": 0, "rk45": 1}
 BC_KIND = {"state": 0, "extrap": 1}
 
@@ -86,6 +87,7 @@ def load():
         "fr_get_metrics": (I, [P, I, P, P]),
         "fr_get_pairs": (I, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "fr_profile_step": (I, [P, I, D, P, P]),
+        "fr_set_kernel_variant": (I, [P, I]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -248,6 +250,10 @@ class FRMesh:
                                       _ptr(ms), _ptr(n)))
         return {k: (float(ms[i]), int(n[i]))
                 for i, k in enumerate(self.KERNEL_CLASSES)}
+
+    def set_variant(self, name):
+        """Kernel family for hexahedra: 'auto', 'dense' or 'sumfact'."""
+        _check(load().fr_set_kernel_variant(self._h, VARIANTS[name]))
 
     def set_stream(self, stream):
         """stream: a torch.cuda.Stream, a raw cudaStream_t int, or None."""

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/frgb.h"
+#include "fr_hex.cuh"
 #include "fr_kernels.cuh"
 #include "fr_mesh.hpp"
 
@@ -75,6 +76,8 @@ struct DevType {
   void* DT = nullptr;
   void* LIFTT = nullptr;
   void* NREF = nullptr;
+  HexOps<double> hx64{};
+  HexOps<float> hx32{};
 };
 
 void free_all(std::vector<void*>& v) {
@@ -88,7 +91,8 @@ void free_all(std::vector<void*>& v) {
 struct fr_mesh {
   int device = 0, precision = FR_FP64, physics = FR_EULER, order = 0;
   bool host_only = false;
-  size_t wsize = 8;
+  size_t wsize = 8;   // bytes of a trace / flux / stage value
+  size_t rsize = 8;   // bytes of a solution-register value
   cudaStream_t stream = nullptr, own_stream = nullptr;
   double gamma = 1.4, mu = 0.0, prandtl = 0.72;
   std::vector<HostType> host;
@@ -117,6 +121,8 @@ struct fr_mesh {
   bool uf_valid = false;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   cudaStream_t graph_stream[2] = {nullptr, nullptr};
+  int variant = FR_VARIANT_AUTO;
+  int graph_variant[2] = {-1, -1};
   std::vector<void*> allocs;
   void* d_staging = nullptr;   // host-layout FP64 staging for set/get
   size_t staging_bytes = 0;
@@ -162,6 +168,22 @@ int dev_zeros(fr_mesh* m, size_t bytes, void** out) {
 }
 
 template <typename T>
+HexOps<T> hex_ops(const RefElement& R) {
+  HexOps<T> h{};
+  const int n = R.p + 1;
+  for (int a = 0; a < n; ++a) {
+    for (int m = 0; m < n; ++m) h.d1[a][m] = T(R.d1[a * n + m]);
+    h.lm[a] = T(R.lm[a]);
+    h.lp[a] = T(R.lp[a]);
+    h.gl[a] = T(R.gl[a]);
+    h.gr[a] = T(R.gr[a]);
+  }
+  return h;
+}
+
+// T: storage/compute type of traces, fluxes and stage values;
+// TR: type of the RK solution and accumulator registers (X, A).
+template <typename T, typename TR>
 int setup_device(fr_mesh* m) {
   int rc;
   long long off = 0;
@@ -177,13 +199,13 @@ int setup_device(fr_mesh* m) {
     m->tt.nf[t] = D.nf;
     m->tt.off_f[t] = D.off_f;
     m->type_of_kind[D.kind] = int(t);
-    size_t sol = size_t(D.ne) * 5 * D.nu * sizeof(T);
-    if ((rc = dev_zeros(m, sol, &D.X))) return rc;
-    if ((rc = dev_zeros(m, sol, &D.Y))) return rc;
-    if ((rc = dev_zeros(m, sol, &D.A))) return rc;
-    if ((rc = dev_zeros(m, sol, &D.R))) return rc;
+    size_t n = size_t(D.ne) * 5 * D.nu;
+    if ((rc = dev_zeros(m, n * sizeof(TR), &D.X))) return rc;
+    if ((rc = dev_zeros(m, n * sizeof(T), &D.Y))) return rc;
+    if ((rc = dev_zeros(m, n * sizeof(TR), &D.A))) return rc;
+    if ((rc = dev_zeros(m, n * sizeof(T), &D.R))) return rc;
     if (m->physics == FR_NAVIER_STOKES &&
-        (rc = dev_zeros(m, 3 * sol, &D.grad)))
+        (rc = dev_zeros(m, 3 * n * sizeof(T), &D.grad)))
       return rc;
     if ((rc = dev_upload<T>(m, H.smat, &D.smat))) return rc;
     if ((rc = dev_upload<T>(m, H.rcpdjac, &D.rcpdjac))) return rc;
@@ -204,6 +226,10 @@ int setup_device(fr_mesh* m) {
     if ((rc = dev_upload<T>(m, dt, &D.DT))) return rc;
     if ((rc = dev_upload<T>(m, lt, &D.LIFTT))) return rc;
     if ((rc = dev_upload<T>(m, R.fnorm, &D.NREF))) return rc;
+    if (D.kind == EK_HEX) {
+      D.hx64 = hex_ops<double>(R);
+      D.hx32 = hex_ops<float>(R);
+    }
     m->types.push_back(D);
   }
   m->nf_total = off;
@@ -254,6 +280,17 @@ const BCTab<float>& bctab<float>(const fr_mesh* m) {
 }
 
 template <typename T>
+const HexOps<T>& hexops(const DevType& D);
+template <>
+const HexOps<double>& hexops<double>(const DevType& D) {
+  return D.hx64;
+}
+template <>
+const HexOps<float>& hexops<float>(const DevType& D) {
+  return D.hx32;
+}
+
+template <typename T>
 DenseOps<T> ops_of(const DevType& D) {
   return DenseOps<T>{(const T*)D.M0T, (const T*)D.DT, (const T*)D.LIFTT,
                      (const T*)D.NREF};
@@ -261,10 +298,74 @@ DenseOps<T> ops_of(const DevType& D) {
 
 inline unsigned nblk(long long n, int b) { return unsigned((n + b - 1) / b); }
 
-template <typename T>
+// hexahedron kernels: N = p + 1 solution points per line
+template <class F>
+bool hex_dispatch(int p, F&& f) {
+  switch (p) {
+    case 1: f(std::integral_constant<int, 2>{}); return true;
+    case 2: f(std::integral_constant<int, 3>{}); return true;
+    case 3: f(std::integral_constant<int, 4>{}); return true;
+    case 4: f(std::integral_constant<int, 5>{}); return true;
+  }
+  return false;
+}
+
+template <int N>
+constexpr int hex_epb() {
+  return (N * N * N) >= 256 ? 1 : 256 / (N * N * N);
+}
+
+template <typename T, int N>
+constexpr size_t hex_vol_smem() {
+  return size_t(hex_epb<N>()) * (15 * N * N * N + 30 * N * N) * sizeof(T);
+}
+
+template <typename T, int N>
+constexpr size_t hex_grad_smem() {
+  return size_t(hex_epb<N>()) * (20 * N * N * N + 30 * N * N) * sizeof(T);
+}
+
+bool use_hex(const fr_mesh* m, const DevType& D) {
+  return D.kind == EK_HEX && m->variant != FR_VARIANT_DENSE;
+}
+
+// Opt in to > 48 KB of dynamic shared memory where a kernel needs it.  Runs
+// once per handle outside any stream capture.
+template <typename T, typename TR>
+int prepare_kernels(fr_mesh* m) {
+  for (auto& D : m->types) {
+    if (D.kind != EK_HEX) continue;
+    hex_dispatch(m->order, [&](auto n) {
+      constexpr int N = decltype(n)::value;
+      constexpr int E = hex_epb<N>();
+      cudaFuncSetAttribute(k_hex_vol<T, TR, N, E, false>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(hex_vol_smem<T, N>()));
+      cudaFuncSetAttribute(k_hex_vol<T, TR, N, E, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(hex_vol_smem<T, N>()));
+      cudaFuncSetAttribute(k_hex_grad<T, TR, N, E>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(hex_grad_smem<T, N>()));
+    });
+  }
+  CK(cudaGetLastError());
+  return FR_OK;
+}
+
+template <typename T, typename TR>
 void launch_interp(fr_mesh* m, cudaStream_t s) {
   for (auto& D : m->types) {
     T* uf = (T*)m->uf + D.off_f;
+    if (use_hex(m, D)) {
+      hex_dispatch(m->order, [&](auto n) {
+        constexpr int N = decltype(n)::value;
+        constexpr int E = hex_epb<N>();
+        k_hex_interp<T, TR, N, E><<<nblk(D.ne, E), E * N * N * N, 0, s>>>(
+            D.ne, (const TR*)D.X, hexops<T>(D), uf);
+      });
+      continue;
+    }
     dispatch(D.kind, m->order, [&](auto nu, auto nf) {
       constexpr int NU = decltype(nu)::value, NF = decltype(nf)::value;
       constexpr int E = epb<NU>();
@@ -293,17 +394,16 @@ struct Prof {
   if (prof) prof->mark(c, s, false)
 
 // Launch one RK stage (or a bare right-hand side when mode == 0).
-template <typename T>
+template <typename T, typename TR>
 void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
                   Prof* prof = nullptr) {
   const bool ns = m->physics == FR_NAVIER_STOKES;
   const Phys<T> ph = phys<T>(m);
   const BCTab<T>& bc = bctab<T>(m);
   const int tb = 256;
-  auto input = [&](const DevType& D) -> const T* {
-    if (mode == 0 || stage == 0) return (const T*)D.X;
-    return (const T*)D.Y;
-  };
+  // stage input: the solution register X for a bare RHS and the first
+  // stage, the stage register Y afterwards
+  const bool from_x = (mode == 0 || stage == 0);
   if (ns) {
     if (m->np) {
       PROF_BEGIN(FR_KC_FACE_U);
@@ -318,17 +418,31 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
       PROF_END(FR_KC_BND_U);
     }
     for (auto& D : m->types) {
-      dispatch(D.kind, m->order, [&](auto nu, auto nf) {
-        constexpr int NU = decltype(nu)::value, NF = decltype(nf)::value;
-        constexpr int E = epb<NU>();
-        size_t sm = size_t(E) * (5 * NU + 5 * NF + 15 * NU) * sizeof(T);
-        PROF_BEGIN(FR_KC_GRAD);
-        k_grad_dense<T, NU, NF, E><<<nblk(D.ne, E), E * NU, sm, s>>>(
-            D.ne, input(D), (const T*)m->du + D.off_f, (const T*)D.smat,
-            (const T*)D.rcpdjac, ops_of<T>(D), (T*)D.grad,
-            (T*)m->gradf + D.off_f * 3);
-        PROF_END(FR_KC_GRAD);
-      });
+      const T* du = (const T*)m->du + D.off_f;
+      T* gradf = (T*)m->gradf + D.off_f * 3;
+      PROF_BEGIN(FR_KC_GRAD);
+      if (use_hex(m, D)) {
+        hex_dispatch(m->order, [&](auto n) {
+          constexpr int N = decltype(n)::value;
+          constexpr int E = hex_epb<N>();
+          k_hex_grad<T, TR, N, E>
+              <<<nblk(D.ne, E), E * N * N * N, hex_grad_smem<T, N>(), s>>>(
+                  D.ne, from_x ? nullptr : (const T*)D.Y, (const TR*)D.X, du,
+                  (const T*)D.smat, (const T*)D.rcpdjac, hexops<T>(D),
+                  (T*)D.grad, gradf);
+        });
+      } else {
+        dispatch(D.kind, m->order, [&](auto nu, auto nf) {
+          constexpr int NU = decltype(nu)::value, NF = decltype(nf)::value;
+          constexpr int E = epb<NU>();
+          size_t sm = size_t(E) * (5 * NU + 5 * NF + 15 * NU) * sizeof(T);
+          k_grad_dense<T, NU, NF, E><<<nblk(D.ne, E), E * NU, sm, s>>>(
+              D.ne, from_x ? (const T*)D.X : (const T*)D.Y, du,
+              (const T*)D.smat, (const T*)D.rcpdjac, ops_of<T>(D), (T*)D.grad,
+              gradf);
+        });
+      }
+      PROF_END(FR_KC_GRAD);
     }
   }
   if (m->np) {
@@ -356,31 +470,53 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
     PROF_END(FR_KC_BND_F);
   }
   for (auto& D : m->types) {
-    StageArgs<T> sa;
-    sa.mode = mode;
-    sa.stage = stage;
-    sa.X = (T*)D.X;
-    sa.A = (T*)D.A;
-    sa.Y = (T*)D.Y;
-    sa.out = (T*)D.R;
-    sa.dt = m->d_dt;
-    sa.flag = m->d_flag;
-    sa.uf_next = mode == 0 ? nullptr : (T*)m->uf + D.off_f;
-    dispatch(D.kind, m->order, [&](auto nu, auto nf) {
-      constexpr int NU = decltype(nu)::value, NF = decltype(nf)::value;
-      constexpr int E = epb<NU>();
-      size_t sm = size_t(E) * (15 * NU + 5 * NF) * sizeof(T);
-      PROF_BEGIN(FR_KC_VOL);
-      if (ns)
-        k_vol_dense<T, NU, NF, E, true><<<nblk(D.ne, E), E * NU, sm, s>>>(
-            D.ne, input(D), (const T*)D.grad, (const T*)m->fc + D.off_f,
-            (const T*)D.smat, (const T*)D.rcpdjac, ops_of<T>(D), ph, sa);
-      else
-        k_vol_dense<T, NU, NF, E, false><<<nblk(D.ne, E), E * NU, sm, s>>>(
-            D.ne, input(D), nullptr, (const T*)m->fc + D.off_f,
-            (const T*)D.smat, (const T*)D.rcpdjac, ops_of<T>(D), ph, sa);
-      PROF_END(FR_KC_VOL);
-    });
+    T* uf_next = mode == 0 ? nullptr : (T*)m->uf + D.off_f;
+    const T* fc = (const T*)m->fc + D.off_f;
+    PROF_BEGIN(FR_KC_VOL);
+    if (use_hex(m, D)) {
+      HexStage<T, TR> sa{mode, stage, (TR*)D.X, (TR*)D.A, (T*)D.Y, (T*)D.R,
+                         m->d_dt, m->d_flag, uf_next};
+      hex_dispatch(m->order, [&](auto n) {
+        constexpr int N = decltype(n)::value;
+        constexpr int E = hex_epb<N>();
+        const size_t sm = hex_vol_smem<T, N>();
+        const T* uin = from_x ? nullptr : (const T*)D.Y;
+        if (ns)
+          k_hex_vol<T, TR, N, E, true><<<nblk(D.ne, E), E * N * N * N, sm, s>>>(
+              D.ne, uin, (const T*)D.grad, fc, (const T*)D.smat,
+              (const T*)D.rcpdjac, hexops<T>(D), ph, sa);
+        else
+          k_hex_vol<T, TR, N, E, false><<<nblk(D.ne, E), E * N * N * N, sm, s>>>(
+              D.ne, uin, nullptr, fc, (const T*)D.smat, (const T*)D.rcpdjac,
+              hexops<T>(D), ph, sa);
+      });
+    } else {
+      StageArgs<T> sa;
+      sa.mode = mode;
+      sa.stage = stage;
+      sa.X = (T*)D.X;
+      sa.A = (T*)D.A;
+      sa.Y = (T*)D.Y;
+      sa.out = (T*)D.R;
+      sa.dt = m->d_dt;
+      sa.flag = m->d_flag;
+      sa.uf_next = uf_next;
+      const T* uin = from_x ? (const T*)D.X : (const T*)D.Y;
+      dispatch(D.kind, m->order, [&](auto nu, auto nf) {
+        constexpr int NU = decltype(nu)::value, NF = decltype(nf)::value;
+        constexpr int E = epb<NU>();
+        size_t sm = size_t(E) * (15 * NU + 5 * NF) * sizeof(T);
+        if (ns)
+          k_vol_dense<T, NU, NF, E, true><<<nblk(D.ne, E), E * NU, sm, s>>>(
+              D.ne, uin, (const T*)D.grad, fc, (const T*)D.smat,
+              (const T*)D.rcpdjac, ops_of<T>(D), ph, sa);
+        else
+          k_vol_dense<T, NU, NF, E, false><<<nblk(D.ne, E), E * NU, sm, s>>>(
+              D.ne, uin, nullptr, fc, (const T*)D.smat, (const T*)D.rcpdjac,
+              ops_of<T>(D), ph, sa);
+      });
+    }
+    PROF_END(FR_KC_VOL);
   }
 }
 
@@ -418,10 +554,10 @@ const HostType* host_ptr(const fr_mesh* m, int etype) {
   return &m->host[m->type_of_kind[etype]];
 }
 
-template <typename T>
+template <typename TR>
 int set_solution_dev(fr_mesh* m, DevType& D, const double* dsrc) {
   long long n = D.ne * 5 * D.nu;
-  k_layout_in<T><<<nblk(n, 256), 256, 0, m->stream>>>(n, D.nu, dsrc, (T*)D.X);
+  k_layout_in<TR><<<nblk(n, 256), 256, 0, m->stream>>>(n, D.nu, dsrc, (TR*)D.X);
   CK(cudaGetLastError());
   m->uf_valid = false;
   return FR_OK;
@@ -436,21 +572,21 @@ int get_dev(fr_mesh* m, const DevType& D, const void* src, double* ddst) {
   return FR_OK;
 }
 
-template <typename T>
+template <typename T, typename TR>
 int ensure_uf(fr_mesh* m) {
   if (m->uf_valid) return FR_OK;
-  launch_interp<T>(m, m->stream);
+  launch_interp<T, TR>(m, m->stream);
   CK(cudaGetLastError());
   m->uf_valid = true;
   return FR_OK;
 }
 
-template <typename T>
+template <typename T, typename TR>
 int do_rhs(fr_mesh* m) {
-  int rc = ensure_uf<T>(m);
+  int rc = ensure_uf<T, TR>(m);
   if (rc) return rc;
   CK(cudaMemsetAsync(m->d_flag, 0, sizeof(int), m->stream));
-  launch_stage<T>(m, m->stream, 0, 0);
+  launch_stage<T, TR>(m, m->stream, 0, 0);
   CK(cudaGetLastError());
   int flag = 0;
   CK(cudaMemcpyAsync(&flag, m->d_flag, sizeof(int), cudaMemcpyDeviceToHost,
@@ -460,29 +596,34 @@ int do_rhs(fr_mesh* m) {
   return FR_OK;
 }
 
-template <typename T>
+template <typename T, typename TR>
 int build_graph(fr_mesh* m, int scheme) {
   cudaStream_t s = m->stream;
   CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   const int nst = scheme == FR_RK4 ? 4 : 5;
-  for (int st = 0; st < nst; ++st) launch_stage<T>(m, s, scheme == FR_RK4 ? 1 : 2, st);
+  for (int st = 0; st < nst; ++st)
+    launch_stage<T, TR>(m, s, scheme == FR_RK4 ? 1 : 2, st);
   cudaGraph_t g;
   cudaError_t e = cudaStreamEndCapture(s, &g);
-  if (e != cudaSuccess) return fail(FR_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess)
+    return fail(FR_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
   if (m->graph[scheme]) cudaGraphExecDestroy(m->graph[scheme]);
   e = cudaGraphInstantiate(&m->graph[scheme], g, 0);
   cudaGraphDestroy(g);
-  if (e != cudaSuccess) return fail(FR_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess)
+    return fail(FR_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
   m->graph_stream[scheme] = s;
+  m->graph_variant[scheme] = m->variant;
   return FR_OK;
 }
 
-template <typename T>
+template <typename T, typename TR>
 int do_rk(fr_mesh* m, int scheme, double dt, int nsteps) {
-  int rc = ensure_uf<T>(m);
+  int rc = ensure_uf<T, TR>(m);
   if (rc) return rc;
-  if (!m->graph[scheme] || m->graph_stream[scheme] != m->stream) {
-    if ((rc = build_graph<T>(m, scheme))) return rc;
+  if (!m->graph[scheme] || m->graph_stream[scheme] != m->stream ||
+      m->graph_variant[scheme] != m->variant) {
+    if ((rc = build_graph<T, TR>(m, scheme))) return rc;
   }
   m->h_dt = dt;
   CK(cudaMemcpyAsync(m->d_dt, &m->h_dt, sizeof(double), cudaMemcpyHostToDevice,
@@ -497,9 +638,9 @@ int do_rk(fr_mesh* m, int scheme, double dt, int nsteps) {
   return FR_OK;
 }
 
-template <typename T>
+template <typename T, typename TR>
 int do_profile(fr_mesh* m, int scheme, double dt, double* ms, int* launches) {
-  int rc = ensure_uf<T>(m);
+  int rc = ensure_uf<T, TR>(m);
   if (rc) return rc;
   m->h_dt = dt;
   CK(cudaMemcpyAsync(m->d_dt, &m->h_dt, sizeof(double), cudaMemcpyHostToDevice,
@@ -507,7 +648,7 @@ int do_profile(fr_mesh* m, int scheme, double dt, double* ms, int* launches) {
   Prof prof;
   const int nst = scheme == FR_RK4 ? 4 : 5;
   for (int st = 0; st < nst; ++st)
-    launch_stage<T>(m, m->stream, scheme == FR_RK4 ? 1 : 2, st, &prof);
+    launch_stage<T, TR>(m, m->stream, scheme == FR_RK4 ? 1 : 2, st, &prof);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(m->stream));
   for (int k = 0; k < FR_KC_COUNT; ++k) {
@@ -524,6 +665,12 @@ int do_profile(fr_mesh* m, int scheme, double dt, double* ms, int* launches) {
   return FR_OK;
 }
 
+// Run fn<T, TR>(m) for the handle's precision.
+#define FR_PREC(m, fn, ...)                                   \
+  ((m)->precision == FR_FP64   ? fn<double, double>(__VA_ARGS__) \
+   : (m)->precision == FR_FP32 ? fn<float, float>(__VA_ARGS__)   \
+                               : fn<float, double>(__VA_ARGS__))
+
 }  // namespace
 
 // ===================================================================== ABI
@@ -537,7 +684,8 @@ int fr_mesh_create(const fr_mesh_desc* d, fr_mesh** out) {
   if (d->order < 1 || d->order > 4) return fail(FR_EINVAL, "order must be 1..4");
   if (d->physics != FR_EULER && d->physics != FR_NAVIER_STOKES)
     return fail(FR_EINVAL, "unknown physics");
-  if (d->precision != FR_FP64 && d->precision != FR_FP32)
+  if (d->precision != FR_FP64 && d->precision != FR_FP32 &&
+      d->precision != FR_MIXED)
     return fail(FR_EINVAL, "unknown precision");
   if (d->n_bcs < 0 || d->n_bcs > kMaxBC) return fail(FR_EINVAL, "too many boundary conditions");
   if (d->n_periodic < 0 || d->n_periodic > 3) return fail(FR_EINVAL, "n_periodic must be 0..3");
@@ -554,6 +702,7 @@ int fr_mesh_create(const fr_mesh_desc* d, fr_mesh** out) {
   m->mu = d->mu;
   m->prandtl = d->prandtl > 0 ? d->prandtl : 0.72;
   m->wsize = d->precision == FR_FP64 ? 8 : 4;
+  m->rsize = d->precision == FR_FP32 ? 4 : 8;
   MeshInput in;
   in.n_nodes = d->n_nodes;
   in.nodes = d->nodes;
@@ -626,8 +775,13 @@ int fr_mesh_create(const fr_mesh_desc* d, fr_mesh** out) {
     CK(cudaMemcpyToSymbol(c_rk45_b, b, sizeof(b)));
     consts_done[dev] = true;
   }
-  int rc = m->precision == FR_FP64 ? setup_device<double>(m.get())
-                                   : setup_device<float>(m.get());
+  if (m->precision == FR_MIXED)
+    for (auto& H : m->host)
+      if (H.kind != EK_HEX)
+        return fail(FR_EINVAL, "FR_MIXED supports hexahedral meshes only");
+  int rc = FR_PREC(m, setup_device, m.get());
+  if (rc) return rc;
+  rc = FR_PREC(m, prepare_kernels, m.get());
   if (rc) return rc;
   *out = m.release();
   return FR_OK;
@@ -684,7 +838,7 @@ int fr_set_solution(fr_mesh* m, int etype, const double* u) {
   int rc = ensure_staging(m, bytes);
   if (rc) return rc;
   CK(cudaMemcpyAsync(m->d_staging, u, bytes, cudaMemcpyHostToDevice, m->stream));
-  rc = m->precision == FR_FP64
+  rc = m->rsize == 8
            ? set_solution_dev<double>(m, *D, (const double*)m->d_staging)
            : set_solution_dev<float>(m, *D, (const double*)m->d_staging);
   if (rc) return rc;
@@ -702,8 +856,8 @@ static int get_host(const fr_mesh* mc, int etype, double* out, bool rhs) {
   int rc = ensure_staging(m, bytes);
   if (rc) return rc;
   const void* src = rhs ? D->R : D->X;
-  rc = m->precision == FR_FP64
-           ? get_dev<double>(m, *D, src, (double*)m->d_staging)
+  bool dbl = rhs ? m->wsize == 8 : m->rsize == 8;
+  rc = dbl ? get_dev<double>(m, *D, src, (double*)m->d_staging)
            : get_dev<float>(m, *D, src, (double*)m->d_staging);
   if (rc) return rc;
   CK(cudaMemcpyAsync(out, m->d_staging, bytes, cudaMemcpyDeviceToHost, m->stream));
@@ -724,9 +878,8 @@ int fr_set_solution_device(fr_mesh* m, int etype, const void* dptr) {
   DevType* D = type_ptr(m, etype);
   if (!D) return fail(FR_EINVAL, "mesh has no elements of this type");
   CK(cudaSetDevice(m->device));
-  return m->precision == FR_FP64
-             ? set_solution_dev<double>(m, *D, (const double*)dptr)
-             : set_solution_dev<float>(m, *D, (const double*)dptr);
+  return m->rsize == 8 ? set_solution_dev<double>(m, *D, (const double*)dptr)
+                       : set_solution_dev<float>(m, *D, (const double*)dptr);
 }
 
 int fr_get_solution_device(const fr_mesh* mc, int etype, void* dptr) {
@@ -735,16 +888,15 @@ int fr_get_solution_device(const fr_mesh* mc, int etype, void* dptr) {
   DevType* D = type_ptr(m, etype);
   if (!D) return fail(FR_EINVAL, "mesh has no elements of this type");
   CK(cudaSetDevice(m->device));
-  return m->precision == FR_FP64
-             ? get_dev<double>(m, *D, D->X, (double*)dptr)
-             : get_dev<float>(m, *D, D->X, (double*)dptr);
+  return m->rsize == 8 ? get_dev<double>(m, *D, D->X, (double*)dptr)
+                       : get_dev<float>(m, *D, D->X, (double*)dptr);
 }
 
 int fr_rhs(fr_mesh* m) {
   if (!m) return fail(FR_EINVAL, "null mesh");
   if (m->host_only) return fail(FR_EINVAL, "host-only handle (device < 0)");
   CK(cudaSetDevice(m->device));
-  return m->precision == FR_FP64 ? do_rhs<double>(m) : do_rhs<float>(m);
+  return FR_PREC(m, do_rhs, m);
 }
 
 int fr_rk_step(fr_mesh* m, int scheme, double dt, int nsteps) {
@@ -754,8 +906,7 @@ int fr_rk_step(fr_mesh* m, int scheme, double dt, int nsteps) {
   if (nsteps < 0) return fail(FR_EINVAL, "negative step count");
   if (nsteps == 0) return FR_OK;
   CK(cudaSetDevice(m->device));
-  return m->precision == FR_FP64 ? do_rk<double>(m, scheme, dt, nsteps)
-                                 : do_rk<float>(m, scheme, dt, nsteps);
+  return FR_PREC(m, do_rk, m, scheme, dt, nsteps);
 }
 
 int fr_profile_step(fr_mesh* m, int scheme, double dt, double* ms,
@@ -764,8 +915,18 @@ int fr_profile_step(fr_mesh* m, int scheme, double dt, double* ms,
   if (m->host_only) return fail(FR_EINVAL, "host-only handle (device < 0)");
   if (scheme != FR_RK4 && scheme != FR_RK45) return fail(FR_EINVAL, "unknown scheme");
   CK(cudaSetDevice(m->device));
-  return m->precision == FR_FP64 ? do_profile<double>(m, scheme, dt, ms, launches)
-                                 : do_profile<float>(m, scheme, dt, ms, launches);
+  return FR_PREC(m, do_profile, m, scheme, dt, ms, launches);
+}
+
+int fr_set_kernel_variant(fr_mesh* m, int variant) {
+  if (!m) return fail(FR_EINVAL, "null mesh");
+  if (variant != FR_VARIANT_AUTO && variant != FR_VARIANT_DENSE &&
+      variant != FR_VARIANT_SUMFACT)
+    return fail(FR_EINVAL, "unknown kernel variant");
+  if (variant == FR_VARIANT_DENSE && m->precision == FR_MIXED)
+    return fail(FR_EINVAL, "FR_MIXED runs the sum-factorised kernels only");
+  m->variant = variant;
+  return FR_OK;
 }
 
 int fr_set_stream(fr_mesh* m, void* s) {

@@ -1,0 +1,349 @@
+// Sum-factorised hexahedron kernels (PyFR v2.0.3, Section 2, Eqs. disu and
+// FRfinal, on tensor-product elements).
+//
+// The hexahedron's operators are Kronecker products of 1D factors on the
+// N = p+1 Gauss-Legendre points: interpolation to a face is one
+// N-point dot product along the line normal to it, the derivative along
+// x~_d is the 1D derivative matrix along the d-lines, and the DG correction
+// of a face point touches only the N solution points of its line, with
+// weights g_R'(x_a) (plus face) and -g_L'(x_a) (minus face) (Huynh 2007).
+// This is the "bespoke kernel that elides multiplications by zero" idea of
+// the paper's matrix-multiplication paragraph, done by construction.
+//
+// Thread mapping: one thread per solution point (a, b, c), point index
+// a + N b + N^2 c; EPB elements per CTA.  Flux point index
+// face * N^2 + i + N j, faces x-, x+, y-, y+, z-, z+ with (i, j) the two
+// tangential indices in (y,z), (x,z), (x,y) order.
+#pragma once
+#include "fr_kernels.cuh"
+
+namespace frgb {
+
+template <typename T>
+struct HexOps {
+  T d1[8][8];  // d1[a][m] = l_m'(x_a)
+  T lm[8], lp[8];  // l_m(-1), l_m(+1)
+  T gl[8], gr[8];  // correction weights of the minus / plus face
+};
+
+// register type used for the RK solution / accumulator registers
+template <typename T, typename TR>
+struct HexStage {
+  int mode, stage;
+  TR* X;
+  TR* A;
+  T* Y;
+  T* out;
+  const double* dt;
+  int* flag;
+  T* uf_next;
+};
+
+template <int N>
+__device__ __forceinline__ int fp_of(int face, int i, int j) {
+  return face * N * N + i + N * j;
+}
+
+// solution point of face point (face, i, j) at position m along its line
+template <int N>
+__device__ __forceinline__ int line_pt(int face, int i, int j, int m) {
+  int dir = face >> 1;
+  if (dir == 0) return m + N * i + N * N * j;
+  if (dir == 1) return i + N * m + N * N * j;
+  return i + N * j + N * N * m;
+}
+
+template <typename T, typename TR>
+__device__ __forceinline__ void hex_stage_update(const HexStage<T, TR>& a,
+                                                 long long i0, long long vstr,
+                                                 const T u[5], const T R[5],
+                                                 T s[5]) {
+  bool bad = false;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) bad |= !isfinite(R[k]);
+  if (bad) atomicOr(a.flag, 1);
+  if (a.mode == 0) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      a.out[i0 + k * vstr] = R[k];
+      s[k] = u[k];
+    }
+    return;
+  }
+  const TR dt = TR(*a.dt);
+  const int st = a.stage;
+  if (a.mode == 1) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      long long i = i0 + k * vstr;
+      TR r = TR(R[k]);
+      if (st == 0) {
+        TR x = a.X[i];
+        a.A[i] = x + dt * TR(1.0 / 6.0) * r;
+        T y = T(x + dt * TR(0.5) * r);
+        a.Y[i] = y;
+        s[k] = y;
+      } else if (st < 3) {
+        TR x = a.X[i];
+        a.A[i] = a.A[i] + dt * TR(1.0 / 3.0) * r;
+        T y = T(x + (st == 1 ? dt * TR(0.5) : dt) * r);
+        a.Y[i] = y;
+        s[k] = y;
+      } else {
+        TR x = a.A[i] + dt * TR(1.0 / 6.0) * r;
+        a.X[i] = x;
+        s[k] = T(x);
+      }
+    }
+    return;
+  }
+  const TR b = TR(c_rk45_b[st]);
+  const TR am = st < 4 ? TR(c_rk45_a[st]) - b : TR(0);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    long long i = i0 + k * vstr;
+    TR r = TR(R[k]);
+    TR x = a.X[i] + b * dt * r;
+    a.X[i] = x;
+    if (st < 4) {
+      T y = T(x + am * dt * r);
+      a.Y[i] = y;
+      s[k] = y;
+    } else {
+      s[k] = T(x);
+    }
+  }
+}
+
+// interpolate smem field src[v][pt] to face point fp (5 variables)
+template <typename T, int N, int NV>
+__device__ __forceinline__ void face_interp(const T* src, int fp,
+                                            const HexOps<T>& op, T out[NV]) {
+  const int NF1 = N * N;
+  int face = fp / NF1, r = fp - face * NF1;
+  int i = r % N, j = r / N;
+  const T* w = (face & 1) ? op.lp : op.lm;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) out[k] = T(0);
+#pragma unroll
+  for (int m = 0; m < N; ++m) {
+    int q = line_pt<N>(face, i, j, m);
+    T c = w[m];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) out[k] += c * src[k * N * N * N + q];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// NS gradients on hexahedra: corrected reference gradient, physical gradient
+// at solution points, and its value at the flux points.
+template <typename T, typename TR, int N, int EPB>
+__global__ void __launch_bounds__(EPB* N* N* N)
+    k_hex_grad(long long ne, const T* __restrict__ uin, const TR* __restrict__ X,
+               const T* __restrict__ du, const T* __restrict__ smat,
+               const T* __restrict__ rcpdjac, HexOps<T> op,
+               T* __restrict__ grad, T* __restrict__ gradf) {
+  constexpr int NU = N * N * N, NF = 6 * N * N;
+  extern __shared__ unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int le = threadIdx.x / NU, z = threadIdx.x - le * NU;
+  const long long e = (long long)blockIdx.x * EPB + le;
+  T* us = sm + le * (5 * NU + 5 * NF + 15 * NU);
+  T* ds = us + 5 * NU;
+  T* gs = ds + 5 * NF;
+  const int a = z % N, b = (z / N) % N, c = z / (N * N);
+  if (e < ne) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+      us[k * NU + z] = uin ? uin[(e * 5 + k) * NU + z] : T(X[(e * 5 + k) * NU + z]);
+    for (int f = z; f < NF; f += NU)
+#pragma unroll
+      for (int k = 0; k < 5; ++k) ds[k * NF + f] = du[(e * 5 + k) * NF + f];
+  }
+  __syncthreads();
+  if (e < ne) {
+    T gref[3][5];
+    const int N2 = N * N;
+    T da[N], db[N], dc[N];
+#pragma unroll
+    for (int m = 0; m < N; ++m) {
+      da[m] = op.d1[a][m];
+      db[m] = op.d1[b][m];
+      dc[m] = op.d1[c][m];
+    }
+    const T gla = op.gl[a], gra = op.gr[a], glb = op.gl[b], grb = op.gr[b],
+            glc = op.gl[c], grc = op.gr[c];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      T gx = T(0), gy = T(0), gz = T(0);
+#pragma unroll
+      for (int m = 0; m < N; ++m) {
+        gx += da[m] * us[k * NU + m + N * b + N2 * c];
+        gy += db[m] * us[k * NU + a + N * m + N2 * c];
+        gz += dc[m] * us[k * NU + a + N * b + N2 * m];
+      }
+      // correction: the face normal n~ is -e_d on the minus face
+      gx += -gla * ds[k * NF + fp_of<N>(0, b, c)] +
+            gra * ds[k * NF + fp_of<N>(1, b, c)];
+      gy += -glb * ds[k * NF + fp_of<N>(2, a, c)] +
+            grb * ds[k * NF + fp_of<N>(3, a, c)];
+      gz += -glc * ds[k * NF + fp_of<N>(4, a, b)] +
+            grc * ds[k * NF + fp_of<N>(5, a, b)];
+      gref[0][k] = gx;
+      gref[1][k] = gy;
+      gref[2][k] = gz;
+    }
+    T S[3][3];
+#pragma unroll
+    for (int r = 0; r < 9; ++r) S[r / 3][r % 3] = smat[(e * 9 + r) * NU + z];
+    const T rj = rcpdjac[e * NU + z];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        T g = rj * (S[0][j] * gref[0][k] + S[1][j] * gref[1][k] +
+                    S[2][j] * gref[2][k]);
+        grad[(e * 15 + j * 5 + k) * NU + z] = g;
+        gs[(j * 5 + k) * NU + z] = g;
+      }
+  }
+  __syncthreads();
+  if (e >= ne) return;
+  for (int f = z; f < NF; f += NU) {
+    T g[15];
+    face_interp<T, N, 15>(gs, f, op, g);
+#pragma unroll
+    for (int k = 0; k < 15; ++k) gradf[(e * 15 + k) * NF + f] = g[k];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Volume kernel on hexahedra: f~ = S F, divergence along the three line
+// families, DG correction with the jump F^C - n~.f~ computed once per flux
+// point, R = -div / J, RK epilogue and the next stage's u_f.
+template <typename T, typename TR, int N, int EPB, bool NS>
+__global__ void __launch_bounds__(EPB* N* N* N)
+    k_hex_vol(long long ne, const T* __restrict__ uin, const T* __restrict__ grad,
+              const T* __restrict__ fc, const T* __restrict__ smat,
+              const T* __restrict__ rcpdjac, HexOps<T> op, Phys<T> ph,
+              HexStage<T, TR> sa) {
+  constexpr int NU = N * N * N, NF = 6 * N * N, N2 = N * N;
+  extern __shared__ unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int le = threadIdx.x / NU, z = threadIdx.x - le * NU;
+  const long long e = (long long)blockIdx.x * EPB + le;
+  T* ft = sm + le * (15 * NU + 5 * NF);  // [3][5][NU]
+  T* jm = ft + 15 * NU;                  // [5][NF]
+  const int a = z % N, b = (z / N) % N, c = z / N2;
+  T uz[5];
+  if (e < ne) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+      uz[k] = uin ? uin[(e * 5 + k) * NU + z] : T(sa.X[(e * 5 + k) * NU + z]);
+    T F[3][5];
+    euler_flux(uz, ph, F);
+    if (NS) {
+      T g[3][5];
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) g[j][k] = grad[(e * 15 + j * 5 + k) * NU + z];
+      viscous_flux_acc(uz, g, ph, T(-1), F);
+    }
+    T S[3][3];
+#pragma unroll
+    for (int r = 0; r < 9; ++r) S[r / 3][r % 3] = smat[(e * 9 + r) * NU + z];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int k = 0; k < 5; ++k)
+        ft[(d * 5 + k) * NU + z] =
+            S[d][0] * F[0][k] + S[d][1] * F[1][k] + S[d][2] * F[2][k];
+  }
+  __syncthreads();
+  if (e < ne) {
+    // jump at every flux point: F^C - n~ . M0 f~ (only the normal direction)
+    for (int f = z; f < NF; f += NU) {
+      int face = f / N2;
+      int dir = face >> 1;
+      T fn[5];
+      face_interp<T, N, 5>(ft + dir * 5 * NU, f, op, fn);
+      T sgn = (face & 1) ? T(1) : T(-1);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) jm[k * NF + f] = fc[(e * 5 + k) * NF + f] - sgn * fn[k];
+    }
+  }
+  __syncthreads();
+  T s[5];
+  if (e < ne) {
+    T R[5];
+    const T rj = rcpdjac[e * NU + z];
+    T da[N], db[N], dc[N];
+#pragma unroll
+    for (int m = 0; m < N; ++m) {
+      da[m] = op.d1[a][m];
+      db[m] = op.d1[b][m];
+      dc[m] = op.d1[c][m];
+    }
+    const T gla = op.gl[a], gra = op.gr[a], glb = op.gl[b], grb = op.gr[b],
+            glc = op.gl[c], grc = op.gr[c];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const T* fx = ft + (0 * 5 + k) * NU;
+      const T* fy = ft + (1 * 5 + k) * NU;
+      const T* fz = ft + (2 * 5 + k) * NU;
+      T dv = T(0);
+#pragma unroll
+      for (int m = 0; m < N; ++m) {
+        dv += da[m] * fx[m + N * b + N2 * c];
+        dv += db[m] * fy[a + N * m + N2 * c];
+        dv += dc[m] * fz[a + N * b + N2 * m];
+      }
+      const T* jk = jm + k * NF;
+      dv += gla * jk[fp_of<N>(0, b, c)] + gra * jk[fp_of<N>(1, b, c)];
+      dv += glb * jk[fp_of<N>(2, a, c)] + grb * jk[fp_of<N>(3, a, c)];
+      dv += glc * jk[fp_of<N>(4, a, b)] + grc * jk[fp_of<N>(5, a, b)];
+      R[k] = -dv * rj;
+    }
+    hex_stage_update(sa, e * 5 * NU + z, NU, uz, R, s);
+  }
+  if (sa.uf_next == nullptr) return;
+  __syncthreads();
+  if (e < ne) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) ft[k * NU + z] = s[k];
+  }
+  __syncthreads();
+  if (e >= ne) return;
+  for (int f = z; f < NF; f += NU) {
+    T v[5];
+    face_interp<T, N, 5>(ft, f, op, v);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) sa.uf_next[(e * 5 + k) * NF + f] = v[k];
+  }
+}
+
+// Eq. (disu) on hexahedra from the solution register.
+template <typename T, typename TR, int N, int EPB>
+__global__ void __launch_bounds__(EPB* N* N* N)
+    k_hex_interp(long long ne, const TR* __restrict__ X, HexOps<T> op,
+                 T* __restrict__ uf) {
+  constexpr int NU = N * N * N, NF = 6 * N * N;
+  __shared__ T us[EPB][5 * NU];
+  const int le = threadIdx.x / NU, z = threadIdx.x - le * NU;
+  const long long e = (long long)blockIdx.x * EPB + le;
+  if (e < ne) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) us[le][k * NU + z] = T(X[(e * 5 + k) * NU + z]);
+  }
+  __syncthreads();
+  if (e >= ne) return;
+  for (int f = z; f < NF; f += NU) {
+    T v[5];
+    face_interp<T, N, 5>(us[le], f, op, v);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) uf[(e * 5 + k) * NF + f] = v[k];
+  }
+}
+
+}  // namespace frgb

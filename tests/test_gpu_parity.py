@@ -193,3 +193,55 @@ def test_full_size_tgv_against_oracle():
     u = rk.step(osys.rhs, u, 1e-3, "rk45")
     err = rel_l2(g.get_solution(), u)
     assert err.max() < 1e-12, err
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("physics", ["euler", "ns"])
+def test_hex_sumfact_equals_dense(p, physics):
+    """The sum-factorised hexahedron kernels and the dense-operator kernels
+    compute the same right-hand side and RK steps (rounding only)."""
+    spec = box_hex((3, 2, 2), perturb=0.1)
+    outs = []
+    for variant in ("dense", "sumfact"):
+        g = fr.FRMesh(spec, p, physics=physics, mu=0.02, prandtl=0.71)
+        g.set_variant(variant)
+        g.set_solution(lib_state(g, _tgv))
+        r = g.rhs()
+        g.rk_step("rk45", 1e-3, 2)
+        outs.append((r, g.get_solution()))
+    assert rel_l2_rhs(outs[1][0], outs[0][0]).max() < (5e-12 if p == 4 else 1e-12)
+    assert rel_l2(outs[1][1], outs[0][1]).max() < 1e-13
+
+
+def _vortex_run(precision, n=8, p=2, steps=10, dt=0.01):
+    spec = box_hex((n, n, 1), hi=(10.0, 10.0, 10.0 / n))
+    o, osys, g = _pair(spec, p, "euler", precision=precision)
+    g.set_solution(lib_state(g, ics.isentropic_vortex))
+    u = oracle_state(o, ics.isentropic_vortex)
+    for _ in range(steps):
+        u = rk.step(osys.rhs, u, dt, "rk4")
+    g.rk_step("rk4", dt, steps)
+    return rel_l2(g.get_solution(), u)
+
+
+def test_mixed_precision_vortex_within_stated_tolerance():
+    """Mixed form (FP32 operators/fluxes, FP64 RK registers) against the
+    FP64 oracle on the isentropic vortex: <= 1e-5 per variable."""
+    err = _vortex_run("mixed")
+    assert err.max() < 1e-5, err
+    err64 = _vortex_run("fp64")
+    assert err64.max() < 1e-12, err64
+
+
+@pytest.mark.parametrize("p", [3, 4])
+def test_mixed_precision_tgv_within_stated_tolerance(p):
+    spec = box_hex((4, 4, 4), hi=(2 * np.pi,) * 3, perturb=0.1)
+    o, osys, g = _pair(spec, p, "ns", precision="mixed", mu=1 / 1600)
+    ic = lambda x: ics.taylor_green(x, mach=0.1)  # noqa: E731
+    g.set_solution(lib_state(g, ic))
+    u = oracle_state(o, ic)
+    for _ in range(5):
+        u = rk.step(osys.rhs, u, 1e-3, "rk45")
+    g.rk_step("rk45", 1e-3, 5)
+    err = rel_l2(g.get_solution(), u)
+    assert err.max() < 1e-5, err
