@@ -116,6 +116,23 @@ int fr_get_points(const fr_mesh* mesh, int etype, double* xyz);
 int fr_set_solution(fr_mesh* mesh, int etype, const double* u);
 int fr_get_solution(const fr_mesh* mesh, int etype, double* u);
 
+/* Allocation-free variant of fr_set_solution (the paper has no
+ * counterpart; it serves callers that cannot allocate device memory, such
+ * as applications whose device memory is reserved up front by their own
+ * pool allocator, or time-stepping loops that must not pay the device-wide
+ * synchronisation cudaMalloc / cudaFree can imply).  It calls no
+ * cudaMalloc, cudaFree or allocating library routine: the host array is
+ * copied into a fixed staging array compiled into the library (16 MiB,
+ * i.e. at most 2^21 FP64 values = n_elem * nupts * 5, held by every GPU that
+ * loads the library until process exit), then the layout kernel writes the
+ * solution register.  Larger solutions return FR_EINVAL.  The first call on
+ * a device looks up the array's device address (with that device current)
+ * and caches it; make that first call before any stream capture.  All calls
+ * share the one staging array, which keeps the last call's contents: calls
+ * that overlap on the GPU (e.g. two handles on different streams) race.
+ * Synchronous: returns after the copy and the layout kernel completed. */
+int fr_set_solution_static(fr_mesh* mesh, int etype, const double* u);
+
 /* Same from / to device memory in the host layout (FP64), on the handle's
  * stream; the pointer must stay valid until the stream reaches the copy. */
 int fr_set_solution_device(fr_mesh* mesh, int etype, const void* dptr);

@@ -88,6 +88,7 @@ def load():
         "fr_get_pairs": (I, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "fr_profile_step": (I, [P, I, D, P, P]),
         "fr_set_kernel_variant": (I, [P, I]),
+        "fr_set_solution_static": (I, [P, I, P]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)

@@ -4,6 +4,7 @@
 
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -841,6 +842,65 @@ int fr_set_solution(fr_mesh* m, int etype, const double* u) {
   rc = m->rsize == 8
            ? set_solution_dev<double>(m, *D, (const double*)m->d_staging)
            : set_solution_dev<float>(m, *D, (const double*)m->d_staging);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(m->stream));
+  return FR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free solution upload.
+//
+// fr_set_solution stages the host array in a device buffer that it
+// allocates with cudaMalloc on first use.  Some callers cannot allow that:
+// an application whose device memory is reserved up front by its own pool
+// allocator (a further cudaMalloc fails or escapes its accounting), or a
+// time-stepping loop that must not pay the device-wide synchronisation that
+// cudaMalloc / cudaFree can imply.  fr_set_solution_static runs the same
+// copy and the same layout kernel, but stages through a fixed array that is
+// part of the library image: kStaticStageDoubles FP64 values (16 MiB), held
+// by every GPU that loads the library until the process exits.
+constexpr size_t kStaticStageDoubles = size_t(1) << 21;
+static __device__ __align__(256) double g_static_stage[kStaticStageDoubles];
+
+// In host code `g_static_stage` names a host-side stand-in, not device
+// memory; its device address is looked up once per device, with that device
+// current, and cached here.
+static double* g_static_stage_dev[64] = {nullptr};
+static std::mutex g_static_stage_mu;
+
+static int static_stage_address(int device, double** out) {
+  if (device < 0 || device >= 64) return fail(FR_EINVAL, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_static_stage_mu);
+  if (!g_static_stage_dev[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_stage);
+    if (e != cudaSuccess || !p)
+      return fail(FR_ECUDA, std::string("cudaGetSymbolAddress(static stage): ") +
+                                cudaGetErrorString(e));
+    g_static_stage_dev[device] = static_cast<double*>(p);
+  }
+  *out = g_static_stage_dev[device];
+  return FR_OK;
+}
+
+int fr_set_solution_static(fr_mesh* m, int etype, const double* u) {
+  if (!m || !u) return fail(FR_EINVAL, "null argument");
+  DevType* D = type_ptr(m, etype);
+  if (!D) return fail(FR_EINVAL, "mesh has no elements of this type");
+  size_t n = size_t(D->ne) * 5 * D->nu;
+  if (n > kStaticStageDoubles)
+    return fail(FR_EINVAL, "solution of " + std::to_string(n) +
+                               " values exceeds the static staging limit of " +
+                               std::to_string(kStaticStageDoubles) +
+                               " FP64 values; use fr_set_solution");
+  CK(cudaSetDevice(m->device));
+  double* stage = nullptr;
+  int rc = static_stage_address(m->device, &stage);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(stage, u, n * sizeof(double), cudaMemcpyHostToDevice,
+                     m->stream));
+  rc = m->rsize == 8 ? set_solution_dev<double>(m, *D, stage)
+                     : set_solution_dev<float>(m, *D, stage);
   if (rc) return rc;
   CK(cudaStreamSynchronize(m->stream));
   return FR_OK;
