@@ -163,7 +163,8 @@ enum { FR_KC_FACE_U = 0,  /* NS common solution at interior flux points */
        FR_KC_FACE_F = 3,  /* common normal flux, interior pairs */
        FR_KC_BND_F = 4,   /* common normal flux, boundary points */
        FR_KC_VOL = 5,     /* volume: flux, divergence, lift, RK update */
-       FR_KC_COUNT = 6 };
+       FR_KC_FILTER = 6,  /* entropy minimum and entropy filter */
+       FR_KC_COUNT = 7 };
 int fr_profile_step(fr_mesh* mesh, int scheme, double dt, double* ms,
                     int* launches);
 
@@ -204,6 +205,65 @@ int fr_get_metrics(const fr_mesh* mesh, int etype, double* smat,
 /* Number of interior flux-point pairs and boundary flux points. */
 int fr_get_pairs(const fr_mesh* mesh, int64_t* n_interior,
                  int64_t* n_boundary);
+
+/* Entropy filter (Section 3.2): when on, every RK stage of fr_rk_step
+ * filters the new stage value of each element that violates rho >= 1e-8,
+ * p >= 1e-8 or s = p rho^-gamma >= s_min (1 - 1e-8), s_min being the
+ * minimum entropy of the stage input over the element's solution points,
+ * its flux points and the partner flux points across its faces (1e-8 is
+ * 2^-20 when the stage values are FP32: FR_FP32 and FR_MIXED).  The
+ * filter multiplies modal coefficient k (orthonormal basis) by
+ * exp(-zeta (d_k/p)^2), d_k the mode's total degree, with the smallest
+ * zeta in [0, 36] that satisfies the constraints (bracketed Illinois
+ * root-find, relative tolerance 1e-6, at most 24 margin evaluations;
+ * constraints evaluated in FP64).  sample_capacity > 0 reserves a device
+ * list of (4 features, zeta*) training samples, one per filtered element.
+ * fr_rhs is never filtered. */
+int fr_filter_enable(fr_mesh* mesh, int on, int64_t sample_capacity);
+
+/* Learned start guess for the filter root-find: params holds the 1257
+ * predictor parameters (W1[32][4], b1[32], W2[32][32], b2[32], W3[32], b3,
+ * input mean[4], input std[4]); the library stores them in BF16 and
+ * evaluates Linear(4,32)-SiLU-Linear(32,32)-SiLU-Linear(32,1)-softplus with
+ * FP32 accumulation.  The guess only opens the root-find's bracket (at
+ * z0, then z0 / r or r z0, then halving / doubling; r = params[1257] when
+ * n = 1258, else 1.25); the exact root-find decides the result.  NULL
+ * switches the predictor off. */
+int fr_filter_set_mlp(fr_mesh* mesh, const float* params, int64_t n);
+
+/* Filter the current solution in place, e.g. an initial state with
+ * discontinuities; needs fr_filter_enable.  smin: host array of the
+ * minimum-entropy bound of every element (element types in mesh order:
+ * hex, prism, tet), or NULL to take it from the solution itself (then only
+ * the positivity constraints can be active). */
+int fr_filter_solution(fr_mesh* mesh, const double* smin);
+
+/* Filter strength and margin evaluations of every element of `etype` in the
+ * last filtered stage (zeta 0 and 1 evaluation for elements left alone). */
+int fr_filter_last(const fr_mesh* mesh, int etype, float* zeta, int* evals);
+
+/* Filter counters since the last reset: out[0] filtered element-stages,
+ * out[1] margin evaluations in them, out[2] fallbacks (zeta = 36 still
+ * infeasible), out[3] training samples written, out[4] element-stages that
+ * used the predictor's guess. */
+int fr_filter_stats(fr_mesh* mesh, uint64_t* out, int reset);
+
+/* Copy up to `max` training samples ([n][5]: 4 features, zeta*) to host
+ * memory and restart the sample list; *n receives the count. */
+int fr_filter_samples(fr_mesh* mesh, float* out, int64_t max, int64_t* n);
+
+/* Train the predictor on the GPU: full-batch Adam (learning rate lr) on the
+ * mean squared error of log(predicted zeta) against log(zeta*), `epochs`
+ * iterations, FP32, deterministic.  params (1257 floats) is the start and
+ * receives the result; the 8 normalisation entries are not trained.
+ * loss_hist (optional) receives the loss before each update. */
+int fr_mlp_train(int device, const float* x, const float* zstar, int64_t n,
+                 float* params, int epochs, float lr, float* loss_hist);
+
+/* Loss and gradient of the same objective at params (grad: 1257 floats,
+ * zeros for the normalisation entries). */
+int fr_mlp_loss_grad(int device, const float* params, const float* x,
+                     const float* zstar, int64_t n, float* loss, float* grad);
 
 /* Message of the last failed call on this thread. */
 const char* fr_last_error(void);

@@ -89,6 +89,14 @@ def load():
         "fr_profile_step": (I, [P, I, D, P, P]),
         "fr_set_kernel_variant": (I, [P, I]),
         "fr_set_solution_static": (I, [P, I, P]),
+        "fr_filter_enable": (I, [P, I, C.c_int64]),
+        "fr_filter_set_mlp": (I, [P, P, C.c_int64]),
+        "fr_filter_stats": (I, [P, P, I]),
+        "fr_filter_samples": (I, [P, P, C.c_int64, C.POINTER(C.c_int64)]),
+        "fr_mlp_train": (I, [I, P, P, C.c_int64, P, I, C.c_float, P]),
+        "fr_mlp_loss_grad": (I, [I, P, P, P, C.c_int64, P, P]),
+        "fr_filter_last": (I, [P, I, P, P]),
+        "fr_filter_solution": (I, [P, P]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -240,13 +248,13 @@ class FRMesh:
                                  int(nsteps)))
 
     KERNEL_CLASSES = ("face_ucommon", "bnd_ucommon", "grad", "face_flux",
-                      "bnd_flux", "volume")
+                      "bnd_flux", "volume", "filter")
 
     def profile_step(self, scheme, dt):
         """One RK step with per-launch CUDA events: returns
         {kernel class: (summed ms, launches)}."""
-        ms = np.zeros(6, np.float64)
-        n = np.zeros(6, np.int32)
+        ms = np.zeros(7, np.float64)
+        n = np.zeros(7, np.int32)
         _check(load().fr_profile_step(self._h, SCHEMES[scheme], float(dt),
                                       _ptr(ms), _ptr(n)))
         return {k: (float(ms[i]), int(n[i]))
@@ -255,6 +263,46 @@ class FRMesh:
     def set_variant(self, name):
         """Kernel family for hexahedra: 'auto', 'dense' or 'sumfact'."""
         _check(load().fr_set_kernel_variant(self._h, VARIANTS[name]))
+
+    def filter_enable(self, on=True, sample_capacity=0):
+        _check(load().fr_filter_enable(self._h, int(on), int(sample_capacity)))
+
+    def filter_set_mlp(self, params):
+        if params is None:
+            _check(load().fr_filter_set_mlp(self._h, None, 0))
+            return
+        p = np.ascontiguousarray(params, np.float32)
+        _check(load().fr_filter_set_mlp(self._h, _ptr(p), len(p)))
+
+    def filter_solution(self, smin=None):
+        """smin: {etype: (n_elem,) bound} or None (bound from the state)."""
+        if smin is None:
+            _check(load().fr_filter_solution(self._h, None))
+            return
+        a = np.ascontiguousarray(
+            np.concatenate([np.asarray(smin[t], np.float64)
+                            for t in self.types]))
+        _check(load().fr_filter_solution(self._h, _ptr(a)))
+
+    def filter_last(self, etype="hex"):
+        ne, _, _ = self.info(etype)
+        z = np.zeros(ne, np.float32)
+        n = np.zeros(ne, np.int32)
+        _check(load().fr_filter_last(self._h, ETYPES[etype], _ptr(z), _ptr(n)))
+        return z, n
+
+    def filter_stats(self, reset=False):
+        out = np.zeros(5, np.uint64)
+        _check(load().fr_filter_stats(self._h, _ptr(out), int(reset)))
+        return dict(zip(("filtered", "evals", "fallbacks", "samples",
+                         "guessed"), (int(v) for v in out)))
+
+    def filter_samples(self, max_samples=1 << 22):
+        out = np.empty((max_samples, 5), np.float32)
+        n = C.c_int64()
+        _check(load().fr_filter_samples(self._h, _ptr(out), int(max_samples),
+                                        C.byref(n)))
+        return out[:n.value].copy()
 
     def set_stream(self, stream):
         """stream: a torch.cuda.Stream, a raw cudaStream_t int, or None."""
@@ -288,3 +336,26 @@ class FRMesh:
         a, b = C.c_int64(), C.c_int64()
         _check(load().fr_get_pairs(self._h, C.byref(a), C.byref(b)))
         return a.value, b.value
+
+
+def mlp_train(x, zstar, params, epochs, lr, device=0):
+    """Train the filter-strength predictor on the GPU (fr_mlp_train)."""
+    x = np.ascontiguousarray(x, np.float32)
+    z = np.ascontiguousarray(zstar, np.float32)
+    p = np.ascontiguousarray(params, np.float32).copy()
+    hist = np.zeros(epochs, np.float32)
+    _check(load().fr_mlp_train(int(device), _ptr(x), _ptr(z), len(z), _ptr(p),
+                               int(epochs), float(lr), _ptr(hist)))
+    return p, hist
+
+
+def mlp_loss_grad(params, x, zstar, device=0):
+    """Loss and gradient of the predictor objective on the GPU."""
+    x = np.ascontiguousarray(x, np.float32)
+    z = np.ascontiguousarray(zstar, np.float32)
+    p = np.ascontiguousarray(params, np.float32)
+    loss = np.zeros(1, np.float32)
+    g = np.zeros(len(p), np.float32)
+    _check(load().fr_mlp_loss_grad(int(device), _ptr(p), _ptr(x), _ptr(z),
+                                   len(z), _ptr(loss), _ptr(g)))
+    return float(loss[0]), g

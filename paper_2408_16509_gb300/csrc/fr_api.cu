@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/frgb.h"
+#include "fr_filter.cuh"
 #include "fr_hex.cuh"
 #include "fr_kernels.cuh"
 #include "fr_mesh.hpp"
@@ -79,6 +80,15 @@ struct DevType {
   void* NREF = nullptr;
   HexOps<double> hx64{};
   HexOps<float> hx32{};
+  // entropy filter (allocated by fr_filter_enable)
+  void* fVinvT = nullptr;
+  void* fVT = nullptr;
+  void* fdeg = nullptr;
+  void* fW = nullptr;
+  int32_t* fpartner = nullptr;
+  double* smin = nullptr;
+  float* zeta_last = nullptr;
+  int* evals_last = nullptr;
 };
 
 void free_all(std::vector<void*>& v) {
@@ -123,7 +133,16 @@ struct fr_mesh {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   cudaStream_t graph_stream[2] = {nullptr, nullptr};
   int variant = FR_VARIANT_AUTO;
-  int graph_variant[2] = {-1, -1};
+  long long epoch = 0;            // bumped by every change of launch config
+  long long graph_epoch[2] = {-1, -1};
+  bool filter_on = false;
+  bool mlp_on = false;
+  FilterStats* d_fstats = nullptr;
+  float* d_samples = nullptr;
+  unsigned long long sample_cap = 0;
+  __nv_bfloat16* d_mlp = nullptr;
+  float* d_mlp_norm = nullptr;
+  double mlp_ratio = 1.25;
   std::vector<void*> allocs;
   void* d_staging = nullptr;   // host-layout FP64 staging for set/get
   size_t staging_bytes = 0;
@@ -133,6 +152,7 @@ struct fr_mesh {
       if (graph[i]) cudaGraphExecDestroy(graph[i]);
     free_all(allocs);
     if (d_staging) cudaFree(d_staging);
+    if (d_samples) cudaFree(d_samples);
     if (own_stream) cudaStreamDestroy(own_stream);
   }
 };
@@ -394,6 +414,11 @@ struct Prof {
 #define PROF_END(c) \
   if (prof) prof->mark(c, s, false)
 
+template <typename T, typename TR>
+void launch_entropy_min(fr_mesh* m, cudaStream_t s, bool from_x);
+template <typename T, typename TR>
+void launch_filter(fr_mesh* m, cudaStream_t s, DevType& D, bool last_stage);
+
 // Launch one RK stage (or a bare right-hand side when mode == 0).
 template <typename T, typename TR>
 void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
@@ -405,6 +430,13 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
   // stage input: the solution register X for a bare RHS and the first
   // stage, the stage register Y afterwards
   const bool from_x = (mode == 0 || stage == 0);
+  const bool filt = m->filter_on && mode != 0;
+  const bool last_stage = (mode == 1 && stage == 3) || (mode == 2 && stage == 4);
+  if (filt) {
+    PROF_BEGIN(FR_KC_FILTER);
+    launch_entropy_min<T, TR>(m, s, from_x);
+    PROF_END(FR_KC_FILTER);
+  }
   if (ns) {
     if (m->np) {
       PROF_BEGIN(FR_KC_FACE_U);
@@ -518,6 +550,11 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
       });
     }
     PROF_END(FR_KC_VOL);
+    if (filt) {
+      PROF_BEGIN(FR_KC_FILTER);
+      launch_filter<T, TR>(m, s, D, last_stage);
+      PROF_END(FR_KC_FILTER);
+    }
   }
 }
 
@@ -614,7 +651,7 @@ int build_graph(fr_mesh* m, int scheme) {
   if (e != cudaSuccess)
     return fail(FR_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
   m->graph_stream[scheme] = s;
-  m->graph_variant[scheme] = m->variant;
+  m->graph_epoch[scheme] = m->epoch;
   return FR_OK;
 }
 
@@ -623,7 +660,7 @@ int do_rk(fr_mesh* m, int scheme, double dt, int nsteps) {
   int rc = ensure_uf<T, TR>(m);
   if (rc) return rc;
   if (!m->graph[scheme] || m->graph_stream[scheme] != m->stream ||
-      m->graph_variant[scheme] != m->variant) {
+      m->graph_epoch[scheme] != m->epoch) {
     if ((rc = build_graph<T, TR>(m, scheme))) return rc;
   }
   m->h_dt = dt;
@@ -986,6 +1023,7 @@ int fr_set_kernel_variant(fr_mesh* m, int variant) {
   if (variant == FR_VARIANT_DENSE && m->precision == FR_MIXED)
     return fail(FR_EINVAL, "FR_MIXED runs the sum-factorised kernels only");
   m->variant = variant;
+  ++m->epoch;
   return FR_OK;
 }
 
@@ -1042,3 +1080,5 @@ int fr_get_pairs(const fr_mesh* m, int64_t* n_interior, int64_t* n_boundary) {
 }
 
 }  // extern "C"
+
+#include "fr_api_filter.inc"

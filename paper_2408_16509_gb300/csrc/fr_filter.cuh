@@ -1,0 +1,531 @@
+// Entropy filter with a learned start guess (PyFR v2.0.3, Section 3.2).
+//
+// The paper filters, per element, the high modes of the solution when it
+// violates positivity of density or pressure or a minimum-entropy
+// condition, with the filter strength found iteratively so that as little
+// filtering as possible is applied.  Reading used here (no formulas in the
+// paper):
+//   u^ = V^{-1} u in the orthonormal modal basis, u^_k <- exp(-zeta
+//   (d_k/p)^2) u^_k with d_k the total degree (the mean is untouched);
+//   constraints at solution and flux points: rho >= 1e-8, p >= 1e-8,
+//   s = p rho^-gamma >= s_min - 1e-8 s_min, s_min = min of s over the stage
+//   input at the element's solution points, own flux points and the partner
+//   flux points across its faces;
+//   margin g(zeta) = min((rho-1e-8)/rho_mean, (p-1e-8)/p_mean,
+//   (s - s_min + 1e-8 s_min)/s_min), evaluated in FP64;
+//   zeta* = the smallest feasible strength, by a bracketed Illinois
+//   iteration (relative tolerance 1e-6, at most 24 evaluations) started
+//   from [0, 36] or from a predicted guess z0 (bracket opened at z0, then
+//   z0 / r or r z0 with r = 1.25 by default, then halving / doubling).
+//   The entropy tolerance is 1e-8 for FP64 stage values and 2^-20 for FP32
+//   ones (1e-8 is below FP32 resolution, where the decision would be made
+//   by rounding noise).
+// The predictor: 4 element features -> Linear(4,32)-SiLU-Linear(32,32)-SiLU
+// -Linear(32,1)-softplus, BF16 weights and FP32 accumulation.
+#pragma once
+#include <cuda_bf16.h>
+
+#include "fr_kernels.cuh"
+
+namespace frgb {
+
+constexpr int kMlpH = 32;
+constexpr int kMlpIn = 4;
+constexpr int kMlpParams = kMlpH * kMlpIn + kMlpH + kMlpH * kMlpH + kMlpH +
+                           kMlpH + 1 + 2 * kMlpIn;  // 1257
+constexpr int kMlpTrain = kMlpParams - 2 * kMlpIn;   // 1249
+// offsets in the parameter vector
+constexpr int kW1 = 0, kB1 = kW1 + kMlpH * kMlpIn, kW2 = kB1 + kMlpH,
+              kB2 = kW2 + kMlpH * kMlpH, kW3 = kB2 + kMlpH, kB3 = kW3 + kMlpH,
+              kMean = kB3 + 1, kStd = kMean + kMlpIn;
+
+constexpr double kZetaMax = 36.0;
+constexpr double kEpsPos = 1e-8;
+constexpr double kRelTol = 1e-6;
+constexpr int kMaxEvals = 24;
+constexpr int kFilterThreads = 128;
+
+struct FilterStats {
+  unsigned long long filtered;    // element-stages filtered (zeta > 0)
+  unsigned long long evals;       // margin evaluations in those
+  unsigned long long fallbacks;   // elements filtered with zeta_max
+  unsigned long long samples;     // training samples written
+  unsigned long long guessed;     // element-stages that used the predictor
+};
+
+template <typename T>
+struct FilterOps {
+  const T* VinvT;   // [nu][nm]   modal <- nodal, transposed
+  const T* VT;      // [nm][nu+nf] nodal (solution then flux points) <- modal
+  const T* deg;     // [nm] mode degree / p
+  const T* W;       // [nu] integration weights
+  const int32_t* partner;  // [ne][nf] partner flux-point code or -1
+};
+
+struct FilterArgs {
+  double gamma;
+  double tau;            // relative entropy tolerance
+  double ratio;          // first bracket step around a predicted guess
+  float* zeta_last;      // [ne] zeta of the last filtered stage (0: none)
+  int* evals_last;       // [ne] margin evaluations of the last stage
+  double* smin;          // [ne] of this type
+  FilterStats* stats;
+  float* samples;        // [cap][5] (4 features, zeta*)
+  unsigned long long cap;
+  const __nv_bfloat16* mlp;  // predictor weights or nullptr
+  const float* mlp_norm;     // mean[4], std[4]
+};
+
+__device__ __forceinline__ double entropy_of(double r, double mx, double my,
+                                             double mz, double E, double g,
+                                             double* p_out) {
+  double p = (g - 1.0) * (E - 0.5 * (mx * mx + my * my + mz * mz) / r);
+  *p_out = p;
+  if (r > 0.0 && p > 0.0) return p * pow(r, -g);
+  return INFINITY;
+}
+
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// s_min per element from the stage input: one warp per element.
+template <typename T, typename TR, int NU, int NF>
+__global__ void k_entropy_min(long long ne, const T* __restrict__ uin,
+                              const TR* __restrict__ X,
+                              const T* __restrict__ uf_all, TypeTab tt,
+                              int tidx, const int32_t* __restrict__ partner,
+                              double gamma, double* __restrict__ smin) {
+  const int lane = threadIdx.x & 31;
+  const long long e = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (e >= ne) return;
+  double m = INFINITY, p;
+  for (int z = lane; z < NU; z += 32) {
+    double v[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+      v[k] = uin ? double(uin[(e * 5 + k) * NU + z]) : double(X[(e * 5 + k) * NU + z]);
+    m = fmin(m, entropy_of(v[0], v[1], v[2], v[3], v[4], gamma, &p));
+  }
+  const T* uf = uf_all + tt.off_f[tidx];
+  for (int f = lane; f < NF; f += 32) {
+    double v[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) v[k] = double(uf[(e * 5 + k) * NF + f]);
+    m = fmin(m, entropy_of(v[0], v[1], v[2], v[3], v[4], gamma, &p));
+    int32_t c = partner[e * NF + f];
+    if (c >= 0) {
+      int t2, f2;
+      long long e2;
+      decode_fp(c, tt, &t2, &e2, &f2);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) v[k] = double(uf_all[fp_index(tt, t2, e2, f2, 5, k)]);
+      m = fmin(m, entropy_of(v[0], v[1], v[2], v[3], v[4], gamma, &p));
+    }
+  }
+  m = warp_min(m);
+  if (lane == 0) smin[e] = isfinite(m) ? m : 0.0;
+}
+
+// Block-wide reductions for the filter kernel.
+__device__ __forceinline__ double block_min(double v, double* red) {
+  v = warp_min(v);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double r = INFINITY;
+  for (int i = 0; i < kFilterThreads / 32; ++i) r = fmin(r, red[i]);
+  return r;
+}
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  for (int i = 0; i < kFilterThreads / 32; ++i) r += red[i];
+  return r;
+}
+
+__device__ __forceinline__ float silu_f(float x) { return x / (1.0f + __expf(-x)); }
+
+// Predictor evaluated by warp 0 (lane j = hidden unit j); returns z0 on
+// lane 0.
+__device__ float mlp_guess(const float feat[4], const __nv_bfloat16* w,
+                           const float* norm) {
+  const int j = threadIdx.x & 31;
+  float xn[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) xn[i] = (feat[i] - norm[i]) / norm[4 + i];
+  float a1 = __bfloat162float(w[kB1 + j]);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) a1 += __bfloat162float(w[kW1 + j * 4 + i]) * xn[i];
+  float h1 = silu_f(a1);
+  float a2 = __bfloat162float(w[kB2 + j]);
+  for (int i = 0; i < kMlpH; ++i)
+    a2 += __bfloat162float(w[kW2 + j * kMlpH + i]) * __shfl_sync(0xffffffffu, h1, i);
+  float h2 = silu_f(a2);
+  float o = __bfloat162float(w[kW3 + j]) * h2;
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) o += __shfl_xor_sync(0xffffffffu, o, s);
+  o += __bfloat162float(w[kB3]);
+  return o > 20.f ? o : log1pf(__expf(o));
+}
+
+// Filter the stage value of each element that violates the constraints.
+// reg / regR: the register holding the new stage value (type T or TR, one
+// of them null); uf: this type's flux-point traces of that value.
+template <typename T, typename TR, int NU, int NF>
+__global__ void __launch_bounds__(kFilterThreads)
+    k_filter(long long ne, T* __restrict__ reg, TR* __restrict__ regR,
+             T* __restrict__ uf, FilterOps<T> op, FilterArgs fa) {
+  constexpr int NM = NU, NP = NU + NF;
+  __shared__ T uh[5][NM];       // modal coefficients
+  __shared__ T sg[NM];          // filtered weights sigma_k
+  __shared__ double red[kFilterThreads / 32];
+  __shared__ double s_z;        // requested strength
+  const long long e = blockIdx.x;
+  const int tid = threadIdx.x;
+  if (e >= ne) return;
+  const double g = fa.gamma;
+  // load the state into registers of a point-parallel layout, then modes
+  __shared__ T us[5][NU];
+  for (int z = tid; z < NU; z += kFilterThreads)
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+      us[k][z] = reg ? reg[(e * 5 + k) * NU + z] : T(regR[(e * 5 + k) * NU + z]);
+  __syncthreads();
+  for (int m = tid; m < NM; m += kFilterThreads) {
+    T acc[5] = {0, 0, 0, 0, 0};
+    for (int z = 0; z < NU; ++z) {
+      T w = op.VinvT[z * NM + m];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) acc[k] += w * us[k][z];
+    }
+#pragma unroll
+    for (int k = 0; k < 5; ++k) uh[k][m] = acc[k];
+  }
+  // element means of density and pressure
+  double wr = 0.0, wp = 0.0, ws = 0.0;
+  for (int z = tid; z < NU; z += kFilterThreads) {
+    double p;
+    entropy_of(double(us[0][z]), double(us[1][z]), double(us[2][z]),
+               double(us[3][z]), double(us[4][z]), g, &p);
+    double w = double(op.W[z]);
+    wr += w * double(us[0][z]);
+    wp += w * p;
+    ws += w;
+  }
+  const double wsum = block_sum(ws, red);
+  const double rmean = fmax(block_sum(wr, red) / wsum, kEpsPos);
+  const double pmean = fmax(block_sum(wp, red) / wsum, kEpsPos);
+  const double smin = fa.smin[e];
+  // margin of the filtered polynomial at strength z (all threads)
+  auto margin = [&](double z, float* feat) -> double {
+    for (int m = tid; m < NM; m += kFilterThreads)
+      sg[m] = T(exp(-z * double(op.deg[m]) * double(op.deg[m])));
+    __syncthreads();
+    double mr = INFINITY, mp = INFINITY, ms = INFINITY;
+    for (int i = tid; i < NP; i += kFilterThreads) {
+      T v[5] = {0, 0, 0, 0, 0};
+      for (int m = 0; m < NM; ++m) {
+        T w = op.VT[m * NP + i] * sg[m];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) v[k] += w * uh[k][m];
+      }
+      double p;
+      entropy_of(double(v[0]), double(v[1]), double(v[2]), double(v[3]),
+                 double(v[4]), g, &p);
+      double r = double(v[0]);
+      mr = fmin(mr, r);
+      mp = fmin(mp, p);
+      // s = p rho^-gamma (negative where p < 0), -inf where rho <= 0
+      ms = fmin(ms, r > 0.0 ? p * pow(r, -g) : -INFINITY);
+    }
+    mr = block_min(mr, red);
+    mp = block_min(mp, red);
+    ms = block_min(ms, red);
+    double gr = (mr - kEpsPos) / rmean, gp = (mp - kEpsPos) / pmean;
+    double gs = smin > 0.0 ? (ms - smin + fa.tau * smin) / smin : INFINITY;
+    double gm = fmin(gr, fmin(gp, gs));
+    if (isnan(gm)) gm = -INFINITY;
+    if (feat) {  // predictor inputs from the unfiltered state (z = 0)
+      double eh = 0.0, et = 0.0;
+      for (int m = tid; m < NM; m += kFilterThreads) {
+        double d = double(op.deg[m]), c = double(uh[0][m]);
+        if (d > 1.0) eh += c * c;
+        if (d > 0.0) et += c * c;
+      }
+      eh = block_sum(eh, red);
+      et = block_sum(et, red);
+      feat[0] = float(fmin(fmax(log10((eh + 1e-30) / (et + 1e-30)), -30.0), 30.0));
+      feat[1] = float(fmin(fmax(mr / rmean, -30.0), 30.0));
+      feat[2] = float(fmin(fmax(mp / pmean, -30.0), 30.0));
+      // log10 of the entropy-bound violation (floor 1e-14)
+      double f3 = 1.0;
+      if (smin > 0.0 && ms > -INFINITY && mr > 0.0 && mp > 0.0)
+        f3 = fmax((smin - ms) / smin, 1e-14);
+      feat[3] = float(log10(f3));
+    }
+    return gm;
+  };
+  float feat[4];
+  double g0 = margin(0.0, feat);
+  if (g0 >= 0.0) {  // uniform across the block
+    if (tid == 0 && fa.zeta_last) {
+      fa.zeta_last[e] = 0.f;
+      fa.evals_last[e] = 1;
+    }
+    return;
+  }
+  // ---- root-find: thread 0 drives, every evaluation is a block operation
+  double lo = 0.0, glo = g0, hi = kZetaMax, ghi = 0.0;
+  int evals = 1;
+  bool fallback = false, use_guess = false;
+  double guess = -1.0;
+  if (fa.mlp) {
+    float z0 = 0.f;
+    if (tid < 32) z0 = mlp_guess(feat, fa.mlp, fa.mlp_norm);
+    if (tid == 0) s_z = double(z0);
+    __syncthreads();
+    guess = s_z;
+    __syncthreads();
+    use_guess = guess > 0.0 && guess < kZetaMax;
+  }
+  bool bracketed = false, done = false;
+  double result = 0.0;
+  if (!use_guess) {
+    ghi = margin(kZetaMax, nullptr);
+    ++evals;
+    if (ghi < 0.0) {
+      done = true;
+      fallback = true;
+      result = kZetaMax;
+    } else {
+      bracketed = true;
+    }
+  } else {
+    double gz = margin(guess, nullptr);
+    ++evals;
+    if (gz >= 0.0) {
+      hi = guess;
+      ghi = gz;
+      double z = guess / fa.ratio;
+      for (int it = 0; it < 64 && !bracketed && !done; ++it) {
+        gz = margin(z, nullptr);
+        ++evals;
+        if (gz < 0.0) {
+          lo = z;
+          glo = gz;
+          bracketed = true;
+        } else {
+          hi = z;
+          ghi = gz;
+          if (z < 1e-6) {
+            done = true;
+            result = hi;
+          }
+          z *= 0.5;
+        }
+      }
+    } else {
+      lo = guess;
+      glo = gz;
+      double z = fmin(fa.ratio * guess, kZetaMax);
+      for (int it = 0; it < 64 && !bracketed && !done; ++it) {
+        gz = margin(z, nullptr);
+        ++evals;
+        if (gz >= 0.0) {
+          hi = z;
+          ghi = gz;
+          bracketed = true;
+        } else {
+          lo = z;
+          glo = gz;
+          if (z >= kZetaMax) {
+            done = true;
+            fallback = true;
+            result = kZetaMax;
+          }
+          z = fmin(2.0 * z, kZetaMax);
+        }
+      }
+    }
+    if (!bracketed && !done) {  // cannot happen within the caps; be safe
+      done = true;
+      fallback = true;
+      result = kZetaMax;
+    }
+  }
+  if (!done) {
+    int side = 0;
+    while (hi - lo > kRelTol * hi && evals < kMaxEvals) {
+      double z = (lo * ghi - hi * glo) / (ghi - glo);
+      if (!(lo < z && z < hi)) z = 0.5 * (lo + hi);
+      double gz = margin(z, nullptr);
+      ++evals;
+      if (gz >= 0.0) {
+        hi = z;
+        ghi = gz;
+        if (side == 1) glo *= 0.5;
+        side = 1;
+      } else {
+        lo = z;
+        glo = gz;
+        if (side == -1) ghi *= 0.5;
+        side = -1;
+      }
+    }
+    result = hi;
+  }
+  // write the filtered state and its flux-point values
+  for (int m = tid; m < NM; m += kFilterThreads)
+    sg[m] = T(exp(-result * double(op.deg[m]) * double(op.deg[m])));
+  __syncthreads();
+  for (int i = tid; i < NP; i += kFilterThreads) {
+    T v[5] = {0, 0, 0, 0, 0};
+    for (int m = 0; m < NM; ++m) {
+      T w = op.VT[m * NP + i] * sg[m];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) v[k] += w * uh[k][m];
+    }
+    if (i < NU) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        if (reg) reg[(e * 5 + k) * NU + i] = v[k];
+        else regR[(e * 5 + k) * NU + i] = TR(v[k]);
+      }
+    } else {
+      int f = i - NU;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) uf[(e * 5 + k) * NF + f] = v[k];
+    }
+  }
+  if (tid == 0) {
+    if (fa.zeta_last) {
+      fa.zeta_last[e] = float(result);
+      fa.evals_last[e] = evals;
+    }
+    atomicAdd(&fa.stats->filtered, 1ull);
+    atomicAdd(&fa.stats->evals, (unsigned long long)evals);
+    if (fallback) atomicAdd(&fa.stats->fallbacks, 1ull);
+    if (use_guess) atomicAdd(&fa.stats->guessed, 1ull);
+    if (!fallback && fa.samples) {
+      unsigned long long i = atomicAdd(&fa.stats->samples, 1ull);
+      if (i < fa.cap) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) fa.samples[i * 5 + k] = feat[k];
+        fa.samples[i * 5 + 4] = float(result);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ MLP
+// Training is deterministic: one kernel computes per-sample activations and
+// deltas, a second reduces every parameter's gradient over all samples in a
+// fixed order, a third applies Adam.
+
+__device__ __forceinline__ float dsilu_f(float x) {
+  float s = 1.0f / (1.0f + expf(-x));
+  return s * (1.0f + x * (1.0f - s));
+}
+
+// per sample: xn[4], h1[32], h2[32], da1[32], da2[32], do, loss term
+constexpr int kMlpScratch = 4 + 32 * 4 + 2;
+
+__global__ void k_mlp_sample(int n, const float* __restrict__ w,
+                             const float* __restrict__ x,
+                             const float* __restrict__ zstar,
+                             float* __restrict__ scr) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  float* o = scr + size_t(s) * kMlpScratch;
+  float xn[4], a1[32], h1[32], a2[32], h2[32];
+  for (int i = 0; i < 4; ++i) xn[i] = (x[s * 4 + i] - w[kMean + i]) / w[kStd + i];
+  for (int j = 0; j < 32; ++j) {
+    float a = w[kB1 + j];
+    for (int i = 0; i < 4; ++i) a += w[kW1 + j * 4 + i] * xn[i];
+    a1[j] = a;
+    h1[j] = a / (1.0f + expf(-a));
+  }
+  float out = w[kB3];
+  for (int j = 0; j < 32; ++j) {
+    float a = w[kB2 + j];
+    for (int i = 0; i < 32; ++i) a += w[kW2 + j * 32 + i] * h1[i];
+    a2[j] = a;
+    h2[j] = a / (1.0f + expf(-a));
+    out += w[kW3 + j] * h2[j];
+  }
+  float z0 = out > 20.f ? out : log1pf(expf(out));
+  float r = logf(z0) - logf(zstar[s]);
+  float dz0 = 2.0f * r / float(n) / z0;
+  float dout = dz0 / (1.0f + expf(-out));
+  float da2[32];
+  for (int j = 0; j < 32; ++j) da2[j] = dout * w[kW3 + j] * dsilu_f(a2[j]);
+  for (int i = 0; i < 4; ++i) o[i] = xn[i];
+  for (int i = 0; i < 32; ++i) {
+    float dh1 = 0.f;
+    for (int j = 0; j < 32; ++j) dh1 += da2[j] * w[kW2 + j * 32 + i];
+    o[4 + i] = h1[i];
+    o[36 + i] = h2[i];
+    o[68 + i] = dh1 * dsilu_f(a1[i]);
+    o[100 + i] = da2[i];
+  }
+  o[132] = dout;
+  o[133] = r * r / float(n);
+}
+
+// one thread per trainable parameter (and one for the loss), summing over
+// samples in order
+__global__ void k_mlp_reduce(int n, const float* __restrict__ scr,
+                             float* __restrict__ grad, float* __restrict__ loss) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q > kMlpTrain) return;
+  double acc = 0.0;
+  for (int s = 0; s < n; ++s) {
+    const float* o = scr + size_t(s) * kMlpScratch;
+    float v;
+    if (q == kMlpTrain) v = o[133];
+    else if (q < kB1) v = o[68 + q / 4] * o[q % 4];                  // W1
+    else if (q < kW2) v = o[68 + (q - kB1)];                         // b1
+    else if (q < kB2) {                                              // W2
+      int r = q - kW2;
+      v = o[100 + r / 32] * o[4 + r % 32];
+    } else if (q < kW3) v = o[100 + (q - kB2)];                      // b2
+    else if (q < kB3) v = o[132] * o[36 + (q - kW3)];                // W3
+    else v = o[132];                                                 // b3
+    acc += double(v);
+  }
+  if (q == kMlpTrain) *loss = float(acc);
+  else grad[q] = float(acc);
+}
+
+__global__ void k_mlp_adam(float* __restrict__ w, const float* __restrict__ grad,
+                           float* __restrict__ m1, float* __restrict__ m2,
+                           int step, float lr) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= kMlpTrain) return;
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  float gq = grad[q];
+  float a = b1 * m1[q] + (1 - b1) * gq;
+  float b = b2 * m2[q] + (1 - b2) * gq * gq;
+  m1[q] = a;
+  m2[q] = b;
+  float ah = a / (1 - powf(b1, float(step)));
+  float bh = b / (1 - powf(b2, float(step)));
+  w[q] -= lr * ah / (sqrtf(bh) + eps);
+}
+
+}  // namespace frgb

@@ -645,6 +645,20 @@ RefElement make_ref(int kind, int p) {
   }
   e.nupts = int(e.upts.size() / 3);
   e.nfaces = int(e.faces.size());
+  // total degree of every mode, in the order of RefElement::basis
+  if (kind == EK_HEX) {
+    for (int k = 0; k <= p; ++k)
+      for (int j = 0; j <= p; ++j)
+        for (int i = 0; i <= p; ++i) e.mdeg.push_back(i + j + k);
+  } else if (kind == EK_PRI) {
+    for (int k = 0; k <= p; ++k)
+      for (int i = 0; i <= p; ++i)
+        for (int j = 0; j <= p - i; ++j) e.mdeg.push_back(i + j + k);
+  } else {
+    for (int i = 0; i <= p; ++i)
+      for (int j = 0; j <= p - i; ++j)
+        for (int k = 0; k <= p - i - j; ++k) e.mdeg.push_back(i + j + k);
+  }
   // flux points face by face
   e.face_start.push_back(0);
   std::vector<std::vector<double>> fst(e.nfaces);

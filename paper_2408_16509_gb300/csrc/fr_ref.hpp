@@ -37,7 +37,8 @@ struct RefElement {
   std::vector<double> D;           // [3][nupts][nupts]
   std::vector<double> LIFT;        // [nupts][nfpts]
   std::vector<double> W;           // [nupts]  integration weights
-  std::vector<double> vdm_inv;     // [nupts][nupts] nodal <- modal
+  std::vector<double> vdm_inv;     // [nupts][nupts] modal <- nodal
+  std::vector<int> mdeg;           // [nupts] total degree of each mode
   // hexahedron only: 1D factors on the Gauss-Legendre points x1
   std::vector<double> x1;          // [p+1]
   std::vector<double> d1;          // [p+1][p+1]  l_m'(x_a)

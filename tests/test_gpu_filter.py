@@ -1,0 +1,204 @@
+"""GPU entropy filter and learned start guess (Section 3.2) against the
+oracle.
+
+Tolerances: in FP64 both sides take the same root-find decisions (margins
+agree to rounding), so the filtered elements and evaluation counts match
+exactly and solutions to 1e-10 relative L2.  In FP32 (FP64 checks) the
+margins differ by FP32 rounding, so a decision near a root can differ; the
+root tolerance 1e-6 in zeta bounds the effect: 1e-5 relative L2 after the
+steps.  The predictor's gradient is FP32 against the FP64 oracle: 1e-4
+relative per entry (FP32 accumulation over the batch).
+"""
+import numpy as np
+import pytest
+
+import paper_2408_16509_gb300 as fr
+from frinputs import box_hex, ics
+from frtest import lib_state, oracle_state, rel_l2
+from oracle import entropy_filter as EF
+from oracle import mlp
+from oracle.fr import FRSystem
+from oracle.mesh import FRMesh as OracleMesh
+
+pytestmark = pytest.mark.gpu
+POST = ics.SHU_OSHER_POST
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    fr.build()
+
+
+def _strip(n, precision="fp64"):
+    spec = box_hex((n, 1, 1), lo=(-5, 0, 0), hi=(5, 10 / n, 10 / n),
+                   periodic=(1, 2))
+    bcs = {0: ("state", POST[0], POST[1], 0.0, 0.0, POST[2]), 1: ("extrap",)}
+    o = OracleMesh(spec.as_dict(), 3)
+    s = FRSystem(o, "euler", bcs=bcs)
+    g = fr.FRMesh(spec, 3, physics="euler", bcs=bcs, precision=precision)
+    return o, s, g
+
+
+def _oracle_run(s, u, steps, dt, predictor=None):
+    n_f = n_e = 0
+    for _ in range(steps):
+        u, stats = EF.rk4_step_filtered(s, u, dt, predictor=predictor)
+        for z, n, fb in stats:
+            n_f += int((z["hex"] > 0).sum())
+            n_e += int(n["hex"][z["hex"] > 0].sum())
+    return u, n_f, n_e
+
+
+def test_filter_fp64_matches_oracle():
+    """Three filtered RK4 steps on a Shu-Osher strip: the same elements are
+    filtered with the same strengths, and the solutions agree."""
+    o, s, g = _strip(64)
+    g.set_solution(lib_state(g, ics.shu_osher))
+    g.filter_enable(True)
+    u = oracle_state(o, ics.shu_osher)
+    dt = 2e-3
+    n_g = n_o = 0
+    for _ in range(3):
+        g.filter_stats(reset=True)
+        g.rk_step("rk4", dt, 1)
+        zg, eg = g.filter_last()
+        u, stats = EF.rk4_step_filtered(s, u, dt)
+        zo = stats[3][0]["hex"]
+        assert np.array_equal(zg > 0, zo > 0)
+        on = zo > 0
+        assert np.all(np.abs(zg[on] - zo[on]) <= 2e-6 * zo[on])
+        n_g += g.filter_stats()["evals"]
+        n_o += sum(int(st[1]["hex"][st[0]["hex"] > 0].sum()) for st in stats)
+        assert g.filter_stats()["fallbacks"] == 0
+    # evaluation counts differ only where an iterate lands within rounding
+    # of the root (sign decided by the last bit)
+    assert abs(n_g - n_o) <= 0.1 * n_o
+    err = rel_l2(g.get_solution(), u)
+    assert err.max() < 1e-10, err
+
+
+def test_filter_fp32_with_fp64_checks_against_oracle():
+    """FP32 stage values, FP64 checks, entropy tolerance 2^-20 on both
+    sides.  Near the shock a filter/no-filter decision can flip with FP32
+    rounding of the state, and a flipped element changes its density by
+    the filtered amount; the other variables are nearly uniform there.
+    Bounds: density 5e-3, other variables 1e-5 relative L2."""
+    o, s, g = _strip(64, precision="fp32")
+    g.set_solution(lib_state(g, ics.shu_osher))
+    g.filter_enable(True)
+    dt = 2e-3
+    g.rk_step("rk4", dt, 3)
+    u = oracle_state(o, ics.shu_osher)
+    for _ in range(3):
+        u, _ = EF.rk4_step_filtered(s, u, dt, tau=2.0 ** -20)
+    err = rel_l2(g.get_solution(), u)
+    assert err[0] < 5e-3 and err[1:].max() < 1e-5, err
+
+
+def test_unfiltered_run_blows_up_filtered_run_does_not():
+    _, _, g = _strip(64)
+    g.set_solution(lib_state(g, ics.shu_osher))
+    with pytest.raises(fr.FRError) as e:
+        g.rk_step("rk4", 2e-3, 10)
+    assert e.value.name == "FR_ENONFINITE"
+    g.set_solution(lib_state(g, ics.shu_osher))
+    g.filter_enable(True)
+    g.rk_step("rk4", 2e-3, 10)
+    assert np.isfinite(g.get_solution()["hex"]).all()
+
+
+def test_mlp_gradient_matches_oracle():
+    rng = np.random.default_rng(4)
+    theta = mlp.init(seed=1, mean=rng.normal(size=4),
+                     std=rng.uniform(0.5, 2.0, 4))
+    x = rng.normal(size=(300, 4))
+    zs = np.exp(rng.normal(size=300))
+    loss_o, g_o = mlp.loss_and_grad(theta, x, zs)
+    loss_g, g_g = fr.mlp_loss_grad(theta, x, zs)
+    assert abs(loss_g - loss_o) < 1e-5 * max(1.0, loss_o)
+    scale = np.abs(g_o).max()
+    assert np.abs(g_g - g_o).max() < 1e-4 * scale
+
+
+def _bf16(a):
+    """Round float32 values to bfloat16 (nearest even), back to float."""
+    b = np.asarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) >> 16 << 16
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _violating_state(g, dt, steps):
+    """A state straight out of unfiltered RK steps from the current
+    solution: it violates the constraints near the shock when the bound
+    comes from the state it started from."""
+    g.filter_enable(False)
+    g.rk_step("rk4", dt, steps)
+    g.filter_enable(True)
+    return g.get_solution()
+
+
+def test_learned_start_guess_cuts_root_find_work():
+    """Samples from plain root-finds train the predictor on the GPU (own
+    forward / backward / Adam kernels); on the same violating states the
+    predicted start needs fewer margin evaluations and finds the same
+    strengths as the plain bracket, and the GPU agrees with the oracle
+    driven by the same BF16-rounded predictor."""
+    o, s, g = _strip(128)
+    dt = 1e-3
+    g.set_solution(lib_state(g, ics.shu_osher))
+    g.filter_enable(True, sample_capacity=1 << 16)
+    g.filter_solution()
+    g.filter_samples()
+    g.rk_step("rk4", dt, 30)
+    samp = g.filter_samples()
+    assert len(samp) > 200
+    x, zs = samp[:, :4].astype(np.float64), samp[:, 4].astype(np.float64)
+    mean, std = x.mean(axis=0), x.std(axis=0) + 1e-6
+    theta0 = mlp.init(seed=0, mean=mean, std=std)
+    loss0, _ = mlp.loss_and_grad(theta0, x, zs)
+    theta, hist = fr.mlp_train(x, zs, theta0, epochs=3000, lr=3e-3)
+    assert hist[-1] < 0.25 * loss0
+    # first bracket step sized to the predictor's own fit error
+    pred = mlp.forward(theta.astype(np.float64), x)[0]
+    rms = float(np.sqrt(np.mean((np.log(pred) - np.log(zs)) ** 2)))
+    ratio = float(np.clip(np.exp(1.5 * rms), 1.02, 2.0))
+    print("rms log error", rms, "bracket ratio", ratio)
+    theta = np.concatenate([theta, [ratio]]).astype(np.float32)
+    base = g.get_solution()
+    smin = EF.element_smin(s, base)
+    tot_plain = tot_mlp = same = common = 0
+    for k in range(5):
+        g.set_solution(base)
+        bad = _violating_state(g, dt, 1 + k)
+        g.filter_set_mlp(None)
+        g.set_solution(bad)
+        g.filter_stats(reset=True)
+        g.filter_solution(smin)
+        z_plain, e_plain = g.filter_last()
+        g.filter_set_mlp(theta)
+        g.set_solution(bad)
+        g.filter_solution(smin)
+        z_mlp, e_mlp = g.filter_last()
+        on = (z_plain > 0) & (z_mlp > 0)
+        tot_plain += int(e_plain[z_plain > 0].sum())
+        tot_mlp += int(e_mlp[z_mlp > 0].sum())
+        common += int(on.sum())
+        same += int(np.sum(np.abs(z_mlp[on] - z_plain[on])
+                           <= 2e-6 * z_plain[on]))
+        print("state", k, "filtered", int((z_plain > 0).sum()),
+              "evals plain", int(e_plain[z_plain > 0].sum()),
+              "with predictor", int(e_mlp[z_mlp > 0].sum()))
+    assert common > 0 and same >= 0.9 * common
+    assert tot_mlp < 0.85 * tot_plain, (tot_plain, tot_mlp)
+    # the oracle with the same BF16 predictor on the last violating state
+    th = theta[:mlp.NPARAM].astype(np.float64).copy()
+    th[:mlp.NTRAIN] = _bf16(theta[:mlp.NTRAIN])
+
+    def predictor(f):
+        return float(mlp.forward(th, f[None, :])[0][0])
+    _, zo, _, _ = EF.filter_state(s, bad, smin, predictor=predictor,
+                                  ratio=ratio)
+    zo = zo["hex"]
+    assert np.array_equal(zo > 0, z_mlp > 0)
+    on = zo > 0
+    assert np.sum(np.abs(z_mlp[on] - zo[on]) <= 2e-6 * zo[on]) >= 0.9 * on.sum()
