@@ -217,6 +217,7 @@ def measure(fr, torch, precision, steps, warmup, device, dist):
         ms = float(tt.item())
         dist.barrier()
     final = mesh.get_solution()["hex"]
+    tuning = mesh.tuning()
     prof = {}
     reps = 3
     for _ in range(reps):
@@ -224,6 +225,7 @@ def measure(fr, torch, precision, steps, warmup, device, dist):
             a = prof.setdefault(k, [0.0, 0])
             a[0] += t / reps
             a[1] = n
+    prof["_tuning"] = tuning
     return mesh, u0, ms, clocks, prof, final
 
 
@@ -246,6 +248,7 @@ def run_ours(args):
     peaks, src = _peaks()
     mesh, u0, ms, clocks, prof, final = measure(
         fr, torch, args.precision, args.steps, args.warmup, local, dist)
+    tuning = prof.pop("_tuning")
     ne, nu, nf = mesh.info("hex")
     units_per_step = ne * nu * 5 * STAGES
     value = units_per_step * args.steps * world / (ms * 1e-3) / 1e9
@@ -293,6 +296,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(hout.nbytes)},
         "gpu_launches": launches_per_step * args.steps,
         "kernel_ms_per_step": {k: v[0] for k, v in prof.items() if v[1]},
+        "kernel_family": {"active": tuning[0], "tuned_ms_per_step": tuning[1]},
         "roofline": roof,
     }
     mesh.close()
@@ -303,6 +307,7 @@ def run_ours(args):
                 continue
             m2, _, ms2, _, prof2, fin2 = measure(
                 fr, torch, prec, args.steps, args.warmup, local, None)
+            tun2 = prof2.pop("_tuning")
             w2 = 8 if prec == "fp64" else 4
             wr2 = 4 if prec == "fp32" else 8
             if args.precision == "fp64":
@@ -322,14 +327,199 @@ def run_ours(args):
                     prof2, kernel_models(nu, nf, ne, w2, wr2, npair), peaks,
                     src, prec),
                 "kernel_ms_per_step": {k: v[0] for k, v in prof2.items()
-                                       if v[1]}}
+                                       if v[1]},
+                "kernel_family": {"active": tun2[0],
+                                  "tuned_ms_per_step": tun2[1]}}
             m2.close()
+    if args.configs and world == 1:
+        line["configs"] = other_configs(fr, torch, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------- other workloads
+def _timed_steps(torch, mesh, stream, scheme, dt, steps):
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    mesh.rk_step(scheme, dt, steps)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    return t0.elapsed_time(t1)
+
+
+def _gdofs(mesh, stages, steps, ms):
+    pts = sum(mesh.info(t)[0] * mesh.info(t)[1] for t in mesh.types)
+    return pts * 5 * stages * steps / (ms * 1e-3) / 1e9
+
+
+def _state(mesh, fn):
+    out = {}
+    for t in mesh.types:
+        x = mesh.points(t)
+        out[t] = fn(x.reshape(-1, 3)).reshape(x.shape[0], x.shape[1], 5)
+    return out
+
+
+def _rel_l2(a, b):
+    num = np.zeros(5)
+    den = np.zeros(5)
+    rho = 0.0
+    for t in b:
+        d = (a[t] - b[t]).reshape(-1, 5)
+        r = b[t].reshape(-1, 5)
+        num += (d * d).sum(0)
+        den += (r * r).sum(0)
+        rho += (r[:, 0] ** 2).sum()
+    return (np.sqrt(num) / np.maximum(np.sqrt(den), np.sqrt(rho))).tolist()
+
+
+def config_vortex(fr, torch, device):
+    """Isentropic vortex, 8^3 hexes on [0,10]^3, p=2, Euler, RK4,
+    dt 0.01 x 100, FP64; error against the closed form."""
+    from frinputs import box_hex, ics
+    mesh = fr.FRMesh(box_hex((8, 8, 8), hi=(10.0, 10.0, 10.0)), 2,
+                     physics="euler", device=device)
+    st = torch.cuda.Stream(device=device)
+    mesh.set_stream(st)
+    mesh.set_solution(_state(mesh, ics.isentropic_vortex))
+    mesh.rk_step("rk4", 0.01, 3)
+    mesh.set_solution(_state(mesh, ics.isentropic_vortex))
+    ms = _timed_steps(torch, mesh, st, "rk4", 0.01, 100)
+    exact = _state(mesh, lambda x: ics.isentropic_vortex(x, t=1.0))
+    err = _rel_l2(mesh.get_solution(), exact)
+    out = {"gdof_stage_s": _gdofs(mesh, 4, 100, ms), "ms_per_step": ms / 100,
+           "rel_l2_vs_closed_form_t1": err, "precision": "fp64"}
+    mesh.close()
+    return out
+
+
+def config_tgv48_mixed(fr, torch, device, steps=10, dt=2.5e-4):
+    """TGV on 48^3 perturbed hexes, p=4, RK45 dt 2.5e-4 (1e-3 is beyond the
+    explicit limit at this h and p): mixed precision against the FP64 form
+    after the same steps."""
+    from frinputs import box_hex, ics
+    spec = box_hex((48, 48, 48), hi=(2 * np.pi,) * 3, perturb=0.1)
+    out, fin = {}, {}
+    for prec in ("mixed", "fp64"):
+        mesh = fr.FRMesh(spec, 4, physics="ns", mu=1 / RE, prandtl=PR,
+                         precision=prec, device=device)
+        st = torch.cuda.Stream(device=device)
+        mesh.set_stream(st)
+        u0 = _state(mesh, lambda x: ics.taylor_green(x, mach=MACH))
+        mesh.set_solution(u0)
+        mesh.rk_step("rk45", dt, 2)
+        mesh.set_solution(u0)
+        ms = _timed_steps(torch, mesh, st, "rk45", dt, steps)
+        fin[prec] = mesh.get_solution()
+        out[prec] = {"gdof_stage_s": _gdofs(mesh, 5, steps, ms),
+                     "ms_per_step": ms / steps}
+        mesh.close()
+    out["mixed"]["rel_l2_vs_fp64_after_steps"] = _rel_l2(fin["mixed"],
+                                                         fin["fp64"])
+    out["steps"] = steps
+    return out
+
+
+def config_mixed_elements(fr, torch, device, steps=20):
+    """40^3 cells: hexes x < 0.5, 2 prisms per cell 0.5 <= x < 0.8, 6 tets
+    x >= 0.8 (5% jitter), p=3, NS Re 1000, Ma 0.2, RK4, FP32."""
+    from frinputs import ics, mixed_box
+    spec = mixed_box(n=40)
+    pinf = 1.0 / (1.4 * 0.04)
+    far = ("state", 1.0, 1.0, 0.0, 0.0, pinf)
+    mesh = fr.FRMesh(spec, 3, physics="ns", mu=1e-3, prandtl=PR,
+                     bcs={0: far, 1: far, 2: far, 3: far}, precision="fp32",
+                     device=device)
+    st = torch.cuda.Stream(device=device)
+    mesh.set_stream(st)
+    mesh.set_solution(_state(mesh, lambda x: ics.perturbed_uniform(x)))
+    mesh.rk_step("rk4", 2e-4, 2)
+    ms = _timed_steps(torch, mesh, st, "rk4", 2e-4, steps)
+    prof = mesh.profile_step("rk4", 2e-4)
+    out = {"gdof_stage_s": _gdofs(mesh, 4, steps, ms), "ms_per_step": ms / steps,
+           "elements": {t: mesh.info(t)[0] for t in mesh.types},
+           "kernel_ms_per_step": {k: v[0] for k, v in prof.items() if v[1]}}
+    mesh.close()
+    return out
+
+
+def config_shu_osher(fr, torch, device, steps=40):
+    """256x8x8 hexes on [-5,5]x[0,0.3125]^2, p=3, Euler, RK4 dt 9e-4, FP32,
+    entropy filter: plain root-find, then the predictor trained on the
+    run's own filter solves."""
+    from frinputs import box_hex, ics
+    post = ics.SHU_OSHER_POST
+    spec = box_hex((256, 8, 8), lo=(-5.0, 0, 0), hi=(5.0, 0.3125, 0.3125),
+                   periodic=(1, 2))
+    bcs = {0: ("state", post[0], post[1], 0.0, 0.0, post[2]), 1: ("extrap",)}
+    mesh = fr.FRMesh(spec, 3, physics="euler", bcs=bcs, precision="fp32",
+                     device=device)
+    st = torch.cuda.Stream(device=device)
+    mesh.set_stream(st)
+    mesh.set_solution(_state(mesh, ics.shu_osher))
+    mesh.filter_enable(True, sample_capacity=1 << 20)
+    mesh.filter_solution()
+    mesh.filter_samples()
+    mesh.rk_step("rk4", 9e-4, 40)            # warm-up and training data
+    samp = mesh.filter_samples()
+    start = mesh.get_solution()
+    mesh.filter_stats(reset=True)
+    ms_plain = _timed_steps(torch, mesh, st, "rk4", 9e-4, steps)
+    plain = mesh.filter_stats(reset=True)
+    prof = mesh.profile_step("rk4", 9e-4)
+    mesh.filter_stats(reset=True)
+    out = {"samples": int(len(samp)),
+           "plain": {"gdof_stage_s": _gdofs(mesh, 4, steps, ms_plain),
+                     "ms_per_step": ms_plain / steps,
+                     "evals_per_filtered": plain["evals"] / max(1, plain["filtered"]),
+                     "filtered_per_step": plain["filtered"] / steps,
+                     "kernel_ms_one_step": {k: v[0] for k, v in prof.items()
+                                            if v[1]}}}
+    if len(samp) > 100:
+        x = samp[:, :4].astype(np.float64)
+        z = samp[:, 4].astype(np.float64)
+        theta = np.zeros(1257)
+        rng = np.random.default_rng(0)
+        theta[0:128] = rng.normal(0, 0.5, 128)
+        theta[160:1184] = rng.normal(0, 1 / np.sqrt(32), 1024)
+        theta[1216:1248] = rng.normal(0, 1 / np.sqrt(32), 32)
+        theta[1249:1253] = x.mean(0)
+        theta[1253:1257] = x.std(0) + 1e-6
+        th, hist = fr.mlp_train(x, z, theta, epochs=2000, lr=3e-3)
+        rms = float(np.sqrt(hist[-1]))
+        ratio = float(np.clip(np.exp(1.5 * rms), 1.02, 2.0))
+        mesh.filter_set_mlp(np.concatenate([th, [ratio]]).astype(np.float32))
+        mesh.set_solution(start)
+        mesh.filter_stats(reset=True)
+        ms_mlp = _timed_steps(torch, mesh, st, "rk4", 9e-4, steps)
+        lrn = mesh.filter_stats(reset=True)
+        out["learned"] = {"gdof_stage_s": _gdofs(mesh, 4, steps, ms_mlp),
+                          "ms_per_step": ms_mlp / steps,
+                          "evals_per_filtered": lrn["evals"] / max(1, lrn["filtered"]),
+                          "filtered_per_step": lrn["filtered"] / steps,
+                          "train_loss": [float(hist[0]), float(hist[-1])],
+                          "bracket_ratio": ratio}
+    mesh.close()
+    return out
+
+
+def other_configs(fr, torch, device):
+    out = {}
+    for name, fn in (("vortex_8^3_p2_fp64", config_vortex),
+                     ("tgv_48^3_p4_mixed", config_tgv48_mixed),
+                     ("mixed_elements_40^3_p3_fp32", config_mixed_elements),
+                     ("shu_osher_256x8x8_p3_filter", config_shu_osher)):
+        try:
+            out[name] = fn(fr, torch, device)
+        except Exception as exc:  # a failing side workload must not hide the rest
+            out[name] = {"error": repr(exc)[:300]}
+    return out
 
 
 # ------------------------------------------------------ oracle baseline
@@ -407,6 +597,8 @@ def main():
                     choices=["fp64", "fp32", "mixed"])
     ap.add_argument("--variants", type=int, default=1,
                     help="also time the other precision modes (N=1 only)")
+    ap.add_argument("--configs", type=int, default=1,
+                    help="also time the other workloads (N=1 only)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

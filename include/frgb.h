@@ -168,13 +168,23 @@ enum { FR_KC_FACE_U = 0,  /* NS common solution at interior flux points */
 int fr_profile_step(fr_mesh* mesh, int scheme, double dt, double* ms,
                     int* launches);
 
-/* Kernel family for hexahedra: FR_VARIANT_SUMFACT applies the operators
- * line by line (1D factors of the tensor-product basis), FR_VARIANT_DENSE
- * applies the full operator matrices as for prisms and tetrahedra;
- * FR_VARIANT_AUTO (default) is the sum-factorised family.  Both give the
- * same result up to rounding. */
-enum { FR_VARIANT_AUTO = 0, FR_VARIANT_DENSE = 1, FR_VARIANT_SUMFACT = 2 };
+/* Kernel family for hexahedra.  FR_VARIANT_SUMFACT applies the operators
+ * line by line (1D factors of the tensor-product basis) with metric terms
+ * stored per solution point; FR_VARIANT_SUMFACT_VERTEX (FP32 values only)
+ * computes the metric terms from the 8 vertices and recomputes gradients
+ * instead of storing them (less DRAM traffic, more arithmetic);
+ * FR_VARIANT_DENSE applies the full operator matrices as for prisms and
+ * tetrahedra.  All give the same result up to rounding.  FR_VARIANT_AUTO
+ * (default): the first fr_rk_step times one step of each applicable family
+ * on a copy of the state (restored afterwards) and keeps the fastest;
+ * fr_get_tuning reports the choice. */
+enum { FR_VARIANT_AUTO = 0, FR_VARIANT_DENSE = 1, FR_VARIANT_SUMFACT = 2,
+       FR_VARIANT_SUMFACT_VERTEX = 3 };
 int fr_set_kernel_variant(fr_mesh* mesh, int variant);
+
+/* Kernel family in use and the step times (ms, 0 if not tried) the tuner
+ * measured for families 1..3 (index = FR_VARIANT_*). */
+int fr_get_tuning(const fr_mesh* mesh, int* active, float* ms_per_step);
 
 /* Kernels and copies of the handle run on this stream (cudaStream_t);
  * NULL selects the handle's own stream. */

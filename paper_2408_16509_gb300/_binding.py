@@ -17,7 +17,7 @@ ERRORS = {-1: "FR_EINVAL", -2: "FR_ENOMEM", -3: "FR_ECUDA", -4: "FR_EMESH",
 ETYPES = {"hex": 0, "pri": 1, "tet": 2}
 PHYSICS = {"euler": 0, "ns": 1}
 PRECISION = {"fp64": 0, "fp32": 1, "mixed": 2}
-VARIANTS = {"auto": 0, "dense": 1, "sumfact": 2}
+VARIANTS = {"auto": 0, "dense": 1, "sumfact": 2, "sumfact_vertex": 3}
 SCHEMES = {"rk4": 0, "rk45": 1}
 BC_KIND = {"state": 0, "extrap": 1}
 
@@ -88,6 +88,7 @@ def load():
         "fr_get_pairs": (I, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "fr_profile_step": (I, [P, I, D, P, P]),
         "fr_set_kernel_variant": (I, [P, I]),
+        "fr_get_tuning": (I, [P, C.POINTER(I), P]),
         "fr_set_solution_static": (I, [P, I, P]),
         "fr_filter_enable": (I, [P, I, C.c_int64]),
         "fr_filter_set_mlp": (I, [P, P, C.c_int64]),
@@ -259,6 +260,15 @@ class FRMesh:
                                       _ptr(ms), _ptr(n)))
         return {k: (float(ms[i]), int(n[i]))
                 for i, k in enumerate(self.KERNEL_CLASSES)}
+
+    def tuning(self):
+        """(active kernel family, {family: ms per tuned step})."""
+        a = C.c_int()
+        ms = np.zeros(4, np.float32)
+        _check(load().fr_get_tuning(self._h, C.byref(a), _ptr(ms)))
+        names = {v: k for k, v in VARIANTS.items()}
+        return names[a.value], {names[i]: float(ms[i]) for i in range(1, 4)
+                                if ms[i] > 0}
 
     def set_variant(self, name):
         """Kernel family for hexahedra: 'auto', 'dense' or 'sumfact'."""

@@ -2,6 +2,7 @@
 // sequences and CUDA-graph replay of Runge-Kutta steps.  See include/frgb.h.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -63,6 +64,24 @@ constexpr int epb() {
   return NU >= 128 ? 1 : 128 / NU;
 }
 
+// elements per CTA of the persistent dense kernels
+template <int NU>
+constexpr int dense_epb() {
+  return NU >= 256 ? 1 : 256 / NU;
+}
+
+template <typename T, int NU, int NF>
+constexpr size_t dense_grad_smem() {
+  return (size_t(DenseLayout<T, NU, NF>::kStagedCount) +
+          size_t(dense_epb<NU>()) * (20 * NU + 5 * NF)) * sizeof(T);
+}
+
+template <typename T, int NU, int NF>
+constexpr size_t dense_vol_smem() {
+  return (size_t(DenseLayout<T, NU, NF>::kStagedCount) +
+          size_t(dense_epb<NU>()) * (15 * NU + 5 * NF)) * sizeof(T);
+}
+
 struct DevType {
   int kind = 0, nu = 0, nf = 0;
   long long ne = 0;
@@ -89,6 +108,10 @@ struct DevType {
   double* smin = nullptr;
   float* zeta_last = nullptr;
   int* evals_last = nullptr;
+  int grad_ctas = 1, vol_ctas = 1;  // resident CTAs per SM (dense kernels)
+  void* fnv = nullptr;       // [ne][3][nf] S^T n~ at flux points (NS)
+  int8_t* fbc = nullptr;     // [ne][nf] boundary-condition index or -1 (NS)
+  void* verts = nullptr;     // [ne][8][3] vertices minus vertex 0 (hex, FP32)
 };
 
 void free_all(std::vector<void*>& v) {
@@ -102,6 +125,7 @@ void free_all(std::vector<void*>& v) {
 struct fr_mesh {
   int device = 0, precision = FR_FP64, physics = FR_EULER, order = 0;
   bool host_only = false;
+  int num_sms = 152;
   size_t wsize = 8;   // bytes of a trace / flux / stage value
   size_t rsize = 8;   // bytes of a solution-register value
   cudaStream_t stream = nullptr, own_stream = nullptr;
@@ -132,7 +156,10 @@ struct fr_mesh {
   bool uf_valid = false;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   cudaStream_t graph_stream[2] = {nullptr, nullptr};
-  int variant = FR_VARIANT_AUTO;
+  int variant = FR_VARIANT_AUTO;   // requested kernel family
+  int active = FR_VARIANT_SUMFACT; // family in use (the tuner's choice)
+  bool tuned = false;
+  float tune_ms[4] = {0, 0, 0, 0}; // ms per step of each family tried
   long long epoch = 0;            // bumped by every change of launch config
   long long graph_epoch[2] = {-1, -1};
   bool filter_on = false;
@@ -198,6 +225,7 @@ HexOps<T> hex_ops(const RefElement& R) {
     h.lp[a] = T(R.lp[a]);
     h.gl[a] = T(R.gl[a]);
     h.gr[a] = T(R.gr[a]);
+    h.xg[a] = T(R.x1[a]);
   }
   return h;
 }
@@ -250,6 +278,37 @@ int setup_device(fr_mesh* m) {
     if (D.kind == EK_HEX) {
       D.hx64 = hex_ops<double>(R);
       D.hx32 = hex_ops<float>(R);
+      if (sizeof(T) == 4) {  // vertex metrics for the FP32-value kernels
+        std::vector<double> xv(size_t(D.ne) * 24);
+        for (long long e = 0; e < D.ne; ++e)
+          for (int v = 0; v < 8; ++v)
+            for (int k = 0; k < 3; ++k)
+              xv[size_t(e) * 24 + v * 3 + k] = H.verts[(size_t(e) * 8 + v) * 3 + k] -
+                                               H.verts[size_t(e) * 24 + k];
+        if ((rc = dev_upload<T>(m, xv, &D.verts))) return rc;
+      }
+    }
+    if (m->physics == FR_NAVIER_STOKES) {
+      std::vector<double> nv(size_t(D.ne) * 3 * D.nf);
+      for (long long e = 0; e < D.ne; ++e)
+        for (int f = 0; f < D.nf; ++f)
+          for (int j = 0; j < 3; ++j)
+            nv[(size_t(e) * 3 + j) * D.nf + f] = H.fnvec[(size_t(e) * D.nf + f) * 3 + j];
+      if ((rc = dev_upload<T>(m, nv, &D.fnv))) return rc;
+      std::vector<int8_t> fbc(size_t(D.ne) * D.nf, -1);
+      for (size_t i = 0; i < m->conn.bidx.size(); ++i) {
+        int32_t code = m->conn.bidx[i];
+        if ((code >> 29) != int(t)) continue;
+        long long l = code & ((1 << 29) - 1);
+        long long e = l / (5 * D.nf);
+        int f = int(l - e * 5 * D.nf);
+        fbc[size_t(e) * D.nf + f] = int8_t(m->conn.bbc[i]);
+      }
+      void* p = nullptr;
+      CK(cudaMalloc(&p, fbc.size()));
+      m->allocs.push_back(p);
+      CK(cudaMemcpy(p, fbc.data(), fbc.size(), cudaMemcpyHostToDevice));
+      D.fbc = (int8_t*)p;
     }
     m->types.push_back(D);
   }
@@ -259,7 +318,9 @@ int setup_device(fr_mesh* m) {
   if ((rc = dev_zeros(m, fb, &m->fc))) return rc;
   if (m->physics == FR_NAVIER_STOKES) {
     if ((rc = dev_zeros(m, fb, &m->du))) return rc;
-    if ((rc = dev_zeros(m, 3 * fb, &m->gradf))) return rc;
+    // FP32 values: viscous normal flux q (5 per flux point); FP64: the 15
+    // gradient components at flux points
+    if ((rc = dev_zeros(m, (sizeof(T) == 4 ? 1 : 3) * fb, &m->gradf))) return rc;
   }
   const HostConn& C = m->conn;
   m->np = int(C.pl.size());
@@ -347,14 +408,45 @@ constexpr size_t hex_grad_smem() {
 }
 
 bool use_hex(const fr_mesh* m, const DevType& D) {
-  return D.kind == EK_HEX && m->variant != FR_VARIANT_DENSE;
+  return D.kind == EK_HEX && m->active != FR_VARIANT_DENSE;
+}
+
+// shared memory of the FP32-value hexahedron kernels (vertex metrics,
+// recomputed gradients)
+template <typename T, int N>
+constexpr size_t hexv_grad_smem() {
+  return size_t(hex_epb<N>()) * (20 * N * N * N + 30 * N * N + 24) * sizeof(T);
+}
+
+template <typename T, int N>
+constexpr size_t hexv_vol_smem() {
+  return size_t(hex_epb<N>()) * (20 * N * N * N + 60 * N * N + 24) * sizeof(T);
 }
 
 // Opt in to > 48 KB of dynamic shared memory where a kernel needs it.  Runs
 // once per handle outside any stream capture.
 template <typename T, typename TR>
 int prepare_kernels(fr_mesh* m) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, dev);
   for (auto& D : m->types) {
+    dispatch(D.kind, m->order, [&](auto nu, auto nf) {
+      constexpr int NU = decltype(nu)::value, NF = decltype(nf)::value;
+      constexpr int E = dense_epb<NU>();
+      auto kg = k_grad_dense<T, NU, NF, E, sizeof(T) == 4>;
+      auto kv0 = k_vol_dense<T, NU, NF, E, false>;
+      auto kv1 = k_vol_dense<T, NU, NF, E, true>;
+      const int sg = int(dense_grad_smem<T, NU, NF>()), sv = int(dense_vol_smem<T, NU, NF>());
+      cudaFuncSetAttribute(kg, cudaFuncAttributeMaxDynamicSharedMemorySize, sg);
+      cudaFuncSetAttribute(kv0, cudaFuncAttributeMaxDynamicSharedMemorySize, sv);
+      cudaFuncSetAttribute(kv1, cudaFuncAttributeMaxDynamicSharedMemorySize, sv);
+      int a = 0, b = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, kg, E * NU, sg);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kv1, E * NU, sv);
+      D.grad_ctas = a > 0 ? a : 1;
+      D.vol_ctas = b > 0 ? b : 1;
+    });
     if (D.kind != EK_HEX) continue;
     hex_dispatch(m->order, [&](auto n) {
       constexpr int N = decltype(n)::value;
@@ -365,9 +457,18 @@ int prepare_kernels(fr_mesh* m) {
       cudaFuncSetAttribute(k_hex_vol<T, TR, N, E, true>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                            int(hex_vol_smem<T, N>()));
-      cudaFuncSetAttribute(k_hex_grad<T, TR, N, E>,
+      cudaFuncSetAttribute(k_hex_grad<T, TR, N, E, sizeof(T) == 4>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                            int(hex_grad_smem<T, N>()));
+      cudaFuncSetAttribute(k_hex_grad_v<T, TR, N, E>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(hexv_grad_smem<T, N>()));
+      cudaFuncSetAttribute(k_hex_vol_v<T, TR, N, E, false>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(hexv_vol_smem<T, N>()));
+      cudaFuncSetAttribute(k_hex_vol_v<T, TR, N, E, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(hexv_vol_smem<T, N>()));
     });
   }
   CK(cudaGetLastError());
@@ -452,27 +553,40 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
     }
     for (auto& D : m->types) {
       const T* du = (const T*)m->du + D.off_f;
-      T* gradf = (T*)m->gradf + D.off_f * 3;
+      ViscArgs<T> va{(const T*)m->uf + D.off_f, (const T*)D.fnv, D.fbc,
+                     (T*)m->gradf + D.off_f * (sizeof(T) == 4 ? 1 : 3)};
       PROF_BEGIN(FR_KC_GRAD);
-      if (use_hex(m, D)) {
+      if (use_hex(m, D) && sizeof(T) == 4 &&
+          m->active == FR_VARIANT_SUMFACT_VERTEX) {
         hex_dispatch(m->order, [&](auto n) {
           constexpr int N = decltype(n)::value;
           constexpr int E = hex_epb<N>();
-          k_hex_grad<T, TR, N, E>
+          k_hex_grad_v<T, TR, N, E>
+              <<<nblk(D.ne, E), E * N * N * N, hexv_grad_smem<T, N>(), s>>>(
+                  D.ne, from_x ? nullptr : (const T*)D.Y, (const TR*)D.X, du,
+                  (const T*)D.verts, hexops<T>(D), va, bc, ph);
+        });
+      } else if (use_hex(m, D)) {
+        hex_dispatch(m->order, [&](auto n) {
+          constexpr int N = decltype(n)::value;
+          constexpr int E = hex_epb<N>();
+          k_hex_grad<T, TR, N, E, sizeof(T) == 4>
               <<<nblk(D.ne, E), E * N * N * N, hex_grad_smem<T, N>(), s>>>(
                   D.ne, from_x ? nullptr : (const T*)D.Y, (const TR*)D.X, du,
                   (const T*)D.smat, (const T*)D.rcpdjac, hexops<T>(D),
-                  (T*)D.grad, gradf);
+                  (T*)D.grad, va, bc, ph);
         });
       } else {
         dispatch(D.kind, m->order, [&](auto nu, auto nf) {
           constexpr int NU = decltype(nu)::value, NF = decltype(nf)::value;
-          constexpr int E = epb<NU>();
-          size_t sm = size_t(E) * (5 * NU + 5 * NF + 15 * NU) * sizeof(T);
-          k_grad_dense<T, NU, NF, E><<<nblk(D.ne, E), E * NU, sm, s>>>(
+          constexpr int E = dense_epb<NU>();
+          const size_t sm = dense_grad_smem<T, NU, NF>();
+          const unsigned grid = unsigned(std::min<long long>(
+              (D.ne + E - 1) / E, (long long)m->num_sms * D.grad_ctas));
+          k_grad_dense<T, NU, NF, E, sizeof(T) == 4><<<grid, E * NU, sm, s>>>(
               D.ne, from_x ? (const T*)D.X : (const T*)D.Y, du,
               (const T*)D.smat, (const T*)D.rcpdjac, ops_of<T>(D), (T*)D.grad,
-              gradf);
+              va, bc, ph);
         });
       }
       PROF_END(FR_KC_GRAD);
@@ -480,7 +594,11 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
   }
   if (m->np) {
     PROF_BEGIN(FR_KC_FACE_F);
-    if (ns)
+    if (ns && sizeof(T) == 4)
+      k_face_flux_ns<T><<<nblk(m->np, tb), tb, 0, s>>>(
+          m->np, m->pl, m->pr, (const T*)m->pn, (const T*)m->pmr,
+          (const T*)m->uf, (const T*)m->gradf, (T*)m->fc, m->tt, ph);
+    else if (ns)
       k_face_flux<T, true><<<nblk(m->np, tb), tb, 0, s>>>(
           m->np, m->pl, m->pr, (const T*)m->pn, (const T*)m->pmr,
           (const T*)m->uf, (const T*)m->gradf, (T*)m->fc, m->tt, ph);
@@ -492,7 +610,11 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
   }
   if (m->nb) {
     PROF_BEGIN(FR_KC_BND_F);
-    if (ns)
+    if (ns && sizeof(T) == 4)
+      k_bnd_flux_ns<T><<<nblk(m->nb, tb), tb, 0, s>>>(
+          m->nb, m->bidx, m->bbc, (const T*)m->bn, (const T*)m->uf,
+          (const T*)m->gradf, (T*)m->fc, m->tt, ph, bc);
+    else if (ns)
       k_bnd_flux<T, true><<<nblk(m->nb, tb), tb, 0, s>>>(
           m->nb, m->bidx, m->bbc, (const T*)m->bn, (const T*)m->uf,
           (const T*)m->gradf, (T*)m->fc, m->tt, ph, bc);
@@ -514,6 +636,17 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
         constexpr int E = hex_epb<N>();
         const size_t sm = hex_vol_smem<T, N>();
         const T* uin = from_x ? nullptr : (const T*)D.Y;
+        if (sizeof(T) == 4 && m->active == FR_VARIANT_SUMFACT_VERTEX) {
+          const size_t smv = hexv_vol_smem<T, N>();
+          const T* dup = (const T*)m->du + D.off_f;
+          if (ns)
+            k_hex_vol_v<T, TR, N, E, true><<<nblk(D.ne, E), E * N * N * N, smv, s>>>(
+                D.ne, uin, dup, fc, (const T*)D.verts, hexops<T>(D), ph, sa);
+          else
+            k_hex_vol_v<T, TR, N, E, false><<<nblk(D.ne, E), E * N * N * N, smv, s>>>(
+                D.ne, uin, nullptr, fc, (const T*)D.verts, hexops<T>(D), ph, sa);
+          return;
+        }
         if (ns)
           k_hex_vol<T, TR, N, E, true><<<nblk(D.ne, E), E * N * N * N, sm, s>>>(
               D.ne, uin, (const T*)D.grad, fc, (const T*)D.smat,
@@ -537,14 +670,16 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
       const T* uin = from_x ? (const T*)D.X : (const T*)D.Y;
       dispatch(D.kind, m->order, [&](auto nu, auto nf) {
         constexpr int NU = decltype(nu)::value, NF = decltype(nf)::value;
-        constexpr int E = epb<NU>();
-        size_t sm = size_t(E) * (15 * NU + 5 * NF) * sizeof(T);
+        constexpr int E = dense_epb<NU>();
+        const size_t sm = dense_vol_smem<T, NU, NF>();
+        const unsigned grid = unsigned(std::min<long long>(
+            (D.ne + E - 1) / E, (long long)m->num_sms * D.vol_ctas));
         if (ns)
-          k_vol_dense<T, NU, NF, E, true><<<nblk(D.ne, E), E * NU, sm, s>>>(
+          k_vol_dense<T, NU, NF, E, true><<<grid, E * NU, sm, s>>>(
               D.ne, uin, (const T*)D.grad, fc, (const T*)D.smat,
               (const T*)D.rcpdjac, ops_of<T>(D), ph, sa);
         else
-          k_vol_dense<T, NU, NF, E, false><<<nblk(D.ne, E), E * NU, sm, s>>>(
+          k_vol_dense<T, NU, NF, E, false><<<grid, E * NU, sm, s>>>(
               D.ne, uin, nullptr, fc, (const T*)D.smat, (const T*)D.rcpdjac,
               ops_of<T>(D), ph, sa);
       });
@@ -620,7 +755,14 @@ int ensure_uf(fr_mesh* m) {
 }
 
 template <typename T, typename TR>
+int resolve_variant(fr_mesh* m, int scheme, double dt);
+
+template <typename T, typename TR>
 int do_rhs(fr_mesh* m) {
+  if (m->variant != FR_VARIANT_AUTO) {  // a fixed family; no tuning here
+    int rv = resolve_variant<T, TR>(m, FR_RK4, 0.0);
+    if (rv) return rv;
+  }
   int rc = ensure_uf<T, TR>(m);
   if (rc) return rc;
   CK(cudaMemsetAsync(m->d_flag, 0, sizeof(int), m->stream));
@@ -655,9 +797,103 @@ int build_graph(fr_mesh* m, int scheme) {
   return FR_OK;
 }
 
+// Kernel family for hexahedra: the requested one, or the autotuner's pick.
+// The tuner runs one warm-up and one timed step of every applicable family
+// from a saved copy of the solution registers, keeps the fastest and
+// restores the registers (and the filter counters), so the caller's state is
+// unchanged.
+template <typename T, typename TR>
+int resolve_variant(fr_mesh* m, int scheme, double dt) {
+  bool has_hex = false;
+  for (auto& D : m->types) has_hex |= D.kind == EK_HEX;
+  if (m->variant != FR_VARIANT_AUTO) {
+    int v = m->variant;
+    if (v == FR_VARIANT_SUMFACT_VERTEX && sizeof(T) != 4) v = FR_VARIANT_SUMFACT;
+    if (v != m->active) {
+      m->active = v;
+      m->uf_valid = false;
+      ++m->epoch;
+    }
+    return FR_OK;
+  }
+  if (m->tuned || !has_hex) return FR_OK;
+  std::vector<int> cand = {FR_VARIANT_SUMFACT};
+  if (sizeof(T) == 4) cand.push_back(FR_VARIANT_SUMFACT_VERTEX);
+  if (m->precision != FR_MIXED) cand.push_back(FR_VARIANT_DENSE);
+  std::vector<void*> saved;
+  auto release = [&]() {
+    for (void* p : saved)
+      if (p) cudaFree(p);
+  };
+  for (auto& D : m->types) {
+    void* p = nullptr;
+    size_t bytes = size_t(D.ne) * 5 * D.nu * sizeof(TR);
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      release();
+      return fail(FR_ENOMEM, "autotuner: no room for a state copy");
+    }
+    saved.push_back(p);
+    cudaMemcpyAsync(p, D.X, bytes, cudaMemcpyDeviceToDevice, m->stream);
+  }
+  FilterStats st0{};
+  if (m->d_fstats)
+    cudaMemcpyAsync(&st0, m->d_fstats, sizeof(st0), cudaMemcpyDeviceToHost, m->stream);
+  m->h_dt = dt;
+  cudaMemcpyAsync(m->d_dt, &m->h_dt, sizeof(double), cudaMemcpyHostToDevice, m->stream);
+  const int nst = scheme == FR_RK4 ? 4 : 5, mode = scheme == FR_RK4 ? 1 : 2;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int pick = FR_VARIANT_SUMFACT;
+  for (int c : cand) {
+    m->active = c;
+    for (int rep = 0; rep < 2; ++rep) {
+      for (size_t t = 0; t < m->types.size(); ++t)
+        cudaMemcpyAsync(m->types[t].X, saved[t],
+                        size_t(m->types[t].ne) * 5 * m->types[t].nu * sizeof(TR),
+                        cudaMemcpyDeviceToDevice, m->stream);
+      m->uf_valid = false;
+      ensure_uf<T, TR>(m);
+      if (rep == 1) cudaEventRecord(e0, m->stream);
+      for (int s2 = 0; s2 < nst; ++s2) launch_stage<T, TR>(m, m->stream, mode, s2);
+      if (rep == 1) cudaEventRecord(e1, m->stream);
+    }
+    cudaError_t err = cudaStreamSynchronize(m->stream);
+    if (err != cudaSuccess) {
+      release();
+      return fail(FR_ECUDA, std::string("autotuner: ") + cudaGetErrorString(err));
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    m->tune_ms[c] = ms;
+    if (ms < best) {
+      best = ms;
+      pick = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (size_t t = 0; t < m->types.size(); ++t)
+    cudaMemcpyAsync(m->types[t].X, saved[t],
+                    size_t(m->types[t].ne) * 5 * m->types[t].nu * sizeof(TR),
+                    cudaMemcpyDeviceToDevice, m->stream);
+  if (m->d_fstats)
+    cudaMemcpyAsync(m->d_fstats, &st0, sizeof(st0), cudaMemcpyHostToDevice, m->stream);
+  CK(cudaStreamSynchronize(m->stream));
+  release();
+  m->active = pick;
+  m->tuned = true;
+  m->uf_valid = false;
+  ++m->epoch;
+  return FR_OK;
+}
+
 template <typename T, typename TR>
 int do_rk(fr_mesh* m, int scheme, double dt, int nsteps) {
-  int rc = ensure_uf<T, TR>(m);
+  int rc = resolve_variant<T, TR>(m, scheme, dt);
+  if (rc) return rc;
+  rc = ensure_uf<T, TR>(m);
   if (rc) return rc;
   if (!m->graph[scheme] || m->graph_stream[scheme] != m->stream ||
       m->graph_epoch[scheme] != m->epoch) {
@@ -678,7 +914,9 @@ int do_rk(fr_mesh* m, int scheme, double dt, int nsteps) {
 
 template <typename T, typename TR>
 int do_profile(fr_mesh* m, int scheme, double dt, double* ms, int* launches) {
-  int rc = ensure_uf<T, TR>(m);
+  int rc = resolve_variant<T, TR>(m, scheme, dt);
+  if (rc) return rc;
+  rc = ensure_uf<T, TR>(m);
   if (rc) return rc;
   m->h_dt = dt;
   CK(cudaMemcpyAsync(m->d_dt, &m->h_dt, sizeof(double), cudaMemcpyHostToDevice,
@@ -1018,12 +1256,21 @@ int fr_profile_step(fr_mesh* m, int scheme, double dt, double* ms,
 int fr_set_kernel_variant(fr_mesh* m, int variant) {
   if (!m) return fail(FR_EINVAL, "null mesh");
   if (variant != FR_VARIANT_AUTO && variant != FR_VARIANT_DENSE &&
-      variant != FR_VARIANT_SUMFACT)
+      variant != FR_VARIANT_SUMFACT && variant != FR_VARIANT_SUMFACT_VERTEX)
     return fail(FR_EINVAL, "unknown kernel variant");
   if (variant == FR_VARIANT_DENSE && m->precision == FR_MIXED)
     return fail(FR_EINVAL, "FR_MIXED runs the sum-factorised kernels only");
   m->variant = variant;
+  m->tuned = false;
   ++m->epoch;
+  return FR_OK;
+}
+
+int fr_get_tuning(const fr_mesh* m, int* active, float* ms) {
+  if (!m) return fail(FR_EINVAL, "null mesh");
+  if (active) *active = m->active;
+  if (ms)
+    for (int i = 0; i < 4; ++i) ms[i] = m->tune_ms[i];
   return FR_OK;
 }
 

@@ -97,40 +97,71 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// s_min per element from the stage input: one warp per element.
+// s_min per element from the stage input: one warp per element.  Every
+// point gets an FP32 estimate of s; the exact FP64 value is computed for the
+// points whose estimate is within 1e-4 (relative) of the warp's smallest.
 template <typename T, typename TR, int NU, int NF>
 __global__ void k_entropy_min(long long ne, const T* __restrict__ uin,
                               const TR* __restrict__ X,
                               const T* __restrict__ uf_all, TypeTab tt,
                               int tidx, const int32_t* __restrict__ partner,
                               double gamma, double* __restrict__ smin) {
+  constexpr int NQ = (NU + 2 * NF + 31) / 32;
   const int lane = threadIdx.x & 31;
   const long long e = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (e >= ne) return;
-  double m = INFINITY, p;
-  for (int z = lane; z < NU; z += 32) {
-    double v[5];
-#pragma unroll
-    for (int k = 0; k < 5; ++k)
-      v[k] = uin ? double(uin[(e * 5 + k) * NU + z]) : double(X[(e * 5 + k) * NU + z]);
-    m = fmin(m, entropy_of(v[0], v[1], v[2], v[3], v[4], gamma, &p));
-  }
   const T* uf = uf_all + tt.off_f[tidx];
-  for (int f = lane; f < NF; f += 32) {
+  float est[NQ];
+  double rr[NQ], pp[NQ];
+  float emin = INFINITY;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int i = lane + 32 * q;
+    est[q] = INFINITY;
+    rr[q] = 1.0;
+    pp[q] = -1.0;
     double v[5];
+    bool have = true;
+    if (i < NU) {
 #pragma unroll
-    for (int k = 0; k < 5; ++k) v[k] = double(uf[(e * 5 + k) * NF + f]);
-    m = fmin(m, entropy_of(v[0], v[1], v[2], v[3], v[4], gamma, &p));
-    int32_t c = partner[e * NF + f];
-    if (c >= 0) {
-      int t2, f2;
-      long long e2;
-      decode_fp(c, tt, &t2, &e2, &f2);
+      for (int k = 0; k < 5; ++k)
+        v[k] = uin ? double(uin[(e * 5 + k) * NU + i]) : double(X[(e * 5 + k) * NU + i]);
+    } else if (i < NU + NF) {
+      const int f = i - NU;
 #pragma unroll
-      for (int k = 0; k < 5; ++k) v[k] = double(uf_all[fp_index(tt, t2, e2, f2, 5, k)]);
-      m = fmin(m, entropy_of(v[0], v[1], v[2], v[3], v[4], gamma, &p));
+      for (int k = 0; k < 5; ++k) v[k] = double(uf[(e * 5 + k) * NF + f]);
+    } else if (i < NU + 2 * NF) {
+      const int f = i - NU - NF;
+      int32_t c = partner[e * NF + f];
+      if (c >= 0) {
+        int t2, f2;
+        long long e2;
+        decode_fp(c, tt, &t2, &e2, &f2);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) v[k] = double(uf_all[fp_index(tt, t2, e2, f2, 5, k)]);
+      } else {
+        have = false;
+      }
+    } else {
+      have = false;
+    }
+    if (!have) continue;
+    double p = (gamma - 1.0) * (v[4] - 0.5 * (v[1] * v[1] + v[2] * v[2] + v[3] * v[3]) / v[0]);
+    rr[q] = v[0];
+    pp[q] = p;
+    if (v[0] > 0.0 && p > 0.0) {
+      est[q] = float(p) * __powf(float(v[0]), -float(gamma));
+      emin = fminf(emin, est[q]);
     }
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) emin = fminf(emin, __shfl_xor_sync(0xffffffffu, emin, o));
+  double m = INFINITY;
+  const float cut = emin * (1.0f + 1e-4f);
+#pragma unroll
+  for (int q = 0; q < NQ; ++q)
+    if (est[q] <= cut && rr[q] > 0.0 && pp[q] > 0.0)
+      m = fmin(m, pp[q] * pow(rr[q], -gamma));
   m = warp_min(m);
   if (lane == 0) smin[e] = isfinite(m) ? m : 0.0;
 }
@@ -231,13 +262,28 @@ __global__ void __launch_bounds__(kFilterThreads)
   const double rmean = fmax(block_sum(wr, red) / wsum, kEpsPos);
   const double pmean = fmax(block_sum(wp, red) / wsum, kEpsPos);
   const double smin = fa.smin[e];
-  // margin of the filtered polynomial at strength z (all threads)
+  // margin of the filtered polynomial at strength z (all threads).  The
+  // entropy margin needs s = p rho^-gamma: every point gets a fast FP32
+  // estimate, and the exact FP64 value is computed only for points whose
+  // estimate lies within 1e-4 of the element's smallest estimate (the FP32
+  // estimate is accurate to ~1e-6), so the FP64 minimum is exact.
+  constexpr int NPT = (NP + kFilterThreads - 1) / kFilterThreads;
+  const double sb = smin * (1.0 - fa.tau);
   auto margin = [&](double z, float* feat) -> double {
-    for (int m = tid; m < NM; m += kFilterThreads)
-      sg[m] = T(exp(-z * double(op.deg[m]) * double(op.deg[m])));
+    for (int m = tid; m < NM; m += kFilterThreads) {
+      double d = double(op.deg[m]);
+      sg[m] = sizeof(T) == 4 ? T(__expf(-float(z * d * d))) : T(exp(-z * d * d));
+    }
     __syncthreads();
-    double mr = INFINITY, mp = INFINITY, ms = INFINITY;
-    for (int i = tid; i < NP; i += kFilterThreads) {
+    double mr = INFINITY, mp = INFINITY, mse = INFINITY;
+    double rr[NPT], pp[NPT], se[NPT];
+#pragma unroll
+    for (int q = 0; q < NPT; ++q) {
+      const int i = tid + q * kFilterThreads;
+      rr[q] = 1.0;
+      pp[q] = 1.0;
+      se[q] = INFINITY;
+      if (i >= NP) continue;
       T v[5] = {0, 0, 0, 0, 0};
       for (int m = 0; m < NM; ++m) {
         T w = op.VT[m * NP + i] * sg[m];
@@ -247,17 +293,32 @@ __global__ void __launch_bounds__(kFilterThreads)
       double p;
       entropy_of(double(v[0]), double(v[1]), double(v[2]), double(v[3]),
                  double(v[4]), g, &p);
-      double r = double(v[0]);
+      const double r = double(v[0]);
+      rr[q] = r;
+      pp[q] = p;
       mr = fmin(mr, r);
       mp = fmin(mp, p);
-      // s = p rho^-gamma (negative where p < 0), -inf where rho <= 0
-      ms = fmin(ms, r > 0.0 ? p * pow(r, -g) : -INFINITY);
+      // s estimate (negative where p < 0), -inf where rho <= 0
+      se[q] = r > 0.0 ? double(float(p) * __powf(float(r), -float(g))) : -INFINITY;
+      mse = fmin(mse, se[q]);
     }
     mr = block_min(mr, red);
     mp = block_min(mp, red);
-    ms = block_min(ms, red);
+    mse = block_min(mse, red);
+    double ms = INFINITY;
+    if (smin > 0.0) {
+      const double cut = mse + 1e-4 * smin;
+#pragma unroll
+      for (int q = 0; q < NPT; ++q) {
+        if (se[q] > cut) continue;
+        ms = fmin(ms, rr[q] > 0.0 ? pp[q] * pow(rr[q], -g) : -INFINITY);
+      }
+      ms = block_min(ms, red);
+    } else {
+      ms = block_min(ms, red);
+    }
     double gr = (mr - kEpsPos) / rmean, gp = (mp - kEpsPos) / pmean;
-    double gs = smin > 0.0 ? (ms - smin + fa.tau * smin) / smin : INFINITY;
+    double gs = smin > 0.0 ? (ms - sb) / smin : INFINITY;
     double gm = fmin(gr, fmin(gp, gs));
     if (isnan(gm)) gm = -INFINITY;
     if (feat) {  // predictor inputs from the unfiltered state (z = 0)

@@ -24,6 +24,7 @@ struct HexOps {
   T d1[8][8];  // d1[a][m] = l_m'(x_a)
   T lm[8], lp[8];  // l_m(-1), l_m(+1)
   T gl[8], gr[8];  // correction weights of the minus / plus face
+  T xg[8];         // the Gauss-Legendre points themselves
 };
 
 // register type used for the RK solution / accumulator registers
@@ -137,12 +138,15 @@ __device__ __forceinline__ void face_interp(const T* src, int fp,
 // ---------------------------------------------------------------------------
 // NS gradients on hexahedra: corrected reference gradient, physical gradient
 // at solution points, and its value at the flux points.
-template <typename T, typename TR, int N, int EPB>
+// QV: write the viscous normal flux q (5 per flux point, for the q-based
+// interface kernel) instead of the 15 gradient components at flux points.
+template <typename T, typename TR, int N, int EPB, bool QV>
 __global__ void __launch_bounds__(EPB* N* N* N)
     k_hex_grad(long long ne, const T* __restrict__ uin, const TR* __restrict__ X,
                const T* __restrict__ du, const T* __restrict__ smat,
                const T* __restrict__ rcpdjac, HexOps<T> op,
-               T* __restrict__ grad, T* __restrict__ gradf) {
+               T* __restrict__ grad, ViscArgs<T> va, BCTab<T> bc,
+               Phys<T> ph) {
   constexpr int NU = N * N * N, NF = 6 * N * N;
   extern __shared__ unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
@@ -212,8 +216,12 @@ __global__ void __launch_bounds__(EPB* N* N* N)
   for (int f = z; f < NF; f += NU) {
     T g[15];
     face_interp<T, N, 15>(gs, f, op, g);
+    if (QV) {
+      write_visc_q(va, bc, ph, e, f, NF, g);
+    } else {
 #pragma unroll
-    for (int k = 0; k < 15; ++k) gradf[(e * 15 + k) * NF + f] = g[k];
+      for (int k = 0; k < 15; ++k) va.q[(e * 15 + k) * NF + f] = g[k];
+    }
   }
 }
 
@@ -343,6 +351,293 @@ __global__ void __launch_bounds__(EPB* N* N* N)
     face_interp<T, N, 5>(us[le], f, op, v);
 #pragma unroll
     for (int k = 0; k < 5; ++k) uf[(e * 5 + k) * NF + f] = v[k];
+  }
+}
+
+}  // namespace frgb
+
+namespace frgb {
+
+// ---------------------------------------------------------------------------
+// Variants for FP32 values (FP32 and mixed precision), where the path is
+// bound by DRAM traffic rather than arithmetic: the metric terms of linear
+// hexahedra are computed on the fly from the 8 vertices (24 numbers per
+// element instead of 10 per solution point, Section 3.4 of the paper), and
+// the volume kernel recomputes the corrected gradient from u and the
+// flux-point jumps instead of reading 15 stored components per point.
+
+// S = det(J) J^{-1} (rows a_j x a_k) and det J of the trilinear map at
+// reference point x, vertices relative to vertex 0 (X[v][k]).
+template <typename T>
+__device__ __forceinline__ void hex_metric_at(const T* X, T x0, T x1, T x2,
+                                              T S[3][3], T* det) {
+  const int sg[8][3] = {{-1, -1, -1}, {1, -1, -1}, {1, 1, -1}, {-1, 1, -1},
+                        {-1, -1, 1},  {1, -1, 1},  {1, 1, 1},  {-1, 1, 1}};
+  T a[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+  for (int v = 1; v < 8; ++v) {
+    const T f0 = T(1) + T(sg[v][0]) * x0, f1 = T(1) + T(sg[v][1]) * x1,
+            f2 = T(1) + T(sg[v][2]) * x2;
+    const T d0 = T(0.125) * T(sg[v][0]) * f1 * f2;
+    const T d1 = T(0.125) * T(sg[v][1]) * f0 * f2;
+    const T d2 = T(0.125) * T(sg[v][2]) * f0 * f1;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const T xv = X[v * 3 + k];
+      a[0][k] += d0 * xv;
+      a[1][k] += d1 * xv;
+      a[2][k] += d2 * xv;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const T* b = a[(i + 1) % 3];
+    const T* c = a[(i + 2) % 3];
+    S[i][0] = b[1] * c[2] - b[2] * c[1];
+    S[i][1] = b[2] * c[0] - b[0] * c[2];
+    S[i][2] = b[0] * c[1] - b[1] * c[0];
+  }
+  *det = a[0][0] * S[0][0] + a[0][1] * S[0][1] + a[0][2] * S[0][2];
+}
+
+// reference coordinates of solution point (a,b,c) / flux point f
+template <typename T, int N>
+__device__ __forceinline__ void hex_fpt_ref(const HexOps<T>& op, const T* x1,
+                                            int f, T x[3], T n[3]) {
+  (void)op;
+  const int face = f / (N * N), r = f - face * N * N;
+  const int i = r % N, j = r / N, dir = face >> 1;
+  const T side = (face & 1) ? T(1) : T(-1);
+  const T s = x1[i], t = x1[j];
+  if (dir == 0) { x[0] = side; x[1] = s; x[2] = t; }
+  else if (dir == 1) { x[0] = s; x[1] = side; x[2] = t; }
+  else { x[0] = s; x[1] = t; x[2] = side; }
+  n[0] = n[1] = n[2] = T(0);
+  n[dir] = side;
+}
+
+// corrected reference gradient at (a, b, c) from u (smem [5][NU]) and the
+// flux-point jumps du (smem [5][NF])
+template <typename T, int N>
+__device__ __forceinline__ void hex_ref_grad(const T* us, const T* ds,
+                                             const HexOps<T>& op, int a, int b,
+                                             int c, T gref[3][5]) {
+  constexpr int NU = N * N * N, NF = 6 * N * N, N2 = N * N;
+  T da[N], db[N], dc[N];
+#pragma unroll
+  for (int m = 0; m < N; ++m) {
+    da[m] = op.d1[a][m];
+    db[m] = op.d1[b][m];
+    dc[m] = op.d1[c][m];
+  }
+  const T gla = op.gl[a], gra = op.gr[a], glb = op.gl[b], grb = op.gr[b],
+          glc = op.gl[c], grc = op.gr[c];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    T gx = T(0), gy = T(0), gz = T(0);
+#pragma unroll
+    for (int m = 0; m < N; ++m) {
+      gx += da[m] * us[k * NU + m + N * b + N2 * c];
+      gy += db[m] * us[k * NU + a + N * m + N2 * c];
+      gz += dc[m] * us[k * NU + a + N * b + N2 * m];
+    }
+    gx += -gla * ds[k * NF + fp_of<N>(0, b, c)] + gra * ds[k * NF + fp_of<N>(1, b, c)];
+    gy += -glb * ds[k * NF + fp_of<N>(2, a, c)] + grb * ds[k * NF + fp_of<N>(3, a, c)];
+    gz += -glc * ds[k * NF + fp_of<N>(4, a, b)] + grc * ds[k * NF + fp_of<N>(5, a, b)];
+    gref[0][k] = gx;
+    gref[1][k] = gy;
+    gref[2][k] = gz;
+  }
+}
+
+// NS gradients (FP32 values): vertex metrics, viscous flux at the flux
+// points; nothing is stored at the solution points.
+template <typename T, typename TR, int N, int EPB>
+__global__ void __launch_bounds__(EPB* N* N* N)
+    k_hex_grad_v(long long ne, const T* __restrict__ uin, const TR* __restrict__ X,
+                 const T* __restrict__ du, const T* __restrict__ verts,
+                 HexOps<T> op, ViscArgs<T> va, BCTab<T> bc, Phys<T> ph) {
+  constexpr int NU = N * N * N, NF = 6 * N * N;
+  extern __shared__ unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int le = threadIdx.x / NU, z = threadIdx.x - le * NU;
+  const long long e = (long long)blockIdx.x * EPB + le;
+  T* us = sm + le * (5 * NU + 5 * NF + 15 * NU + 24);
+  T* ds = us + 5 * NU;
+  T* gs = ds + 5 * NF;
+  T* xv = gs + 15 * NU;
+  const int a = z % N, b = (z / N) % N, c = z / (N * N);
+  if (e < ne) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+      us[k * NU + z] = uin ? uin[(e * 5 + k) * NU + z] : T(X[(e * 5 + k) * NU + z]);
+    for (int f = z; f < NF; f += NU)
+#pragma unroll
+      for (int k = 0; k < 5; ++k) ds[k * NF + f] = du[(e * 5 + k) * NF + f];
+    if (z < 24) xv[z] = verts[e * 24 + z];
+  }
+  __syncthreads();
+  if (e < ne) {
+    T gref[3][5];
+    hex_ref_grad<T, N>(us, ds, op, a, b, c, gref);
+    T S[3][3], det;
+    hex_metric_at(xv, op.xg[a], op.xg[b], op.xg[c], S, &det);
+    const T rj = T(1) / det;
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int k = 0; k < 5; ++k)
+        gs[(j * 5 + k) * NU + z] =
+            rj * (S[0][j] * gref[0][k] + S[1][j] * gref[1][k] + S[2][j] * gref[2][k]);
+  }
+  __syncthreads();
+  if (e >= ne) return;
+  for (int f = z; f < NF; f += NU) {
+    T g[15];
+    face_interp<T, N, 15>(gs, f, op, g);
+    // S^T n~ at the flux point from the vertex map
+    T xr[3], nr[3], S[3][3], det;
+    hex_fpt_ref<T, N>(op, op.xg, f, xr, nr);
+    hex_metric_at(xv, xr[0], xr[1], xr[2], S, &det);
+    T nv[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) nv[j] = S[0][j] * nr[0] + S[1][j] * nr[1] + S[2][j] * nr[2];
+    T u[5], G[3][5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) u[k] = va.uf[(e * 5 + k) * NF + f];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int k = 0; k < 5; ++k) G[j][k] = g[j * 5 + k];
+    T q[5] = {0, 0, 0, 0, 0};
+    viscous_normal_acc(u, G, nv, ph, T(1), q);
+    const int bb = va.fbc[e * NF + f];
+    if (bb >= 0) {
+      T ur[5], q2[5] = {0, 0, 0, 0, 0};
+      ghost_state(bc, bb, u, ur);
+      viscous_normal_acc(ur, G, nv, ph, T(1), q2);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) q[k] = T(0.5) * (q[k] + q2[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 5; ++k) va.q[(e * 5 + k) * NF + f] = q[k];
+  }
+}
+
+// Volume kernel (FP32 values): vertex metrics; for NS the corrected
+// gradient is recomputed from u and du.
+template <typename T, typename TR, int N, int EPB, bool NS>
+__global__ void __launch_bounds__(EPB* N* N* N)
+    k_hex_vol_v(long long ne, const T* __restrict__ uin, const T* __restrict__ du,
+                const T* __restrict__ fc, const T* __restrict__ verts,
+                HexOps<T> op, Phys<T> ph, HexStage<T, TR> sa) {
+  constexpr int NU = N * N * N, NF = 6 * N * N, N2 = N * N;
+  extern __shared__ unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int le = threadIdx.x / NU, z = threadIdx.x - le * NU;
+  const long long e = (long long)blockIdx.x * EPB + le;
+  T* ft = sm + le * (15 * NU + 5 * NF + 5 * NU + 5 * NF + 24);
+  T* jm = ft + 15 * NU;
+  T* us = jm + 5 * NF;
+  T* ds = us + 5 * NU;
+  T* xv = ds + 5 * NF;
+  const int a = z % N, b = (z / N) % N, c = z / N2;
+  T uz[5];
+  if (e < ne) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      uz[k] = uin ? uin[(e * 5 + k) * NU + z] : T(sa.X[(e * 5 + k) * NU + z]);
+      us[k * NU + z] = uz[k];
+    }
+    if (NS)
+      for (int f = z; f < NF; f += NU)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) ds[k * NF + f] = du[(e * 5 + k) * NF + f];
+    if (z < 24) xv[z] = verts[e * 24 + z];
+  }
+  __syncthreads();
+  T rj = T(0);
+  if (e < ne) {
+    T S[3][3], det;
+    hex_metric_at(xv, op.xg[a], op.xg[b], op.xg[c], S, &det);
+    rj = T(1) / det;
+    T F[3][5];
+    euler_flux(uz, ph, F);
+    if (NS) {
+      T gref[3][5], g[3][5];
+      hex_ref_grad<T, N>(us, ds, op, a, b, c, gref);
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+          g[j][k] = rj * (S[0][j] * gref[0][k] + S[1][j] * gref[1][k] +
+                          S[2][j] * gref[2][k]);
+      viscous_flux_acc(uz, g, ph, T(-1), F);
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int k = 0; k < 5; ++k)
+        ft[(d * 5 + k) * NU + z] = S[d][0] * F[0][k] + S[d][1] * F[1][k] + S[d][2] * F[2][k];
+  }
+  __syncthreads();
+  if (e < ne) {
+    for (int f = z; f < NF; f += NU) {
+      int face = f / N2;
+      int dir = face >> 1;
+      T fn[5];
+      face_interp<T, N, 5>(ft + dir * 5 * NU, f, op, fn);
+      T sgn = (face & 1) ? T(1) : T(-1);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) jm[k * NF + f] = fc[(e * 5 + k) * NF + f] - sgn * fn[k];
+    }
+  }
+  __syncthreads();
+  T s[5];
+  if (e < ne) {
+    T R[5];
+    T da[N], db[N], dc[N];
+#pragma unroll
+    for (int m = 0; m < N; ++m) {
+      da[m] = op.d1[a][m];
+      db[m] = op.d1[b][m];
+      dc[m] = op.d1[c][m];
+    }
+    const T gla = op.gl[a], gra = op.gr[a], glb = op.gl[b], grb = op.gr[b],
+            glc = op.gl[c], grc = op.gr[c];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const T* fx = ft + (0 * 5 + k) * NU;
+      const T* fy = ft + (1 * 5 + k) * NU;
+      const T* fz = ft + (2 * 5 + k) * NU;
+      T dv = T(0);
+#pragma unroll
+      for (int m = 0; m < N; ++m) {
+        dv += da[m] * fx[m + N * b + N2 * c];
+        dv += db[m] * fy[a + N * m + N2 * c];
+        dv += dc[m] * fz[a + N * b + N2 * m];
+      }
+      const T* jk = jm + k * NF;
+      dv += gla * jk[fp_of<N>(0, b, c)] + gra * jk[fp_of<N>(1, b, c)];
+      dv += glb * jk[fp_of<N>(2, a, c)] + grb * jk[fp_of<N>(3, a, c)];
+      dv += glc * jk[fp_of<N>(4, a, b)] + grc * jk[fp_of<N>(5, a, b)];
+      R[k] = -dv * rj;
+    }
+    hex_stage_update(sa, e * 5 * NU + z, NU, uz, R, s);
+  }
+  if (sa.uf_next == nullptr) return;
+  __syncthreads();
+  if (e < ne) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) ft[k * NU + z] = s[k];
+  }
+  __syncthreads();
+  if (e >= ne) return;
+  for (int f = z; f < NF; f += NU) {
+    T v[5];
+    face_interp<T, N, 5>(ft, f, op, v);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) sa.uf_next[(e * 5 + k) * NF + f] = v[k];
   }
 }
 

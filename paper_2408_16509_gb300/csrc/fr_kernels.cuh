@@ -296,82 +296,240 @@ __global__ void k_bnd_ucommon(int nb, const int32_t* __restrict__ bidx,
 }
 
 // ---------------------------------------------------------------------------
+// Viscous coupling at flux points.  Each element evaluates, at its own flux
+// points, the transformed normal viscous flux q = F_v(u_f, grad u_f) .
+// (S^T n~) with its own metric (S^T n~ = |S^T n~| n, Nanson); at boundary
+// points q is the average over the inside state and the boundary's outside
+// state, which shares the inside gradient.  The interface kernel then forms
+// the BR1 average from q of both sides, so the 15 gradient components never
+// leave the element.
+template <typename T>
+struct ViscArgs {
+  const T* uf;          // this type's [ne][5][nf] solution traces
+  const T* fnv;         // this type's [ne][3][nf] S^T n~ at flux points
+  const int8_t* fbc;    // this type's [ne][nf]: -1 interior, else bc index
+  T* q;                 // this type's [ne][5][nf] output
+};
+
+template <typename T>
+__device__ __forceinline__ void write_visc_q(const ViscArgs<T>& va,
+                                             const BCTab<T>& bc,
+                                             const Phys<T>& ph, long long e,
+                                             int f, int nf, const T g[15]) {
+  T u[5], G[3][5], nv[3];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) u[k] = va.uf[(e * 5 + k) * nf + f];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    nv[j] = va.fnv[(e * 3 + j) * nf + f];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) G[j][k] = g[j * 5 + k];
+  }
+  T q[5] = {0, 0, 0, 0, 0};
+  viscous_normal_acc(u, G, nv, ph, T(1), q);
+  const int b = va.fbc[e * nf + f];
+  if (b >= 0) {
+    T ur[5], q2[5] = {0, 0, 0, 0, 0};
+    if (bc.kind[b] == 0) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) ur[k] = bc.state[b][k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) ur[k] = u[k];
+    }
+    viscous_normal_acc(ur, G, nv, ph, T(1), q2);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) q[k] = T(0.5) * (q[k] + q2[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < 5; ++k) va.q[(e * 5 + k) * nf + f] = q[k];
+}
+
+// Common flux on interior pairs from the sides' viscous fluxes q:
+// F^C_L = |S^T n~|_L Rus - (q_L - (m_L/m_R) q_R)/2,
+// F^C_R = -|S^T n~|_R Rus + ((m_R/m_L) q_L - q_R)/2.
+template <typename T>
+__global__ void k_face_flux_ns(int np, const int32_t* __restrict__ pl,
+                               const int32_t* __restrict__ pr,
+                               const T* __restrict__ pn,
+                               const T* __restrict__ pmr,
+                               const T* __restrict__ uf,
+                               const T* __restrict__ q, T* __restrict__ fc,
+                               TypeTab tt, Phys<T> ph) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  int tl, tr, fl, frr;
+  long long el, er;
+  decode_fp(pl[i], tt, &tl, &el, &fl);
+  decode_fp(pr[i], tt, &tr, &er, &frr);
+  T ul[5], ur[5], ql[5], qr[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    long long il = fp_index(tt, tl, el, fl, 5, k);
+    long long ir = fp_index(tt, tr, er, frr, 5, k);
+    ul[k] = uf[il];
+    ur[k] = uf[ir];
+    ql[k] = q[il];
+    qr[k] = q[ir];
+  }
+  T n[3] = {pn[4 * i], pn[4 * i + 1], pn[4 * i + 2]};
+  T ml = pn[4 * i + 3], mr = pmr[i];
+  T F[5];
+  rusanov(ul, ur, n, ph, F);
+  const T rl = ml / mr, rr = mr / ml;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    fc[fp_index(tt, tl, el, fl, 5, k)] = ml * F[k] - T(0.5) * (ql[k] - rl * qr[k]);
+    fc[fp_index(tt, tr, er, frr, 5, k)] = -mr * F[k] + T(0.5) * (rr * ql[k] - qr[k]);
+  }
+}
+
+// Boundary points: F^C = |S^T n~| Rus(u, ghost) - q (q already averaged).
+template <typename T>
+__global__ void k_bnd_flux_ns(int nb, const int32_t* __restrict__ bidx,
+                              const int32_t* __restrict__ bbc,
+                              const T* __restrict__ bn,
+                              const T* __restrict__ uf,
+                              const T* __restrict__ q, T* __restrict__ fc,
+                              TypeTab tt, Phys<T> ph, BCTab<T> bc) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nb) return;
+  int t, f;
+  long long e;
+  decode_fp(bidx[i], tt, &t, &e, &f);
+  T ul[5], ur[5], n[3] = {bn[4 * i], bn[4 * i + 1], bn[4 * i + 2]};
+#pragma unroll
+  for (int k = 0; k < 5; ++k) ul[k] = uf[fp_index(tt, t, e, f, 5, k)];
+  ghost_state(bc, bbc[i], ul, ur);
+  T F[5];
+  rusanov(ul, ur, n, ph, F);
+  T m = bn[4 * i + 3];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    long long ix = fp_index(tt, t, e, f, 5, k);
+    fc[ix] = m * F[k] - q[ix];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Dense kernels (prisms, tetrahedra, and the dense hexahedron variant) are
+// persistent: each CTA copies the type's operators into shared memory once
+// (when they fit) and then loops over groups of EPB elements.
+
+template <typename T, int NU, int NF>
+struct DenseLayout {
+  static constexpr int kOps = 3 * NU * NU + 2 * NU * NF + 3 * NF;
+  static constexpr bool kStaged = kOps * sizeof(T) <= 48 * 1024;
+  static constexpr int kStagedCount = kStaged ? kOps : 0;
+};
+
+template <typename T, int NU, int NF>
+__device__ __forceinline__ DenseOps<T> stage_dense_ops(const DenseOps<T>& g,
+                                                       T* s) {
+  if (!DenseLayout<T, NU, NF>::kStaged) return g;
+  T* dt = s;
+  T* m0 = dt + 3 * NU * NU;
+  T* li = m0 + NU * NF;
+  T* nr = li + NU * NF;
+  for (int i = threadIdx.x; i < 3 * NU * NU; i += blockDim.x) dt[i] = g.DT[i];
+  for (int i = threadIdx.x; i < NU * NF; i += blockDim.x) {
+    m0[i] = g.M0T[i];
+    li[i] = g.LIFTT[i];
+  }
+  for (int i = threadIdx.x; i < 3 * NF; i += blockDim.x) nr[i] = g.NREF[i];
+  __syncthreads();
+  return DenseOps<T>{m0, dt, li, nr};
+}
+
 // NS gradient path: corrected reference gradient D u + LIFT (n~ du), physical
 // gradient (1/J) S^T grad~ u at solution points, and its interpolation to
 // the flux points.
-template <typename T, int NU, int NF, int EPB>
+template <typename T, int NU, int NF, int EPB, bool QV>
 __global__ void __launch_bounds__(EPB* NU)
     k_grad_dense(long long ne, const T* __restrict__ u,
                  const T* __restrict__ du, const T* __restrict__ smat,
-                 const T* __restrict__ rcpdjac, DenseOps<T> ops,
-                 T* __restrict__ grad, T* __restrict__ gradf) {
+                 const T* __restrict__ rcpdjac, DenseOps<T> gops,
+                 T* __restrict__ grad, ViscArgs<T> va, BCTab<T> bc,
+                 Phys<T> ph) {
   extern __shared__ unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
+  const DenseOps<T> ops = stage_dense_ops<T, NU, NF>(gops, sm);
+  T* buf = sm + DenseLayout<T, NU, NF>::kStagedCount;
   const int le = threadIdx.x / NU, z = threadIdx.x % NU;
-  const long long e = (long long)blockIdx.x * EPB + le;
-  T* us = sm + le * (5 * NU + 5 * NF + 15 * NU);
+  T* us = buf + le * (5 * NU + 5 * NF + 15 * NU);
   T* ds = us + 5 * NU;
   T* gs = ds + 5 * NF;
-  if (e < ne) {
+  const long long ngroups = (ne + EPB - 1) / EPB;
+  for (long long grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+    const long long e = grp * EPB + le;
+    const bool act = e < ne;
+    if (act) {
 #pragma unroll
-    for (int k = 0; k < 5; ++k) us[k * NU + z] = u[(e * 5 + k) * NU + z];
-    for (int f = z; f < NF; f += NU)
+      for (int k = 0; k < 5; ++k) us[k * NU + z] = u[(e * 5 + k) * NU + z];
+      for (int f = z; f < NF; f += NU)
 #pragma unroll
-      for (int k = 0; k < 5; ++k) ds[k * NF + f] = du[(e * 5 + k) * NF + f];
-  }
-  __syncthreads();
-  if (e < ne) {
-    T gref[3][5];
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-#pragma unroll
-      for (int k = 0; k < 5; ++k) gref[d][k] = T(0);
-    for (int q = 0; q < NU; ++q) {
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        T w = ops.DT[(d * NU + q) * NU + z];
-#pragma unroll
-        for (int k = 0; k < 5; ++k) gref[d][k] += w * us[k * NU + q];
-      }
+        for (int k = 0; k < 5; ++k) ds[k * NF + f] = du[(e * 5 + k) * NF + f];
     }
-    for (int f = 0; f < NF; ++f) {
-      T l = ops.LIFTT[f * NU + z];
+    __syncthreads();
+    if (act) {
+      T gref[3][5];
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        T w = l * ops.NREF[f * 3 + d];
-        if (w != T(0)) {
+      for (int d = 0; d < 3; ++d)
 #pragma unroll
-          for (int k = 0; k < 5; ++k) gref[d][k] += w * ds[k * NF + f];
+        for (int k = 0; k < 5; ++k) gref[d][k] = T(0);
+      for (int q = 0; q < NU; ++q) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          T w = ops.DT[(d * NU + q) * NU + z];
+#pragma unroll
+          for (int k = 0; k < 5; ++k) gref[d][k] += w * us[k * NU + q];
+        }
+      }
+      for (int f = 0; f < NF; ++f) {
+        T l = ops.LIFTT[f * NU + z];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          T w = l * ops.NREF[f * 3 + d];
+          if (w != T(0)) {
+#pragma unroll
+            for (int k = 0; k < 5; ++k) gref[d][k] += w * ds[k * NF + f];
+          }
+        }
+      }
+      T S[3][3];
+#pragma unroll
+      for (int r = 0; r < 9; ++r) S[r / 3][r % 3] = smat[(e * 9 + r) * NU + z];
+      T rj = rcpdjac[e * NU + z];
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+          T gg = rj * (S[0][j] * gref[0][k] + S[1][j] * gref[1][k] +
+                       S[2][j] * gref[2][k]);
+          grad[(e * 15 + j * 5 + k) * NU + z] = gg;
+          gs[(j * 5 + k) * NU + z] = gg;
+        }
+    }
+    __syncthreads();
+    if (act) {
+      for (int f = z; f < NF; f += NU) {
+        T acc[15];
+#pragma unroll
+        for (int c = 0; c < 15; ++c) acc[c] = T(0);
+        for (int q = 0; q < NU; ++q) {
+          T m = ops.M0T[q * NF + f];
+#pragma unroll
+          for (int c = 0; c < 15; ++c) acc[c] += m * gs[c * NU + q];
+        }
+        if (QV) {
+          write_visc_q(va, bc, ph, e, f, NF, acc);
+        } else {
+#pragma unroll
+          for (int c = 0; c < 15; ++c) va.q[(e * 15 + c) * NF + f] = acc[c];
         }
       }
     }
-    T S[3][3];
-#pragma unroll
-    for (int r = 0; r < 9; ++r) S[r / 3][r % 3] = smat[(e * 9 + r) * NU + z];
-    T rj = rcpdjac[e * NU + z];
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-#pragma unroll
-      for (int k = 0; k < 5; ++k) {
-        T g = rj * (S[0][j] * gref[0][k] + S[1][j] * gref[1][k] +
-                    S[2][j] * gref[2][k]);
-        grad[(e * 15 + j * 5 + k) * NU + z] = g;
-        gs[(j * 5 + k) * NU + z] = g;
-      }
-  }
-  __syncthreads();
-  if (e >= ne) return;
-  for (int f = z; f < NF; f += NU) {
-    T acc[15];
-#pragma unroll
-    for (int c = 0; c < 15; ++c) acc[c] = T(0);
-    for (int q = 0; q < NU; ++q) {
-      T m = ops.M0T[q * NF + f];
-#pragma unroll
-      for (int c = 0; c < 15; ++c) acc[c] += m * gs[c * NU + q];
-    }
-#pragma unroll
-    for (int c = 0; c < 15; ++c) gradf[(e * 15 + c) * NF + f] = acc[c];
+    __syncthreads();
   }
 }
 
@@ -384,96 +542,105 @@ __global__ void __launch_bounds__(EPB* NU)
     k_vol_dense(long long ne, const T* __restrict__ u,
                 const T* __restrict__ grad, const T* __restrict__ fc,
                 const T* __restrict__ smat, const T* __restrict__ rcpdjac,
-                DenseOps<T> ops, Phys<T> ph, StageArgs<T> sa) {
+                DenseOps<T> gops, Phys<T> ph, StageArgs<T> sa) {
   extern __shared__ unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
+  const DenseOps<T> ops = stage_dense_ops<T, NU, NF>(gops, sm);
+  T* buf = sm + DenseLayout<T, NU, NF>::kStagedCount;
   const int le = threadIdx.x / NU, z = threadIdx.x % NU;
-  const long long e = (long long)blockIdx.x * EPB + le;
-  T* ft = sm + le * (15 * NU + 5 * NF);  // [3][5][NU]
-  T* jm = ft + 15 * NU;                  // [5][NF]
-  T uz[5];
-  if (e < ne) {
+  T* ft = buf + le * (15 * NU + 5 * NF);  // [3][5][NU]
+  T* jm = ft + 15 * NU;                   // [5][NF]
+  const long long ngroups = (ne + EPB - 1) / EPB;
+  for (long long grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+    const long long e = grp * EPB + le;
+    const bool act = e < ne;
+    T uz[5];
+    if (act) {
 #pragma unroll
-    for (int k = 0; k < 5; ++k) uz[k] = u[(e * 5 + k) * NU + z];
-    T F[3][5];
-    euler_flux(uz, ph, F);
-    if (NS) {
-      T g[3][5];
+      for (int k = 0; k < 5; ++k) uz[k] = u[(e * 5 + k) * NU + z];
+      T F[3][5];
+      euler_flux(uz, ph, F);
+      if (NS) {
+        T g[3][5];
 #pragma unroll
-      for (int j = 0; j < 3; ++j)
+        for (int j = 0; j < 3; ++j)
 #pragma unroll
-        for (int k = 0; k < 5; ++k) g[j][k] = grad[(e * 15 + j * 5 + k) * NU + z];
-      viscous_flux_acc(uz, g, ph, T(-1), F);
+          for (int k = 0; k < 5; ++k) g[j][k] = grad[(e * 15 + j * 5 + k) * NU + z];
+        viscous_flux_acc(uz, g, ph, T(-1), F);
+      }
+      T S[3][3];
+#pragma unroll
+      for (int r = 0; r < 9; ++r) S[r / 3][r % 3] = smat[(e * 9 + r) * NU + z];
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+          ft[(d * 5 + k) * NU + z] =
+              S[d][0] * F[0][k] + S[d][1] * F[1][k] + S[d][2] * F[2][k];
     }
-    T S[3][3];
+    __syncthreads();
+    if (act) {
+      for (int f = z; f < NF; f += NU) {
+        T fn[5] = {0, 0, 0, 0, 0};
+        T nr[3] = {ops.NREF[f * 3], ops.NREF[f * 3 + 1], ops.NREF[f * 3 + 2]};
+        for (int q = 0; q < NU; ++q) {
+          T m = ops.M0T[q * NF + f];
 #pragma unroll
-    for (int r = 0; r < 9; ++r) S[r / 3][r % 3] = smat[(e * 9 + r) * NU + z];
+          for (int d = 0; d < 3; ++d) {
+            if (nr[d] == T(0)) continue;
+            T w = m * nr[d];
 #pragma unroll
-    for (int d = 0; d < 3; ++d)
+            for (int k = 0; k < 5; ++k) fn[k] += w * ft[(d * 5 + k) * NU + q];
+          }
+        }
 #pragma unroll
-      for (int k = 0; k < 5; ++k)
-        ft[(d * 5 + k) * NU + z] =
-            S[d][0] * F[0][k] + S[d][1] * F[1][k] + S[d][2] * F[2][k];
-  }
-  __syncthreads();
-  if (e < ne) {
-    for (int f = z; f < NF; f += NU) {
-      T fn[5] = {0, 0, 0, 0, 0};
-      T nr[3] = {ops.NREF[f * 3], ops.NREF[f * 3 + 1], ops.NREF[f * 3 + 2]};
+        for (int k = 0; k < 5; ++k) jm[k * NF + f] = fc[(e * 5 + k) * NF + f] - fn[k];
+      }
+    }
+    __syncthreads();
+    T s[5];
+    if (act) {
+      T div[5] = {0, 0, 0, 0, 0};
       for (int q = 0; q < NU; ++q) {
-        T m = ops.M0T[q * NF + f];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-          if (nr[d] == T(0)) continue;
-          T w = m * nr[d];
+          T w = ops.DT[(d * NU + q) * NU + z];
 #pragma unroll
-          for (int k = 0; k < 5; ++k) fn[k] += w * ft[(d * 5 + k) * NU + q];
+          for (int k = 0; k < 5; ++k) div[k] += w * ft[(d * 5 + k) * NU + q];
         }
       }
+      for (int f = 0; f < NF; ++f) {
+        T l = ops.LIFTT[f * NU + z];
 #pragma unroll
-      for (int k = 0; k < 5; ++k) jm[k * NF + f] = fc[(e * 5 + k) * NF + f] - fn[k];
+        for (int k = 0; k < 5; ++k) div[k] += l * jm[k * NF + f];
+      }
+      T rj = rcpdjac[e * NU + z];
+      T R[5];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) R[k] = -div[k] * rj;
+      stage_update(sa, e * 5 * NU + z, NU, uz, R, s);
     }
-  }
-  __syncthreads();
-  T s[5];
-  if (e < ne) {
-    T div[5] = {0, 0, 0, 0, 0};
-    for (int q = 0; q < NU; ++q) {
+    if (sa.uf_next != nullptr) {
+      __syncthreads();  // ft no longer read: reuse it for the next stage value
+      if (act) {
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        T w = ops.DT[(d * NU + q) * NU + z];
+        for (int k = 0; k < 5; ++k) ft[k * NU + z] = s[k];
+      }
+      __syncthreads();
+      if (act) {
+        for (int f = z; f < NF; f += NU) {
+          T acc[5] = {0, 0, 0, 0, 0};
+          for (int q = 0; q < NU; ++q) {
+            T m = ops.M0T[q * NF + f];
 #pragma unroll
-        for (int k = 0; k < 5; ++k) div[k] += w * ft[(d * 5 + k) * NU + q];
+            for (int k = 0; k < 5; ++k) acc[k] += m * ft[k * NU + q];
+          }
+#pragma unroll
+          for (int k = 0; k < 5; ++k) sa.uf_next[(e * 5 + k) * NF + f] = acc[k];
+        }
       }
     }
-    for (int f = 0; f < NF; ++f) {
-      T l = ops.LIFTT[f * NU + z];
-#pragma unroll
-      for (int k = 0; k < 5; ++k) div[k] += l * jm[k * NF + f];
-    }
-    T rj = rcpdjac[e * NU + z];
-    T R[5];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) R[k] = -div[k] * rj;
-    stage_update(sa, e * 5 * NU + z, NU, uz, R, s);
-  }
-  if (sa.uf_next == nullptr) return;
-  __syncthreads();  // ft no longer read: reuse it for the next stage value
-  if (e < ne) {
-#pragma unroll
-    for (int k = 0; k < 5; ++k) ft[k * NU + z] = s[k];
-  }
-  __syncthreads();
-  if (e >= ne) return;
-  for (int f = z; f < NF; f += NU) {
-    T acc[5] = {0, 0, 0, 0, 0};
-    for (int q = 0; q < NU; ++q) {
-      T m = ops.M0T[q * NF + f];
-#pragma unroll
-      for (int k = 0; k < 5; ++k) acc[k] += m * ft[k * NU + q];
-    }
-#pragma unroll
-    for (int k = 0; k < 5; ++k) sa.uf_next[(e * 5 + k) * NF + f] = acc[k];
+    __syncthreads();
   }
 }
 

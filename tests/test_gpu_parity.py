@@ -245,3 +245,36 @@ def test_mixed_precision_tgv_within_stated_tolerance(p):
     g.rk_step("rk45", 1e-3, 5)
     err = rel_l2(g.get_solution(), u)
     assert err.max() < 1e-5, err
+
+
+@pytest.mark.parametrize("variant", ["sumfact", "sumfact_vertex", "dense"])
+def test_fp32_hex_families_against_oracle(variant):
+    spec = box_hex((3, 3, 2), perturb=0.1)
+    o, osys, g = _pair(spec, 3, "ns", precision="fp32")
+    g.set_variant(variant)
+    g.set_solution(lib_state(g, _tgv))
+    u = oracle_state(o, _tgv)
+    for _ in range(2):
+        u = rk.step(osys.rhs, u, 1e-3, "rk45")
+    g.rk_step("rk45", 1e-3, 2)
+    err = rel_l2(g.get_solution(), u)
+    assert err.max() < 1e-6, err
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_autotuner_picks_a_family_and_keeps_the_state(precision):
+    spec = box_hex((5, 5, 5), perturb=0.1)
+    kw = dict(physics="ns", mu=0.02, prandtl=0.71, precision=precision)
+    g = fr.FRMesh(spec, 3, **kw)
+    u0 = lib_state(g, _tgv)
+    g.set_solution(u0)
+    g.rk_step("rk45", 1e-3, 2)
+    active, ms = g.tuning()
+    expect = 3 if precision == "fp32" else 2
+    assert len(ms) == expect and active in ms
+    assert ms[active] == min(ms.values())
+    h = fr.FRMesh(spec, 3, **kw)
+    h.set_variant(active)
+    h.set_solution(u0)
+    h.rk_step("rk45", 1e-3, 2)
+    assert np.array_equal(g.get_solution()["hex"], h.get_solution()["hex"])
