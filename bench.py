@@ -132,15 +132,19 @@ def kernel_models(nu, nf, ne, w, wr, npair):
     right-hand side on hexahedra (sum-factorised operators), N = p + 1.
     w: bytes of a trace/stage value, wr: bytes of a solution register."""
     n = round(nu ** (1.0 / 3.0))
+    # FP64 values: 15 gradient components per flux point go to the face
+    # kernel; FP32 values: 5 viscous normal-flux values q per flux point
+    # (plus the 5 solution traces the grad kernel reads to form q)
+    gf = 15 if w == 8 else 10
     bytes_ = {
-        # u(5) + metrics(10) + du(5 per flux pt) in, grad(15) + gradf(15) out
-        "grad": ne * (w * (5 * nu + 10 * nu + 5 * nf + 15 * nu + 15 * nf)),
+        # u(5) + metrics(10) + du(5 per flux pt) in, grad(15) + gradf out
+        "grad": ne * (w * (5 * nu + 10 * nu + 5 * nf + 15 * nu + gf * nf)),
         # u(5) + grad(15) + metrics(10) + F^C(5/fpt) in; Y and u_f out;
         # solution register X in and out
         "volume": ne * (w * (5 * nu + 15 * nu + 10 * nu + 5 * nf + 5 * nu
                              + 5 * nf) + wr * 10 * nu),
         "face_ucommon": npair * (w * 20 + 8),
-        "face_flux": npair * (w * (2 * 20 + 5 + 10) + 8),
+        "face_flux": npair * (w * (2 * (20 if w == 8 else 10) + 5 + 10) + 8),
     }
     flops = {
         "grad": ne * (2 * nu * (15 * n + 30 + 45) + 15 * nu
@@ -185,6 +189,20 @@ def roofline(prof, models, peaks, src, precision):
 
 
 # ------------------------------------------------------------ our arm
+def aggregate(ms_local, units_local, dist=None, device="cpu"):
+    """Whole-job figures over ranks running independent replicas: the
+    slowest rank's time and the units processed by all ranks."""
+    if dist is None:
+        return float(ms_local), float(units_local)
+    import torch
+    mx = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    sm = torch.tensor([float(units_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx.item()), float(sm.item())
+
+
+
 def measure(fr, torch, precision, steps, warmup, device, dist):
     spec = workload_spec(N_CELLS)
     mesh = fr.FRMesh(spec, ORDER, physics="ns", gamma=1.4, mu=1.0 / RE,
@@ -211,10 +229,9 @@ def measure(fr, torch, precision, steps, warmup, device, dist):
     torch.cuda.synchronize()
     clocks = sampler.stop()
     ms = t0.elapsed_time(t1)
+    ne, nu, _ = mesh.info("hex")
+    ms, units = aggregate(ms, ne * nu * 5 * STAGES * steps, dist, "cuda")
     if dist:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
         dist.barrier()
     final = mesh.get_solution()["hex"]
     tuning = mesh.tuning()
@@ -226,6 +243,7 @@ def measure(fr, torch, precision, steps, warmup, device, dist):
             a[0] += t / reps
             a[1] = n
     prof["_tuning"] = tuning
+    prof["_units"] = units
     return mesh, u0, ms, clocks, prof, final
 
 
@@ -249,9 +267,11 @@ def run_ours(args):
     mesh, u0, ms, clocks, prof, final = measure(
         fr, torch, args.precision, args.steps, args.warmup, local, dist)
     tuning = prof.pop("_tuning")
+    units_all = prof.pop("_units")
     ne, nu, nf = mesh.info("hex")
     units_per_step = ne * nu * 5 * STAGES
-    value = units_per_step * args.steps * world / (ms * 1e-3) / 1e9
+    # whole job: units of all replicas / slowest rank's time
+    value = units_all / (ms * 1e-3) / 1e9
     launches_per_step = sum(n for _, n in prof.values())
     # end-to-end through the C ABI with pinned host buffers: every step
     # copies the state in, runs one RK step and copies the state out
@@ -308,6 +328,7 @@ def run_ours(args):
             m2, _, ms2, _, prof2, fin2 = measure(
                 fr, torch, prec, args.steps, args.warmup, local, None)
             tun2 = prof2.pop("_tuning")
+            prof2.pop("_units")
             w2 = 8 if prec == "fp64" else 4
             wr2 = 4 if prec == "fp32" else 8
             if args.precision == "fp64":
