@@ -463,9 +463,11 @@ def config_mixed_elements(fr, torch, device, steps=20):
     mesh.rk_step("rk4", 2e-4, 2)
     ms = _timed_steps(torch, mesh, st, "rk4", 2e-4, steps)
     prof = mesh.profile_step("rk4", 2e-4)
+    active, tuned = mesh.tuning()
     out = {"gdof_stage_s": _gdofs(mesh, 4, steps, ms), "ms_per_step": ms / steps,
            "elements": {t: mesh.info(t)[0] for t in mesh.types},
-           "kernel_ms_per_step": {k: v[0] for k, v in prof.items() if v[1]}}
+           "kernel_ms_per_step": {k: v[0] for k, v in prof.items() if v[1]},
+           "kernel_family": {"active": active, "tuned_ms_per_step": tuned}}
     mesh.close()
     return out
 

@@ -168,22 +168,28 @@ enum { FR_KC_FACE_U = 0,  /* NS common solution at interior flux points */
 int fr_profile_step(fr_mesh* mesh, int scheme, double dt, double* ms,
                     int* launches);
 
-/* Kernel family for hexahedra.  FR_VARIANT_SUMFACT applies the operators
+/* Kernel family.  For hexahedra: FR_VARIANT_SUMFACT applies the operators
  * line by line (1D factors of the tensor-product basis) with metric terms
  * stored per solution point; FR_VARIANT_SUMFACT_VERTEX (FP32 values only)
  * computes the metric terms from the 8 vertices and recomputes gradients
  * instead of storing them (less DRAM traffic, more arithmetic);
  * FR_VARIANT_DENSE applies the full operator matrices as for prisms and
- * tetrahedra.  All give the same result up to rounding.  FR_VARIANT_AUTO
- * (default): the first fr_rk_step times one step of each applicable family
- * on a copy of the state (restored afterwards) and keeps the fastest;
- * fr_get_tuning reports the choice. */
+ * tetrahedra.  FR_VARIANT_TENSOR (FP32 values; prisms and tetrahedra of
+ * order 2..3, tetrahedra of order 4): hexahedra as FR_VARIANT_SUMFACT,
+ * and the dense operator products of prisms and tetrahedra (Eqs. disu,
+ * FRfinal and the gradient path) on the tensor cores as three TF32 products
+ * per product (operands split into TF32 hi + lo parts, FP32 accumulation);
+ * types without that form keep the CUDA-core kernels.  The other families run
+ * prisms and tetrahedra on the CUDA cores.  All give the same result up to
+ * rounding.  FR_VARIANT_AUTO (default): the first fr_rk_step times one step
+ * of each applicable family on a copy of the state (restored afterwards) and
+ * keeps the fastest; fr_get_tuning reports the choice. */
 enum { FR_VARIANT_AUTO = 0, FR_VARIANT_DENSE = 1, FR_VARIANT_SUMFACT = 2,
-       FR_VARIANT_SUMFACT_VERTEX = 3 };
+       FR_VARIANT_SUMFACT_VERTEX = 3, FR_VARIANT_TENSOR = 4 };
 int fr_set_kernel_variant(fr_mesh* mesh, int variant);
 
 /* Kernel family in use and the step times (ms, 0 if not tried) the tuner
- * measured for families 1..3 (index = FR_VARIANT_*). */
+ * measured, ms_per_step[5] indexed by FR_VARIANT_* (entry 0 unused). */
 int fr_get_tuning(const fr_mesh* mesh, int* active, float* ms_per_step);
 
 /* Kernels and copies of the handle run on this stream (cudaStream_t);

@@ -17,7 +17,8 @@ ERRORS = {-1: "FR_EINVAL", -2: "FR_ENOMEM", -3: "FR_ECUDA", -4: "FR_EMESH",
 ETYPES = {"hex": 0, "pri": 1, "tet": 2}
 PHYSICS = {"euler": 0, "ns": 1}
 PRECISION = {"fp64": 0, "fp32": 1, "mixed": 2}
-VARIANTS = {"auto": 0, "dense": 1, "sumfact": 2, "sumfact_vertex": 3}
+VARIANTS = {"auto": 0, "dense": 1, "sumfact": 2, "sumfact_vertex": 3,
+            "tensor": 4}
 SCHEMES = {"rk4": 0, "rk45": 1}
 BC_KIND = {"state": 0, "extrap": 1}
 
@@ -264,14 +265,15 @@ class FRMesh:
     def tuning(self):
         """(active kernel family, {family: ms per tuned step})."""
         a = C.c_int()
-        ms = np.zeros(4, np.float32)
+        ms = np.zeros(5, np.float32)
         _check(load().fr_get_tuning(self._h, C.byref(a), _ptr(ms)))
         names = {v: k for k, v in VARIANTS.items()}
-        return names[a.value], {names[i]: float(ms[i]) for i in range(1, 4)
+        return names[a.value], {names[i]: float(ms[i]) for i in range(1, 5)
                                 if ms[i] > 0}
 
     def set_variant(self, name):
-        """Kernel family for hexahedra: 'auto', 'dense' or 'sumfact'."""
+        """Kernel family: 'auto', 'dense', 'sumfact', 'sumfact_vertex' or
+        'tensor' (tensor-core prisms / tetrahedra, FP32 values)."""
         _check(load().fr_set_kernel_variant(self._h, VARIANTS[name]))
 
     def filter_enable(self, on=True, sample_capacity=0):

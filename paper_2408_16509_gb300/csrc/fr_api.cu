@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "../../include/frgb.h"
+#include "fr_dense_tc.cuh"
 #include "fr_filter.cuh"
 #include "fr_hex.cuh"
 #include "fr_kernels.cuh"
@@ -112,6 +113,11 @@ struct DevType {
   void* fnv = nullptr;       // [ne][3][nf] S^T n~ at flux points (NS)
   int8_t* fbc = nullptr;     // [ne][nf] boundary-condition index or -1 (NS)
   void* verts = nullptr;     // [ne][8][3] vertices minus vertex 0 (hex, FP32)
+  // tensor-core kernels (prisms / tetrahedra, FP32 values)
+  bool tc_ok = false;
+  void* tcimg = nullptr;     // split-TF32 operator image
+  TcGeom tcgeo{};
+  int tc_vol_ctas = 1, tc_grad_ctas = 1;
 };
 
 void free_all(std::vector<void*>& v) {
@@ -159,7 +165,7 @@ struct fr_mesh {
   int variant = FR_VARIANT_AUTO;   // requested kernel family
   int active = FR_VARIANT_SUMFACT; // family in use (the tuner's choice)
   bool tuned = false;
-  float tune_ms[4] = {0, 0, 0, 0}; // ms per step of each family tried
+  float tune_ms[5] = {0, 0, 0, 0, 0}; // ms per step of each family tried
   long long epoch = 0;            // bumped by every change of launch config
   long long graph_epoch[2] = {-1, -1};
   bool filter_on = false;
@@ -230,6 +236,91 @@ HexOps<T> hex_ops(const RefElement& R) {
   return h;
 }
 
+// TF32 value of x rounded to nearest, ties away from zero (the rounding of
+// cvt.rna.tf32.f32): the low 13 mantissa bits become zero.
+float tf32_rna_host(float x) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  if ((u & 0x7f800000u) != 0x7f800000u) {
+    u += 0x1000u;
+    u &= 0xffffe000u;
+  }
+  float r;
+  std::memcpy(&r, &u, 4);
+  return r;
+}
+
+// Face-aligned flux-point order and split-TF32 operator image of the
+// tensor-core kernels for a prism or tetrahedron (layout documented in
+// fr_dense_tc.cuh).  False when the element does not have the expected face
+// structure (contiguous faces with one reference normal each).
+bool build_tc(const RefElement& R, std::vector<double>& img, TcGeom& geo) {
+  const int nu = R.nupts, nf = R.nfpts;
+  const int KU = tc_ru(nu, 8), K3 = 3 * KU, KFP = tc_kfp(nu, nf);
+  const int NFACE = tc_nface(nu, nf);
+  if (KFP == 0 || KFP > 128 || nf > 128 || nu > 128 || R.nfaces != NFACE ||
+      int(R.face_start.size()) != NFACE + 1)
+    return false;
+  const int MU = nu <= 64 ? 64 : 128, MF = nf <= 64 ? 64 : 128;
+  geo = TcGeom{};
+  std::vector<int> fpad(nf, -1);
+  int kofs = 0;
+  for (int fa = 0; fa < NFACE; ++fa) {
+    const int f0 = R.face_start[fa], f1 = R.face_start[fa + 1];
+    geo.fslice[fa] = kofs / 8;
+    for (int f = f0; f < f1; ++f) {
+      fpad[f] = kofs + (f - f0);
+      for (int d = 0; d < 3; ++d)
+        if (R.fnorm[size_t(f) * 3 + d] != R.faces[fa].normal[d]) return false;
+    }
+    for (int d = 0; d < 3; ++d) geo.nface[fa][d] = float(R.faces[fa].normal[d]);
+    kofs += tc_ru(f1 - f0, 8);
+  }
+  geo.fslice[NFACE] = kofs / 8;
+  if (kofs != KFP) return false;
+  std::vector<bool> used(KFP, false);
+  for (int f = 0; f < nf; ++f) {
+    if (fpad[f] < 0) return false;
+    geo.fpad[f] = uint8_t(fpad[f]);
+    used[fpad[f]] = true;
+  }
+  geo.npad = 0;
+  for (int k = 0; k < KFP; ++k)
+    if (!used[k]) geo.pad[geo.npad++] = uint8_t(k);
+  const size_t sm0 = size_t(MF) * KU, sd3 = size_t(MU) * K3, sl = size_t(MU) * KFP;
+  img.assign(2 * (sm0 + sd3 + sl), 0.0);
+  auto put = [&](size_t base, size_t plane, int off, double x) {
+    const float h = tf32_rna_host(float(x));
+    img[base + off] = h;
+    img[base + plane + off] = tf32_rna_host(float(x - double(h)));
+  };
+  const size_t b_m0 = 0, b_d3 = 2 * sm0, b_l = 2 * (sm0 + sd3);
+  for (int f = 0; f < nf; ++f)
+    for (int q = 0; q < nu; ++q)
+      put(b_m0, sm0, tc_offset(f, q, KU), R.M0[size_t(f) * nu + q]);
+  for (int d = 0; d < 3; ++d)
+    for (int z = 0; z < nu; ++z)
+      for (int q = 0; q < nu; ++q)
+        put(b_d3, sd3, tc_offset(z, d * KU + q, K3), R.D[(size_t(d) * nu + z) * nu + q]);
+  for (int z = 0; z < nu; ++z)
+    for (int f = 0; f < nf; ++f)
+      put(b_l, sl, tc_offset(z, fpad[f], KFP), R.LIFT[size_t(z) * nf + f]);
+  return true;
+}
+
+// Compile-time tile of the tensor-core kernels for (NU, NF); false when the
+// type has no tensor-core form (then the CUDA-core dense kernels run).
+template <int NU, int NF>
+constexpr bool tc_supported() {
+  return tc_vol_epb<NU, NF>() > 0 && tc_grad_epb<NU, NF>() > 0;
+}
+
+// precisions with tensor-core kernels: FP32 values and registers
+template <typename T, typename TR>
+constexpr bool tc_types() {
+  return std::is_same<T, float>::value && std::is_same<TR, float>::value;
+}
+
 // T: storage/compute type of traces, fluxes and stage values;
 // TR: type of the RK solution and accumulator registers (X, A).
 template <typename T, typename TR>
@@ -275,6 +366,17 @@ int setup_device(fr_mesh* m) {
     if ((rc = dev_upload<T>(m, dt, &D.DT))) return rc;
     if ((rc = dev_upload<T>(m, lt, &D.LIFTT))) return rc;
     if ((rc = dev_upload<T>(m, R.fnorm, &D.NREF))) return rc;
+    if (sizeof(T) == 4 && D.kind != EK_HEX) {
+      bool fits = false;
+      dispatch(D.kind, m->order, [&](auto nu, auto nf) {
+        fits = tc_supported<decltype(nu)::value, decltype(nf)::value>();
+      });
+      std::vector<double> img;
+      if (fits && build_tc(R, img, D.tcgeo)) {
+        if ((rc = dev_upload<float>(m, img, &D.tcimg))) return rc;
+        D.tc_ok = true;
+      }
+    }
     if (D.kind == EK_HEX) {
       D.hx64 = hex_ops<double>(R);
       D.hx32 = hex_ops<float>(R);
@@ -411,6 +513,68 @@ bool use_hex(const fr_mesh* m, const DevType& D) {
   return D.kind == EK_HEX && m->active != FR_VARIANT_DENSE;
 }
 
+bool use_tc(const fr_mesh* m, const DevType& D) {
+  return D.tc_ok && m->active == FR_VARIANT_TENSOR;
+}
+
+// Tensor-core gradient kernel of a prism / tetrahedron type (FP32 values).
+template <typename T, typename TR>
+void launch_grad_tc(fr_mesh* m, const DevType& D, cudaStream_t s, bool from_x,
+                    const T* du, const ViscArgs<T>& va, const BCTab<T>& bc,
+                    const Phys<T>& ph) {
+  if constexpr (tc_types<T, TR>()) {
+    if (D.ne == 0) return;
+    dispatch(D.kind, m->order, [&](auto nu, auto nf) {
+      constexpr int NU = decltype(nu)::value, NF = decltype(nf)::value;
+      if constexpr (tc_supported<NU, NF>()) {
+        constexpr int EG = tc_grad_epb<NU, NF>();
+        constexpr int BG = tc_minb_grad<NU, NF, EG>();
+        const long long tiles = (D.ne + EG - 1) / EG;
+        const unsigned grid = unsigned(
+            std::min<long long>(tiles, (long long)m->num_sms * D.tc_grad_ctas));
+        k_grad_tc<NU, NF, EG, TR, BG>
+            <<<grid, kTcThreads, TcGradCfg<NU, NF, EG>::SMEM, s>>>(
+                D.ne, from_x ? nullptr : (const float*)D.Y, (const TR*)D.X, du,
+                (const float*)D.smat, (const float*)D.rcpdjac,
+                (const float*)D.tcimg, D.tcgeo, (float*)D.grad, va, bc, ph,
+                m->d_flag);
+      }
+    });
+  }
+}
+
+// Tensor-core volume kernel of a prism / tetrahedron type (FP32 values).
+template <typename T, typename TR>
+void launch_vol_tc(fr_mesh* m, const DevType& D, cudaStream_t s, bool from_x,
+                   bool ns, const T* fc, const Phys<T>& ph,
+                   const HexStage<T, TR>& sa) {
+  if constexpr (tc_types<T, TR>()) {
+    if (D.ne == 0) return;
+    dispatch(D.kind, m->order, [&](auto nu, auto nf) {
+      constexpr int NU = decltype(nu)::value, NF = decltype(nf)::value;
+      if constexpr (tc_supported<NU, NF>()) {
+        constexpr int EV = tc_vol_epb<NU, NF>();
+        constexpr int BV = tc_minb_vol<NU, NF, EV>();
+        const long long tiles = (D.ne + EV - 1) / EV;
+        const unsigned grid = unsigned(
+            std::min<long long>(tiles, (long long)m->num_sms * D.tc_vol_ctas));
+        const size_t sm = TcVolCfg<NU, NF, EV>::SMEM;
+        const float* uin = from_x ? nullptr : (const float*)D.Y;
+        if (ns)
+          k_vol_tc<NU, NF, EV, true, TR, BV><<<grid, kTcThreads, sm, s>>>(
+              D.ne, uin, (const float*)D.grad, fc, (const float*)D.smat,
+              (const float*)D.rcpdjac, (const float*)D.tcimg,
+              (const float*)D.NREF, D.tcgeo, ph, sa);
+        else
+          k_vol_tc<NU, NF, EV, false, TR, BV><<<grid, kTcThreads, sm, s>>>(
+              D.ne, uin, nullptr, fc, (const float*)D.smat,
+              (const float*)D.rcpdjac, (const float*)D.tcimg,
+              (const float*)D.NREF, D.tcgeo, ph, sa);
+      }
+    });
+  }
+}
+
 // shared memory of the FP32-value hexahedron kernels (vertex metrics,
 // recomputed gradients)
 template <typename T, int N>
@@ -446,6 +610,29 @@ int prepare_kernels(fr_mesh* m) {
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kv1, E * NU, sv);
       D.grad_ctas = a > 0 ? a : 1;
       D.vol_ctas = b > 0 ? b : 1;
+      if constexpr (tc_types<T, TR>() && tc_supported<NU, NF>()) {
+        if (D.tc_ok) {
+          constexpr int EV = tc_vol_epb<NU, NF>(), EG = tc_grad_epb<NU, NF>();
+          constexpr int BV = tc_minb_vol<NU, NF, EV>(), BG = tc_minb_grad<NU, NF, EG>();
+          auto tv0 = k_vol_tc<NU, NF, EV, false, TR, BV>;
+          auto tv1 = k_vol_tc<NU, NF, EV, true, TR, BV>;
+          auto tg = k_grad_tc<NU, NF, EG, TR, BG>;
+          const int smv = int(TcVolCfg<NU, NF, EV>::SMEM);
+          const int smg = int(TcGradCfg<NU, NF, EG>::SMEM);
+          cudaFuncSetAttribute(tv0, cudaFuncAttributeMaxDynamicSharedMemorySize, smv);
+          cudaFuncSetAttribute(tv1, cudaFuncAttributeMaxDynamicSharedMemorySize, smv);
+          cudaFuncSetAttribute(tg, cudaFuncAttributeMaxDynamicSharedMemorySize, smg);
+          for (auto fn : {(const void*)tv0, (const void*)tv1, (const void*)tg})
+            cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 int(cudaSharedmemCarveoutMaxShared));
+          // resident CTAs per SM as designed: shared memory (the MINB bound
+          // of the kernel's launch bounds) and the 512 TMEM columns.  (The
+          // occupancy calculator reports one CTA for these kernels although
+          // two fit; a grid that is too large would only run in two waves.)
+          D.tc_vol_ctas = std::max(1, std::min(BV, 512 / TcVolCfg<NU, NF, EV>::TCOLS));
+          D.tc_grad_ctas = std::max(1, std::min(BG, 512 / TcGradCfg<NU, NF, EG>::TCOLS));
+        }
+      }
     });
     if (D.kind != EK_HEX) continue;
     hex_dispatch(m->order, [&](auto n) {
@@ -576,6 +763,8 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
                   (const T*)D.smat, (const T*)D.rcpdjac, hexops<T>(D),
                   (T*)D.grad, va, bc, ph);
         });
+      } else if (use_tc(m, D)) {
+        launch_grad_tc<T, TR>(m, D, s, from_x, du, va, bc, ph);
       } else {
         dispatch(D.kind, m->order, [&](auto nu, auto nf) {
           constexpr int NU = decltype(nu)::value, NF = decltype(nf)::value;
@@ -656,6 +845,10 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
               D.ne, uin, nullptr, fc, (const T*)D.smat, (const T*)D.rcpdjac,
               hexops<T>(D), ph, sa);
       });
+    } else if (use_tc(m, D)) {
+      HexStage<T, TR> sa{mode, stage, (TR*)D.X, (TR*)D.A, (T*)D.Y, (T*)D.R,
+                         m->d_dt, m->d_flag, uf_next};
+      launch_vol_tc<T, TR>(m, D, s, from_x, ns, fc, ph, sa);
     } else {
       StageArgs<T> sa;
       sa.mode = mode;
@@ -772,6 +965,7 @@ int do_rhs(fr_mesh* m) {
   CK(cudaMemcpyAsync(&flag, m->d_flag, sizeof(int), cudaMemcpyDeviceToHost,
                      m->stream));
   CK(cudaStreamSynchronize(m->stream));
+  if (flag & 2) return fail(FR_ETIMEOUT, "a tensor-core wait timed out");
   if (flag) return fail(FR_ENONFINITE, "right-hand side is not finite");
   return FR_OK;
 }
@@ -804,11 +998,15 @@ int build_graph(fr_mesh* m, int scheme) {
 // unchanged.
 template <typename T, typename TR>
 int resolve_variant(fr_mesh* m, int scheme, double dt) {
-  bool has_hex = false;
-  for (auto& D : m->types) has_hex |= D.kind == EK_HEX;
+  bool has_hex = false, has_tc = false;
+  for (auto& D : m->types) {
+    has_hex |= D.kind == EK_HEX;
+    has_tc |= D.tc_ok;
+  }
   if (m->variant != FR_VARIANT_AUTO) {
     int v = m->variant;
     if (v == FR_VARIANT_SUMFACT_VERTEX && sizeof(T) != 4) v = FR_VARIANT_SUMFACT;
+    if (v == FR_VARIANT_TENSOR && !has_tc) v = FR_VARIANT_SUMFACT;
     if (v != m->active) {
       m->active = v;
       m->uf_valid = false;
@@ -816,10 +1014,11 @@ int resolve_variant(fr_mesh* m, int scheme, double dt) {
     }
     return FR_OK;
   }
-  if (m->tuned || !has_hex) return FR_OK;
+  if (m->tuned || !(has_hex || has_tc)) return FR_OK;
   std::vector<int> cand = {FR_VARIANT_SUMFACT};
-  if (sizeof(T) == 4) cand.push_back(FR_VARIANT_SUMFACT_VERTEX);
-  if (m->precision != FR_MIXED) cand.push_back(FR_VARIANT_DENSE);
+  if (has_hex && sizeof(T) == 4) cand.push_back(FR_VARIANT_SUMFACT_VERTEX);
+  if (has_hex && m->precision != FR_MIXED) cand.push_back(FR_VARIANT_DENSE);
+  if (has_tc) cand.push_back(FR_VARIANT_TENSOR);
   std::vector<void*> saved;
   auto release = [&]() {
     for (void* p : saved)
@@ -908,6 +1107,7 @@ int do_rk(fr_mesh* m, int scheme, double dt, int nsteps) {
   CK(cudaMemcpyAsync(&flag, m->d_flag, sizeof(int), cudaMemcpyDeviceToHost,
                      m->stream));
   CK(cudaStreamSynchronize(m->stream));
+  if (flag & 2) return fail(FR_ETIMEOUT, "a tensor-core wait timed out");
   if (flag) return fail(FR_ENONFINITE, "a Runge-Kutta stage is not finite");
   return FR_OK;
 }
@@ -1256,7 +1456,8 @@ int fr_profile_step(fr_mesh* m, int scheme, double dt, double* ms,
 int fr_set_kernel_variant(fr_mesh* m, int variant) {
   if (!m) return fail(FR_EINVAL, "null mesh");
   if (variant != FR_VARIANT_AUTO && variant != FR_VARIANT_DENSE &&
-      variant != FR_VARIANT_SUMFACT && variant != FR_VARIANT_SUMFACT_VERTEX)
+      variant != FR_VARIANT_SUMFACT && variant != FR_VARIANT_SUMFACT_VERTEX &&
+      variant != FR_VARIANT_TENSOR)
     return fail(FR_EINVAL, "unknown kernel variant");
   if (variant == FR_VARIANT_DENSE && m->precision == FR_MIXED)
     return fail(FR_EINVAL, "FR_MIXED runs the sum-factorised kernels only");
@@ -1270,7 +1471,7 @@ int fr_get_tuning(const fr_mesh* m, int* active, float* ms) {
   if (!m) return fail(FR_EINVAL, "null mesh");
   if (active) *active = m->active;
   if (ms)
-    for (int i = 0; i < 4; ++i) ms[i] = m->tune_ms[i];
+    for (int i = 0; i < 5; ++i) ms[i] = m->tune_ms[i];
   return FR_OK;
 }
 
