@@ -25,6 +25,8 @@
 #pragma once
 #include <cuda_bf16.h>
 
+#include <type_traits>
+
 #include "fr_kernels.cuh"
 
 namespace frgb {
@@ -85,6 +87,43 @@ __device__ __forceinline__ double entropy_of(double r, double mx, double my,
   return INFINITY;
 }
 
+// FP32 screen of a point for the exact FP64 minima of p and s = p rho^-g.
+// From the state rounded to FP32, p32 and a bound dp with |p32 - p| <= dp
+// (p the FP64 pressure of the same state): every operation of
+// p = (g-1)(E - (mx^2+my^2+mz^2)/(2 rho)) and the rounding of the inputs
+// contribute at most ~11 unit roundoffs (2^-24) of (g-1)(|E| + |k|); dp
+// takes 2e-6 ~ 34 of them.  __powf(rho, -g) is within ~2e-6 relative; the s
+// bounds widen it to 1e-5.  Points with rho <= 0 (or NaN) get no bounds.
+struct PtScreen {
+  float plo, phi, slo, shi;
+  bool pos;  // rho > 0 in FP32 (bounds valid)
+};
+
+__device__ __forceinline__ PtScreen screen_point(float r, float mx, float my,
+                                                 float mz, float E, float g) {
+  PtScreen o;
+  o.pos = r > 0.f;
+  if (!o.pos) {
+    o.plo = o.slo = -INFINITY;
+    o.phi = o.shi = INFINITY;
+    return o;
+  }
+  const float k = 0.5f * (mx * mx + my * my + mz * mz) / r;
+  const float gm1 = g - 1.f;
+  const float p = gm1 * (E - k);
+  const float dp = 2e-6f * gm1 * (fabsf(E) + fabsf(k));
+  o.plo = p - dp;
+  o.phi = p + dp;
+  const float rg = __powf(r, -g);
+  o.slo = o.plo * rg * (o.plo >= 0.f ? 1.f - 1e-5f : 1.f + 1e-5f);
+  o.shi = o.phi * rg * (o.phi >= 0.f ? 1.f + 1e-5f : 1.f - 1e-5f);
+  return o;
+}
+
+__device__ __forceinline__ double pressure64(const double v[5], double g) {
+  return (g - 1.0) * (v[4] - 0.5 * (v[1] * v[1] + v[2] * v[2] + v[3] * v[3]) / v[0]);
+}
+
 __device__ __forceinline__ double warp_min(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -97,9 +136,12 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// s_min per element from the stage input: one warp per element.  Every
-// point gets an FP32 estimate of s; the exact FP64 value is computed for the
-// points whose estimate is within 1e-4 (relative) of the warp's smallest.
+// s_min per element from the stage input: one warp per element, over the
+// element's solution and flux points and its face neighbours' flux points,
+// s = p rho^-g at the admissible points (rho > 0, p > 0), 0 when there are
+// none.  Every point is screened in FP32 (screen_point); the FP64 value is
+// computed only where the screen cannot exclude the minimum or cannot decide
+// admissibility, so the result equals the all-FP64 minimum.
 template <typename T, typename TR, int NU, int NF>
 __global__ void k_entropy_min(long long ne, const T* __restrict__ uin,
                               const TR* __restrict__ X,
@@ -111,57 +153,69 @@ __global__ void k_entropy_min(long long ne, const T* __restrict__ uin,
   const long long e = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (e >= ne) return;
   const T* uf = uf_all + tt.off_f[tidx];
-  float est[NQ];
-  double rr[NQ], pp[NQ];
-  float emin = INFINITY;
-#pragma unroll
-  for (int q = 0; q < NQ; ++q) {
-    const int i = lane + 32 * q;
-    est[q] = INFINITY;
-    rr[q] = 1.0;
-    pp[q] = -1.0;
-    double v[5];
-    bool have = true;
+  // state at point slot i, converted to V (float for the screen, double
+  // for the exact value); false when the slot holds no point
+  auto load = [&](int i, auto* v) -> bool {
+    using V = std::remove_pointer_t<decltype(v)>;
     if (i < NU) {
 #pragma unroll
       for (int k = 0; k < 5; ++k)
-        v[k] = uin ? double(uin[(e * 5 + k) * NU + i]) : double(X[(e * 5 + k) * NU + i]);
-    } else if (i < NU + NF) {
+        v[k] = uin ? V(uin[(e * 5 + k) * NU + i]) : V(X[(e * 5 + k) * NU + i]);
+      return true;
+    }
+    if (i < NU + NF) {
       const int f = i - NU;
 #pragma unroll
-      for (int k = 0; k < 5; ++k) v[k] = double(uf[(e * 5 + k) * NF + f]);
-    } else if (i < NU + 2 * NF) {
-      const int f = i - NU - NF;
-      int32_t c = partner[e * NF + f];
-      if (c >= 0) {
-        int t2, f2;
-        long long e2;
-        decode_fp(c, tt, &t2, &e2, &f2);
+      for (int k = 0; k < 5; ++k) v[k] = V(uf[(e * 5 + k) * NF + f]);
+      return true;
+    }
+    if (i < NU + 2 * NF) {
+      const int32_t c = partner[e * NF + (i - NU - NF)];
+      if (c < 0) return false;
+      int t2, f2;
+      long long e2;
+      decode_fp(c, tt, &t2, &e2, &f2);
 #pragma unroll
-        for (int k = 0; k < 5; ++k) v[k] = double(uf_all[fp_index(tt, t2, e2, f2, 5, k)]);
-      } else {
-        have = false;
-      }
-    } else {
-      have = false;
+      for (int k = 0; k < 5; ++k) v[k] = V(uf_all[fp_index(tt, t2, e2, f2, 5, k)]);
+      return true;
     }
-    if (!have) continue;
-    double p = (gamma - 1.0) * (v[4] - 0.5 * (v[1] * v[1] + v[2] * v[2] + v[3] * v[3]) / v[0]);
-    rr[q] = v[0];
-    pp[q] = p;
-    if (v[0] > 0.0 && p > 0.0) {
-      est[q] = float(p) * __powf(float(v[0]), -float(gamma));
-      emin = fminf(emin, est[q]);
+    return false;
+  };
+  const float gf = float(gamma);
+  float slo[NQ];
+  uint32_t cand = 0;  // bit q: slot q needs the FP64 value
+  float shi_min = INFINITY;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    slo[q] = INFINITY;
+    float v[5];
+    if (!load(lane + 32 * q, v)) continue;
+    const PtScreen sc = screen_point(v[0], v[1], v[2], v[3], v[4], gf);
+    if (!sc.pos || sc.phi <= 0.f) {
+      // p < 0 for sure: not admissible.  rho <= 0 in FP32: FP64 decides
+      // (an FP64 density can round to zero in FP32)
+      if (!sc.pos) cand |= 1u << q;
+      continue;
     }
+    if (sc.plo <= 0.f) {  // admissibility undecided
+      cand |= 1u << q;
+      continue;
+    }
+    slo[q] = sc.slo;
+    shi_min = fminf(shi_min, sc.shi);
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) emin = fminf(emin, __shfl_xor_sync(0xffffffffu, emin, o));
+  for (int o = 16; o > 0; o >>= 1)
+    shi_min = fminf(shi_min, __shfl_xor_sync(0xffffffffu, shi_min, o));
   double m = INFINITY;
-  const float cut = emin * (1.0f + 1e-4f);
 #pragma unroll
-  for (int q = 0; q < NQ; ++q)
-    if (est[q] <= cut && rr[q] > 0.0 && pp[q] > 0.0)
-      m = fmin(m, pp[q] * pow(rr[q], -gamma));
+  for (int q = 0; q < NQ; ++q) {
+    if (!((cand >> q) & 1u) && !(slo[q] <= shi_min)) continue;
+    double v[5];
+    if (!load(lane + 32 * q, v)) continue;
+    const double p = pressure64(v, gamma);
+    if (v[0] > 0.0 && p > 0.0) m = fmin(m, p * pow(v[0], -gamma));
+  }
   m = warp_min(m);
   if (lane == 0) smin[e] = isfinite(m) ? m : 0.0;
 }
@@ -176,6 +230,68 @@ __device__ __forceinline__ double block_min(double v, double* red) {
   double r = INFINITY;
   for (int i = 0; i < kFilterThreads / 32; ++i) r = fmin(r, red[i]);
   return r;
+}
+
+// Order-preserving integer key of a double (signed compare of keys = fmin
+// order, positive NaN last), so that minima of doubles reduce on the
+// integer pipes instead of the (slow) FP64 pipe.
+__device__ __forceinline__ long long dkey(double x) {
+  const long long k = __double_as_longlong(x);
+  return k ^ ((k >> 63) & 0x7fffffffffffffffLL);
+}
+
+__device__ __forceinline__ double dunkey(long long k) {
+  return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
+}
+
+// exact minima of three doubles over the block (one pair of barriers)
+__device__ __forceinline__ void block_min3_key(double& a, double& b, double& c,
+                                               long long* red) {
+  long long ka = dkey(a), kb = dkey(b), kc = dkey(c);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ka = min(ka, __shfl_xor_sync(0xffffffffu, ka, o));
+    kb = min(kb, __shfl_xor_sync(0xffffffffu, kb, o));
+    kc = min(kc, __shfl_xor_sync(0xffffffffu, kc, o));
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) {
+    red[3 * w] = ka;
+    red[3 * w + 1] = kb;
+    red[3 * w + 2] = kc;
+  }
+  __syncthreads();
+  ka = kb = kc = 0x7fffffffffffffffLL;
+  for (int i = 0; i < kFilterThreads / 32; ++i) {
+    ka = min(ka, red[3 * i]);
+    kb = min(kb, red[3 * i + 1]);
+    kc = min(kc, red[3 * i + 2]);
+  }
+  a = dunkey(ka);
+  b = dunkey(kb);
+  c = dunkey(kc);
+}
+
+// minima of two floats over the block (one pair of barriers)
+__device__ __forceinline__ void block_min2f(float& a, float& b, float* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a = fminf(a, __shfl_xor_sync(0xffffffffu, a, o));
+    b = fminf(b, __shfl_xor_sync(0xffffffffu, b, o));
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) {
+    red[2 * w] = a;
+    red[2 * w + 1] = b;
+  }
+  __syncthreads();
+  a = b = INFINITY;
+  for (int i = 0; i < kFilterThreads / 32; ++i) {
+    a = fminf(a, red[2 * i]);
+    b = fminf(b, red[2 * i + 1]);
+  }
 }
 
 __device__ __forceinline__ double block_sum(double v, double* red) {
@@ -225,11 +341,14 @@ __global__ void __launch_bounds__(kFilterThreads)
   __shared__ T uh[5][NM];       // modal coefficients
   __shared__ T sg[NM];          // filtered weights sigma_k
   __shared__ double red[kFilterThreads / 32];
+  __shared__ long long redk[3 * (kFilterThreads / 32)];
+  __shared__ float redf[2 * (kFilterThreads / 32)];
   __shared__ double s_z;        // requested strength
   const long long e = blockIdx.x;
   const int tid = threadIdx.x;
   if (e >= ne) return;
   const double g = fa.gamma;
+  const float gf = float(g);
   // load the state into registers of a point-parallel layout, then modes
   __shared__ T us[5][NU];
   for (int z = tid; z < NU; z += kFilterThreads)
@@ -247,7 +366,81 @@ __global__ void __launch_bounds__(kFilterThreads)
 #pragma unroll
     for (int k = 0; k < 5; ++k) uh[k][m] = acc[k];
   }
-  // element means of density and pressure
+  const double smin = fa.smin[e];
+  const double sb = smin * (1.0 - fa.tau);
+  // Exact minima of rho, p and s = p rho^-g (-inf where rho <= 0) of the
+  // filtered polynomial at strength z over the solution and flux points
+  // (all threads).  Every point is screened in FP32 (screen_point); the FP64
+  // p and s are computed only for the points whose lower bound reaches the
+  // block's smallest upper bound, so the minima equal those of an all-FP64
+  // pass over the same values.
+  constexpr int NPT = (NP + kFilterThreads - 1) / kFilterThreads;
+  struct Mins {
+    double r, p, s;
+  };
+  auto minima = [&](double z) -> Mins {
+    for (int m = tid; m < NM; m += kFilterThreads) {
+      double d = double(op.deg[m]);
+      sg[m] = sizeof(T) == 4 ? T(__expf(-float(z * d * d))) : T(exp(-z * d * d));
+    }
+    __syncthreads();
+    T v[NPT][5];
+    PtScreen sc[NPT];
+    T rmin_t = T(INFINITY);
+    float phi = INFINITY, shi = INFINITY;
+#pragma unroll
+    for (int q = 0; q < NPT; ++q) {
+      const int i = tid + q * kFilterThreads;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) v[q][k] = T(0);
+      sc[q].pos = false;
+      sc[q].plo = sc[q].slo = INFINITY;  // no point: never a candidate
+      if (i >= NP) continue;
+      for (int m = 0; m < NM; ++m) {
+        T w = op.VT[m * NP + i] * sg[m];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) v[q][k] += w * uh[k][m];
+      }
+      rmin_t = sizeof(T) == 4 ? T(fminf(float(rmin_t), float(v[q][0])))
+                              : T(fmin(double(rmin_t), double(v[q][0])));
+      sc[q] = screen_point(float(v[q][0]), float(v[q][1]), float(v[q][2]),
+                           float(v[q][3]), float(v[q][4]), gf);
+      if (sc[q].pos) {
+        phi = fminf(phi, sc[q].phi);
+        shi = fminf(shi, sc[q].shi);
+      }
+    }
+    block_min2f(phi, shi, redf);
+    double rmin = double(rmin_t), mp = INFINITY, ms = INFINITY;
+#pragma unroll
+    for (int q = 0; q < NPT; ++q) {
+      if (tid + q * kFilterThreads >= NP) continue;
+      const bool cp = !sc[q].pos || sc[q].plo <= phi;
+      const bool cs = smin > 0.0 && (!sc[q].pos || sc[q].slo <= shi);
+      if (!cp && !cs) continue;
+      double w[5];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) w[k] = double(v[q][k]);
+      const double p = pressure64(w, g);
+      if (cp) mp = fmin(mp, p);
+      if (cs) ms = fmin(ms, w[0] > 0.0 ? p * pow(w[0], -g) : -INFINITY);
+    }
+    block_min3_key(rmin, mp, ms, redk);
+    return Mins{rmin, mp, ms};
+  };
+  const Mins m0 = minima(0.0);
+  // unfiltered state admissible (the sign of the margin below, which the
+  // positive means do not change): nothing to do (uniform across the block)
+  const double gm0 = fmin(m0.r - kEpsPos,
+                          fmin(m0.p - kEpsPos, smin > 0.0 ? m0.s - sb : INFINITY));
+  if (!isnan(gm0) && gm0 >= 0.0) {
+    if (tid == 0 && fa.zeta_last) {
+      fa.zeta_last[e] = 0.f;
+      fa.evals_last[e] = 1;
+    }
+    return;
+  }
+  // element means of density and pressure (normalise the margin)
   double wr = 0.0, wp = 0.0, ws = 0.0;
   for (int z = tid; z < NU; z += kFilterThreads) {
     double p;
@@ -261,195 +454,172 @@ __global__ void __launch_bounds__(kFilterThreads)
   const double wsum = block_sum(ws, red);
   const double rmean = fmax(block_sum(wr, red) / wsum, kEpsPos);
   const double pmean = fmax(block_sum(wp, red) / wsum, kEpsPos);
-  const double smin = fa.smin[e];
-  // margin of the filtered polynomial at strength z (all threads).  The
-  // entropy margin needs s = p rho^-gamma: every point gets a fast FP32
-  // estimate, and the exact FP64 value is computed only for points whose
-  // estimate lies within 1e-4 of the element's smallest estimate (the FP32
-  // estimate is accurate to ~1e-6), so the FP64 minimum is exact.
-  constexpr int NPT = (NP + kFilterThreads - 1) / kFilterThreads;
-  const double sb = smin * (1.0 - fa.tau);
-  auto margin = [&](double z, float* feat) -> double {
-    for (int m = tid; m < NM; m += kFilterThreads) {
-      double d = double(op.deg[m]);
-      sg[m] = sizeof(T) == 4 ? T(__expf(-float(z * d * d))) : T(exp(-z * d * d));
-    }
-    __syncthreads();
-    double mr = INFINITY, mp = INFINITY, mse = INFINITY;
-    double rr[NPT], pp[NPT], se[NPT];
-#pragma unroll
-    for (int q = 0; q < NPT; ++q) {
-      const int i = tid + q * kFilterThreads;
-      rr[q] = 1.0;
-      pp[q] = 1.0;
-      se[q] = INFINITY;
-      if (i >= NP) continue;
-      T v[5] = {0, 0, 0, 0, 0};
-      for (int m = 0; m < NM; ++m) {
-        T w = op.VT[m * NP + i] * sg[m];
-#pragma unroll
-        for (int k = 0; k < 5; ++k) v[k] += w * uh[k][m];
-      }
-      double p;
-      entropy_of(double(v[0]), double(v[1]), double(v[2]), double(v[3]),
-                 double(v[4]), g, &p);
-      const double r = double(v[0]);
-      rr[q] = r;
-      pp[q] = p;
-      mr = fmin(mr, r);
-      mp = fmin(mp, p);
-      // s estimate (negative where p < 0), -inf where rho <= 0
-      se[q] = r > 0.0 ? double(float(p) * __powf(float(r), -float(g))) : -INFINITY;
-      mse = fmin(mse, se[q]);
-    }
-    mr = block_min(mr, red);
-    mp = block_min(mp, red);
-    mse = block_min(mse, red);
-    double ms = INFINITY;
-    if (smin > 0.0) {
-      const double cut = mse + 1e-4 * smin;
-#pragma unroll
-      for (int q = 0; q < NPT; ++q) {
-        if (se[q] > cut) continue;
-        ms = fmin(ms, rr[q] > 0.0 ? pp[q] * pow(rr[q], -g) : -INFINITY);
-      }
-      ms = block_min(ms, red);
-    } else {
-      ms = block_min(ms, red);
-    }
-    double gr = (mr - kEpsPos) / rmean, gp = (mp - kEpsPos) / pmean;
-    double gs = smin > 0.0 ? (ms - sb) / smin : INFINITY;
+  // margin g(z) = min((rho-eps)/rho_mean, (p-eps)/p_mean, (s-sb)/s_min)
+  auto gval = [&](const Mins& q) -> double {
+    const double gr = (q.r - kEpsPos) / rmean, gp = (q.p - kEpsPos) / pmean;
+    const double gs = smin > 0.0 ? (q.s - sb) / smin : INFINITY;
     double gm = fmin(gr, fmin(gp, gs));
     if (isnan(gm)) gm = -INFINITY;
-    if (feat) {  // predictor inputs from the unfiltered state (z = 0)
-      double eh = 0.0, et = 0.0;
-      for (int m = tid; m < NM; m += kFilterThreads) {
-        double d = double(op.deg[m]), c = double(uh[0][m]);
-        if (d > 1.0) eh += c * c;
-        if (d > 0.0) et += c * c;
-      }
-      eh = block_sum(eh, red);
-      et = block_sum(et, red);
-      feat[0] = float(fmin(fmax(log10((eh + 1e-30) / (et + 1e-30)), -30.0), 30.0));
-      feat[1] = float(fmin(fmax(mr / rmean, -30.0), 30.0));
-      feat[2] = float(fmin(fmax(mp / pmean, -30.0), 30.0));
-      // log10 of the entropy-bound violation (floor 1e-14)
-      double f3 = 1.0;
-      if (smin > 0.0 && ms > -INFINITY && mr > 0.0 && mp > 0.0)
-        f3 = fmax((smin - ms) / smin, 1e-14);
-      feat[3] = float(log10(f3));
-    }
     return gm;
   };
-  float feat[4];
-  double g0 = margin(0.0, feat);
-  if (g0 >= 0.0) {  // uniform across the block
-    if (tid == 0 && fa.zeta_last) {
-      fa.zeta_last[e] = 0.f;
-      fa.evals_last[e] = 1;
+  auto margin = [&](double z) -> double { return gval(minima(z)); };
+  // predictor inputs from the unfiltered state (z = 0)
+  float feat[4] = {0.f, 0.f, 0.f, 0.f};
+  if (fa.mlp || fa.samples) {
+    double eh = 0.0, et = 0.0;
+    for (int m = tid; m < NM; m += kFilterThreads) {
+      double d = double(op.deg[m]), c = double(uh[0][m]);
+      if (d > 1.0) eh += c * c;
+      if (d > 0.0) et += c * c;
     }
-    return;
+    eh = block_sum(eh, red);
+    et = block_sum(et, red);
+    feat[0] = float(fmin(fmax(log10((eh + 1e-30) / (et + 1e-30)), -30.0), 30.0));
+    feat[1] = float(fmin(fmax(m0.r / rmean, -30.0), 30.0));
+    feat[2] = float(fmin(fmax(m0.p / pmean, -30.0), 30.0));
+    // log10 of the entropy-bound violation (floor 1e-14)
+    double f3 = 1.0;
+    if (smin > 0.0 && m0.s > -INFINITY && m0.r > 0.0 && m0.p > 0.0)
+      f3 = fmax((smin - m0.s) / smin, 1e-14);
+    feat[3] = float(log10(f3));
   }
-  // ---- root-find: thread 0 drives, every evaluation is a block operation
-  double lo = 0.0, glo = g0, hi = kZetaMax, ghi = 0.0;
-  int evals = 1;
+  const double g0 = gval(m0);
+  // ---- root-find.  Thread 0 runs the bracketing and Illinois logic as a
+  // state machine and publishes the next strength in shared memory; every
+  // evaluation of the margin is a block operation.
+  enum { kPlainHi = 0, kGuess = 1, kDown = 2, kUp = 3, kIllinois = 4, kDone = 5 };
+  __shared__ double s_next;
+  __shared__ int s_go;
+  double lo = 0.0, glo = g0, hi = kZetaMax, ghi = 0.0, result = 0.0, zc = 0.0;
+  int evals = 1, state = kPlainHi, it = 0, side = 0;
   bool fallback = false, use_guess = false;
-  double guess = -1.0;
   if (fa.mlp) {
     float z0 = 0.f;
     if (tid < 32) z0 = mlp_guess(feat, fa.mlp, fa.mlp_norm);
     if (tid == 0) s_z = double(z0);
     __syncthreads();
-    guess = s_z;
-    __syncthreads();
+    const double guess = s_z;
     use_guess = guess > 0.0 && guess < kZetaMax;
-  }
-  bool bracketed = false, done = false;
-  double result = 0.0;
-  if (!use_guess) {
-    ghi = margin(kZetaMax, nullptr);
-    ++evals;
-    if (ghi < 0.0) {
-      done = true;
-      fallback = true;
-      result = kZetaMax;
-    } else {
-      bracketed = true;
+    if (use_guess) {
+      state = kGuess;
+      zc = guess;
     }
-  } else {
-    double gz = margin(guess, nullptr);
+  }
+  if (state == kPlainHi) zc = kZetaMax;
+  // next Illinois point, or kDone when the bracket is tight / evals spent
+  auto illinois_next = [&]() {
+    if (!(hi - lo > kRelTol * hi && evals < kMaxEvals)) {
+      state = kDone;
+      result = hi;
+      return;
+    }
+    double z = (lo * ghi - hi * glo) / (ghi - glo);
+    if (!(lo < z && z < hi)) z = 0.5 * (lo + hi);
+    zc = z;
+  };
+  if (tid == 0) {
+    s_next = zc;
+    s_go = 1;
+  }
+  for (;;) {
+    __syncthreads();
+    if (!s_go) break;
+    const double z = s_next;
+    const Mins mz = minima(z);  // ends with a barrier: s_next / s_go reusable
+    if (tid != 0) continue;
+    const double gz = gval(mz);
     ++evals;
-    if (gz >= 0.0) {
-      hi = guess;
-      ghi = gz;
-      double z = guess / fa.ratio;
-      for (int it = 0; it < 64 && !bracketed && !done; ++it) {
-        gz = margin(z, nullptr);
-        ++evals;
+    switch (state) {
+      case kPlainHi:
+        ghi = gz;
+        if (gz < 0.0) {
+          state = kDone;
+          fallback = true;
+          result = kZetaMax;
+        } else {
+          state = kIllinois;
+          illinois_next();
+        }
+        break;
+      case kGuess:
+        if (gz >= 0.0) {
+          hi = z;
+          ghi = gz;
+          state = kDown;
+          zc = z / fa.ratio;
+        } else {
+          lo = z;
+          glo = gz;
+          state = kUp;
+          zc = fmin(fa.ratio * z, kZetaMax);
+        }
+        it = 0;
+        break;
+      case kDown:  // halve until the margin is negative
         if (gz < 0.0) {
           lo = z;
           glo = gz;
-          bracketed = true;
+          state = kIllinois;
+          illinois_next();
         } else {
           hi = z;
           ghi = gz;
           if (z < 1e-6) {
-            done = true;
+            state = kDone;
             result = hi;
+          } else {
+            zc = 0.5 * z;
+            if (++it >= 64) {
+              state = kDone;
+              fallback = true;
+              result = kZetaMax;
+            }
           }
-          z *= 0.5;
         }
-      }
-    } else {
-      lo = guess;
-      glo = gz;
-      double z = fmin(fa.ratio * guess, kZetaMax);
-      for (int it = 0; it < 64 && !bracketed && !done; ++it) {
-        gz = margin(z, nullptr);
-        ++evals;
+        break;
+      case kUp:  // double until the margin is non-negative
         if (gz >= 0.0) {
           hi = z;
           ghi = gz;
-          bracketed = true;
+          state = kIllinois;
+          illinois_next();
         } else {
           lo = z;
           glo = gz;
           if (z >= kZetaMax) {
-            done = true;
+            state = kDone;
             fallback = true;
             result = kZetaMax;
+          } else {
+            zc = fmin(2.0 * z, kZetaMax);
+            if (++it >= 64) {
+              state = kDone;
+              fallback = true;
+              result = kZetaMax;
+            }
           }
-          z = fmin(2.0 * z, kZetaMax);
         }
-      }
+        break;
+      case kIllinois:
+        if (gz >= 0.0) {
+          hi = z;
+          ghi = gz;
+          if (side == 1) glo *= 0.5;
+          side = 1;
+        } else {
+          lo = z;
+          glo = gz;
+          if (side == -1) ghi *= 0.5;
+          side = -1;
+        }
+        illinois_next();
+        break;
     }
-    if (!bracketed && !done) {  // cannot happen within the caps; be safe
-      done = true;
-      fallback = true;
-      result = kZetaMax;
-    }
+    s_go = state != kDone;
+    s_next = state == kDone ? result : zc;
   }
-  if (!done) {
-    int side = 0;
-    while (hi - lo > kRelTol * hi && evals < kMaxEvals) {
-      double z = (lo * ghi - hi * glo) / (ghi - glo);
-      if (!(lo < z && z < hi)) z = 0.5 * (lo + hi);
-      double gz = margin(z, nullptr);
-      ++evals;
-      if (gz >= 0.0) {
-        hi = z;
-        ghi = gz;
-        if (side == 1) glo *= 0.5;
-        side = 1;
-      } else {
-        lo = z;
-        glo = gz;
-        if (side == -1) ghi *= 0.5;
-        side = -1;
-      }
-    }
-    result = hi;
-  }
+  // every thread: the strength found by thread 0
+  result = s_next;
   // write the filtered state and its flux-point values
   for (int m = tid; m < NM; m += kFilterThreads)
     sg[m] = T(exp(-result * double(op.deg[m]) * double(op.deg[m])));
