@@ -499,14 +499,14 @@ constexpr int hex_epb() {
   return (N * N * N) >= 256 ? 1 : 256 / (N * N * N);
 }
 
-template <typename T, int N>
+template <typename T, typename TR, int N>
 constexpr size_t hex_vol_smem() {
-  return size_t(hex_epb<N>()) * (15 * N * N * N + 30 * N * N) * sizeof(T);
+  return size_t(hex_epb<N>()) * size_t(hex_vol_bytes_per_elem<T, TR, N>());
 }
 
 template <typename T, int N>
 constexpr size_t hex_grad_smem() {
-  return size_t(hex_epb<N>()) * (20 * N * N * N + 30 * N * N) * sizeof(T);
+  return size_t(hex_epb<N>()) * size_t(hex_grad_bytes_per_elem<T, N, sizeof(T) == 4>());
 }
 
 bool use_hex(const fr_mesh* m, const DevType& D) {
@@ -640,10 +640,10 @@ int prepare_kernels(fr_mesh* m) {
       constexpr int E = hex_epb<N>();
       cudaFuncSetAttribute(k_hex_vol<T, TR, N, E, false>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           int(hex_vol_smem<T, N>()));
+                           int(hex_vol_smem<T, TR, N>()));
       cudaFuncSetAttribute(k_hex_vol<T, TR, N, E, true>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           int(hex_vol_smem<T, N>()));
+                           int(hex_vol_smem<T, TR, N>()));
       cudaFuncSetAttribute(k_hex_grad<T, TR, N, E, sizeof(T) == 4>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                            int(hex_grad_smem<T, N>()));
@@ -823,7 +823,7 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
       hex_dispatch(m->order, [&](auto n) {
         constexpr int N = decltype(n)::value;
         constexpr int E = hex_epb<N>();
-        const size_t sm = hex_vol_smem<T, N>();
+        const size_t sm = hex_vol_smem<T, TR, N>();
         const T* uin = from_x ? nullptr : (const T*)D.Y;
         if (sizeof(T) == 4 && m->active == FR_VARIANT_SUMFACT_VERTEX) {
           const size_t smv = hexv_vol_smem<T, N>();

@@ -195,109 +195,6 @@ __device__ __forceinline__ void tc_epilogue(uint32_t tm, uint64_t* mbar,
   if (threadIdx.x == 0) mbar_inval(mbar);
 }
 
-// RK register values the stage update of one point reads (5 variables);
-// loaded ahead of the update so that a thread's loads for several elements
-// are in flight together.
-template <typename TR>
-__device__ __forceinline__ void tc_stage_load(const HexStage<float, TR>& a,
-                                              long long i0, long long vstr,
-                                              TR x[5], TR ac[5]) {
-  const int st = a.stage;
-  const bool nx = a.mode == 2 || (a.mode == 1 && st < 3);
-  const bool na = a.mode == 1 && st > 0;
-#pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    x[k] = nx ? a.X[i0 + k * vstr] : TR(0);
-    ac[k] = na ? a.A[i0 + k * vstr] : TR(0);
-  }
-}
-
-// The stage update of hex_stage_update (same arithmetic) from preloaded
-// register values x (X) and ac (A); s receives the next stage value.
-template <typename TR>
-__device__ __forceinline__ void tc_stage_apply(const HexStage<float, TR>& a,
-                                               long long i0, long long vstr,
-                                               const float R[5], const TR x[5],
-                                               const TR ac[5], float s[5]) {
-  bool bad = false;
-#pragma unroll
-  for (int k = 0; k < 5; ++k) bad |= !isfinite(R[k]);
-  if (bad) atomicOr(a.flag, 1);
-  if (a.mode == 0) {
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-      a.out[i0 + k * vstr] = R[k];
-      s[k] = 0.f;
-    }
-    return;
-  }
-  const TR dt = TR(*a.dt);
-  const int st = a.stage;
-  if (a.mode == 1) {
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-      const long long i = i0 + k * vstr;
-      const TR r = TR(R[k]);
-      if (st == 0) {
-        a.A[i] = x[k] + dt * TR(1.0 / 6.0) * r;
-        const float y = float(x[k] + dt * TR(0.5) * r);
-        a.Y[i] = y;
-        s[k] = y;
-      } else if (st < 3) {
-        a.A[i] = ac[k] + dt * TR(1.0 / 3.0) * r;
-        const float y = float(x[k] + (st == 1 ? dt * TR(0.5) : dt) * r);
-        a.Y[i] = y;
-        s[k] = y;
-      } else {
-        const TR xx = ac[k] + dt * TR(1.0 / 6.0) * r;
-        a.X[i] = xx;
-        s[k] = float(xx);
-      }
-    }
-    return;
-  }
-  const TR b = TR(c_rk45_b[st]);
-  const TR am = st < 4 ? TR(c_rk45_a[st]) - b : TR(0);
-#pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    const long long i = i0 + k * vstr;
-    const TR r = TR(R[k]);
-    const TR xx = x[k] + b * dt * r;
-    a.X[i] = xx;
-    if (st < 4) {
-      const float y = float(xx + am * dt * r);
-      a.Y[i] = y;
-      s[k] = y;
-    } else {
-      s[k] = float(xx);
-    }
-  }
-}
-
-// Viscous normal flux q of write_visc_q from preloaded inputs: u (trace),
-// nv = S^T n~, b = boundary-condition index or -1.
-__device__ __forceinline__ void tc_visc_q(const BCTab<float>& bc,
-                                          const Phys<float>& ph, const float u[5],
-                                          const float G[3][5], const float nv[3],
-                                          int b, float q[5]) {
-#pragma unroll
-  for (int k = 0; k < 5; ++k) q[k] = 0.f;
-  viscous_normal_acc(u, G, nv, ph, 1.f, q);
-  if (b >= 0) {
-    float ur[5], q2[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-    if (bc.kind[b] == 0) {
-#pragma unroll
-      for (int k = 0; k < 5; ++k) ur[k] = bc.state[b][k];
-    } else {
-#pragma unroll
-      for (int k = 0; k < 5; ++k) ur[k] = u[k];
-    }
-    viscous_normal_acc(ur, G, nv, ph, 1.f, q2);
-#pragma unroll
-    for (int k = 0; k < 5; ++k) q[k] = 0.5f * (q[k] + q2[k]);
-  }
-}
-
 // Transformed flux f~_d = S_d . F (Euler, plus the viscous part for NS) at
 // one solution point from preloaded state, gradient and metric.
 template <bool NS>
@@ -481,7 +378,7 @@ __global__ void __launch_bounds__(kTcThreads, MINB)
         live[j] = ru >= 0 && ru < NU && e < ne;
         rj[j] = live[j] ? rcpdjac[e * NU + ru] : 0.f;
         if (live[j]) {
-          tc_stage_load(sa, e * 5 * NU + ru, NU, xr[j], ar[j]);
+          hex_stage_load(sa, e * 5 * NU + ru, NU, xr[j], ar[j]);
         } else {
 #pragma unroll
           for (int k = 0; k < 5; ++k) xr[j][k] = ar[j][k] = TR(0);
@@ -499,9 +396,10 @@ __global__ void __launch_bounds__(kTcThreads, MINB)
           float s[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
           if (live[j]) {
             float R[5];
+            const float u0[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int k = 0; k < 5; ++k) R[k] = -dv[k][j] * rj[j];
-            tc_stage_apply(sa, e * 5 * NU + ru, NU, R, xr[j], ar[j], s);
+            hex_stage_apply(sa, e * 5 * NU + ru, NU, u0, R, xr[j], ar[j], s);
           }
           if (next) {
 #pragma unroll
@@ -757,7 +655,7 @@ __global__ void __launch_bounds__(kTcThreads, MINB)
         for (int c = 0; c < 3; ++c)
 #pragma unroll
           for (int k = 0; k < 5; ++k) G[c][k] = gf[c][k][j];
-        tc_visc_q(bc, ph, ut[j], G, nv[j], fb[j], q);
+        visc_q_pre(bc, ph, ut[j], G, nv[j], fb[j], q);
 #pragma unroll
         for (int k = 0; k < 5; ++k) va.q[(e * 5 + k) * NF + rf] = q[k];
       }

@@ -54,11 +54,23 @@ __device__ __forceinline__ int line_pt(int face, int i, int j, int m) {
   return i + N * j + N * N * m;
 }
 
+// Which RK registers the stage update reads: X (nx) and A (na).
 template <typename T, typename TR>
-__device__ __forceinline__ void hex_stage_update(const HexStage<T, TR>& a,
-                                                 long long i0, long long vstr,
-                                                 const T u[5], const T R[5],
-                                                 T s[5]) {
+__device__ __forceinline__ void hex_stage_needs(const HexStage<T, TR>& a, bool* nx,
+                                                bool* na) {
+  *nx = a.mode == 2 || (a.mode == 1 && a.stage < 3);
+  *na = a.mode == 1 && a.stage > 0;
+}
+
+// RK epilogue for one point from the register values x (X) and ac (A) read
+// beforehand: R[5] -> registers; s receives the next stage value (u for a
+// bare right-hand side, mode 0).
+template <typename T, typename TR>
+__device__ __forceinline__ void hex_stage_apply(const HexStage<T, TR>& a,
+                                                long long i0, long long vstr,
+                                                const T u[5], const T R[5],
+                                                const TR x[5], const TR ac[5],
+                                                T s[5]) {
   bool bad = false;
 #pragma unroll
   for (int k = 0; k < 5; ++k) bad |= !isfinite(R[k]);
@@ -76,24 +88,22 @@ __device__ __forceinline__ void hex_stage_update(const HexStage<T, TR>& a,
   if (a.mode == 1) {
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
-      long long i = i0 + k * vstr;
-      TR r = TR(R[k]);
+      const long long i = i0 + k * vstr;
+      const TR r = TR(R[k]);
       if (st == 0) {
-        TR x = a.X[i];
-        a.A[i] = x + dt * TR(1.0 / 6.0) * r;
-        T y = T(x + dt * TR(0.5) * r);
+        a.A[i] = x[k] + dt * TR(1.0 / 6.0) * r;
+        const T y = T(x[k] + dt * TR(0.5) * r);
         a.Y[i] = y;
         s[k] = y;
       } else if (st < 3) {
-        TR x = a.X[i];
-        a.A[i] = a.A[i] + dt * TR(1.0 / 3.0) * r;
-        T y = T(x + (st == 1 ? dt * TR(0.5) : dt) * r);
+        a.A[i] = ac[k] + dt * TR(1.0 / 3.0) * r;
+        const T y = T(x[k] + (st == 1 ? dt * TR(0.5) : dt) * r);
         a.Y[i] = y;
         s[k] = y;
       } else {
-        TR x = a.A[i] + dt * TR(1.0 / 6.0) * r;
-        a.X[i] = x;
-        s[k] = T(x);
+        const TR xx = ac[k] + dt * TR(1.0 / 6.0) * r;
+        a.X[i] = xx;
+        s[k] = T(xx);
       }
     }
     return;
@@ -102,18 +112,42 @@ __device__ __forceinline__ void hex_stage_update(const HexStage<T, TR>& a,
   const TR am = st < 4 ? TR(c_rk45_a[st]) - b : TR(0);
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
-    long long i = i0 + k * vstr;
-    TR r = TR(R[k]);
-    TR x = a.X[i] + b * dt * r;
-    a.X[i] = x;
+    const long long i = i0 + k * vstr;
+    const TR r = TR(R[k]);
+    const TR xx = x[k] + b * dt * r;
+    a.X[i] = xx;
     if (st < 4) {
-      T y = T(x + am * dt * r);
+      const T y = T(xx + am * dt * r);
       a.Y[i] = y;
       s[k] = y;
     } else {
-      s[k] = T(x);
+      s[k] = T(xx);
     }
   }
+}
+
+// Register values the stage update of one point reads, from global memory.
+template <typename T, typename TR>
+__device__ __forceinline__ void hex_stage_load(const HexStage<T, TR>& a,
+                                               long long i0, long long vstr,
+                                               TR x[5], TR ac[5]) {
+  bool nx, na;
+  hex_stage_needs(a, &nx, &na);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    x[k] = nx ? a.X[i0 + k * vstr] : TR(0);
+    ac[k] = na ? a.A[i0 + k * vstr] : TR(0);
+  }
+}
+
+template <typename T, typename TR>
+__device__ __forceinline__ void hex_stage_update(const HexStage<T, TR>& a,
+                                                 long long i0, long long vstr,
+                                                 const T u[5], const T R[5],
+                                                 T s[5]) {
+  TR x[5], ac[5];
+  hex_stage_load(a, i0, vstr, x, ac);
+  hex_stage_apply(a, i0, vstr, u, R, x, ac, s);
 }
 
 // interpolate smem field src[v][pt] to face point fp (5 variables)
@@ -140,6 +174,14 @@ __device__ __forceinline__ void face_interp(const T* src, int fp,
 // at solution points, and its value at the flux points.
 // QV: write the viscous normal flux q (5 per flux point, for the q-based
 // interface kernel) instead of the 15 gradient components at flux points.
+// Shared memory per element of k_hex_grad: u [5][NU], du [5][NF], physical
+// gradient [15][NU], and for the q form the traces [5][NF] and S^T n~
+// [3][NF] at the flux points (type T, 16-byte padded).
+template <typename T, int N, bool QV>
+__host__ __device__ constexpr int hex_grad_bytes_per_elem() {
+  return ((20 * N * N * N + (QV ? 78 : 30) * N * N) * int(sizeof(T)) + 15) / 16 * 16;
+}
+
 template <typename T, typename TR, int N, int EPB, bool QV>
 __global__ void __launch_bounds__(EPB* N* N* N)
     k_hex_grad(long long ne, const T* __restrict__ uin, const TR* __restrict__ X,
@@ -148,22 +190,35 @@ __global__ void __launch_bounds__(EPB* N* N* N)
                T* __restrict__ grad, ViscArgs<T> va, BCTab<T> bc,
                Phys<T> ph) {
   constexpr int NU = N * N * N, NF = 6 * N * N;
-  extern __shared__ unsigned char smem_raw[];
-  T* sm = reinterpret_cast<T*>(smem_raw);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int le = threadIdx.x / NU, z = threadIdx.x - le * NU;
   const long long e = (long long)blockIdx.x * EPB + le;
-  T* us = sm + le * (5 * NU + 5 * NF + 15 * NU);
+  T* us = reinterpret_cast<T*>(smem_raw + le * hex_grad_bytes_per_elem<T, N, QV>());
   T* ds = us + 5 * NU;
   T* gs = ds + 5 * NF;
+  T* ufs = gs + 15 * NU;  // [5][NF] traces (q form)
+  T* nvs = ufs + 5 * NF;  // [3][NF] S^T n~ (q form)
   const int a = z % N, b = (z / N) % N, c = z / (N * N);
+  // the element's u, du (and the q form's inputs) arrive by cp.async while
+  // the metric terms load into registers
+  T S[3][3], rj = T(0);
   if (e < ne) {
+    if (uin) {
+      async_copy(us, uin + e * 5 * NU, 5 * NU * int(sizeof(T)), z, NU);
+    } else {
 #pragma unroll
-    for (int k = 0; k < 5; ++k)
-      us[k * NU + z] = uin ? uin[(e * 5 + k) * NU + z] : T(X[(e * 5 + k) * NU + z]);
-    for (int f = z; f < NF; f += NU)
+      for (int k = 0; k < 5; ++k) us[k * NU + z] = T(X[(e * 5 + k) * NU + z]);
+    }
+    async_copy(ds, du + e * 5 * NF, 5 * NF * int(sizeof(T)), z, NU);
+    if (QV) {
+      async_copy(ufs, va.uf + e * 5 * NF, 5 * NF * int(sizeof(T)), z, NU);
+      async_copy(nvs, va.fnv + e * 3 * NF, 3 * NF * int(sizeof(T)), z, NU);
+    }
 #pragma unroll
-      for (int k = 0; k < 5; ++k) ds[k * NF + f] = du[(e * 5 + k) * NF + f];
+    for (int r = 0; r < 9; ++r) S[r / 3][r % 3] = smat[(e * 9 + r) * NU + z];
+    rj = rcpdjac[e * NU + z];
   }
+  cp_async_wait_all();
   __syncthreads();
   if (e < ne) {
     T gref[3][5];
@@ -197,10 +252,6 @@ __global__ void __launch_bounds__(EPB* N* N* N)
       gref[1][k] = gy;
       gref[2][k] = gz;
     }
-    T S[3][3];
-#pragma unroll
-    for (int r = 0; r < 9; ++r) S[r / 3][r % 3] = smat[(e * 9 + r) * NU + z];
-    const T rj = rcpdjac[e * NU + z];
 #pragma unroll
     for (int j = 0; j < 3; ++j)
 #pragma unroll
@@ -217,7 +268,18 @@ __global__ void __launch_bounds__(EPB* N* N* N)
     T g[15];
     face_interp<T, N, 15>(gs, f, op, g);
     if (QV) {
-      write_visc_q(va, bc, ph, e, f, NF, g);
+      T u[5], G[3][5], nv[3], q[5];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) u[k] = ufs[k * NF + f];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        nv[j] = nvs[j * NF + f];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) G[j][k] = g[j * 5 + k];
+      }
+      visc_q_pre(bc, ph, u, G, nv, int(va.fbc[e * NF + f]), q);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) va.q[(e * 5 + k) * NF + f] = q[k];
     } else {
 #pragma unroll
       for (int k = 0; k < 15; ++k) va.q[(e * 15 + k) * NF + f] = g[k];
@@ -229,6 +291,29 @@ __global__ void __launch_bounds__(EPB* N* N* N)
 // Volume kernel on hexahedra: f~ = S F, divergence along the three line
 // families, DG correction with the jump F^C - n~.f~ computed once per flux
 // point, R = -div / J, RK epilogue and the next stage's u_f.
+// Shared memory per element: f~ [3][5][NU] and F^C / jump [5][NF] (type T),
+// then, for FP32 registers, the RK registers X, A [5][NU].  The element's
+// F^C block (and those register blocks) are copied asynchronously
+// (cp.async) at entry, so their loads overlap the flux arithmetic instead
+// of following it.  FP64 registers are read directly: staging them would
+// double the shared memory per element and cost more occupancy than the
+// overlap gains.
+template <typename T, int N>
+__host__ __device__ constexpr int hex_vol_tbytes() {  // T part, 16-byte padded
+  return ((15 * N * N * N + 30 * N * N) * int(sizeof(T)) + 15) / 16 * 16;
+}
+
+template <typename TR>
+__host__ __device__ constexpr bool hex_vol_stage_regs() {
+  return sizeof(TR) == 4;
+}
+
+template <typename T, typename TR, int N>
+__host__ __device__ constexpr int hex_vol_bytes_per_elem() {
+  return hex_vol_tbytes<T, N>() +
+         (hex_vol_stage_regs<TR>() ? (10 * N * N * N * int(sizeof(TR)) + 15) / 16 * 16 : 0);
+}
+
 template <typename T, typename TR, int N, int EPB, bool NS>
 __global__ void __launch_bounds__(EPB* N* N* N)
     k_hex_vol(long long ne, const T* __restrict__ uin, const T* __restrict__ grad,
@@ -236,13 +321,23 @@ __global__ void __launch_bounds__(EPB* N* N* N)
               const T* __restrict__ rcpdjac, HexOps<T> op, Phys<T> ph,
               HexStage<T, TR> sa) {
   constexpr int NU = N * N * N, NF = 6 * N * N, N2 = N * N;
-  extern __shared__ unsigned char smem_raw[];
-  T* sm = reinterpret_cast<T*>(smem_raw);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int le = threadIdx.x / NU, z = threadIdx.x - le * NU;
   const long long e = (long long)blockIdx.x * EPB + le;
-  T* ft = sm + le * (15 * NU + 5 * NF);  // [3][5][NU]
-  T* jm = ft + 15 * NU;                  // [5][NF]
+  unsigned char* eb = smem_raw + le * hex_vol_bytes_per_elem<T, TR, N>();
+  T* ft = reinterpret_cast<T*>(eb);       // [3][5][NU]
+  T* jm = ft + 15 * NU;                   // [5][NF]: F^C, then the jump
+  TR* xs = reinterpret_cast<TR*>(eb + hex_vol_tbytes<T, N>());  // [5][NU]
+  TR* as = xs + 5 * NU;                         // [5][NU]
   const int a = z % N, b = (z / N) % N, c = z / N2;
+  bool nx, na;
+  hex_stage_needs(sa, &nx, &na);
+  constexpr bool SR = hex_vol_stage_regs<TR>();
+  if (e < ne) {
+    async_copy(jm, fc + e * 5 * NF, 5 * NF * int(sizeof(T)), z, NU);
+    if (SR && nx) async_copy(xs, sa.X + e * 5 * NU, 5 * NU * int(sizeof(TR)), z, NU);
+    if (SR && na) async_copy(as, sa.A + e * 5 * NU, 5 * NU * int(sizeof(TR)), z, NU);
+  }
   T uz[5];
   if (e < ne) {
 #pragma unroll
@@ -268,6 +363,7 @@ __global__ void __launch_bounds__(EPB* N* N* N)
         ft[(d * 5 + k) * NU + z] =
             S[d][0] * F[0][k] + S[d][1] * F[1][k] + S[d][2] * F[2][k];
   }
+  cp_async_wait_all();
   __syncthreads();
   if (e < ne) {
     // jump at every flux point: F^C - n~ . M0 f~ (only the normal direction)
@@ -278,7 +374,7 @@ __global__ void __launch_bounds__(EPB* N* N* N)
       face_interp<T, N, 5>(ft + dir * 5 * NU, f, op, fn);
       T sgn = (face & 1) ? T(1) : T(-1);
 #pragma unroll
-      for (int k = 0; k < 5; ++k) jm[k * NF + f] = fc[(e * 5 + k) * NF + f] - sgn * fn[k];
+      for (int k = 0; k < 5; ++k) jm[k * NF + f] = jm[k * NF + f] - sgn * fn[k];
     }
   }
   __syncthreads();
@@ -313,7 +409,17 @@ __global__ void __launch_bounds__(EPB* N* N* N)
       dv += glc * jk[fp_of<N>(4, a, b)] + grc * jk[fp_of<N>(5, a, b)];
       R[k] = -dv * rj;
     }
-    hex_stage_update(sa, e * 5 * NU + z, NU, uz, R, s);
+    TR xr[5], ar[5];
+    if (SR) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        xr[k] = nx ? xs[k * NU + z] : TR(0);
+        ar[k] = na ? as[k * NU + z] : TR(0);
+      }
+    } else {
+      hex_stage_load(sa, e * 5 * NU + z, NU, xr, ar);
+    }
+    hex_stage_apply(sa, e * 5 * NU + z, NU, uz, R, xr, ar, s);
   }
   if (sa.uf_next == nullptr) return;
   __syncthreads();

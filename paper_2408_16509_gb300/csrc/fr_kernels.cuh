@@ -135,6 +135,30 @@ __device__ __forceinline__ void stage_update(const StageArgs<T>& a,
 }
 
 // ---------------------------------------------------------------------------
+// Asynchronous global -> shared copy (cp.async) of `bytes` (a multiple of 4)
+// by the `nthr` threads numbered t: 16-byte chunks when both addresses and
+// the size are 16-byte aligned, else 4-byte chunks.  Completes at
+// cp_async_wait_all() of each issuing thread.
+__device__ __forceinline__ void async_copy(void* sdst, const void* gsrc, int bytes,
+                                           int t, int nthr) {
+  const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(sdst));
+  const unsigned long long g = reinterpret_cast<unsigned long long>(gsrc);
+  if (((s | uint32_t(g) | uint32_t(bytes)) & 15u) == 0) {
+    for (int i = 16 * t; i < bytes; i += 16 * nthr)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s + i), "l"(g + i)
+                   : "memory");
+  } else {
+    for (int i = 4 * t; i < bytes; i += 4 * nthr)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s + i), "l"(g + i)
+                   : "memory");
+  }
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
 // Eq. (disu): u_f = M0 u, one element per EPB group of threads.
 template <typename T, int NU, int NF, int EPB>
 __global__ void __launch_bounds__(EPB* NU)
@@ -343,6 +367,31 @@ __device__ __forceinline__ void write_visc_q(const ViscArgs<T>& va,
   }
 #pragma unroll
   for (int k = 0; k < 5; ++k) va.q[(e * 5 + k) * nf + f] = q[k];
+}
+
+// Viscous normal flux q of write_visc_q from inputs read beforehand: u
+// (trace), G (gradient at the flux point), nv = S^T n~, b = boundary-
+// condition index or -1.
+template <typename T>
+__device__ __forceinline__ void visc_q_pre(const BCTab<T>& bc, const Phys<T>& ph,
+                                           const T u[5], const T G[3][5],
+                                           const T nv[3], int b, T q[5]) {
+#pragma unroll
+  for (int k = 0; k < 5; ++k) q[k] = T(0);
+  viscous_normal_acc(u, G, nv, ph, T(1), q);
+  if (b >= 0) {
+    T ur[5], q2[5] = {0, 0, 0, 0, 0};
+    if (bc.kind[b] == 0) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) ur[k] = bc.state[b][k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) ur[k] = u[k];
+    }
+    viscous_normal_acc(ur, G, nv, ph, T(1), q2);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) q[k] = T(0.5) * (q[k] + q2[k]);
+  }
 }
 
 // Common flux on interior pairs from the sides' viscous fluxes q:
