@@ -447,11 +447,12 @@ def config_tgv48_mixed(fr, torch, device, steps=10, dt=2.5e-4):
     return out
 
 
-def config_mixed_elements(fr, torch, device, steps=20):
+def config_mixed_elements(fr, torch, device, steps=20, cells=40, variant="auto"):
     """40^3 cells: hexes x < 0.5, 2 prisms per cell 0.5 <= x < 0.8, 6 tets
-    x >= 0.8 (5% jitter), p=3, NS Re 1000, Ma 0.2, RK4, FP32."""
+    x >= 0.8 (5% jitter), p=3, NS Re 1000, Ma 0.2, RK4, FP32.  `cells` and
+    `variant` (kernel family) serve profiling runs (--only mixed)."""
     from frinputs import ics, mixed_box
-    spec = mixed_box(n=40)
+    spec = mixed_box(n=cells)
     pinf = 1.0 / (1.4 * 0.04)
     far = ("state", 1.0, 1.0, 0.0, 0.0, pinf)
     mesh = fr.FRMesh(spec, 3, physics="ns", mu=1e-3, prandtl=PR,
@@ -459,6 +460,7 @@ def config_mixed_elements(fr, torch, device, steps=20):
                      device=device)
     st = torch.cuda.Stream(device=device)
     mesh.set_stream(st)
+    mesh.set_variant(variant)
     mesh.set_solution(_state(mesh, lambda x: ics.perturbed_uniform(x)))
     mesh.rk_step("rk4", 2e-4, 2)
     ms = _timed_steps(torch, mesh, st, "rk4", 2e-4, steps)
@@ -624,9 +626,31 @@ def main():
                     help="also time the other workloads (N=1 only)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", default=None,
+                    choices=["vortex", "tgv48", "mixed", "shu_osher"],
+                    help="run one side workload alone and print its record "
+                         "(profiling aid; not a contract line)")
+    ap.add_argument("--cells", type=int, default=40,
+                    help="cells per direction of the mixed-element box (--only mixed)")
+    ap.add_argument("--variant", default="auto",
+                    help="kernel family of the mixed-element run (--only mixed)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.only:
+        import torch
+        import paper_2408_16509_gb300 as fr
+        fr.build()
+        dev = 0
+        torch.cuda.set_device(dev)
+        fns = {"vortex": config_vortex, "tgv48": config_tgv48_mixed,
+               "shu_osher": config_shu_osher,
+               "mixed": lambda f, t, d: config_mixed_elements(
+                   f, t, d, steps=args.steps, cells=args.cells,
+                   variant=args.variant)}
+        rec = fns[args.only](fr, torch, dev)
+        print(json.dumps({"only": args.only, "record": rec}), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
