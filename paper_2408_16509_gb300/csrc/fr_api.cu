@@ -115,6 +115,7 @@ struct DevType {
   void* verts = nullptr;     // [ne][8][3] vertices minus vertex 0 (hex, FP32)
   // tensor-core kernels (prisms / tetrahedra, FP32 values)
   bool tc_ok = false;
+  bool tc_on = true;         // on the tensor cores when the family is TENSOR
   void* tcimg = nullptr;     // split-TF32 operator image
   TcGeom tcgeo{};
   int tc_vol_ctas = 1, tc_grad_ctas = 1;
@@ -514,7 +515,7 @@ bool use_hex(const fr_mesh* m, const DevType& D) {
 }
 
 bool use_tc(const fr_mesh* m, const DevType& D) {
-  return D.tc_ok && m->active == FR_VARIANT_TENSOR;
+  return D.tc_ok && D.tc_on && m->active == FR_VARIANT_TENSOR;
 }
 
 // Tensor-core gradient kernel of a prism / tetrahedron type (FP32 values).
@@ -1007,7 +1008,12 @@ int resolve_variant(fr_mesh* m, int scheme, double dt) {
     int v = m->variant;
     if (v == FR_VARIANT_SUMFACT_VERTEX && sizeof(T) != 4) v = FR_VARIANT_SUMFACT;
     if (v == FR_VARIANT_TENSOR && !has_tc) v = FR_VARIANT_SUMFACT;
-    if (v != m->active) {
+    bool changed = v != m->active;
+    for (auto& D : m->types) {  // a requested tensor family: every capable type
+      changed |= !D.tc_on;
+      D.tc_on = true;
+    }
+    if (changed) {
       m->active = v;
       m->uf_valid = false;
       ++m->epoch;
@@ -1043,32 +1049,94 @@ int resolve_variant(fr_mesh* m, int scheme, double dt) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  float best = 1e30f;
-  int pick = FR_VARIANT_SUMFACT;
-  for (int c : cand) {
-    m->active = c;
-    for (int rep = 0; rep < 2; ++rep) {
-      for (size_t t = 0; t < m->types.size(); ++t)
+  const size_t nt = m->types.size();
+  // per-type grad + volume kernel times (ms) of one profiled step
+  std::vector<float> t_cc(nt, 0.f), t_tc(nt, 0.f);
+  // One warm-up and one timed step of the active configuration from the
+  // saved state; with `per_type`, a third step launched kernel by kernel
+  // with events, its grad and volume times summed per type.
+  auto run = [&](std::vector<float>* per_type, float* ms) -> int {
+    for (int rep = 0; rep < (per_type ? 3 : 2); ++rep) {
+      for (size_t t = 0; t < nt; ++t)
         cudaMemcpyAsync(m->types[t].X, saved[t],
                         size_t(m->types[t].ne) * 5 * m->types[t].nu * sizeof(TR),
                         cudaMemcpyDeviceToDevice, m->stream);
       m->uf_valid = false;
       ensure_uf<T, TR>(m);
+      Prof prof;
       if (rep == 1) cudaEventRecord(e0, m->stream);
-      for (int s2 = 0; s2 < nst; ++s2) launch_stage<T, TR>(m, m->stream, mode, s2);
+      for (int s2 = 0; s2 < nst; ++s2)
+        launch_stage<T, TR>(m, m->stream, mode, s2, rep == 2 ? &prof : nullptr);
       if (rep == 1) cudaEventRecord(e1, m->stream);
+      cudaError_t err = cudaStreamSynchronize(m->stream);
+      if (err != cudaSuccess)
+        return fail(FR_ECUDA, std::string("autotuner: ") + cudaGetErrorString(err));
+      if (rep == 1) cudaEventElapsedTime(ms, e0, e1);
+      if (rep == 2) {
+        // grad and volume launches come once per type per stage, in type order
+        size_t ng = 0, nv = 0;
+        for (size_t i = 0; i < prof.cls.size(); ++i) {
+          float t = 0.f;
+          cudaEventElapsedTime(&t, prof.ev[2 * i], prof.ev[2 * i + 1]);
+          if (prof.cls[i] == FR_KC_GRAD) (*per_type)[ng++ % nt] += t;
+          if (prof.cls[i] == FR_KC_VOL) (*per_type)[nv++ % nt] += t;
+        }
+      }
+      for (cudaEvent_t ev : prof.ev) cudaEventDestroy(ev);
     }
-    cudaError_t err = cudaStreamSynchronize(m->stream);
-    if (err != cudaSuccess) {
-      release();
-      return fail(FR_ECUDA, std::string("autotuner: ") + cudaGetErrorString(err));
-    }
+    return FR_OK;
+  };
+  float best = 1e30f;
+  int pick = FR_VARIANT_SUMFACT;
+  for (auto& D : m->types) D.tc_on = true;
+  for (int c : cand) {
+    m->active = c;
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
+    std::vector<float>* pt = nullptr;
+    if (has_tc && c == FR_VARIANT_SUMFACT) pt = &t_cc;
+    if (c == FR_VARIANT_TENSOR) pt = &t_tc;
+    if (int rr = run(pt, &ms)) {
+      release();
+      return rr;
+    }
     m->tune_ms[c] = ms;
     if (ms < best) {
       best = ms;
       pick = c;
+    }
+  }
+  if (has_tc) {
+    // tensor cores only for the types whose kernels ran faster there; re-time
+    // the tensor family with that choice
+    bool any = false, all = true;
+    for (size_t t = 0; t < nt; ++t) {
+      DevType& D = m->types[t];
+      if (!D.tc_ok) continue;
+      D.tc_on = t_tc[t] < t_cc[t];
+      any |= D.tc_on;
+      all &= D.tc_on;
+    }
+    if (!any) {
+      if (pick == FR_VARIANT_TENSOR) {  // no type gains: best CUDA-core family
+        best = 1e30f;
+        for (int c : cand)
+          if (c != FR_VARIANT_TENSOR && m->tune_ms[c] < best) {
+            best = m->tune_ms[c];
+            pick = c;
+          }
+      }
+    } else if (!all) {
+      m->active = FR_VARIANT_TENSOR;
+      float ms = 0.f;
+      if (int rr = run(nullptr, &ms)) {
+        release();
+        return rr;
+      }
+      m->tune_ms[FR_VARIANT_TENSOR] = ms;
+      if (ms < best) {
+        best = ms;
+        pick = FR_VARIANT_TENSOR;
+      }
     }
   }
   cudaEventDestroy(e0);

@@ -110,33 +110,45 @@ struct TcGradCfg {
                               N2 <= 256 && (3 + S::NFACE) * NCP <= 512;
 };
 
-// Elements per tile: four (two CTAs per SM) when that fits, else the
-// largest of 16 / 8 that fits one CTA per SM; 0 when no tile fits.
+// Elements per tile: the largest of 16 / 12 / 8 / 4 whose shared memory
+// and TMEM columns fit one CTA per SM.  Larger tiles put more elements in
+// flight per SM and amortise each tile's chain of dependent phases; with
+// four-element tiles (two CTAs per SM) the tetrahedron kernels ran 2.4x
+// slower than with these.
 template <int NU, int NF>
 constexpr int tc_vol_epb() {
-  return (TcVolCfg<NU, NF, 4>::kOk && 2 * (TcVolCfg<NU, NF, 4>::SMEM + 1024) <= kTcSmemSm)
-             ? 4
-         : TcVolCfg<NU, NF, 16>::kOk ? 16
+  return TcVolCfg<NU, NF, 16>::kOk   ? 16
+         : TcVolCfg<NU, NF, 12>::kOk ? 12
          : TcVolCfg<NU, NF, 8>::kOk  ? 8
+         : TcVolCfg<NU, NF, 4>::kOk  ? 4
                                      : 0;
 }
 
 template <int NU, int NF>
 constexpr int tc_grad_epb() {
-  return (TcGradCfg<NU, NF, 4>::kOk && 2 * (TcGradCfg<NU, NF, 4>::SMEM + 1024) <= kTcSmemSm)
-             ? 4
-         : TcGradCfg<NU, NF, 8>::kOk ? 8
-                                     : 0;
+  return TcGradCfg<NU, NF, 16>::kOk   ? 16
+         : TcGradCfg<NU, NF, 12>::kOk ? 12
+         : TcGradCfg<NU, NF, 8>::kOk  ? 8
+         : TcGradCfg<NU, NF, 4>::kOk  ? 4
+                                      : 0;
 }
 
+// resident CTAs per SM: two when both shared memory and the 512 TMEM
+// columns allow it
 template <int NU, int NF, int E>
 constexpr int tc_minb_vol() {
-  return 2 * (TcVolCfg<NU, NF, E>::SMEM + 1024) <= kTcSmemSm ? 2 : 1;
+  return 2 * (TcVolCfg<NU, NF, E>::SMEM + 1024) <= kTcSmemSm &&
+                 2 * TcVolCfg<NU, NF, E>::TCOLS <= 512
+             ? 2
+             : 1;
 }
 
 template <int NU, int NF, int E>
 constexpr int tc_minb_grad() {
-  return 2 * (TcGradCfg<NU, NF, E>::SMEM + 1024) <= kTcSmemSm ? 2 : 1;
+  return 2 * (TcGradCfg<NU, NF, E>::SMEM + 1024) <= kTcSmemSm &&
+                 2 * TcGradCfg<NU, NF, E>::TCOLS <= 512
+             ? 2
+             : 1;
 }
 
 constexpr int kTcThreads = 256;
