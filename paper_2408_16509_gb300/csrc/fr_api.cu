@@ -115,8 +115,11 @@ struct DevType {
   void* verts = nullptr;     // [ne][8][3] vertices minus vertex 0 (hex, FP32)
   // tensor-core kernels (prisms / tetrahedra, FP32 values)
   bool tc_ok = false;
-  bool tc_on = true;         // on the tensor cores when the family is TENSOR
+  bool tca_ok = false;       // data-as-A volume kernel available
+  bool tc_grad_on = true;    // kernels on the tensor cores when the family
+  bool tc_vol_on = true;     //   is TENSOR (the tuner decides per type)
   void* tcimg = nullptr;     // split-TF32 operator image
+  void* tcaimg = nullptr;    // the same, output points padded to 16
   TcGeom tcgeo{};
   int tc_vol_ctas = 1, tc_grad_ctas = 1;
 };
@@ -251,20 +254,18 @@ float tf32_rna_host(float x) {
   return r;
 }
 
-// Face-aligned flux-point order and split-TF32 operator image of the
-// tensor-core kernels for a prism or tetrahedron (layout documented in
-// fr_dense_tc.cuh).  False when the element does not have the expected face
-// structure (contiguous faces with one reference normal each).
-bool build_tc(const RefElement& R, std::vector<double>& img, TcGeom& geo) {
+// Face-aligned flux-point order of the tensor-core kernels for a prism or
+// tetrahedron (layout documented in fr_dense_tc.cuh).  False when the
+// element does not have the expected face structure (contiguous faces with
+// one reference normal each).
+bool build_tc_geo(const RefElement& R, TcGeom& geo, std::vector<int>& fpad) {
   const int nu = R.nupts, nf = R.nfpts;
-  const int KU = tc_ru(nu, 8), K3 = 3 * KU, KFP = tc_kfp(nu, nf);
-  const int NFACE = tc_nface(nu, nf);
+  const int KFP = tc_kfp(nu, nf), NFACE = tc_nface(nu, nf);
   if (KFP == 0 || KFP > 128 || nf > 128 || nu > 128 || R.nfaces != NFACE ||
       int(R.face_start.size()) != NFACE + 1)
     return false;
-  const int MU = nu <= 64 ? 64 : 128, MF = nf <= 64 ? 64 : 128;
   geo = TcGeom{};
-  std::vector<int> fpad(nf, -1);
+  fpad.assign(nf, -1);
   int kofs = 0;
   for (int fa = 0; fa < NFACE; ++fa) {
     const int f0 = R.face_start[fa], f1 = R.face_start[fa + 1];
@@ -288,7 +289,19 @@ bool build_tc(const RefElement& R, std::vector<double>& img, TcGeom& geo) {
   geo.npad = 0;
   for (int k = 0; k < KFP; ++k)
     if (!used[k]) geo.pad[geo.npad++] = uint8_t(k);
-  const size_t sm0 = size_t(MF) * KU, sd3 = size_t(MU) * K3, sl = size_t(MU) * KFP;
+  return true;
+}
+
+// Split-TF32 operator image (hi plane, then lo plane, per operator) with the
+// operators' output points padded to mf rows (M0) and mu rows (D, LIFT):
+//   M0  mf x KU    M0[f][q]
+//   D3  mu x 3KU   D_d[z][q] at column d KU + q
+//   L   mu x KFP   LIFT[z][f] at column fpad[f]
+void build_tc_image(const RefElement& R, const std::vector<int>& fpad, int mf, int mu,
+                    std::vector<double>& img) {
+  const int nu = R.nupts, nf = R.nfpts;
+  const int KU = tc_ru(nu, 8), K3 = 3 * KU, KFP = tc_kfp(nu, nf);
+  const size_t sm0 = size_t(mf) * KU, sd3 = size_t(mu) * K3, sl = size_t(mu) * KFP;
   img.assign(2 * (sm0 + sd3 + sl), 0.0);
   auto put = [&](size_t base, size_t plane, int off, double x) {
     const float h = tf32_rna_host(float(x));
@@ -306,7 +319,6 @@ bool build_tc(const RefElement& R, std::vector<double>& img, TcGeom& geo) {
   for (int z = 0; z < nu; ++z)
     for (int f = 0; f < nf; ++f)
       put(b_l, sl, tc_offset(z, fpad[f], KFP), R.LIFT[size_t(z) * nf + f]);
-  return true;
 }
 
 // Compile-time tile of the tensor-core kernels for (NU, NF); false when the
@@ -314,6 +326,13 @@ bool build_tc(const RefElement& R, std::vector<double>& img, TcGeom& geo) {
 template <int NU, int NF>
 constexpr bool tc_supported() {
   return tc_vol_epb<NU, NF>() > 0 && tc_grad_epb<NU, NF>() > 0;
+}
+
+// the data-as-A volume kernel: its MMA height when 128 rows (25 elements)
+// fit, else 0 (with 64 rows it was no faster than k_vol_tc on prisms)
+template <int NU, int NF>
+constexpr int tca_supported() {
+  return tc_supported<NU, NF>() && tca_m<NU, NF>() == 128 ? 128 : 0;
 }
 
 // precisions with tensor-core kernels: FP32 values and registers
@@ -369,13 +388,25 @@ int setup_device(fr_mesh* m) {
     if ((rc = dev_upload<T>(m, R.fnorm, &D.NREF))) return rc;
     if (sizeof(T) == 4 && D.kind != EK_HEX) {
       bool fits = false;
+      int tca = 0;
+      bool order_ok = true;  // host face order = the compile-time one
       dispatch(D.kind, m->order, [&](auto nu, auto nf) {
-        fits = tc_supported<decltype(nu)::value, decltype(nf)::value>();
+        constexpr int NU = decltype(nu)::value, NF = decltype(nf)::value;
+        fits = tc_supported<NU, NF>();
+        tca = tca_supported<NU, NF>();
       });
       std::vector<double> img;
-      if (fits && build_tc(R, img, D.tcgeo)) {
+      std::vector<int> fpad;
+      if (fits && build_tc_geo(R, D.tcgeo, fpad)) {
+        build_tc_image(R, fpad, D.nf <= 64 ? 64 : 128, D.nu <= 64 ? 64 : 128, img);
         if ((rc = dev_upload<float>(m, img, &D.tcimg))) return rc;
         D.tc_ok = true;
+        for (int f = 0; f < D.nf; ++f) order_ok &= fpad[f] == tc_fpad(D.nu, D.nf, f);
+        if (tca && order_ok) {
+          build_tc_image(R, fpad, tc_ru(D.nf, 16), tc_ru(D.nu, 16), img);
+          if ((rc = dev_upload<float>(m, img, &D.tcaimg))) return rc;
+          D.tca_ok = true;
+        }
       }
     }
     if (D.kind == EK_HEX) {
@@ -514,8 +545,12 @@ bool use_hex(const fr_mesh* m, const DevType& D) {
   return D.kind == EK_HEX && m->active != FR_VARIANT_DENSE;
 }
 
-bool use_tc(const fr_mesh* m, const DevType& D) {
-  return D.tc_ok && D.tc_on && m->active == FR_VARIANT_TENSOR;
+bool use_tc_grad(const fr_mesh* m, const DevType& D) {
+  return D.tc_ok && D.tc_grad_on && m->active == FR_VARIANT_TENSOR;
+}
+
+bool use_tc_vol(const fr_mesh* m, const DevType& D) {
+  return D.tc_ok && D.tc_vol_on && m->active == FR_VARIANT_TENSOR;
 }
 
 // Tensor-core gradient kernel of a prism / tetrahedron type (FP32 values).
@@ -553,6 +588,25 @@ void launch_vol_tc(fr_mesh* m, const DevType& D, cudaStream_t s, bool from_x,
     if (D.ne == 0) return;
     dispatch(D.kind, m->order, [&](auto nu, auto nf) {
       constexpr int NU = decltype(nu)::value, NF = decltype(nf)::value;
+      constexpr int MA = tca_supported<NU, NF>();
+      if constexpr (MA > 0) {
+        if (D.tca_ok) {
+          using CA = TcaVolCfg<NU, NF, MA>;
+          const long long tiles = (D.ne + CA::E - 1) / CA::E;
+          const unsigned grid = unsigned(std::min<long long>(tiles, (long long)m->num_sms));
+          const float* uin = from_x ? nullptr : (const float*)D.Y;
+          if (ns)
+            k_vol_tca<NU, NF, MA, true><<<grid, kTcThreads, CA::SMEM, s>>>(
+                D.ne, uin, (const float*)D.grad, fc, (const float*)D.smat,
+                (const float*)D.rcpdjac, (const float*)D.tcaimg, (const float*)D.NREF, ph,
+                sa);
+          else
+            k_vol_tca<NU, NF, MA, false><<<grid, kTcThreads, CA::SMEM, s>>>(
+                D.ne, uin, nullptr, fc, (const float*)D.smat, (const float*)D.rcpdjac,
+                (const float*)D.tcaimg, (const float*)D.NREF, ph, sa);
+          return;
+        }
+      }
       if constexpr (tc_supported<NU, NF>()) {
         constexpr int EV = tc_vol_epb<NU, NF>();
         constexpr int BV = tc_minb_vol<NU, NF, EV>();
@@ -632,6 +686,18 @@ int prepare_kernels(fr_mesh* m) {
           // two fit; a grid that is too large would only run in two waves.)
           D.tc_vol_ctas = std::max(1, std::min(BV, 512 / TcVolCfg<NU, NF, EV>::TCOLS));
           D.tc_grad_ctas = std::max(1, std::min(BG, 512 / TcGradCfg<NU, NF, EG>::TCOLS));
+          constexpr int MA = tca_supported<NU, NF>();
+          if constexpr (MA > 0) {
+            if (D.tca_ok) {
+              const int sma = int(TcaVolCfg<NU, NF, MA>::SMEM);
+              for (auto fn : {(const void*)k_vol_tca<NU, NF, MA, true>,
+                              (const void*)k_vol_tca<NU, NF, MA, false>}) {
+                cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, sma);
+                cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     int(cudaSharedmemCarveoutMaxShared));
+              }
+            }
+          }
         }
       }
     });
@@ -764,7 +830,7 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
                   (const T*)D.smat, (const T*)D.rcpdjac, hexops<T>(D),
                   (T*)D.grad, va, bc, ph);
         });
-      } else if (use_tc(m, D)) {
+      } else if (use_tc_grad(m, D)) {
         launch_grad_tc<T, TR>(m, D, s, from_x, du, va, bc, ph);
       } else {
         dispatch(D.kind, m->order, [&](auto nu, auto nf) {
@@ -846,7 +912,7 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
               D.ne, uin, nullptr, fc, (const T*)D.smat, (const T*)D.rcpdjac,
               hexops<T>(D), ph, sa);
       });
-    } else if (use_tc(m, D)) {
+    } else if (use_tc_vol(m, D)) {
       HexStage<T, TR> sa{mode, stage, (TR*)D.X, (TR*)D.A, (T*)D.Y, (T*)D.R,
                          m->d_dt, m->d_flag, uf_next};
       launch_vol_tc<T, TR>(m, D, s, from_x, ns, fc, ph, sa);
@@ -1010,8 +1076,8 @@ int resolve_variant(fr_mesh* m, int scheme, double dt) {
     if (v == FR_VARIANT_TENSOR && !has_tc) v = FR_VARIANT_SUMFACT;
     bool changed = v != m->active;
     for (auto& D : m->types) {  // a requested tensor family: every capable type
-      changed |= !D.tc_on;
-      D.tc_on = true;
+      changed |= !D.tc_grad_on || !D.tc_vol_on;
+      D.tc_grad_on = D.tc_vol_on = true;
     }
     if (changed) {
       m->active = v;
@@ -1050,11 +1116,12 @@ int resolve_variant(fr_mesh* m, int scheme, double dt) {
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   const size_t nt = m->types.size();
-  // per-type grad + volume kernel times (ms) of one profiled step
-  std::vector<float> t_cc(nt, 0.f), t_tc(nt, 0.f);
+  // per-type gradient and volume kernel times (ms) of one profiled step:
+  // [2 t] gradient, [2 t + 1] volume
+  std::vector<float> t_cc(2 * nt, 0.f), t_tc(2 * nt, 0.f);
   // One warm-up and one timed step of the active configuration from the
   // saved state; with `per_type`, a third step launched kernel by kernel
-  // with events, its grad and volume times summed per type.
+  // with events, its gradient and volume times summed per type.
   auto run = [&](std::vector<float>* per_type, float* ms) -> int {
     for (int rep = 0; rep < (per_type ? 3 : 2); ++rep) {
       for (size_t t = 0; t < nt; ++t)
@@ -1078,8 +1145,8 @@ int resolve_variant(fr_mesh* m, int scheme, double dt) {
         for (size_t i = 0; i < prof.cls.size(); ++i) {
           float t = 0.f;
           cudaEventElapsedTime(&t, prof.ev[2 * i], prof.ev[2 * i + 1]);
-          if (prof.cls[i] == FR_KC_GRAD) (*per_type)[ng++ % nt] += t;
-          if (prof.cls[i] == FR_KC_VOL) (*per_type)[nv++ % nt] += t;
+          if (prof.cls[i] == FR_KC_GRAD) (*per_type)[2 * (ng++ % nt)] += t;
+          if (prof.cls[i] == FR_KC_VOL) (*per_type)[2 * (nv++ % nt) + 1] += t;
         }
       }
       for (cudaEvent_t ev : prof.ev) cudaEventDestroy(ev);
@@ -1088,7 +1155,7 @@ int resolve_variant(fr_mesh* m, int scheme, double dt) {
   };
   float best = 1e30f;
   int pick = FR_VARIANT_SUMFACT;
-  for (auto& D : m->types) D.tc_on = true;
+  for (auto& D : m->types) D.tc_grad_on = D.tc_vol_on = true;
   for (int c : cand) {
     m->active = c;
     float ms = 0.f;
@@ -1106,15 +1173,16 @@ int resolve_variant(fr_mesh* m, int scheme, double dt) {
     }
   }
   if (has_tc) {
-    // tensor cores only for the types whose kernels ran faster there; re-time
-    // the tensor family with that choice
+    // tensor cores only for the kernels (gradient, volume) of the types that
+    // ran faster there; re-time the tensor family with that choice
     bool any = false, all = true;
     for (size_t t = 0; t < nt; ++t) {
       DevType& D = m->types[t];
       if (!D.tc_ok) continue;
-      D.tc_on = t_tc[t] < t_cc[t];
-      any |= D.tc_on;
-      all &= D.tc_on;
+      D.tc_grad_on = t_tc[2 * t] < t_cc[2 * t];
+      D.tc_vol_on = t_tc[2 * t + 1] < t_cc[2 * t + 1];
+      any |= D.tc_grad_on || D.tc_vol_on;
+      all &= D.tc_grad_on && D.tc_vol_on;
     }
     if (!any) {
       if (pick == FR_VARIANT_TENSOR) {  // no type gains: best CUDA-core family

@@ -20,6 +20,7 @@
 // (constant) reference normal being applied in the epilogue.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 
 #include "fr_hex.cuh"
 #include "fr_kernels.cuh"
@@ -54,6 +55,55 @@ __host__ __device__ constexpr int tc_nface(int nu, int nf) {
     if (nu == nt * (p + 3) / 3 && nf == 4 * nt) return 4;
   }
   return 0;
+}
+
+// order p of the prism / tetrahedron with (nupts, nfpts); 0 otherwise
+__host__ __device__ constexpr int tc_order(int nu, int nf) {
+  for (int p = 1; p <= 8; ++p) {
+    const int nt = (p + 1) * (p + 2) / 2, nq = (p + 1) * (p + 1);
+    if (nu == nq * (p + 2) / 2 && nf == 2 * nt + 3 * nq) return p;
+    if (nu == nt * (p + 3) / 3 && nf == 4 * nt) return p;
+  }
+  return 0;
+}
+
+// flux points on face fa: prisms list the two triangles, then the three
+// quadrilaterals; tetrahedra four triangles
+__host__ __device__ constexpr int tc_face_n(int nu, int nf, int fa) {
+  const int p = tc_order(nu, nf);
+  const int nt = (p + 1) * (p + 2) / 2, nq = (p + 1) * (p + 1);
+  return tc_nface(nu, nf) == 5 ? (fa < 2 ? nt : nq) : nt;
+}
+
+// face-aligned K position of flux point f, and its inverse (-1: padding)
+__host__ __device__ constexpr int tc_fpad(int nu, int nf, int f) {
+  int fa = 0, f0 = 0, k0 = 0;
+  while (f >= f0 + tc_face_n(nu, nf, fa)) {
+    f0 += tc_face_n(nu, nf, fa);
+    k0 += tc_ru(tc_face_n(nu, nf, fa), 8);
+    ++fa;
+  }
+  return k0 + (f - f0);
+}
+
+__host__ __device__ constexpr int tc_kinv(int nu, int nf, int k) {
+  int f0 = 0, k0 = 0;
+  for (int fa = 0; fa < tc_nface(nu, nf); ++fa) {
+    const int n = tc_face_n(nu, nf, fa);
+    if (k < k0 + tc_ru(n, 8)) return k - k0 < n ? f0 + (k - k0) : -1;
+    f0 += n;
+    k0 += tc_ru(n, 8);
+  }
+  return -1;
+}
+
+// compile-time loop: f(std::integral_constant<int, I>) for I = B .. E-1
+template <int B, int E, typename F>
+__device__ __forceinline__ void tc_static_for(F&& f) {
+  if constexpr (B < E) {
+    f(std::integral_constant<int, B>{});
+    tc_static_for<B + 1, E>(f);
+  }
 }
 
 // Operator image: [M0 hi | M0 lo | D3 hi | D3 lo | L hi | L lo] (floats)
@@ -677,6 +727,391 @@ __global__ void __launch_bounds__(kTcThreads, MINB)
     tc_fence_after();
   }
   tc_epilogue<C::TCOLS>(tm, &mbar, ok, flag);
+}
+
+// ---------------------------------------------------------------------------
+// Volume kernel with the data as the MMA's A operand.  A = data of E
+// elements, row el 5 + k (element el, variable k; M = 128 rows: E = 25,
+// M = 64: E = 12), K = input points, 128-byte swizzle; B = operator, rows =
+// output points padded to 16, canonical K-major layout.  TMEM lane r holds
+// data row r and columns are output points, so every epilogue thread owns
+// one (element, variable) row and reads and writes it with contiguous
+// 16-byte accesses.  Operator image as TcShape but with row counts NUN /
+// NFN (ru16).
+template <int NU, int NF, int M>
+struct TcaVolCfg {
+  using S = TcShape<NU, NF>;
+  static constexpr int E = M / 5, ROWS = 5 * E;
+  static constexpr int NUN = tc_ru(NU, 16), NFN = tc_ru(NF, 16);
+  static constexpr int SZ_M0 = NFN * S::KU, SZ_D3 = NUN * S::K3, SZ_L = NUN * S::KFP;
+  static constexpr int OPS = 2 * (SZ_M0 + SZ_D3 + SZ_L);
+  static constexpr int KA = tc_ru(tc_max(tc_max(S::K3, S::KFP), S::KU), 32);
+  static constexpr int AFL = M * KA;  // floats per A plane
+  static constexpr size_t SMEM =
+      (size_t(OPS) + 2 * size_t(AFL) + size_t(tc_ru(3 * NF, 4))) * 4 + 1024;
+  static constexpr int TCOLS = tc_pow2(3 * NFN + NUN);
+  static constexpr bool kOk = S::kShapeOk && SMEM <= kTcSmemMax && 3 * NFN + NUN <= 512 &&
+                              NFN <= 256 && NUN <= 256 && S::KU % 4 == 0;
+};
+
+template <int NU, int NF>
+constexpr int tca_m() {
+  return TcaVolCfg<NU, NF, 128>::kOk ? 128 : TcaVolCfg<NU, NF, 64>::kOk ? 64 : 0;
+}
+
+// D (+)= A B^T, A = data (128-byte swizzle, R rows), B = operator
+// (canonical, K columns), K slice sa of A and sb of B
+__device__ __forceinline__ void mma3a(uint32_t d, const float* ah, const float* al,
+                                      int R, int sa, const float* bh, const float* bl,
+                                      int K, int sb, uint32_t idesc, bool acc) {
+  const uint32_t sbo = uint32_t(K / 4) * 128u;
+  const uint64_t a_h = tc_desc_sw128(ah, R, sa), a_l = tc_desc_sw128(al, R, sa);
+  const uint64_t b_h = tc_desc(bh + sb * 64, 128, sbo);
+  const uint64_t b_l = tc_desc(bl + sb * 64, 128, sbo);
+  tc_mma_tf32(d, a_l, b_h, idesc, acc);
+  tc_mma_tf32(d, a_h, b_l, idesc, true);
+  tc_mma_tf32(d, a_h, b_h, idesc, true);
+}
+
+// four consecutive K values (k0 a multiple of 4) of row r as TF32 pairs
+__device__ __forceinline__ void put_split4(float* hi, float* lo, int R, int r, int k0,
+                                           float4 x) {
+  const int o = sw128_offset(r, k0, R);
+  float4 h, l;
+  h.x = tf32_hi(x.x); l.x = tf32_hi(x.x - h.x);
+  h.y = tf32_hi(x.y); l.y = tf32_hi(x.y - h.y);
+  h.z = tf32_hi(x.z); l.z = tf32_hi(x.z - h.z);
+  h.w = tf32_hi(x.w); l.w = tf32_hi(x.w - h.w);
+  *reinterpret_cast<float4*>(hi + o) = h;
+  *reinterpret_cast<float4*>(lo + o) = l;
+}
+
+// n consecutive values of a row from global memory: 16-byte loads when n
+// and the address allow it
+template <int N>
+__device__ __forceinline__ void tc_row_load(const float* __restrict__ src, bool vec,
+                                            float v[N]) {
+  if (N % 4 == 0 && vec) {
+#pragma unroll
+    for (int i = 0; i < N / 4; ++i) {
+      const float4 q = reinterpret_cast<const float4*>(src)[i];
+      v[4 * i] = q.x;
+      v[4 * i + 1] = q.y;
+      v[4 * i + 2] = q.z;
+      v[4 * i + 3] = q.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = src[i];
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void tc_row_store(float* __restrict__ dst, bool vec,
+                                             const float v[N]) {
+  if (N % 4 == 0 && vec) {
+#pragma unroll
+    for (int i = 0; i < N / 4; ++i)
+      reinterpret_cast<float4*>(dst)[i] =
+          make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) dst[i] = v[i];
+  }
+}
+
+// RK epilogue of one variable over the N points of an element row at i0
+// (the arithmetic of hex_stage_apply, FP32 registers), from the register
+// values x (X) and ac (A) read beforehand; s receives the next stage value.
+template <int N>
+__device__ __forceinline__ void tc_stage_row(const HexStage<float, float>& a,
+                                             long long i0, bool vec, const float R[N],
+                                             const float x[N], const float ac[N],
+                                             float s[N]) {
+  if (a.mode == 0) {
+    tc_row_store<N>(a.out + i0, vec, R);
+#pragma unroll
+    for (int z = 0; z < N; ++z) s[z] = 0.f;
+    return;
+  }
+  const float dt = float(*a.dt);
+  const int st = a.stage;
+  if (a.mode == 1) {
+    if (st < 3) {
+      float ao[N];
+#pragma unroll
+      for (int z = 0; z < N; ++z) {
+        const float r = R[z];
+        if (st == 0) {
+          ao[z] = x[z] + dt * float(1.0 / 6.0) * r;
+          s[z] = x[z] + dt * 0.5f * r;
+        } else {
+          ao[z] = ac[z] + dt * float(1.0 / 3.0) * r;
+          s[z] = x[z] + (st == 1 ? dt * 0.5f : dt) * r;
+        }
+      }
+      tc_row_store<N>(a.A + i0, vec, ao);
+      tc_row_store<N>(a.Y + i0, vec, s);
+    } else {
+#pragma unroll
+      for (int z = 0; z < N; ++z) s[z] = ac[z] + dt * float(1.0 / 6.0) * R[z];
+      tc_row_store<N>(a.X + i0, vec, s);
+    }
+    return;
+  }
+  const float b = float(c_rk45_b[st]);
+  const float am = st < 4 ? float(c_rk45_a[st]) - b : 0.f;
+  float xo[N];
+#pragma unroll
+  for (int z = 0; z < N; ++z) {
+    xo[z] = x[z] + b * dt * R[z];
+    s[z] = st < 4 ? xo[z] + am * dt * R[z] : xo[z];
+  }
+  tc_row_store<N>(a.X + i0, vec, xo);
+  if (st < 4) tc_row_store<N>(a.Y + i0, vec, s);
+}
+
+template <int NU, int NF, int M, bool NS>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_vol_tca(long long ne, const float* __restrict__ uin,
+              const float* __restrict__ grad, const float* __restrict__ fc,
+              const float* __restrict__ smat, const float* __restrict__ rcpdjac,
+              const float* __restrict__ opimg, const float* __restrict__ nref,
+              Phys<float> ph, HexStage<float, float> sa) {
+  using S = TcShape<NU, NF>;
+  using C = TcaVolCfg<NU, NF, M>;
+  constexpr int E = C::E, KU = S::KU, K3 = S::K3, KFP = S::KFP;
+  constexpr int NUN = C::NUN, NFN = C::NFN;
+  extern __shared__ unsigned char tc_raw[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tslot;
+  float* m0h = tc_align1024(tc_raw);
+  float* m0l = m0h + C::SZ_M0;
+  float* d3h = m0l + C::SZ_M0;
+  float* d3l = d3h + C::SZ_D3;
+  float* lfh = d3l + C::SZ_D3;
+  float* lfl = lfh + C::SZ_L;
+  float* ah = lfl + C::SZ_L;  // 1024-aligned: OPS is a multiple of 256
+  float* al = ah + C::AFL;
+  float* nrs = al + C::AFL;   // [NF][3] reference normals
+  const uint32_t tm = tc_prologue<C::OPS, 2 * C::AFL, C::TCOLS>(opimg, m0h, ah, &mbar, &tslot);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int i = tid; i < 3 * NF; i += blockDim.x) nrs[i] = nref[i];
+  __syncthreads();
+  const uint32_t tl = tm + (uint32_t(32 * (warp & 3)) << 16);
+  constexpr uint32_t id_f = tc_idesc_tf32(M, NFN), id_u = tc_idesc_tf32(M, NUN);
+  const bool epi = warp < 4;  // warps 0-3 (one per TMEM lane quarter) run the epilogues
+  const int row = tc_row<M>(warp, lane);  // data row of this thread's TMEM lane
+  const int rel = row >= 0 ? row / 5 : 0, rk = row >= 0 ? row - 5 * rel : 0;
+  const bool vf = (reinterpret_cast<unsigned long long>(fc) & 15u) == 0;
+  const bool vu = (reinterpret_cast<unsigned long long>(sa.X) & 15u) == 0 &&
+                  (reinterpret_cast<unsigned long long>(sa.Y) & 15u) == 0 &&
+                  (reinterpret_cast<unsigned long long>(sa.A) & 15u) == 0 &&
+                  (reinterpret_cast<unsigned long long>(sa.out) & 15u) == 0 &&
+                  (reinterpret_cast<unsigned long long>(rcpdjac) & 15u) == 0;
+  const bool vn = sa.uf_next == nullptr ||
+                  (reinterpret_cast<unsigned long long>(sa.uf_next) & 15u) == 0;
+  const float* X = sa.X;
+  uint32_t phase = 0;
+  bool ok = true;
+  const long long ntiles = (ne + E - 1) / E;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long e0 = tile * E;
+    const long long e = e0 + rel;
+    const bool live = row >= 0 && row < C::ROWS && e < ne;
+    // (1) transformed flux -> A rows el 5 + k, K = d KU + z
+    constexpr int PP = E * KU > kTcThreads ? 2 : 1;
+    for (int i0 = tid; i0 < E * KU; i0 += PP * kTcThreads) {
+      float uz[PP][5], g[PP][3][5], Sm[PP][9];
+      bool pl[PP];
+#pragma unroll
+      for (int p = 0; p < PP; ++p) {
+        const int i = i0 + p * kTcThreads;
+        const int el = i / KU, z = i - el * KU;
+        const long long ee = e0 + el;
+        pl[p] = i < E * KU && z < NU && ee < ne;
+        if (pl[p]) {
+#pragma unroll
+          for (int k = 0; k < 5; ++k) {
+            const long long ix = (ee * 5 + k) * NU + z;
+            uz[p][k] = uin ? uin[ix] : X[ix];
+          }
+          if (NS) {
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+              for (int k = 0; k < 5; ++k) g[p][j][k] = grad[(ee * 15 + j * 5 + k) * NU + z];
+          }
+#pragma unroll
+          for (int r = 0; r < 9; ++r) Sm[p][r] = smat[(ee * 9 + r) * NU + z];
+        }
+      }
+#pragma unroll
+      for (int p = 0; p < PP; ++p) {
+        const int i = i0 + p * kTcThreads;
+        if (i >= E * KU) continue;
+        const int el = i / KU, z = i - el * KU;
+        float ft[3][5];
+        if (pl[p]) {
+          tc_point_flux<NS>(uz[p], g[p], Sm[p], ph, ft);
+        } else {
+#pragma unroll
+          for (int d = 0; d < 3; ++d)
+#pragma unroll
+            for (int k = 0; k < 5; ++k) ft[d][k] = 0.f;
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+          for (int k = 0; k < 5; ++k) put_split(ah, al, M, el * 5 + k, d * KU + z, ft[d][k]);
+      }
+    }
+    tc_sync_for_mma();
+    if (tid == 0) {
+#pragma unroll 1
+      for (int d = 0; d < 3; ++d)
+#pragma unroll 1
+        for (int s2 = 0; s2 < KU / 8; ++s2)
+          mma3a(tm + d * NFN, ah, al, M, d * (KU / 8) + s2, m0h, m0l, KU, s2, id_f, s2 > 0);
+#pragma unroll 1
+      for (int s2 = 0; s2 < K3 / 8; ++s2)
+        mma3a(tm + 3 * NFN, ah, al, M, s2, d3h, d3l, K3, s2, id_u, s2 > 0);
+      tc_commit(&mbar);
+    }
+    ok = tc_wait_all(&mbar, phase);
+    phase ^= 1;
+    if (!ok) break;
+    // (2) jump F^C - n~ . M0 f~ of this row at all flux points -> A row, K =
+    //     face-aligned flux-point order
+    if (epi) {
+      float jv[NF];
+      if (live) {
+        tc_row_load<NF>(fc + (e * 5 + rk) * NF, vf, jv);
+      } else {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) jv[f] = 0.f;
+      }
+      tc_static_for<0, NFN / 16>([&](auto CI) {
+        constexpr int c = decltype(CI)::value;
+        float g0[16], g1[16], g2[16];
+        tmem_ld16(tl + 0 * NFN + 16 * c, g0);
+        tmem_ld16(tl + 1 * NFN + 16 * c, g1);
+        tmem_ld16(tl + 2 * NFN + 16 * c, g2);
+        tc_static_for<0, 16>([&](auto II) {
+          constexpr int i = decltype(II)::value, f = 16 * c + i;
+          if constexpr (f < NF)
+            jv[f] -= nrs[3 * f] * g0[i] + nrs[3 * f + 1] * g1[i] + nrs[3 * f + 2] * g2[i];
+        });
+      });
+      if (row >= 0) {
+        if (!live) {
+#pragma unroll
+          for (int f = 0; f < NF; ++f) jv[f] = 0.f;
+        }
+        tc_static_for<0, KFP / 4>([&](auto KC) {
+          constexpr int k0 = 4 * decltype(KC)::value;
+          constexpr int f0 = tc_kinv(NU, NF, k0), f1 = tc_kinv(NU, NF, k0 + 1);
+          constexpr int f2 = tc_kinv(NU, NF, k0 + 2), f3 = tc_kinv(NU, NF, k0 + 3);
+          float4 w;
+          w.x = f0 >= 0 ? jv[f0 < 0 ? 0 : f0] : 0.f;
+          w.y = f1 >= 0 ? jv[f1 < 0 ? 0 : f1] : 0.f;
+          w.z = f2 >= 0 ? jv[f2 < 0 ? 0 : f2] : 0.f;
+          w.w = f3 >= 0 ? jv[f3 < 0 ? 0 : f3] : 0.f;
+          put_split4(ah, al, M, row, k0, w);
+        });
+      }
+    }
+    tc_sync_for_mma();
+    if (tid == 0) {
+#pragma unroll 1
+      for (int s2 = 0; s2 < KFP / 8; ++s2)
+        mma3a(tm + 3 * NFN, ah, al, M, s2, lfh, lfl, KFP, s2, id_u, true);
+      tc_commit(&mbar);
+    }
+    ok = tc_wait_all(&mbar, phase);
+    phase ^= 1;
+    if (!ok) break;
+    // (3) R = -div / J and the RK update of this row, 16 points at a time;
+    //     next stage value -> A (K = z, zero beyond NU)
+    const bool next = sa.uf_next != nullptr;
+    if (epi) {
+      bool nx, na;
+      hex_stage_needs(sa, &nx, &na);
+      const long long i0 = (e * 5 + rk) * NU;
+      bool bad = false;
+      tc_static_for<0, KU / 16 + (KU % 16 ? 1 : 0)>([&](auto CI) {
+        constexpr int c = decltype(CI)::value, z0 = 16 * c;
+        constexpr int n = NU - z0 < 16 ? (NU - z0 > 0 ? NU - z0 : 0) : 16;
+        float sv[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) sv[i] = 0.f;
+        float t[16];
+        if constexpr (z0 < NUN) tmem_ld16(tl + 3 * NFN + z0, t);
+        if constexpr (n > 0) {
+          if (live) {
+            const bool vc = vu && NU % 4 == 0 && n % 4 == 0;
+            float rj[n], R[n], xr[n], ar[n], so[n];
+            tc_row_load<n>(rcpdjac + e * NU + z0, vc, rj);
+            if (nx) {
+              tc_row_load<n>(sa.X + i0 + z0, vc, xr);
+            } else {
+#pragma unroll
+              for (int i = 0; i < n; ++i) xr[i] = 0.f;
+            }
+            if (na) {
+              tc_row_load<n>(sa.A + i0 + z0, vc, ar);
+            } else {
+#pragma unroll
+              for (int i = 0; i < n; ++i) ar[i] = 0.f;
+            }
+#pragma unroll
+            for (int i = 0; i < n; ++i) {
+              R[i] = -t[i] * rj[i];
+              bad |= !isfinite(R[i]);
+            }
+            tc_stage_row<n>(sa, i0 + z0, vc, R, xr, ar, so);
+#pragma unroll
+            for (int i = 0; i < n; ++i) sv[i] = so[i];
+          }
+        }
+        if (next && row >= 0) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (z0 + 4 * q < KU)
+              put_split4(ah, al, M, row, z0 + 4 * q,
+                         make_float4(sv[4 * q], sv[4 * q + 1], sv[4 * q + 2], sv[4 * q + 3]));
+        }
+      });
+      if (bad) atomicOr(sa.flag, 1);
+    }
+    if (next) {
+      tc_sync_for_mma();
+      if (tid == 0) {
+#pragma unroll 1
+        for (int s2 = 0; s2 < KU / 8; ++s2)
+          mma3a(tm, ah, al, M, s2, m0h, m0l, KU, s2, id_f, s2 > 0);
+        tc_commit(&mbar);
+      }
+      ok = tc_wait_all(&mbar, phase);
+      phase ^= 1;
+      if (!ok) break;
+      // (4) u_f of the next stage, row by row, 16 flux points at a time
+      if (epi) {
+        tc_static_for<0, NFN / 16>([&](auto CI) {
+          constexpr int f0 = 16 * decltype(CI)::value;
+          constexpr int n = NF - f0 < 16 ? NF - f0 : 16;
+          float t[16];
+          tmem_ld16(tl + f0, t);
+          if (live)
+            tc_row_store<n>(sa.uf_next + (e * 5 + rk) * NF + f0, vn && NF % 4 == 0 && n % 4 == 0, t);
+        });
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+  }
+  tc_epilogue<C::TCOLS>(tm, &mbar, ok, sa.flag);
 }
 
 }  // namespace frgb
