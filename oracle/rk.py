@@ -63,3 +63,77 @@ def step(rhs, u, dt, scheme):
         ks.append(rhs(ui))
     return {t: u[t] + dt * sum(b[j] * ks[j][t] for j in range(len(b)))
             for t in u}
+
+
+# ------------------------------------------------------------------------
+# Adaptive step-size control with the embedded pair (Section 3.5, "Adaptive
+# Time Stepping": the embedded estimate of the local error, normalised,
+# decides acceptance and grows or shrinks the step; the paper cites Hairer,
+# Norsett & Wanner for the method).  Readings taken here (the paper gives no
+# formulas):
+#   error estimate  e = u_{n+1} - uhat_{n+1} = dt sum_i (b_i - bhat_i) k_i
+#   norm            err = sqrt(mean_c (e_c / (atol + rtol max(|u_n,c|, |u_{n+1},c|)))^2)
+#                   over every component c of every element type; accept when
+#                   err <= 1
+#   step control    PI controller with exponents 0.7/k and 0.4/k, k = 4 (the
+#                   estimate is O(dt^4)): accepted steps take
+#                   dt * clip(0.9 err^-0.175 err_prev^0.1, 0.2, 5) (at most 1
+#                   right after a rejection), rejected steps
+#                   dt * max(0.2, 0.9 err^-0.25); err_prev starts at 1.
+ADAPT_SAFETY = 0.9
+ADAPT_FACMIN = 0.2
+ADAPT_FACMAX = 5.0
+ADAPT_ALPHA = 0.7 / 4.0
+ADAPT_BETA = 0.4 / 4.0
+
+
+def embedded_step(rhs, u, dt):
+    """One RK4(3)5[2R+] step: (u_{n+1}, dt sum_i (b_i - bhat_i) k_i)."""
+    A, b = rk45_tableau()
+    d = b - RK45_BHAT
+    ks = []
+    for i in range(len(b)):
+        ui = {t: u[t] + dt * sum(A[i, j] * ks[j][t] for j in range(i)
+                                 if A[i, j] != 0.0)
+              for t in u}
+        ks.append(rhs(ui))
+    u1 = {t: u[t] + dt * sum(b[j] * ks[j][t] for j in range(len(b))) for t in u}
+    e = {t: dt * sum(d[j] * ks[j][t] for j in range(len(b))) for t in u}
+    return u1, e
+
+
+def error_norm(u0, u1, e, atol, rtol):
+    """Root mean square of e scaled by atol + rtol max(|u0|, |u1|)."""
+    s, n = 0.0, 0
+    for t in u0:
+        sc = atol + rtol * np.maximum(np.abs(u0[t]), np.abs(u1[t]))
+        s += float(np.sum((e[t] / sc) ** 2))
+        n += e[t].size
+    return float(np.sqrt(s / n))
+
+
+def next_dt(dt, err, err_prev, after_reject):
+    """Step size after a step of size dt with normalised error err."""
+    if err <= 1.0:
+        fac = ADAPT_SAFETY * max(err, 1e-10) ** -ADAPT_ALPHA * err_prev ** ADAPT_BETA
+        fac = min(max(fac, ADAPT_FACMIN), ADAPT_FACMAX)
+        if after_reject:
+            fac = min(fac, 1.0)
+    else:
+        fac = max(ADAPT_FACMIN, ADAPT_SAFETY * err ** -0.25)
+    return dt * fac
+
+
+def adaptive_step(rhs, u, dt, atol, rtol, state):
+    """One attempted adaptive step.  state: {"err_prev", "rejected"} (updated).
+    Returns (u_next, accepted, err, dt_next); u_next is u when rejected."""
+    u1, e = embedded_step(rhs, u, dt)
+    err = error_norm(u, u1, e, atol, rtol)
+    accepted = err <= 1.0
+    dt_next = next_dt(dt, err, state["err_prev"], state["rejected"])
+    if accepted:
+        state["err_prev"] = max(err, 1e-4)
+        state["rejected"] = False
+        return u1, True, err, dt_next
+    state["rejected"] = True
+    return u, False, err, dt_next
