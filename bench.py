@@ -420,6 +420,47 @@ def config_vortex(fr, torch, device):
     return out
 
 
+def config_tgv_adaptive(fr, torch, device, attempts=30):
+    """TGV 32^3 p=3 (the bench workload) in FP32 with adaptive RK45 steps
+    (Section 3.5): atol = rtol = 1e-6 from dt = 1e-3.  Every attempt is one
+    graph (stages + embedded error + norm) plus the host's accept / reject
+    decision; the time covers all attempts, rejected ones included."""
+    spec = workload_spec(N_CELLS)
+    mesh = fr.FRMesh(spec, ORDER, physics="ns", gamma=1.4, mu=1.0 / RE,
+                     prandtl=PR, precision="fp32", device=device)
+    st = torch.cuda.Stream(device=device)
+    mesh.set_stream(st)
+    mesh.set_solution(_state(mesh, tgv))
+    mesh.rk_step("rk45", 1e-3, 2)     # tuning and warm-up
+    ctl = fr.AdaptCtl(1e-6, 1e-6, 1.0, 0)
+    dt, log = 1e-3, []
+    for _ in range(3):                # warm-up attempts (graph build)
+        ok, err, dt = mesh.rk_adaptive_step(dt, ctl)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(st)
+    for _ in range(attempts):
+        h = dt
+        ok, err, dt = mesh.rk_adaptive_step(h, ctl)
+        log.append((ok, err, h))
+    t1.record(st)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    fixed = _timed_steps(torch, mesh, st, "rk45", 1e-4, attempts)
+    acc = [x for x in log if x[0]]
+    out = {"attempts": attempts, "accepted": len(acc),
+           "rejected": attempts - len(acc),
+           "ms_per_attempt": ms / attempts,
+           "ms_per_fixed_step": fixed / attempts,
+           "gdof_stage_s": _gdofs(mesh, 5, attempts, ms),
+           "dt_first_last": [log[0][2], log[-1][2]],
+           "err_mean_accepted": float(np.mean([x[1] for x in acc])) if acc else None,
+           "tolerance": 1e-6}
+    mesh.close()
+    return out
+
+
 def config_tgv48_mixed(fr, torch, device, steps=10, dt=2.5e-4):
     """TGV on 48^3 perturbed hexes, p=4, RK45 dt 2.5e-4 (1e-3 is beyond the
     explicit limit at this h and p): mixed precision against the FP64 form
@@ -539,6 +580,7 @@ def other_configs(fr, torch, device):
     for name, fn in (("vortex_8^3_p2_fp64", config_vortex),
                      ("tgv_48^3_p4_mixed", config_tgv48_mixed),
                      ("mixed_elements_40^3_p3_fp32", config_mixed_elements),
+                     ("tgv_32^3_p3_fp32_adaptive", config_tgv_adaptive),
                      ("shu_osher_256x8x8_p3_filter", config_shu_osher)):
         try:
             out[name] = fn(fr, torch, device)
@@ -627,7 +669,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", default=None,
-                    choices=["vortex", "tgv48", "mixed", "shu_osher"],
+                    choices=["vortex", "tgv48", "mixed", "shu_osher", "adaptive"],
                     help="run one side workload alone and print its record "
                          "(profiling aid; not a contract line)")
     ap.add_argument("--cells", type=int, default=40,
@@ -644,6 +686,7 @@ def main():
         dev = 0
         torch.cuda.set_device(dev)
         fns = {"vortex": config_vortex, "tgv48": config_tgv48_mixed,
+               "adaptive": config_tgv_adaptive,
                "shu_osher": config_shu_osher,
                "mixed": lambda f, t, d: config_mixed_elements(
                    f, t, d, steps=args.steps, cells=args.cells,

@@ -152,6 +152,26 @@ int fr_get_rhs(const fr_mesh* mesh, int etype, double* rhs);
  * CUDA graph.  Returns FR_ENONFINITE if any stage produced NaN/Inf. */
 int fr_rk_step(fr_mesh* mesh, int scheme, double dt, int nsteps);
 
+/* Adaptive time stepping (Section 3.5, low-storage RK with an embedded
+ * pair).  One attempted FR_RK45 step of size *dt: the embedded third-order
+ * weights bhat give the error estimate e = dt sum_i (b_i - bhat_i) k_i; its
+ * norm err = sqrt(mean_c (e_c / (atol + rtol max(|u^n_c|, |u^{n+1}_c|)))^2)
+ * over every component c of every element decides acceptance (err <= 1; a
+ * rejected step restores u^n).  *dt receives the next step size from a PI
+ * controller: accepted steps dt * clip(0.9 err^-0.175 err_prev^0.1, 0.2, 5)
+ * (at most dt right after a rejection), rejected ones
+ * dt * max(0.2, 0.9 err^-0.25).  The controller state is the caller's
+ * (`ctl`: set atol, rtol; start with err_prev = 1, after_reject = 0).  A
+ * stage that produces NaN/Inf counts as a rejection (err = +inf).  Not
+ * available with the entropy filter (FR_EINVAL). */
+typedef struct {
+  double atol, rtol;  /* tolerances of the error norm */
+  double err_prev;    /* norm of the last accepted step (controller memory) */
+  int after_reject;   /* 1 when the previous attempt was rejected */
+} fr_adapt_t;
+int fr_rk_adaptive_step(fr_mesh* mesh, fr_adapt_t* ctl, double* dt, int* accepted,
+                        double* err);
+
 /* Measurement aid: advances the solution by ONE step of `scheme` exactly
  * as fr_rk_step does, but launches the kernels one by one (no graph) with
  * CUDA events around every launch on the handle's stream.  On return

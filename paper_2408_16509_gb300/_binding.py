@@ -81,6 +81,8 @@ def load():
         "fr_rhs": (I, [P]),
         "fr_get_rhs": (I, [P, I, P]),
         "fr_rk_step": (I, [P, I, D, I]),
+        "fr_rk_adaptive_step": (I, [P, C.POINTER(AdaptCtl), C.POINTER(D),
+                                    C.POINTER(I), C.POINTER(D)]),
         "fr_set_stream": (I, [P, P]),
         "fr_sync": (I, [P]),
         "fr_last_error": (C.c_char_p, []),
@@ -111,6 +113,12 @@ def load():
 def _check(rc):
     if rc != FR_OK:
         raise FRError(rc, load().fr_last_error().decode())
+
+
+class AdaptCtl(C.Structure):
+    """fr_adapt_t: tolerances and the PI controller's memory."""
+    _fields_ = [("atol", C.c_double), ("rtol", C.c_double),
+                ("err_prev", C.c_double), ("after_reject", C.c_int)]
 
 
 def _ptr(a):
@@ -248,6 +256,31 @@ class FRMesh:
     def rk_step(self, scheme, dt, nsteps=1):
         _check(load().fr_rk_step(self._h, SCHEMES[scheme], float(dt),
                                  int(nsteps)))
+
+    def rk_adaptive_step(self, dt, ctl):
+        """One attempted adaptive RK45 step (fr_rk_adaptive_step).  `ctl` is
+        an AdaptCtl, updated in place.  Returns (accepted, err, dt_next)."""
+        d = C.c_double(float(dt))
+        acc = C.c_int(0)
+        err = C.c_double(0.0)
+        _check(load().fr_rk_adaptive_step(self._h, C.byref(ctl), C.byref(d),
+                                          C.byref(acc), C.byref(err)))
+        return bool(acc.value), err.value, d.value
+
+    def integrate_adaptive(self, t_end, dt, atol, rtol, max_attempts=100000):
+        """Adaptive RK45 steps from t = 0 to t_end (the last step shortened
+        to land on t_end).  Returns a list of (t_after, dt, accepted, err)."""
+        ctl = AdaptCtl(atol, rtol, 1.0, 0)
+        t, log = 0.0, []
+        for _ in range(max_attempts):
+            if t >= t_end - 1e-14 * max(1.0, abs(t_end)):
+                break
+            h = min(dt, t_end - t)
+            ok, err, dt = self.rk_adaptive_step(h, ctl)
+            if ok:
+                t += h
+            log.append((t, h, ok, err))
+        return log
 
     KERNEL_CLASSES = ("face_ucommon", "bnd_ucommon", "grad", "face_flux",
                       "bnd_flux", "volume", "filter")

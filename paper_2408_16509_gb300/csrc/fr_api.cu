@@ -119,6 +119,8 @@ struct DevType {
   bool tc_grad_on = true;    // kernels on the tensor cores when the family
   bool tc_vol_on = true;     //   is TENSOR (the tuner decides per type)
   void* tcimg = nullptr;     // split-TF32 operator image
+  void* E = nullptr;         // embedded-error register (adaptive steps)
+  void* Xs = nullptr;        // solution at the start of an adaptive step
   void* tcaimg = nullptr;    // the same, output points padded to 16
   TcGeom tcgeo{};
   int tc_vol_ctas = 1, tc_grad_ctas = 1;
@@ -164,14 +166,21 @@ struct fr_mesh {
   int* d_flag = nullptr;
   double h_dt = 0.0;
   bool uf_valid = false;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
-  cudaStream_t graph_stream[2] = {nullptr, nullptr};
+  // RK step graphs: FR_RK4, FR_RK45, and the adaptive RK45 step (index 2)
+  cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
+  cudaStream_t graph_stream[3] = {nullptr, nullptr, nullptr};
   int variant = FR_VARIANT_AUTO;   // requested kernel family
   int active = FR_VARIANT_SUMFACT; // family in use (the tuner's choice)
   bool tuned = false;
   float tune_ms[5] = {0, 0, 0, 0, 0}; // ms per step of each family tried
   long long epoch = 0;            // bumped by every change of launch config
-  long long graph_epoch[2] = {-1, -1};
+  long long graph_epoch[3] = {-1, -1, -1};
+  bool err_on = false;        // stage epilogues accumulate the embedded error
+  double* d_errpart = nullptr;  // per-block partial sums of the error norm
+  double* d_errsum = nullptr;   // total
+  double* d_tol = nullptr;      // atol, rtol
+  double h_tol[2] = {0.0, 0.0};
+  int n_errpart = 0;
   bool filter_on = false;
   bool mlp_on = false;
   FilterStats* d_fstats = nullptr;
@@ -185,7 +194,7 @@ struct fr_mesh {
   size_t staging_bytes = 0;
 
   ~fr_mesh() {
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 3; ++i)
       if (graph[i]) cudaGraphExecDestroy(graph[i]);
     free_all(allocs);
     if (d_staging) cudaFree(d_staging);
@@ -887,6 +896,7 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
     if (use_hex(m, D)) {
       HexStage<T, TR> sa{mode, stage, (TR*)D.X, (TR*)D.A, (T*)D.Y, (T*)D.R,
                          m->d_dt, m->d_flag, uf_next};
+      sa.E = m->err_on ? (TR*)D.E : nullptr;
       hex_dispatch(m->order, [&](auto n) {
         constexpr int N = decltype(n)::value;
         constexpr int E = hex_epb<N>();
@@ -915,6 +925,7 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
     } else if (use_tc_vol(m, D)) {
       HexStage<T, TR> sa{mode, stage, (TR*)D.X, (TR*)D.A, (T*)D.Y, (T*)D.R,
                          m->d_dt, m->d_flag, uf_next};
+      sa.E = m->err_on ? (TR*)D.E : nullptr;
       launch_vol_tc<T, TR>(m, D, s, from_x, ns, fc, ph, sa);
     } else {
       StageArgs<T> sa;
@@ -927,6 +938,7 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
       sa.dt = m->d_dt;
       sa.flag = m->d_flag;
       sa.uf_next = uf_next;
+      sa.E = m->err_on ? (T*)D.E : nullptr;
       const T* uin = from_x ? (const T*)D.X : (const T*)D.Y;
       dispatch(D.kind, m->order, [&](auto nu, auto nf) {
         constexpr int NU = decltype(nu)::value, NF = decltype(nf)::value;
@@ -1037,13 +1049,80 @@ int do_rhs(fr_mesh* m) {
   return FR_OK;
 }
 
+// ---------------------------------------------------------------- adaptive
+constexpr int kAdaptive = 2;      // graph index of the adaptive RK45 step
+constexpr int kErrBlocks = 256;   // partial sums per element type
+
+// Sum of (e / (atol + rtol max(|x0|, |x1|)))^2 over n components, one
+// partial sum per block (fixed grid and order: deterministic).  C is the
+// arithmetic type of the scaled error (FP64 for FP64 values, else FP32).
+template <typename TR, typename C>
+__global__ void __launch_bounds__(256)
+    k_err_partial(long long n, const TR* __restrict__ x0, const TR* __restrict__ x1,
+                  const TR* __restrict__ e, const double* __restrict__ tol,
+                  double* __restrict__ part) {
+  __shared__ double red[8];
+  const C atol = C(tol[0]), rtol = C(tol[1]);
+  C acc = C(0);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const C sc = atol + rtol * fmax(fabs(C(x0[i])), fabs(C(x1[i])));
+    const C q = C(e[i]) / sc;
+    acc += q * q;
+  }
+  double v = double(acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_err_final(int np, const double* __restrict__ part,
+                            double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < np; ++i) t += part[i];
+    out[0] = t;
+  }
+}
+
+template <typename T, typename TR>
+void launch_err_norm(fr_mesh* m, cudaStream_t s) {
+  using C = typename std::conditional<sizeof(T) == 8, double, float>::type;
+  int off = 0;
+  for (auto& D : m->types) {
+    const long long n = D.ne * 5 * D.nu;
+    k_err_partial<TR, C><<<kErrBlocks, 256, 0, s>>>(n, (const TR*)D.Xs, (const TR*)D.X,
+                                                    (const TR*)D.E, m->d_tol,
+                                                    m->d_errpart + off);
+    off += kErrBlocks;
+  }
+  k_err_final<<<1, 32, 0, s>>>(off, m->d_errpart, m->d_errsum);
+}
+
 template <typename T, typename TR>
 int build_graph(fr_mesh* m, int scheme) {
   cudaStream_t s = m->stream;
   CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-  const int nst = scheme == FR_RK4 ? 4 : 5;
-  for (int st = 0; st < nst; ++st)
-    launch_stage<T, TR>(m, s, scheme == FR_RK4 ? 1 : 2, st);
+  if (scheme == kAdaptive) {
+    // save u^n, five RK45 stages accumulating the embedded error, error norm
+    for (auto& D : m->types)
+      cudaMemcpyAsync(D.Xs, D.X, size_t(D.ne) * 5 * D.nu * sizeof(TR),
+                      cudaMemcpyDeviceToDevice, s);
+    m->err_on = true;
+    for (int st = 0; st < 5; ++st) launch_stage<T, TR>(m, s, 2, st);
+    m->err_on = false;
+    launch_err_norm<T, TR>(m, s);
+  } else {
+    const int nst = scheme == FR_RK4 ? 4 : 5;
+    for (int st = 0; st < nst; ++st)
+      launch_stage<T, TR>(m, s, scheme == FR_RK4 ? 1 : 2, st);
+  }
   cudaGraph_t g;
   cudaError_t e = cudaStreamEndCapture(s, &g);
   if (e != cudaSuccess)
@@ -1248,6 +1327,86 @@ int do_rk(fr_mesh* m, int scheme, double dt, int nsteps) {
   return FR_OK;
 }
 
+// One attempted adaptive step (Section 3.5): the stages, the embedded error
+// estimate and its norm run in kernels captured as one graph; acceptance,
+// the restore of a rejected step and the PI step-size controller are host
+// logic on the norm.
+template <typename T, typename TR>
+int do_rk_adaptive(fr_mesh* m, fr_adapt_t* ctl, double* dt, int* accepted, double* err) {
+  if (m->filter_on)
+    return fail(FR_EINVAL, "adaptive steps with the entropy filter are not supported");
+  if (!(*dt > 0.0) || !(ctl->atol >= 0.0) || !(ctl->rtol >= 0.0) ||
+      !(ctl->atol + ctl->rtol > 0.0) || !(ctl->err_prev > 0.0))
+    return fail(FR_EINVAL, "adaptive step: dt, tolerances and err_prev must be positive");
+  int rc = resolve_variant<T, TR>(m, FR_RK45, *dt);
+  if (rc) return rc;
+  if (!m->d_errsum) {
+    for (auto& D : m->types) {
+      const size_t bytes = size_t(D.ne) * 5 * D.nu * sizeof(TR);
+      if ((rc = dev_zeros(m, bytes, &D.E))) return rc;
+      if ((rc = dev_zeros(m, bytes, &D.Xs))) return rc;
+    }
+    m->n_errpart = kErrBlocks * int(m->types.size());
+    void* p = nullptr;
+    if ((rc = dev_zeros(m, size_t(m->n_errpart) * sizeof(double), &p))) return rc;
+    m->d_errpart = (double*)p;
+    if ((rc = dev_zeros(m, sizeof(double), &p))) return rc;
+    m->d_errsum = (double*)p;
+    if ((rc = dev_zeros(m, 2 * sizeof(double), &p))) return rc;
+    m->d_tol = (double*)p;
+  }
+  rc = ensure_uf<T, TR>(m);
+  if (rc) return rc;
+  if (!m->graph[kAdaptive] || m->graph_stream[kAdaptive] != m->stream ||
+      m->graph_epoch[kAdaptive] != m->epoch) {
+    if ((rc = build_graph<T, TR>(m, kAdaptive))) return rc;
+  }
+  m->h_dt = *dt;
+  m->h_tol[0] = ctl->atol;
+  m->h_tol[1] = ctl->rtol;
+  CK(cudaMemcpyAsync(m->d_dt, &m->h_dt, sizeof(double), cudaMemcpyHostToDevice, m->stream));
+  CK(cudaMemcpyAsync(m->d_tol, m->h_tol, 2 * sizeof(double), cudaMemcpyHostToDevice,
+                     m->stream));
+  CK(cudaMemsetAsync(m->d_flag, 0, sizeof(int), m->stream));
+  CK(cudaGraphLaunch(m->graph[kAdaptive], m->stream));
+  int flag = 0;
+  double sum = 0.0;
+  CK(cudaMemcpyAsync(&flag, m->d_flag, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+  CK(cudaMemcpyAsync(&sum, m->d_errsum, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+  CK(cudaStreamSynchronize(m->stream));
+  if (flag & 2) return fail(FR_ETIMEOUT, "a tensor-core wait timed out");
+  long long ncomp = 0;
+  for (auto& D : m->types) ncomp += D.ne * 5 * D.nu;
+  // a non-finite stage counts as a rejection
+  const double e = flag ? INFINITY : std::sqrt(sum / double(ncomp));
+  const bool ok = e <= 1.0;
+  if (!ok) {  // restore u^n; its flux-point traces are recomputed on demand
+    for (auto& D : m->types)
+      CK(cudaMemcpyAsync(D.X, D.Xs, size_t(D.ne) * 5 * D.nu * sizeof(TR),
+                         cudaMemcpyDeviceToDevice, m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+    m->uf_valid = false;
+  }
+  // PI controller: exponents 0.7/4 and 0.4/4 (the estimate is O(dt^4)),
+  // safety 0.9, factors clipped to [0.2, 5], no growth right after a
+  // rejection; a rejected step shrinks by max(0.2, 0.9 err^-1/4)
+  double fac;
+  if (ok) {
+    fac = 0.9 * std::pow(std::max(e, 1e-10), -0.7 / 4.0) * std::pow(ctl->err_prev, 0.4 / 4.0);
+    fac = std::min(std::max(fac, 0.2), 5.0);
+    if (ctl->after_reject) fac = std::min(fac, 1.0);
+    ctl->err_prev = std::max(e, 1e-4);
+    ctl->after_reject = 0;
+  } else {
+    fac = std::max(0.2, 0.9 * std::pow(e, -0.25));
+    ctl->after_reject = 1;
+  }
+  *dt *= fac;
+  *accepted = ok ? 1 : 0;
+  *err = e;
+  return FR_OK;
+}
+
 template <typename T, typename TR>
 int do_profile(fr_mesh* m, int scheme, double dt, double* ms, int* launches) {
   int rc = resolve_variant<T, TR>(m, scheme, dt);
@@ -1383,8 +1542,17 @@ int fr_mesh_create(const fr_mesh_desc* d, fr_mesh** out) {
                          -1672844663538.0 / 4480602732383.0,
                          2114624349019.0 / 3568978502595.0,
                          5198255086312.0 / 14908931495163.0};
+    // embedded third-order weights of the same publication
+    const double bh[5] = {1016888040809.0 / 7410784769900.0,
+                          11231460423587.0 / 58533540763752.0,
+                          -1563879915014.0 / 6823010717585.0,
+                          606302364029.0 / 971179775848.0,
+                          1097981568119.0 / 3980877426909.0};
+    double eb[5];
+    for (int i = 0; i < 5; ++i) eb[i] = b[i] - bh[i];
     CK(cudaMemcpyToSymbol(c_rk45_a, a, sizeof(a)));
     CK(cudaMemcpyToSymbol(c_rk45_b, b, sizeof(b)));
+    CK(cudaMemcpyToSymbol(c_rk45_e, eb, sizeof(eb)));
     consts_done[dev] = true;
   }
   if (m->precision == FR_MIXED)
@@ -1578,6 +1746,14 @@ int fr_rk_step(fr_mesh* m, int scheme, double dt, int nsteps) {
   if (nsteps == 0) return FR_OK;
   CK(cudaSetDevice(m->device));
   return FR_PREC(m, do_rk, m, scheme, dt, nsteps);
+}
+
+int fr_rk_adaptive_step(fr_mesh* m, fr_adapt_t* ctl, double* dt, int* accepted,
+                        double* err) {
+  if (!m || !ctl || !dt || !accepted || !err) return fail(FR_EINVAL, "null argument");
+  if (m->host_only) return fail(FR_EINVAL, "host-only handle (device < 0)");
+  CK(cudaSetDevice(m->device));
+  return FR_PREC(m, do_rk_adaptive, m, ctl, dt, accepted, err);
 }
 
 int fr_profile_step(fr_mesh* m, int scheme, double dt, double* ms,

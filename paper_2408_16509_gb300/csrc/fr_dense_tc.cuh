@@ -869,6 +869,19 @@ __device__ __forceinline__ void tc_stage_row(const HexStage<float, float>& a,
   }
   tc_row_store<N>(a.X + i0, vec, xo);
   if (st < 4) tc_row_store<N>(a.Y + i0, vec, s);
+  if (a.E) {  // error estimate dt sum_i (b_i - bhat_i) R_i
+    const float ec = float(c_rk45_e[st]);
+    float ev[N];
+    if (st > 0) {
+      tc_row_load<N>(a.E + i0, vec, ev);
+    } else {
+#pragma unroll
+      for (int z = 0; z < N; ++z) ev[z] = 0.f;
+    }
+#pragma unroll
+    for (int z = 0; z < N; ++z) ev[z] = st == 0 ? ec * dt * R[z] : ev[z] + ec * dt * R[z];
+    tc_row_store<N>(a.E + i0, vec, ev);
+  }
 }
 
 template <int NU, int NF, int M, bool NS>

@@ -38,6 +38,7 @@ struct HexStage {
   const double* dt;
   int* flag;
   T* uf_next;
+  TR* E = nullptr;  // embedded-error register of an adaptive step (or nullptr)
 };
 
 template <int N>
@@ -116,6 +117,10 @@ __device__ __forceinline__ void hex_stage_apply(const HexStage<T, TR>& a,
     const TR r = TR(R[k]);
     const TR xx = x[k] + b * dt * r;
     a.X[i] = xx;
+    if (a.E) {  // error estimate dt sum_i (b_i - bhat_i) R_i
+      const TR ev = TR(c_rk45_e[st]) * dt * r;
+      a.E[i] = st == 0 ? ev : a.E[i] + ev;
+    }
     if (st < 4) {
       const T y = T(xx + am * dt * r);
       a.Y[i] = y;

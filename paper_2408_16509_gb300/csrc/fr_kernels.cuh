@@ -54,10 +54,12 @@ struct StageArgs {
   const double* dt;  // device scalar
   int* flag;         // non-finite flag (bit 0)
   T* uf_next;        // flux-point buffer for the next stage (or nullptr)
+  T* E = nullptr;    // embedded-error register of an adaptive step (or nullptr)
 };
 
 __constant__ double c_rk45_a[4];  // sub-diagonal a_{i+1,i}
 __constant__ double c_rk45_b[5];
+__constant__ double c_rk45_e[5];  // b_i - bhat_i (embedded pair)
 
 __device__ __forceinline__ void decode_fp(int32_t code, const TypeTab& tt,
                                           int* t, long long* e, int* f) {
@@ -125,6 +127,10 @@ __device__ __forceinline__ void stage_update(const StageArgs<T>& a,
     long long i = idx0 + k * vstr;
     T x = (st == 0 ? u[k] : a.X[i]) + b * dt * R[k];
     a.X[i] = x;
+    if (a.E) {  // error estimate dt sum_i (b_i - bhat_i) R_i
+      const T ev = T(c_rk45_e[st]) * dt * R[k];
+      a.E[i] = st == 0 ? ev : a.E[i] + ev;
+    }
     if (st < 4) {
       s[k] = x + am * dt * R[k];
       a.Y[i] = s[k];
