@@ -157,6 +157,13 @@ def kernel_models(nu, nf, ne, w, wr, npair):
     return bytes_, flops
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, mean
+# of two launches of one ncu capture) of the volume kernel of the 32^3 p=3
+# workload, for the kernel version these counters were taken on.  Any
+# change to that kernel must refresh or drop the entry (traffic -> null).
+MEASURED_TRAFFIC = {("fp64", "volume"): 969768960, ("fp32", "volume"): 467274496}
+
+
 def roofline(prof, models, peaks, src, precision):
     """Roofline record of the dominant kernel class: the bound is whichever
     of DRAM bytes / HBM peak and flops / arithmetic peak takes longer."""
@@ -181,6 +188,7 @@ def roofline(prof, models, peaks, src, precision):
                "peak": peaks["hbm_gbs"], "unit": "GB/s",
                "frac": bw / peaks["hbm_gbs"], "traffic": None,
                "peak_source": src + " hbm_gbs (MEASURED_PEAKS.json)"}
+    out["traffic"] = MEASURED_TRAFFIC.get((precision, dom))
     out.update({"launches_per_step": prof[dom][1], "kernel_ms": t * 1e3,
                 "algorithmic_bytes": b, "algorithmic_flops": f,
                 "achieved_gbs": bw, "achieved_tflops": fl,
