@@ -9,6 +9,10 @@ Vertex order conventions (the library's documented input format):
 
 Boundary nodes of periodic directions are distinct nodes; periodic faces are
 paired by the translation vectors returned in ``periodic``.
+
+Curved (quadratic) hexahedra carry, besides their 8 corner ids, the ids of
+27 map nodes in tensor order: node a + 3 b + 9 c sits at reference point
+(-1 + a, -1 + b, -1 + c), a, b, c in {0, 1, 2} (``maps``).
 """
 from dataclasses import dataclass, field
 
@@ -21,10 +25,12 @@ class MeshSpec:
     elements: dict
     periodic: list = field(default_factory=list)
     bfaces: list = field(default_factory=list)    # [(node ids, tag)]
+    maps: dict = field(default_factory=dict)      # {etype: (order, map node ids)}
 
     def as_dict(self):
         return {"nodes": self.nodes, "elements": self.elements,
-                "periodic": self.periodic, "bfaces": self.bfaces}
+                "periodic": self.periodic, "bfaces": self.bfaces,
+                "maps": self.maps}
 
     @property
     def n_elements(self):
@@ -217,3 +223,49 @@ def _plane_faces(elements, plane_nodes, _unused, tag):
             if len(vs) == want:
                 out.append((tuple(vs), tag))
     return out
+
+
+def curved_box_hex(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), periodic=(0, 1, 2),
+                   amp=0.05, tags=None):
+    """Box of n[0] x n[1] x n[2] curved hexahedra with quadratic maps.
+
+    The (2n+1)^3 lattice of corner, mid-edge, mid-face and centre nodes is
+    displaced by d_k = amp h_k (sin(pi n_{k+1} X_{k+1}) + sin(pi n_{k+2}
+    X_{k+2})) (1 + cos(2 pi n_k X_k) / 2) (X the box coordinates scaled to
+    [0, 1], indices cyclic).  Corners stay on the grid (the sines vanish
+    there), the field is the same on opposite box sides (faces pair by their
+    corner ids or periodic translation), and each component depends on all
+    three coordinates, so the map's cofactors are of high degree.
+    """
+    n = tuple(int(v) for v in n)
+    m = tuple(2 * v for v in n)
+    lo_a, hi_a = np.asarray(lo, float), np.asarray(hi, float)
+    nodes = _grid_nodes(m, lo, hi)
+    L = hi_a - lo_a
+    h = L / np.asarray(n, float)
+    X = (nodes - lo_a) / L
+    sn = [np.sin(np.pi * n[k] * X[:, k]) for k in range(3)]
+    d = np.stack([h[k] * (sn[(k + 1) % 3] + sn[(k + 2) % 3])
+                  * (1.0 + 0.5 * np.cos(2.0 * np.pi * n[k] * X[:, k]))
+                  for k in range(3)], axis=1)
+    nodes = nodes + amp * d
+    g = _nid(m)
+    I, J, K = _hex_cells(n)
+    a = np.arange(3)
+    A, B, C = np.meshgrid(a, a, a, indexing="ij")
+    A, B, C = (v.transpose(2, 1, 0).ravel() for v in (A, B, C))   # a fastest
+    hmap = g(2 * I[:, None] + A[None, :], 2 * J[:, None] + B[None, :],
+             2 * K[:, None] + C[None, :])
+    corner = hmap[:, [0, 2, 8, 6, 18, 20, 26, 24]]
+    pv = []
+    for dd in periodic:
+        T = np.zeros(3)
+        T[dd] = hi[dd] - lo[dd]
+        pv.append(T)
+    if tags is None:
+        tags = {(dd, s_): 2 * dd + s_ for dd in range(3) for s_ in (0, 1)}
+    # boundary faces on the half-spacing lattice: corner ids of each quad
+    f2 = lambda i, j, k: g(2 * i, 2 * j, 2 * k)  # noqa: E731
+    bf = _boundary_faces(n, f2, set(periodic), tags)
+    return MeshSpec(nodes, {"hex": corner.astype(np.int64)}, pv, bf,
+                    {"hex": (2, hmap.astype(np.int64))})

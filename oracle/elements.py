@@ -223,6 +223,29 @@ class Hex(ElementType):
         return np.stack(out)
 
 
+    # quadratic map (27 nodes, tensor order a + 3b + 9c at (-1+a, -1+b, -1+c))
+    @staticmethod
+    def _lag2(s):
+        """Quadratic Lagrange polynomials on {-1, 0, 1} and their slopes."""
+        v = np.stack([0.5 * s * (s - 1.0), 1.0 - s * s, 0.5 * s * (s + 1.0)], axis=-1)
+        d = np.stack([s - 0.5, -2.0 * s, s + 0.5], axis=-1)
+        return v, d
+
+    def q2_shape(self, x):
+        """(npts, 27) values of the quadratic map's basis at points x."""
+        v = [self._lag2(x[:, i])[0] for i in range(3)]
+        return np.einsum("pa,pb,pc->pcba", v[0], v[1], v[2]).reshape(len(x), 27)
+
+    def q2_dshape(self, x):
+        """(3, npts, 27): derivative along x~_j of each quadratic basis function."""
+        vd = [self._lag2(x[:, i]) for i in range(3)]
+        out = []
+        for j in range(3):
+            f = [vd[i][1] if i == j else vd[i][0] for i in range(3)]
+            out.append(np.einsum("pa,pb,pc->pcba", f[0], f[1], f[2]).reshape(len(x), 27))
+        return np.stack(out)
+
+
 class Prism(ElementType):
     name = "pri"
     nverts = 6

@@ -8,6 +8,11 @@ partner with the same physical coordinates.
 
 * metrics: S = det(J) J^{-1} at solution and flux points, straight from the
   vertex map (linear elements, Section 3.4: metrics from the vertices);
+* curved elements (hexahedra with a quadratic 27-node map, "Curved
+  Elements" of Section 3.4): the conservative metric, i.e. the curl form
+  S[i][n] = -(curl_xi I(X_l grad_xi X_m))_i, (n, m, l) cyclic, with I the
+  order-p interpolation on the Gauss-Lobatto nodes, evaluated at the
+  solution and flux points; det J is the map's own;
 * surface normal at a flux point: S^T n~ (Nanson), split into its magnitude
   and the physical unit normal;
 * faces are paired by their vertex sets; faces left over are paired
@@ -20,12 +25,44 @@ import numpy as np
 from scipy.spatial import cKDTree
 
 from .elements import element
+from .polys import dlagrange_matrix, gauss_lobatto, lagrange_matrix
 
 ETYPE_ORDER = ("hex", "pri", "tet")
 
 
 class MeshError(ValueError):
     pass
+
+
+def curl_metric(el, Xm, pts):
+    """Conservative (curl-form) metric of quadratic hexahedron maps at the
+    reference points pts.  Xm: (ne, 27, 3) map nodes.  The fields
+    w^n_j = X_l dX_m/dxi_j ((n, m, l) cyclic) are interpolated by the
+    order-p tensor Lagrange polynomial on the (p+1)^3 Gauss-Lobatto nodes
+    (nodes on every face: a face's normal component depends on that face
+    only, so neighbours agree), and S[i][n] = -(curl_xi of it)_i at pts.
+    Returns S[e, q, i, n] (= det J dxi_i/dx_n)."""
+    g, _ = gauss_lobatto(el.p + 1)
+    n1 = len(g)
+    c, b, a = np.meshgrid(g, g, g, indexing="ij")
+    G = np.stack([a.ravel(), b.ravel(), c.ravel()], axis=1)      # x~_0 fastest
+    X = np.einsum("pv,evk->epk", el.q2_shape(G), Xm)
+    dX = np.einsum("jpv,evk->epjk", el.q2_dshape(G), Xm)        # d x_k / d xi_j
+    L = [lagrange_matrix(g, pts[:, i]) for i in range(3)]
+    dL = [dlagrange_matrix(g, pts[:, i]) for i in range(3)]
+
+    def tensor(f0, f1, f2):
+        return np.einsum("pa,pb,pc->pcba", f0, f1, f2).reshape(len(pts), n1 ** 3)
+    dB = [tensor(*(dL[i] if i == j else L[i] for i in range(3))) for j in range(3)]
+    S = np.zeros((Xm.shape[0], len(pts), 3, 3))
+    for n in range(3):
+        m, l = (n + 1) % 3, (n + 2) % 3
+        w = X[:, :, l, None] * dX[:, :, :, m]                    # w_j = X_l dX_m/dxi_j
+        for i in range(3):
+            j, k = (i + 1) % 3, (i + 2) % 3
+            S[:, :, i, n] = -(np.einsum("pg,eg->ep", dB[j], w[:, :, k])
+                              - np.einsum("pg,eg->ep", dB[k], w[:, :, j]))
+    return S
 
 
 class FRMesh:
@@ -50,14 +87,31 @@ class FRMesh:
         self.ne = {t: len(self.conn[t]) for t in self.types}
         self.upts_x, self.S_u, self.detJ = {}, {}, {}
         self.fpts_x, self.fnorm, self.fmag = {}, {}, {}
+        maps = spec.get("maps", {}) or {}
+        self.curved = {}
         for t in self.types:
             el, V = self.el[t], self.verts[t]
-            self.upts_x[t] = el.map_points(V, el.upts)
-            self.S_u[t], self.detJ[t] = el.metrics(V, el.upts)
+            morder, mconn = maps.get(t, (1, None))
+            self.curved[t] = morder == 2
+            if morder == 2:
+                if t != "hex":
+                    raise MeshError("quadratic maps are implemented for hexahedra")
+                Xm = nodes[np.asarray(mconn, np.int64)]
+                self.upts_x[t] = np.einsum("pv,evk->epk", el.q2_shape(el.upts), Xm)
+                self.S_u[t] = curl_metric(el, Xm, el.upts)
+                dX = np.einsum("jpv,evk->epjk", el.q2_dshape(el.upts), Xm)
+                self.detJ[t] = np.linalg.det(dX)
+                self.fpts_x[t] = np.einsum("pv,evk->epk", el.q2_shape(el.fpts), Xm)
+                Sf = curl_metric(el, Xm, el.fpts)
+            elif morder == 1:
+                self.upts_x[t] = el.map_points(V, el.upts)
+                self.S_u[t], self.detJ[t] = el.metrics(V, el.upts)
+                self.fpts_x[t] = el.map_points(V, el.fpts)
+                Sf, _ = el.metrics(V, el.fpts)
+            else:
+                raise MeshError(f"map order {morder} not implemented")
             if np.any(self.detJ[t] <= 0):
                 raise MeshError(f"non-positive Jacobian in {t} elements")
-            self.fpts_x[t] = el.map_points(V, el.fpts)
-            Sf, _ = el.metrics(V, el.fpts)
             nv = np.einsum("epij,pi->epj", Sf, el.fpts_norm)
             mag = np.linalg.norm(nv, axis=2)
             self.fmag[t] = mag

@@ -64,3 +64,21 @@ def lagrange_matrix(nodes, x):
             if m != j:
                 out[:, j] *= (x - nodes[m]) / (nodes[j] - nodes[m])
     return out
+
+
+def dlagrange_matrix(nodes, x):
+    """D[i, j] = l_j'(x_i): derivatives of the 1D Lagrange basis on ``nodes``."""
+    nodes = np.asarray(nodes, np.float64)
+    x = np.asarray(x, np.float64)
+    n = len(nodes)
+    out = np.zeros((len(x), n))
+    for j in range(n):
+        for k in range(n):
+            if k == j:
+                continue
+            term = np.full(len(x), 1.0 / (nodes[j] - nodes[k]))
+            for m in range(n):
+                if m != j and m != k:
+                    term *= (x - nodes[m]) / (nodes[j] - nodes[m])
+            out[:, j] += term
+    return out
