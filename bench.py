@@ -523,6 +523,36 @@ def config_mixed_elements(fr, torch, device, steps=20, cells=40, variant="auto")
     return out
 
 
+def config_tgv_curved(fr, torch, device, steps=10):
+    """TGV on 32^3 curved hexahedra (quadratic maps, Section 3.4; nodes moved
+    by 5% of the cell size in a smooth field) on [0, 2 pi]^3, p=3, NS Re
+    1600, RK45 dt 1e-3: FP64 and FP32 beside the straight-element workload.
+    Curved elements run the table-metric families only."""
+    from frinputs import curved_box_hex
+    t_setup = time.perf_counter()
+    spec = curved_box_hex((N_CELLS,) * 3, hi=(2 * np.pi,) * 3)
+    out = {}
+    for prec in ("fp64", "fp32"):
+        t0 = time.perf_counter()
+        mesh = fr.FRMesh(spec, ORDER, physics="ns", gamma=1.4, mu=1.0 / RE,
+                         prandtl=PR, precision=prec, device=device)
+        setup_s = time.perf_counter() - t0
+        st = torch.cuda.Stream(device=device)
+        mesh.set_stream(st)
+        u0 = _state(mesh, tgv)
+        mesh.set_solution(u0)
+        mesh.rk_step("rk45", 1e-3, 2)
+        mesh.set_solution(u0)
+        ms = _timed_steps(torch, mesh, st, "rk45", 1e-3, steps)
+        active, _ = mesh.tuning()
+        out[prec] = {"gdof_stage_s": _gdofs(mesh, 5, steps, ms),
+                     "ms_per_step": ms / steps, "kernel_family": active,
+                     "mesh_setup_s": setup_s}
+        mesh.close()
+    out["spec_s"] = time.perf_counter() - t_setup
+    return out
+
+
 def config_shu_osher(fr, torch, device, steps=40):
     """256x8x8 hexes on [-5,5]x[0,0.3125]^2, p=3, Euler, RK4 dt 9e-4, FP32,
     entropy filter: plain root-find, then the predictor trained on the
@@ -589,6 +619,7 @@ def other_configs(fr, torch, device):
                      ("tgv_48^3_p4_mixed", config_tgv48_mixed),
                      ("mixed_elements_40^3_p3_fp32", config_mixed_elements),
                      ("tgv_32^3_p3_fp32_adaptive", config_tgv_adaptive),
+                     ("tgv_32^3_p3_curved", config_tgv_curved),
                      ("shu_osher_256x8x8_p3_filter", config_shu_osher)):
         try:
             out[name] = fn(fr, torch, device)
@@ -677,7 +708,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", default=None,
-                    choices=["vortex", "tgv48", "mixed", "shu_osher", "adaptive"],
+                    choices=["vortex", "tgv48", "mixed", "shu_osher", "adaptive",
+                             "curved"],
                     help="run one side workload alone and print its record "
                          "(profiling aid; not a contract line)")
     ap.add_argument("--cells", type=int, default=40,
@@ -695,6 +727,7 @@ def main():
         torch.cuda.set_device(dev)
         fns = {"vortex": config_vortex, "tgv48": config_tgv48_mixed,
                "adaptive": config_tgv_adaptive,
+               "curved": config_tgv_curved,
                "shu_osher": config_shu_osher,
                "mixed": lambda f, t, d: config_mixed_elements(
                    f, t, d, steps=args.steps, cells=args.cells,

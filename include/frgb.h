@@ -59,7 +59,18 @@ typedef struct fr_mesh fr_mesh;
 typedef struct {
   int etype;            /* FR_HEX8, FR_PRI6 or FR_TET4 */
   int64_t n_elem;
-  const int64_t* conn;  /* [n_elem][n_vertices] node ids */
+  const int64_t* conn;  /* [n_elem][n_vertices] node ids (face pairing; and
+                           the map of straight elements) */
+  int map_order;        /* 0 or 1: straight elements (vertex map); 2:
+                           quadratic map (hexahedra only, Section 3.4
+                           "Curved Elements") given by map_conn */
+  const int64_t* map_conn;  /* map_order 2: [n_elem][27] node ids, node
+                               a + 3b + 9c at reference point (-1+a, -1+b,
+                               -1+c); its corner nodes must be the vertices
+                               of conn.  Metrics of curved elements: the
+                               conservative curl form
+                               S[i][n] = -(curl I(X_l grad X_m))_i, I the
+                               order-p interpolant on Gauss-Lobatto nodes */
 } fr_etype_desc;
 
 typedef struct {

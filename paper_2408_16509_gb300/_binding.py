@@ -32,7 +32,8 @@ class FRError(RuntimeError):
 
 class EtypeDesc(C.Structure):
     _fields_ = [("etype", C.c_int), ("n_elem", C.c_int64),
-                ("conn", C.POINTER(C.c_int64))]
+                ("conn", C.POINTER(C.c_int64)), ("map_order", C.c_int),
+                ("map_conn", C.POINTER(C.c_int64))]
 
 
 class BCDesc(C.Structure):
@@ -141,13 +142,21 @@ class FRMesh:
         nodes = np.ascontiguousarray(spec["nodes"], np.float64)
         self._keep = [nodes]
         ets = []
+        maps = spec.get("maps", {}) or {}
         for name, conn in spec["elements"].items():
             conn = np.ascontiguousarray(conn, np.int64)
             if len(conn) == 0:
                 continue
             self._keep.append(conn)
+            morder, mconn = maps.get(name, (1, None))
+            mptr = None
+            if morder == 2:
+                mconn = np.ascontiguousarray(mconn, np.int64)
+                self._keep.append(mconn)
+                mptr = mconn.ctypes.data_as(C.POINTER(C.c_int64))
             ets.append(EtypeDesc(ETYPES[name], len(conn),
-                                 conn.ctypes.data_as(C.POINTER(C.c_int64))))
+                                 conn.ctypes.data_as(C.POINTER(C.c_int64)),
+                                 int(morder), mptr))
         et_arr = (EtypeDesc * len(ets))(*ets)
         bfl = spec.get("bfaces", [])
         bnodes = np.full((max(len(bfl), 1), 4), -1, np.int64)

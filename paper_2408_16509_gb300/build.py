@@ -64,7 +64,7 @@ def build(force=False, verbose=False, ptxas_info=False):
     for src in CXX_SRCS:
         obj = os.path.join(OBJ_DIR, src + ".o")
         jobs.append([shutil.which("g++") or "g++", "-std=c++17", "-O2",
-                     "-fPIC", "-c", os.path.join(CSRC, src), "-o", obj,
+                     "-fPIC", "-pthread", "-c", os.path.join(CSRC, src), "-o", obj,
                      "-I" + INCLUDE])
     for src in CU_SRCS:
         obj = os.path.join(OBJ_DIR, src + ".o")
@@ -80,7 +80,7 @@ def build(force=False, verbose=False, ptxas_info=False):
         for lg in logs:
             sys.stdout.write(lg)
     objs = [os.path.join(OBJ_DIR, s + ".o") for s in CXX_SRCS + CU_SRCS]
-    _run([nvcc, "-shared", ARCH, "-o", LIB] + objs + ["-lcudart"])
+    _run([nvcc, "-shared", ARCH, "-o", LIB] + objs + ["-lcudart", "-lpthread"])
     return LIB
 
 

@@ -113,6 +113,7 @@ struct DevType {
   void* fnv = nullptr;       // [ne][3][nf] S^T n~ at flux points (NS)
   int8_t* fbc = nullptr;     // [ne][nf] boundary-condition index or -1 (NS)
   void* verts = nullptr;     // [ne][8][3] vertices minus vertex 0 (hex, FP32)
+  bool curved = false;       // quadratic map: metrics only from the tables
   // tensor-core kernels (prisms / tetrahedra, FP32 values)
   bool tc_ok = false;
   bool tca_ok = false;       // data-as-A volume kernel available
@@ -360,6 +361,7 @@ int setup_device(fr_mesh* m) {
     const HostType& H = m->host[t];
     DevType D;
     D.kind = H.kind;
+    D.curved = H.map_order == 2;
     D.nu = H.ref.nupts;
     D.nf = H.ref.nfpts;
     D.ne = H.ne;
@@ -421,7 +423,7 @@ int setup_device(fr_mesh* m) {
     if (D.kind == EK_HEX) {
       D.hx64 = hex_ops<double>(R);
       D.hx32 = hex_ops<float>(R);
-      if (sizeof(T) == 4) {  // vertex metrics for the FP32-value kernels
+      if (sizeof(T) == 4 && !D.curved) {  // vertex metrics for the FP32-value kernels
         std::vector<double> xv(size_t(D.ne) * 24);
         for (long long e = 0; e < D.ne; ++e)
           for (int v = 0; v < 8; ++v)
@@ -819,7 +821,7 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
       ViscArgs<T> va{(const T*)m->uf + D.off_f, (const T*)D.fnv, D.fbc,
                      (T*)m->gradf + D.off_f * (sizeof(T) == 4 ? 1 : 3)};
       PROF_BEGIN(FR_KC_GRAD);
-      if (use_hex(m, D) && sizeof(T) == 4 &&
+      if (use_hex(m, D) && sizeof(T) == 4 && D.verts &&
           m->active == FR_VARIANT_SUMFACT_VERTEX) {
         hex_dispatch(m->order, [&](auto n) {
           constexpr int N = decltype(n)::value;
@@ -902,7 +904,7 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
         constexpr int E = hex_epb<N>();
         const size_t sm = hex_vol_smem<T, TR, N>();
         const T* uin = from_x ? nullptr : (const T*)D.Y;
-        if (sizeof(T) == 4 && m->active == FR_VARIANT_SUMFACT_VERTEX) {
+        if (sizeof(T) == 4 && D.verts && m->active == FR_VARIANT_SUMFACT_VERTEX) {
           const size_t smv = hexv_vol_smem<T, N>();
           const T* dup = (const T*)m->du + D.off_f;
           if (ns)
@@ -1144,14 +1146,18 @@ int build_graph(fr_mesh* m, int scheme) {
 // unchanged.
 template <typename T, typename TR>
 int resolve_variant(fr_mesh* m, int scheme, double dt) {
-  bool has_hex = false, has_tc = false;
+  bool has_hex = false, has_tc = false, curved = false;
   for (auto& D : m->types) {
     has_hex |= D.kind == EK_HEX;
     has_tc |= D.tc_ok;
+    curved |= D.curved;
   }
+  // The vertex-metric family rebuilds trilinear metrics in the kernel: not
+  // for curved (quadratic-map) hexahedra, whose metrics are the tables.
+  const bool vertex_ok = sizeof(T) == 4 && !curved;
   if (m->variant != FR_VARIANT_AUTO) {
     int v = m->variant;
-    if (v == FR_VARIANT_SUMFACT_VERTEX && sizeof(T) != 4) v = FR_VARIANT_SUMFACT;
+    if (v == FR_VARIANT_SUMFACT_VERTEX && !vertex_ok) v = FR_VARIANT_SUMFACT;
     if (v == FR_VARIANT_TENSOR && !has_tc) v = FR_VARIANT_SUMFACT;
     bool changed = v != m->active;
     for (auto& D : m->types) {  // a requested tensor family: every capable type
@@ -1167,7 +1173,7 @@ int resolve_variant(fr_mesh* m, int scheme, double dt) {
   }
   if (m->tuned || !(has_hex || has_tc)) return FR_OK;
   std::vector<int> cand = {FR_VARIANT_SUMFACT};
-  if (has_hex && sizeof(T) == 4) cand.push_back(FR_VARIANT_SUMFACT_VERTEX);
+  if (has_hex && vertex_ok) cand.push_back(FR_VARIANT_SUMFACT_VERTEX);
   if (has_hex && m->precision != FR_MIXED) cand.push_back(FR_VARIANT_DENSE);
   if (has_tc) cand.push_back(FR_VARIANT_TENSOR);
   std::vector<void*> saved;
@@ -1484,12 +1490,19 @@ int fr_mesh_create(const fr_mesh_desc* d, fr_mesh** out) {
     if (t.etype < 0 || t.etype > 2 || seen[t.etype])
       return fail(FR_EINVAL, "bad or repeated element type");
     if (t.n_elem < 0 || (t.n_elem > 0 && !t.conn)) return fail(FR_EINVAL, "bad connectivity");
+    if (t.map_order < 0 || t.map_order > 2)
+      return fail(FR_EINVAL, "map order must be 0, 1 or 2");
+    if (t.map_order == 2 && (t.etype != FR_HEX8 || (t.n_elem > 0 && !t.map_conn)))
+      return fail(FR_EINVAL, "quadratic maps: hexahedra with map_conn only");
     seen[t.etype] = true;
   }
   for (int k = 0; k < 3; ++k)  // canonical type order: hex, prism, tet
     for (int i = 0; i < d->n_etypes; ++i)
-      if (d->etypes[i].etype == k)
+      if (d->etypes[i].etype == k) {
         in.types.push_back({k, {d->etypes[i].n_elem, d->etypes[i].conn}});
+        in.map_order.push_back(d->etypes[i].map_order == 2 ? 2 : 1);
+        in.map_conn.push_back(d->etypes[i].map_order == 2 ? d->etypes[i].map_conn : nullptr);
+      }
   for (int i = 0; i < d->n_periodic; ++i)
     in.periodic.push_back({d->periodic[i][0], d->periodic[i][1], d->periodic[i][2]});
   in.n_bfaces = d->n_bfaces;

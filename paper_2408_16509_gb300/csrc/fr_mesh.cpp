@@ -4,6 +4,8 @@
 #include <algorithm>
 #include <cmath>
 #include <numeric>
+#include <system_error>
+#include <thread>
 #include <unordered_map>
 
 namespace frgb {
@@ -123,6 +125,181 @@ void geometry(HostType& T, const double* nodes) {
   }
 }
 
+// Curved hexahedra ("Curved Elements", Section 3.4): the map is the
+// triquadratic interpolant of 27 nodes, node a + 3b + 9c at (-1+a, -1+b,
+// -1+c).  Positions and det J come from that map exactly.  The metric terms
+// det J dxi_i/dx_n are taken in the conservative curl form
+//   S[i][n] = -(curl_xi I(X_l grad_xi X_m))_i,   (n, m, l) cyclic,
+// I the order-p tensor Lagrange interpolant on the (p+1)^3 Gauss-Lobatto
+// nodes.  Its discrete divergence vanishes (a uniform flow stays uniform) and,
+// because the Gauss-Lobatto set has nodes on every face, the normal component
+// on a face depends on that face's nodes only, so both sides of an interface
+// see the same normal.
+struct Quad1D {  // 1D quadratic Lagrange factors on {-1, 0, 1}
+  static void val(double s, double* l) {
+    l[0] = 0.5 * s * (s - 1.0);
+    l[1] = 1.0 - s * s;
+    l[2] = 0.5 * s * (s + 1.0);
+  }
+  static void der(double s, double* d) {
+    d[0] = s - 0.5;
+    d[1] = -2.0 * s;
+    d[2] = s + 0.5;
+  }
+};
+
+// x_k(pt) and a[j][k] = d x_k / d xi_j of a 27-node map X[27][3].
+void q2_eval(const double* X, const double* pt, double x[3], double a[3][3]) {
+  double l[3][3], d[3][3];
+  for (int i = 0; i < 3; ++i) {
+    Quad1D::val(pt[i], l[i]);
+    Quad1D::der(pt[i], d[i]);
+  }
+  for (int k = 0; k < 3; ++k) {
+    x[k] = 0.0;
+    for (int j = 0; j < 3; ++j) a[j][k] = 0.0;
+  }
+  for (int c = 0; c < 3; ++c)
+    for (int b = 0; b < 3; ++b)
+      for (int aa = 0; aa < 3; ++aa) {
+        const double* P = &X[(aa + 3 * b + 9 * c) * 3];
+        const double N = l[0][aa] * l[1][b] * l[2][c];
+        const double g0 = d[0][aa] * l[1][b] * l[2][c];
+        const double g1 = l[0][aa] * d[1][b] * l[2][c];
+        const double g2 = l[0][aa] * l[1][b] * d[2][c];
+        for (int k = 0; k < 3; ++k) {
+          x[k] += N * P[k];
+          a[0][k] += g0 * P[k];
+          a[1][k] += g1 * P[k];
+          a[2][k] += g2 * P[k];
+        }
+      }
+}
+
+// Lagrange basis of the nodes g[0..n) at s: values l[n] and derivatives d[n].
+void lagrange1d(int n, const double* g, double s, double* l, double* d) {
+  for (int i = 0; i < n; ++i) {
+    double v = 1.0, dv = 0.0;
+    for (int k = 0; k < n; ++k) {
+      if (k == i) continue;
+      const double r = 1.0 / (g[i] - g[k]);
+      dv = dv * (s - g[k]) * r + v * r;
+      v *= (s - g[k]) * r;
+    }
+    l[i] = v;
+    d[i] = dv;
+  }
+}
+
+void curved_geometry(HostType& T, const double* nodes) {
+  const RefElement& R = T.ref;
+  const int nu = R.nupts, nf = R.nfpts, n1 = R.p + 1, ng = n1 * n1 * n1;
+  std::vector<double> g(n1);
+  gauss_lobatto(n1, g.data());
+  // Cardinal-function factors at the solution and flux points.
+  auto factors = [&](int np, const double* pts, std::vector<double>& L,
+                     std::vector<double>& dL) {
+    L.resize(size_t(np) * 3 * n1);
+    dL.resize(size_t(np) * 3 * n1);
+    for (int q = 0; q < np; ++q)
+      for (int i = 0; i < 3; ++i)
+        lagrange1d(n1, g.data(), pts[3 * q + i], &L[(size_t(q) * 3 + i) * n1],
+                   &dL[(size_t(q) * 3 + i) * n1]);
+  };
+  std::vector<double> Lu, dLu, Lf, dLf;
+  factors(nu, R.upts.data(), Lu, dLu);
+  factors(nf, R.fpts.data(), Lf, dLf);
+  T.verts.resize(size_t(T.ne) * 8 * 3);
+  T.upts_x.resize(size_t(T.ne) * nu * 3);
+  T.smat.resize(size_t(T.ne) * 9 * nu);
+  T.rcpdjac.resize(size_t(T.ne) * nu);
+  T.fpts_x.resize(size_t(T.ne) * nf * 3);
+  T.fnvec.resize(size_t(T.ne) * nf * 3);
+  static const int corner[8] = {0, 2, 8, 6, 18, 20, 26, 24};
+  // Elements [e0, e1) with their own scratch; elements write disjoint slices,
+  // so ranges run on separate host threads.
+  auto range = [&](int64_t e0, int64_t e1) {
+  std::vector<double> X(27 * 3), w(size_t(3) * 3 * ng);  // w[n][j][node]
+  // S[i][n] at one point from the nodal fields w, given its 1D factors.
+  auto curl = [&](const double* L, const double* dL, double S[3][3]) {
+    double dw[3][3][3] = {};  // dw[n][j][i] = d_i I(w^n_j)
+    for (int c = 0; c < n1; ++c)
+      for (int b = 0; b < n1; ++b)
+        for (int a = 0; a < n1; ++a) {
+          const int node = a + n1 * (b + n1 * c);
+          const double B[3] = {dL[a] * L[n1 + b] * L[2 * n1 + c],
+                               L[a] * dL[n1 + b] * L[2 * n1 + c],
+                               L[a] * L[n1 + b] * dL[2 * n1 + c]};
+          for (int n = 0; n < 3; ++n)
+            for (int j = 0; j < 3; ++j) {
+              const double v = w[(size_t(n) * 3 + j) * ng + node];
+              for (int i = 0; i < 3; ++i) dw[n][j][i] += B[i] * v;
+            }
+        }
+    for (int i = 0; i < 3; ++i) {
+      const int j = (i + 1) % 3, k = (i + 2) % 3;
+      for (int n = 0; n < 3; ++n) S[i][n] = dw[n][j][k] - dw[n][k][j];
+    }
+  };
+  for (int64_t e = e0; e < e1; ++e) {
+    for (int v = 0; v < 27; ++v)
+      for (int k = 0; k < 3; ++k)
+        X[v * 3 + k] = nodes[T.map_conn[size_t(e) * 27 + v] * 3 + k];
+    for (int v = 0; v < 8; ++v)
+      for (int k = 0; k < 3; ++k)
+        T.verts[(size_t(e) * 8 + v) * 3 + k] = X[corner[v] * 3 + k];
+    for (int c = 0; c < n1; ++c)
+      for (int b = 0; b < n1; ++b)
+        for (int a = 0; a < n1; ++a) {
+          const int node = a + n1 * (b + n1 * c);
+          const double pt[3] = {g[a], g[b], g[c]};
+          double x[3], J[3][3];
+          q2_eval(X.data(), pt, x, J);
+          for (int n = 0; n < 3; ++n) {
+            const int m = (n + 1) % 3, l = (n + 2) % 3;
+            for (int j = 0; j < 3; ++j)
+              w[(size_t(n) * 3 + j) * ng + node] = x[l] * J[j][m];
+          }
+        }
+    for (int q = 0; q < nu; ++q) {
+      double x[3], J[3][3], S[3][3];
+      q2_eval(X.data(), &R.upts[3 * q], x, J);
+      for (int k = 0; k < 3; ++k) T.upts_x[(size_t(e) * nu + q) * 3 + k] = x[k];
+      const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                         J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                         J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+      curl(&Lu[size_t(q) * 3 * n1], &dLu[size_t(q) * 3 * n1], S);
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+          T.smat[(size_t(e) * 9 + i * 3 + j) * nu + q] = S[i][j];
+      T.rcpdjac[size_t(e) * nu + q] = det > 0 ? 1.0 / det : -1.0;
+    }
+    for (int q = 0; q < nf; ++q) {
+      double x[3], J[3][3], S[3][3];
+      q2_eval(X.data(), &R.fpts[3 * q], x, J);
+      for (int k = 0; k < 3; ++k) T.fpts_x[(size_t(e) * nf + q) * 3 + k] = x[k];
+      curl(&Lf[size_t(q) * 3 * n1], &dLf[size_t(q) * 3 * n1], S);
+      const double* n = &R.fnorm[3 * q];
+      for (int j = 0; j < 3; ++j)
+        T.fnvec[(size_t(e) * nf + q) * 3 + j] =
+            S[0][j] * n[0] + S[1][j] * n[1] + S[2][j] * n[2];
+    }
+  }
+  };
+  const int64_t nthr = std::max<int64_t>(
+      1, std::min<int64_t>(std::thread::hardware_concurrency(), T.ne / 64));
+  std::vector<std::thread> pool;
+  int64_t t = 1;
+  try {
+    for (; t < nthr; ++t)
+      pool.emplace_back(range, T.ne * t / nthr, T.ne * (t + 1) / nthr);
+  } catch (const std::system_error&) {  // no more threads: the rest runs here
+    range(T.ne * t / nthr, T.ne);
+  }
+  range(0, T.ne / nthr);
+  for (auto& th : pool) th.join();
+}
+
 }  // namespace
 
 std::string build_mesh(const MeshInput& in, std::vector<HostType>& types,
@@ -141,7 +318,25 @@ std::string build_mesh(const MeshInput& in, std::vector<HostType>& types,
       if (v < 0 || v >= in.n_nodes) return "connectivity refers to a missing node";
     int64_t span = T.ne * 5 * int64_t(T.ref.nfpts);
     if (span >= (int64_t(1) << 29)) return "too many elements of one type";
-    geometry(T, in.nodes);
+    const size_t ti = size_t(&t - in.types.data());
+    if (ti < in.map_order.size() && in.map_order[ti] == 2) {
+      if (T.kind != EK_HEX) return "quadratic maps are supported on hexahedra only";
+      T.map_order = 2;
+      T.map_conn.assign(in.map_conn[ti], in.map_conn[ti] + size_t(T.ne) * 27);
+      static const int corner[8] = {0, 2, 8, 6, 18, 20, 26, 24};
+      for (int64_t e = 0; e < T.ne; ++e) {
+        for (int v = 0; v < 27; ++v) {
+          const int64_t id = T.map_conn[size_t(e) * 27 + v];
+          if (id < 0 || id >= in.n_nodes) return "map connectivity refers to a missing node";
+        }
+        for (int v = 0; v < 8; ++v)
+          if (T.map_conn[size_t(e) * 27 + corner[v]] != T.conn[size_t(e) * 8 + v])
+            return "map corner nodes differ from the element vertices";
+      }
+      curved_geometry(T, in.nodes);
+    } else {
+      geometry(T, in.nodes);
+    }
     for (double r : T.rcpdjac)
       if (r <= 0) {
         *err_mesh = true;

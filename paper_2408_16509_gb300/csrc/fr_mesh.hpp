@@ -19,6 +19,8 @@ struct HostType {
   int64_t ne = 0;
   RefElement ref;
   std::vector<int64_t> conn;     // [ne][nv]
+  int map_order = 1;             // 2: quadratic (27-node) hexahedron map
+  std::vector<int64_t> map_conn; // [ne][27] (map_order 2)
   std::vector<double> verts;     // [ne][nv][3]
   std::vector<double> upts_x;    // [ne][nupts][3]
   std::vector<double> smat;      // [ne][9][nupts]   S[i][j] = row i, col j
@@ -47,6 +49,8 @@ struct MeshInput {
   const double* nodes = nullptr;
   int order = 0;
   std::vector<std::pair<int, std::pair<int64_t, const int64_t*>>> types;
+  std::vector<int> map_order;               // per entry of types: 1 or 2
+  std::vector<const int64_t*> map_conn;     // per entry: [ne][27] or null
   std::vector<std::array<double, 3>> periodic;
   int64_t n_bfaces = 0;
   const int64_t* bface_nodes = nullptr;  // [n][4], -1 pads triangles

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import paper_2408_16509_gb300 as fr
-from frinputs import box_hex, mixed_box
+from frinputs import box_hex, curved_box_hex, mixed_box
 from oracle.mesh import FRMesh as OracleMesh
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -51,6 +51,7 @@ def test_compute_calls_refuse_host_only_handles():
 SPECS = {
     "hex": lambda: box_hex((3, 2, 2), perturb=0.1),
     "mixed": lambda: mixed_box(n=3, x_pri=0.34, x_tet=0.67, perturb=0.05),
+    "curved": lambda: curved_box_hex((3, 2, 2)),
 }
 
 
@@ -115,3 +116,25 @@ def test_single_element_periodic_with_itself():
     g = fr.FRMesh(spec, 2, device=-1)
     o = OracleMesh(spec.as_dict(), 2)
     assert g.pair_counts() == (len(o.pair_l), 0)
+
+
+def test_curved_maps_are_validated():
+    """A quadratic map whose corner nodes are not the element's vertices, a
+    node id out of range, or a quadratic map on a non-hexahedron is refused
+    at creation."""
+    spec = curved_box_hex((2, 2, 2))
+    order, mconn = spec.maps["hex"]
+    bad = mconn.copy()
+    bad[0, [0, 2]] = bad[0, [2, 0]]
+    spec.maps["hex"] = (order, bad)
+    with pytest.raises(fr.FRError):
+        fr.FRMesh(spec, 2, device=-1)
+    bad = mconn.copy()
+    bad[1, 13] = len(spec.nodes)
+    spec.maps["hex"] = (order, bad)
+    with pytest.raises(fr.FRError):
+        fr.FRMesh(spec, 2, device=-1)
+    m = mixed_box(n=2, x_pri=0.5, x_tet=1.0)
+    m.maps = {"pri": (2, np.zeros((len(m.elements["pri"]), 27), np.int64))}
+    with pytest.raises(fr.FRError):
+        fr.FRMesh(m, 2, device=-1)
