@@ -18,6 +18,14 @@ Section 2 of the paper:
   Pin: on the hexahedron it equals the tensor-product right/left Radau form
   g_R' = (P'_{p+1} + P'_p)/2 (tests/test_oracle_operators.py).
 * integration weights ``W[z] = int l_z`` for discrete conservation checks.
+* anti-aliasing (Section 3.2, "Anti-aliasing"): a volume quadrature rule of
+  degree qdeg, ``B[q, z] = l_z(x_q)`` (solution -> quadrature points) and the
+  least-squares projection ``P[z, q]`` onto the solution space: with the
+  orthonormal basis phi_k, the projection of f has modal coefficients
+  c_k = sum_q w_q phi_k(x_q) f(x_q), so P = V Phi_q^T diag(w).  Reading: the
+  paper's Polyquad rules are not available here; the rules are collapsed
+  Gauss-Jacobi products (tensor Gauss on the hexahedron), exact to degree
+  2n - 1 with n = qdeg // 2 + 1 points per direction.
 """
 import numpy as np
 
@@ -156,6 +164,20 @@ class ElementType:
         # integration weights of the nodal basis
         xq, wq = self.volume_rule(self.p + 2)
         self.W = (self.basis(xq) @ Vi).T @ wq
+
+    # anti-aliasing ---------------------------------------------------------
+    def quadrature(self, qdeg):
+        """Volume rule exact for polynomials of degree qdeg."""
+        return self.volume_rule(qdeg // 2 + 1)
+
+    def aa_operators(self, qdeg):
+        """(xq, wq, B, P): quadrature points and weights, interpolation from
+        the solution points, least-squares projection back onto them."""
+        xq, wq = self.quadrature(qdeg)
+        phi = self.basis(xq)                                 # (nq, nmodes)
+        B = phi @ self.vdm_inv
+        P = self.basis(self.upts) @ (phi.T * wq[None, :])
+        return xq, wq, B, P
 
     # geometry of the vertex map ------------------------------------------
     def map_points(self, verts, x):

@@ -21,6 +21,12 @@ average of both sides' viscous fluxes.  At a boundary flux point the outside
 state comes from the boundary condition and the outside gradient equals the
 inside one.
 
+Anti-aliasing (Section 3.2, "Anti-aliasing"; ``antialias=qdeg``): step 3
+takes the transformed flux at the points of a degree-qdeg volume rule
+(u and, for NS, the physical gradient interpolated there, S evaluated
+there) and replaces the collocated f~ by its least-squares projection onto
+the solution space, f~ = P f~_q; steps 4 and 5 are unchanged.
+
 Boundary conditions (by tag): ('state', rho, u, v, w, p) -- outside state is
 the given constant state; ('extrap',) -- outside state = inside state.
 """
@@ -31,8 +37,13 @@ from .physics import euler_flux, prim_to_cons, rusanov, viscous_flux
 
 class FRSystem:
     def __init__(self, mesh, physics="euler", gamma=1.4, mu=0.0, pr=0.72,
-                 bcs=None):
+                 bcs=None, antialias=None):
         self.m = mesh
+        self.aa = {}
+        if antialias is not None:
+            for t in mesh.types:
+                xq, _, B, P = mesh.el[t].aa_operators(int(antialias))
+                self.aa[t] = (B, P, mesh.metric_at(t, xq))
         self.physics = physics
         self.gamma, self.mu, self.pr = gamma, mu, pr
         self.bcs = dict(bcs or {})
@@ -127,10 +138,20 @@ class FRSystem:
         out = {}
         for t in m.types:
             el = m.el[t]
-            f = euler_flux(u[t], g)                          # (e, z, 3, 5)
-            if ns:
-                f = f - viscous_flux(u[t], grads[t], g, self.mu, self.pr)
-            ft = np.einsum("ezij,ezjk->ezik", m.S_u[t], f)   # Step 3
+            if t in self.aa:                                 # Step 3, projected
+                B, P, Sq = self.aa[t]
+                uq = np.einsum("qz,ezk->eqk", B, u[t])
+                f = euler_flux(uq, g)
+                if ns:
+                    gq = np.einsum("qz,ezjk->eqjk", B, grads[t])
+                    f = f - viscous_flux(uq, gq, g, self.mu, self.pr)
+                ftq = np.einsum("eqij,eqjk->eqik", Sq, f)
+                ft = np.einsum("zq,eqik->ezik", P, ftq)
+            else:
+                f = euler_flux(u[t], g)                      # (e, z, 3, 5)
+                if ns:
+                    f = f - viscous_flux(u[t], grads[t], g, self.mu, self.pr)
+                ft = np.einsum("ezij,ezjk->ezik", m.S_u[t], f)   # Step 3
             div = sum(np.einsum("zv,evk->ezk", el.D[d], ft[:, :, d])
                       for d in range(3))
             ff = np.einsum("fz,ezdk->efdk", el.M0, ft)

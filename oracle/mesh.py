@@ -89,6 +89,7 @@ class FRMesh:
         self.fpts_x, self.fnorm, self.fmag = {}, {}, {}
         maps = spec.get("maps", {}) or {}
         self.curved = {}
+        self._Xm = {}
         for t in self.types:
             el, V = self.el[t], self.verts[t]
             morder, mconn = maps.get(t, (1, None))
@@ -97,6 +98,7 @@ class FRMesh:
                 if t != "hex":
                     raise MeshError("quadratic maps are implemented for hexahedra")
                 Xm = nodes[np.asarray(mconn, np.int64)]
+                self._Xm[t] = Xm
                 self.upts_x[t] = np.einsum("pv,evk->epk", el.q2_shape(el.upts), Xm)
                 self.S_u[t] = curl_metric(el, Xm, el.upts)
                 dX = np.einsum("jpv,evk->epjk", el.q2_dshape(el.upts), Xm)
@@ -123,6 +125,14 @@ class FRMesh:
             n += self.ne[t] * self.el[t].nfpts
         self.nfpts_total = n
         self._pair(nodes, spec.get("periodic", []), spec.get("bfaces", []))
+
+    def metric_at(self, t, pts):
+        """S = det J J^{-1} of every element of type t at reference points
+        pts, in the form the mesh uses (curl form on curved elements, the
+        map's cross products otherwise).  Shape (ne, npts, 3, 3)."""
+        if self.curved[t]:
+            return curl_metric(self.el[t], self._Xm[t], pts)
+        return self.el[t].metrics(self.verts[t], pts)[0]
 
     def gidx(self, t, e, i):
         return self.foff[t] + e * self.el[t].nfpts + i
