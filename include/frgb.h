@@ -195,7 +195,8 @@ enum { FR_KC_FACE_U = 0,  /* NS common solution at interior flux points */
        FR_KC_BND_F = 4,   /* common normal flux, boundary points */
        FR_KC_VOL = 5,     /* volume: flux, divergence, lift, RK update */
        FR_KC_FILTER = 6,  /* entropy minimum and entropy filter */
-       FR_KC_COUNT = 7 };
+       FR_KC_AAFLUX = 7,  /* anti-aliased transformed flux (one per type) */
+       FR_KC_COUNT = 8 };
 int fr_profile_step(fr_mesh* mesh, int scheme, double dt, double* ms,
                     int* launches);
 
@@ -238,10 +239,33 @@ int fr_sync(fr_mesh* mesh);
  *   FR_OP_WEIGHTS [nupts]               int l_z over the reference element
  *   FR_OP_UPTS    [nupts][3]            reference solution points
  *   FR_OP_FPTS    [nfpts][3]            reference flux points
+ * With anti-aliasing on (fr_set_antialias, degree qdeg; nq = (qdeg/2+1)^3
+ * quadrature points on every element type), else FR_EINVAL:
+ *   FR_OP_AA_QPTS [nq][3]               quadrature points
+ *   FR_OP_AA_QWTS [nq]                  quadrature weights
+ *   FR_OP_AA_B    [nq][nupts]           l_z(x_q), solution -> quadrature points
+ *   FR_OP_AA_P    [nupts][nq]           least-squares projection back
  * Works on host-only handles too. */
 enum { FR_OP_M0 = 0, FR_OP_D = 1, FR_OP_LIFT = 2, FR_OP_WEIGHTS = 3,
-       FR_OP_UPTS = 4, FR_OP_FPTS = 5 };
+       FR_OP_UPTS = 4, FR_OP_FPTS = 5, FR_OP_AA_QPTS = 6, FR_OP_AA_QWTS = 7,
+       FR_OP_AA_B = 8, FR_OP_AA_P = 9 };
 int fr_get_operator(const fr_mesh* mesh, int etype, int which, double* out);
+
+/* Anti-aliasing (Section 3.2, "Anti-aliasing"): for qdeg > 0 the transformed
+ * flux is no longer collocated at the solution points.  It is evaluated at
+ * the points of a volume quadrature rule exact to degree qdeg (u and, for
+ * Navier-Stokes, the corrected gradient interpolated there; the metric
+ * evaluated there in the mesh's own form) and projected onto the solution
+ * space by least squares, f~ = P f~_q; the divergence, correction and RK
+ * update then use that f~.  Rules: n = qdeg/2 + 1 points per direction,
+ * tensor Gauss-Legendre on hexahedra, collapsed Gauss-Legendre x
+ * Gauss-Jacobi(1,0) [x Gauss-Jacobi(2,0)] on prisms and tetrahedra.
+ * qdeg = 0 restores collocation.  qdeg in 0..24, else FR_EINVAL.  Adds per
+ * element type the operators, the metric at the quadrature points ([ne][9]
+ * [nq]) and a projected-flux buffer ([ne][15][nupts]) in device memory; the
+ * vertex-metric and tensor-core volume kernels are not used while it is on.
+ * Synchronises the handle's stream; later steps rebuild their graphs. */
+int fr_set_antialias(fr_mesh* mesh, int qdeg);
 
 /* Metric terms at the solution points: smat [n_elem][9][nupts] holds
  * S = det(J) J^{-1} (row-major 3x3 per point), rcpdjac [n_elem][nupts]

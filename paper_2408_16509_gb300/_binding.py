@@ -91,6 +91,7 @@ def load():
         "fr_get_metrics": (I, [P, I, P, P]),
         "fr_get_pairs": (I, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "fr_profile_step": (I, [P, I, D, P, P]),
+        "fr_set_antialias": (I, [P, I]),
         "fr_set_kernel_variant": (I, [P, I]),
         "fr_get_tuning": (I, [P, C.POINTER(I), P]),
         "fr_set_solution_static": (I, [P, I, P]),
@@ -292,13 +293,13 @@ class FRMesh:
         return log
 
     KERNEL_CLASSES = ("face_ucommon", "bnd_ucommon", "grad", "face_flux",
-                      "bnd_flux", "volume", "filter")
+                      "bnd_flux", "volume", "filter", "aa_flux")
 
     def profile_step(self, scheme, dt):
         """One RK step with per-launch CUDA events: returns
         {kernel class: (summed ms, launches)}."""
-        ms = np.zeros(7, np.float64)
-        n = np.zeros(7, np.int32)
+        ms = np.zeros(len(self.KERNEL_CLASSES), np.float64)
+        n = np.zeros(len(self.KERNEL_CLASSES), np.int32)
         _check(load().fr_profile_step(self._h, SCHEMES[scheme], float(dt),
                                       _ptr(ms), _ptr(n)))
         return {k: (float(ms[i]), int(n[i]))
@@ -366,13 +367,25 @@ class FRMesh:
     def sync(self):
         _check(load().fr_sync(self._h))
 
-    OPS = {"M0": 0, "D": 1, "LIFT": 2, "W": 3, "upts": 4, "fpts": 5}
+    _aa_qdeg = 0
+
+    def set_antialias(self, qdeg):
+        """Anti-aliased flux (Section 3.2): transformed flux projected from a
+        volume rule of degree qdeg; 0 restores collocation."""
+        _check(load().fr_set_antialias(self._h, int(qdeg)))
+        self._aa_qdeg = int(qdeg)
+
+    OPS = {"M0": 0, "D": 1, "LIFT": 2, "W": 3, "upts": 4, "fpts": 5,
+           "aa_qpts": 6, "aa_qwts": 7, "aa_B": 8, "aa_P": 9}
 
     def operator(self, etype, which):
         """Reference-element data built by the library (FR_OP_*)."""
         ne, nu, nf = self.info(etype)
+        nq = (self._aa_qdeg // 2 + 1) ** 3
         shape = {"M0": (nf, nu), "D": (3, nu, nu), "LIFT": (nu, nf),
-                 "W": (nu,), "upts": (nu, 3), "fpts": (nf, 3)}[which]
+                 "W": (nu,), "upts": (nu, 3), "fpts": (nf, 3),
+                 "aa_qpts": (nq, 3), "aa_qwts": (nq,), "aa_B": (nq, nu),
+                 "aa_P": (nu, nq)}[which]
         out = np.empty(shape, np.float64)
         _check(load().fr_get_operator(self._h, ETYPES[etype],
                                       self.OPS[which], _ptr(out)))

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "../../include/frgb.h"
+#include "fr_aa.cuh"
 #include "fr_dense_tc.cuh"
 #include "fr_filter.cuh"
 #include "fr_hex.cuh"
@@ -114,6 +115,13 @@ struct DevType {
   int8_t* fbc = nullptr;     // [ne][nf] boundary-condition index or -1 (NS)
   void* verts = nullptr;     // [ne][8][3] vertices minus vertex 0 (hex, FP32)
   bool curved = false;       // quadratic map: metrics only from the tables
+  // anti-aliasing (Section 3.2): operators, metric at the quadrature
+  // points, and the projected transformed flux
+  void* aaBT = nullptr;      // [nu][nq]
+  void* aaPT = nullptr;      // [nq][nu]
+  void* aasmq = nullptr;     // [ne][9][nq]
+  void* tf = nullptr;        // [ne][3][5][nu]
+  int aa_nq = 0, aa_ctas = 1;
   // tensor-core kernels (prisms / tetrahedra, FP32 values)
   bool tc_ok = false;
   bool tca_ok = false;       // data-as-A volume kernel available
@@ -176,6 +184,7 @@ struct fr_mesh {
   float tune_ms[5] = {0, 0, 0, 0, 0}; // ms per step of each family tried
   long long epoch = 0;            // bumped by every change of launch config
   long long graph_epoch[3] = {-1, -1, -1};
+  int aa_qdeg = 0;            // anti-aliasing rule degree (0: collocation)
   bool err_on = false;        // stage epilogues accumulate the embedded error
   double* d_errpart = nullptr;  // per-block partial sums of the error norm
   double* d_errsum = nullptr;   // total
@@ -561,7 +570,31 @@ bool use_tc_grad(const fr_mesh* m, const DevType& D) {
 }
 
 bool use_tc_vol(const fr_mesh* m, const DevType& D) {
-  return D.tc_ok && D.tc_vol_on && m->active == FR_VARIANT_TENSOR;
+  return D.tc_ok && D.tc_vol_on && m->active == FR_VARIANT_TENSOR && m->aa_qdeg == 0;
+}
+
+// Anti-aliased transformed flux of one element type (Section 3.2) into D.tf;
+// the volume kernel then reads it instead of collocating the flux.
+template <typename T, typename TR>
+void launch_aa_flux(fr_mesh* m, const DevType& D, cudaStream_t s, bool from_x,
+                    bool ns, const Phys<T>& ph) {
+  if (D.ne == 0) return;
+  const bool hexk = use_hex(m, D);
+  const T* uin = hexk ? (from_x ? nullptr : (const T*)D.Y)
+                      : (from_x ? (const T*)D.X : (const T*)D.Y);
+  const TR* X = hexk ? (const TR*)D.X : nullptr;
+  const AaOps<T> op{(const T*)D.aaBT, (const T*)D.aaPT, D.aa_nq};
+  dispatch(D.kind, m->order, [&](auto nu, auto nf) {
+    constexpr int NU = decltype(nu)::value;
+    const unsigned grid = unsigned(std::min<long long>(D.ne, (long long)m->num_sms * D.aa_ctas));
+    const size_t sm = aa_dense_smem<T, NU>(D.aa_nq);
+    if (ns)
+      k_aa_flux_dense<T, TR, NU, true><<<grid, kAaThreads, sm, s>>>(
+          D.ne, uin, X, (const T*)D.grad, (const T*)D.aasmq, op, ph, (T*)D.tf);
+    else
+      k_aa_flux_dense<T, TR, NU, false><<<grid, kAaThreads, sm, s>>>(
+          D.ne, uin, X, nullptr, (const T*)D.aasmq, op, ph, (T*)D.tf);
+  });
 }
 
 // Tensor-core gradient kernel of a prism / tetrahedron type (FP32 values).
@@ -671,6 +704,10 @@ int prepare_kernels(fr_mesh* m) {
       cudaFuncSetAttribute(kg, cudaFuncAttributeMaxDynamicSharedMemorySize, sg);
       cudaFuncSetAttribute(kv0, cudaFuncAttributeMaxDynamicSharedMemorySize, sv);
       cudaFuncSetAttribute(kv1, cudaFuncAttributeMaxDynamicSharedMemorySize, sv);
+      cudaFuncSetAttribute(k_vol_dense<T, NU, NF, E, false, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, sv);
+      cudaFuncSetAttribute(k_vol_dense<T, NU, NF, E, true, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, sv);
       int a = 0, b = 0;
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, kg, E * NU, sg);
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kv1, E * NU, sv);
@@ -720,6 +757,12 @@ int prepare_kernels(fr_mesh* m) {
                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                            int(hex_vol_smem<T, TR, N>()));
       cudaFuncSetAttribute(k_hex_vol<T, TR, N, E, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(hex_vol_smem<T, TR, N>()));
+      cudaFuncSetAttribute(k_hex_vol<T, TR, N, E, false, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(hex_vol_smem<T, TR, N>()));
+      cudaFuncSetAttribute(k_hex_vol<T, TR, N, E, true, true>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                            int(hex_vol_smem<T, TR, N>()));
       cudaFuncSetAttribute(k_hex_grad<T, TR, N, E, sizeof(T) == 4>,
@@ -891,9 +934,15 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
           (T*)m->fc, m->tt, ph, bc);
     PROF_END(FR_KC_BND_F);
   }
+  const bool aa = m->aa_qdeg > 0;
   for (auto& D : m->types) {
     T* uf_next = mode == 0 ? nullptr : (T*)m->uf + D.off_f;
     const T* fc = (const T*)m->fc + D.off_f;
+    if (aa) {
+      PROF_BEGIN(FR_KC_AAFLUX);
+      launch_aa_flux<T, TR>(m, D, s, from_x, ns, ph);
+      PROF_END(FR_KC_AAFLUX);
+    }
     PROF_BEGIN(FR_KC_VOL);
     if (use_hex(m, D)) {
       HexStage<T, TR> sa{mode, stage, (TR*)D.X, (TR*)D.A, (T*)D.Y, (T*)D.R,
@@ -915,7 +964,15 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
                 D.ne, uin, nullptr, fc, (const T*)D.verts, hexops<T>(D), ph, sa);
           return;
         }
-        if (ns)
+        if (aa && ns)
+          k_hex_vol<T, TR, N, E, true, true><<<nblk(D.ne, E), E * N * N * N, sm, s>>>(
+              D.ne, uin, nullptr, fc, nullptr, (const T*)D.rcpdjac, hexops<T>(D),
+              ph, sa, (const T*)D.tf);
+        else if (aa)
+          k_hex_vol<T, TR, N, E, false, true><<<nblk(D.ne, E), E * N * N * N, sm, s>>>(
+              D.ne, uin, nullptr, fc, nullptr, (const T*)D.rcpdjac, hexops<T>(D),
+              ph, sa, (const T*)D.tf);
+        else if (ns)
           k_hex_vol<T, TR, N, E, true><<<nblk(D.ne, E), E * N * N * N, sm, s>>>(
               D.ne, uin, (const T*)D.grad, fc, (const T*)D.smat,
               (const T*)D.rcpdjac, hexops<T>(D), ph, sa);
@@ -948,7 +1005,11 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
         const size_t sm = dense_vol_smem<T, NU, NF>();
         const unsigned grid = unsigned(std::min<long long>(
             (D.ne + E - 1) / E, (long long)m->num_sms * D.vol_ctas));
-        if (ns)
+        if (aa)
+          k_vol_dense<T, NU, NF, E, false, true><<<grid, E * NU, sm, s>>>(
+              D.ne, uin, nullptr, fc, nullptr, (const T*)D.rcpdjac, ops_of<T>(D),
+              ph, sa, (const T*)D.tf);
+        else if (ns)
           k_vol_dense<T, NU, NF, E, true><<<grid, E * NU, sm, s>>>(
               D.ne, uin, (const T*)D.grad, fc, (const T*)D.smat,
               (const T*)D.rcpdjac, ops_of<T>(D), ph, sa);
@@ -1153,8 +1214,9 @@ int resolve_variant(fr_mesh* m, int scheme, double dt) {
     curved |= D.curved;
   }
   // The vertex-metric family rebuilds trilinear metrics in the kernel: not
-  // for curved (quadratic-map) hexahedra, whose metrics are the tables.
-  const bool vertex_ok = sizeof(T) == 4 && !curved;
+  // for curved (quadratic-map) hexahedra, whose metrics are the tables, nor
+  // with anti-aliasing (the flux is then taken at the quadrature points).
+  const bool vertex_ok = sizeof(T) == 4 && !curved && m->aa_qdeg == 0;
   if (m->variant != FR_VARIANT_AUTO) {
     int v = m->variant;
     if (v == FR_VARIANT_SUMFACT_VERTEX && !vertex_ok) v = FR_VARIANT_SUMFACT;
@@ -1443,6 +1505,65 @@ int do_profile(fr_mesh* m, int scheme, double dt, double* ms, int* launches) {
 }
 
 // Run fn<T, TR>(m) for the handle's precision.
+// Device side of fr_set_antialias: release the previous buffers, then (for
+// qdeg > 0) upload the transposed operators, the metric at the quadrature
+// points and allocate the projected-flux buffer of every type.
+void dev_release(fr_mesh* m, void** p) {
+  if (!*p) return;
+  cudaFree(*p);
+  m->allocs.erase(std::remove(m->allocs.begin(), m->allocs.end(), *p), m->allocs.end());
+  *p = nullptr;
+}
+
+template <typename T, typename TR>
+int aa_setup(fr_mesh* m) {
+  int rc;
+  for (size_t t = 0; t < m->types.size(); ++t) {
+    DevType& D = m->types[t];
+    const HostType& H = m->host[t];
+    for (void** p : {&D.aaBT, &D.aaPT, &D.aasmq, &D.tf}) dev_release(m, p);
+    D.aa_nq = 0;
+    if (m->aa_qdeg == 0) continue;
+    const int nq = int(H.aa_w.size()), nu = D.nu;
+    int smax = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    size_t need = 0;
+    dispatch(D.kind, m->order, [&](auto nuc, auto) {
+      need = aa_dense_smem<T, decltype(nuc)::value>(nq);
+    });
+    if (need > size_t(smax)) {
+      m->aa_qdeg = 0;
+      return fail(FR_EINVAL, "quadrature rule too large for the shared memory of a block");
+    }
+    std::vector<double> bt(size_t(nu) * nq), pt(size_t(nq) * nu);
+    for (int q = 0; q < nq; ++q)
+      for (int z = 0; z < nu; ++z) {
+        bt[size_t(z) * nq + q] = H.aa_B[size_t(q) * nu + z];
+        pt[size_t(q) * nu + z] = H.aa_P[size_t(z) * nq + q];
+      }
+    std::vector<double> smq;
+    metric_points(H, nq, H.aa_x.data(), smq);
+    if ((rc = dev_upload<T>(m, bt, &D.aaBT))) return rc;
+    if ((rc = dev_upload<T>(m, pt, &D.aaPT))) return rc;
+    if ((rc = dev_upload<T>(m, smq, &D.aasmq))) return rc;
+    if ((rc = dev_zeros(m, size_t(D.ne) * 15 * nu * sizeof(T), &D.tf))) return rc;
+    D.aa_nq = nq;
+    dispatch(D.kind, m->order, [&](auto nuc, auto nfc) {
+      constexpr int NU = decltype(nuc)::value;
+      const int sm = int(aa_dense_smem<T, NU>(nq));
+      int a = 0;
+      for (auto fn : {k_aa_flux_dense<T, TR, NU, true>, k_aa_flux_dense<T, TR, NU, false>}) {
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, fn, kAaThreads, sm);
+      }
+      D.aa_ctas = a > 0 ? a : 1;
+    });
+  }
+  CK(cudaGetLastError());
+  return FR_OK;
+}
+
 #define FR_PREC(m, fn, ...)                                   \
   ((m)->precision == FR_FP64   ? fn<double, double>(__VA_ARGS__) \
    : (m)->precision == FR_FP32 ? fn<float, float>(__VA_ARGS__)   \
@@ -1830,8 +1951,13 @@ int fr_get_operator(const fr_mesh* m, int etype, int which, double* out) {
     case FR_OP_WEIGHTS: v = &R.W; break;
     case FR_OP_UPTS: v = &R.upts; break;
     case FR_OP_FPTS: v = &R.fpts; break;
+    case FR_OP_AA_QPTS: v = &H->aa_x; break;
+    case FR_OP_AA_QWTS: v = &H->aa_w; break;
+    case FR_OP_AA_B: v = &H->aa_B; break;
+    case FR_OP_AA_P: v = &H->aa_P; break;
     default: return fail(FR_EINVAL, "unknown operator");
   }
+  if (v->empty()) return fail(FR_EINVAL, "anti-aliasing is off (fr_set_antialias)");
   std::memcpy(out, v->data(), v->size() * sizeof(double));
   return FR_OK;
 }
@@ -1842,6 +1968,30 @@ int fr_get_metrics(const fr_mesh* m, int etype, double* smat, double* rcpdjac) {
   if (!H) return fail(FR_EINVAL, "mesh has no elements of this type");
   if (smat) std::memcpy(smat, H->smat.data(), H->smat.size() * sizeof(double));
   if (rcpdjac) std::memcpy(rcpdjac, H->rcpdjac.data(), H->rcpdjac.size() * sizeof(double));
+  return FR_OK;
+}
+
+int fr_set_antialias(fr_mesh* m, int qdeg) {
+  if (!m) return fail(FR_EINVAL, "null argument");
+  if (qdeg < 0 || qdeg > 24) return fail(FR_EINVAL, "quadrature degree must be 0..24");
+  for (auto& H : m->host) {
+    H.aa_qdeg = qdeg;
+    H.aa_x.clear();
+    H.aa_w.clear();
+    H.aa_B.clear();
+    H.aa_P.clear();
+    if (qdeg == 0) continue;
+    aa_rule(H.kind, qdeg, H.aa_x, H.aa_w);
+    aa_operators(H.ref, H.aa_x, H.aa_w, H.aa_B, H.aa_P);
+  }
+  m->aa_qdeg = qdeg;
+  if (m->host_only) return FR_OK;
+  CK(cudaSetDevice(m->device));
+  CK(cudaStreamSynchronize(m->stream));
+  int rc = FR_PREC(m, aa_setup, m);
+  if (rc) return rc;
+  ++m->epoch;            // graphs hold the old launch sequence
+  if (m->variant == FR_VARIANT_AUTO) m->tuned = false;
   return FR_OK;
 }
 

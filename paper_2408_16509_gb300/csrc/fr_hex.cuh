@@ -319,12 +319,14 @@ __host__ __device__ constexpr int hex_vol_bytes_per_elem() {
          (hex_vol_stage_regs<TR>() ? (10 * N * N * N * int(sizeof(TR)) + 15) / 16 * 16 : 0);
 }
 
-template <typename T, typename TR, int N, int EPB, bool NS>
+// AA: f~ is the anti-aliased projection precomputed in tflux
+// ([ne][3][5][NU], Section 3.2) and is copied in instead of collocated.
+template <typename T, typename TR, int N, int EPB, bool NS, bool AA = false>
 __global__ void __launch_bounds__(EPB* N* N* N)
     k_hex_vol(long long ne, const T* __restrict__ uin, const T* __restrict__ grad,
               const T* __restrict__ fc, const T* __restrict__ smat,
               const T* __restrict__ rcpdjac, HexOps<T> op, Phys<T> ph,
-              HexStage<T, TR> sa) {
+              HexStage<T, TR> sa, const T* __restrict__ tflux = nullptr) {
   constexpr int NU = N * N * N, NF = 6 * N * N, N2 = N * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int le = threadIdx.x / NU, z = threadIdx.x - le * NU;
@@ -340,6 +342,7 @@ __global__ void __launch_bounds__(EPB* N* N* N)
   constexpr bool SR = hex_vol_stage_regs<TR>();
   if (e < ne) {
     async_copy(jm, fc + e * 5 * NF, 5 * NF * int(sizeof(T)), z, NU);
+    if (AA) async_copy(ft, tflux + e * 15 * NU, 15 * NU * int(sizeof(T)), z, NU);
     if (SR && nx) async_copy(xs, sa.X + e * 5 * NU, 5 * NU * int(sizeof(TR)), z, NU);
     if (SR && na) async_copy(as, sa.A + e * 5 * NU, 5 * NU * int(sizeof(TR)), z, NU);
   }
@@ -348,6 +351,8 @@ __global__ void __launch_bounds__(EPB* N* N* N)
 #pragma unroll
     for (int k = 0; k < 5; ++k)
       uz[k] = uin ? uin[(e * 5 + k) * NU + z] : T(sa.X[(e * 5 + k) * NU + z]);
+  }
+  if (!AA && e < ne) {
     T F[3][5];
     euler_flux(uz, ph, F);
     if (NS) {

@@ -592,12 +592,15 @@ __global__ void __launch_bounds__(EPB* NU)
 // Volume kernel: transformed flux f~ = S F at solution points, Eq. (FRfinal)
 // divergence  sum_d D_d f~_d + LIFT (F^C - n~.M0 f~), negdivconf R = -div/J,
 // the RK epilogue, and the next stage's u_f = M0 u_next.
-template <typename T, int NU, int NF, int EPB, bool NS>
+// AA: f~ is the anti-aliased projection precomputed in tflux
+// ([ne][3][5][NU], Section 3.2) and is read instead of collocated.
+template <typename T, int NU, int NF, int EPB, bool NS, bool AA = false>
 __global__ void __launch_bounds__(EPB* NU)
     k_vol_dense(long long ne, const T* __restrict__ u,
                 const T* __restrict__ grad, const T* __restrict__ fc,
                 const T* __restrict__ smat, const T* __restrict__ rcpdjac,
-                DenseOps<T> gops, Phys<T> ph, StageArgs<T> sa) {
+                DenseOps<T> gops, Phys<T> ph, StageArgs<T> sa,
+                const T* __restrict__ tflux = nullptr) {
   extern __shared__ unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   const DenseOps<T> ops = stage_dense_ops<T, NU, NF>(gops, sm);
@@ -613,6 +616,11 @@ __global__ void __launch_bounds__(EPB* NU)
     if (act) {
 #pragma unroll
       for (int k = 0; k < 5; ++k) uz[k] = u[(e * 5 + k) * NU + z];
+    }
+    if (AA && act) {
+#pragma unroll
+      for (int c = 0; c < 15; ++c) ft[c * NU + z] = tflux[(e * 15 + c) * NU + z];
+    } else if (act) {
       T F[3][5];
       euler_flux(uz, ph, F);
       if (NS) {

@@ -191,116 +191,175 @@ void lagrange1d(int n, const double* g, double s, double* l, double* d) {
   }
 }
 
-void curved_geometry(HostType& T, const double* nodes) {
-  const RefElement& R = T.ref;
-  const int nu = R.nupts, nf = R.nfpts, n1 = R.p + 1, ng = n1 * n1 * n1;
+// Nodal fields w[n][j][node] = X_l d X_m / d xi_j ((n, m, l) cyclic) of a
+// 27-node map at the Gauss-Lobatto tensor nodes g (n1 per direction).
+void curl_fields(const double* X, const std::vector<double>& g, double* w) {
+  const int n1 = int(g.size()), ng = n1 * n1 * n1;
+  for (int c = 0; c < n1; ++c)
+    for (int b = 0; b < n1; ++b)
+      for (int a = 0; a < n1; ++a) {
+        const int node = a + n1 * (b + n1 * c);
+        const double pt[3] = {g[a], g[b], g[c]};
+        double x[3], J[3][3];
+        q2_eval(X, pt, x, J);
+        for (int n = 0; n < 3; ++n) {
+          const int m = (n + 1) % 3, l = (n + 2) % 3;
+          for (int j = 0; j < 3; ++j) w[(size_t(n) * 3 + j) * ng + node] = x[l] * J[j][m];
+        }
+      }
+}
+
+// S[i][n] = -(curl_xi I(w^n))_i at one point, from its 1D Lagrange factors
+// L[3][n1] (values) and dL[3][n1] (derivatives) on the nodes.
+void curl_eval(int n1, const double* L, const double* dL, const double* w,
+               double S[3][3]) {
+  const int ng = n1 * n1 * n1;
+  double dw[3][3][3] = {};  // dw[n][j][i] = d_i I(w^n_j)
+  for (int c = 0; c < n1; ++c)
+    for (int b = 0; b < n1; ++b)
+      for (int a = 0; a < n1; ++a) {
+        const int node = a + n1 * (b + n1 * c);
+        const double B[3] = {dL[a] * L[n1 + b] * L[2 * n1 + c],
+                             L[a] * dL[n1 + b] * L[2 * n1 + c],
+                             L[a] * L[n1 + b] * dL[2 * n1 + c]};
+        for (int n = 0; n < 3; ++n)
+          for (int j = 0; j < 3; ++j) {
+            const double v = w[(size_t(n) * 3 + j) * ng + node];
+            for (int i = 0; i < 3; ++i) dw[n][j][i] += B[i] * v;
+          }
+      }
+  for (int i = 0; i < 3; ++i) {
+    const int j = (i + 1) % 3, k = (i + 2) % 3;
+    for (int n = 0; n < 3; ++n) S[i][n] = dw[n][j][k] - dw[n][k][j];
+  }
+}
+
+// 1D Lagrange factors of the Gauss-Lobatto nodes at np points: [np][3][n1].
+void curl_factors(const std::vector<double>& g, int np, const double* pts,
+                  std::vector<double>& L, std::vector<double>& dL) {
+  const int n1 = int(g.size());
+  L.resize(size_t(np) * 3 * n1);
+  dL.resize(size_t(np) * 3 * n1);
+  for (int q = 0; q < np; ++q)
+    for (int i = 0; i < 3; ++i)
+      lagrange1d(n1, g.data(), pts[3 * q + i], &L[(size_t(q) * 3 + i) * n1],
+                 &dL[(size_t(q) * 3 + i) * n1]);
+}
+
+std::vector<double> gll_nodes(int n1) {
   std::vector<double> g(n1);
   gauss_lobatto(n1, g.data());
-  // Cardinal-function factors at the solution and flux points.
-  auto factors = [&](int np, const double* pts, std::vector<double>& L,
-                     std::vector<double>& dL) {
-    L.resize(size_t(np) * 3 * n1);
-    dL.resize(size_t(np) * 3 * n1);
-    for (int q = 0; q < np; ++q)
-      for (int i = 0; i < 3; ++i)
-        lagrange1d(n1, g.data(), pts[3 * q + i], &L[(size_t(q) * 3 + i) * n1],
-                   &dL[(size_t(q) * 3 + i) * n1]);
-  };
+  return g;
+}
+
+// Runs body(e0, e1) over [0, ne) split across host threads; elements write
+// disjoint slices.  Falls back to the calling thread when none can start.
+template <typename F>
+void parallel_elements(int64_t ne, F body) {
+  const int64_t nthr = std::max<int64_t>(
+      1, std::min<int64_t>(std::thread::hardware_concurrency(), ne / 64));
+  std::vector<std::thread> pool;
+  int64_t t = 1;
+  try {
+    for (; t < nthr; ++t)
+      pool.emplace_back(body, ne * t / nthr, ne * (t + 1) / nthr);
+  } catch (const std::system_error&) {  // no more threads: the rest runs here
+    body(ne * t / nthr, ne);
+  }
+  body(0, ne / nthr);
+  for (auto& th : pool) th.join();
+}
+
+void curved_geometry(HostType& T) {
+  const RefElement& R = T.ref;
+  const int nu = R.nupts, nf = R.nfpts, n1 = R.p + 1, ng = n1 * n1 * n1;
+  const std::vector<double> g = gll_nodes(n1);
   std::vector<double> Lu, dLu, Lf, dLf;
-  factors(nu, R.upts.data(), Lu, dLu);
-  factors(nf, R.fpts.data(), Lf, dLf);
-  T.verts.resize(size_t(T.ne) * 8 * 3);
+  curl_factors(g, nu, R.upts.data(), Lu, dLu);
+  curl_factors(g, nf, R.fpts.data(), Lf, dLf);
   T.upts_x.resize(size_t(T.ne) * nu * 3);
   T.smat.resize(size_t(T.ne) * 9 * nu);
   T.rcpdjac.resize(size_t(T.ne) * nu);
   T.fpts_x.resize(size_t(T.ne) * nf * 3);
   T.fnvec.resize(size_t(T.ne) * nf * 3);
-  static const int corner[8] = {0, 2, 8, 6, 18, 20, 26, 24};
-  // Elements [e0, e1) with their own scratch; elements write disjoint slices,
-  // so ranges run on separate host threads.
-  auto range = [&](int64_t e0, int64_t e1) {
-  std::vector<double> X(27 * 3), w(size_t(3) * 3 * ng);  // w[n][j][node]
-  // S[i][n] at one point from the nodal fields w, given its 1D factors.
-  auto curl = [&](const double* L, const double* dL, double S[3][3]) {
-    double dw[3][3][3] = {};  // dw[n][j][i] = d_i I(w^n_j)
-    for (int c = 0; c < n1; ++c)
-      for (int b = 0; b < n1; ++b)
-        for (int a = 0; a < n1; ++a) {
-          const int node = a + n1 * (b + n1 * c);
-          const double B[3] = {dL[a] * L[n1 + b] * L[2 * n1 + c],
-                               L[a] * dL[n1 + b] * L[2 * n1 + c],
-                               L[a] * L[n1 + b] * dL[2 * n1 + c]};
-          for (int n = 0; n < 3; ++n)
-            for (int j = 0; j < 3; ++j) {
-              const double v = w[(size_t(n) * 3 + j) * ng + node];
-              for (int i = 0; i < 3; ++i) dw[n][j][i] += B[i] * v;
-            }
-        }
-    for (int i = 0; i < 3; ++i) {
-      const int j = (i + 1) % 3, k = (i + 2) % 3;
-      for (int n = 0; n < 3; ++n) S[i][n] = dw[n][j][k] - dw[n][k][j];
-    }
-  };
-  for (int64_t e = e0; e < e1; ++e) {
-    for (int v = 0; v < 27; ++v)
-      for (int k = 0; k < 3; ++k)
-        X[v * 3 + k] = nodes[T.map_conn[size_t(e) * 27 + v] * 3 + k];
-    for (int v = 0; v < 8; ++v)
-      for (int k = 0; k < 3; ++k)
-        T.verts[(size_t(e) * 8 + v) * 3 + k] = X[corner[v] * 3 + k];
-    for (int c = 0; c < n1; ++c)
-      for (int b = 0; b < n1; ++b)
-        for (int a = 0; a < n1; ++a) {
-          const int node = a + n1 * (b + n1 * c);
-          const double pt[3] = {g[a], g[b], g[c]};
-          double x[3], J[3][3];
-          q2_eval(X.data(), pt, x, J);
-          for (int n = 0; n < 3; ++n) {
-            const int m = (n + 1) % 3, l = (n + 2) % 3;
-            for (int j = 0; j < 3; ++j)
-              w[(size_t(n) * 3 + j) * ng + node] = x[l] * J[j][m];
-          }
-        }
-    for (int q = 0; q < nu; ++q) {
-      double x[3], J[3][3], S[3][3];
-      q2_eval(X.data(), &R.upts[3 * q], x, J);
-      for (int k = 0; k < 3; ++k) T.upts_x[(size_t(e) * nu + q) * 3 + k] = x[k];
-      const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
-                         J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
-                         J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
-      curl(&Lu[size_t(q) * 3 * n1], &dLu[size_t(q) * 3 * n1], S);
-      for (int i = 0; i < 3; ++i)
+  parallel_elements(T.ne, [&](int64_t e0, int64_t e1) {
+    std::vector<double> w(size_t(9) * ng);
+    for (int64_t e = e0; e < e1; ++e) {
+      const double* X = &T.mapx[size_t(e) * 81];
+      curl_fields(X, g, w.data());
+      for (int q = 0; q < nu; ++q) {
+        double x[3], J[3][3], S[3][3];
+        q2_eval(X, &R.upts[3 * q], x, J);
+        for (int k = 0; k < 3; ++k) T.upts_x[(size_t(e) * nu + q) * 3 + k] = x[k];
+        const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                           J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                           J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+        curl_eval(n1, &Lu[size_t(q) * 3 * n1], &dLu[size_t(q) * 3 * n1], w.data(), S);
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j) T.smat[(size_t(e) * 9 + i * 3 + j) * nu + q] = S[i][j];
+        T.rcpdjac[size_t(e) * nu + q] = det > 0 ? 1.0 / det : -1.0;
+      }
+      for (int q = 0; q < nf; ++q) {
+        double x[3], J[3][3], S[3][3];
+        q2_eval(X, &R.fpts[3 * q], x, J);
+        for (int k = 0; k < 3; ++k) T.fpts_x[(size_t(e) * nf + q) * 3 + k] = x[k];
+        curl_eval(n1, &Lf[size_t(q) * 3 * n1], &dLf[size_t(q) * 3 * n1], w.data(), S);
+        const double* n = &R.fnorm[3 * q];
         for (int j = 0; j < 3; ++j)
-          T.smat[(size_t(e) * 9 + i * 3 + j) * nu + q] = S[i][j];
-      T.rcpdjac[size_t(e) * nu + q] = det > 0 ? 1.0 / det : -1.0;
+          T.fnvec[(size_t(e) * nf + q) * 3 + j] =
+              S[0][j] * n[0] + S[1][j] * n[1] + S[2][j] * n[2];
+      }
     }
-    for (int q = 0; q < nf; ++q) {
-      double x[3], J[3][3], S[3][3];
-      q2_eval(X.data(), &R.fpts[3 * q], x, J);
-      for (int k = 0; k < 3; ++k) T.fpts_x[(size_t(e) * nf + q) * 3 + k] = x[k];
-      curl(&Lf[size_t(q) * 3 * n1], &dLf[size_t(q) * 3 * n1], S);
-      const double* n = &R.fnorm[3 * q];
-      for (int j = 0; j < 3; ++j)
-        T.fnvec[(size_t(e) * nf + q) * 3 + j] =
-            S[0][j] * n[0] + S[1][j] * n[1] + S[2][j] * n[2];
-    }
-  }
-  };
-  const int64_t nthr = std::max<int64_t>(
-      1, std::min<int64_t>(std::thread::hardware_concurrency(), T.ne / 64));
-  std::vector<std::thread> pool;
-  int64_t t = 1;
-  try {
-    for (; t < nthr; ++t)
-      pool.emplace_back(range, T.ne * t / nthr, T.ne * (t + 1) / nthr);
-  } catch (const std::system_error&) {  // no more threads: the rest runs here
-    range(T.ne * t / nthr, T.ne);
-  }
-  range(0, T.ne / nthr);
-  for (auto& th : pool) th.join();
+  });
 }
 
 }  // namespace
+
+void metric_points(const HostType& T, int np, const double* pts,
+                   std::vector<double>& S) {
+  const RefElement& R = T.ref;
+  S.assign(size_t(T.ne) * 9 * np, 0.0);
+  if (T.map_order == 2) {
+    const int n1 = R.p + 1, ng = n1 * n1 * n1;
+    const std::vector<double> g = gll_nodes(n1);
+    std::vector<double> L, dL;
+    curl_factors(g, np, pts, L, dL);
+    parallel_elements(T.ne, [&](int64_t e0, int64_t e1) {
+      std::vector<double> w(size_t(9) * ng);
+      for (int64_t e = e0; e < e1; ++e) {
+        curl_fields(&T.mapx[size_t(e) * 81], g, w.data());
+        for (int q = 0; q < np; ++q) {
+          double M[3][3];
+          curl_eval(n1, &L[size_t(q) * 3 * n1], &dL[size_t(q) * 3 * n1], w.data(), M);
+          for (int r = 0; r < 9; ++r) S[(size_t(e) * 9 + r) * np + q] = M[r / 3][r % 3];
+        }
+      }
+    });
+    return;
+  }
+  const int nv = R.nverts;
+  std::vector<double> dN(size_t(np) * 3 * nv);
+  for (int q = 0; q < np; ++q) R.dshape(&pts[3 * q], &dN[size_t(q) * 3 * nv]);
+  for (int64_t e = 0; e < T.ne; ++e) {
+    const double* X = &T.verts[size_t(e) * nv * 3];
+    for (int q = 0; q < np; ++q) {
+      double a[3][3];  // a[j] = d x / d x~_j
+      for (int j = 0; j < 3; ++j)
+        for (int k = 0; k < 3; ++k) {
+          double v = 0.0;
+          for (int i = 0; i < nv; ++i) v += dN[(size_t(q) * 3 + j) * nv + i] * X[i * 3 + k];
+          a[j][k] = v;
+        }
+      for (int i = 0; i < 3; ++i) {
+        const double* b = a[(i + 1) % 3];
+        const double* c = a[(i + 2) % 3];
+        const double row[3] = {b[1] * c[2] - b[2] * c[1], b[2] * c[0] - b[0] * c[2],
+                               b[0] * c[1] - b[1] * c[0]};
+        for (int j = 0; j < 3; ++j) S[(size_t(e) * 9 + i * 3 + j) * np + q] = row[j];
+      }
+    }
+  }
+}
 
 std::string build_mesh(const MeshInput& in, std::vector<HostType>& types,
                        HostConn& conn, bool* err_mesh) {
@@ -333,7 +392,17 @@ std::string build_mesh(const MeshInput& in, std::vector<HostType>& types,
           if (T.map_conn[size_t(e) * 27 + corner[v]] != T.conn[size_t(e) * 8 + v])
             return "map corner nodes differ from the element vertices";
       }
-      curved_geometry(T, in.nodes);
+      T.mapx.resize(size_t(T.ne) * 81);
+      T.verts.resize(size_t(T.ne) * 24);
+      for (int64_t e = 0; e < T.ne; ++e) {
+        for (int v = 0; v < 27; ++v)
+          for (int k = 0; k < 3; ++k)
+            T.mapx[(size_t(e) * 27 + v) * 3 + k] = in.nodes[T.map_conn[size_t(e) * 27 + v] * 3 + k];
+        for (int v = 0; v < 8; ++v)
+          for (int k = 0; k < 3; ++k)
+            T.verts[(size_t(e) * 8 + v) * 3 + k] = T.mapx[(size_t(e) * 27 + corner[v]) * 3 + k];
+      }
+      curved_geometry(T);
     } else {
       geometry(T, in.nodes);
     }

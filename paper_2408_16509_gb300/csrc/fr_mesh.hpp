@@ -21,6 +21,12 @@ struct HostType {
   std::vector<int64_t> conn;     // [ne][nv]
   int map_order = 1;             // 2: quadratic (27-node) hexahedron map
   std::vector<int64_t> map_conn; // [ne][27] (map_order 2)
+  std::vector<double> mapx;      // [ne][27][3] map node coordinates (map_order 2)
+  // anti-aliasing (Section 3.2): rule of degree aa_qdeg and its operators
+  int aa_qdeg = 0;
+  std::vector<double> aa_x, aa_w;  // [nq][3], [nq]
+  std::vector<double> aa_B;        // [nq][nupts]
+  std::vector<double> aa_P;        // [nupts][nq]
   std::vector<double> verts;     // [ne][nv][3]
   std::vector<double> upts_x;    // [ne][nupts][3]
   std::vector<double> smat;      // [ne][9][nupts]   S[i][j] = row i, col j
@@ -57,6 +63,12 @@ struct MeshInput {
   const int* bface_tags = nullptr;
   std::vector<int> bc_tags;              // tag of bc index i
 };
+
+// S = det J J^{-1} of every element at reference points pts [np][3], laid
+// out [ne][9][np]: the curl form on curved elements, the map's cross
+// products on straight ones (the metric the mesh itself uses).
+void metric_points(const HostType& T, int np, const double* pts,
+                   std::vector<double>& S);
 
 // Returns an empty string on success, else an error message.  ``err_mesh``
 // is set when the failure is a non-conforming / unmatched mesh.

@@ -115,6 +115,95 @@ void gauss_lobatto(int n, double* x) {
   }
 }
 
+void gauss_jacobi(int n, double a, double b, double* x, double* w) {
+  // Nodes: roots of the degree-n orthonormal Jacobi polynomial by Newton's
+  // method, each iteration deflated by the roots already found.  Weights:
+  // Christoffel numbers 1 / sum_{k<n} p_k(x_i)^2 of the orthonormal family.
+  for (int k = 0; k < n; ++k) {
+    double z = -std::cos(M_PI * (2.0 * k + 1.0) / (2.0 * n));
+    if (k > 0) z = 0.5 * (z + x[k - 1]);
+    for (int it = 0; it < 200; ++it) {
+      double s = 0.0;
+      for (int j = 0; j < k; ++j) s += 1.0 / (z - x[j]);
+      const double p = jacobi_p(n, a, b, z);
+      const double dz = -p / (jacobi_dp(n, a, b, z) - p * s);
+      z += dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    x[k] = z;
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j)
+      if (x[j] < x[i]) std::swap(x[i], x[j]);
+  for (int i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int k = 0; k < n; ++k) {
+      const double p = jacobi_p(k, a, b, x[i]);
+      s += p * p;
+    }
+    w[i] = 1.0 / s;
+  }
+}
+
+void aa_rule(int kind, int qdeg, std::vector<double>& xq, std::vector<double>& wq) {
+  const int n = qdeg / 2 + 1;
+  std::vector<double> xa(n), wa(n), xb(n), wb(n), xc(n), wc(n);
+  gauss_legendre(n, xa.data(), wa.data());
+  if (kind == EK_HEX) {
+    xb = xc = xa;
+    wb = wc = wa;
+  } else if (kind == EK_PRI) {
+    gauss_jacobi(n, 1.0, 0.0, xb.data(), wb.data());
+    xc = xa;
+    wc = wa;
+  } else {
+    gauss_jacobi(n, 1.0, 0.0, xb.data(), wb.data());
+    gauss_jacobi(n, 2.0, 0.0, xc.data(), wc.data());
+  }
+  xq.clear();
+  wq.clear();
+  for (int k = 0; k < n; ++k)
+    for (int j = 0; j < n; ++j)
+      for (int i = 0; i < n; ++i) {
+        const double A = xa[i], B = xb[j], C = xc[k];
+        const double w = wa[i] * wb[j] * wc[k];
+        if (kind == EK_HEX) {
+          xq.insert(xq.end(), {A, B, C});
+          wq.push_back(w);
+        } else if (kind == EK_PRI) {  // (a, b) -> triangle, Jacobian (1-b)/2
+          xq.insert(xq.end(), {0.5 * (1 + A) * (1 - B) - 1, B, C});
+          wq.push_back(0.5 * w);
+        } else {  // Jacobian (1-b)(1-c)^2 / 8: weights of the Jacobi factors
+          xq.insert(xq.end(), {0.25 * (1 + A) * (1 - B) * (1 - C) - 1,
+                               0.5 * (1 + B) * (1 - C) - 1, C});
+          wq.push_back(0.125 * w);
+        }
+      }
+}
+
+void aa_operators(const RefElement& R, const std::vector<double>& xq,
+                  const std::vector<double>& wq, std::vector<double>& B,
+                  std::vector<double>& P) {
+  const int nu = R.nupts, nq = int(wq.size());
+  std::vector<double> phi(size_t(nq) * nu), V(size_t(nu) * nu);
+  R.basis(nq, xq.data(), phi.data());
+  R.basis(nu, R.upts.data(), V.data());
+  B.assign(size_t(nq) * nu, 0.0);
+  for (int q = 0; q < nq; ++q)
+    for (int z = 0; z < nu; ++z) {
+      double s = 0.0;
+      for (int k = 0; k < nu; ++k) s += phi[size_t(q) * nu + k] * R.vdm_inv[size_t(k) * nu + z];
+      B[size_t(q) * nu + z] = s;
+    }
+  P.assign(size_t(nu) * nq, 0.0);
+  for (int z = 0; z < nu; ++z)
+    for (int q = 0; q < nq; ++q) {
+      double s = 0.0;
+      for (int k = 0; k < nu; ++k) s += V[size_t(z) * nu + k] * phi[size_t(q) * nu + k];
+      P[size_t(z) * nq + q] = s * wq[q];
+    }
+}
+
 bool invert(int n, const double* A, double* Ainv) {
   std::vector<double> a(A, A + n * n);
   std::vector<int> piv(n);

@@ -58,6 +58,18 @@ RefElement make_ref(int kind, int p);
 // 1D helpers (exposed for unit use)
 void gauss_legendre(int n, double* x, double* w);
 void gauss_lobatto(int n, double* x);
+// n-point Gauss rule of the weight (1-x)^a (1+x)^b on [-1, 1], ascending.
+void gauss_jacobi(int n, double a, double b, double* x, double* w);
+// Anti-aliasing (Section 3.2): volume rule exact to degree qdeg, n = qdeg/2+1
+// points per direction (n^3 points on every type): tensor Gauss-Legendre on
+// the hexahedron; collapsed products with Gauss-Jacobi (1,0) / (2,0) factors
+// on the prism's triangle and the tetrahedron.  xq [nq][3], wq [nq].
+void aa_rule(int kind, int qdeg, std::vector<double>& xq, std::vector<double>& wq);
+// B [nq][nupts]: l_z(x_q);  P [nupts][nq]: least-squares projection onto the
+// solution space, P = V Phi_q^T diag(w) with the orthonormal basis Phi.
+void aa_operators(const RefElement& R, const std::vector<double>& xq,
+                  const std::vector<double>& wq, std::vector<double>& B,
+                  std::vector<double>& P);
 double jacobi_p(int n, double a, double b, double x);
 double jacobi_dp(int n, double a, double b, double x);
 bool invert(int n, const double* A, double* Ainv);

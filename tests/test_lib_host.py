@@ -138,3 +138,31 @@ def test_curved_maps_are_validated():
     m.maps = {"pri": (2, np.zeros((len(m.elements["pri"]), 27), np.int64))}
     with pytest.raises(fr.FRError):
         fr.FRMesh(m, 2, device=-1)
+
+
+@pytest.mark.parametrize("name", ["hex", "mixed", "curved"])
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_antialias_operators_match_oracle(name, p):
+    """Anti-aliasing rule (points, weights), interpolation B and projection
+    P of every type against the oracle's.  The two enumerate the rule's
+    points in different orders: points are matched by coordinates."""
+    spec = SPECS[name]()
+    bcs = {k: ("extrap",) for k in range(6)}
+    g = fr.FRMesh(spec, p, bcs=bcs, device=-1)
+    o = OracleMesh(spec.as_dict(), p)
+    qdeg = 3 * p
+    g.set_antialias(qdeg)
+    for t in g.types:
+        xo, wo, Bo, Po = o.el[t].aa_operators(qdeg)
+        x = g.operator(t, "aa_qpts")
+        assert x.shape == xo.shape
+        d = np.linalg.norm(x[:, None, :] - xo[None, :, :], axis=2)
+        perm = d.argmin(axis=1)
+        assert np.abs(d[np.arange(len(x)), perm]).max() < 1e-14
+        assert len(set(perm.tolist())) == len(x)
+        assert np.abs(g.operator(t, "aa_qwts") - wo[perm]).max() < 1e-15
+        assert np.abs(g.operator(t, "aa_B") - Bo[perm]).max() < 1e-13
+        assert np.abs(g.operator(t, "aa_P") - Po[:, perm]).max() < 1e-13
+    g.set_antialias(0)
+    with pytest.raises(fr.FRError):
+        g.operator(g.types[0], "aa_B")
