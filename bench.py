@@ -553,6 +553,32 @@ def config_tgv_curved(fr, torch, device, steps=10):
     return out
 
 
+def config_tgv_antialias(fr, torch, device, steps=10, qdeg=9):
+    """TGV 32^3 p=3 (the bench workload) with the anti-aliased flux of
+    Section 3.2: transformed flux at the 125 points of a degree-9 Gauss rule,
+    projected back by least squares.  FP64 and FP32, beside collocation."""
+    spec = workload_spec(N_CELLS)
+    out = {"qdeg": qdeg}
+    for prec in ("fp64", "fp32"):
+        mesh = fr.FRMesh(spec, ORDER, physics="ns", gamma=1.4, mu=1.0 / RE,
+                         prandtl=PR, precision=prec, device=device)
+        mesh.set_antialias(qdeg)
+        st = torch.cuda.Stream(device=device)
+        mesh.set_stream(st)
+        u0 = _state(mesh, tgv)
+        mesh.set_solution(u0)
+        mesh.rk_step("rk45", 1e-3, 2)
+        mesh.set_solution(u0)
+        ms = _timed_steps(torch, mesh, st, "rk45", 1e-3, steps)
+        prof = mesh.profile_step("rk45", 1e-3)
+        active, _ = mesh.tuning()
+        out[prec] = {"gdof_stage_s": _gdofs(mesh, 5, steps, ms),
+                     "ms_per_step": ms / steps, "kernel_family": active,
+                     "kernel_ms_per_step": {k: v[0] for k, v in prof.items() if v[1]}}
+        mesh.close()
+    return out
+
+
 def config_shu_osher(fr, torch, device, steps=40):
     """256x8x8 hexes on [-5,5]x[0,0.3125]^2, p=3, Euler, RK4 dt 9e-4, FP32,
     entropy filter: plain root-find, then the predictor trained on the
@@ -620,6 +646,7 @@ def other_configs(fr, torch, device):
                      ("mixed_elements_40^3_p3_fp32", config_mixed_elements),
                      ("tgv_32^3_p3_fp32_adaptive", config_tgv_adaptive),
                      ("tgv_32^3_p3_curved", config_tgv_curved),
+                     ("tgv_32^3_p3_antialias_q9", config_tgv_antialias),
                      ("shu_osher_256x8x8_p3_filter", config_shu_osher)):
         try:
             out[name] = fn(fr, torch, device)
@@ -709,7 +736,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", default=None,
                     choices=["vortex", "tgv48", "mixed", "shu_osher", "adaptive",
-                             "curved"],
+                             "curved", "antialias"],
                     help="run one side workload alone and print its record "
                          "(profiling aid; not a contract line)")
     ap.add_argument("--cells", type=int, default=40,
@@ -728,6 +755,7 @@ def main():
         fns = {"vortex": config_vortex, "tgv48": config_tgv48_mixed,
                "adaptive": config_tgv_adaptive,
                "curved": config_tgv_curved,
+               "antialias": config_tgv_antialias,
                "shu_osher": config_shu_osher,
                "mixed": lambda f, t, d: config_mixed_elements(
                    f, t, d, steps=args.steps, cells=args.cells,

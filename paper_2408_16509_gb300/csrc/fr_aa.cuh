@@ -120,4 +120,185 @@ __global__ void __launch_bounds__(kAaThreads)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Hexahedra, sum-factorised.  The basis, the solution points and the rule are
+// tensor products, so B = B1 (x) B1 (x) B1 and P = P1 (x) P1 (x) P1 with the 1D
+// factors B1[i][a] = l_a(x_i) (Q rule points, N solution points per line) and
+// P1[a][i] = w_i sum_m psi_m(x_a) psi_m(x_i) (orthonormal Legendre psi).
+// Each operator is applied one direction at a time: 20 fields (u and the
+// gradient) go N -> Q along x, y, z; the transformed flux (15 fields) comes
+// back Q -> N along z, y, x.  One thread takes one line of a pass (N loads,
+// Q outputs or the reverse), so shared memory is read once per line.
+constexpr int kAaQMax = 13;  // qdeg <= 24
+
+template <typename T>
+struct HexAaOps {
+  T b1[kAaQMax][5];  // [Q][N]
+  T p1[5][kAaQMax];  // [N][Q]
+  int q;
+};
+
+// shared memory of one element: ping-pong buffers A and B (T values)
+__host__ __device__ inline int hex_aa_buf_a(int n, int q) {
+  return 20 * n * (n * n > q * q ? n * n : q * q);
+}
+__host__ __device__ inline int hex_aa_buf_b(int n, int q) {
+  return 20 * q * (n * n > q * q ? n * n : q * q);
+}
+constexpr int kAaOpsT = 2 * kAaQMax * 5;  // staged b1 and p1 (T values)
+template <typename T>
+inline size_t hex_aa_smem(int n, int q) {
+  return size_t(kAaOpsT + hex_aa_buf_a(n, q) + hex_aa_buf_b(n, q)) * sizeof(T);
+}
+
+// QT > 0: the rule's point count per direction is a compile-time constant
+// (loops unroll and the 1D coefficients are read as constant operands);
+// QT = 0: any Q, coefficients from shared memory.
+template <typename T, typename TR, int N, int QT, bool NS>
+__global__ void __launch_bounds__(kAaThreads)
+    k_hex_aa_flux(long long ne, const T* __restrict__ uin,
+                  const TR* __restrict__ X, const T* __restrict__ grad,
+                  const T* __restrict__ smq, HexAaOps<T> op, Phys<T> ph,
+                  T* __restrict__ tf) {
+  constexpr int NU = N * N * N;
+  constexpr int NFLD = NS ? 20 : 5;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int Q = QT > 0 ? QT : op.q, Q2 = Q * Q, Q3 = Q2 * Q;
+  T* b1 = reinterpret_cast<T*>(smem_raw);  // [Q][N]
+  T* p1 = b1 + kAaQMax * 5;                // [N][Q]
+  T* A = b1 + kAaOpsT;
+  T* Bf = A + hex_aa_buf_a(N, Q);
+  const int t = threadIdx.x, nt = blockDim.x;
+  for (int i = t; i < Q * N; i += nt) {
+    b1[i] = op.b1[i / N][i % N];
+    p1[i] = op.p1[i / Q][i % Q];
+  }
+  auto cb = [&](int i, int a) -> T { return QT > 0 ? op.b1[i][a] : b1[i * N + a]; };
+  auto cp = [&](int a, int i) -> T { return QT > 0 ? op.p1[a][i] : p1[a * Q + i]; };
+  for (long long e = blockIdx.x; e < ne; e += gridDim.x) {
+    // A[f][c][b][a] <- u (5 fields), then the gradient (15)
+    for (int i = t; i < 5 * NU; i += nt)
+      A[i] = uin ? uin[e * 5 * NU + i] : T(X[e * 5 * NU + i]);
+    if (NS)
+      for (int i = t; i < 15 * NU; i += nt) A[5 * NU + i] = grad[e * 15 * NU + i];
+    __syncthreads();
+    // x: A[f][c][b][a] -> Bf[f][c][b][i]
+    for (int l = t; l < NFLD * N * N; l += nt) {
+      T in[N];
+#pragma unroll
+      for (int a = 0; a < N; ++a) in[a] = A[l * N + a];
+#pragma unroll
+      for (int i = 0; i < (QT > 0 ? QT : Q); ++i) {
+        T s = T(0);
+#pragma unroll
+        for (int a = 0; a < N; ++a) s += cb(i, a) * in[a];
+        Bf[l * Q + i] = s;
+      }
+    }
+    __syncthreads();
+    // y: Bf[f][c][b][i] -> A[f][c][j][i]   (line = (f, c), i)
+    for (int l = t; l < NFLD * N * Q; l += nt) {
+      const int fc = l / Q, i = l - fc * Q;
+      T in[N];
+#pragma unroll
+      for (int b = 0; b < N; ++b) in[b] = Bf[(fc * N + b) * Q + i];
+#pragma unroll
+      for (int j = 0; j < (QT > 0 ? QT : Q); ++j) {
+        T s = T(0);
+#pragma unroll
+        for (int b = 0; b < N; ++b) s += cb(j, b) * in[b];
+        A[(fc * Q + j) * Q + i] = s;
+      }
+    }
+    __syncthreads();
+    // z: A[f][c][j][i] -> Bf[f][k][j][i]   (line = f, (j, i))
+    for (int l = t; l < NFLD * Q2; l += nt) {
+      const int f = l / Q2, ji = l - f * Q2;
+      T in[N];
+#pragma unroll
+      for (int c = 0; c < N; ++c) in[c] = A[(f * N + c) * Q2 + ji];
+#pragma unroll
+      for (int k = 0; k < (QT > 0 ? QT : Q); ++k) {
+        T s = T(0);
+#pragma unroll
+        for (int c = 0; c < N; ++c) s += cb(k, c) * in[c];
+        Bf[(f * Q + k) * Q2 + ji] = s;
+      }
+    }
+    __syncthreads();
+    // flux at every quadrature point, transformed, written in place
+    for (int pt = t; pt < Q3; pt += nt) {
+      T uq[5];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) uq[k] = Bf[k * Q3 + pt];
+      T F[3][5];
+      euler_flux(uq, ph, F);
+      if (NS) {
+        T g[3][5];
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+          for (int k = 0; k < 5; ++k) g[j][k] = Bf[(5 + j * 5 + k) * Q3 + pt];
+        viscous_flux_acc(uq, g, ph, T(-1), F);
+      }
+      T S[3][3];
+#pragma unroll
+      for (int r = 0; r < 9; ++r) S[r / 3][r % 3] = smq[(e * 9 + r) * Q3 + pt];
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+          Bf[(d * 5 + k) * Q3 + pt] = S[d][0] * F[0][k] + S[d][1] * F[1][k] + S[d][2] * F[2][k];
+    }
+    __syncthreads();
+    // z back: Bf[f][k][j][i] -> A[f][c][j][i]
+    for (int l = t; l < 15 * Q2; l += nt) {
+      const int f = l / Q2, ji = l - f * Q2;
+      T acc[N];
+#pragma unroll
+      for (int c = 0; c < N; ++c) acc[c] = T(0);
+#pragma unroll
+      for (int k = 0; k < (QT > 0 ? QT : Q); ++k) {
+        const T v = Bf[(f * Q + k) * Q2 + ji];
+#pragma unroll
+        for (int c = 0; c < N; ++c) acc[c] += cp(c, k) * v;
+      }
+#pragma unroll
+      for (int c = 0; c < N; ++c) A[(f * N + c) * Q2 + ji] = acc[c];
+    }
+    __syncthreads();
+    // y back: A[f][c][j][i] -> Bf[f][c][b][i]
+    for (int l = t; l < 15 * N * Q; l += nt) {
+      const int fc = l / Q, i = l - fc * Q;
+      T acc[N];
+#pragma unroll
+      for (int b = 0; b < N; ++b) acc[b] = T(0);
+#pragma unroll
+      for (int j = 0; j < (QT > 0 ? QT : Q); ++j) {
+        const T v = A[(fc * Q + j) * Q + i];
+#pragma unroll
+        for (int b = 0; b < N; ++b) acc[b] += cp(b, j) * v;
+      }
+#pragma unroll
+      for (int b = 0; b < N; ++b) Bf[(fc * N + b) * Q + i] = acc[b];
+    }
+    __syncthreads();
+    // x back: Bf[f][c][b][i] -> tf[e][f][c][b][a]
+    for (int l = t; l < 15 * N * N; l += nt) {
+      T acc[N];
+#pragma unroll
+      for (int a = 0; a < N; ++a) acc[a] = T(0);
+#pragma unroll
+      for (int i = 0; i < (QT > 0 ? QT : Q); ++i) {
+        const T v = Bf[l * Q + i];
+#pragma unroll
+        for (int a = 0; a < N; ++a) acc[a] += cp(a, i) * v;
+      }
+#pragma unroll
+      for (int a = 0; a < N; ++a) tf[e * 15 * NU + l * N + a] = acc[a];
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace frgb

@@ -122,6 +122,11 @@ struct DevType {
   void* aasmq = nullptr;     // [ne][9][nq]
   void* tf = nullptr;        // [ne][3][5][nu]
   int aa_nq = 0, aa_ctas = 1;
+  bool aa_hex = false;        // sum-factorised hexahedron form fits
+  bool aa_dense = false;      // dense form fits
+  int aa_hex_ctas = 1;
+  HexAaOps<double> hxaa64{};
+  HexAaOps<float> hxaa32{};
   // tensor-core kernels (prisms / tetrahedra, FP32 values)
   bool tc_ok = false;
   bool tca_ok = false;       // data-as-A volume kernel available
@@ -575,6 +580,12 @@ bool use_tc_vol(const fr_mesh* m, const DevType& D) {
 
 // Anti-aliased transformed flux of one element type (Section 3.2) into D.tf;
 // the volume kernel then reads it instead of collocating the flux.
+template <typename T>
+const HexAaOps<T>& hexaa_of(const DevType& D) {
+  if constexpr (sizeof(T) == 8) return D.hxaa64;
+  else return D.hxaa32;
+}
+
 template <typename T, typename TR>
 void launch_aa_flux(fr_mesh* m, const DevType& D, cudaStream_t s, bool from_x,
                     bool ns, const Phys<T>& ph) {
@@ -583,6 +594,31 @@ void launch_aa_flux(fr_mesh* m, const DevType& D, cudaStream_t s, bool from_x,
   const T* uin = hexk ? (from_x ? nullptr : (const T*)D.Y)
                       : (from_x ? (const T*)D.X : (const T*)D.Y);
   const TR* X = hexk ? (const TR*)D.X : nullptr;
+  if (hexk && D.aa_hex) {
+    const HexAaOps<T>& hop = hexaa_of<T>(D);
+    hex_dispatch(m->order, [&](auto n) {
+      constexpr int N = decltype(n)::value;
+      const unsigned grid = unsigned(std::min<long long>(D.ne, (long long)m->num_sms * D.aa_hex_ctas));
+      const size_t sm = hex_aa_smem<T>(N, hop.q);
+      auto go = [&](auto qt) {
+        constexpr int QT = decltype(qt)::value;
+        if (ns)
+          k_hex_aa_flux<T, TR, N, QT, true><<<grid, kAaThreads, sm, s>>>(
+              D.ne, uin, X, (const T*)D.grad, (const T*)D.aasmq, hop, ph, (T*)D.tf);
+        else
+          k_hex_aa_flux<T, TR, N, QT, false><<<grid, kAaThreads, sm, s>>>(
+              D.ne, uin, X, nullptr, (const T*)D.aasmq, hop, ph, (T*)D.tf);
+      };
+      // compile-time point counts for FP32 values (the FP64 form is bound by
+      // FP64 arithmetic, where the coefficient loads cost nothing extra)
+      if constexpr (sizeof(T) == 4) {
+        if (hop.q == N + 1) return go(std::integral_constant<int, N + 1>{});
+        if (hop.q == N + 2) return go(std::integral_constant<int, N + 2>{});
+      }
+      go(std::integral_constant<int, 0>{});
+    });
+    return;
+  }
   const AaOps<T> op{(const T*)D.aaBT, (const T*)D.aaPT, D.aa_nq};
   dispatch(D.kind, m->order, [&](auto nu, auto nf) {
     constexpr int NU = decltype(nu)::value;
@@ -1207,11 +1243,12 @@ int build_graph(fr_mesh* m, int scheme) {
 // unchanged.
 template <typename T, typename TR>
 int resolve_variant(fr_mesh* m, int scheme, double dt) {
-  bool has_hex = false, has_tc = false, curved = false;
+  bool has_hex = false, has_tc = false, curved = false, dense_aa_ok = true;
   for (auto& D : m->types) {
     has_hex |= D.kind == EK_HEX;
     has_tc |= D.tc_ok;
     curved |= D.curved;
+    dense_aa_ok &= m->aa_qdeg == 0 || D.kind != EK_HEX || D.aa_dense;
   }
   // The vertex-metric family rebuilds trilinear metrics in the kernel: not
   // for curved (quadratic-map) hexahedra, whose metrics are the tables, nor
@@ -1220,6 +1257,7 @@ int resolve_variant(fr_mesh* m, int scheme, double dt) {
   if (m->variant != FR_VARIANT_AUTO) {
     int v = m->variant;
     if (v == FR_VARIANT_SUMFACT_VERTEX && !vertex_ok) v = FR_VARIANT_SUMFACT;
+    if (v == FR_VARIANT_DENSE && !dense_aa_ok) v = FR_VARIANT_SUMFACT;
     if (v == FR_VARIANT_TENSOR && !has_tc) v = FR_VARIANT_SUMFACT;
     bool changed = v != m->active;
     for (auto& D : m->types) {  // a requested tensor family: every capable type
@@ -1236,7 +1274,7 @@ int resolve_variant(fr_mesh* m, int scheme, double dt) {
   if (m->tuned || !(has_hex || has_tc)) return FR_OK;
   std::vector<int> cand = {FR_VARIANT_SUMFACT};
   if (has_hex && vertex_ok) cand.push_back(FR_VARIANT_SUMFACT_VERTEX);
-  if (has_hex && m->precision != FR_MIXED) cand.push_back(FR_VARIANT_DENSE);
+  if (has_hex && m->precision != FR_MIXED && dense_aa_ok) cand.push_back(FR_VARIANT_DENSE);
   if (has_tc) cand.push_back(FR_VARIANT_TENSOR);
   std::vector<void*> saved;
   auto release = [&]() {
@@ -1532,9 +1570,57 @@ int aa_setup(fr_mesh* m) {
     dispatch(D.kind, m->order, [&](auto nuc, auto) {
       need = aa_dense_smem<T, decltype(nuc)::value>(nq);
     });
-    if (need > size_t(smax)) {
+    const int q1 = m->aa_qdeg / 2 + 1, n1 = m->order + 1;
+    D.aa_hex = D.kind == EK_HEX && q1 <= kAaQMax && hex_aa_smem<T>(n1, q1) <= size_t(smax);
+    D.aa_dense = need <= size_t(smax);
+    if (need > size_t(smax) && !D.aa_hex) {
       m->aa_qdeg = 0;
       return fail(FR_EINVAL, "quadrature rule too large for the shared memory of a block");
+    }
+    if (D.aa_hex) {
+      // 1D factors: Lagrange values of the solution points at the rule's
+      // Gauss points, and the 1D least-squares projection back.
+      std::vector<double> xg(q1), wg(q1);
+      gauss_legendre(q1, xg.data(), wg.data());
+      const std::vector<double>& xs = H.ref.x1;
+      HexAaOps<double> o64{};
+      HexAaOps<float> o32{};
+      o64.q = o32.q = q1;
+      for (int i = 0; i < q1; ++i)
+        for (int a = 0; a < n1; ++a) {
+          double l = 1.0;
+          for (int k = 0; k < n1; ++k)
+            if (k != a) l *= (xg[i] - xs[k]) / (xs[a] - xs[k]);
+          double pr = 0.0;
+          for (int mm = 0; mm < n1; ++mm)
+            pr += jacobi_p(mm, 0.0, 0.0, xs[a]) * jacobi_p(mm, 0.0, 0.0, xg[i]);
+          o64.b1[i][a] = l;
+          o64.p1[a][i] = wg[i] * pr;
+          o32.b1[i][a] = float(l);
+          o32.p1[a][i] = float(wg[i] * pr);
+        }
+      D.hxaa64 = o64;
+      D.hxaa32 = o32;
+      hex_dispatch(m->order, [&](auto nc) {
+        constexpr int N = decltype(nc)::value;
+        const int sm = int(hex_aa_smem<T>(N, q1));
+        int amin = 1 << 20;
+        auto attr = [&](auto fn) {
+          int a = 0;
+          cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, fn, kAaThreads, sm);
+          amin = std::min(amin, a);
+        };
+        attr(k_hex_aa_flux<T, TR, N, 0, true>);
+        attr(k_hex_aa_flux<T, TR, N, 0, false>);
+        if constexpr (sizeof(T) == 4) {
+          attr(k_hex_aa_flux<T, TR, N, N + 1, true>);
+          attr(k_hex_aa_flux<T, TR, N, N + 1, false>);
+          attr(k_hex_aa_flux<T, TR, N, N + 2, true>);
+          attr(k_hex_aa_flux<T, TR, N, N + 2, false>);
+        }
+        D.aa_hex_ctas = amin > 0 ? amin : 1;
+      });
     }
     std::vector<double> bt(size_t(nu) * nq), pt(size_t(nq) * nu);
     for (int q = 0; q < nq; ++q)
@@ -1549,7 +1635,7 @@ int aa_setup(fr_mesh* m) {
     if ((rc = dev_upload<T>(m, smq, &D.aasmq))) return rc;
     if ((rc = dev_zeros(m, size_t(D.ne) * 15 * nu * sizeof(T), &D.tf))) return rc;
     D.aa_nq = nq;
-    dispatch(D.kind, m->order, [&](auto nuc, auto nfc) {
+    if (need <= size_t(smax)) dispatch(D.kind, m->order, [&](auto nuc, auto nfc) {
       constexpr int NU = decltype(nuc)::value;
       const int sm = int(aa_dense_smem<T, NU>(nq));
       int a = 0;

@@ -140,3 +140,17 @@ def test_aa_profile_and_tuner():
     assert "sumfact_vertex" not in ms and active in ms
     prof = g.profile_step("rk45", 1e-3)
     assert prof["aa_flux"][1] == 5 and prof["aa_flux"][0] > 0
+
+
+@pytest.mark.parametrize("qdeg", [7, 9, 11])
+def test_aa_fp32_hex_point_counts(qdeg):
+    """FP32 hexahedra with 4, 5 and 6 rule points per direction at p = 3
+    (the general kernel and both compile-time point counts)."""
+    o, osys, g = _pair("hex", 3, "ns", qdeg, precision="fp32")
+    g.set_variant("sumfact")
+    g.set_solution(lib_state(g, _tgv))
+    u = oracle_state(o, _tgv)
+    for _ in range(2):
+        u = rk.step(osys.rhs, u, 1e-3, "rk45")
+    g.rk_step("rk45", 1e-3, 2)
+    assert rel_l2(g.get_solution(), u).max() < 1e-6
