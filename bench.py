@@ -523,7 +523,7 @@ def config_mixed_elements(fr, torch, device, steps=20, cells=40, variant="auto")
     return out
 
 
-def config_tgv_curved(fr, torch, device, steps=10):
+def config_tgv_curved(fr, torch, device, steps=10, precisions=("fp64", "fp32")):
     """TGV on 32^3 curved hexahedra (quadratic maps, Section 3.4; nodes moved
     by 5% of the cell size in a smooth field) on [0, 2 pi]^3, p=3, NS Re
     1600, RK45 dt 1e-3: FP64 and FP32 beside the straight-element workload.
@@ -532,7 +532,7 @@ def config_tgv_curved(fr, torch, device, steps=10):
     t_setup = time.perf_counter()
     spec = curved_box_hex((N_CELLS,) * 3, hi=(2 * np.pi,) * 3)
     out = {}
-    for prec in ("fp64", "fp32"):
+    for prec in precisions:
         t0 = time.perf_counter()
         mesh = fr.FRMesh(spec, ORDER, physics="ns", gamma=1.4, mu=1.0 / RE,
                          prandtl=PR, precision=prec, device=device)
@@ -553,13 +553,14 @@ def config_tgv_curved(fr, torch, device, steps=10):
     return out
 
 
-def config_tgv_antialias(fr, torch, device, steps=10, qdeg=9):
+def config_tgv_antialias(fr, torch, device, steps=10, qdeg=9,
+                         precisions=("fp64", "fp32")):
     """TGV 32^3 p=3 (the bench workload) with the anti-aliased flux of
     Section 3.2: transformed flux at the 125 points of a degree-9 Gauss rule,
     projected back by least squares.  FP64 and FP32, beside collocation."""
     spec = workload_spec(N_CELLS)
     out = {"qdeg": qdeg}
-    for prec in ("fp64", "fp32"):
+    for prec in precisions:
         mesh = fr.FRMesh(spec, ORDER, physics="ns", gamma=1.4, mu=1.0 / RE,
                          prandtl=PR, precision=prec, device=device)
         mesh.set_antialias(qdeg)
@@ -741,6 +742,8 @@ def main():
                          "(profiling aid; not a contract line)")
     ap.add_argument("--cells", type=int, default=40,
                     help="cells per direction of the mixed-element box (--only mixed)")
+    ap.add_argument("--precisions", default="fp64,fp32",
+                    help="precisions of the curved / anti-aliased runs (--only)")
     ap.add_argument("--variant", default="auto",
                     help="kernel family of the mixed-element run (--only mixed)")
     args = ap.parse_args()
@@ -754,8 +757,10 @@ def main():
         torch.cuda.set_device(dev)
         fns = {"vortex": config_vortex, "tgv48": config_tgv48_mixed,
                "adaptive": config_tgv_adaptive,
-               "curved": config_tgv_curved,
-               "antialias": config_tgv_antialias,
+               "curved": lambda f, t, d: config_tgv_curved(
+                   f, t, d, precisions=tuple(args.precisions.split(","))),
+               "antialias": lambda f, t, d: config_tgv_antialias(
+                   f, t, d, precisions=tuple(args.precisions.split(","))),
                "shu_osher": config_shu_osher,
                "mixed": lambda f, t, d: config_mixed_elements(
                    f, t, d, steps=args.steps, cells=args.cells,

@@ -146,6 +146,43 @@ __host__ __device__ inline int hex_aa_buf_b(int n, int q) {
   return 20 * q * (n * n > q * q ? n * n : q * q);
 }
 constexpr int kAaOpsT = 2 * kAaQMax * 5;  // staged b1 and p1 (T values)
+
+// One line of N values from / to global memory; 16-byte vector accesses when
+// a line is a whole number of them (every line then starts 16-byte aligned).
+template <int N, typename S, typename T>
+__device__ __forceinline__ void aa_line_load(const S* __restrict__ p, T* v) {
+  if constexpr ((N * sizeof(S)) % 16 == 0) {
+    constexpr int W = 16 / sizeof(S);
+#pragma unroll
+    for (int j = 0; j < N / W; ++j) {
+      const uint4 r = *reinterpret_cast<const uint4*>(p + j * W);
+      const S* s = reinterpret_cast<const S*>(&r);
+#pragma unroll
+      for (int a = 0; a < W; ++a) v[j * W + a] = T(s[a]);
+    }
+  } else {
+#pragma unroll
+    for (int a = 0; a < N; ++a) v[a] = T(p[a]);
+  }
+}
+
+template <int N, typename T>
+__device__ __forceinline__ void aa_line_store(T* __restrict__ p, const T* v) {
+  if constexpr ((N * sizeof(T)) % 16 == 0) {
+    constexpr int W = 16 / sizeof(T);
+#pragma unroll
+    for (int j = 0; j < N / W; ++j) {
+      uint4 r;
+      T* s = reinterpret_cast<T*>(&r);
+#pragma unroll
+      for (int a = 0; a < W; ++a) s[a] = v[j * W + a];
+      *reinterpret_cast<uint4*>(p + j * W) = r;
+    }
+  } else {
+#pragma unroll
+    for (int a = 0; a < N; ++a) p[a] = v[a];
+  }
+}
 template <typename T>
 inline size_t hex_aa_smem(int n, int q) {
   return size_t(kAaOpsT + hex_aa_buf_a(n, q) + hex_aa_buf_b(n, q)) * sizeof(T);
@@ -175,18 +212,18 @@ __global__ void __launch_bounds__(kAaThreads)
   }
   auto cb = [&](int i, int a) -> T { return QT > 0 ? op.b1[i][a] : b1[i * N + a]; };
   auto cp = [&](int a, int i) -> T { return QT > 0 ? op.p1[a][i] : p1[a * Q + i]; };
+  __syncthreads();
   for (long long e = blockIdx.x; e < ne; e += gridDim.x) {
-    // A[f][c][b][a] <- u (5 fields), then the gradient (15)
-    for (int i = t; i < 5 * NU; i += nt)
-      A[i] = uin ? uin[e * 5 * NU + i] : T(X[e * 5 * NU + i]);
-    if (NS)
-      for (int i = t; i < 15 * NU; i += nt) A[5 * NU + i] = grad[e * 15 * NU + i];
-    __syncthreads();
-    // x: A[f][c][b][a] -> Bf[f][c][b][i]
+    // x: u (5 fields), then the gradient (15), read line by line from
+    // global memory: [f][c][b][a] -> Bf[f][c][b][i]
     for (int l = t; l < NFLD * N * N; l += nt) {
       T in[N];
-#pragma unroll
-      for (int a = 0; a < N; ++a) in[a] = A[l * N + a];
+      if (l >= 5 * N * N)
+        aa_line_load<N>(grad + e * 15 * NU + (l - 5 * N * N) * N, in);
+      else if (uin)
+        aa_line_load<N>(uin + e * 5 * NU + l * N, in);
+      else
+        aa_line_load<N>(X + e * 5 * NU + l * N, in);
 #pragma unroll
       for (int i = 0; i < (QT > 0 ? QT : Q); ++i) {
         T s = T(0);
@@ -294,8 +331,7 @@ __global__ void __launch_bounds__(kAaThreads)
 #pragma unroll
         for (int a = 0; a < N; ++a) acc[a] += cp(a, i) * v;
       }
-#pragma unroll
-      for (int a = 0; a < N; ++a) tf[e * 15 * NU + l * N + a] = acc[a];
+      aa_line_store<N>(tf + e * 15 * NU + l * N, acc);
     }
     __syncthreads();
   }

@@ -1604,22 +1604,24 @@ int aa_setup(fr_mesh* m) {
       hex_dispatch(m->order, [&](auto nc) {
         constexpr int N = decltype(nc)::value;
         const int sm = int(hex_aa_smem<T>(N, q1));
+        // resident CTAs per SM of the variant that will run (rule size q1)
         int amin = 1 << 20;
-        auto attr = [&](auto fn) {
+        auto attr = [&](auto fn, bool used) {
           int a = 0;
           cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
           cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, fn, kAaThreads, sm);
-          amin = std::min(amin, a);
+          if (used) amin = std::min(amin, a);
         };
-        attr(k_hex_aa_flux<T, TR, N, 0, true>);
-        attr(k_hex_aa_flux<T, TR, N, 0, false>);
+        const bool q_n1 = sizeof(T) == 4 && q1 == N + 1, q_n2 = sizeof(T) == 4 && q1 == N + 2;
+        attr(k_hex_aa_flux<T, TR, N, 0, true>, !q_n1 && !q_n2);
+        attr(k_hex_aa_flux<T, TR, N, 0, false>, !q_n1 && !q_n2);
         if constexpr (sizeof(T) == 4) {
-          attr(k_hex_aa_flux<T, TR, N, N + 1, true>);
-          attr(k_hex_aa_flux<T, TR, N, N + 1, false>);
-          attr(k_hex_aa_flux<T, TR, N, N + 2, true>);
-          attr(k_hex_aa_flux<T, TR, N, N + 2, false>);
+          attr(k_hex_aa_flux<T, TR, N, N + 1, true>, q_n1);
+          attr(k_hex_aa_flux<T, TR, N, N + 1, false>, q_n1);
+          attr(k_hex_aa_flux<T, TR, N, N + 2, true>, q_n2);
+          attr(k_hex_aa_flux<T, TR, N, N + 2, false>, q_n2);
         }
-        D.aa_hex_ctas = amin > 0 ? amin : 1;
+        D.aa_hex_ctas = amin > 0 && amin < (1 << 20) ? amin : 1;
       });
     }
     std::vector<double> bt(size_t(nu) * nq), pt(size_t(nq) * nu);
