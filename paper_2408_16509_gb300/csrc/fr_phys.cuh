@@ -112,22 +112,41 @@ __device__ __forceinline__ void viscous_flux_acc(const T u[5], const T g[3][5],
   }
 }
 
-// normal viscous flux n.Fv accumulated into f[k] with sign sgn
+// normal viscous flux n.Fv accumulated into f[k] with sign sgn, formed
+// directly: (tau n)_i = mu (sum_j (dv_i/dx_j + dv_j/dx_i) n_j - 2/3 div v n_i),
+// energy v.(tau n) + kappa n.grad e (the full tensor is never built).
 template <typename T>
 __device__ __forceinline__ void viscous_normal_acc(const T u[5],
                                                    const T g[3][5],
                                                    const T n[3],
                                                    const Phys<T>& ph, T sgn,
                                                    T f[5]) {
-  T F[3][5];
+  const T ri = T(1) / u[0];
+  const T v[3] = {u[1] * ri, u[2] * ri, u[3] * ri};
+  const T er = u[4] * ri;
+  T gv[3][3];  // gv[j][i] = d v_i / d x_j
+  T gen = T(0);  // n . grad e
 #pragma unroll
-  for (int j = 0; j < 3; ++j)
+  for (int j = 0; j < 3; ++j) {
 #pragma unroll
-    for (int k = 0; k < 5; ++k) F[j][k] = T(0);
-  viscous_flux_acc(u, g, ph, T(1), F);
+    for (int i = 0; i < 3; ++i) gv[j][i] = (g[j][1 + i] - v[i] * g[j][0]) * ri;
+    const T ge = (g[j][4] - er * g[j][0]) * ri -
+                 (v[0] * gv[j][0] + v[1] * gv[j][1] + v[2] * gv[j][2]);
+    gen += n[j] * ge;
+  }
+  const T div23 = T(2.0 / 3.0) * (gv[0][0] + gv[1][1] + gv[2][2]);
+  T tn[3];
 #pragma unroll
-  for (int k = 1; k < 5; ++k)
-    f[k] += sgn * (n[0] * F[0][k] + n[1] * F[1][k] + n[2] * F[2][k]);
+  for (int i = 0; i < 3; ++i) {
+    T s = -div23 * n[i];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) s += (gv[j][i] + gv[i][j]) * n[j];
+    tn[i] = ph.mu * s;
+  }
+  f[1] += sgn * tn[0];
+  f[2] += sgn * tn[1];
+  f[3] += sgn * tn[2];
+  f[4] += sgn * (v[0] * tn[0] + v[1] * tn[1] + v[2] * tn[2] + ph.kappa * gen);
 }
 
 }  // namespace frgb
