@@ -496,7 +496,8 @@ def config_tgv48_mixed(fr, torch, device, steps=10, dt=2.5e-4):
     return out
 
 
-def config_mixed_elements(fr, torch, device, steps=20, cells=40, variant="auto"):
+def config_mixed_elements(fr, torch, device, steps=20, cells=40, variant="auto",
+                          qdeg=0):
     """40^3 cells: hexes x < 0.5, 2 prisms per cell 0.5 <= x < 0.8, 6 tets
     x >= 0.8 (5% jitter), p=3, NS Re 1000, Ma 0.2, RK4, FP32.  `cells` and
     `variant` (kernel family) serve profiling runs (--only mixed)."""
@@ -510,6 +511,8 @@ def config_mixed_elements(fr, torch, device, steps=20, cells=40, variant="auto")
     st = torch.cuda.Stream(device=device)
     mesh.set_stream(st)
     mesh.set_variant(variant)
+    if qdeg:
+        mesh.set_antialias(qdeg)
     mesh.set_solution(_state(mesh, lambda x: ics.perturbed_uniform(x)))
     mesh.rk_step("rk4", 2e-4, 2)
     ms = _timed_steps(torch, mesh, st, "rk4", 2e-4, steps)
@@ -742,6 +745,8 @@ def main():
                          "(profiling aid; not a contract line)")
     ap.add_argument("--cells", type=int, default=40,
                     help="cells per direction of the mixed-element box (--only mixed)")
+    ap.add_argument("--qdeg", type=int, default=0,
+                    help="anti-aliasing rule degree of the mixed-element run (--only mixed)")
     ap.add_argument("--precisions", default="fp64,fp32",
                     help="precisions of the curved / anti-aliased runs (--only)")
     ap.add_argument("--variant", default="auto",
@@ -764,7 +769,7 @@ def main():
                "shu_osher": config_shu_osher,
                "mixed": lambda f, t, d: config_mixed_elements(
                    f, t, d, steps=args.steps, cells=args.cells,
-                   variant=args.variant)}
+                   variant=args.variant, qdeg=args.qdeg)}
         rec = fns[args.only](fr, torch, dev)
         print(json.dumps({"only": args.only, "record": rec}), flush=True)
         return

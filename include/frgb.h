@@ -51,10 +51,11 @@ enum { FR_EULER = 0, FR_NAVIER_STOKES = 1 };
  * FR_MIXED: traces, fluxes, operators and stage values in FP32, the RK
  * solution and accumulator registers in FP64 (hexahedral meshes). */
 enum { FR_FP64 = 0, FR_FP32 = 1, FR_MIXED = 2 };
-enum { FR_BC_STATE = 0, FR_BC_EXTRAPOLATE = 1 };
+enum { FR_BC_STATE = 0, FR_BC_EXTRAPOLATE = 1, FR_BC_EXCHANGE = 2 };
 enum { FR_RK4 = 0, FR_RK45 = 1 };
 
 typedef struct fr_mesh fr_mesh;
+typedef struct fr_group fr_group;
 
 typedef struct {
   int etype;            /* FR_HEX8, FR_PRI6 or FR_TET4 */
@@ -75,7 +76,11 @@ typedef struct {
 
 typedef struct {
   int tag;              /* boundary-face tag this condition applies to */
-  int kind;             /* FR_BC_STATE: outside state = state (primitive
+  int kind;             /* FR_BC_EXCHANGE: a face between parts of a
+                           partitioned mesh, its outside state the partner
+                           part's (meshes with such faces run only in a
+                           group, fr_group_create); FR_BC_STATE: outside
+                           state = state (primitive
                            rho, u, v, w, p); FR_BC_EXTRAPOLATE: outside
                            state = inside state */
   double state[5];
@@ -250,6 +255,59 @@ enum { FR_OP_M0 = 0, FR_OP_D = 1, FR_OP_LIFT = 2, FR_OP_WEIGHTS = 3,
        FR_OP_UPTS = 4, FR_OP_FPTS = 5, FR_OP_AA_QPTS = 6, FR_OP_AA_QWTS = 7,
        FR_OP_AA_B = 8, FR_OP_AA_P = 9 };
 int fr_get_operator(const fr_mesh* mesh, int etype, int which, double* out);
+
+/* ---------------------------------------------------------------------------
+ * Domain decomposition (Section 4, "Mixed Elements and Domain Decomposition").
+ * Elements carry a global index: the element types in the order hexahedra,
+ * prisms, tetrahedra (those present), then the element number.  All three
+ * calls work on host-only handles.
+ *
+ * fr_get_adjacency: nbr [n_elem of etype][n_faces]: global index of the
+ * element across each face (periodic partners included), -1 on a boundary.
+ *
+ * fr_partition: part [total elements] in 0..nparts-1, by recursive
+ * coordinate bisection of element centroids.  mode 0 (weighted): element of
+ * type k weighs weights[k] (null: all 1); mode 1 (balanced): each type is
+ * bisected on its own, so every part holds the same number of elements of
+ * each type (to within one) whatever their relative cost.  FR_EINVAL for
+ * nparts < 1, another mode or a non-positive weight.
+ *
+ * fr_partition_faces: the faces of part `rank`'s elements whose neighbour
+ * lies in another part, as [count][4] node ids (-1 pads triangles); with
+ * faces = null only count is returned.  A sub-mesh of that part lists them
+ * as boundary faces with an FR_BC_EXCHANGE condition. */
+int fr_get_adjacency(const fr_mesh* mesh, int etype, int64_t* nbr);
+/* Boundary flux points in the library's order (count: n_boundary of
+ * fr_get_pairs): physical position x [n][3] and condition kind [n]
+ * (FR_BC_*); either pointer may be null. */
+int fr_get_boundary_points(const fr_mesh* mesh, double* x, int* kind);
+int fr_partition(const fr_mesh* mesh, int nparts, int mode, const double* weights,
+                 int32_t* part);
+int fr_partition_faces(const fr_mesh* mesh, const int32_t* part, int rank,
+                       int64_t* faces, int64_t* count);
+
+/* Partition groups: the parts of one mesh (each created from its elements,
+ * with its faces towards other parts as FR_BC_EXCHANGE boundary faces) run
+ * together on one device.  fr_group_create matches every exchange flux
+ * point with exactly one exchange point of another member by physical
+ * position (the members' common periodic translations included); FR_EMESH
+ * if a point has no partner or several.  Members must share device,
+ * precision, physics, order, constants and periodic vectors, must not run
+ * the entropy filter, and must outlive the group; each keeps its own
+ * solution (fr_set_solution / fr_get_solution / fr_get_rhs on the member).
+ * fr_group_rhs and fr_group_rk_step evaluate the right-hand side / advance
+ * all members: at each coupling point of a stage (solution traces before
+ * the common solution and fluxes; for Navier-Stokes the gradient traces, or
+ * with FP32 values the viscous normal fluxes, before the common fluxes) each
+ * member pushes its traces into the partners' receive buffers on the
+ * device, then the stage continues, so the result is the unpartitioned
+ * mesh's up to rounding.  Runs on the first member's stream and
+ * synchronises it.  fr_rhs / fr_rk_step on a member outside its group
+ * return FR_EINVAL. */
+int fr_group_create(fr_mesh* const* meshes, int n, fr_group** out);
+int fr_group_destroy(fr_group* group);
+int fr_group_rhs(fr_group* group);
+int fr_group_rk_step(fr_group* group, int scheme, double dt, int nsteps);
 
 /* Anti-aliasing (Section 3.2, "Anti-aliasing"): for qdeg > 0 the transformed
  * flux is no longer collocated at the solution points.  It is evaluated at

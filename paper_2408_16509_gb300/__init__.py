@@ -4,6 +4,6 @@ The compute path is the CUDA library ``lib/libfrgb.so`` (sources in
 ``csrc/``, C ABI in ``include/frgb.h``); this package only marshals
 arguments to it.
 """
-from ._binding import (ERRORS, ETYPES, AdaptCtl, FRError, FRMesh, load,  # noqa: F401
+from ._binding import (ERRORS, ETYPES, AdaptCtl, FRError, FRGroup, FRMesh, load,  # noqa: F401
                        mlp_loss_grad, mlp_train)
 from .build import build  # noqa: F401

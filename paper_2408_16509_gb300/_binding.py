@@ -20,7 +20,7 @@ PRECISION = {"fp64": 0, "fp32": 1, "mixed": 2}
 VARIANTS = {"auto": 0, "dense": 1, "sumfact": 2, "sumfact_vertex": 3,
             "tensor": 4}
 SCHEMES = {"rk4": 0, "rk45": 1}
-BC_KIND = {"state": 0, "extrap": 1}
+BC_KIND = {"state": 0, "extrap": 1, "exchange": 2}
 
 
 class FRError(RuntimeError):
@@ -90,6 +90,14 @@ def load():
         "fr_get_operator": (I, [P, I, I, P]),
         "fr_get_metrics": (I, [P, I, P, P]),
         "fr_get_pairs": (I, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+        "fr_get_adjacency": (I, [P, I, P]),
+        "fr_get_boundary_points": (I, [P, P, P]),
+        "fr_partition": (I, [P, I, I, P, P]),
+        "fr_partition_faces": (I, [P, P, I, P, C.POINTER(C.c_int64)]),
+        "fr_group_create": (I, [P, I, C.POINTER(C.c_void_p)]),
+        "fr_group_destroy": (I, [P]),
+        "fr_group_rhs": (I, [P]),
+        "fr_group_rk_step": (I, [P, I, D, I]),
         "fr_profile_step": (I, [P, I, D, P, P]),
         "fr_set_antialias": (I, [P, I]),
         "fr_set_kernel_variant": (I, [P, I]),
@@ -251,6 +259,10 @@ class FRMesh:
     def rhs(self):
         """One right-hand-side evaluation at the current solution."""
         _check(load().fr_rhs(self._h))
+        return self.get_rhs()
+
+    def get_rhs(self):
+        """The last right-hand side (fr_get_rhs)."""
         out = {}
         for t in self.types:
             ne, nu, _ = self.info(t)
@@ -403,6 +415,79 @@ class FRMesh:
         a, b = C.c_int64(), C.c_int64()
         _check(load().fr_get_pairs(self._h, C.byref(a), C.byref(b)))
         return a.value, b.value
+
+    def boundary_points(self):
+        """(x [nb][3], kind [nb]) of the boundary flux points."""
+        _, nb = self.pair_counts()
+        x = np.empty((nb, 3), np.float64)
+        k = np.empty(nb, np.int32)
+        _check(load().fr_get_boundary_points(self._h, _ptr(x), _ptr(k)))
+        return x, k
+
+    def n_elements(self):
+        return sum(self.info(t)[0] for t in self.types)
+
+    def adjacency(self, etype):
+        """[ne][nfaces] global index of the neighbour across each face, -1
+        on a boundary (fr_get_adjacency)."""
+        ne = self.info(etype)[0]
+        nf = {"hex": 6, "pri": 5, "tet": 4}[etype]
+        out = np.empty((ne, nf), np.int64)
+        _check(load().fr_get_adjacency(self._h, ETYPES[etype], _ptr(out)))
+        return out
+
+    def partition(self, nparts, mode="weighted", weights=None):
+        """Part of every element (global index order) by recursive
+        coordinate bisection; mode 'weighted' (weights per type hex, pri,
+        tet) or 'balanced' (fr_partition)."""
+        part = np.empty(self.n_elements(), np.int32)
+        w = None if weights is None else np.ascontiguousarray(weights, np.float64)
+        _check(load().fr_partition(self._h, int(nparts), {"weighted": 0, "balanced": 1}[mode],
+                                   None if w is None else _ptr(w), _ptr(part)))
+        return part
+
+    def partition_faces(self, part, rank):
+        """Node ids [n][4] of the faces of part `rank` that border another
+        part (fr_partition_faces)."""
+        part = np.ascontiguousarray(part, np.int32)
+        n = C.c_int64()
+        _check(load().fr_partition_faces(self._h, _ptr(part), int(rank), None, C.byref(n)))
+        out = np.empty((n.value, 4), np.int64)
+        if n.value:
+            _check(load().fr_partition_faces(self._h, _ptr(part), int(rank), _ptr(out),
+                                             C.byref(n)))
+        return out
+
+
+class FRGroup:
+    """Partitions of one mesh run together on one device (fr_group_*): the
+    right-hand side and RK steps of the whole mesh, with the traces of
+    exchange faces pushed between the members at every coupling point."""
+
+    def __init__(self, members):
+        self.members = list(members)
+        arr = (C.c_void_p * len(self.members))(*[m._h for m in self.members])
+        h = C.c_void_p()
+        _check(load().fr_group_create(arr, len(self.members), C.byref(h)))
+        self._h = h
+
+    def rhs(self):
+        _check(load().fr_group_rhs(self._h))
+        return [m.get_rhs() for m in self.members]
+
+    def rk_step(self, scheme, dt, nsteps=1):
+        _check(load().fr_group_rk_step(self._h, SCHEMES[scheme], float(dt), int(nsteps)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().fr_group_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def mlp_train(x, zstar, params, epochs, lr, device=0):

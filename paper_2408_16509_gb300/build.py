@@ -19,7 +19,7 @@ OBJ_DIR = os.path.join(HERE, "lib", "obj")
 LIB = os.path.join(OUT_DIR, "libfrgb.so")
 
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-CXX_SRCS = ["fr_ref.cpp", "fr_mesh.cpp"]
+CXX_SRCS = ["fr_ref.cpp", "fr_mesh.cpp", "fr_part.cpp"]
 CU_SRCS = ["fr_api.cu"]
 
 

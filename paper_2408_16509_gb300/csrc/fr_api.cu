@@ -3,6 +3,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
+#include <memory>
+#include <unordered_map>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -190,6 +193,14 @@ struct fr_mesh {
   long long epoch = 0;            // bumped by every change of launch config
   long long graph_epoch[3] = {-1, -1, -1};
   int aa_qdeg = 0;            // anti-aliasing rule degree (0: collocation)
+  // exchange boundary points (partitioned meshes): receive buffers filled
+  // by the group's push kernels, indexed by boundary point
+  bool has_exch = false;
+  bool in_group = false;
+  void* xu = nullptr;         // [nb][5] partner solution traces
+  void* xg = nullptr;         // [nb][15] partner gradients (FP64) or [nb][5] q (FP32)
+  void* xm = nullptr;         // [nb] partner |S^T n~|
+  std::vector<double> periodic;  // [n][3] translation vectors
   bool err_on = false;        // stage epilogues accumulate the embedded error
   double* d_errpart = nullptr;  // per-block partial sums of the error norm
   double* d_errsum = nullptr;   // total
@@ -864,10 +875,13 @@ void launch_entropy_min(fr_mesh* m, cudaStream_t s, bool from_x);
 template <typename T, typename TR>
 void launch_filter(fr_mesh* m, cudaStream_t s, DevType& D, bool last_stage);
 
-// Launch one RK stage (or a bare right-hand side when mode == 0).
+// Launch one RK stage (or a bare right-hand side when mode == 0).  phase
+// bit 1: the NS common solution and gradients; bit 2: the common fluxes and
+// the volume kernels.  A partitioned group exchanges the gradient traces
+// between the two (and the solution traces before bit 1).
 template <typename T, typename TR>
 void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
-                  Prof* prof = nullptr) {
+                  Prof* prof = nullptr, int phase = 3) {
   const bool ns = m->physics == FR_NAVIER_STOKES;
   const Phys<T> ph = phys<T>(m);
   const BCTab<T>& bc = bctab<T>(m);
@@ -877,12 +891,12 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
   const bool from_x = (mode == 0 || stage == 0);
   const bool filt = m->filter_on && mode != 0;
   const bool last_stage = (mode == 1 && stage == 3) || (mode == 2 && stage == 4);
-  if (filt) {
+  if (filt && (phase & 1)) {
     PROF_BEGIN(FR_KC_FILTER);
     launch_entropy_min<T, TR>(m, s, from_x);
     PROF_END(FR_KC_FILTER);
   }
-  if (ns) {
+  if (ns && (phase & 1)) {
     if (m->np) {
       PROF_BEGIN(FR_KC_FACE_U);
       k_face_ucommon<T><<<nblk(m->np, tb), tb, 0, s>>>(
@@ -892,7 +906,8 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
     if (m->nb) {
       PROF_BEGIN(FR_KC_BND_U);
       k_bnd_ucommon<T><<<nblk(m->nb, tb), tb, 0, s>>>(
-          m->nb, m->bidx, m->bbc, (const T*)m->uf, (T*)m->du, m->tt, bc);
+          m->nb, m->bidx, m->bbc, (const T*)m->uf, (T*)m->du, m->tt, bc,
+          (const T*)m->xu);
       PROF_END(FR_KC_BND_U);
     }
     for (auto& D : m->types) {
@@ -938,6 +953,7 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
       PROF_END(FR_KC_GRAD);
     }
   }
+  if (!(phase & 2)) return;
   if (m->np) {
     PROF_BEGIN(FR_KC_FACE_F);
     if (ns && sizeof(T) == 4)
@@ -959,15 +975,17 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
     if (ns && sizeof(T) == 4)
       k_bnd_flux_ns<T><<<nblk(m->nb, tb), tb, 0, s>>>(
           m->nb, m->bidx, m->bbc, (const T*)m->bn, (const T*)m->uf,
-          (const T*)m->gradf, (T*)m->fc, m->tt, ph, bc);
+          (const T*)m->gradf, (T*)m->fc, m->tt, ph, bc, (const T*)m->xu,
+          (const T*)m->xg, (const T*)m->xm);
     else if (ns)
       k_bnd_flux<T, true><<<nblk(m->nb, tb), tb, 0, s>>>(
           m->nb, m->bidx, m->bbc, (const T*)m->bn, (const T*)m->uf,
-          (const T*)m->gradf, (T*)m->fc, m->tt, ph, bc);
+          (const T*)m->gradf, (T*)m->fc, m->tt, ph, bc, (const T*)m->xu,
+          (const T*)m->xg);
     else
       k_bnd_flux<T, false><<<nblk(m->nb, tb), tb, 0, s>>>(
           m->nb, m->bidx, m->bbc, (const T*)m->bn, (const T*)m->uf, nullptr,
-          (T*)m->fc, m->tt, ph, bc);
+          (T*)m->fc, m->tt, ph, bc, (const T*)m->xu);
     PROF_END(FR_KC_BND_F);
   }
   const bool aa = m->aa_qdeg > 0;
@@ -1659,6 +1677,278 @@ int aa_setup(fr_mesh* m) {
 
 }  // namespace
 
+// ============================================================ partition groups
+// Partitions of one mesh on one device, run together.  Every exchange point
+// of a member is matched (by physical position, periodic translations
+// included) with exactly one exchange point of another member; at each
+// coupling point of a stage (solution traces before the common solution /
+// fluxes; for NS also the gradient traces or the viscous normal fluxes
+// before the common fluxes) every member pushes its traces into the
+// partners' receive buffers, as a halo exchange between GPUs would.
+struct fr_group {
+  std::vector<fr_mesh*> m;
+  struct Push {
+    int32_t* code = nullptr;  // sender flux points
+    int32_t* to = nullptr;    // receiving member
+    int32_t* slot = nullptr;  // receiver's boundary-point index
+    int n = 0;
+  };
+  std::vector<Push> push;
+  void** d_xu = nullptr;  // members' xu pointers (device array)
+  void** d_xg = nullptr;  // members' xg pointers
+  std::vector<void*> allocs;
+  ~fr_group() {
+    for (void* p : allocs)
+      if (p) cudaFree(p);
+    for (fr_mesh* x : m) x->in_group = false;
+  }
+};
+
+namespace {
+
+struct CellHash {
+  size_t operator()(const std::array<int64_t, 3>& k) const {
+    uint64_t h = 1469598103934665603ull;
+    for (int i = 0; i < 3; ++i) {
+      h ^= uint64_t(k[i]);
+      h *= 1099511628211ull;
+    }
+    return size_t(h);
+  }
+};
+
+template <typename T, typename TR>
+int group_run(fr_group* g, int mode, double dt, int nsteps) {
+  fr_mesh* m0 = g->m[0];
+  cudaStream_t s = m0->stream;
+  for (fr_mesh* m : g->m) {
+    CK(cudaStreamSynchronize(m->stream));
+    if (m->variant != FR_VARIANT_AUTO) {
+      int rv = resolve_variant<T, TR>(m, FR_RK4, 0.0);
+      if (rv) return rv;
+    } else {
+      m->tuned = true;  // no tuning inside a group: the members' default family
+    }
+  }
+  std::vector<cudaStream_t> own(g->m.size());
+  for (size_t i = 0; i < g->m.size(); ++i) {
+    own[i] = g->m[i]->stream;
+    g->m[i]->stream = s;
+  }
+  auto restore = [&]() {
+    for (size_t i = 0; i < g->m.size(); ++i) g->m[i]->stream = own[i];
+  };
+  const bool ns = m0->physics == FR_NAVIER_STOKES;
+  const int nv2 = sizeof(T) == 4 ? 5 : 15;
+  auto push = [&](int which) {
+    for (size_t r = 0; r < g->m.size(); ++r) {
+      const fr_group::Push& p = g->push[r];
+      if (!p.n) continue;
+      fr_mesh* m = g->m[r];
+      k_exchange_push<T><<<nblk(p.n, 256), 256, 0, s>>>(
+          p.n, p.code, p.to, p.slot, which == 0 ? (const T*)m->uf : (const T*)m->gradf,
+          which == 0 ? 5 : nv2, reinterpret_cast<T* const*>(which == 0 ? g->d_xu : g->d_xg),
+          m->tt);
+    }
+  };
+  for (fr_mesh* m : g->m) {
+    if (!m->uf_valid) {
+      launch_interp<T, TR>(m, s);
+      m->uf_valid = true;
+    }
+    m->h_dt = dt;
+    cudaMemcpyAsync(m->d_dt, &m->h_dt, sizeof(double), cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(m->d_flag, 0, sizeof(int), s);
+  }
+  const int nst = mode == 0 ? 1 : (mode == 1 ? 4 : 5);
+  for (int it = 0; it < nsteps; ++it)
+    for (int st = 0; st < nst; ++st) {
+      push(0);
+      if (ns) {
+        for (fr_mesh* m : g->m) launch_stage<T, TR>(m, s, mode, st, nullptr, 1);
+        push(1);
+      }
+      for (fr_mesh* m : g->m) launch_stage<T, TR>(m, s, mode, st, nullptr, 2);
+    }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    restore();
+    return fail(FR_ECUDA, cudaGetErrorString(e));
+  }
+  int bad = 0;
+  for (fr_mesh* m : g->m) {
+    int flag = 0;
+    cudaMemcpyAsync(&flag, m->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    bad |= flag;
+  }
+  restore();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(FR_ECUDA, cudaGetErrorString(e));
+  if (bad & 2) return fail(FR_ETIMEOUT, "a tensor-core wait timed out");
+  if (bad) return fail(FR_ENONFINITE, "a partitioned stage is not finite");
+  return FR_OK;
+}
+
+// Match every member's exchange points with their partners; fills the push
+// lists and the partners' |S^T n~| (xm) of every member.
+template <typename T, typename TR>
+int group_setup(fr_group* g) {
+  // Exchange points grouped by face: flux points on face edges of
+  // simplices occur on two faces, so faces are matched first (by translated
+  // centroid), then points within each matched face pair.
+  struct XF {
+    int r;
+    std::vector<int> pt;  // boundary-point indices in member r
+    double c[3];
+  };
+  std::vector<XF> fl;
+  auto pos = [&](const fr_mesh* m, int i, double* x) {
+    const int32_t code = m->conn.bidx[i];
+    const HostType& H = m->host[code >> 29];
+    const int64_t rem = code & ((int64_t(1) << 29) - 1);
+    const int64_t e = rem / (5 * H.ref.nfpts);
+    const int f = int(rem - e * 5 * H.ref.nfpts);
+    for (int k = 0; k < 3; ++k) x[k] = H.fpts_x[(size_t(e) * H.ref.nfpts + f) * 3 + k];
+    return std::array<int64_t, 3>{code >> 29, e, H.ref.fpts_face[f]};
+  };
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (size_t r = 0; r < g->m.size(); ++r) {
+    const fr_mesh* m = g->m[r];
+    std::array<int64_t, 3> prev = {-1, -1, -1};
+    for (size_t i = 0; i < m->conn.bidx.size(); ++i) {
+      if (m->bc64.kind[m->conn.bbc[i]] != FR_BC_EXCHANGE) continue;
+      double x[3];
+      const std::array<int64_t, 3> face = pos(m, int(i), x);
+      if (face != prev || fl.empty() || fl.back().r != int(r)) {
+        fl.push_back(XF{int(r), {}, {0, 0, 0}});
+        prev = face;
+      }
+      fl.back().pt.push_back(int(i));
+      for (int k = 0; k < 3; ++k) {
+        fl.back().c[k] += x[k];
+        lo[k] = std::min(lo[k], x[k]);
+        hi[k] = std::max(hi[k], x[k]);
+      }
+    }
+  }
+  for (XF& f : fl)
+    for (int k = 0; k < 3; ++k) f.c[k] /= double(f.pt.size());
+  double ext = 0.0;
+  for (int k = 0; k < 3; ++k) ext = std::max(ext, hi[k] - lo[k]);
+  const double tol = 1e-8 * std::max(ext, 1e-300), cell = 16.0 * tol;
+  auto key = [&](const double* x, int dx, int dy, int dz) {
+    return std::array<int64_t, 3>{int64_t(std::floor(x[0] / cell)) + dx,
+                                  int64_t(std::floor(x[1] / cell)) + dy,
+                                  int64_t(std::floor(x[2] / cell)) + dz};
+  };
+  std::unordered_multimap<std::array<int64_t, 3>, int, CellHash> grid;
+  for (int j = 0; j < int(fl.size()); ++j) grid.emplace(key(fl[j].c, 0, 0, 0), j);
+  // translations: sums of -1, 0 or +1 times each periodic vector
+  const std::vector<double>& pv = g->m[0]->periodic;
+  const int np = int(pv.size() / 3);
+  std::vector<std::array<double, 3>> shifts;
+  int ncomb = 1;
+  for (int a = 0; a < np; ++a) ncomb *= 3;
+  for (int c = 0; c < ncomb; ++c) {
+    std::array<double, 3> sh = {0, 0, 0};
+    int cc = c;
+    for (int a = 0; a < np; ++a, cc /= 3)
+      for (int k = 0; k < 3; ++k) sh[k] += double(cc % 3 - 1) * pv[3 * a + k];
+    shifts.push_back(sh);
+  }
+  std::vector<std::vector<int32_t>> code(g->m.size()), to(g->m.size()), slot(g->m.size());
+  std::vector<std::vector<double>> xm(g->m.size());
+  for (size_t r = 0; r < g->m.size(); ++r) xm[r].assign(g->m[r]->conn.bidx.size(), 1.0);
+  for (const XF& F : fl) {
+    int found = -1, hits = 0;
+    std::array<double, 3> fsh = {0, 0, 0};
+    for (const auto& sh : shifts) {
+      const double y[3] = {F.c[0] + sh[0], F.c[1] + sh[1], F.c[2] + sh[2]};
+      for (int dx = -1; dx <= 1; ++dx)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dz = -1; dz <= 1; ++dz) {
+            auto rng = grid.equal_range(key(y, dx, dy, dz));
+            for (auto it = rng.first; it != rng.second; ++it) {
+              const XF& G = fl[it->second];
+              if (G.r == F.r || G.pt.size() != F.pt.size()) continue;
+              double d2 = 0;
+              for (int k = 0; k < 3; ++k) d2 += (G.c[k] - y[k]) * (G.c[k] - y[k]);
+              if (d2 <= tol * tol) {
+                found = it->second;
+                fsh = sh;
+                ++hits;
+              }
+            }
+          }
+    }
+    if (hits != 1)
+      return fail(FR_EMESH, hits ? "an exchange face matches several partners"
+                                 : "an exchange face has no partner in the group");
+    const XF& G = fl[found];
+    const fr_mesh* ms = g->m[F.r];
+    const fr_mesh* mr = g->m[G.r];
+    std::vector<char> taken(G.pt.size(), 0);
+    for (int i : F.pt) {
+      double x[3], y[3];
+      pos(ms, i, x);
+      for (int k = 0; k < 3; ++k) x[k] += fsh[k];
+      int best = -1;
+      double bd = 1e300;
+      for (size_t j = 0; j < G.pt.size(); ++j) {
+        pos(mr, G.pt[j], y);
+        double d2 = 0;
+        for (int k = 0; k < 3; ++k) d2 += (x[k] - y[k]) * (x[k] - y[k]);
+        if (d2 < bd) {
+          bd = d2;
+          best = int(j);
+        }
+      }
+      if (best < 0 || bd > tol * tol || taken[best])
+        return fail(FR_EMESH, "flux points do not conform across an exchange face");
+      taken[best] = 1;
+      const int q = G.pt[best];
+      code[F.r].push_back(ms->conn.bidx[i]);  // F's point pushes to G's slot q
+      to[F.r].push_back(G.r);
+      slot[F.r].push_back(q);
+      xm[G.r][q] = ms->conn.bn[4 * i + 3];    // q's partner magnitude
+    }
+  }
+  g->push.resize(g->m.size());
+  for (size_t r = 0; r < g->m.size(); ++r) {
+    fr_mesh* m = g->m[r];
+    fr_group::Push& p = g->push[r];
+    p.n = int(code[r].size());
+    if (p.n) {
+      for (auto pr : {std::make_pair(&code[r], &p.code), std::make_pair(&to[r], &p.to),
+                      std::make_pair(&slot[r], &p.slot)}) {
+        CK(cudaMalloc((void**)pr.second, size_t(p.n) * sizeof(int32_t)));
+        g->allocs.push_back(*pr.second);
+        CK(cudaMemcpy(*pr.second, pr.first->data(), size_t(p.n) * sizeof(int32_t),
+                      cudaMemcpyHostToDevice));
+      }
+    }
+    if (m->xm) {
+      std::vector<T> h(xm[r].begin(), xm[r].end());
+      CK(cudaMemcpy(m->xm, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    }
+  }
+  std::vector<void*> xu(g->m.size()), xg(g->m.size());
+  for (size_t r = 0; r < g->m.size(); ++r) {
+    xu[r] = g->m[r]->xu;
+    xg[r] = g->m[r]->xg;
+  }
+  for (auto pr : {std::make_pair(&xu, &g->d_xu), std::make_pair(&xg, &g->d_xg)}) {
+    CK(cudaMalloc((void**)pr.second, g->m.size() * sizeof(void*)));
+    g->allocs.push_back(*pr.second);
+    CK(cudaMemcpy(*pr.second, pr.first->data(), g->m.size() * sizeof(void*),
+                  cudaMemcpyHostToDevice));
+  }
+  return FR_OK;
+}
+
+}  // namespace
+
 // ===================================================================== ABI
 extern "C" {
 
@@ -1721,7 +2011,7 @@ int fr_mesh_create(const fr_mesh_desc* d, fr_mesh** out) {
     return fail(FR_EINVAL, "boundary faces without nodes or tags");
   for (int i = 0; i < d->n_bcs; ++i) {
     const fr_bc_desc& b = d->bcs[i];
-    if (b.kind != FR_BC_STATE && b.kind != FR_BC_EXTRAPOLATE)
+    if (b.kind != FR_BC_STATE && b.kind != FR_BC_EXTRAPOLATE && b.kind != FR_BC_EXCHANGE)
       return fail(FR_EINVAL, "unknown boundary condition");
     in.bc_tags.push_back(b.tag);
     double rho = b.state[0], u = b.state[1], v = b.state[2], w = b.state[3],
@@ -1743,6 +2033,8 @@ int fr_mesh_create(const fr_mesh_desc* d, fr_mesh** out) {
     return fail(FR_EINVAL, ex.what());
   }
   if (!err.empty()) return fail(emesh ? FR_EMESH : FR_EINVAL, err);
+  for (auto& p : in.periodic) m->periodic.insert(m->periodic.end(), p.begin(), p.end());
+  for (int32_t b : m->conn.bbc) m->has_exch |= m->bc64.kind[b] == FR_BC_EXCHANGE;
   if (d->device < 0) {  // host-only handle: geometry and operators, no GPU
     m->host_only = true;
     for (size_t t = 0; t < m->host.size(); ++t) m->type_of_kind[m->host[t].kind] = int(t);
@@ -1785,6 +2077,12 @@ int fr_mesh_create(const fr_mesh_desc* d, fr_mesh** out) {
   if (rc) return rc;
   rc = FR_PREC(m, prepare_kernels, m.get());
   if (rc) return rc;
+  if (m->has_exch) {
+    const size_t nb = m->conn.bidx.size();
+    if ((rc = dev_zeros(m.get(), nb * 5 * m->wsize, &m->xu))) return rc;
+    if ((rc = dev_zeros(m.get(), nb * 15 * m->wsize, &m->xg))) return rc;
+    if ((rc = dev_zeros(m.get(), nb * m->wsize, &m->xm))) return rc;
+  }
   *out = m.release();
   return FR_OK;
 }
@@ -1956,6 +2254,7 @@ int fr_get_solution_device(const fr_mesh* mc, int etype, void* dptr) {
 int fr_rhs(fr_mesh* m) {
   if (!m) return fail(FR_EINVAL, "null mesh");
   if (m->host_only) return fail(FR_EINVAL, "host-only handle (device < 0)");
+  if (m->has_exch) return fail(FR_EINVAL, "mesh has exchange faces: run it in a group");
   CK(cudaSetDevice(m->device));
   return FR_PREC(m, do_rhs, m);
 }
@@ -1965,6 +2264,7 @@ int fr_rk_step(fr_mesh* m, int scheme, double dt, int nsteps) {
   if (m->host_only) return fail(FR_EINVAL, "host-only handle (device < 0)");
   if (scheme != FR_RK4 && scheme != FR_RK45) return fail(FR_EINVAL, "unknown scheme");
   if (nsteps < 0) return fail(FR_EINVAL, "negative step count");
+  if (m->has_exch) return fail(FR_EINVAL, "mesh has exchange faces: run it in a group");
   if (nsteps == 0) return FR_OK;
   CK(cudaSetDevice(m->device));
   return FR_PREC(m, do_rk, m, scheme, dt, nsteps);
@@ -1974,6 +2274,7 @@ int fr_rk_adaptive_step(fr_mesh* m, fr_adapt_t* ctl, double* dt, int* accepted,
                         double* err) {
   if (!m || !ctl || !dt || !accepted || !err) return fail(FR_EINVAL, "null argument");
   if (m->host_only) return fail(FR_EINVAL, "host-only handle (device < 0)");
+  if (m->has_exch) return fail(FR_EINVAL, "mesh has exchange faces: run it in a group");
   CK(cudaSetDevice(m->device));
   return FR_PREC(m, do_rk_adaptive, m, ctl, dt, accepted, err);
 }
@@ -1982,6 +2283,7 @@ int fr_profile_step(fr_mesh* m, int scheme, double dt, double* ms,
                     int* launches) {
   if (!m || !ms || !launches) return fail(FR_EINVAL, "null argument");
   if (m->host_only) return fail(FR_EINVAL, "host-only handle (device < 0)");
+  if (m->has_exch) return fail(FR_EINVAL, "mesh has exchange faces: run it in a group");
   if (scheme != FR_RK4 && scheme != FR_RK45) return fail(FR_EINVAL, "unknown scheme");
   CK(cudaSetDevice(m->device));
   return FR_PREC(m, do_profile, m, scheme, dt, ms, launches);
@@ -2083,11 +2385,120 @@ int fr_set_antialias(fr_mesh* m, int qdeg) {
   return FR_OK;
 }
 
+int fr_get_boundary_points(const fr_mesh* m, double* x, int* kind) {
+  if (!m) return fail(FR_EINVAL, "null argument");
+  for (size_t i = 0; i < m->conn.bidx.size(); ++i) {
+    const int32_t code = m->conn.bidx[i];
+    const HostType& H = m->host[code >> 29];
+    const int64_t rem = code & ((int64_t(1) << 29) - 1);
+    const int64_t e = rem / (5 * H.ref.nfpts);
+    const int f = int(rem - e * 5 * H.ref.nfpts);
+    if (x)
+      for (int k = 0; k < 3; ++k) x[3 * i + k] = H.fpts_x[(size_t(e) * H.ref.nfpts + f) * 3 + k];
+    if (kind) kind[i] = m->bc64.kind[m->conn.bbc[i]];
+  }
+  return FR_OK;
+}
+
+int fr_get_adjacency(const fr_mesh* m, int etype, int64_t* nbr) {
+  if (!m || !nbr) return fail(FR_EINVAL, "null argument");
+  const HostType* H = host_ptr(m, etype);
+  if (!H) return fail(FR_EINVAL, "mesh has no elements of this type");
+  std::memcpy(nbr, H->nbr.data(), H->nbr.size() * sizeof(int64_t));
+  return FR_OK;
+}
+
+int fr_partition(const fr_mesh* m, int nparts, int mode, const double* weights,
+                 int32_t* part) {
+  if (!m || !part) return fail(FR_EINVAL, "null argument");
+  const double ones[3] = {1.0, 1.0, 1.0};
+  std::vector<int32_t> p;
+  std::string err = partition_elements(m->host, nparts, mode, weights ? weights : ones, p);
+  if (!err.empty()) return fail(FR_EINVAL, err);
+  std::memcpy(part, p.data(), p.size() * sizeof(int32_t));
+  return FR_OK;
+}
+
+int fr_partition_faces(const fr_mesh* m, const int32_t* part, int rank,
+                       int64_t* faces, int64_t* count) {
+  if (!m || !part || !count) return fail(FR_EINVAL, "null argument");
+  int64_t n = 0, off = 0;
+  for (const HostType& H : m->host) {
+    const int nf = H.ref.nfaces, nv = H.ref.nverts;
+    for (int64_t e = 0; e < H.ne; ++e) {
+      if (part[off + e] != rank) continue;
+      for (int f = 0; f < nf; ++f) {
+        const int64_t nb = H.nbr[size_t(e) * nf + f];
+        if (nb < 0 || part[nb] == rank) continue;
+        if (faces) {
+          const RefFace& F = H.ref.faces[f];
+          for (int i = 0; i < 4; ++i)
+            faces[4 * n + i] = i < F.nv ? H.conn[size_t(e) * nv + F.verts[i]] : -1;
+        }
+        ++n;
+      }
+    }
+    off += H.ne;
+  }
+  *count = n;
+  return FR_OK;
+}
+
 int fr_get_pairs(const fr_mesh* m, int64_t* n_interior, int64_t* n_boundary) {
   if (!m) return fail(FR_EINVAL, "null argument");
   if (n_interior) *n_interior = int64_t(m->conn.pl.size());
   if (n_boundary) *n_boundary = int64_t(m->conn.bidx.size());
   return FR_OK;
+}
+
+int fr_group_create(fr_mesh* const* meshes, int n, fr_group** out) {
+  if (!meshes || !out || n < 1) return fail(FR_EINVAL, "null argument or empty group");
+  *out = nullptr;
+  const fr_mesh* a = meshes[0];
+  for (int i = 0; i < n; ++i) {
+    const fr_mesh* m = meshes[i];
+    if (!m) return fail(FR_EINVAL, "null member");
+    if (m->host_only) return fail(FR_EINVAL, "host-only member");
+    if (m->in_group) return fail(FR_EINVAL, "mesh already belongs to a group");
+    if (m->device != a->device || m->precision != a->precision || m->physics != a->physics ||
+        m->order != a->order || m->gamma != a->gamma || m->mu != a->mu ||
+        m->prandtl != a->prandtl || m->periodic != a->periodic)
+      return fail(FR_EINVAL, "members differ in device, precision, physics, order or constants");
+    if (m->filter_on) return fail(FR_EINVAL, "the entropy filter is not supported in a group");
+    for (int j = 0; j < i; ++j)
+      if (meshes[j] == m) return fail(FR_EINVAL, "a mesh appears twice in the group");
+  }
+  CK(cudaSetDevice(a->device));
+  auto g = std::make_unique<fr_group>();
+  g->m.assign(meshes, meshes + n);
+  int rc = FR_PREC(a, group_setup, g.get());
+  if (rc) return rc;
+  for (fr_mesh* m : g->m) m->in_group = true;
+  *out = g.release();
+  return FR_OK;
+}
+
+int fr_group_destroy(fr_group* g) {
+  if (!g) return FR_OK;
+  cudaSetDevice(g->m[0]->device);
+  cudaStreamSynchronize(g->m[0]->stream);
+  delete g;
+  return FR_OK;
+}
+
+int fr_group_rhs(fr_group* g) {
+  if (!g) return fail(FR_EINVAL, "null group");
+  CK(cudaSetDevice(g->m[0]->device));
+  return FR_PREC(g->m[0], group_run, g, 0, 0.0, 1);
+}
+
+int fr_group_rk_step(fr_group* g, int scheme, double dt, int nsteps) {
+  if (!g) return fail(FR_EINVAL, "null group");
+  if (scheme != FR_RK4 && scheme != FR_RK45) return fail(FR_EINVAL, "unknown scheme");
+  if (nsteps < 0) return fail(FR_EINVAL, "negative step count");
+  if (nsteps == 0) return FR_OK;
+  CK(cudaSetDevice(g->m[0]->device));
+  return FR_PREC(g->m[0], group_run, g, scheme == FR_RK4 ? 1 : 2, dt, nsteps);
 }
 
 }  // extern "C"

@@ -628,7 +628,7 @@ __global__ void __launch_bounds__(EPB* N* N* N)
     T q[5] = {0, 0, 0, 0, 0};
     viscous_normal_acc(u, G, nv, ph, T(1), q);
     const int bb = va.fbc[e * NF + f];
-    if (bb >= 0) {
+    if (bb >= 0 && bc.kind[bb] != 2) {  // exchange points keep the inside q
       T ur[5], q2[5] = {0, 0, 0, 0, 0};
       ghost_state(bc, bb, u, ur);
       viscous_normal_acc(ur, G, nv, ph, T(1), q2);

@@ -28,7 +28,8 @@ struct TypeTab {
 
 template <typename T>
 struct BCTab {
-  int kind[kMaxBC];      // 0 = prescribed state, 1 = extrapolate
+  int kind[kMaxBC];      // 0 = prescribed state, 1 = extrapolate,
+                         // 2 = exchange (outside state of a partner part)
   T state[kMaxBC][5];    // conserved ghost state
 };
 
@@ -250,14 +251,31 @@ __device__ __forceinline__ void ghost_state(const BCTab<T>& bc, int b,
   }
 }
 
+// Outside state of boundary point i: the condition's, or for an exchange
+// point the partner part's trace received in xu ([nb][5]).
+template <typename T>
+__device__ __forceinline__ void ghost_state_x(const BCTab<T>& bc, int b, int i,
+                                              const T* __restrict__ xu,
+                                              const T ul[5], T ur[5]) {
+  if (bc.kind[b] == 2) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) ur[k] = xu[5 * i + k];
+  } else {
+    ghost_state(bc, b, ul, ur);
+  }
+}
+
 // Boundary flux points: outside state from the boundary condition, outside
-// gradient equal to the inside one.
+// gradient equal to the inside one; at exchange points both come from the
+// partner part (xu [nb][5], xg [nb][15]), which makes them interior faces.
 template <typename T, bool NS>
 __global__ void k_bnd_flux(int nb, const int32_t* __restrict__ bidx,
                            const int32_t* __restrict__ bbc,
                            const T* __restrict__ bn, const T* __restrict__ uf,
                            const T* __restrict__ gf, T* __restrict__ fc,
-                           TypeTab tt, Phys<T> ph, BCTab<T> bc) {
+                           TypeTab tt, Phys<T> ph, BCTab<T> bc,
+                           const T* __restrict__ xu = nullptr,
+                           const T* __restrict__ xg = nullptr) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nb) return;
   int t, f;
@@ -266,17 +284,22 @@ __global__ void k_bnd_flux(int nb, const int32_t* __restrict__ bidx,
   T ul[5], ur[5], n[3] = {bn[4 * i], bn[4 * i + 1], bn[4 * i + 2]};
 #pragma unroll
   for (int k = 0; k < 5; ++k) ul[k] = uf[fp_index(tt, t, e, f, 5, k)];
-  ghost_state(bc, bbc[i], ul, ur);
+  const int b = bbc[i];
+  ghost_state_x(bc, b, i, xu, ul, ur);
   T F[5];
   rusanov(ul, ur, n, ph, F);
   if (NS) {
-    T g[3][5];
+    T g[3][5], gr[3][5];
+    const bool x = bc.kind[b] == 2;
 #pragma unroll
     for (int j = 0; j < 3; ++j)
 #pragma unroll
-      for (int k = 0; k < 5; ++k) g[j][k] = gf[fp_index(tt, t, e, f, 15, j * 5 + k)];
+      for (int k = 0; k < 5; ++k) {
+        g[j][k] = gf[fp_index(tt, t, e, f, 15, j * 5 + k)];
+        gr[j][k] = x ? xg[15 * i + j * 5 + k] : g[j][k];
+      }
     viscous_normal_acc(ul, g, n, ph, T(-0.5), F);
-    viscous_normal_acc(ur, g, n, ph, T(-0.5), F);
+    viscous_normal_acc(ur, gr, n, ph, T(-0.5), F);
   }
   T m = bn[4 * i + 3];
 #pragma unroll
@@ -310,7 +333,8 @@ template <typename T>
 __global__ void k_bnd_ucommon(int nb, const int32_t* __restrict__ bidx,
                               const int32_t* __restrict__ bbc,
                               const T* __restrict__ uf, T* __restrict__ du,
-                              TypeTab tt, BCTab<T> bc) {
+                              TypeTab tt, BCTab<T> bc,
+                              const T* __restrict__ xu = nullptr) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nb) return;
   int t, f;
@@ -319,7 +343,7 @@ __global__ void k_bnd_ucommon(int nb, const int32_t* __restrict__ bidx,
   T ul[5], ur[5];
 #pragma unroll
   for (int k = 0; k < 5; ++k) ul[k] = uf[fp_index(tt, t, e, f, 5, k)];
-  ghost_state(bc, bbc[i], ul, ur);
+  ghost_state_x(bc, bbc[i], i, xu, ul, ur);
 #pragma unroll
   for (int k = 0; k < 5; ++k)
     du[fp_index(tt, t, e, f, 5, k)] = T(0.5) * (ur[k] - ul[k]);
@@ -358,7 +382,7 @@ __device__ __forceinline__ void write_visc_q(const ViscArgs<T>& va,
   T q[5] = {0, 0, 0, 0, 0};
   viscous_normal_acc(u, G, nv, ph, T(1), q);
   const int b = va.fbc[e * nf + f];
-  if (b >= 0) {
+  if (b >= 0 && bc.kind[b] != 2) {  // exchange points keep the inside q
     T ur[5], q2[5] = {0, 0, 0, 0, 0};
     if (bc.kind[b] == 0) {
 #pragma unroll
@@ -385,7 +409,7 @@ __device__ __forceinline__ void visc_q_pre(const BCTab<T>& bc, const Phys<T>& ph
 #pragma unroll
   for (int k = 0; k < 5; ++k) q[k] = T(0);
   viscous_normal_acc(u, G, nv, ph, T(1), q);
-  if (b >= 0) {
+  if (b >= 0 && bc.kind[b] != 2) {  // exchange points keep the inside q
     T ur[5], q2[5] = {0, 0, 0, 0, 0};
     if (bc.kind[b] == 0) {
 #pragma unroll
@@ -440,13 +464,18 @@ __global__ void k_face_flux_ns(int np, const int32_t* __restrict__ pl,
 }
 
 // Boundary points: F^C = |S^T n~| Rus(u, ghost) - q (q already averaged).
+// Exchange points take the partner's q (xq [nb][5]) and |S^T n~| (xm [nb])
+// as an interior face does: F^C = m Rus - (q - (m / m_R) q_R) / 2.
 template <typename T>
 __global__ void k_bnd_flux_ns(int nb, const int32_t* __restrict__ bidx,
                               const int32_t* __restrict__ bbc,
                               const T* __restrict__ bn,
                               const T* __restrict__ uf,
                               const T* __restrict__ q, T* __restrict__ fc,
-                              TypeTab tt, Phys<T> ph, BCTab<T> bc) {
+                              TypeTab tt, Phys<T> ph, BCTab<T> bc,
+                              const T* __restrict__ xu = nullptr,
+                              const T* __restrict__ xq = nullptr,
+                              const T* __restrict__ xm = nullptr) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nb) return;
   int t, f;
@@ -455,15 +484,44 @@ __global__ void k_bnd_flux_ns(int nb, const int32_t* __restrict__ bidx,
   T ul[5], ur[5], n[3] = {bn[4 * i], bn[4 * i + 1], bn[4 * i + 2]};
 #pragma unroll
   for (int k = 0; k < 5; ++k) ul[k] = uf[fp_index(tt, t, e, f, 5, k)];
-  ghost_state(bc, bbc[i], ul, ur);
+  const int b = bbc[i];
+  ghost_state_x(bc, b, i, xu, ul, ur);
   T F[5];
   rusanov(ul, ur, n, ph, F);
   T m = bn[4 * i + 3];
+  if (bc.kind[b] == 2) {
+    const T rl = m / xm[i];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      long long ix = fp_index(tt, t, e, f, 5, k);
+      fc[ix] = m * F[k] - T(0.5) * (q[ix] - rl * xq[5 * i + k]);
+    }
+    return;
+  }
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
     long long ix = fp_index(tt, t, e, f, 5, k);
     fc[ix] = m * F[k] - q[ix];
   }
+}
+
+// Halo exchange of one part: every exchange point it owns pushes its trace
+// (nv values at the flux point: u, the gradient, or the viscous normal flux
+// q) into the receive buffer of the part that shares the point, at that
+// part's boundary-point slot.  dst[r] is part r's buffer ([nb_r][nv]).
+template <typename T>
+__global__ void k_exchange_push(int n, const int32_t* __restrict__ code,
+                                const int32_t* __restrict__ to,
+                                const int32_t* __restrict__ slot,
+                                const T* __restrict__ src, int nv,
+                                T* const* __restrict__ dst, TypeTab tt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int t, f;
+  long long e;
+  decode_fp(code[i], tt, &t, &e, &f);
+  T* d = dst[to[i]] + (long long)slot[i] * nv;
+  for (int c = 0; c < nv; ++c) d[c] = src[fp_index(tt, t, e, f, nv, c)];
 }
 
 // ---------------------------------------------------------------------------

@@ -518,6 +518,18 @@ std::string build_mesh(const MeshInput& in, std::vector<HostType>& types,
         fpairs.push_back({left[i], left[found], {T[0], T[1], T[2]}});
       }
   }
+  // ---- element adjacency across every paired face (periodic ones too)
+  {
+    std::vector<int64_t> goff(types.size(), 0);
+    for (size_t t = 1; t < types.size(); ++t) goff[t] = goff[t - 1] + types[t - 1].ne;
+    for (auto& T : types) T.nbr.assign(size_t(T.ne) * T.ref.nfaces, -1);
+    for (auto& fp : fpairs) {
+      const FaceRec& A = faces[fp.a];
+      const FaceRec& B = faces[fp.b];
+      types[A.t].nbr[size_t(A.e) * types[A.t].ref.nfaces + A.f] = goff[B.t] + B.e;
+      types[B.t].nbr[size_t(B.e) * types[B.t].ref.nfaces + B.f] = goff[A.t] + A.e;
+    }
+  }
   // ---- boundary faces
   std::unordered_map<std::array<int64_t, 4>, int, Key4Hash> bkey;
   for (int64_t b = 0; b < in.n_bfaces; ++b) {

@@ -33,6 +33,9 @@ struct HostType {
   std::vector<double> rcpdjac;   // [ne][nupts]
   std::vector<double> fpts_x;    // [ne][nfpts][3]
   std::vector<double> fnvec;     // [ne][nfpts][3]  S^T n~ at flux points
+  std::vector<int64_t> nbr;      // [ne][nfaces] neighbour element across each
+                                 // face (global index: types in order hex,
+                                 // prism, tet, then element), -1 on a boundary
 };
 
 // One side of a flux-point pair: element type in bits 29..30, offset of
@@ -69,6 +72,15 @@ struct MeshInput {
 // products on straight ones (the metric the mesh itself uses).
 void metric_points(const HostType& T, int np, const double* pts,
                    std::vector<double>& S);
+
+// Partition all elements (global index as in HostType::nbr) into nparts by
+// recursive coordinate bisection of the element centroids.  mode 0
+// (weighted): one bisection of all elements, element of kind k weighing
+// w[k]; mode 1 (balanced): each element type bisected on its own, so every
+// part gets the same number of elements of each type (to within one).
+std::string partition_elements(const std::vector<HostType>& types, int nparts,
+                               int mode, const double w[3],
+                               std::vector<int32_t>& part);
 
 // Returns an empty string on success, else an error message.  ``err_mesh``
 // is set when the failure is a non-conforming / unmatched mesh.
