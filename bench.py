@@ -583,6 +583,68 @@ def config_tgv_antialias(fr, torch, device, steps=10, qdeg=9,
     return out
 
 
+def config_tgv_partitioned(fr, torch, device, steps=10, parts=(2, 4),
+                           precisions=("fp64", "fp32")):
+    """TGV 32^3 p=3 (the bench workload) split by recursive coordinate
+    bisection into 2 and 4 parts that run as one group on this GPU: each
+    stage pushes the exchange faces' solution traces, then the gradient
+    traces (FP64) or viscous normal fluxes (FP32), into the partners'
+    receive buffers.  Against the unpartitioned mesh: the cost of the
+    decomposition and exchange, and the difference after the steps."""
+    from paper_2408_16509_gb300 import partition
+    spec = workload_spec(N_CELLS)
+    out = {}
+    for prec in precisions:
+        kw = dict(physics="ns", gamma=1.4, mu=1.0 / RE, prandtl=PR,
+                  precision=prec, device=device)
+        whole = fr.FRMesh(spec, ORDER, **kw)
+        whole.set_variant("sumfact")
+        st = torch.cuda.Stream(device=device)
+        whole.set_stream(st)
+        u0 = _state(whole, tgv)
+        whole.set_solution(u0)
+        whole.rk_step("rk45", 1e-3, 2)
+        whole.set_solution(u0)
+        ms_whole = _timed_steps(torch, whole, st, "rk45", 1e-3, steps)
+        ref = whole.get_solution()
+        rec = {"whole_ms_per_step": ms_whole / steps}
+        for k in parts:
+            subs, ids, _ = partition.split(spec, k, "weighted")
+            members = []
+            for sp in subs:
+                g = fr.FRMesh(sp, ORDER, bcs=partition.exchange_bcs({}), **kw)
+                g.set_variant("sumfact")
+                g.set_stream(st)
+                members.append(g)
+            grp = fr.FRGroup(members)
+            for g, ur in zip(members, partition.scatter(u0, ids)):
+                g.set_solution(ur)
+            grp.rk_step("rk45", 1e-3, 2)
+            for g, ur in zip(members, partition.scatter(u0, ids)):
+                g.set_solution(ur)
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            t0.record(st)
+            grp.rk_step("rk45", 1e-3, steps)
+            t1.record(st)
+            torch.cuda.synchronize()
+            ms = t0.elapsed_time(t1)
+            got = partition.gather([g.get_solution() for g in members], ids, ref)
+            nb = [g.pair_counts()[1] for g in members]
+            rec[f"{k}_parts"] = {
+                "ms_per_step": ms / steps,
+                "gdof_stage_s": _gdofs(whole, 5, steps, ms),
+                "exchange_points": int(sum(nb)),
+                "rel_l2_vs_whole": _rel_l2(got, ref)}
+            grp.close()
+            for g in members:
+                g.close()
+        whole.close()
+        out[prec] = rec
+    return out
+
+
 def config_shu_osher(fr, torch, device, steps=40):
     """256x8x8 hexes on [-5,5]x[0,0.3125]^2, p=3, Euler, RK4 dt 9e-4, FP32,
     entropy filter: plain root-find, then the predictor trained on the
@@ -651,6 +713,7 @@ def other_configs(fr, torch, device):
                      ("tgv_32^3_p3_fp32_adaptive", config_tgv_adaptive),
                      ("tgv_32^3_p3_curved", config_tgv_curved),
                      ("tgv_32^3_p3_antialias_q9", config_tgv_antialias),
+                     ("tgv_32^3_p3_partitioned", config_tgv_partitioned),
                      ("shu_osher_256x8x8_p3_filter", config_shu_osher)):
         try:
             out[name] = fn(fr, torch, device)
@@ -740,7 +803,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", default=None,
                     choices=["vortex", "tgv48", "mixed", "shu_osher", "adaptive",
-                             "curved", "antialias"],
+                             "curved", "antialias", "partitioned"],
                     help="run one side workload alone and print its record "
                          "(profiling aid; not a contract line)")
     ap.add_argument("--cells", type=int, default=40,
@@ -765,6 +828,8 @@ def main():
                "curved": lambda f, t, d: config_tgv_curved(
                    f, t, d, precisions=tuple(args.precisions.split(","))),
                "antialias": lambda f, t, d: config_tgv_antialias(
+                   f, t, d, precisions=tuple(args.precisions.split(","))),
+               "partitioned": lambda f, t, d: config_tgv_partitioned(
                    f, t, d, precisions=tuple(args.precisions.split(","))),
                "shu_osher": config_shu_osher,
                "mixed": lambda f, t, d: config_mixed_elements(

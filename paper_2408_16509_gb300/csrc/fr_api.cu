@@ -1697,7 +1697,22 @@ struct fr_group {
   void** d_xu = nullptr;  // members' xu pointers (device array)
   void** d_xg = nullptr;  // members' xg pointers
   std::vector<void*> allocs;
+  // one captured step per scheme (RK4, RK45), valid for the members' epochs
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  std::vector<long long> graph_epoch[2];
+  // one stream and event per member: the members' kernels of a phase are
+  // captured as parallel branches between the exchange points
+  std::vector<cudaStream_t> aux;
+  std::vector<cudaEvent_t> ev;
+  cudaEvent_t fork = nullptr;
   ~fr_group() {
+    for (auto& ge : graph)
+      if (ge) cudaGraphExecDestroy(ge);
+    for (cudaStream_t st : aux)
+      if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+    if (fork) cudaEventDestroy(fork);
     for (void* p : allocs)
       if (p) cudaFree(p);
     for (fr_mesh* x : m) x->in_group = false;
@@ -1761,15 +1776,59 @@ int group_run(fr_group* g, int mode, double dt, int nsteps) {
     cudaMemsetAsync(m->d_flag, 0, sizeof(int), s);
   }
   const int nst = mode == 0 ? 1 : (mode == 1 ? 4 : 5);
-  for (int it = 0; it < nsteps; ++it)
+  // members' launches of one phase on their own streams, joined back into s
+  auto phase_all = [&](int st, int ph, bool par) {
+    if (!par) {
+      for (fr_mesh* m : g->m) launch_stage<T, TR>(m, s, mode, st, nullptr, ph);
+      return;
+    }
+    cudaEventRecord(g->fork, s);
+    for (size_t r = 0; r < g->m.size(); ++r) {
+      cudaStreamWaitEvent(g->aux[r], g->fork, 0);
+      launch_stage<T, TR>(g->m[r], g->aux[r], mode, st, nullptr, ph);
+      cudaEventRecord(g->ev[r], g->aux[r]);
+    }
+    for (size_t r = 0; r < g->m.size(); ++r) cudaStreamWaitEvent(s, g->ev[r], 0);
+  };
+  auto one_step = [&](bool par) {
     for (int st = 0; st < nst; ++st) {
       push(0);
       if (ns) {
-        for (fr_mesh* m : g->m) launch_stage<T, TR>(m, s, mode, st, nullptr, 1);
+        phase_all(st, 1, par);
         push(1);
       }
-      for (fr_mesh* m : g->m) launch_stage<T, TR>(m, s, mode, st, nullptr, 2);
+      phase_all(st, 2, par);
     }
+  };
+  if (mode == 0) {
+    one_step(false);
+  } else {
+    // RK steps replay one captured graph (rebuilt when a member's launch
+    // configuration changed)
+    const int gi = mode - 1;
+    std::vector<long long> ep;
+    for (fr_mesh* m : g->m) ep.push_back(m->epoch);
+    if (!g->graph[gi] || g->graph_epoch[gi] != ep) {
+      cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+      one_step(g->m.size() > 1);
+      cudaGraph_t gr;
+      cudaError_t ce = cudaStreamEndCapture(s, &gr);
+      if (ce != cudaSuccess) {
+        restore();
+        return fail(FR_ECUDA, std::string("group graph capture: ") + cudaGetErrorString(ce));
+      }
+      if (g->graph[gi]) cudaGraphExecDestroy(g->graph[gi]);
+      ce = cudaGraphInstantiate(&g->graph[gi], gr, 0);
+      cudaGraphDestroy(gr);
+      if (ce != cudaSuccess) {
+        g->graph[gi] = nullptr;
+        restore();
+        return fail(FR_ECUDA, std::string("group graph instantiate: ") + cudaGetErrorString(ce));
+      }
+      g->graph_epoch[gi] = ep;
+    }
+    for (int it = 0; it < nsteps; ++it) cudaGraphLaunch(g->graph[gi], s);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     restore();
@@ -2473,6 +2532,13 @@ int fr_group_create(fr_mesh* const* meshes, int n, fr_group** out) {
   g->m.assign(meshes, meshes + n);
   int rc = FR_PREC(a, group_setup, g.get());
   if (rc) return rc;
+  g->aux.assign(n, nullptr);
+  g->ev.assign(n, nullptr);
+  for (int i = 0; i < n; ++i) {
+    CK(cudaStreamCreateWithFlags(&g->aux[i], cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&g->ev[i], cudaEventDisableTiming));
+  }
+  CK(cudaEventCreateWithFlags(&g->fork, cudaEventDisableTiming));
   for (fr_mesh* m : g->m) m->in_group = true;
   *out = g.release();
   return FR_OK;
