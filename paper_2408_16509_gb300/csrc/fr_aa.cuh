@@ -121,6 +121,136 @@ __global__ void __launch_bounds__(kAaThreads)
 }
 
 // ---------------------------------------------------------------------------
+// Dense form with the operators resident in shared memory and E elements per
+// pass.  Solution-point and rule-point counts are padded to a multiple of
+// W = 16 / sizeof(T) (zero rows / columns), so the per-element operands
+// that every thread of a pass reads alike (the element's u and gradient in
+// phase 1, its transformed flux at the rule points in phase 2) come as
+// 16-byte broadcast loads: W FMAs per load of those operands.
+template <typename T>
+__host__ __device__ constexpr int aa_w() { return 16 / int(sizeof(T)); }
+__host__ __device__ inline int aa_ru(int n, int w) { return (n + w - 1) / w * w; }
+
+template <typename T, int NU>
+inline size_t aa_dense_v_smem(int nq, int epb) {
+  constexpr int W = aa_w<T>();
+  const int nup = aa_ru(NU, W), nqp = aa_ru(nq, W);
+  return (2 * size_t(nup) * nqp + size_t(epb) * (20 * nup + 15 * nqp)) * sizeof(T);
+}
+
+template <typename T, typename TR, int NU, bool NS>
+__global__ void __launch_bounds__(kAaThreads)
+    k_aa_flux_dense_v(long long ne, int epb, const T* __restrict__ uin,
+                      const TR* __restrict__ X, const T* __restrict__ grad,
+                      const T* __restrict__ smq, AaOps<T> gop, Phys<T> ph,
+                      T* __restrict__ tf) {
+  constexpr int W = aa_w<T>();
+  constexpr int NUP = (NU + W - 1) / W * W;
+  using V = uint4;  // 16 bytes of W values
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nq = gop.nq, nqp = aa_ru(nq, W);
+  T* BT = reinterpret_cast<T*>(smem_raw);  // [NUP][nqp]
+  T* PT = BT + NUP * nqp;                   // [nqp][NUP]
+  T* us = PT + NUP * nqp;                   // [epb][20][NUP]
+  T* fq = us + epb * 20 * NUP;              // [epb][15][nqp]
+  for (int i = threadIdx.x; i < NUP * nqp; i += blockDim.x) {
+    const int z = i / nqp, q = i - z * nqp;
+    BT[i] = (z < NU && q < nq) ? gop.BT[z * nq + q] : T(0);
+    const int q2 = i / NUP, z2 = i - q2 * NUP;
+    PT[i] = (z2 < NU && q2 < nq) ? gop.PT[q2 * NU + z2] : T(0);
+  }
+  for (int i = threadIdx.x; i < epb * 20 * NUP; i += blockDim.x) us[i] = T(0);
+  __syncthreads();
+  const int nf = NS ? 20 : 5;
+  for (long long e0 = (long long)blockIdx.x * epb; e0 < ne; e0 += (long long)gridDim.x * epb) {
+    const int ecnt = int(ne - e0 < epb ? ne - e0 : epb);
+    for (int i = threadIdx.x; i < ecnt * 5 * NU; i += blockDim.x) {
+      const int le = i / (5 * NU), r = i - le * 5 * NU, k = r / NU, z = r - k * NU;
+      const long long g = (e0 + le) * 5 * NU + r;
+      us[(le * 20 + k) * NUP + z] = uin ? uin[g] : T(X[g]);
+    }
+    if (NS)
+      for (int i = threadIdx.x; i < ecnt * 15 * NU; i += blockDim.x) {
+        const int le = i / (15 * NU), r = i - le * 15 * NU, c = r / NU, z = r - c * NU;
+        us[(le * 20 + 5 + c) * NUP + z] = grad[(e0 + le) * 15 * NU + r];
+      }
+    __syncthreads();
+    // phase 1: one thread per (element, rule point)
+    for (int it = threadIdx.x; it < ecnt * nqp; it += blockDim.x) {
+      const int le = it / nqp, q = it - le * nqp;
+      const T* ue = us + le * 20 * NUP;
+      T* fe = fq + le * 15 * nqp;
+      if (q >= nq) {
+#pragma unroll
+        for (int c = 0; c < 15; ++c) fe[c * nqp + q] = T(0);
+        continue;
+      }
+      T acc[20];
+#pragma unroll
+      for (int k = 0; k < 20; ++k) acc[k] = T(0);
+      for (int z0 = 0; z0 < NUP; z0 += W) {
+        T b[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) b[w] = BT[(z0 + w) * nqp + q];
+#pragma unroll
+        for (int k = 0; k < 20; ++k) {
+          if (k >= nf) break;
+          const V r = *reinterpret_cast<const V*>(ue + k * NUP + z0);
+          const T* v = reinterpret_cast<const T*>(&r);
+#pragma unroll
+          for (int w = 0; w < W; ++w) acc[k] += b[w] * v[w];
+        }
+      }
+      T F[3][5];
+      euler_flux(acc, ph, F);
+      if (NS) {
+        T gq[3][5];
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+          for (int k = 0; k < 5; ++k) gq[j][k] = acc[5 + j * 5 + k];
+        viscous_flux_acc(acc, gq, ph, T(-1), F);
+      }
+      T S[3][3];
+      const long long e = e0 + le;
+#pragma unroll
+      for (int r = 0; r < 9; ++r) S[r / 3][r % 3] = smq[(e * 9 + r) * nq + q];
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+          fe[(d * 5 + k) * nqp + q] = S[d][0] * F[0][k] + S[d][1] * F[1][k] + S[d][2] * F[2][k];
+    }
+    __syncthreads();
+    // phase 2: one thread per (element, direction, solution point), the
+    // five variables of that direction
+    for (int it = threadIdx.x; it < ecnt * 3 * NU; it += blockDim.x) {
+      const int le = it / (3 * NU), r = it - le * 3 * NU, d = r / NU, z = r - d * NU;
+      const T* fe = fq + (le * 15 + d * 5) * nqp;
+      T acc[5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) acc[c] = T(0);
+      for (int q0 = 0; q0 < nqp; q0 += W) {
+        T p[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) p[w] = PT[(q0 + w) * NUP + z];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          const V rv = *reinterpret_cast<const V*>(fe + c * nqp + q0);
+          const T* v = reinterpret_cast<const T*>(&rv);
+#pragma unroll
+          for (int w = 0; w < W; ++w) acc[c] += p[w] * v[w];
+        }
+      }
+      const long long e = e0 + le;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) tf[(e * 15 + d * 5 + c) * NU + z] = acc[c];
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Hexahedra, sum-factorised.  The basis, the solution points and the rule are
 // tensor products, so B = B1 (x) B1 (x) B1 and P = P1 (x) P1 (x) P1 with the 1D
 // factors B1[i][a] = l_a(x_i) (Q rule points, N solution points per line) and

@@ -127,6 +127,8 @@ struct DevType {
   int aa_nq = 0, aa_ctas = 1;
   bool aa_hex = false;        // sum-factorised hexahedron form fits
   bool aa_dense = false;      // dense form fits
+  bool aa_dv = false;         // vectorised dense form (operators resident)
+  int aa_epb = 1, aa_dv_ctas = 1;
   int aa_hex_ctas = 1;
   HexAaOps<double> hxaa64{};
   HexAaOps<float> hxaa32{};
@@ -633,6 +635,18 @@ void launch_aa_flux(fr_mesh* m, const DevType& D, cudaStream_t s, bool from_x,
   const AaOps<T> op{(const T*)D.aaBT, (const T*)D.aaPT, D.aa_nq};
   dispatch(D.kind, m->order, [&](auto nu, auto nf) {
     constexpr int NU = decltype(nu)::value;
+    if (D.aa_dv) {
+      const long long groups = (D.ne + D.aa_epb - 1) / D.aa_epb;
+      const unsigned grid = unsigned(std::min<long long>(groups, (long long)m->num_sms * D.aa_dv_ctas));
+      const size_t sm = aa_dense_v_smem<T, NU>(D.aa_nq, D.aa_epb);
+      if (ns)
+        k_aa_flux_dense_v<T, TR, NU, true><<<grid, kAaThreads, sm, s>>>(
+            D.ne, D.aa_epb, uin, X, (const T*)D.grad, (const T*)D.aasmq, op, ph, (T*)D.tf);
+      else
+        k_aa_flux_dense_v<T, TR, NU, false><<<grid, kAaThreads, sm, s>>>(
+            D.ne, D.aa_epb, uin, X, nullptr, (const T*)D.aasmq, op, ph, (T*)D.tf);
+      return;
+    }
     const unsigned grid = unsigned(std::min<long long>(D.ne, (long long)m->num_sms * D.aa_ctas));
     const size_t sm = aa_dense_smem<T, NU>(D.aa_nq);
     if (ns)
@@ -1657,6 +1671,23 @@ int aa_setup(fr_mesh* m) {
     D.aa_nq = nq;
     if (need <= size_t(smax)) dispatch(D.kind, m->order, [&](auto nuc, auto nfc) {
       constexpr int NU = decltype(nuc)::value;
+      // vectorised form: several elements per pass (3 NU threads each in the
+      // projection) while a block stays <= 56 KB, for 4 blocks per SM
+      int epb = std::max(1, std::min(8, (kAaThreads + 3 * NU - 1) / (3 * NU)));
+      while (epb > 1 && aa_dense_v_smem<T, NU>(nq, epb) > 56 * 1024) --epb;
+      D.aa_epb = epb;
+      D.aa_dv = aa_dense_v_smem<T, NU>(nq, epb) <= 100 * 1024;
+      if (D.aa_dv) {
+        const int smv = int(aa_dense_v_smem<T, NU>(nq, epb));
+        int av = 1 << 20;
+        for (auto fn : {k_aa_flux_dense_v<T, TR, NU, true>, k_aa_flux_dense_v<T, TR, NU, false>}) {
+          int a1 = 0;
+          cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smv);
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a1, fn, kAaThreads, smv);
+          av = std::min(av, a1);
+        }
+        D.aa_dv_ctas = av > 0 && av < (1 << 20) ? av : 1;
+      }
       const int sm = int(aa_dense_smem<T, NU>(nq));
       int a = 0;
       for (auto fn : {k_aa_flux_dense<T, TR, NU, true>, k_aa_flux_dense<T, TR, NU, false>}) {
