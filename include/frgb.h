@@ -303,7 +303,8 @@ int fr_partition_faces(const fr_mesh* mesh, const int32_t* part, int rank,
  * device, then the stage continues, so the result is the unpartitioned
  * mesh's up to rounding.  Runs on the first member's stream and
  * synchronises it.  fr_rhs / fr_rk_step on a member outside its group
- * return FR_EINVAL. */
+ * return FR_EINVAL, and so does fr_mesh_destroy of a member (the mesh is
+ * kept) until its group is destroyed. */
 int fr_group_create(fr_mesh* const* meshes, int n, fr_group** out);
 int fr_group_destroy(fr_group* group);
 int fr_group_rhs(fr_group* group);

@@ -268,12 +268,24 @@ struct HexAaOps {
   int q;
 };
 
+// Field strides of the layouts read by whole warps across field boundaries
+// ([f][c][j][i] in buffer A, [f][k][j][i] in buffer B): padded to the
+// smallest value >= the field's size that is congruent to Q^2 modulo 32
+// banks, so a warp whose lines continue into the next field keeps distinct
+// banks.
+__host__ __device__ inline int hex_aa_pad(int size, int q) {
+  return size + (((q * q - size) % 32) + 32) % 32;
+}
+__host__ __device__ inline int hex_aa_fsa(int n, int q) { return hex_aa_pad(n * q * q, q); }
+__host__ __device__ inline int hex_aa_fsb(int q) { return hex_aa_pad(q * q * q, q); }
 // shared memory of one element: ping-pong buffers A and B (T values)
 __host__ __device__ inline int hex_aa_buf_a(int n, int q) {
-  return 20 * n * (n * n > q * q ? n * n : q * q);
+  const int t = 20 * n * n * n, u = 20 * hex_aa_fsa(n, q);
+  return t > u ? t : u;
 }
 __host__ __device__ inline int hex_aa_buf_b(int n, int q) {
-  return 20 * q * (n * n > q * q ? n * n : q * q);
+  const int t = 20 * q * n * n, u = 20 * hex_aa_fsb(q);
+  return t > u ? t : u;
 }
 constexpr int kAaOpsT = 2 * kAaQMax * 5;  // staged b1 and p1 (T values)
 
@@ -331,6 +343,7 @@ __global__ void __launch_bounds__(kAaThreads)
   constexpr int NFLD = NS ? 20 : 5;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int Q = QT > 0 ? QT : op.q, Q2 = Q * Q, Q3 = Q2 * Q;
+  const int FA = hex_aa_fsa(N, Q), FB = hex_aa_fsb(Q);
   T* b1 = reinterpret_cast<T*>(smem_raw);  // [Q][N]
   T* p1 = b1 + kAaQMax * 5;                // [N][Q]
   T* A = b1 + kAaOpsT;
@@ -365,7 +378,7 @@ __global__ void __launch_bounds__(kAaThreads)
     __syncthreads();
     // y: Bf[f][c][b][i] -> A[f][c][j][i]   (line = (f, c), i)
     for (int l = t; l < NFLD * N * Q; l += nt) {
-      const int fc = l / Q, i = l - fc * Q;
+      const int fc = l / Q, i = l - fc * Q, f = fc / N, c = fc - f * N;
       T in[N];
 #pragma unroll
       for (int b = 0; b < N; ++b) in[b] = Bf[(fc * N + b) * Q + i];
@@ -374,7 +387,7 @@ __global__ void __launch_bounds__(kAaThreads)
         T s = T(0);
 #pragma unroll
         for (int b = 0; b < N; ++b) s += cb(j, b) * in[b];
-        A[(fc * Q + j) * Q + i] = s;
+        A[f * FA + (c * Q + j) * Q + i] = s;
       }
     }
     __syncthreads();
@@ -383,13 +396,13 @@ __global__ void __launch_bounds__(kAaThreads)
       const int f = l / Q2, ji = l - f * Q2;
       T in[N];
 #pragma unroll
-      for (int c = 0; c < N; ++c) in[c] = A[(f * N + c) * Q2 + ji];
+      for (int c = 0; c < N; ++c) in[c] = A[f * FA + c * Q2 + ji];
 #pragma unroll
       for (int k = 0; k < (QT > 0 ? QT : Q); ++k) {
         T s = T(0);
 #pragma unroll
         for (int c = 0; c < N; ++c) s += cb(k, c) * in[c];
-        Bf[(f * Q + k) * Q2 + ji] = s;
+        Bf[f * FB + k * Q2 + ji] = s;
       }
     }
     __syncthreads();
@@ -397,7 +410,7 @@ __global__ void __launch_bounds__(kAaThreads)
     for (int pt = t; pt < Q3; pt += nt) {
       T uq[5];
 #pragma unroll
-      for (int k = 0; k < 5; ++k) uq[k] = Bf[k * Q3 + pt];
+      for (int k = 0; k < 5; ++k) uq[k] = Bf[k * FB + pt];
       T F[3][5];
       euler_flux(uq, ph, F);
       if (NS) {
@@ -405,17 +418,18 @@ __global__ void __launch_bounds__(kAaThreads)
 #pragma unroll
         for (int j = 0; j < 3; ++j)
 #pragma unroll
-          for (int k = 0; k < 5; ++k) g[j][k] = Bf[(5 + j * 5 + k) * Q3 + pt];
+          for (int k = 0; k < 5; ++k) g[j][k] = Bf[(5 + j * 5 + k) * FB + pt];
         viscous_flux_acc(uq, g, ph, T(-1), F);
       }
       T S[3][3];
 #pragma unroll
-      for (int r = 0; r < 9; ++r) S[r / 3][r % 3] = smq[(e * 9 + r) * Q3 + pt];
+      for (int r = 0; r < 9; ++r)
+        S[r / 3][r % 3] = smq[(e * 9 + r) * Q3 + pt];
 #pragma unroll
       for (int d = 0; d < 3; ++d)
 #pragma unroll
         for (int k = 0; k < 5; ++k)
-          Bf[(d * 5 + k) * Q3 + pt] = S[d][0] * F[0][k] + S[d][1] * F[1][k] + S[d][2] * F[2][k];
+          Bf[(d * 5 + k) * FB + pt] = S[d][0] * F[0][k] + S[d][1] * F[1][k] + S[d][2] * F[2][k];
     }
     __syncthreads();
     // z back: Bf[f][k][j][i] -> A[f][c][j][i]
@@ -426,23 +440,23 @@ __global__ void __launch_bounds__(kAaThreads)
       for (int c = 0; c < N; ++c) acc[c] = T(0);
 #pragma unroll
       for (int k = 0; k < (QT > 0 ? QT : Q); ++k) {
-        const T v = Bf[(f * Q + k) * Q2 + ji];
+        const T v = Bf[f * FB + k * Q2 + ji];
 #pragma unroll
         for (int c = 0; c < N; ++c) acc[c] += cp(c, k) * v;
       }
 #pragma unroll
-      for (int c = 0; c < N; ++c) A[(f * N + c) * Q2 + ji] = acc[c];
+      for (int c = 0; c < N; ++c) A[f * FA + c * Q2 + ji] = acc[c];
     }
     __syncthreads();
     // y back: A[f][c][j][i] -> Bf[f][c][b][i]
     for (int l = t; l < 15 * N * Q; l += nt) {
-      const int fc = l / Q, i = l - fc * Q;
+      const int fc = l / Q, i = l - fc * Q, f = fc / N, c = fc - f * N;
       T acc[N];
 #pragma unroll
       for (int b = 0; b < N; ++b) acc[b] = T(0);
 #pragma unroll
       for (int j = 0; j < (QT > 0 ? QT : Q); ++j) {
-        const T v = A[(fc * Q + j) * Q + i];
+        const T v = A[f * FA + (c * Q + j) * Q + i];
 #pragma unroll
         for (int b = 0; b < N; ++b) acc[b] += cp(b, j) * v;
       }

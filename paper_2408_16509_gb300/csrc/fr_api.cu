@@ -2179,6 +2179,7 @@ int fr_mesh_create(const fr_mesh_desc* d, fr_mesh** out) {
 
 int fr_mesh_destroy(fr_mesh* m) {
   if (!m) return FR_OK;
+  if (m->in_group) return fail(FR_EINVAL, "the mesh belongs to a group: destroy the group first");
   if (!m->host_only) {
     cudaSetDevice(m->device);
     if (m->stream) cudaStreamSynchronize(m->stream);

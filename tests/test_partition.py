@@ -182,3 +182,15 @@ def test_partitioned_setup_two_gloo_ranks():
             assert same
             assert counts[0] == counts[1] > 0
         assert out[0][2] + out[1][2] == 64
+
+
+def test_boundary_points_of_a_part():
+    """A part of a fully periodic box has only exchange boundary points, at
+    the positions of its faces towards the other part."""
+    spec = box_hex((4, 2, 2), perturb=0.1)
+    subs, ids, part = partition.split(spec, 2, "weighted")
+    g = fr.FRMesh(subs[0], 2, bcs=partition.exchange_bcs({}), device=-1)
+    x, kind = g.boundary_points()
+    _, nb = g.pair_counts()
+    assert len(x) == nb > 0 and np.all(kind == 2)
+    assert np.all((x >= -1e-12) & (x <= 1 + 1e-12))
