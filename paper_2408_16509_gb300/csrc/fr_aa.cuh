@@ -138,8 +138,11 @@ inline size_t aa_dense_v_smem(int nq, int epb) {
   return (2 * size_t(nup) * nqp + size_t(epb) * (20 * nup + 15 * nqp)) * sizeof(T);
 }
 
+// 256 threads: the resident operators (up to 41 KB) are shared by more warps
+constexpr int kAaVThreads = 256;
+
 template <typename T, typename TR, int NU, bool NS>
-__global__ void __launch_bounds__(kAaThreads)
+__global__ void __launch_bounds__(kAaVThreads)
     k_aa_flux_dense_v(long long ne, int epb, const T* __restrict__ uin,
                       const TR* __restrict__ X, const T* __restrict__ grad,
                       const T* __restrict__ smq, AaOps<T> gop, Phys<T> ph,

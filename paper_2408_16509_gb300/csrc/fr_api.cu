@@ -640,10 +640,10 @@ void launch_aa_flux(fr_mesh* m, const DevType& D, cudaStream_t s, bool from_x,
       const unsigned grid = unsigned(std::min<long long>(groups, (long long)m->num_sms * D.aa_dv_ctas));
       const size_t sm = aa_dense_v_smem<T, NU>(D.aa_nq, D.aa_epb);
       if (ns)
-        k_aa_flux_dense_v<T, TR, NU, true><<<grid, kAaThreads, sm, s>>>(
+        k_aa_flux_dense_v<T, TR, NU, true><<<grid, kAaVThreads, sm, s>>>(
             D.ne, D.aa_epb, uin, X, (const T*)D.grad, (const T*)D.aasmq, op, ph, (T*)D.tf);
       else
-        k_aa_flux_dense_v<T, TR, NU, false><<<grid, kAaThreads, sm, s>>>(
+        k_aa_flux_dense_v<T, TR, NU, false><<<grid, kAaVThreads, sm, s>>>(
             D.ne, D.aa_epb, uin, X, nullptr, (const T*)D.aasmq, op, ph, (T*)D.tf);
       return;
     }
@@ -1672,18 +1672,18 @@ int aa_setup(fr_mesh* m) {
     if (need <= size_t(smax)) dispatch(D.kind, m->order, [&](auto nuc, auto nfc) {
       constexpr int NU = decltype(nuc)::value;
       // vectorised form: several elements per pass (3 NU threads each in the
-      // projection) while a block stays <= 56 KB, for 4 blocks per SM
-      int epb = std::max(1, std::min(8, (kAaThreads + 3 * NU - 1) / (3 * NU)));
-      while (epb > 1 && aa_dense_v_smem<T, NU>(nq, epb) > 56 * 1024) --epb;
+      // projection) while a block stays <= 110 KB (two or more per SM)
+      int epb = std::max(1, std::min(8, (kAaVThreads + 3 * NU - 1) / (3 * NU)));
+      while (epb > 1 && aa_dense_v_smem<T, NU>(nq, epb) > 110 * 1024) --epb;
       D.aa_epb = epb;
-      D.aa_dv = aa_dense_v_smem<T, NU>(nq, epb) <= 100 * 1024;
+      D.aa_dv = aa_dense_v_smem<T, NU>(nq, epb) <= 110 * 1024;
       if (D.aa_dv) {
         const int smv = int(aa_dense_v_smem<T, NU>(nq, epb));
         int av = 1 << 20;
         for (auto fn : {k_aa_flux_dense_v<T, TR, NU, true>, k_aa_flux_dense_v<T, TR, NU, false>}) {
           int a1 = 0;
           cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smv);
-          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a1, fn, kAaThreads, smv);
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a1, fn, kAaVThreads, smv);
           av = std::min(av, a1);
         }
         D.aa_dv_ctas = av > 0 && av < (1 << 20) ? av : 1;
