@@ -286,7 +286,9 @@ int fr_partition(const fr_mesh* mesh, int nparts, int mode, const double* weight
 int fr_partition_faces(const fr_mesh* mesh, const int32_t* part, int rank,
                        int64_t* faces, int64_t* count);
 
-/* Partition groups: the parts of one mesh (each created from its elements,
+/* Partition groups (the exchange between partitions of Section 3,
+ * "Multi-node capabilities", here between the parts of a mesh on one
+ * device): the parts of one mesh (each created from its elements,
  * with its faces towards other parts as FR_BC_EXCHANGE boundary faces) run
  * together on one device.  fr_group_create matches every exchange flux
  * point with exactly one exchange point of another member by physical

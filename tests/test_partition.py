@@ -194,3 +194,14 @@ def test_boundary_points_of_a_part():
     _, nb = g.pair_counts()
     assert len(x) == nb > 0 and np.all(kind == 2)
     assert np.all((x >= -1e-12) & (x <= 1 + 1e-12))
+
+
+def test_groups_refuse_host_only_members():
+    """Grouping needs device handles; host-only parts are refused before any
+    device call."""
+    spec = box_hex((4, 2, 2), perturb=0.1)
+    subs, _, _ = partition.split(spec, 2, "weighted")
+    parts = [fr.FRMesh(s, 2, bcs=partition.exchange_bcs({}), device=-1) for s in subs]
+    with pytest.raises(fr.FRError) as e:
+        fr.FRGroup(parts)
+    assert e.value.name == "FR_EINVAL"
