@@ -27,6 +27,13 @@ takes the transformed flux at the points of a degree-qdeg volume rule
 there) and replaces the collocated f~ by its least-squares projection onto
 the solution space, f~ = P f~_q; steps 4 and 5 are unchanged.
 
+LDG (``ldg=(beta, tau)``; the paper names no viscous scheme, reading of the
+local DG flux of Cockburn and Shu): along every interface's orientation
+(mesh.pair_l is the "-" side, a boundary's inside is "-" and its outside
+state "+"), u^C = (1/2 - beta) u- + (1/2 + beta) u+, the viscous common
+flux (1/2 + beta) F_v- + (1/2 - beta) F_v+ (biased the other way), and the
+common normal flux gains the penalty tau (u- - u+).  beta = tau = 0 is BR1.
+
 Boundary conditions (by tag): ('state', rho, u, v, w, p) -- outside state is
 the given constant state; ('extrap',) -- outside state = inside state.
 """
@@ -37,8 +44,9 @@ from .physics import euler_flux, prim_to_cons, rusanov, viscous_flux
 
 class FRSystem:
     def __init__(self, mesh, physics="euler", gamma=1.4, mu=0.0, pr=0.72,
-                 bcs=None, antialias=None):
+                 bcs=None, antialias=None, ldg=None):
         self.m = mesh
+        self.beta, self.tau = (0.0, 0.0) if ldg is None else (float(ldg[0]), float(ldg[1]))
         self.aa = {}
         if antialias is not None:
             for t in mesh.types:
@@ -86,10 +94,11 @@ class FRSystem:
         m = self.m
         uc = np.empty_like(uf)
         l, r = m.pair_l, m.pair_r
-        uc[l] = uc[r] = 0.5 * (uf[l] + uf[r])
+        wl, wr = 0.5 - self.beta, 0.5 + self.beta
+        uc[l] = uc[r] = wl * uf[l] + wr * uf[r]
         if len(m.bnd_g):
             ub = uf[m.bnd_g]
-            uc[m.bnd_g] = 0.5 * (ub + self.ghost(ub))
+            uc[m.bnd_g] = wl * ub + wr * self.ghost(ub)
         du = self._split(uc - uf)
         grads = {}
         for t in m.types:
@@ -117,10 +126,11 @@ class FRSystem:
         l, r = m.pair_l, m.pair_r
         n = m.fn_all[l]
         F = rusanov(uf[l], uf[r], n, g)
+        vl, vr = 0.5 + self.beta, 0.5 - self.beta
         if ns:
-            fv = 0.5 * (viscous_flux(uf[l], gf[l], g, self.mu, self.pr)
-                        + viscous_flux(uf[r], gf[r], g, self.mu, self.pr))
-            F = F - np.einsum("pj,pjk->pk", n, fv)
+            fv = (vl * viscous_flux(uf[l], gf[l], g, self.mu, self.pr)
+                  + vr * viscous_flux(uf[r], gf[r], g, self.mu, self.pr))
+            F = F - np.einsum("pj,pjk->pk", n, fv) + self.tau * (uf[l] - uf[r])
         fc[l] = m.fm_all[l][:, None] * F
         fc[r] = -m.fm_all[r][:, None] * F
         if len(m.bnd_g):
@@ -130,9 +140,9 @@ class FRSystem:
             nb = m.fn_all[b]
             F = rusanov(ub, ug, nb, g)
             if ns:
-                fv = 0.5 * (viscous_flux(ub, gf[b], g, self.mu, self.pr)
-                            + viscous_flux(ug, gf[b], g, self.mu, self.pr))
-                F = F - np.einsum("pj,pjk->pk", nb, fv)
+                fv = (vl * viscous_flux(ub, gf[b], g, self.mu, self.pr)
+                      + vr * viscous_flux(ug, gf[b], g, self.mu, self.pr))
+                F = F - np.einsum("pj,pjk->pk", nb, fv) + self.tau * (ub - ug)
             fc[b] = m.fm_all[b][:, None] * F
         fc = self._split(fc)
         out = {}

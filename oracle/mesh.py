@@ -204,8 +204,20 @@ class FRMesh:
         self._pair_points(face_pairs, bnd, tol)
 
     def _pair_points(self, face_pairs, bnd, tol):
+        # Orientation of every interface: its "-" side (pair_l) is the
+        # element with the lower global index (types in the order hex, pri,
+        # tet, then element number), the lower face number for an element
+        # paired with itself.  Upwind-biased schemes (LDG) depend on it.
+        eoff, n = {}, 0
+        for t in self.types:
+            eoff[t] = n
+            n += self.ne[t]
         gl, gr = [], []
         for rl, rr, T in face_pairs:
+            kl = (eoff[ETYPE_ORDER[rl[0]]] + rl[1], rl[2])
+            kr = (eoff[ETYPE_ORDER[rr[0]]] + rr[1], rr[2])
+            if kr < kl:
+                rl, rr, T = rr, rl, -np.asarray(T, float)
             tl, tr = ETYPE_ORDER[rl[0]], ETYPE_ORDER[rr[0]]
             il = self.el[tl].face_fpts[rl[2]]
             ir = self.el[tr].face_fpts[rr[2]]
