@@ -312,6 +312,18 @@ int fr_group_destroy(fr_group* group);
 int fr_group_rhs(fr_group* group);
 int fr_group_rk_step(fr_group* group, int scheme, double dt, int nsteps);
 
+/* Viscous coupling of a Navier-Stokes mesh (the paper names the compressible
+ * Navier-Stokes solver, not its interface scheme; reading of the local DG
+ * flux).  Along every interface's orientation, whose "-" side is the
+ * element with the lower global index (a boundary's inside is "-"), the
+ * common solution is (1/2 - beta) u- + (1/2 + beta) u+, the viscous common
+ * flux (1/2 + beta) F_v- + (1/2 - beta) F_v+, and the common normal flux
+ * gains tau (u- - u+).  beta = tau = 0 (the default) is BR1; PyFR's LDG
+ * default is beta = 1/2, tau = 0.1.  FR_EINVAL: not Navier-Stokes, beta
+ * outside [-1/2, 1/2], tau negative or not finite, or beta != 0 on a member
+ * of a partition group. */
+int fr_set_viscous_scheme(fr_mesh* mesh, double beta, double tau);
+
 /* Anti-aliasing (Section 3.2, "Anti-aliasing"): for qdeg > 0 the transformed
  * flux is no longer collocated at the solution points.  It is evaluated at
  * the points of a volume quadrature rule exact to degree qdeg (u and, for

@@ -100,6 +100,7 @@ def load():
         "fr_group_rk_step": (I, [P, I, D, I]),
         "fr_profile_step": (I, [P, I, D, P, P]),
         "fr_set_antialias": (I, [P, I]),
+        "fr_set_viscous_scheme": (I, [P, D, D]),
         "fr_set_kernel_variant": (I, [P, I]),
         "fr_get_tuning": (I, [P, C.POINTER(I), P]),
         "fr_set_solution_static": (I, [P, I, P]),
@@ -380,6 +381,11 @@ class FRMesh:
         _check(load().fr_sync(self._h))
 
     _aa_qdeg = 0
+
+    def set_viscous_scheme(self, beta=0.0, tau=0.0):
+        """Viscous coupling: beta = tau = 0 is BR1, (0.5, 0.1) the usual LDG
+        (fr_set_viscous_scheme)."""
+        _check(load().fr_set_viscous_scheme(self._h, float(beta), float(tau)))
 
     def set_antialias(self, qdeg):
         """Anti-aliased flux (Section 3.2): transformed flux projected from a

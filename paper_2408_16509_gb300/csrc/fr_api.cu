@@ -195,6 +195,7 @@ struct fr_mesh {
   long long epoch = 0;            // bumped by every change of launch config
   long long graph_epoch[3] = {-1, -1, -1};
   int aa_qdeg = 0;            // anti-aliasing rule degree (0: collocation)
+  double ldg_beta = 0.0, ldg_tau = 0.0;  // viscous coupling (0, 0: BR1)
   // exchange boundary points (partitioned meshes): receive buffers filled
   // by the group's push kernels, indexed by boundary point
   bool has_exch = false;
@@ -519,6 +520,8 @@ Phys<T> phys(const fr_mesh* m) {
   p.gm1 = T(m->gamma - 1.0);
   p.mu = T(m->mu);
   p.kappa = T(m->mu * m->gamma / m->prandtl);
+  p.beta = T(m->ldg_beta);
+  p.tau = T(m->ldg_tau);
   return p;
 }
 
@@ -914,14 +917,14 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
     if (m->np) {
       PROF_BEGIN(FR_KC_FACE_U);
       k_face_ucommon<T><<<nblk(m->np, tb), tb, 0, s>>>(
-          m->np, m->pl, m->pr, (const T*)m->uf, (T*)m->du, m->tt);
+          m->np, m->pl, m->pr, (const T*)m->uf, (T*)m->du, m->tt, ph.beta);
       PROF_END(FR_KC_FACE_U);
     }
     if (m->nb) {
       PROF_BEGIN(FR_KC_BND_U);
       k_bnd_ucommon<T><<<nblk(m->nb, tb), tb, 0, s>>>(
           m->nb, m->bidx, m->bbc, (const T*)m->uf, (T*)m->du, m->tt, bc,
-          (const T*)m->xu);
+          (const T*)m->xu, ph.beta);
       PROF_END(FR_KC_BND_U);
     }
     for (auto& D : m->types) {
@@ -2452,6 +2455,19 @@ int fr_get_metrics(const fr_mesh* m, int etype, double* smat, double* rcpdjac) {
   return FR_OK;
 }
 
+int fr_set_viscous_scheme(fr_mesh* m, double beta, double tau) {
+  if (!m) return fail(FR_EINVAL, "null argument");
+  if (m->physics != FR_NAVIER_STOKES) return fail(FR_EINVAL, "viscous scheme of a Navier-Stokes mesh only");
+  if (!(beta >= -0.5 && beta <= 0.5) || !(tau >= 0.0) || !std::isfinite(tau))
+    return fail(FR_EINVAL, "beta must lie in [-1/2, 1/2] and tau be finite and >= 0");
+  if (m->in_group && beta != 0.0)
+    return fail(FR_EINVAL, "an LDG bias needs one interface orientation: not across parts");
+  m->ldg_beta = beta;
+  m->ldg_tau = tau;
+  ++m->epoch;  // the constants are kernel arguments captured in the graphs
+  return FR_OK;
+}
+
 int fr_set_antialias(fr_mesh* m, int qdeg) {
   if (!m) return fail(FR_EINVAL, "null argument");
   if (qdeg < 0 || qdeg > 24) return fail(FR_EINVAL, "quadrature degree must be 0..24");
@@ -2556,6 +2572,8 @@ int fr_group_create(fr_mesh* const* meshes, int n, fr_group** out) {
         m->prandtl != a->prandtl || m->periodic != a->periodic)
       return fail(FR_EINVAL, "members differ in device, precision, physics, order or constants");
     if (m->filter_on) return fail(FR_EINVAL, "the entropy filter is not supported in a group");
+    if (m->ldg_beta != 0.0)
+      return fail(FR_EINVAL, "an LDG bias needs one interface orientation: not across parts");
     for (int j = 0; j < i; ++j)
       if (meshes[j] == m) return fail(FR_EINVAL, "a mesh appears twice in the group");
   }

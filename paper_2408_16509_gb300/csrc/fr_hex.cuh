@@ -633,7 +633,8 @@ __global__ void __launch_bounds__(EPB* N* N* N)
       ghost_state(bc, bb, u, ur);
       viscous_normal_acc(ur, G, nv, ph, T(1), q2);
 #pragma unroll
-      for (int k = 0; k < 5; ++k) q[k] = T(0.5) * (q[k] + q2[k]);
+      for (int k = 0; k < 5; ++k)
+        q[k] = (T(0.5) + ph.beta) * q[k] + (T(0.5) - ph.beta) * q2[k];
     }
 #pragma unroll
     for (int k = 0; k < 5; ++k) va.q[(e * 5 + k) * NF + f] = q[k];

@@ -229,8 +229,10 @@ __global__ void k_face_flux(int np, const int32_t* __restrict__ pl,
         gl[j][k] = gf[fp_index(tt, tl, el, fl, 15, j * 5 + k)];
         gr[j][k] = gf[fp_index(tt, tr, er, frr, 15, j * 5 + k)];
       }
-    viscous_normal_acc(ul, gl, n, ph, T(-0.5), F);
-    viscous_normal_acc(ur, gr, n, ph, T(-0.5), F);
+    viscous_normal_acc(ul, gl, n, ph, -(T(0.5) + ph.beta), F);
+    viscous_normal_acc(ur, gr, n, ph, -(T(0.5) - ph.beta), F);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) F[k] += ph.tau * (ul[k] - ur[k]);
   }
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
@@ -298,8 +300,11 @@ __global__ void k_bnd_flux(int nb, const int32_t* __restrict__ bidx,
         g[j][k] = gf[fp_index(tt, t, e, f, 15, j * 5 + k)];
         gr[j][k] = x ? xg[15 * i + j * 5 + k] : g[j][k];
       }
-    viscous_normal_acc(ul, g, n, ph, T(-0.5), F);
-    viscous_normal_acc(ur, gr, n, ph, T(-0.5), F);
+    const T vb = x ? T(0) : ph.beta;  // exchange points: BR1 weights
+    viscous_normal_acc(ul, g, n, ph, -(T(0.5) + vb), F);
+    viscous_normal_acc(ur, gr, n, ph, -(T(0.5) - vb), F);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) F[k] += ph.tau * (ul[k] - ur[k]);
   }
   T m = bn[4 * i + 3];
 #pragma unroll
@@ -307,11 +312,12 @@ __global__ void k_bnd_flux(int nb, const int32_t* __restrict__ bidx,
 }
 
 // NS: common solution u^C = (u- + u+)/2; stores u^C - u_f on both sides.
+// (LDG: u^C = (1/2 - beta) u_L + (1/2 + beta) u_R along the orientation.)
 template <typename T>
 __global__ void k_face_ucommon(int np, const int32_t* __restrict__ pl,
                                const int32_t* __restrict__ pr,
                                const T* __restrict__ uf, T* __restrict__ du,
-                               TypeTab tt) {
+                               TypeTab tt, T beta = T(0)) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= np) return;
   int tl, tr, fl, frr;
@@ -323,9 +329,8 @@ __global__ void k_face_ucommon(int np, const int32_t* __restrict__ pl,
     long long il = fp_index(tt, tl, el, fl, 5, k);
     long long ir = fp_index(tt, tr, er, frr, 5, k);
     T a = uf[il], b = uf[ir];
-    T h = T(0.5) * (b - a);
-    du[il] = h;
-    du[ir] = -h;
+    du[il] = (T(0.5) + beta) * (b - a);
+    du[ir] = -(T(0.5) - beta) * (b - a);
   }
 }
 
@@ -334,7 +339,7 @@ __global__ void k_bnd_ucommon(int nb, const int32_t* __restrict__ bidx,
                               const int32_t* __restrict__ bbc,
                               const T* __restrict__ uf, T* __restrict__ du,
                               TypeTab tt, BCTab<T> bc,
-                              const T* __restrict__ xu = nullptr) {
+                              const T* __restrict__ xu = nullptr, T ph_beta = T(0)) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nb) return;
   int t, f;
@@ -343,10 +348,12 @@ __global__ void k_bnd_ucommon(int nb, const int32_t* __restrict__ bidx,
   T ul[5], ur[5];
 #pragma unroll
   for (int k = 0; k < 5; ++k) ul[k] = uf[fp_index(tt, t, e, f, 5, k)];
-  ghost_state_x(bc, bbc[i], i, xu, ul, ur);
+  const int b = bbc[i];
+  ghost_state_x(bc, b, i, xu, ul, ur);
+  const T w = bc.kind[b] == 2 ? T(0.5) : T(0.5) + ph_beta;
 #pragma unroll
   for (int k = 0; k < 5; ++k)
-    du[fp_index(tt, t, e, f, 5, k)] = T(0.5) * (ur[k] - ul[k]);
+    du[fp_index(tt, t, e, f, 5, k)] = w * (ur[k] - ul[k]);
 }
 
 // ---------------------------------------------------------------------------
@@ -393,7 +400,8 @@ __device__ __forceinline__ void write_visc_q(const ViscArgs<T>& va,
     }
     viscous_normal_acc(ur, G, nv, ph, T(1), q2);
 #pragma unroll
-    for (int k = 0; k < 5; ++k) q[k] = T(0.5) * (q[k] + q2[k]);
+    for (int k = 0; k < 5; ++k)
+      q[k] = (T(0.5) + ph.beta) * q[k] + (T(0.5) - ph.beta) * q2[k];
   }
 #pragma unroll
   for (int k = 0; k < 5; ++k) va.q[(e * 5 + k) * nf + f] = q[k];
@@ -420,7 +428,8 @@ __device__ __forceinline__ void visc_q_pre(const BCTab<T>& bc, const Phys<T>& ph
     }
     viscous_normal_acc(ur, G, nv, ph, T(1), q2);
 #pragma unroll
-    for (int k = 0; k < 5; ++k) q[k] = T(0.5) * (q[k] + q2[k]);
+    for (int k = 0; k < 5; ++k)
+      q[k] = (T(0.5) + ph.beta) * q[k] + (T(0.5) - ph.beta) * q2[k];
   }
 }
 
@@ -456,10 +465,12 @@ __global__ void k_face_flux_ns(int np, const int32_t* __restrict__ pl,
   T F[5];
   rusanov(ul, ur, n, ph, F);
   const T rl = ml / mr, rr = mr / ml;
+  const T wl = T(0.5) + ph.beta, wr = T(0.5) - ph.beta;
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
-    fc[fp_index(tt, tl, el, fl, 5, k)] = ml * F[k] - T(0.5) * (ql[k] - rl * qr[k]);
-    fc[fp_index(tt, tr, er, frr, 5, k)] = -mr * F[k] + T(0.5) * (rr * ql[k] - qr[k]);
+    const T G = F[k] + ph.tau * (ul[k] - ur[k]);
+    fc[fp_index(tt, tl, el, fl, 5, k)] = ml * G - (wl * ql[k] - wr * rl * qr[k]);
+    fc[fp_index(tt, tr, er, frr, 5, k)] = -mr * G + (wl * rr * ql[k] - wr * qr[k]);
   }
 }
 
@@ -494,14 +505,14 @@ __global__ void k_bnd_flux_ns(int nb, const int32_t* __restrict__ bidx,
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
       long long ix = fp_index(tt, t, e, f, 5, k);
-      fc[ix] = m * F[k] - T(0.5) * (q[ix] - rl * xq[5 * i + k]);
+      fc[ix] = m * (F[k] + ph.tau * (ul[k] - ur[k])) - T(0.5) * (q[ix] - rl * xq[5 * i + k]);
     }
     return;
   }
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
     long long ix = fp_index(tt, t, e, f, 5, k);
-    fc[ix] = m * F[k] - q[ix];
+    fc[ix] = m * (F[k] + ph.tau * (ul[k] - ur[k])) - q[ix];
   }
 }
 

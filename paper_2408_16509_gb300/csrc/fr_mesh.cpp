@@ -571,7 +571,21 @@ std::string build_mesh(const MeshInput& in, std::vector<HostType>& types,
     double n[4], mr;
   };
   std::vector<PairRec> prs;
-  for (auto& fp : fpairs) {
+  std::vector<int64_t> eoff(types.size(), 0);
+  for (size_t t = 1; t < types.size(); ++t) eoff[t] = eoff[t - 1] + types[t - 1].ne;
+  for (auto& fp0 : fpairs) {
+    // orientation: the "-" (left) side is the element with the lower global
+    // index, the lower face for an element paired with itself
+    FacePair fp = fp0;
+    {
+      const FaceRec& a = faces[fp.a];
+      const FaceRec& b = faces[fp.b];
+      const int64_t ga = eoff[a.t] + a.e, gb = eoff[b.t] + b.e;
+      if (gb < ga || (gb == ga && b.f < a.f)) {
+        std::swap(fp.a, fp.b);
+        for (int k = 0; k < 3; ++k) fp.T[k] = -fp.T[k];
+      }
+    }
     const FaceRec& A = faces[fp.a];
     const FaceRec& B = faces[fp.b];
     const HostType& TA = types[A.t];

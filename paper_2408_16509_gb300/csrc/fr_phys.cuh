@@ -17,9 +17,11 @@
 
 namespace frgb {
 
+// beta, tau: LDG bias and penalty of the viscous coupling (0, 0: BR1)
 template <typename T>
 struct Phys {
   T gamma, gm1, mu, kappa;
+  T beta = T(0), tau = T(0);
 };
 
 template <typename T>
