@@ -281,6 +281,11 @@ int fr_get_adjacency(const fr_mesh* mesh, int etype, int64_t* nbr);
  * fr_get_pairs): physical position x [n][3] and condition kind [n]
  * (FR_BC_*); either pointer may be null. */
 int fr_get_boundary_points(const fr_mesh* mesh, double* x, int* kind);
+/* Interior flux-point pairs in the library's order (count: n_interior of
+ * fr_get_pairs): global element index of the "-" (left) and "+" (right)
+ * side of each; left <= right by the orientation rule of
+ * fr_set_viscous_scheme.  Either pointer may be null. */
+int fr_get_interfaces(const fr_mesh* mesh, int64_t* left, int64_t* right);
 int fr_partition(const fr_mesh* mesh, int nparts, int mode, const double* weights,
                  int32_t* part);
 int fr_partition_faces(const fr_mesh* mesh, const int32_t* part, int rank,

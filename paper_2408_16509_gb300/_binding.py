@@ -92,6 +92,7 @@ def load():
         "fr_get_pairs": (I, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "fr_get_adjacency": (I, [P, I, P]),
         "fr_get_boundary_points": (I, [P, P, P]),
+        "fr_get_interfaces": (I, [P, P, P]),
         "fr_partition": (I, [P, I, I, P, P]),
         "fr_partition_faces": (I, [P, P, I, P, C.POINTER(C.c_int64)]),
         "fr_group_create": (I, [P, I, C.POINTER(C.c_void_p)]),
@@ -429,6 +430,15 @@ class FRMesh:
         k = np.empty(nb, np.int32)
         _check(load().fr_get_boundary_points(self._h, _ptr(x), _ptr(k)))
         return x, k
+
+    def interfaces(self):
+        """(left, right) global element indices of every interior flux-point
+        pair (fr_get_interfaces)."""
+        n, _ = self.pair_counts()
+        a = np.empty(n, np.int64)
+        b = np.empty(n, np.int64)
+        _check(load().fr_get_interfaces(self._h, _ptr(a), _ptr(b)))
+        return a, b
 
     def n_elements(self):
         return sum(self.info(t)[0] for t in self.types)

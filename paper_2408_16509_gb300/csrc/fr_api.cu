@@ -2507,6 +2507,22 @@ int fr_get_boundary_points(const fr_mesh* m, double* x, int* kind) {
   return FR_OK;
 }
 
+int fr_get_interfaces(const fr_mesh* m, int64_t* left, int64_t* right) {
+  if (!m) return fail(FR_EINVAL, "null argument");
+  std::vector<int64_t> eoff(m->host.size(), 0);
+  for (size_t t = 1; t < m->host.size(); ++t) eoff[t] = eoff[t - 1] + m->host[t - 1].ne;
+  auto elem = [&](int32_t code) {
+    const int t = code >> 29;
+    const int64_t rem = code & ((int64_t(1) << 29) - 1);
+    return eoff[t] + rem / (5 * m->host[t].ref.nfpts);
+  };
+  for (size_t i = 0; i < m->conn.pl.size(); ++i) {
+    if (left) left[i] = elem(m->conn.pl[i]);
+    if (right) right[i] = elem(m->conn.pr[i]);
+  }
+  return FR_OK;
+}
+
 int fr_get_adjacency(const fr_mesh* m, int etype, int64_t* nbr) {
   if (!m || !nbr) return fail(FR_EINVAL, "null argument");
   const HostType* H = host_ptr(m, etype);

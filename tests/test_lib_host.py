@@ -166,3 +166,33 @@ def test_antialias_operators_match_oracle(name, p):
     g.set_antialias(0)
     with pytest.raises(fr.FRError):
         g.operator(g.types[0], "aa_B")
+
+
+@pytest.mark.parametrize("name", ["hex", "mixed", "curved"])
+def test_interface_orientation_matches_oracle(name):
+    """The library orients every interface by the rule the oracle applies
+    independently (lower global element on the "-" side): the multisets of
+    (left element, right element) pairs agree."""
+    spec = SPECS[name]()
+    bcs = {k: ("extrap",) for k in range(6)}
+    g = fr.FRMesh(spec, 2, bcs=bcs, device=-1)
+    o = OracleMesh(spec.as_dict(), 2)
+    left, right = g.interfaces()
+    assert np.all(left <= right)
+    eoff, n = {}, 0
+    for t in o.types:
+        eoff[t] = n
+        n += o.ne[t]
+
+    def elem(gidx):
+        out = np.empty(len(gidx), np.int64)
+        for t in o.types:
+            lo = o.foff[t]
+            hi = lo + o.ne[t] * o.el[t].nfpts
+            sel = (gidx >= lo) & (gidx < hi)
+            out[sel] = eoff[t] + (gidx[sel] - lo) // o.el[t].nfpts
+        return out
+    ol, orr = elem(o.pair_l), elem(o.pair_r)
+    lib = sorted(zip(left.tolist(), right.tolist()))
+    ora = sorted(zip(ol.tolist(), orr.tolist()))
+    assert lib == ora

@@ -205,3 +205,12 @@ def test_groups_refuse_host_only_members():
     with pytest.raises(fr.FRError) as e:
         fr.FRGroup(parts)
     assert e.value.name == "FR_EINVAL"
+
+
+def test_one_part_has_no_exchange_faces():
+    spec = mixed_box(n=3, x_pri=0.34, x_tet=0.67)
+    subs, ids, part = partition.split(spec, 1)
+    assert np.all(part == 0) and len(subs) == 1
+    g = fr.FRMesh(subs[0], 2, bcs=partition.exchange_bcs(MIXED_BCS), device=-1)
+    _, kind = g.boundary_points()
+    assert not np.any(kind == 2)
