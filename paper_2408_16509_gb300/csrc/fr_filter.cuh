@@ -309,7 +309,7 @@ __device__ __forceinline__ float silu_f(float x) { return x / (1.0f + __expf(-x)
 
 // Predictor evaluated by warp 0 (lane j = hidden unit j); returns z0 on
 // lane 0.
-__device__ float mlp_guess(const float feat[4], const __nv_bfloat16* w,
+static __device__ float mlp_guess(const float feat[4], const __nv_bfloat16* w,
                            const float* norm) {
   const int j = threadIdx.x & 31;
   float xn[4];
@@ -676,7 +676,7 @@ __device__ __forceinline__ float dsilu_f(float x) {
 // per sample: xn[4], h1[32], h2[32], da1[32], da2[32], do, loss term
 constexpr int kMlpScratch = 4 + 32 * 4 + 2;
 
-__global__ void k_mlp_sample(int n, const float* __restrict__ w,
+static __global__ void k_mlp_sample(int n, const float* __restrict__ w,
                              const float* __restrict__ x,
                              const float* __restrict__ zstar,
                              float* __restrict__ scr) {
@@ -720,7 +720,7 @@ __global__ void k_mlp_sample(int n, const float* __restrict__ w,
 
 // one thread per trainable parameter (and one for the loss), summing over
 // samples in order
-__global__ void k_mlp_reduce(int n, const float* __restrict__ scr,
+static __global__ void k_mlp_reduce(int n, const float* __restrict__ scr,
                              float* __restrict__ grad, float* __restrict__ loss) {
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q > kMlpTrain) return;
@@ -743,7 +743,7 @@ __global__ void k_mlp_reduce(int n, const float* __restrict__ scr,
   else grad[q] = float(acc);
 }
 
-__global__ void k_mlp_adam(float* __restrict__ w, const float* __restrict__ grad,
+static __global__ void k_mlp_adam(float* __restrict__ w, const float* __restrict__ grad,
                            float* __restrict__ m1, float* __restrict__ m2,
                            int step, float lr) {
   int q = blockIdx.x * blockDim.x + threadIdx.x;

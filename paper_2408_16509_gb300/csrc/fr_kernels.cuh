@@ -58,9 +58,23 @@ struct StageArgs {
   T* E = nullptr;    // embedded-error register of an adaptive step (or nullptr)
 };
 
-__constant__ double c_rk45_a[4];  // sub-diagonal a_{i+1,i}
-__constant__ double c_rk45_b[5];
-__constant__ double c_rk45_e[5];  // b_i - bhat_i (embedded pair)
+// RK4(3)5[2R+]C of Kennedy, Carpenter & Lewis (2000): the sub-diagonal
+// a_{i+1,i} of the two-register scheme, the weights b and b - bhat with the
+// embedded third-order weights bhat of the same publication.  Statically
+// initialised: every translation unit holds its own copy.
+static __constant__ double c_rk45_a[4] = {
+    970286171893.0 / 4311952581923.0, 6584761158862.0 / 12103376702013.0,
+    2251764453980.0 / 15575788980749.0, 26877169314380.0 / 34165994151039.0};
+static __constant__ double c_rk45_b[5] = {
+    1153189308089.0 / 22510343858157.0, 1772645290293.0 / 4653164025191.0,
+    -1672844663538.0 / 4480602732383.0, 2114624349019.0 / 3568978502595.0,
+    5198255086312.0 / 14908931495163.0};
+static __constant__ double c_rk45_e[5] = {
+    1153189308089.0 / 22510343858157.0 - 1016888040809.0 / 7410784769900.0,
+    1772645290293.0 / 4653164025191.0 - 11231460423587.0 / 58533540763752.0,
+    -1672844663538.0 / 4480602732383.0 + 1563879915014.0 / 6823010717585.0,
+    2114624349019.0 / 3568978502595.0 - 606302364029.0 / 971179775848.0,
+    5198255086312.0 / 14908931495163.0 - 1097981568119.0 / 3980877426909.0};
 
 __device__ __forceinline__ void decode_fp(int32_t code, const TypeTab& tt,
                                           int* t, long long* e, int* f) {
