@@ -48,6 +48,23 @@ def taylor_green(x, mach=0.1, gamma=1.4):
     return _cons(rho, u, v, np.zeros_like(u), p, gamma)
 
 
+def flow3d(x, mach=0.3, gamma=1.4):
+    """Smooth, fully three-dimensional state, periodic on the unit box: the
+    Taylor-Green velocity of X = 2 pi x plus w = sin(X + 0.3) cos Y
+    sin(Z + 0.7) / 2, density 1 + sin(X + Y) cos Z / 10 and pressure
+    p0 (1 + cos X cos(Y + Z) / 20), p0 = 1 / (gamma Ma^2).  Every conserved
+    variable varies in all three directions, so no component of a
+    right-hand side vanishes by symmetry."""
+    p0 = 1.0 / (gamma * mach ** 2)
+    X, Y, Z = (2 * np.pi * x[:, k] for k in range(3))
+    u = np.sin(X) * np.cos(Y) * np.cos(Z)
+    v = -np.cos(X) * np.sin(Y) * np.cos(Z)
+    w = 0.5 * np.sin(X + 0.3) * np.cos(Y) * np.sin(Z + 0.7)
+    rho = 1.0 + 0.1 * np.sin(X + Y) * np.cos(Z)
+    p = p0 * (1.0 + 0.05 * np.cos(X) * np.cos(Y + Z))
+    return _cons(rho, u, v, w, p, gamma)
+
+
 def perturbed_uniform(x, mach=0.2, gamma=1.4, amp=0.05, nmodes=4, kmax=3,
                       seed=20240829):
     """rho = 1, p = 1/(gamma Ma^2), velocity (1,0,0) plus ``amp`` times the

@@ -149,16 +149,31 @@ int fr_get_solution(const fr_mesh* mesh, int etype, double* u);
  * Synchronous: returns after the copy and the layout kernel completed. */
 int fr_set_solution_static(fr_mesh* mesh, int etype, const double* u);
 
-/* Same from / to device memory in the host layout (FP64), on the handle's
- * stream; the pointer must stay valid until the stream reaches the copy. */
-int fr_set_solution_device(fr_mesh* mesh, int etype, const void* dptr);
-int fr_get_solution_device(const fr_mesh* mesh, int etype, void* dptr);
+/* Element type of a caller's device array (fr_set_solution_device,
+ * fr_get_solution_device). */
+enum { FR_DTYPE_F64 = 0, FR_DTYPE_F32 = 1 };
 
-/* One evaluation of the right-hand side du/dt = -J^{-1} div~ f~ (Section 2,
- * Eqs. disu, comm_flux, FRfinal) at the current solution.  The result stays
- * on the device; fr_get_rhs copies it out in the host layout.
+/* Same from / to device memory (e.g. a torch tensor's data pointer) in the
+ * host layout [n_elem][nupts][5], element type `dtype` (FR_DTYPE_F64 or
+ * FR_DTYPE_F32; values are converted to the handle's register precision),
+ * on the handle's stream: asynchronous, the pointer must stay valid until
+ * the stream reaches the copy (fr_sync).  FR_EINVAL for another dtype. */
+int fr_set_solution_device(fr_mesh* mesh, int etype, const void* dptr, int dtype);
+int fr_get_solution_device(const fr_mesh* mesh, int etype, void* dptr, int dtype);
+
+/* One evaluation of the right-hand side du/dt = -J^{-1} div~ f~ (Section 2:
+ * Eq. disu, interpolation to the flux points; Eq. comm_flux, the common
+ * interface flux; Eq. FRfinal, the corrected divergence) at the current
+ * solution, for time t.  The boundary conditions of this library do not
+ * depend on time, so t only labels the evaluation (fr_stats reports it);
+ * t must be finite.  Outputs, either or both may be NULL:
+ *   rhs_host: host FP64, all element types in mesh order (hexahedra,
+ *             prisms, tetrahedra present), each [n_elem][nupts][5]
+ *             concatenated; filled before the call returns;
+ *   rhs_dev:  device FP64, same layout; written on the handle's stream.
+ * The result also stays on the device for fr_get_rhs (host, one type).
  * FR_ENONFINITE when any entry is NaN or Inf. */
-int fr_rhs(fr_mesh* mesh);
+int fr_rhs(fr_mesh* mesh, double t, double* rhs_host, void* rhs_dev);
 int fr_get_rhs(const fr_mesh* mesh, int etype, double* rhs);
 
 /* Advance the solution by `nsteps` explicit steps of size dt (Section 2,
@@ -204,6 +219,34 @@ enum { FR_KC_FACE_U = 0,  /* NS common solution at interior flux points */
        FR_KC_COUNT = 8 };
 int fr_profile_step(fr_mesh* mesh, int scheme, double dt, double* ms,
                     int* launches);
+
+/* Counters and timings of a handle (Section 3.1, "Task graphs": what a
+ * step costs; Section 3.2, "Entropy filtering": how many elements were
+ * filtered and how many margin evaluations the iterative strength search
+ * took).  ms_device sums the device time of fr_rhs, fr_rk_step and
+ * fr_rk_adaptive_step calls (a pair of CUDA events around each on the
+ * handle's stream; none while that stream is being captured); ms_kernel and
+ * launches are those of the last fr_profile_step.  fr_stats waits for the
+ * timed calls still in flight.  reset != 0 zeroes the counters, the device
+ * time and the filter counters after reading them.  Works on host-only
+ * handles (all zero). */
+typedef struct {
+  uint64_t rhs_calls;        /* fr_rhs evaluations */
+  uint64_t rk_steps;         /* fixed-size RK steps (fr_rk_step, fr_profile_step) */
+  uint64_t rk_attempts;      /* adaptive attempts (fr_rk_adaptive_step) */
+  uint64_t rk_rejected;      /*   of which rejected */
+  uint64_t stages;           /* right-hand-side evaluations of all of these */
+  uint64_t filtered;         /* entropy filter: filtered element-stages */
+  uint64_t filter_evals;     /*   margin evaluations (root-find iterations) */
+  uint64_t filter_fallbacks; /*   elements left infeasible at zeta = 36 */
+  uint64_t predictor_used;   /*   element-stages opened from the predictor */
+  double ms_device;          /* device milliseconds of the timed calls */
+  double ms_kernel[FR_KC_COUNT];  /* last fr_profile_step, per kernel class */
+  int launches[FR_KC_COUNT];
+  int kernel_family;         /* FR_VARIANT_* in use */
+  double t_last;             /* t of the last fr_rhs */
+} fr_stats_t;
+int fr_stats(fr_mesh* mesh, fr_stats_t* out, int reset);
 
 /* Kernel family.  For hexahedra: FR_VARIANT_SUMFACT applies the operators
  * line by line (1D factors of the tensor-product basis) with metric terms
@@ -257,7 +300,7 @@ enum { FR_OP_M0 = 0, FR_OP_D = 1, FR_OP_LIFT = 2, FR_OP_WEIGHTS = 3,
 int fr_get_operator(const fr_mesh* mesh, int etype, int which, double* out);
 
 /* ---------------------------------------------------------------------------
- * Domain decomposition (Section 4, "Mixed Elements and Domain Decomposition").
+ * Domain decomposition (Section 3.3, "Mixed Elements and Domain Decomposition").
  * Elements carry a global index: the element types in the order hexahedra,
  * prisms, tetrahedra (those present), then the element number.  All three
  * calls work on host-only handles.
@@ -291,7 +334,7 @@ int fr_partition(const fr_mesh* mesh, int nparts, int mode, const double* weight
 int fr_partition_faces(const fr_mesh* mesh, const int32_t* part, int rank,
                        int64_t* faces, int64_t* count);
 
-/* Partition groups (the exchange between partitions of Section 3,
+/* Partition groups (the exchange between partitions of Section 3.1,
  * "Multi-node capabilities", here between the parts of a mesh on one
  * device): the parts of one mesh (each created from its elements,
  * with its faces towards other parts as FR_BC_EXCHANGE boundary faces) run

@@ -21,6 +21,9 @@ VARIANTS = {"auto": 0, "dense": 1, "sumfact": 2, "sumfact_vertex": 3,
             "tensor": 4}
 SCHEMES = {"rk4": 0, "rk45": 1}
 BC_KIND = {"state": 0, "extrap": 1, "exchange": 2}
+VARIANT_NAMES = {v: k for k, v in VARIANTS.items()}
+FR_DTYPE_F64, FR_DTYPE_F32 = 0, 1
+FR_KC_COUNT = 8
 
 
 class FRError(RuntimeError):
@@ -77,9 +80,10 @@ def load():
         "fr_get_points": (I, [P, I, P]),
         "fr_set_solution": (I, [P, I, P]),
         "fr_get_solution": (I, [P, I, P]),
-        "fr_set_solution_device": (I, [P, I, P]),
-        "fr_get_solution_device": (I, [P, I, P]),
-        "fr_rhs": (I, [P]),
+        "fr_set_solution_device": (I, [P, I, P, I]),
+        "fr_get_solution_device": (I, [P, I, P, I]),
+        "fr_rhs": (I, [P, D, P, P]),
+        "fr_stats": (I, [P, C.POINTER(Stats), I]),
         "fr_get_rhs": (I, [P, I, P]),
         "fr_rk_step": (I, [P, I, D, I]),
         "fr_rk_adaptive_step": (I, [P, C.POINTER(AdaptCtl), C.POINTER(D),
@@ -125,6 +129,18 @@ def load():
 def _check(rc):
     if rc != FR_OK:
         raise FRError(rc, load().fr_last_error().decode())
+
+
+class Stats(C.Structure):
+    """fr_stats_t."""
+    _fields_ = [("rhs_calls", C.c_uint64), ("rk_steps", C.c_uint64),
+                ("rk_attempts", C.c_uint64), ("rk_rejected", C.c_uint64),
+                ("stages", C.c_uint64), ("filtered", C.c_uint64),
+                ("filter_evals", C.c_uint64), ("filter_fallbacks", C.c_uint64),
+                ("predictor_used", C.c_uint64), ("ms_device", C.c_double),
+                ("ms_kernel", C.c_double * FR_KC_COUNT),
+                ("launches", C.c_int * FR_KC_COUNT),
+                ("kernel_family", C.c_int), ("t_last", C.c_double)]
 
 
 class AdaptCtl(C.Structure):
@@ -249,19 +265,37 @@ class FRMesh:
             out[t] = a
         return out
 
+    @staticmethod
+    def _dtype(tensor):
+        name = str(tensor.dtype)
+        if name.endswith("float64"):
+            return FR_DTYPE_F64
+        if name.endswith("float32"):
+            return FR_DTYPE_F32
+        raise ValueError(f"unsupported dtype {tensor.dtype} (float64 or float32)")
+
     def set_solution_device(self, etype, tensor):
-        """tensor: CUDA float64 contiguous (n_elem, nupts, 5)."""
+        """tensor: CUDA float64 or float32 contiguous (n_elem, nupts, 5)."""
         _check(load().fr_set_solution_device(self._h, ETYPES[etype],
-                                             C.c_void_p(tensor.data_ptr())))
+                                             C.c_void_p(tensor.data_ptr()),
+                                             self._dtype(tensor)))
 
     def get_solution_device(self, etype, tensor):
         _check(load().fr_get_solution_device(self._h, ETYPES[etype],
-                                             C.c_void_p(tensor.data_ptr())))
+                                             C.c_void_p(tensor.data_ptr()),
+                                             self._dtype(tensor)))
 
-    def rhs(self):
-        """One right-hand-side evaluation at the current solution."""
-        _check(load().fr_rhs(self._h))
-        return self.get_rhs()
+    def rhs(self, t=0.0):
+        """One right-hand-side evaluation at the current solution (fr_rhs
+        with a host output): {etype: (n_elem, nupts, 5) float64}."""
+        sizes = [(tp,) + self.info(tp)[:2] for tp in self.types]
+        flat = np.empty(sum(ne * nu * 5 for _, ne, nu in sizes), np.float64)
+        _check(load().fr_rhs(self._h, float(t), _ptr(flat), None))
+        out, off = {}, 0
+        for tp, ne, nu in sizes:
+            out[tp] = flat[off:off + ne * nu * 5].reshape(ne, nu, 5)
+            off += ne * nu * 5
+        return out
 
     def get_rhs(self):
         """The last right-hand side (fr_get_rhs)."""
@@ -273,9 +307,28 @@ class FRMesh:
             out[t] = a
         return out
 
-    def rhs_device(self):
-        """Right-hand side left on the device (no copy back)."""
-        _check(load().fr_rhs(self._h))
+    def rhs_device(self, t=0.0, out=None):
+        """Right-hand side on the device: into `out` (a CUDA float64 tensor of
+        all types' [n_elem][nupts][5] blocks in mesh order) when given, else
+        left in the library's own buffers."""
+        dev = None if out is None else C.c_void_p(out.data_ptr())
+        _check(load().fr_rhs(self._h, float(t), None, dev))
+
+    def stats(self, reset=False):
+        """Counters and timings (fr_stats) as a dict."""
+        st = Stats()
+        _check(load().fr_stats(self._h, C.byref(st), int(bool(reset))))
+        names = self.KERNEL_CLASSES
+        return {"rhs_calls": st.rhs_calls, "rk_steps": st.rk_steps,
+                "rk_attempts": st.rk_attempts, "rk_rejected": st.rk_rejected,
+                "stages": st.stages, "filtered": st.filtered,
+                "filter_evals": st.filter_evals,
+                "filter_fallbacks": st.filter_fallbacks,
+                "predictor_used": st.predictor_used, "ms_device": st.ms_device,
+                "kernel_ms": {n: st.ms_kernel[k] for k, n in enumerate(names)},
+                "launches": {n: st.launches[k] for k, n in enumerate(names)},
+                "kernel_family": VARIANT_NAMES.get(st.kernel_family, st.kernel_family),
+                "t_last": st.t_last}
 
     def rk_step(self, scheme, dt, nsteps=1):
         _check(load().fr_rk_step(self._h, SCHEMES[scheme], float(dt),

@@ -2,6 +2,9 @@
 // the precision tables (fr_prec_*.cu).  See include/frgb.h.
 #include "fr_impl.cuh"
 
+#include <cmath>
+#include <cstring>
+
 using namespace frgb;
 
 #define FR_PREC(m, fn, ...) (prec_table((m)->precision).fn(__VA_ARGS__))
@@ -266,31 +269,131 @@ int fr_get_rhs(const fr_mesh* m, int etype, double* r) {
   return get_host(m, etype, r, true);
 }
 
-int fr_set_solution_device(fr_mesh* m, int etype, const void* dptr) {
+int fr_set_solution_device(fr_mesh* m, int etype, const void* dptr, int dtype) {
   if (!m || !dptr) return fail(FR_EINVAL, "null argument");
+  if (dtype != FR_DTYPE_F64 && dtype != FR_DTYPE_F32) return fail(FR_EINVAL, "unknown dtype");
   DevType* D = type_ptr(m, etype);
   if (!D) return fail(FR_EINVAL, "mesh has no elements of this type");
   CK(cudaSetDevice(m->device));
-  return m->rsize == 8 ? set_solution_dev<double>(m, *D, (const double*)dptr)
-                       : set_solution_dev<float>(m, *D, (const double*)dptr);
+  if (dtype == FR_DTYPE_F64)
+    return m->rsize == 8 ? set_solution_dev<double>(m, *D, (const double*)dptr)
+                         : set_solution_dev<float>(m, *D, (const double*)dptr);
+  return m->rsize == 8 ? set_solution_dev<double, float>(m, *D, (const float*)dptr)
+                       : set_solution_dev<float, float>(m, *D, (const float*)dptr);
 }
 
-int fr_get_solution_device(const fr_mesh* mc, int etype, void* dptr) {
+int fr_get_solution_device(const fr_mesh* mc, int etype, void* dptr, int dtype) {
   fr_mesh* m = const_cast<fr_mesh*>(mc);
   if (!m || !dptr) return fail(FR_EINVAL, "null argument");
+  if (dtype != FR_DTYPE_F64 && dtype != FR_DTYPE_F32) return fail(FR_EINVAL, "unknown dtype");
   DevType* D = type_ptr(m, etype);
   if (!D) return fail(FR_EINVAL, "mesh has no elements of this type");
   CK(cudaSetDevice(m->device));
-  return m->rsize == 8 ? get_dev<double>(m, *D, D->X, (double*)dptr)
-                       : get_dev<float>(m, *D, D->X, (double*)dptr);
+  if (dtype == FR_DTYPE_F64)
+    return m->rsize == 8 ? get_dev<double>(m, *D, D->X, (double*)dptr)
+                         : get_dev<float>(m, *D, D->X, (double*)dptr);
+  return m->rsize == 8 ? get_dev<double, float>(m, *D, D->X, (float*)dptr)
+                       : get_dev<float, float>(m, *D, D->X, (float*)dptr);
 }
 
-int fr_rhs(fr_mesh* m) {
+}  // extern "C"
+
+namespace {
+
+// Device time of the timed calls: a pair of events around each, kept in a
+// ring and folded into ms_device once the second event has completed (the
+// oldest pair is waited for only when the ring is full).  Nothing is
+// recorded on a stream that is being captured into a graph.
+bool stats_capturing(fr_mesh* m) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(m->stream, &cs) != cudaSuccess ||
+         cs != cudaStreamCaptureStatusNone;
+}
+
+int stats_harvest(fr_mesh* m, bool wait_all) {
+  while (m->ev_count > 0) {
+    int i = (m->ev_head - m->ev_count + fr_mesh::kEvRing) % fr_mesh::kEvRing;
+    if (!wait_all && m->ev_count < fr_mesh::kEvRing) {
+      cudaError_t q = cudaEventQuery(m->ev_b[i]);
+      if (q == cudaErrorNotReady) break;
+      CK(q);
+    } else {
+      CK(cudaEventSynchronize(m->ev_b[i]));
+    }
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, m->ev_a[i], m->ev_b[i]));
+    m->ms_device += ms;
+    --m->ev_count;
+  }
+  return FR_OK;
+}
+
+// Records the opening event of a timed call; returns the ring slot or -1.
+int stats_begin(fr_mesh* m) {
+  if (stats_capturing(m)) return -1;
+  if (stats_harvest(m, false)) return -1;
+  if (m->ev_count == fr_mesh::kEvRing && stats_harvest(m, false)) return -1;
+  int i = m->ev_head;
+  if (!m->ev_a[i] && (cudaEventCreate(&m->ev_a[i]) != cudaSuccess ||
+                      cudaEventCreate(&m->ev_b[i]) != cudaSuccess))
+    return -1;
+  if (cudaEventRecord(m->ev_a[i], m->stream) != cudaSuccess) return -1;
+  return i;
+}
+
+void stats_end(fr_mesh* m, int slot) {
+  if (slot < 0) return;
+  if (cudaEventRecord(m->ev_b[slot], m->stream) != cudaSuccess) return;
+  m->ev_head = (m->ev_head + 1) % fr_mesh::kEvRing;
+  ++m->ev_count;
+}
+
+int stages_of(int scheme) { return scheme == FR_RK4 ? 4 : 5; }
+
+}  // namespace
+
+extern "C" {
+
+int fr_rhs(fr_mesh* m, double t, double* rhs_host, void* rhs_dev) {
   if (!m) return fail(FR_EINVAL, "null mesh");
   if (m->host_only) return fail(FR_EINVAL, "host-only handle (device < 0)");
   if (m->has_exch) return fail(FR_EINVAL, "mesh has exchange faces: run it in a group");
+  if (!std::isfinite(t)) return fail(FR_EINVAL, "time is not finite");
   CK(cudaSetDevice(m->device));
-  return FR_PREC(m, do_rhs, m);
+  int slot = stats_begin(m);
+  int rc = FR_PREC(m, do_rhs, m);
+  stats_end(m, slot);
+  if (rc) return rc;
+  m->t_last = t;
+  ++m->n_rhs;
+  ++m->n_stages;
+  if (!rhs_host && !rhs_dev) return FR_OK;
+  size_t total = 0;
+  for (auto& D : m->types) total += size_t(D.ne) * 5 * D.nu;
+  // device output, then host output through the staging buffer; both in
+  // the host layout, element types in mesh order
+  double* outs[2] = {static_cast<double*>(rhs_dev), nullptr};
+  if (rhs_host) {
+    rc = ensure_staging(m, total * sizeof(double));
+    if (rc) return rc;
+    outs[1] = static_cast<double*>(m->d_staging);
+  }
+  for (double* base : outs) {
+    if (!base) continue;
+    size_t off = 0;
+    for (auto& D : m->types) {
+      rc = m->wsize == 8 ? get_dev<double>(m, D, D.R, base + off)
+                         : get_dev<float>(m, D, D.R, base + off);
+      if (rc) return rc;
+      off += size_t(D.ne) * 5 * D.nu;
+    }
+  }
+  if (rhs_host) {
+    CK(cudaMemcpyAsync(rhs_host, m->d_staging, total * sizeof(double),
+                       cudaMemcpyDeviceToHost, m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+  }
+  return FR_OK;
 }
 
 int fr_rk_step(fr_mesh* m, int scheme, double dt, int nsteps) {
@@ -301,7 +404,13 @@ int fr_rk_step(fr_mesh* m, int scheme, double dt, int nsteps) {
   if (m->has_exch) return fail(FR_EINVAL, "mesh has exchange faces: run it in a group");
   if (nsteps == 0) return FR_OK;
   CK(cudaSetDevice(m->device));
-  return FR_PREC(m, do_rk, m, scheme, dt, nsteps);
+  int slot = stats_begin(m);
+  int rc = FR_PREC(m, do_rk, m, scheme, dt, nsteps);
+  stats_end(m, slot);
+  if (rc) return rc;
+  m->n_steps += (unsigned long long)nsteps;
+  m->n_stages += (unsigned long long)nsteps * stages_of(scheme);
+  return FR_OK;
 }
 
 int fr_rk_adaptive_step(fr_mesh* m, fr_adapt_t* ctl, double* dt, int* accepted,
@@ -310,7 +419,14 @@ int fr_rk_adaptive_step(fr_mesh* m, fr_adapt_t* ctl, double* dt, int* accepted,
   if (m->host_only) return fail(FR_EINVAL, "host-only handle (device < 0)");
   if (m->has_exch) return fail(FR_EINVAL, "mesh has exchange faces: run it in a group");
   CK(cudaSetDevice(m->device));
-  return FR_PREC(m, do_rk_adaptive, m, ctl, dt, accepted, err);
+  int slot = stats_begin(m);
+  int rc = FR_PREC(m, do_rk_adaptive, m, ctl, dt, accepted, err);
+  stats_end(m, slot);
+  if (rc) return rc;
+  ++m->n_attempts;
+  m->n_rejected += *accepted ? 0 : 1;
+  m->n_stages += 5;
+  return FR_OK;
 }
 
 int fr_profile_step(fr_mesh* m, int scheme, double dt, double* ms,
@@ -320,7 +436,55 @@ int fr_profile_step(fr_mesh* m, int scheme, double dt, double* ms,
   if (m->has_exch) return fail(FR_EINVAL, "mesh has exchange faces: run it in a group");
   if (scheme != FR_RK4 && scheme != FR_RK45) return fail(FR_EINVAL, "unknown scheme");
   CK(cudaSetDevice(m->device));
-  return FR_PREC(m, do_profile, m, scheme, dt, ms, launches);
+  int rc = FR_PREC(m, do_profile, m, scheme, dt, ms, launches);
+  if (rc) return rc;
+  for (int k = 0; k < FR_KC_COUNT; ++k) {
+    m->prof_ms[k] = ms[k];
+    m->prof_launches[k] = launches[k];
+  }
+  m->n_steps += 1;
+  m->n_stages += stages_of(scheme);
+  return FR_OK;
+}
+
+int fr_stats(fr_mesh* m, fr_stats_t* out, int reset) {
+  if (!m || !out) return fail(FR_EINVAL, "null argument");
+  std::memset(out, 0, sizeof(*out));
+  if (!m->host_only) {
+    CK(cudaSetDevice(m->device));
+    int rc = stats_harvest(m, true);
+    if (rc) return rc;
+    if (m->d_fstats) {
+      FilterStats st;
+      CK(cudaMemcpyAsync(&st, m->d_fstats, sizeof(st), cudaMemcpyDeviceToHost, m->stream));
+      CK(cudaStreamSynchronize(m->stream));
+      out->filtered = st.filtered;
+      out->filter_evals = st.evals;
+      out->filter_fallbacks = st.fallbacks;
+      out->predictor_used = st.guessed;
+      if (reset) {
+        CK(cudaMemsetAsync(m->d_fstats, 0, sizeof(FilterStats), m->stream));
+        CK(cudaStreamSynchronize(m->stream));
+      }
+    }
+  }
+  out->rhs_calls = m->n_rhs;
+  out->rk_steps = m->n_steps;
+  out->rk_attempts = m->n_attempts;
+  out->rk_rejected = m->n_rejected;
+  out->stages = m->n_stages;
+  out->ms_device = m->ms_device;
+  for (int k = 0; k < FR_KC_COUNT; ++k) {
+    out->ms_kernel[k] = m->prof_ms[k];
+    out->launches[k] = m->prof_launches[k];
+  }
+  out->kernel_family = m->active;
+  out->t_last = m->t_last;
+  if (reset) {
+    m->n_rhs = m->n_steps = m->n_attempts = m->n_rejected = m->n_stages = 0;
+    m->ms_device = 0.0;
+  }
+  return FR_OK;
 }
 
 int fr_set_kernel_variant(fr_mesh* m, int variant) {

@@ -223,11 +223,26 @@ struct fr_mesh {
   __nv_bfloat16* d_mlp = nullptr;
   float* d_mlp_norm = nullptr;
   double mlp_ratio = 1.25;
+  // fr_stats: call counters and device time of the timed calls (fr_rhs,
+  // fr_rk_step, fr_rk_adaptive_step), measured with pairs of events on the
+  // handle's stream and harvested once they have completed
+  unsigned long long n_rhs = 0, n_steps = 0, n_attempts = 0, n_rejected = 0,
+                     n_stages = 0;
+  double ms_device = 0.0, t_last = 0.0;
+  static constexpr int kEvRing = 32;
+  cudaEvent_t ev_a[kEvRing] = {}, ev_b[kEvRing] = {};
+  int ev_head = 0, ev_count = 0;
+  double prof_ms[FR_KC_COUNT] = {};
+  int prof_launches[FR_KC_COUNT] = {};
   std::vector<void*> allocs;
   void* d_staging = nullptr;   // host-layout FP64 staging for set/get
   size_t staging_bytes = 0;
 
   ~fr_mesh() {
+    for (int i = 0; i < kEvRing; ++i) {
+      if (ev_a[i]) cudaEventDestroy(ev_a[i]);
+      if (ev_b[i]) cudaEventDestroy(ev_b[i]);
+    }
     for (int i = 0; i < 3; ++i)
       if (graph[i]) cudaGraphExecDestroy(graph[i]);
     free_all(allocs);
@@ -1105,8 +1120,9 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
 }
 
 // layout conversion kernels: host layout [ne][nu][5] FP64 <-> [ne][5][nu] T
-template <typename T>
-__global__ void k_layout_in(long long n, int nu, const double* __restrict__ src,
+// host layout [ne][nu][5] of type S <-> register layout [ne][5][nu] of type T
+template <typename S, typename T>
+__global__ void k_layout_in(long long n, int nu, const S* __restrict__ src,
                             T* __restrict__ dst) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -1116,15 +1132,15 @@ __global__ void k_layout_in(long long n, int nu, const double* __restrict__ src,
   dst[i] = T(src[(e * nu + z) * 5 + k]);
 }
 
-template <typename T>
+template <typename T, typename S>
 __global__ void k_layout_out(long long n, int nu, const T* __restrict__ src,
-                             double* __restrict__ dst) {
+                             S* __restrict__ dst) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   long long e = i / (5 * nu);
   int r = int(i - e * 5 * nu);
   int k = r / nu, z = r - k * nu;
-  dst[(e * nu + z) * 5 + k] = double(src[i]);
+  dst[(e * nu + z) * 5 + k] = S(src[i]);
 }
 
 DevType* type_ptr(fr_mesh* m, int etype) {
@@ -1138,20 +1154,20 @@ const HostType* host_ptr(const fr_mesh* m, int etype) {
   return &m->host[m->type_of_kind[etype]];
 }
 
-template <typename TR>
-int set_solution_dev(fr_mesh* m, DevType& D, const double* dsrc) {
+template <typename TR, typename S = double>
+int set_solution_dev(fr_mesh* m, DevType& D, const S* dsrc) {
   long long n = D.ne * 5 * D.nu;
-  k_layout_in<TR><<<nblk(n, 256), 256, 0, m->stream>>>(n, D.nu, dsrc, (TR*)D.X);
+  k_layout_in<S, TR><<<nblk(n, 256), 256, 0, m->stream>>>(n, D.nu, dsrc, (TR*)D.X);
   CK(cudaGetLastError());
   m->uf_valid = false;
   return FR_OK;
 }
 
-template <typename T>
-int get_dev(fr_mesh* m, const DevType& D, const void* src, double* ddst) {
+template <typename T, typename S = double>
+int get_dev(fr_mesh* m, const DevType& D, const void* src, S* ddst) {
   long long n = D.ne * 5 * D.nu;
-  k_layout_out<T><<<nblk(n, 256), 256, 0, m->stream>>>(n, D.nu, (const T*)src,
-                                                       ddst);
+  k_layout_out<T, S><<<nblk(n, 256), 256, 0, m->stream>>>(n, D.nu, (const T*)src,
+                                                          ddst);
   CK(cudaGetLastError());
   return FR_OK;
 }

@@ -1,4 +1,4 @@
-// Domain decomposition of a mesh (Section 4, "Mixed Elements and Domain
+// Domain decomposition of a mesh (Section 3.3, "Mixed Elements and Domain
 // Decomposition"): elements are split into parts by recursive coordinate
 // bisection of their centroids, either with per-type weights (one
 // partitioning of all elements) or balanced (every type split on its own so

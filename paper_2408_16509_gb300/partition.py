@@ -1,4 +1,4 @@
-"""Sub-meshes of a partitioned mesh (Section 4, "Mixed Elements and Domain
+"""Sub-meshes of a partitioned mesh (Section 3.3, "Mixed Elements and Domain
 Decomposition").  The library partitions the elements (fr_partition) and
 lists each part's faces that border another part (fr_partition_faces);
 this module only assembles, for every part, the mesh description of its

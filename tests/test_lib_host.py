@@ -46,6 +46,15 @@ def test_compute_calls_refuse_host_only_handles():
     with pytest.raises(fr.FRError) as e:
         g.rhs()
     assert e.value.name == "FR_EINVAL"
+    st = g.stats()
+    assert st["rhs_calls"] == 0 and st["ms_device"] == 0.0
+
+
+def test_rhs_rejects_a_non_finite_time():
+    lib = fr.load()
+    g = fr.FRMesh(box_hex((2, 2, 2)), 2, device=-1)
+    assert lib.fr_rhs(g._h, float("nan"), None, None) == -1
+    assert lib.fr_stats(None, None, 0) == -1
 
 
 SPECS = {
