@@ -6,7 +6,8 @@ Section 2 of the paper:
 * the vertex map x = M_n(x~) (trilinear hex, linear prism, affine tet) and
   its derivatives, for the Jacobian J = dM/dx~ of Section 2;
 * solution points, flux points on every face, reference unit outward
-  normals at the flux points and each face's area scale;
+  normals at the flux points and each face's area scale; hexahedra take
+  Gauss-Legendre (default) or Gauss-Lobatto line points (``family``);
 * ``M0[s, z] = l_z(x_s^(f))``  -- Eq. (disu), interpolation to flux points;
 * ``D[d][z, v] = d l_v / d x~_d (x_z)`` -- the grad l term of Eq. (FRfinal);
 * ``LIFT[z, s] = (div~ g_s)(x_z)`` -- the correction term of Eq. (FRfinal).
@@ -31,7 +32,7 @@ import numpy as np
 
 from . import bases
 from .points import gl_points, tet_nodes, tri_face_points, tri_solution_points
-from .polys import gauss_jacobi, gauss_legendre
+from .polys import gauss_jacobi, gauss_legendre, gauss_lobatto
 
 SQ2 = np.sqrt(2.0)
 SQ3 = np.sqrt(3.0)
@@ -104,8 +105,9 @@ class ElementType:
     name = None
     nverts = 0
 
-    def __init__(self, p):
+    def __init__(self, p, family="gl"):
         self.p = p
+        self.family = family
         self.upts = self.solution_points()
         self.nupts = len(self.upts)
         fp, fidx, fnrm = [], [], []
@@ -125,10 +127,18 @@ class ElementType:
         self._build_operators()
 
     # face Lagrange basis and exact face quadrature ---------------------
+    def line_points(self):
+        """1D point set of the tensor-product directions: Gauss-Legendre, or
+        Gauss-Lobatto for the hexahedron family "gll" (flux points are then
+        solution points: Section 3.1, "Matrix multiplications")."""
+        if self.family == "gll":
+            return gauss_lobatto(self.p + 1)[0]
+        return gl_points(self.p)
+
     def face_points(self, face):
         p = self.p
         if face.kind == "quad":
-            x = gl_points(p)
+            x = self.line_points()
             X, Y = np.meshgrid(x, x, indexing="xy")
             return np.stack([X.ravel(), Y.ravel()], axis=1)
         return tri_face_points(p)
@@ -215,7 +225,7 @@ class Hex(ElementType):
     ]
 
     def solution_points(self):
-        x = gl_points(self.p)
+        x = self.line_points()
         Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
         return np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
 
@@ -358,8 +368,13 @@ ETYPES = {"hex": Hex, "pri": Prism, "tet": Tet}
 _cache = {}
 
 
-def element(name, p):
-    key = (name, p)
+def element(name, p, family="gl"):
+    """Reference element of type name and order p.  family "gll" (hexahedra
+    only): Gauss-Lobatto solution points, flux points on the faces among
+    them; "gl" (default): Gauss-Legendre."""
+    if family not in ("gl", "gll") or (family == "gll" and name != "hex"):
+        raise ValueError(f"point family {family!r} is not available for {name}")
+    key = (name, p, family)
     if key not in _cache:
-        _cache[key] = ETYPES[name](p)
+        _cache[key] = ETYPES[name](p, family)
     return _cache[key]

@@ -75,12 +75,18 @@ class FRMesh:
       bfaces   list of (node-id tuple, tag) for boundary faces
     """
 
-    def __init__(self, spec, p):
+    def __init__(self, spec, p, family="gl"):
         self.p = p
+        self.family = family
         nodes = np.asarray(spec["nodes"], np.float64)
         self.types = [t for t in ETYPE_ORDER
                       if t in spec["elements"] and len(spec["elements"][t])]
-        self.el = {t: element(t, p) for t in self.types}
+        if family == "gll" and "pri" in self.types:
+            # a hexahedron's Gauss-Lobatto quad faces cannot meet a prism's
+            # Gauss-Legendre ones
+            raise MeshError("the Gauss-Lobatto family needs a mesh without prisms")
+        self.el = {t: element(t, p, family if t == "hex" else "gl")
+                   for t in self.types}
         self.conn = {t: np.asarray(spec["elements"][t], np.int64)
                      for t in self.types}
         self.verts = {t: nodes[self.conn[t]] for t in self.types}

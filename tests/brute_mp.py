@@ -5,8 +5,9 @@ It restates the definitions of the paper's Section 2 for hexahedra with an
 affine map, one scalar at a time in mpmath:
 
 * solution points: the N = p + 1 roots of the Legendre polynomial P_N (Newton
-  iteration on the three-term recurrence), tensorised; flux points: the same
-  1D points on each face;
+  iteration on the three-term recurrence), or the N Gauss-Lobatto points
+  (+-1 and the roots of P'_p), tensorised; flux points: the same 1D points
+  on each face;
 * Lagrange basis l_m and its derivative from the product formula;
 * Eq. (disu): traces by Lagrange interpolation along the line through the
   face point;
@@ -63,6 +64,24 @@ def gauss_points(n):
     return sorted(pts)
 
 
+def lobatto_points(n):
+    """The n Gauss-Lobatto points: +-1 and the roots of P'_{n-1} (Newton,
+    with P'' from Legendre's equation (1 - x^2) P'' = 2 x P' - m(m+1) P)."""
+    m = n - 1
+    inner = []
+    for i in range(1, m):
+        x = -mp.cos(mp.pi * i / m)
+        for _ in range(200):
+            pv, dv = _legendre(m, x)
+            d2 = (2 * x * dv - m * (m + 1) * pv) / (1 - x * x)
+            dx = dv / d2
+            x -= dx
+            if abs(dx) < mp.mpf(10) ** (-mp.mp.dps + 2):
+                break
+        inner.append(x)
+    return [mp.mpf(-1)] + sorted(inner) + [mp.mpf(1)]
+
+
 def lagrange(xs, j, x):
     v = mp.mpf(1)
     for m, xm in enumerate(xs):
@@ -95,14 +114,14 @@ def _mat_inv_t(A):
 
 
 class BruteFR:
-    def __init__(self, p, A, n, gamma=1.4, mu=0.0, pr=0.72, dps=50):
+    def __init__(self, p, A, n, gamma=1.4, mu=0.0, pr=0.72, dps=50, family="gl"):
         mp.mp.dps = dps
         self.p, self.N = p, p + 1
         self.n = tuple(n)
         self.A = mp.matrix([[mp.mpf(float(a)) for a in row] for row in A])
         self.Ainv, self.det = _mat_inv_t(self.A)
         self.gamma, self.mu, self.pr = mp.mpf(gamma), mp.mpf(mu), mp.mpf(pr)
-        self.x1 = gauss_points(self.N)
+        self.x1 = lobatto_points(self.N) if family == "gll" else gauss_points(self.N)
         N = self.N
         self.lm = [lagrange(self.x1, m, mp.mpf(-1)) for m in range(N)]
         self.lp = [lagrange(self.x1, m, mp.mpf(1)) for m in range(N)]

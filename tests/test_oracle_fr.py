@@ -22,12 +22,13 @@ def _uniform_bcs(n, state=(1.0, 0.3, -0.2, 0.5, 1.0)):
     return {k: ("state",) + tuple(state) for k in range(n)}
 
 
+@pytest.mark.parametrize("family", ["gl", "gll"])
 @pytest.mark.parametrize("p", [2, 3])
 @pytest.mark.parametrize("physics", ["euler", "ns"])
-def test_freestream_preserved_on_perturbed_hexes(p, physics):
+def test_freestream_preserved_on_perturbed_hexes(p, physics, family):
     """Section 3.4: a uniform flow stays uniform on a mesh whose interior
     nodes are perturbed by 10% (metric from the vertex map)."""
-    m = FRMesh(box_hex((3, 3, 3), perturb=0.1).as_dict(), p)
+    m = FRMesh(box_hex((3, 3, 3), perturb=0.1).as_dict(), p, family=family)
     s = FRSystem(m, physics, mu=0.01)
     assert _maxabs(s.rhs(_state(m, ics.uniform))) < 1e-11
 
@@ -44,11 +45,12 @@ def _integral(m, r):
                for t in m.types)
 
 
+@pytest.mark.parametrize("family", ["gl", "gll"])
 @pytest.mark.parametrize("physics", ["euler", "ns"])
-def test_discrete_conservation_periodic_hex(physics):
+def test_discrete_conservation_periodic_hex(physics, family):
     """Sum over elements of int J R = 0 on a periodic mesh: the common
     fluxes of both sides of every interface cancel."""
-    m = FRMesh(box_hex((3, 3, 2), perturb=0.1).as_dict(), 3)
+    m = FRMesh(box_hex((3, 3, 2), perturb=0.1).as_dict(), 3, family=family)
     s = FRSystem(m, physics, mu=0.02)
     u = _state(m, lambda x: ics.taylor_green(2 * np.pi * x, mach=0.3))
     r = s.rhs(u)
@@ -131,6 +133,11 @@ def test_planted_lift_error_is_caught():
         for t in m.types:
             m.el[t].LIFT = -m.el[t].LIFT
     assert ok < 1e-12 and bad > 1e-6
+
+
+def test_gll_family_rejects_prisms():
+    with pytest.raises(MeshError):
+        FRMesh(mixed_box(n=3, x_pri=0.34, x_tet=0.67).as_dict(), 2, family="gll")
 
 
 def test_nonconforming_mesh_is_rejected():

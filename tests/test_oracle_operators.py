@@ -8,7 +8,7 @@ from numpy.polynomial import legendre as L
 
 from oracle import bases
 from oracle.elements import element, hex_rule, pri_rule, tet_rule
-from oracle.polys import gauss_legendre, lagrange_matrix
+from oracle.polys import gauss_lobatto, gauss_legendre, lagrange_matrix
 
 TYPES = ["hex", "pri", "tet"]
 
@@ -60,12 +60,13 @@ def test_basis_gradients_against_finite_differences(name):
         assert np.abs(fd - G[d]).max() < 1e-7 * max(1.0, np.abs(G[d]).max())
 
 
-@pytest.mark.parametrize("name", TYPES)
+@pytest.mark.parametrize("name", TYPES + ["hex-gll"])
 @pytest.mark.parametrize("p", [1, 2, 3, 4])
 def test_interpolation_and_derivative_are_exact(name, p):
     """Eq. (disu) and the grad l term of Eq. (FRfinal) are exact on the
     element's polynomial space."""
-    el = element(name, p)
+    name, _, fam = name.partition("-")
+    el = element(name, p, fam or "gl")
     for e in _monomials(name, p):
         f = _mono(el.upts, e)
         assert np.abs(el.M0 @ f - _mono(el.fpts, e)).max() < 1e-13
@@ -83,14 +84,17 @@ def _radau_derivs(p, x):
     return 0.5 * (dp1 + dp), (-1) ** (p + 1) * 0.5 * (dp1 - dp)
 
 
+@pytest.mark.parametrize("family", ["gl", "gll"])
 @pytest.mark.parametrize("p", [1, 2, 3, 4])
-def test_hex_lift_equals_tensor_radau(p):
+def test_hex_lift_equals_tensor_radau(p, family):
     """The DG lift built from face quadrature equals the tensor-product
     Radau correction of Huynh (2007): for a flux point on x=+1 at (y_j,z_k)
     the lift at (x_a,y_b,z_c) is g_R'(x_a) d_jb d_kc, on x=-1 it is
-    -g_L'(x_a) d_jb d_kc (outward normal -x)."""
-    el = element("hex", p)
-    x1 = gauss_legendre(p + 1)[0]
+    -g_L'(x_a) d_jb d_kc (outward normal -x).  The correction function does
+    not depend on the solution points: the same formula holds at the
+    Gauss-Lobatto points."""
+    el = element("hex", p, family)
+    x1 = (gauss_legendre(p + 1) if family == "gl" else gauss_lobatto(p + 1))[0]
     gr, gl = _radau_derivs(p, x1)
     n = p + 1
     ref = np.zeros_like(el.LIFT)
@@ -161,3 +165,25 @@ def test_bases_module_sizes():
     for p in range(5):
         assert len(bases.tri_modes(p)) == (p + 1) * (p + 2) // 2
         assert len(bases.tet_modes(p)) == (p + 1) * (p + 2) * (p + 3) // 6
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_gll_flux_points_are_solution_points(p):
+    """Gauss-Lobatto hexahedra (Section 3.1, "Matrix multiplications", last
+    paragraph): every flux point is a solution point, so the interpolation
+    of Eq. (disu) is a gather -- each row of M0 one 1 at the coinciding
+    solution point, zeros elsewhere."""
+    el = element("hex", p, "gll")
+    for f in range(el.nfpts):
+        d = np.linalg.norm(el.upts - el.fpts[f], axis=1)
+        z = int(np.argmin(d))
+        assert d[z] < 1e-15
+        row = np.zeros(el.nupts)
+        row[z] = 1.0
+        assert np.abs(el.M0[f] - row).max() < 1e-13
+
+
+def test_gll_family_is_hexahedra_only():
+    for name in ("pri", "tet"):
+        with pytest.raises(ValueError):
+            element(name, 2, "gll")

@@ -39,22 +39,38 @@ def _per_var(a, b):
     return np.linalg.norm(a - b, axis=0) / np.linalg.norm(b, axis=0)
 
 
-def _oracle_on_points(spec, p, physics, keys, pos, state, **kw):
-    """Oracle RHS at every point of ``keys`` (matched by position)."""
-    m = FRMesh(spec, p)
+def _match(m, pos, keys):
+    """Oracle (element, point) order of the keyed points: elements by
+    centroid, then points within each element by position (Gauss-Lobatto
+    points of neighbouring elements coincide on their shared faces)."""
+    els = sorted({k[0] for k in keys})
+    cen = {e: np.mean([pos[k] for k in keys if k[0] == e], axis=0) for e in els}
+    order = []
+    for i, oc in enumerate(m.upts_x["hex"].mean(axis=1)):
+        e = min(els, key=lambda f: np.linalg.norm(cen[f] - oc))
+        ks = [k for k in keys if k[0] == e]
+        d, j = cKDTree(np.array([pos[k] for k in ks])).query(m.upts_x["hex"][i])
+        assert d.max() < 1e-12 and len(set(j.tolist())) == len(j)
+        order += [ks[q] for q in j]
+    return order
+
+
+def _oracle_on_points(spec, p, physics, keys, pos, state, family="gl", **kw):
+    """Oracle RHS at its own points and the matching keys."""
+    m = FRMesh(spec, p, family=family)
     s = FRSystem(m, physics, gamma=GAMMA, mu=MU, pr=PRANDTL, **kw)
-    X = np.array([pos[k] for k in keys])
-    d, idx = cKDTree(X).query(m.upts_x["hex"].reshape(-1, 3))
-    assert d.max() < 1e-12
-    u = np.array([state[keys[i]] for i in idx]).reshape(m.ne["hex"], -1, 5)
+    order = _match(m, pos, keys)
+    u = np.array([state[k] for k in order]).reshape(m.ne["hex"], -1, 5)
+    idx = np.array([keys.index(k) for k in order])
     return s.rhs({"hex": u})["hex"].reshape(-1, 5), idx
 
 
-def _brute_case(p, n, physics, seed=7):
-    br = brute_mp.BruteFR(p, SHEAR, n, gamma=GAMMA, mu=MU, pr=PRANDTL)
+def _brute_case(p, n, physics, seed=7, family="gl"):
+    br = brute_mp.BruteFR(p, SHEAR, n, gamma=GAMMA, mu=MU, pr=PRANDTL,
+                          family=family)
     pos = br.points()
     keys = sorted(pos)
-    st = brute_mp.random_state(keys, seed)
+    st = brute_mp.random_state(keys, seed, amp=0.3 if p < 3 else 0.1)
     R = br.rhs(st, physics)
     rb = np.array([[float(c) for c in R[k]] for k in keys])
     return keys, pos, st, rb
@@ -62,15 +78,18 @@ def _brute_case(p, n, physics, seed=7):
 
 # ------------------------------------------------------------- brute force
 @pytest.mark.parametrize("physics", ["euler", "ns"])
-@pytest.mark.parametrize("p,n", [(1, (2, 1, 1)), (2, (2, 1, 1)), (2, (1, 1, 1))])
-def test_brute_force_small_meshes(physics, p, n):
+@pytest.mark.parametrize("family,p,n", [("gl", 1, (2, 1, 1)), ("gl", 2, (2, 1, 1)),
+                                        ("gl", 2, (1, 1, 1)), ("gll", 1, (2, 1, 1)),
+                                        ("gll", 2, (2, 1, 1)), ("gll", 3, (1, 1, 1))])
+def test_brute_force_small_meshes(physics, family, p, n):
     """Section 2 definitions at 50 digits vs the FP64 oracle: every
     interface carries a jump (random state per point), every face is
     sheared, and one- and two-element periodic meshes pair elements with
-    themselves and with each other."""
-    keys, pos, st, rb = _brute_case(p, n, physics)
+    themselves and with each other; Gauss-Legendre and Gauss-Lobatto
+    hexahedron points."""
+    keys, pos, st, rb = _brute_case(p, n, physics, family=family)
     r, idx = _oracle_on_points(brute_mp.spec_for(SHEAR, n), p, physics,
-                               keys, pos, st)
+                               keys, pos, st, family=family)
     assert _per_var(r, rb[idx]).max() < 1e-13
 
 
