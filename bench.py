@@ -1,17 +1,23 @@
 #!/usr/bin/env python
 """Benchmark: FR right-hand side + RK update throughput on one GB300.
 
-Workload (the Navier-Stokes Taylor-Green vortex of the paper's Section 5,
-at the size of a single-GPU run): periodic [0, 2 pi]^3 box of 32^3
-hexahedra whose interior nodes are perturbed by up to 10% of the spacing
-(seed 20240829), p = 3 (64 Gauss-Legendre solution points per element),
-Re = 1600, Ma = 0.1, Pr = 0.71, constant viscosity, BR1 gradients, Rusanov
-inviscid flux, RK4(3)5[2R+] with dt = 1e-3.  A "step" is one RK step
-(five right-hand-side stages).  Metric: GDOF-stage/s = solution points x 5
-variables x stages / second / 1e9.
+Workload (the Navier-Stokes Taylor-Green vortex of the paper's Section 5
+in the mixed-precision configuration, the largest that fits one GPU):
+periodic [0, 2 pi]^3 box of 48^3 hexahedra whose interior nodes are
+perturbed by up to 10% of the spacing (seed 20240829), p = 4 (125
+Gauss-Legendre solution points per element, 13.8 M points), Re = 1600,
+Ma = 0.1, Pr = 0.71, constant viscosity, BR1 gradients, Rusanov inviscid
+flux, RK4(3)5[2R+] with dt = 2.5e-4 (1e-3 exceeds the explicit limit at
+this h and p).  A "step" is one RK step (five right-hand-side stages).
+Metric: GDOF-stage/s = solution points x 5 variables x stages / s / 1e9.
+The headline value is the plain FP64 form; the mixed form (FP32 values,
+FP64 RK registers) and the FP32 form are reported beside it with their
+relative L2 error per conserved variable against the FP64 form after the
+same steps.
 
 --impl reference times the CPU FP64 oracle (plain numpy) on the same
-workload, on a bounded sample (an 8^3-element box of the same shape).
+workload, on bounded samples (4^3-element boxes of the same shape), one
+single-threaded replica per host core.
 """
 import argparse
 import json
@@ -27,11 +33,14 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-N_CELLS = 32
-ORDER = 3
+N_CELLS = 48
+ORDER = 4
 RE, MACH, PR = 1600.0, 0.1, 0.71
-DT = 1e-3
+DT = 2.5e-4
 STAGES = 5
+SAMPLE_CELLS = 4     # per direction, CPU oracle samples
+# the Navier-Stokes TGV at one-GPU size of the paper's subsonic case
+C2_CELLS, C2_ORDER, C2_DT = 32, 3, 1e-3
 L2_BYTES = 129e6
 
 
@@ -111,21 +120,19 @@ def tgv(x):
 
 
 def config(precision):
+    nu = (ORDER + 1) ** 3
     return {"workload": f"ns-tgv-hex{N_CELLS}^3-p{ORDER}-rk45",
             "elements": N_CELLS ** 3, "order": ORDER,
-            "solution_points": N_CELLS ** 3 * (ORDER + 1) ** 3,
+            "solution_points": N_CELLS ** 3 * nu,
             "physics": "navier-stokes BR1 + Rusanov", "scheme": "RK4(3)5[2R+]",
             "dt": DT, "re": RE, "mach": MACH, "precision": precision,
             "mesh_perturbation": 0.1,
-            "l2": "inputs larger than L2 (state register 84 MB, step working "
-                  "set > 1 GB); no flush"}
+            "l2": f"inputs larger than L2 (state register "
+                  f"{N_CELLS ** 3 * nu * 5 * 8 / 1e6:.0f} MB in FP64, step working "
+                  f"set > 5 GB); no flush"}
 
 
 # ------------------------------------------------------ byte/flop models
-FP64_TFLOPS_PROBE = 1.058   # measured DFMA throughput on this GB300 pool
-FP32_TFLOPS_PROBE = 77.8    # measured FFMA throughput on this GB300 pool
-
-
 def kernel_models(nu, nf, ne, w, wr, npair):
     """Algorithmic DRAM bytes and floating-point operations per launch of
     each kernel class for an RK4(3)5[2R+] stage i > 0 of the Navier-Stokes
@@ -157,43 +164,47 @@ def kernel_models(nu, nf, ne, w, wr, npair):
     return bytes_, flops
 
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, mean
-# of two launches of one ncu capture) of the volume kernel of the 32^3 p=3
-# workload, for the kernel version these counters were taken on.  Any
-# change to that kernel must refresh or drop the entry (traffic -> null).
-MEASURED_TRAFFIC = {("fp64", "volume"): 970041600, ("fp32", "volume"): 467603072}
-
-
-def roofline(prof, models, peaks, src, precision):
+def roofline(prof, models, peaks, src, precision, alu):
     """Roofline record of the dominant kernel class: the bound is whichever
-    of DRAM bytes / HBM peak and flops / arithmetic peak takes longer."""
+    of DRAM bytes / HBM peak and flops / arithmetic peak takes longer.
+    alu: {"fp64": (TFLOP/s, source), "fp32": (...)} measured in this run."""
     bytes_, flops = models
     dom = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
     t = prof[dom][0] / prof[dom][1] * 1e-3
     b, f = bytes_.get(dom), flops.get(dom)
     bw = b / t / 1e9 if b else None
     fl = f / t / 1e12 if f else None
-    if precision == "fp64":
-        fpeak, fsrc = FP64_TFLOPS_PROBE, "FP64 FMA probe on this pool"
-    else:
-        fpeak, fsrc = FP32_TFLOPS_PROBE, "FP32 FMA probe on this pool"
+    fpeak, fsrc = alu["fp64" if precision == "fp64" else "fp32"]
     t_mem = b / (peaks["hbm_gbs"] * 1e9) if b else 0.0
     t_alu = f / (fpeak * 1e12) if f else 0.0
     if t_alu > t_mem:
         out = {"kernel": dom, "bound": "alu", "achieved": fl, "peak": fpeak,
-               "unit": "TFLOP/s", "frac": fl / fpeak, "traffic": None,
-               "peak_source": fsrc}
+               "unit": "TFLOP/s", "frac": fl / fpeak, "peak_source": fsrc}
     else:
         out = {"kernel": dom, "bound": "hbm", "achieved": bw,
                "peak": peaks["hbm_gbs"], "unit": "GB/s",
-               "frac": bw / peaks["hbm_gbs"], "traffic": None,
-               "peak_source": src + " hbm_gbs (MEASURED_PEAKS.json)"}
-    out["traffic"] = MEASURED_TRAFFIC.get((precision, dom))
+               "frac": bw / peaks["hbm_gbs"],
+               "peak_source": src + " hbm_gbs (MEASURED_PEAKS.json), burst copy"}
+    # DRAM traffic needs an ncu capture (profiles/); not measured in a bench run
+    out["traffic"] = None
     out.update({"launches_per_step": prof[dom][1], "kernel_ms": t * 1e3,
                 "algorithmic_bytes": b, "algorithmic_flops": f,
                 "achieved_gbs": bw, "achieved_tflops": fl,
                 "attainable_ms": max(t_mem, t_alu) * 1e3})
     return out
+
+
+def alu_peaks(fr, device):
+    """FMA throughput of this GPU in FP64 and FP32 (fr_probe_fma, CUDA
+    events), with the SM clocks sampled during the probes."""
+    sampler = ClockSampler(device)
+    sampler.start()
+    out = {}
+    for dt in ("fp64", "fp32"):
+        best = max(fr.probe_fma(dt, device=device)[0] for _ in range(3))
+        out[dt] = (best, f"fr_probe_fma {dt} FMA chains, best of 3 launches, this run")
+    clocks = sampler.stop()
+    return out, clocks
 
 
 # ------------------------------------------------------------ our arm
@@ -211,9 +222,13 @@ def aggregate(ms_local, units_local, dist=None, device="cpu"):
 
 
 
-def measure(fr, torch, precision, steps, warmup, device, dist):
-    spec = workload_spec(N_CELLS)
-    mesh = fr.FRMesh(spec, ORDER, physics="ns", gamma=1.4, mu=1.0 / RE,
+METRIC = "GDOF-stage/s per GB300 (plain FP64 vs mixed-prec/batched) at stated L2 error"
+
+
+def measure(fr, torch, precision, steps, warmup, device, dist, n=None,
+            order=ORDER, dt=DT):
+    spec = workload_spec(n or N_CELLS)
+    mesh = fr.FRMesh(spec, order, physics="ns", gamma=1.4, mu=1.0 / RE,
                      prandtl=PR, precision=precision, device=device)
     stream = torch.cuda.Stream(device=device)
     mesh.set_stream(stream)
@@ -221,8 +236,8 @@ def measure(fr, torch, precision, steps, warmup, device, dist):
     ne, nu, nf = mesh.info("hex")
     u0 = tgv(x.reshape(-1, 3)).reshape(ne, nu, 5)
     mesh.set_solution({"hex": u0})
-    for _ in range(warmup):             # the first one builds the CUDA graph
-        mesh.rk_step("rk45", DT, 1)
+    for _ in range(warmup):             # the first one tunes and builds the graph
+        mesh.rk_step("rk45", dt, 1)
     mesh.set_solution({"hex": u0})
     sampler = ClockSampler(device)
     if dist:
@@ -232,12 +247,11 @@ def measure(fr, torch, precision, steps, warmup, device, dist):
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
-    mesh.rk_step("rk45", DT, steps)
+    mesh.rk_step("rk45", dt, steps)
     t1.record(stream)
     torch.cuda.synchronize()
     clocks = sampler.stop()
     ms = t0.elapsed_time(t1)
-    ne, nu, _ = mesh.info("hex")
     ms, units = aggregate(ms, ne * nu * 5 * STAGES * steps, dist, "cuda")
     if dist:
         dist.barrier()
@@ -246,18 +260,52 @@ def measure(fr, torch, precision, steps, warmup, device, dist):
     prof = {}
     reps = 3
     for _ in range(reps):
-        for k, (t, n) in mesh.profile_step("rk45", DT).items():
+        for k, (t, c) in mesh.profile_step("rk45", dt).items():
             a = prof.setdefault(k, [0.0, 0])
             a[0] += t / reps
-            a[1] = n
-    prof["_tuning"] = tuning
-    prof["_units"] = units
-    return mesh, u0, ms, clocks, prof, final
+            a[1] = c
+    return {"mesh": mesh, "u0": u0, "ms": ms, "clocks": clocks, "prof": prof,
+            "final": final, "tuning": tuning, "units": units}
+
+
+def _rel_l2_arrays(a, b):
+    """Per conserved variable: ||a - b|| / max(||b||, ||rho_b||)."""
+    d = (a - b).reshape(-1, 5)
+    r = b.reshape(-1, 5)
+    den = np.maximum(np.linalg.norm(r, axis=0), np.linalg.norm(r[:, 0]))
+    return (np.linalg.norm(d, axis=0) / den).tolist()
+
+
+def _e2e(fr, torch, mesh, u0, steps, world, dist):
+    """Same metric through the C ABI with host buffers: every step copies
+    the state in from pinned memory, runs one RK step and copies it out."""
+    import ctypes
+    lib = fr.load()
+    host_in = torch.from_numpy(np.ascontiguousarray(u0)).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    hin, hout = host_in.numpy(), host_out.numpy()
+    ne, nu, _ = mesh.info("hex")
+    e2e_steps = max(3, min(steps, 10))
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        rc = lib.fr_set_solution(mesh._h, 0, hin.ctypes.data_as(ctypes.c_void_p))
+        rc |= lib.fr_rk_step(mesh._h, 1, DT, 1)
+        rc |= lib.fr_get_solution(mesh._h, 0, hout.ctypes.data_as(ctypes.c_void_p))
+        if rc:
+            raise RuntimeError(lib.fr_last_error().decode())
+    e2e_s = time.perf_counter() - w0
+    if dist:
+        tt = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    val = ne * nu * 5 * STAGES * e2e_steps * world / e2e_s / 1e9
+    return {"value": val, "unit": "GDOF-stage/s",
+            "h2d_bytes_per_step": int(hin.nbytes),
+            "d2h_bytes_per_step": int(hout.nbytes), "steps": e2e_steps}
 
 
 def run_ours(args):
-    import ctypes
-
     import torch
 
     import paper_2408_16509_gb300 as fr
@@ -272,44 +320,22 @@ def run_ours(args):
     torch.cuda.set_device(local)
     fr.build()
     peaks, src = _peaks()
-    mesh, u0, ms, clocks, prof, final = measure(
-        fr, torch, args.precision, args.steps, args.warmup, local, dist)
-    tuning = prof.pop("_tuning")
-    units_all = prof.pop("_units")
+    alu, probe_clocks = alu_peaks(fr, local)
+    r = measure(fr, torch, args.precision, args.steps, args.warmup, local, dist)
+    mesh, prof, ms = r["mesh"], r["prof"], r["ms"]
     ne, nu, nf = mesh.info("hex")
-    units_per_step = ne * nu * 5 * STAGES
-    # whole job: units of all replicas / slowest rank's time
-    value = units_all / (ms * 1e-3) / 1e9
-    launches_per_step = sum(n for _, n in prof.values())
-    # end-to-end through the C ABI with pinned host buffers: every step
-    # copies the state in, runs one RK step and copies the state out
-    lib = fr.load()
-    host_in = torch.from_numpy(np.ascontiguousarray(u0)).pin_memory()
-    host_out = torch.empty_like(host_in).pin_memory()
-    hin, hout = host_in.numpy(), host_out.numpy()
-    e2e_steps = max(3, min(args.steps, 10))
-    torch.cuda.synchronize()
-    w0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        rc = lib.fr_set_solution(mesh._h, 0, hin.ctypes.data_as(ctypes.c_void_p))
-        rc |= lib.fr_rk_step(mesh._h, 1, DT, 1)
-        rc |= lib.fr_get_solution(mesh._h, 0,
-                                  hout.ctypes.data_as(ctypes.c_void_p))
-        if rc:
-            raise RuntimeError(lib.fr_last_error().decode())
-    e2e_s = time.perf_counter() - w0
-    if dist:
-        tt = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e = units_per_step * e2e_steps * world / e2e_s / 1e9
+    value = r["units"] / (ms * 1e-3) / 1e9     # all replicas / slowest rank
+    launches_per_step = sum(c for _, c in prof.values())
+    e2e = _e2e(fr, torch, mesh, r["u0"], args.steps, world, dist)
     npair, _ = mesh.pair_counts()
-    w = 8 if args.precision == "fp64" else 4
-    wr = 4 if args.precision == "fp32" else 8
-    roof = roofline(prof, kernel_models(nu, nf, ne, w, wr, npair), peaks,
-                    src, args.precision)
+
+    def widths(prec):
+        return (8 if prec == "fp64" else 4), (4 if prec == "fp32" else 8)
+    w, wr = widths(args.precision)
+    roof = roofline(prof, kernel_models(nu, nf, ne, w, wr, npair), peaks, src,
+                    args.precision, alu)
     line = {
-        "metric": "GDOF-stage/s per GB300 (NS FR RHS + RK update)",
+        "metric": METRIC,
         "value": value, "unit": "GDOF-stage/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -318,48 +344,51 @@ def run_ours(args):
                   "mixed": "f32 (f64 RK registers)"}[args.precision],
         "data": "synthetic (seeded perturbed mesh, analytic TGV state)",
         "config": config(args.precision),
-        "clocks": clocks,
-        "e2e": {"value": e2e, "unit": "GDOF-stage/s",
-                "h2d_bytes_per_step": int(hin.nbytes),
-                "d2h_bytes_per_step": int(hout.nbytes)},
+        "clocks": r["clocks"],
+        "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
         "kernel_ms_per_step": {k: v[0] for k, v in prof.items() if v[1]},
-        "kernel_family": {"active": tuning[0], "tuned_ms_per_step": tuning[1]},
+        "kernel_family": {"active": r["tuning"][0],
+                          "tuned_ms_per_step": r["tuning"][1]},
         "roofline": roof,
+        "alu_probe": {"fp64_tflops": alu["fp64"][0], "fp32_tflops": alu["fp32"][0],
+                      "clocks": probe_clocks},
+        "l2_error": {args.precision: "reference form of this line; parity with the "
+                     "FP64 oracle is gated per variable in the -m gpu tests"},
     }
+    ref_final = r["final"] if args.precision == "fp64" else None
     mesh.close()
     if args.variants and world == 1:
         line["variants"] = {}
-        for prec in ("fp64", "fp32", "mixed"):
+        finals = {}
+        for prec in ("fp64", "mixed", "fp32"):
             if prec == args.precision:
                 continue
-            m2, _, ms2, _, prof2, fin2 = measure(
-                fr, torch, prec, args.steps, args.warmup, local, None)
-            tun2 = prof2.pop("_tuning")
-            prof2.pop("_units")
-            w2 = 8 if prec == "fp64" else 4
-            wr2 = 4 if prec == "fp32" else 8
-            if args.precision == "fp64":
-                ref, oth = final, fin2
-            else:
-                ref, oth = fin2, final
-            d = (oth - ref).reshape(-1, 5)
-            r = ref.reshape(-1, 5)
-            den = np.maximum(np.linalg.norm(r, axis=0),
-                             np.linalg.norm(r[:, 0]))
+            v = measure(fr, torch, prec, args.steps, args.warmup, local, None)
+            finals[prec] = v["final"]
+            w2, wr2 = widths(prec)
             line["variants"][prec] = {
-                "value": units_per_step * args.steps / (ms2 * 1e-3) / 1e9,
-                "ms_per_step": ms2 / args.steps,
-                "rel_l2_vs_fp64_after_steps": (np.linalg.norm(d, axis=0)
-                                               / den).tolist(),
+                "value": v["units"] / (v["ms"] * 1e-3) / 1e9,
+                "ms_per_step": v["ms"] / args.steps,
                 "roofline": roofline(
-                    prof2, kernel_models(nu, nf, ne, w2, wr2, npair), peaks,
-                    src, prec),
-                "kernel_ms_per_step": {k: v[0] for k, v in prof2.items()
-                                       if v[1]},
-                "kernel_family": {"active": tun2[0],
-                                  "tuned_ms_per_step": tun2[1]}}
-            m2.close()
+                    v["prof"], kernel_models(nu, nf, ne, w2, wr2, npair), peaks,
+                    src, prec, alu),
+                "kernel_ms_per_step": {k: x[0] for k, x in v["prof"].items() if x[1]},
+                "kernel_family": {"active": v["tuning"][0],
+                                  "tuned_ms_per_step": v["tuning"][1]},
+                "clocks": v["clocks"]}
+            v["mesh"].close()
+        if ref_final is None and "fp64" in finals:
+            ref_final = finals["fp64"]
+        if ref_final is not None:
+            for prec, fin in finals.items():
+                if prec == "fp64":
+                    continue
+                err = _rel_l2_arrays(fin, ref_final)
+                line["variants"][prec]["rel_l2_vs_fp64"] = err
+                line["l2_error"][prec] = {
+                    "rel_l2_per_variable_vs_fp64_after_steps": err,
+                    "steps": args.steps, "tolerance": 1e-5}
     if args.configs and world == 1:
         line["configs"] = other_configs(fr, torch, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -433,8 +462,8 @@ def config_tgv_adaptive(fr, torch, device, attempts=30):
     (Section 3.5): atol = rtol = 1e-6 from dt = 1e-3.  Every attempt is one
     graph (stages + embedded error + norm) plus the host's accept / reject
     decision; the time covers all attempts, rejected ones included."""
-    spec = workload_spec(N_CELLS)
-    mesh = fr.FRMesh(spec, ORDER, physics="ns", gamma=1.4, mu=1.0 / RE,
+    spec = workload_spec(C2_CELLS)
+    mesh = fr.FRMesh(spec, C2_ORDER, physics="ns", gamma=1.4, mu=1.0 / RE,
                      prandtl=PR, precision="fp32", device=device)
     st = torch.cuda.Stream(device=device)
     mesh.set_stream(st)
@@ -469,29 +498,22 @@ def config_tgv_adaptive(fr, torch, device, attempts=30):
     return out
 
 
-def config_tgv48_mixed(fr, torch, device, steps=10, dt=2.5e-4):
-    """TGV on 48^3 perturbed hexes, p=4, RK45 dt 2.5e-4 (1e-3 is beyond the
-    explicit limit at this h and p): mixed precision against the FP64 form
-    after the same steps."""
-    from frinputs import box_hex, ics
-    spec = box_hex((48, 48, 48), hi=(2 * np.pi,) * 3, perturb=0.1)
+def config_tgv32(fr, torch, device, steps=20):
+    """TGV on 32^3 perturbed hexes, p=3, RK45 dt 1e-3: FP64, FP32 and
+    mixed, the reduced forms against the FP64 form after the same steps."""
     out, fin = {}, {}
-    for prec in ("mixed", "fp64"):
-        mesh = fr.FRMesh(spec, 4, physics="ns", mu=1 / RE, prandtl=PR,
-                         precision=prec, device=device)
-        st = torch.cuda.Stream(device=device)
-        mesh.set_stream(st)
-        u0 = _state(mesh, lambda x: ics.taylor_green(x, mach=MACH))
-        mesh.set_solution(u0)
-        mesh.rk_step("rk45", dt, 2)
-        mesh.set_solution(u0)
-        ms = _timed_steps(torch, mesh, st, "rk45", dt, steps)
-        fin[prec] = mesh.get_solution()
-        out[prec] = {"gdof_stage_s": _gdofs(mesh, 5, steps, ms),
-                     "ms_per_step": ms / steps}
-        mesh.close()
-    out["mixed"]["rel_l2_vs_fp64_after_steps"] = _rel_l2(fin["mixed"],
-                                                         fin["fp64"])
+    for prec in ("fp64", "fp32", "mixed"):
+        r = measure(fr, torch, prec, steps, 3, device, None, n=C2_CELLS,
+                    order=C2_ORDER, dt=C2_DT)
+        fin[prec] = r["final"]
+        ne, nu, _ = r["mesh"].info("hex")
+        out[prec] = {"gdof_stage_s": r["units"] / (r["ms"] * 1e-3) / 1e9,
+                     "ms_per_step": r["ms"] / steps,
+                     "kernel_family": r["tuning"][0],
+                     "kernel_ms_per_step": {k: v[0] for k, v in r["prof"].items() if v[1]}}
+        r["mesh"].close()
+    for prec in ("fp32", "mixed"):
+        out[prec]["rel_l2_vs_fp64_after_steps"] = _rel_l2_arrays(fin[prec], fin["fp64"])
     out["steps"] = steps
     return out
 
@@ -533,11 +555,11 @@ def config_tgv_curved(fr, torch, device, steps=10, precisions=("fp64", "fp32")):
     Curved elements run the table-metric families only."""
     from frinputs import curved_box_hex
     t_setup = time.perf_counter()
-    spec = curved_box_hex((N_CELLS,) * 3, hi=(2 * np.pi,) * 3)
+    spec = curved_box_hex((C2_CELLS,) * 3, hi=(2 * np.pi,) * 3)
     out = {}
     for prec in precisions:
         t0 = time.perf_counter()
-        mesh = fr.FRMesh(spec, ORDER, physics="ns", gamma=1.4, mu=1.0 / RE,
+        mesh = fr.FRMesh(spec, C2_ORDER, physics="ns", gamma=1.4, mu=1.0 / RE,
                          prandtl=PR, precision=prec, device=device)
         setup_s = time.perf_counter() - t0
         st = torch.cuda.Stream(device=device)
@@ -561,10 +583,10 @@ def config_tgv_antialias(fr, torch, device, steps=10, qdeg=9,
     """TGV 32^3 p=3 (the bench workload) with the anti-aliased flux of
     Section 3.2: transformed flux at the 125 points of a degree-9 Gauss rule,
     projected back by least squares.  FP64 and FP32, beside collocation."""
-    spec = workload_spec(N_CELLS)
+    spec = workload_spec(C2_CELLS)
     out = {"qdeg": qdeg}
     for prec in precisions:
-        mesh = fr.FRMesh(spec, ORDER, physics="ns", gamma=1.4, mu=1.0 / RE,
+        mesh = fr.FRMesh(spec, C2_ORDER, physics="ns", gamma=1.4, mu=1.0 / RE,
                          prandtl=PR, precision=prec, device=device)
         mesh.set_antialias(qdeg)
         st = torch.cuda.Stream(device=device)
@@ -592,12 +614,12 @@ def config_tgv_partitioned(fr, torch, device, steps=10, parts=(2, 4),
     receive buffers.  Against the unpartitioned mesh: the cost of the
     decomposition and exchange, and the difference after the steps."""
     from paper_2408_16509_gb300 import partition
-    spec = workload_spec(N_CELLS)
+    spec = workload_spec(C2_CELLS)
     out = {}
     for prec in precisions:
         kw = dict(physics="ns", gamma=1.4, mu=1.0 / RE, prandtl=PR,
                   precision=prec, device=device)
-        whole = fr.FRMesh(spec, ORDER, **kw)
+        whole = fr.FRMesh(spec, C2_ORDER, **kw)
         whole.set_variant("sumfact")
         st = torch.cuda.Stream(device=device)
         whole.set_stream(st)
@@ -612,7 +634,7 @@ def config_tgv_partitioned(fr, torch, device, steps=10, parts=(2, 4),
             subs, ids, _ = partition.split(spec, k, "weighted")
             members = []
             for sp in subs:
-                g = fr.FRMesh(sp, ORDER, bcs=partition.exchange_bcs({}), **kw)
+                g = fr.FRMesh(sp, C2_ORDER, bcs=partition.exchange_bcs({}), **kw)
                 g.set_variant("sumfact")
                 g.set_stream(st)
                 members.append(g)
@@ -708,7 +730,7 @@ def config_shu_osher(fr, torch, device, steps=40):
 def other_configs(fr, torch, device):
     out = {}
     for name, fn in (("vortex_8^3_p2_fp64", config_vortex),
-                     ("tgv_48^3_p4_mixed", config_tgv48_mixed),
+                     ("tgv_32^3_p3", config_tgv32),
                      ("mixed_elements_40^3_p3_fp32", config_mixed_elements),
                      ("tgv_32^3_p3_fp32_adaptive", config_tgv_adaptive),
                      ("tgv_32^3_p3_curved", config_tgv_curved),
@@ -723,6 +745,10 @@ def other_configs(fr, torch, device):
 
 
 # ------------------------------------------------------ oracle baseline
+# One single-threaded oracle replica: `warmup` untimed RK45 steps, then RK45
+# steps of a SAMPLE_CELLS^3 box of the workload until `budget` seconds or
+# `max_steps` steps.  The oracle is a serial numpy program; the all-cores
+# figure runs one replica per core at the same time (weak scaling).
 ORACLE_SAMPLE = r"""
 import json, os, sys, time
 sys.path.insert(0, {root!r})
@@ -736,6 +762,8 @@ spec = box_hex((n, n, n), hi=(2*np.pi,)*3, perturb=0.1)
 m = FRMesh(spec.as_dict(), {p})
 s = FRSystem(m, "ns", gamma=1.4, mu=1/{re}, pr={pr})
 u = {{"hex": ics.taylor_green(m.upts_x["hex"].reshape(-1,3), mach={mach}).reshape(m.ne["hex"], -1, 5)}}
+for _ in range({warmup}):
+    u = rk.step(s.rhs, u, {dt}, "rk45")
 steps = 0
 t0 = time.perf_counter()
 while True:
@@ -749,36 +777,73 @@ print(json.dumps({{"steps": steps, "seconds": el, "npts": int(npts)}}))
 """
 
 
-def cpu_baseline(budget):
-    n = 8
-    code = ORACLE_SAMPLE.format(root=ROOT, n=n, p=ORDER, re=RE, pr=PR,
-                                mach=MACH, dt=DT, budget=budget, max_steps=50)
+def _cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return "unknown"
+
+
+def _oracle_replicas(nrep, budget, max_steps, warmup=0):
+    """Run nrep single-threaded oracle replicas at once (fresh interpreters,
+    no CUDA); returns (GDOF-stage/s over all replicas, per-replica records)."""
+    code = ORACLE_SAMPLE.format(root=ROOT, n=SAMPLE_CELLS, p=ORDER, re=RE, pr=PR,
+                                mach=MACH, dt=DT, budget=budget,
+                                max_steps=max_steps, warmup=warmup)
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = "1"
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True,
-                       text=True, env=env, timeout=budget * 10 + 120)
-    if r.returncode != 0:
-        return {"value": None, "error": r.stderr[-300:]}
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    val = d["npts"] * 5 * STAGES * d["steps"] / d["seconds"] / 1e9
-    return {"value": val, "unit": "GDOF-stage/s", "cores": 1,
-            "kind": "oracle",
-            "sample": f"{n}^3-element box of the same workload (p={ORDER}, "
-                      f"NS TGV, RK45), {d['steps']} steps in "
-                      f"{d['seconds']:.1f} s, numpy FP64, 1 thread"}
+    procs = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE,
+                              stderr=subprocess.PIPE, text=True, env=env)
+             for _ in range(nrep)]
+    recs = []
+    for pr_ in procs:
+        out, err = pr_.communicate(timeout=min(budget * 20, 3000.0) + 600)
+        if pr_.returncode != 0:
+            raise RuntimeError(err[-300:])
+        recs.append(json.loads(out.strip().splitlines()[-1]))
+    units = sum(r["npts"] * 5 * STAGES * r["steps"] for r in recs)
+    wall = max(r["seconds"] for r in recs)
+    return units / wall / 1e9, recs
+
+
+def cpu_baseline(budget):
+    cores = os.cpu_count() or 1
+    try:
+        one, r1 = _oracle_replicas(1, budget, 200)
+        allc, ra = _oracle_replicas(cores, budget, 200)
+    except Exception as exc:  # noqa: BLE001 - reported, not fatal
+        return {"value": None, "error": repr(exc)[:300]}
+    return {"value": allc, "unit": "GDOF-stage/s", "cores": cores,
+            "kind": "oracle", "one_core": one, "cpu_model": _cpu_model(),
+            "nproc": cores,
+            "sample": f"{SAMPLE_CELLS}^3-element boxes of the same workload "
+                      f"(p={ORDER}, NS TGV, RK45 dt {DT}), numpy FP64: one "
+                      f"single-threaded replica per core, each about {budget:.0f} s "
+                      f"({ra[0]['steps']} steps on the first); 1 core alone: "
+                      f"{r1[0]['steps']} steps in {r1[0]['seconds']:.1f} s"}
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    cb = cpu_baseline(args.cpu_seconds)
-    val = cb.get("value")
-    line = {"impl": "reference",
-            "metric": "GDOF-stage/s per GB300 (NS FR RHS + RK update)",
+    cores = os.cpu_count() or 1
+    val, recs = _oracle_replicas(cores, 1e9, args.steps, warmup=args.warmup)
+    wall = max(r["seconds"] for r in recs)
+    cb = {"value": val, "unit": "GDOF-stage/s", "cores": cores, "kind": "oracle",
+          "cpu_model": _cpu_model(),
+          "sample": f"{cores} single-threaded replicas, each {args.warmup} untimed "
+                    f"+ {args.steps} timed RK45 steps of a {SAMPLE_CELLS}^3-element "
+                    f"box of the workload (p={ORDER}), numpy FP64"}
+    line = {"impl": "reference", "metric": METRIC,
             "value": val, "unit": "GDOF-stage/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": wall * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "config": config("fp64"),
             "cpu_baseline": cb,
@@ -802,10 +867,13 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", default=None,
-                    choices=["vortex", "tgv48", "mixed", "shu_osher", "adaptive",
+                    choices=["vortex", "tgv32", "mixed", "shu_osher", "adaptive",
                              "curved", "antialias", "partitioned"],
                     help="run one side workload alone and print its record "
                          "(profiling aid; not a contract line)")
+    ap.add_argument("--size", type=int, default=N_CELLS,
+                    help="hexahedra per direction of the main workload (smaller "
+                         "sizes for profiling captures; the contract line is 48)")
     ap.add_argument("--cells", type=int, default=40,
                     help="cells per direction of the mixed-element box (--only mixed)")
     ap.add_argument("--qdeg", type=int, default=0,
@@ -817,13 +885,15 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    global N_CELLS
+    N_CELLS = args.size
     if args.only:
         import torch
         import paper_2408_16509_gb300 as fr
         fr.build()
         dev = 0
         torch.cuda.set_device(dev)
-        fns = {"vortex": config_vortex, "tgv48": config_tgv48_mixed,
+        fns = {"vortex": config_vortex, "tgv32": config_tgv32,
                "adaptive": config_tgv_adaptive,
                "curved": lambda f, t, d: config_tgv_curved(
                    f, t, d, precisions=tuple(args.precisions.split(","))),

@@ -53,6 +53,8 @@ enum { FR_EULER = 0, FR_NAVIER_STOKES = 1 };
 enum { FR_FP64 = 0, FR_FP32 = 1, FR_MIXED = 2 };
 enum { FR_BC_STATE = 0, FR_BC_EXTRAPOLATE = 1, FR_BC_EXCHANGE = 2 };
 enum { FR_RK4 = 0, FR_RK45 = 1 };
+/* Line points of hexahedra (fr_mesh_desc.point_family). */
+enum { FR_POINTS_GL = 0, FR_POINTS_GLL = 1 };
 
 typedef struct fr_mesh fr_mesh;
 typedef struct fr_group fr_group;
@@ -107,6 +109,16 @@ typedef struct {
                                      host-only handle (geometry, points and
                                      operators; no GPU is touched and the
                                      compute calls return FR_EINVAL) */
+  int point_family;               /* hexahedra: FR_POINTS_GL (0, default)
+                                     Gauss-Legendre solution and flux
+                                     points; FR_POINTS_GLL Gauss-Lobatto
+                                     solution points with the flux points
+                                     among them, so the interpolation of
+                                     Eq. (disu) is a gather (Section 3.1,
+                                     "Matrix multiplications", last
+                                     paragraph).  GLL needs a mesh without
+                                     prisms (FR_EINVAL): their quad faces
+                                     carry Gauss-Legendre points */
 } fr_mesh_desc;
 
 /* Build a discretisation (Section 2: conforming tessellation, reference
@@ -456,6 +468,15 @@ int fr_mlp_train(int device, const float* x, const float* zstar, int64_t n,
  * zeros for the normalisation entries). */
 int fr_mlp_loss_grad(int device, const float* params, const float* x,
                      const float* zstar, int64_t n, float* loss, float* grad);
+
+/* Measurement aid for the arithmetic roofline (the paper has no
+ * counterpart): one launch of 8 x (number of SMs) blocks of 256 threads,
+ * each thread running eight independent chains of `iters` fused
+ * multiply-adds in FR_DTYPE_F64 or FR_DTYPE_F32, after one shorter warm-up
+ * launch.  *ms: device time of the timed launch (CUDA events), *flops:
+ * 2 * 8 * iters * threads.  Allocates and frees a small output buffer on
+ * `device`; synchronous. */
+int fr_probe_fma(int device, int dtype, int64_t iters, double* ms, double* flops);
 
 /* Message of the last failed call on this thread. */
 const char* fr_last_error(void);

@@ -55,7 +55,8 @@ class MeshDesc(C.Structure):
                 ("bface_nodes", C.POINTER(C.c_int64)),
                 ("bface_tags", C.POINTER(C.c_int)),
                 ("n_bcs", C.c_int), ("bcs", C.POINTER(BCDesc)),
-                ("precision", C.c_int), ("device", C.c_int)]
+                ("precision", C.c_int), ("device", C.c_int),
+                ("point_family", C.c_int)]
 
 
 _lib = None
@@ -84,6 +85,7 @@ def load():
         "fr_get_solution_device": (I, [P, I, P, I]),
         "fr_rhs": (I, [P, D, P, P]),
         "fr_stats": (I, [P, C.POINTER(Stats), I]),
+        "fr_probe_fma": (I, [I, I, C.c_int64, C.POINTER(D), C.POINTER(D)]),
         "fr_get_rhs": (I, [P, I, P]),
         "fr_rk_step": (I, [P, I, D, I]),
         "fr_rk_adaptive_step": (I, [P, C.POINTER(AdaptCtl), C.POINTER(D),
@@ -159,10 +161,13 @@ class FRMesh:
     spec: dict with ``nodes``, ``elements`` ({'hex'|'pri'|'tet': conn}),
     ``periodic`` (translation vectors) and ``bfaces`` ([(node ids, tag)]).
     bcs: {tag: ('state', rho, u, v, w, p) | ('extrap',)}.
+    family: hexahedron line points, 'gl' (Gauss-Legendre) or 'gll'
+    (Gauss-Lobatto: flux points among the solution points).
     """
 
     def __init__(self, spec, order, physics="euler", gamma=1.4, mu=0.0,
-                 prandtl=0.72, bcs=None, precision="fp64", device=0):
+                 prandtl=0.72, bcs=None, precision="fp64", device=0,
+                 family="gl"):
         lib = load()
         if hasattr(spec, "as_dict"):
             spec = spec.as_dict()
@@ -220,6 +225,7 @@ class FRMesh:
         d.bcs = bc_arr
         d.precision = PRECISION[precision]
         d.device = int(device)
+        d.point_family = {"gl": 0, "gll": 1}[family]
         h = C.c_void_p()
         _check(lib.fr_mesh_create(C.byref(d), C.byref(h)))
         self._h = h
@@ -557,6 +563,18 @@ class FRGroup:
             self.close()
         except Exception:
             pass
+
+
+def probe_fma(dtype="fp64", iters=None, device=0):
+    """Fused multiply-add throughput of the device (fr_probe_fma): returns
+    (TFLOP/s, ms, flops) of one timed launch."""
+    code = {"fp64": FR_DTYPE_F64, "fp32": FR_DTYPE_F32}[dtype]
+    if iters is None:
+        iters = 20000 if dtype == "fp64" else 400000
+    ms, fl = C.c_double(), C.c_double()
+    _check(load().fr_probe_fma(int(device), code, int(iters), C.byref(ms),
+                               C.byref(fl)))
+    return fl.value / (ms.value * 1e-3) / 1e12, ms.value, fl.value
 
 
 def mlp_train(x, zstar, params, epochs, lr, device=0):

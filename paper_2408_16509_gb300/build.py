@@ -20,7 +20,7 @@ LIB = os.path.join(OUT_DIR, "libfrgb.so")
 
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 CXX_SRCS = ["fr_ref.cpp", "fr_mesh.cpp", "fr_part.cpp"]
-CU_SRCS = ["fr_api.cu", "fr_prec_f64.cu", "fr_prec_f32.cu", "fr_prec_mix.cu"]
+CU_SRCS = ["fr_api.cu", "fr_prec_f64.cu", "fr_prec_f32.cu", "fr_prec_mix.cu", "fr_probe.cu"]
 
 
 def _nvcc():

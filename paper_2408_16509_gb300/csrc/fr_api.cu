@@ -44,6 +44,9 @@ int fr_mesh_create(const fr_mesh_desc* d, fr_mesh** out) {
   in.n_nodes = d->n_nodes;
   in.nodes = d->nodes;
   in.order = d->order;
+  if (d->point_family != FR_POINTS_GL && d->point_family != FR_POINTS_GLL)
+    return fail(FR_EINVAL, "unknown point family");
+  in.family = d->point_family;
   bool seen[3] = {false, false, false};
   for (int i = 0; i < d->n_etypes; ++i) {
     const fr_etype_desc& t = d->etypes[i];
@@ -55,6 +58,8 @@ int fr_mesh_create(const fr_mesh_desc* d, fr_mesh** out) {
     if (t.map_order == 2 && (t.etype != FR_HEX8 || (t.n_elem > 0 && !t.map_conn)))
       return fail(FR_EINVAL, "quadratic maps: hexahedra with map_conn only");
     seen[t.etype] = true;
+    if (t.etype == FR_PRI6 && t.n_elem > 0 && d->point_family == FR_POINTS_GLL)
+      return fail(FR_EINVAL, "Gauss-Lobatto hexahedra cannot meet prisms (their quad faces carry Gauss-Legendre points)");
   }
   for (int k = 0; k < 3; ++k)  // canonical type order: hex, prism, tet
     for (int i = 0; i < d->n_etypes; ++i)

@@ -24,7 +24,9 @@ struct HexOps {
   T d1[8][8];  // d1[a][m] = l_m'(x_a)
   T lm[8], lp[8];  // l_m(-1), l_m(+1)
   T gl[8], gr[8];  // correction weights of the minus / plus face
-  T xg[8];         // the Gauss-Legendre points themselves
+  T xg[8];         // the line points themselves
+  int gather;      // 1: Gauss-Lobatto lines, the face points are the line
+                   //    end points (interpolation to a face is a copy)
 };
 
 // register type used for the RK solution / accumulator registers
@@ -162,6 +164,12 @@ __device__ __forceinline__ void face_interp(const T* src, int fp,
   const int NF1 = N * N;
   int face = fp / NF1, r = fp - face * NF1;
   int i = r % N, j = r / N;
+  if (op.gather) {  // Gauss-Lobatto: the face point is a solution point
+    const int q = line_pt<N>(face, i, j, (face & 1) ? N - 1 : 0);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) out[k] = src[k * N * N * N + q];
+    return;
+  }
   const T* w = (face & 1) ? op.lp : op.lm;
 #pragma unroll
   for (int k = 0; k < NV; ++k) out[k] = T(0);

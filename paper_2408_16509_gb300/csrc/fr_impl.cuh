@@ -23,26 +23,13 @@
 #include "fr_filter.cuh"
 #include "fr_hex.cuh"
 #include "fr_kernels.cuh"
+#include "fr_err.hpp"
 #include "fr_mesh.hpp"
 
 using namespace frgb;
 
 namespace frgb {
 
-// message of the last failed call, one per thread, shared by every unit
-inline thread_local std::string g_err;
-
-inline int fail(int code, const std::string& msg) {
-  g_err = msg;
-  return code;
-}
-
-#define CK(call)                                                        \
-  do {                                                                  \
-    cudaError_t e_ = (call);                                            \
-    if (e_ != cudaSuccess)                                              \
-      return fail(FR_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
-  } while (0)
 
 // Compile-time (nupts, nfpts) for every supported (element kind, order).
 template <class F>
@@ -295,6 +282,7 @@ HexOps<T> hex_ops(const RefElement& R) {
     h.gr[a] = T(R.gr[a]);
     h.xg[a] = T(R.x1[a]);
   }
+  h.gather = R.family == 1;
   return h;
 }
 

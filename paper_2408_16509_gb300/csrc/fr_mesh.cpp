@@ -370,7 +370,7 @@ std::string build_mesh(const MeshInput& in, std::vector<HostType>& types,
     HostType T;
     T.kind = t.first;
     T.ne = t.second.first;
-    T.ref = make_ref(T.kind, in.order);
+    T.ref = make_ref(T.kind, in.order, T.kind == EK_HEX ? in.family : 0);
     const int nv = T.ref.nverts;
     T.conn.assign(t.second.second, t.second.second + size_t(T.ne) * nv);
     for (int64_t v : T.conn)

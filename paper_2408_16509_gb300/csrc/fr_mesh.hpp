@@ -57,6 +57,7 @@ struct MeshInput {
   int64_t n_nodes = 0;
   const double* nodes = nullptr;
   int order = 0;
+  int family = 0;                       // hexahedron line points: 0 GL, 1 GLL
   std::vector<std::pair<int, std::pair<int64_t, const int64_t*>>> types;
   std::vector<int> map_order;               // per entry of types: 1 or 2
   std::vector<const int64_t*> map_conn;     // per entry: [ne][27] or null

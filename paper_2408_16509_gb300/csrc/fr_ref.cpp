@@ -614,13 +614,22 @@ static RefFace mkface(bool tri, std::initializer_list<int> verts,
 }
 
 // 2D face point sets in face coordinates (s, t)
-static std::vector<double> face_points(const RefFace& f, int p) {
+// 1D line points of a tensor direction: Gauss-Legendre, or Gauss-Lobatto
+static std::vector<double> line_points(int p, int family) {
+  std::vector<double> x(p + 1), w(p + 1);
+  if (family == 1)
+    gauss_lobatto(p + 1, x.data());
+  else
+    gauss_legendre(p + 1, x.data(), w.data());
+  return x;
+}
+
+static std::vector<double> face_points(const RefFace& f, int p, int family) {
   if (f.tri) {
     double a = p <= 15 ? kAlpha3D[std::max(p, 1) - 1] : 1.0;
     return tri_nodes(p, a);
   }
-  std::vector<double> x(p + 1), w(p + 1), out;
-  gauss_legendre(p + 1, x.data(), w.data());
+  std::vector<double> x = line_points(p, family), out;
   for (int j = 0; j <= p; ++j)
     for (int i = 0; i <= p; ++i) {
       out.push_back(x[i]);
@@ -692,11 +701,14 @@ static void volume_rule(int kind, int n, std::vector<double>& xq,
       }
 }
 
-RefElement make_ref(int kind, int p) {
+RefElement make_ref(int kind, int p, int family) {
   if (p < 1 || p > 8) throw std::invalid_argument("order out of range");
+  if (family != 0 && (family != 1 || kind != EK_HEX))
+    throw std::invalid_argument("Gauss-Lobatto points are for hexahedra only");
   RefElement e;
   e.kind = kind;
   e.p = p;
+  e.family = family;
   const double r2 = 1.0 / std::sqrt(2.0), r3 = 1.0 / std::sqrt(3.0);
   if (kind == EK_HEX) {
     e.nverts = 8;
@@ -706,8 +718,7 @@ RefElement make_ref(int kind, int p) {
                mkface(false, {3, 2, 6, 7}, {0, 1, 0}, {1, 0, 0}, {0, 0, 1}, {0, 1, 0}),
                mkface(false, {0, 1, 2, 3}, {0, 0, -1}, {1, 0, 0}, {0, 1, 0}, {0, 0, -1}),
                mkface(false, {4, 5, 6, 7}, {0, 0, 1}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1})};
-    std::vector<double> x(p + 1), w(p + 1);
-    gauss_legendre(p + 1, x.data(), w.data());
+    std::vector<double> x = line_points(p, family);
     for (int k = 0; k <= p; ++k)
       for (int j = 0; j <= p; ++j)
         for (int i = 0; i <= p; ++i) e.upts.insert(e.upts.end(), {x[i], x[j], x[k]});
@@ -753,7 +764,7 @@ RefElement make_ref(int kind, int p) {
   std::vector<std::vector<double>> fst(e.nfaces);
   for (int fi = 0; fi < e.nfaces; ++fi) {
     const RefFace& f = e.faces[fi];
-    fst[fi] = face_points(f, p);
+    fst[fi] = face_points(f, p, family);
     int n = int(fst[fi].size() / 2);
     for (int q = 0; q < n; ++q) {
       double s = fst[fi][2 * q], t = fst[fi][2 * q + 1];
@@ -850,9 +861,7 @@ RefElement make_ref(int kind, int p) {
   }
   if (kind == EK_HEX) {
     int n = p + 1;
-    e.x1.resize(n);
-    std::vector<double> w(n);
-    gauss_legendre(n, e.x1.data(), w.data());
+    e.x1 = line_points(p, family);
     e.d1.resize(n * n);
     e.lm.resize(n);
     e.lp.resize(n);

@@ -39,10 +39,11 @@ struct RefElement {
   std::vector<double> W;           // [nupts]  integration weights
   std::vector<double> vdm_inv;     // [nupts][nupts] modal <- nodal
   std::vector<int> mdeg;           // [nupts] total degree of each mode
-  // hexahedron only: 1D factors on the Gauss-Legendre points x1
+  // hexahedron only: 1D factors on the line points x1
   std::vector<double> x1;          // [p+1]
   std::vector<double> d1;          // [p+1][p+1]  l_m'(x_a)
   std::vector<double> lm, lp;      // [p+1]  l_m(-1), l_m(+1)
+  int family = 0;                  // 0 Gauss-Legendre, 1 Gauss-Lobatto lines
   std::vector<double> gl, gr;      // [p+1]  correction derivative weights:
                                    //  -g_L'(x_a) on x=-1, g_R'(x_a) on x=+1
   // vertex map of the element type
@@ -53,7 +54,8 @@ struct RefElement {
   void grad(int npts, const double* x, double* out) const;            // [3][npts][nm]
 };
 
-RefElement make_ref(int kind, int p);
+// family 0: Gauss-Legendre line points; 1: Gauss-Lobatto (hexahedra only)
+RefElement make_ref(int kind, int p, int family = 0);
 
 // 1D helpers (exposed for unit use)
 void gauss_legendre(int n, double* x, double* w);

@@ -59,6 +59,8 @@ def test_rhs_rejects_a_non_finite_time():
 
 SPECS = {
     "hex": lambda: box_hex((3, 2, 2), perturb=0.1),
+    "hex-gll": lambda: box_hex((3, 2, 2), perturb=0.1),
+    "curved-gll": lambda: curved_box_hex((3, 2, 2)),
     "mixed": lambda: mixed_box(n=3, x_pri=0.34, x_tet=0.67, perturb=0.05),
     "curved": lambda: curved_box_hex((3, 2, 2)),
 }
@@ -68,9 +70,10 @@ SPECS = {
 @pytest.mark.parametrize("p", [1, 2, 3, 4])
 def test_host_setup_matches_oracle(name, p):
     spec = SPECS[name]()
+    fam = "gll" if name.endswith("-gll") else "gl"
     bcs = {k: ("state", 1.0, 0.0, 0.0, 0.0, 1.0) for k in range(6)}
-    g = fr.FRMesh(spec, p, bcs=bcs, device=-1)
-    o = OracleMesh(spec.as_dict(), p)
+    g = fr.FRMesh(spec, p, bcs=bcs, device=-1, family=fam)
+    o = OracleMesh(spec.as_dict(), p, family=fam)
     assert g.types == o.types
     for t in g.types:
         el = o.el[t]
@@ -88,6 +91,12 @@ def test_host_setup_matches_oracle(name, p):
         assert np.abs(rj * o.detJ[t] - 1).max() < 1e-13
     npair, nb = g.pair_counts()
     assert npair == len(o.pair_l) and nb == len(o.bnd_g)
+
+
+def test_gll_family_rejects_prisms():
+    with pytest.raises(fr.FRError) as e:
+        fr.FRMesh(mixed_box(n=3, x_pri=0.34, x_tet=0.67), 2, device=-1, family="gll")
+    assert e.value.name == "FR_EINVAL"
 
 
 def test_nonconforming_mesh_is_rejected():
