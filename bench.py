@@ -853,6 +853,7 @@ def run_reference(args):
 
 
 def main():
+    global N_CELLS
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -885,7 +886,6 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    global N_CELLS
     N_CELLS = args.size
     if args.only:
         import torch
