@@ -284,6 +284,35 @@ int fr_set_kernel_variant(fr_mesh* mesh, int variant);
  * measured, ms_per_step[5] indexed by FR_VARIANT_* (entry 0 unused). */
 int fr_get_tuning(const fr_mesh* mesh, int* active, float* ms_per_step);
 
+/* Tiles and schedule of the kernels (Section 3.1, "Matrix
+ * multiplications": configurations benchmarked at run time, the fastest
+ * kept; "Task graphs": independent kernels run in parallel).  Indexed by
+ * element kind (FR_HEX8, FR_PRI6, FR_TET4):
+ *   tile_grad, tile_vol: gradient / volume kernel tile: elements per CTA of
+ *     the sum-factorised hexahedron kernels (at most 256 threads per CTA),
+ *     persistent CTAs per SM of the dense kernels; 0 = the largest (default),
+ *     -1 = no such element in the mesh;
+ *   tensor_grad, tensor_vol: 1 when that kernel runs on the tensor cores.
+ * face_block: threads per CTA of the interface and boundary kernels (32..1024,
+ * a multiple of 32); parallel_types: the per-type kernels of a phase run as
+ * parallel branches of the step's graph (forked streams) instead of in
+ * order.  ms_default / ms_tuned: step time of the picked family with the
+ * default and the tuned schedule (0 until the autotuner ran).  With
+ * FR_VARIANT_AUTO the first fr_rk_step tunes all of it after picking the
+ * family; every schedule gives the same results bit for bit. */
+typedef struct {
+  int tile_grad[3], tile_vol[3];
+  int tensor_grad[3], tensor_vol[3];
+  int face_block;
+  int parallel_types;
+  float ms_default, ms_tuned;
+} fr_schedule_t;
+int fr_get_schedule(const fr_mesh* mesh, fr_schedule_t* out);
+/* Set the tiles and schedule (tensor_*, ms_* are ignored); FR_EINVAL for a
+ * tile above the kernel's maximum, a bad block size, or a host-only handle.
+ * Later steps rebuild their graphs. */
+int fr_set_schedule(fr_mesh* mesh, const fr_schedule_t* in);
+
 /* Kernels and copies of the handle run on this stream (cudaStream_t);
  * NULL selects the handle's own stream. */
 int fr_set_stream(fr_mesh* mesh, void* cuda_stream);

@@ -85,6 +85,8 @@ def load():
         "fr_get_solution_device": (I, [P, I, P, I]),
         "fr_rhs": (I, [P, D, P, P]),
         "fr_stats": (I, [P, C.POINTER(Stats), I]),
+        "fr_get_schedule": (I, [P, C.POINTER(Schedule)]),
+        "fr_set_schedule": (I, [P, C.POINTER(Schedule)]),
         "fr_probe_fma": (I, [I, I, C.c_int64, C.POINTER(D), C.POINTER(D)]),
         "fr_get_rhs": (I, [P, I, P]),
         "fr_rk_step": (I, [P, I, D, I]),
@@ -143,6 +145,14 @@ class Stats(C.Structure):
                 ("ms_kernel", C.c_double * FR_KC_COUNT),
                 ("launches", C.c_int * FR_KC_COUNT),
                 ("kernel_family", C.c_int), ("t_last", C.c_double)]
+
+
+class Schedule(C.Structure):
+    """fr_schedule_t."""
+    _fields_ = [("tile_grad", C.c_int * 3), ("tile_vol", C.c_int * 3),
+                ("tensor_grad", C.c_int * 3), ("tensor_vol", C.c_int * 3),
+                ("face_block", C.c_int), ("parallel_types", C.c_int),
+                ("ms_default", C.c_float), ("ms_tuned", C.c_float)]
 
 
 class AdaptCtl(C.Structure):
@@ -386,6 +396,35 @@ class FRMesh:
         names = {v: k for k, v in VARIANTS.items()}
         return names[a.value], {names[i]: float(ms[i]) for i in range(1, 5)
                                 if ms[i] > 0}
+
+    def schedule(self):
+        """Tiles and schedule of the kernels (fr_get_schedule): per element
+        type {'grad': tile, 'vol': tile, 'tensor_grad': bool, 'tensor_vol':
+        bool}, plus 'face_block', 'parallel_types', 'ms_default',
+        'ms_tuned'."""
+        sc = Schedule()
+        _check(load().fr_get_schedule(self._h, C.byref(sc)))
+        out = {"face_block": sc.face_block,
+               "parallel_types": bool(sc.parallel_types),
+               "ms_default": sc.ms_default, "ms_tuned": sc.ms_tuned}
+        for name, k in ETYPES.items():
+            if sc.tile_grad[k] >= 0:
+                out[name] = {"grad": sc.tile_grad[k], "vol": sc.tile_vol[k],
+                             "tensor_grad": bool(sc.tensor_grad[k]),
+                             "tensor_vol": bool(sc.tensor_vol[k])}
+        return out
+
+    def set_schedule(self, tiles=None, face_block=256, parallel_types=False):
+        """tiles: {etype: (grad tile, vol tile)}; others keep 0 (default)."""
+        sc = Schedule()
+        cur = self.schedule()
+        for name, k in ETYPES.items():
+            if name in cur:
+                g, v = (tiles or {}).get(name, (cur[name]["grad"], cur[name]["vol"]))
+                sc.tile_grad[k], sc.tile_vol[k] = int(g), int(v)
+        sc.face_block = int(face_block)
+        sc.parallel_types = int(bool(parallel_types))
+        _check(load().fr_set_schedule(self._h, C.byref(sc)))
 
     def set_variant(self, name):
         """Kernel family: 'auto', 'dense', 'sumfact', 'sumfact_vertex' or

@@ -514,6 +514,60 @@ int fr_get_tuning(const fr_mesh* m, int* active, float* ms) {
   return FR_OK;
 }
 
+int fr_get_schedule(const fr_mesh* m, fr_schedule_t* out) {
+  if (!m || !out) return fail(FR_EINVAL, "null argument");
+  std::memset(out, 0, sizeof(*out));
+  for (int k = 0; k < 3; ++k) {
+    out->tile_grad[k] = out->tile_vol[k] = -1;
+    const int t = m->type_of_kind[k];
+    if (t < 0 || m->host_only) continue;
+    const DevType& D = m->types[t];
+    out->tile_grad[k] = D.tile_grad;
+    out->tile_vol[k] = D.tile_vol;
+    out->tensor_grad[k] = use_tc_grad(m, D) ? 1 : 0;
+    out->tensor_vol[k] = use_tc_vol(m, D) ? 1 : 0;
+  }
+  out->face_block = m->face_tb;
+  out->parallel_types = m->par_types ? 1 : 0;
+  out->ms_default = m->sched_ms[0];
+  out->ms_tuned = m->sched_ms[1];
+  return FR_OK;
+}
+
+int fr_set_schedule(fr_mesh* m, const fr_schedule_t* in) {
+  if (!m || !in) return fail(FR_EINVAL, "null argument");
+  if (m->host_only) return fail(FR_EINVAL, "host-only handle (device < 0)");
+  if (in->face_block < 32 || in->face_block > 1024 || in->face_block % 32)
+    return fail(FR_EINVAL, "face_block must be a multiple of 32 in 32..1024");
+  for (int k = 0; k < 3; ++k) {
+    const int t = m->type_of_kind[k];
+    if (t < 0) continue;
+    const DevType& D = m->types[t];
+    const bool hexk = D.kind == EK_HEX && m->active != FR_VARIANT_DENSE;
+    const int mg = hexk ? hex_tile_max(m->order) : D.grad_ctas;
+    const int mv = hexk ? hex_tile_max(m->order) : D.vol_ctas;
+    if (in->tile_grad[k] < 0 || in->tile_grad[k] > mg || in->tile_vol[k] < 0 ||
+        in->tile_vol[k] > mv)
+      return fail(FR_EINVAL, "tile out of range for this kernel");
+  }
+  CK(cudaSetDevice(m->device));
+  if (in->parallel_types) {
+    int rc = ensure_par(m);
+    if (rc) return rc;
+  }
+  CK(cudaStreamSynchronize(m->stream));
+  for (int k = 0; k < 3; ++k) {
+    const int t = m->type_of_kind[k];
+    if (t < 0) continue;
+    m->types[t].tile_grad = in->tile_grad[k];
+    m->types[t].tile_vol = in->tile_vol[k];
+  }
+  m->face_tb = in->face_block;
+  m->par_types = in->parallel_types != 0;
+  ++m->epoch;
+  return FR_OK;
+}
+
 int fr_set_stream(fr_mesh* m, void* s) {
   if (!m) return fail(FR_EINVAL, "null mesh");
   if (m->host_only) return fail(FR_EINVAL, "host-only handle (device < 0)");

@@ -11,7 +11,8 @@
 // the paper's matrix-multiplication paragraph, done by construction.
 //
 // Thread mapping: one thread per solution point (a, b, c), point index
-// a + N b + N^2 c; EPB elements per CTA.  Flux point index
+// a + N b + N^2 c; blockDim.x / NU elements per CTA (at most EPB, the
+// launch bound; the autotuner picks the tile).  Flux point index
 // face * N^2 + i + N j, faces x-, x+, y-, y+, z-, z+ with (i, j) the two
 // tangential indices in (y,z), (x,z), (x,y) order.
 #pragma once
@@ -205,7 +206,7 @@ __global__ void __launch_bounds__(EPB* N* N* N)
   constexpr int NU = N * N * N, NF = 6 * N * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int le = threadIdx.x / NU, z = threadIdx.x - le * NU;
-  const long long e = (long long)blockIdx.x * EPB + le;
+  const long long e = (long long)blockIdx.x * (blockDim.x / NU) + le;
   T* us = reinterpret_cast<T*>(smem_raw + le * hex_grad_bytes_per_elem<T, N, QV>());
   T* ds = us + 5 * NU;
   T* gs = ds + 5 * NF;
@@ -338,7 +339,7 @@ __global__ void __launch_bounds__(EPB* N* N* N)
   constexpr int NU = N * N * N, NF = 6 * N * N, N2 = N * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int le = threadIdx.x / NU, z = threadIdx.x - le * NU;
-  const long long e = (long long)blockIdx.x * EPB + le;
+  const long long e = (long long)blockIdx.x * (blockDim.x / NU) + le;
   unsigned char* eb = smem_raw + le * hex_vol_bytes_per_elem<T, TR, N>();
   T* ft = reinterpret_cast<T*>(eb);       // [3][5][NU]
   T* jm = ft + 15 * NU;                   // [5][NF]: F^C, then the jump
@@ -585,7 +586,7 @@ __global__ void __launch_bounds__(EPB* N* N* N)
   extern __shared__ unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int le = threadIdx.x / NU, z = threadIdx.x - le * NU;
-  const long long e = (long long)blockIdx.x * EPB + le;
+  const long long e = (long long)blockIdx.x * (blockDim.x / NU) + le;
   T* us = sm + le * (5 * NU + 5 * NF + 15 * NU + 24);
   T* ds = us + 5 * NU;
   T* gs = ds + 5 * NF;
@@ -660,7 +661,7 @@ __global__ void __launch_bounds__(EPB* N* N* N)
   extern __shared__ unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int le = threadIdx.x / NU, z = threadIdx.x - le * NU;
-  const long long e = (long long)blockIdx.x * EPB + le;
+  const long long e = (long long)blockIdx.x * (blockDim.x / NU) + le;
   T* ft = sm + le * (15 * NU + 5 * NF + 5 * NU + 5 * NF + 24);
   T* jm = ft + 15 * NU;
   T* us = jm + 5 * NF;

@@ -106,6 +106,9 @@ struct DevType {
   float* zeta_last = nullptr;
   int* evals_last = nullptr;
   int grad_ctas = 1, vol_ctas = 1;  // resident CTAs per SM (dense kernels)
+  // tiles picked by the autotuner (0: the default, the largest): elements per
+  // CTA of the hexahedron kernels, persistent CTAs per SM of the dense ones
+  int tile_grad = 0, tile_vol = 0;
   void* fnv = nullptr;       // [ne][3][nf] S^T n~ at flux points (NS)
   int8_t* fbc = nullptr;     // [ne][nf] boundary-condition index or -1 (NS)
   void* verts = nullptr;     // [ne][8][3] vertices minus vertex 0 (hex, FP32)
@@ -221,11 +224,23 @@ struct fr_mesh {
   int ev_head = 0, ev_count = 0;
   double prof_ms[FR_KC_COUNT] = {};
   int prof_launches[FR_KC_COUNT] = {};
+  // schedule picked by the autotuner: threads per CTA of the interface and
+  // boundary kernels, and whether the per-type kernels of a phase run as
+  // parallel branches (streams forked and joined inside the captured graph)
+  int face_tb = 256;
+  bool par_types = false;
+  std::vector<cudaStream_t> par_st;
+  std::vector<cudaEvent_t> par_ev;
+  float sched_ms[2] = {0.f, 0.f};  // step time before / after tile tuning
   std::vector<void*> allocs;
   void* d_staging = nullptr;   // host-layout FP64 staging for set/get
   size_t staging_bytes = 0;
 
   ~fr_mesh() {
+    for (cudaStream_t st : par_st)
+      if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : par_ev)
+      if (ev) cudaEventDestroy(ev);
     for (int i = 0; i < kEvRing; ++i) {
       if (ev_a[i]) cudaEventDestroy(ev_a[i]);
       if (ev_b[i]) cudaEventDestroy(ev_b[i]);
@@ -900,6 +915,45 @@ void launch_entropy_min(fr_mesh* m, cudaStream_t s, bool from_x);
 template <typename T, typename TR>
 void launch_filter(fr_mesh* m, cudaStream_t s, DevType& D, bool last_stage);
 
+// Streams and events of the parallel per-type branches (created once).
+inline int ensure_par(fr_mesh* m) {
+  const size_t nt = m->types.size();
+  while (m->par_st.size() < nt) {
+    cudaStream_t st = nullptr;
+    CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    m->par_st.push_back(st);
+  }
+  while (m->par_ev.size() < nt + 1) {
+    cudaEvent_t ev = nullptr;
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    m->par_ev.push_back(ev);
+  }
+  return FR_OK;
+}
+
+// Largest elements-per-CTA tile of the hexahedron kernels at order p (the
+// kernels' launch bound) and the tiles the autotuner tries: its divisors
+// down to one element.
+inline int hex_tile_max(int p) {
+  const int nu = (p + 1) * (p + 1) * (p + 1);
+  return nu >= 256 ? 1 : 256 / nu;
+}
+
+inline std::vector<int> tile_candidates(const fr_mesh* m, const DevType& D, bool grad) {
+  std::vector<int> c;
+  if (D.kind == EK_HEX && m->active != FR_VARIANT_DENSE) {
+    const int e = hex_tile_max(m->order);
+    for (int k = e; k >= 1; k = k > 1 ? (k % 2 == 0 ? k / 2 : (k % 3 == 0 ? k / 3 : 1)) : 0) {
+      c.push_back(k);
+      if (k == 1) break;
+    }
+  } else {
+    const int mx = grad ? D.grad_ctas : D.vol_ctas;
+    for (int k = mx; k >= 1; k /= 2) c.push_back(k);
+  }
+  return c;
+}
+
 // Launch one RK stage (or a bare right-hand side when mode == 0).  phase
 // bit 1: the NS common solution and gradients; bit 2: the common fluxes and
 // the volume kernels.  A partitioned group exchanges the gradient traces
@@ -910,7 +964,23 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
   const bool ns = m->physics == FR_NAVIER_STOKES;
   const Phys<T> ph = phys<T>(m);
   const BCTab<T>& bc = bctab<T>(m);
-  const int tb = 256;
+  const int tb = m->face_tb;
+  // the per-type kernels of a phase: in order on s, or (schedule par_types,
+  // not while profiling) as parallel branches forked from and joined to s
+  auto per_type = [&](auto&& fn) {
+    const size_t nt = m->types.size();
+    if (!m->par_types || prof || nt < 2 || m->par_st.size() < nt) {
+      for (auto& D : m->types) fn(D, s);
+      return;
+    }
+    cudaEventRecord(m->par_ev[0], s);
+    for (size_t t = 0; t < nt; ++t) {
+      cudaStreamWaitEvent(m->par_st[t], m->par_ev[0], 0);
+      fn(m->types[t], m->par_st[t]);
+      cudaEventRecord(m->par_ev[1 + t], m->par_st[t]);
+    }
+    for (size_t t = 0; t < nt; ++t) cudaStreamWaitEvent(s, m->par_ev[1 + t], 0);
+  };
   // stage input: the solution register X for a bare RHS and the first
   // stage, the stage register Y afterwards
   const bool from_x = (mode == 0 || stage == 0);
@@ -935,7 +1005,7 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
           (const T*)m->xu, ph.beta);
       PROF_END(FR_KC_BND_U);
     }
-    for (auto& D : m->types) {
+    per_type([&](DevType& D, cudaStream_t s) {
       const T* du = (const T*)m->du + D.off_f;
       ViscArgs<T> va{(const T*)m->uf + D.off_f, (const T*)D.fnv, D.fbc,
                      (T*)m->gradf + D.off_f * (sizeof(T) == 4 ? 1 : 3)};
@@ -945,8 +1015,9 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
         hex_dispatch(m->order, [&](auto n) {
           constexpr int N = decltype(n)::value;
           constexpr int E = hex_epb<N>();
+          const int eb = D.tile_grad > 0 ? D.tile_grad : E;
           k_hex_grad_v<T, TR, N, E>
-              <<<nblk(D.ne, E), E * N * N * N, hexv_grad_smem<T, N>(), s>>>(
+              <<<nblk(D.ne, eb), eb * N * N * N, hexv_grad_smem<T, N>() / E * eb, s>>>(
                   D.ne, from_x ? nullptr : (const T*)D.Y, (const TR*)D.X, du,
                   (const T*)D.verts, hexops<T>(D), va, bc, ph);
         });
@@ -954,8 +1025,9 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
         hex_dispatch(m->order, [&](auto n) {
           constexpr int N = decltype(n)::value;
           constexpr int E = hex_epb<N>();
+          const int eb = D.tile_grad > 0 ? D.tile_grad : E;
           k_hex_grad<T, TR, N, E, sizeof(T) == 4>
-              <<<nblk(D.ne, E), E * N * N * N, hex_grad_smem<T, N>(), s>>>(
+              <<<nblk(D.ne, eb), eb * N * N * N, hex_grad_smem<T, N>() / E * eb, s>>>(
                   D.ne, from_x ? nullptr : (const T*)D.Y, (const TR*)D.X, du,
                   (const T*)D.smat, (const T*)D.rcpdjac, hexops<T>(D),
                   (T*)D.grad, va, bc, ph);
@@ -968,7 +1040,8 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
           constexpr int E = dense_epb<NU>();
           const size_t sm = dense_grad_smem<T, NU, NF>();
           const unsigned grid = unsigned(std::min<long long>(
-              (D.ne + E - 1) / E, (long long)m->num_sms * D.grad_ctas));
+              (D.ne + E - 1) / E,
+              (long long)m->num_sms * (D.tile_grad > 0 ? D.tile_grad : D.grad_ctas)));
           k_grad_dense<T, NU, NF, E, sizeof(T) == 4><<<grid, E * NU, sm, s>>>(
               D.ne, from_x ? (const T*)D.X : (const T*)D.Y, du,
               (const T*)D.smat, (const T*)D.rcpdjac, ops_of<T>(D), (T*)D.grad,
@@ -976,7 +1049,7 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
         });
       }
       PROF_END(FR_KC_GRAD);
-    }
+    });
   }
   if (!(phase & 2)) return;
   if (m->np) {
@@ -1014,7 +1087,7 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
     PROF_END(FR_KC_BND_F);
   }
   const bool aa = m->aa_qdeg > 0;
-  for (auto& D : m->types) {
+  per_type([&](DevType& D, cudaStream_t s) {
     T* uf_next = mode == 0 ? nullptr : (T*)m->uf + D.off_f;
     const T* fc = (const T*)m->fc + D.off_f;
     if (aa) {
@@ -1030,33 +1103,34 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
       hex_dispatch(m->order, [&](auto n) {
         constexpr int N = decltype(n)::value;
         constexpr int E = hex_epb<N>();
-        const size_t sm = hex_vol_smem<T, TR, N>();
+        const int eb = D.tile_vol > 0 ? D.tile_vol : E;
+        const size_t sm = hex_vol_smem<T, TR, N>() / E * eb;
         const T* uin = from_x ? nullptr : (const T*)D.Y;
         if (sizeof(T) == 4 && D.verts && m->active == FR_VARIANT_SUMFACT_VERTEX) {
-          const size_t smv = hexv_vol_smem<T, N>();
+          const size_t smv = hexv_vol_smem<T, N>() / E * eb;
           const T* dup = (const T*)m->du + D.off_f;
           if (ns)
-            k_hex_vol_v<T, TR, N, E, true><<<nblk(D.ne, E), E * N * N * N, smv, s>>>(
+            k_hex_vol_v<T, TR, N, E, true><<<nblk(D.ne, eb), eb * N * N * N, smv, s>>>(
                 D.ne, uin, dup, fc, (const T*)D.verts, hexops<T>(D), ph, sa);
           else
-            k_hex_vol_v<T, TR, N, E, false><<<nblk(D.ne, E), E * N * N * N, smv, s>>>(
+            k_hex_vol_v<T, TR, N, E, false><<<nblk(D.ne, eb), eb * N * N * N, smv, s>>>(
                 D.ne, uin, nullptr, fc, (const T*)D.verts, hexops<T>(D), ph, sa);
           return;
         }
         if (aa && ns)
-          k_hex_vol<T, TR, N, E, true, true><<<nblk(D.ne, E), E * N * N * N, sm, s>>>(
+          k_hex_vol<T, TR, N, E, true, true><<<nblk(D.ne, eb), eb * N * N * N, sm, s>>>(
               D.ne, uin, nullptr, fc, nullptr, (const T*)D.rcpdjac, hexops<T>(D),
               ph, sa, (const T*)D.tf);
         else if (aa)
-          k_hex_vol<T, TR, N, E, false, true><<<nblk(D.ne, E), E * N * N * N, sm, s>>>(
+          k_hex_vol<T, TR, N, E, false, true><<<nblk(D.ne, eb), eb * N * N * N, sm, s>>>(
               D.ne, uin, nullptr, fc, nullptr, (const T*)D.rcpdjac, hexops<T>(D),
               ph, sa, (const T*)D.tf);
         else if (ns)
-          k_hex_vol<T, TR, N, E, true><<<nblk(D.ne, E), E * N * N * N, sm, s>>>(
+          k_hex_vol<T, TR, N, E, true><<<nblk(D.ne, eb), eb * N * N * N, sm, s>>>(
               D.ne, uin, (const T*)D.grad, fc, (const T*)D.smat,
               (const T*)D.rcpdjac, hexops<T>(D), ph, sa);
         else
-          k_hex_vol<T, TR, N, E, false><<<nblk(D.ne, E), E * N * N * N, sm, s>>>(
+          k_hex_vol<T, TR, N, E, false><<<nblk(D.ne, eb), eb * N * N * N, sm, s>>>(
               D.ne, uin, nullptr, fc, (const T*)D.smat, (const T*)D.rcpdjac,
               hexops<T>(D), ph, sa);
       });
@@ -1083,7 +1157,8 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
         constexpr int E = dense_epb<NU>();
         const size_t sm = dense_vol_smem<T, NU, NF>();
         const unsigned grid = unsigned(std::min<long long>(
-            (D.ne + E - 1) / E, (long long)m->num_sms * D.vol_ctas));
+            (D.ne + E - 1) / E,
+            (long long)m->num_sms * (D.tile_vol > 0 ? D.tile_vol : D.vol_ctas)));
         if (aa)
           k_vol_dense<T, NU, NF, E, false, true><<<grid, E * NU, sm, s>>>(
               D.ne, uin, nullptr, fc, nullptr, (const T*)D.rcpdjac, ops_of<T>(D),
@@ -1104,7 +1179,7 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
       launch_filter<T, TR>(m, s, D, last_stage);
       PROF_END(FR_KC_FILTER);
     }
-  }
+  });
 }
 
 // layout conversion kernels: host layout [ne][nu][5] FP64 <-> [ne][5][nu] T
@@ -1311,11 +1386,12 @@ int resolve_variant(fr_mesh* m, int scheme, double dt) {
     if (changed) {
       m->active = v;
       m->uf_valid = false;
+      for (auto& D : m->types) D.tile_grad = D.tile_vol = 0;  // tiles of another family
       ++m->epoch;
     }
     return FR_OK;
   }
-  if (m->tuned || !(has_hex || has_tc)) return FR_OK;
+  if (m->tuned) return FR_OK;
   std::vector<int> cand = {FR_VARIANT_SUMFACT};
   if (has_hex && vertex_ok) cand.push_back(FR_VARIANT_SUMFACT_VERTEX);
   if (has_hex && m->precision != FR_MIXED && dense_aa_ok) cand.push_back(FR_VARIANT_DENSE);
@@ -1435,6 +1511,84 @@ int resolve_variant(fr_mesh* m, int scheme, double dt) {
         pick = FR_VARIANT_TENSOR;
       }
     }
+  }
+  // Tiles and schedule of the picked family (Section 3.1, "Matrix
+  // multiplications": kernel configurations benchmarked at run time, the
+  // fastest kept): per type the elements per CTA of the hexahedron kernels
+  // or the persistent CTAs per SM of the dense ones (timed per kernel from a
+  // profiled step), then the interface kernels' block size and the parallel
+  // per-type branches (timed per step).
+  m->active = pick;
+  {
+    float ms = 0.f;
+    if (int rr = run(nullptr, &ms)) {
+      release();
+      return rr;
+    }
+    m->sched_ms[0] = ms;
+    std::vector<std::vector<int>> cg(nt), cv(nt);
+    size_t nc = 1;
+    for (size_t t = 0; t < nt; ++t) {
+      DevType& D = m->types[t];
+      const bool tcg = pick == FR_VARIANT_TENSOR && use_tc_grad(m, D);
+      const bool tcv = pick == FR_VARIANT_TENSOR && use_tc_vol(m, D);
+      cg[t] = tcg ? std::vector<int>{0} : tile_candidates(m, D, true);
+      cv[t] = tcv ? std::vector<int>{0} : tile_candidates(m, D, false);
+      nc = std::max({nc, cg[t].size(), cv[t].size()});
+    }
+    std::vector<float> bg(nt, 1e30f), bv(nt, 1e30f);
+    std::vector<int> pg(nt, 0), pv(nt, 0);
+    for (size_t i = 0; i < nc && nc > 1; ++i) {
+      for (size_t t = 0; t < nt; ++t) {
+        m->types[t].tile_grad = cg[t][std::min(i, cg[t].size() - 1)];
+        m->types[t].tile_vol = cv[t][std::min(i, cv[t].size() - 1)];
+      }
+      std::vector<float> pt(2 * nt, 0.f);
+      if (int rr = run(&pt, &ms)) {
+        release();
+        return rr;
+      }
+      for (size_t t = 0; t < nt; ++t) {
+        if (pt[2 * t] < bg[t]) {
+          bg[t] = pt[2 * t];
+          pg[t] = m->types[t].tile_grad;
+        }
+        if (pt[2 * t + 1] < bv[t]) {
+          bv[t] = pt[2 * t + 1];
+          pv[t] = m->types[t].tile_vol;
+        }
+      }
+    }
+    for (size_t t = 0; t < nt; ++t) {
+      m->types[t].tile_grad = nc > 1 ? pg[t] : 0;
+      m->types[t].tile_vol = nc > 1 ? pv[t] : 0;
+    }
+    float bt = 1e30f;
+    int btb = 256;
+    for (int tb : {128, 256, 512}) {
+      m->face_tb = tb;
+      if (int rr = run(nullptr, &ms)) {
+        release();
+        return rr;
+      }
+      if (ms < bt) {
+        bt = ms;
+        btb = tb;
+      }
+    }
+    m->face_tb = btb;
+    if (nt > 1 && ensure_par(m) == FR_OK) {
+      m->par_types = true;
+      if (int rr = run(nullptr, &ms)) {
+        release();
+        return rr;
+      }
+      if (ms < bt)
+        bt = ms;
+      else
+        m->par_types = false;
+    }
+    m->sched_ms[1] = bt;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
