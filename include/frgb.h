@@ -401,6 +401,67 @@ int fr_group_destroy(fr_group* group);
 int fr_group_rhs(fr_group* group);
 int fr_group_rk_step(fr_group* group, int scheme, double dt, int nsteps);
 
+/* Exchange between processes (Section 3.1, "Multi-node capabilities": the
+ * packed face buffers of the partitions exchanged by MPI; here any transport
+ * the caller has, e.g. torch.distributed over gloo or NCCL).  A part of a
+ * partitioned mesh, built with its faces towards other parts as
+ * FR_BC_EXCHANGE boundaries, lives in its own process (one GPU each):
+ *
+ * fr_exchange_faces: this part's exchange faces in the library's order,
+ *   for the other ranks: n_faces, n_points, and (arrays may be NULL to query
+ *   the counts) face_npts [n_faces] points per face, centroids
+ *   [n_faces][3], pt_x [n_points][3] positions and pt_mag [n_points] face
+ *   metric magnitudes |S^T n~| of the points, face by face.  Host-only
+ *   handles too.
+ * fr_exchange_setup: match this part's exchange points (rank `rank` of
+ *   nranks) with the other ranks' from all ranks' fr_exchange_faces arrays,
+ *   concatenated in rank order (faces_per_rank, points_per_rank [nranks]);
+ *   faces by translated centroid (the mesh's periodic vectors), then points
+ *   by position.  counts [nranks] receives the number of points exchanged
+ *   with each rank (the same in both directions).  A message to or from rank
+ *   q carries these points ordered by the exchange index on the lower of the
+ *   two ranks, so both sides agree.  FR_EMESH: a face or point without
+ *   exactly one partner.  Host-only handles too (matching only).
+ * fr_exchange_list: the boundary-point indices (fr_get_boundary_points
+ *   order) of this part's exchanged points in message order; *n receives
+ *   the count, points may be NULL.
+ * fr_exchange_pack: gather, on the handle's stream, the traces of kind
+ *   FR_XCH_SOLUTION (5 values per point: the stage input at the flux point)
+ *   or FR_XCH_GRADIENT (after phase 1 of a Navier-Stokes stage: 15 gradient
+ *   values per point with FP64 values, 5 viscous normal-flux values with
+ *   FP32 / mixed values) into dev_buf [sum counts][nv] (value type: FP64 or
+ *   FP32 as the mesh's values), messages in ascending rank order.
+ * fr_exchange_unpack: the received buffer of the same layout into the
+ *   partner-trace slots of the exchange points.
+ * fr_rk_stage: one phase of stage `stage` of an RK step of `scheme`, on the
+ *   handle's stream: phase 1, the NS common solution and gradients (nothing
+ *   for Euler); phase 2, common fluxes, volume kernels and the stage's RK
+ *   update (and the flux-point traces of the next stage).  part 1 launches
+ *   only the work that needs no exchanged value (interior pairs, boundary
+ *   points that are not exchange points, elements that own no exchange
+ *   point), part 2 the rest, part 0 both: so the transport of a phase's
+ *   input can overlap part 1.  Order per stage: pack/send/receive/unpack
+ *   FR_XCH_SOLUTION (part 1 of phase 1 may run meanwhile), phase 1, then the
+ *   same for FR_XCH_GRADIENT and phase 2 (Euler: only the solution exchange
+ *   and phase 2).  Stage 0, phase 1, part 0 or 1 starts the step (dt); the
+ *   last stage's phase 2 (part 0 or 2) synchronises the stream and returns
+ *   FR_ENONFINITE / FR_ETIMEOUT from the device flag.  With
+ *   FR_VARIANT_AUTO the part runs the default family (no tuning across
+ *   processes).  FR_EINVAL: the entropy filter is on, or the mesh has
+ *   exchange points and no fr_exchange_setup. */
+enum { FR_XCH_SOLUTION = 0, FR_XCH_GRADIENT = 1 };
+int fr_exchange_faces(const fr_mesh* mesh, int64_t* n_faces, int64_t* n_points,
+                      int32_t* face_npts, double* centroids, double* pt_x,
+                      double* pt_mag);
+int fr_exchange_setup(fr_mesh* mesh, int rank, int nranks, const int64_t* faces_per_rank,
+                      const int64_t* points_per_rank, const int32_t* face_npts,
+                      const double* centroids, const double* pt_x,
+                      const double* pt_mag, int64_t* counts);
+int fr_exchange_list(const fr_mesh* mesh, int32_t* points, int64_t* n);
+int fr_exchange_pack(fr_mesh* mesh, int what, void* dev_buf);
+int fr_exchange_unpack(fr_mesh* mesh, int what, const void* dev_buf);
+int fr_rk_stage(fr_mesh* mesh, int scheme, double dt, int stage, int phase, int part);
+
 /* Viscous coupling of a Navier-Stokes mesh (the paper names the compressible
  * Navier-Stokes solver, not its interface scheme; reading of the local DG
  * flux).  Along every interface's orientation, whose "-" side is the

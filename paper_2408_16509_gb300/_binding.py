@@ -87,6 +87,13 @@ def load():
         "fr_stats": (I, [P, C.POINTER(Stats), I]),
         "fr_get_schedule": (I, [P, C.POINTER(Schedule)]),
         "fr_set_schedule": (I, [P, C.POINTER(Schedule)]),
+        "fr_exchange_faces": (I, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                  P, P, P, P]),
+        "fr_exchange_setup": (I, [P, I, I, P, P, P, P, P, P, P]),
+        "fr_exchange_list": (I, [P, P, C.POINTER(C.c_int64)]),
+        "fr_exchange_pack": (I, [P, I, P]),
+        "fr_exchange_unpack": (I, [P, I, P]),
+        "fr_rk_stage": (I, [P, I, D, I, I, I]),
         "fr_probe_fma": (I, [I, I, C.c_int64, C.POINTER(D), C.POINTER(D)]),
         "fr_get_rhs": (I, [P, I, P]),
         "fr_rk_step": (I, [P, I, D, I]),
@@ -241,6 +248,7 @@ class FRMesh:
         self._h = h
         self._keep = None
         self.precision = precision
+        self.physics = physics
         self.types = [t for t in ("hex", "pri", "tet") if self.info(t)[0] > 0]
 
     def close(self):
@@ -540,6 +548,59 @@ class FRMesh:
 
     def n_elements(self):
         return sum(self.info(t)[0] for t in self.types)
+
+    def exchange_faces(self):
+        """This part's exchange faces (fr_exchange_faces): (points per face,
+        centroids [nf][3], point positions [np][3], |S^T n~| [np])."""
+        nf, npt = C.c_int64(), C.c_int64()
+        _check(load().fr_exchange_faces(self._h, C.byref(nf), C.byref(npt),
+                                        None, None, None, None))
+        fn = np.empty(nf.value, np.int32)
+        cen = np.empty((nf.value, 3), np.float64)
+        px = np.empty((npt.value, 3), np.float64)
+        pm = np.empty(npt.value, np.float64)
+        _check(load().fr_exchange_faces(self._h, C.byref(nf), C.byref(npt),
+                                        _ptr(fn), _ptr(cen), _ptr(px), _ptr(pm)))
+        return fn, cen, px, pm
+
+    def exchange_setup(self, rank, per_rank):
+        """Match with the other ranks (fr_exchange_setup).  per_rank: every
+        rank's exchange_faces() tuple, in rank order.  Returns the points
+        exchanged with each rank."""
+        nr = len(per_rank)
+        fpr = np.array([len(x[0]) for x in per_rank], np.int64)
+        ppr = np.array([len(x[3]) for x in per_rank], np.int64)
+        fn = np.ascontiguousarray(np.concatenate([x[0] for x in per_rank]), np.int32)
+        cen = np.ascontiguousarray(np.concatenate([np.reshape(x[1], (-1, 3)) for x in per_rank]))
+        px = np.ascontiguousarray(np.concatenate([np.reshape(x[2], (-1, 3)) for x in per_rank]))
+        pm = np.ascontiguousarray(np.concatenate([x[3] for x in per_rank]), np.float64)
+        counts = np.zeros(nr, np.int64)
+        _check(load().fr_exchange_setup(self._h, int(rank), nr, _ptr(fpr), _ptr(ppr),
+                                        _ptr(fn), _ptr(cen), _ptr(px), _ptr(pm),
+                                        _ptr(counts)))
+        return counts
+
+    def exchange_list(self):
+        """Boundary-point indices of the exchanged points in message order."""
+        n = C.c_int64()
+        _check(load().fr_exchange_list(self._h, None, C.byref(n)))
+        out = np.empty(n.value, np.int32)
+        _check(load().fr_exchange_list(self._h, _ptr(out), C.byref(n)))
+        return out
+
+    def exchange_pack(self, what, tensor):
+        """Gather the traces of kind what (0 solution, 1 gradient) into a
+        CUDA tensor [n][nv] on the handle's stream."""
+        _check(load().fr_exchange_pack(self._h, int(what), C.c_void_p(tensor.data_ptr())))
+
+    def exchange_unpack(self, what, tensor):
+        _check(load().fr_exchange_unpack(self._h, int(what), C.c_void_p(tensor.data_ptr())))
+
+    def rk_stage(self, scheme, dt, stage, phase, part=0):
+        """One phase of one RK stage (fr_rk_stage); part 1 interior, 2
+        exchange-adjacent, 0 both."""
+        _check(load().fr_rk_stage(self._h, SCHEMES[scheme], float(dt), int(stage),
+                                  int(phase), int(part)))
 
     def adjacency(self, etype):
         """[ne][nfaces] global index of the neighbour across each face, -1

@@ -101,6 +101,39 @@ int fr_mesh_create(const fr_mesh_desc* d, fr_mesh** out) {
   if (!err.empty()) return fail(emesh ? FR_EMESH : FR_EINVAL, err);
   for (auto& p : in.periodic) m->periodic.insert(m->periodic.end(), p.begin(), p.end());
   for (int32_t b : m->conn.bbc) m->has_exch |= m->bc64.kind[b] == FR_BC_EXCHANGE;
+  {
+    // exchange points last (a contiguous range the halo part of a stage
+    // launches on its own), and per type the leading elements that own no
+    // exchange point (the interior part of a stage)
+    HostConn& C = m->conn;
+    const size_t nb = C.bidx.size();
+    std::vector<size_t> perm(nb);
+    for (size_t i = 0; i < nb; ++i) perm[i] = i;
+    std::stable_partition(perm.begin(), perm.end(), [&](size_t i) {
+      return m->bc64.kind[C.bbc[i]] != FR_BC_EXCHANGE;
+    });
+    std::vector<int32_t> bi(nb), bb(nb);
+    std::vector<double> bn(4 * nb);
+    for (size_t k = 0; k < nb; ++k) {
+      bi[k] = C.bidx[perm[k]];
+      bb[k] = C.bbc[perm[k]];
+      for (int c = 0; c < 4; ++c) bn[4 * k + c] = C.bn[4 * perm[k] + c];
+    }
+    C.bidx.swap(bi);
+    C.bbc.swap(bb);
+    C.bn.swap(bn);
+    m->nb_x0 = 0;
+    while (m->nb_x0 < (long long)nb && m->bc64.kind[C.bbc[m->nb_x0]] != FR_BC_EXCHANGE)
+      ++m->nb_x0;
+    m->n_int.assign(m->host.size(), 0);
+    for (size_t t = 0; t < m->host.size(); ++t) m->n_int[t] = m->host[t].ne;
+    for (long long i = m->nb_x0; i < (long long)nb; ++i) {
+      const int32_t code = C.bidx[i];
+      const int t = code >> 29;
+      const long long e = (code & ((1 << 29) - 1)) / (5 * m->host[t].ref.nfpts);
+      m->n_int[t] = std::min<long long>(m->n_int[t], e);
+    }
+  }
   if (d->device < 0) {  // host-only handle: geometry and operators, no GPU
     m->host_only = true;
     for (size_t t = 0; t < m->host.size(); ++t) m->type_of_kind[m->host[t].kind] = int(t);
@@ -511,6 +544,277 @@ int fr_get_tuning(const fr_mesh* m, int* active, float* ms) {
   if (active) *active = m->active;
   if (ms)
     for (int i = 0; i < 5; ++i) ms[i] = m->tune_ms[i];
+  return FR_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Exchange faces of a part in boundary-point order: consecutive exchange
+// points of one (type, element, face) form a face.
+struct XFace {
+  std::vector<int32_t> pt;  // own boundary-point indices
+  double c[3] = {0, 0, 0};  // centroid of the face's points
+};
+
+std::vector<XFace> exchange_faces_of(const fr_mesh* m) {
+  std::vector<XFace> fl;
+  std::array<int64_t, 3> prev = {-1, -1, -1};
+  for (long long i = m->nb_x0; i < (long long)m->conn.bidx.size(); ++i) {
+    const int32_t code = m->conn.bidx[i];
+    const HostType& H = m->host[code >> 29];
+    const int64_t rem = code & ((int64_t(1) << 29) - 1);
+    const int64_t e = rem / (5 * H.ref.nfpts);
+    const int f = int(rem - e * 5 * H.ref.nfpts);
+    const std::array<int64_t, 3> key = {code >> 29, e, H.ref.fpts_face[f]};
+    if (key != prev || fl.empty()) {
+      fl.push_back(XFace{});
+      prev = key;
+    }
+    fl.back().pt.push_back(int32_t(i));
+    for (int k = 0; k < 3; ++k)
+      fl.back().c[k] += H.fpts_x[(size_t(e) * H.ref.nfpts + f) * 3 + k];
+  }
+  for (XFace& F : fl)
+    for (int k = 0; k < 3; ++k) F.c[k] /= double(F.pt.size());
+  return fl;
+}
+
+const double* bpt_x(const fr_mesh* m, int32_t i) {
+  const int32_t code = m->conn.bidx[i];
+  const HostType& H = m->host[code >> 29];
+  const int64_t rem = code & ((int64_t(1) << 29) - 1);
+  const int64_t e = rem / (5 * H.ref.nfpts);
+  const int f = int(rem - e * 5 * H.ref.nfpts);
+  return &H.fpts_x[(size_t(e) * H.ref.nfpts + f) * 3];
+}
+
+}  // namespace
+
+extern "C" {
+
+int fr_exchange_faces(const fr_mesh* m, int64_t* n_faces, int64_t* n_points,
+                      int32_t* face_npts, double* centroids, double* pt_x,
+                      double* pt_mag) {
+  if (!m || !n_faces || !n_points) return fail(FR_EINVAL, "null argument");
+  const std::vector<XFace> fl = exchange_faces_of(m);
+  *n_faces = int64_t(fl.size());
+  int64_t np = 0;
+  for (const XFace& F : fl) np += int64_t(F.pt.size());
+  *n_points = np;
+  int64_t q = 0;
+  for (size_t j = 0; j < fl.size(); ++j) {
+    if (face_npts) face_npts[j] = int32_t(fl[j].pt.size());
+    if (centroids)
+      for (int k = 0; k < 3; ++k) centroids[3 * j + k] = fl[j].c[k];
+    for (int32_t i : fl[j].pt) {
+      const double* x = bpt_x(m, i);
+      if (pt_x)
+        for (int k = 0; k < 3; ++k) pt_x[3 * q + k] = x[k];
+      if (pt_mag) pt_mag[q] = m->conn.bn[4 * size_t(i) + 3];
+      ++q;
+    }
+  }
+  return FR_OK;
+}
+
+int fr_exchange_setup(fr_mesh* m, int rank, int nranks, const int64_t* faces_per_rank,
+                      const int64_t* points_per_rank, const int32_t* face_npts,
+                      const double* centroids, const double* pt_x,
+                      const double* pt_mag, int64_t* counts) {
+  if (!m || !faces_per_rank || !points_per_rank || !counts)
+    return fail(FR_EINVAL, "null argument");
+  if (nranks < 1 || rank < 0 || rank >= nranks) return fail(FR_EINVAL, "bad rank");
+  if (m->in_group) return fail(FR_EINVAL, "the mesh belongs to a group");
+  // other ranks' faces: (rank, first point, point count, centroid)
+  struct RF {
+    int r;
+    int64_t p0, np;
+    const double* c;
+  };
+  std::vector<RF> rf;
+  std::vector<int64_t> pbase(nranks + 1, 0);
+  int64_t fo = 0;
+  for (int r = 0; r < nranks; ++r) {
+    if (faces_per_rank[r] < 0 || points_per_rank[r] < 0) return fail(FR_EINVAL, "negative count");
+    pbase[r + 1] = pbase[r] + points_per_rank[r];
+    int64_t po = pbase[r];
+    for (int64_t j = 0; j < faces_per_rank[r]; ++j, ++fo) {
+      if (r != rank) rf.push_back(RF{r, po, face_npts[fo], centroids + 3 * fo});
+      po += face_npts[fo];
+    }
+    if (po != pbase[r + 1]) return fail(FR_EINVAL, "face point counts do not add up");
+  }
+  const std::vector<XFace> own = exchange_faces_of(m);
+  {
+    int64_t np = 0;
+    for (const XFace& F : own) np += int64_t(F.pt.size());
+    if (faces_per_rank[rank] != int64_t(own.size()) || points_per_rank[rank] != np)
+      return fail(FR_EINVAL, "this rank's entries differ from fr_exchange_faces");
+  }
+  // grid of the other ranks' face centroids
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int64_t q = 0; q < pbase[nranks]; ++q)
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = std::min(lo[k], pt_x[3 * q + k]);
+      hi[k] = std::max(hi[k], pt_x[3 * q + k]);
+    }
+  double ext = 0.0;
+  for (int k = 0; k < 3; ++k) ext = std::max(ext, hi[k] - lo[k]);
+  const double tol = 1e-8 * std::max(ext, 1e-300), cell = 16.0 * tol;
+  auto key = [&](const double* x, int dx, int dy, int dz) {
+    return std::array<int64_t, 3>{int64_t(std::floor(x[0] / cell)) + dx,
+                                  int64_t(std::floor(x[1] / cell)) + dy,
+                                  int64_t(std::floor(x[2] / cell)) + dz};
+  };
+  std::unordered_multimap<std::array<int64_t, 3>, int, CellHash> grid;
+  for (int j = 0; j < int(rf.size()); ++j) grid.emplace(key(rf[j].c, 0, 0, 0), j);
+  const int np = int(m->periodic.size() / 3);
+  std::vector<std::array<double, 3>> shifts;
+  int ncomb = 1;
+  for (int a = 0; a < np; ++a) ncomb *= 3;
+  for (int c = 0; c < ncomb; ++c) {
+    std::array<double, 3> sh = {0, 0, 0};
+    int cc = c;
+    for (int a = 0; a < np; ++a, cc /= 3)
+      for (int k = 0; k < 3; ++k) sh[k] += double(cc % 3 - 1) * m->periodic[3 * a + k];
+    shifts.push_back(sh);
+  }
+  // pairs: (partner rank, canonical key, own boundary point, partner |S^T n~|)
+  struct PairX {
+    int r;
+    int64_t key;
+    int32_t own;
+    double mag;
+  };
+  std::vector<PairX> pairs;
+  int64_t own_idx = 0;  // own exchange index (position in fr_exchange_faces order)
+  for (const XFace& F : own) {
+    int found = -1, hits = 0;
+    std::array<double, 3> fsh = {0, 0, 0};
+    for (const auto& sh : shifts) {
+      const double y[3] = {F.c[0] + sh[0], F.c[1] + sh[1], F.c[2] + sh[2]};
+      for (int dx = -1; dx <= 1; ++dx)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dz = -1; dz <= 1; ++dz) {
+            auto rg = grid.equal_range(key(y, dx, dy, dz));
+            for (auto it = rg.first; it != rg.second; ++it) {
+              const RF& G = rf[it->second];
+              if (G.np != int64_t(F.pt.size())) continue;
+              double d2 = 0;
+              for (int k = 0; k < 3; ++k) d2 += (G.c[k] - y[k]) * (G.c[k] - y[k]);
+              if (d2 <= tol * tol) {
+                found = it->second;
+                fsh = sh;
+                ++hits;
+              }
+            }
+          }
+    }
+    if (hits != 1)
+      return fail(FR_EMESH, hits ? "an exchange face matches several partners"
+                                 : "an exchange face has no partner among the ranks");
+    const RF& G = rf[found];
+    std::vector<char> taken(size_t(G.np), 0);
+    for (size_t a = 0; a < F.pt.size(); ++a, ++own_idx) {
+      const double* x0 = bpt_x(m, F.pt[a]);
+      const double x[3] = {x0[0] + fsh[0], x0[1] + fsh[1], x0[2] + fsh[2]};
+      int64_t best = -1;
+      double bd = 1e300;
+      for (int64_t j = 0; j < G.np; ++j) {
+        const double* y = pt_x + 3 * (G.p0 + j);
+        double d2 = 0;
+        for (int k = 0; k < 3; ++k) d2 += (x[k] - y[k]) * (x[k] - y[k]);
+        if (d2 < bd) {
+          bd = d2;
+          best = j;
+        }
+      }
+      if (best < 0 || bd > tol * tol || taken[best])
+        return fail(FR_EMESH, "flux points do not conform across an exchange face");
+      taken[best] = 1;
+      const int64_t partner_idx = G.p0 + best - pbase[G.r];  // index in that rank's list
+      // both sides order a rank pair's points by the lower rank's index
+      pairs.push_back(PairX{G.r, rank < G.r ? own_idx : partner_idx, F.pt[a],
+                            pt_mag[G.p0 + best]});
+    }
+  }
+  std::stable_sort(pairs.begin(), pairs.end(), [](const PairX& x, const PairX& y) {
+    return x.r != y.r ? x.r < y.r : x.key < y.key;
+  });
+  std::vector<int32_t> list(pairs.size());
+  m->x_counts.assign(nranks, 0);
+  std::vector<double> xm(m->conn.bidx.size(), 1.0);
+  for (size_t k = 0; k < pairs.size(); ++k) {
+    list[k] = pairs[k].own;
+    ++m->x_counts[pairs[k].r];
+    xm[pairs[k].own] = pairs[k].mag;
+  }
+  for (int r = 0; r < nranks; ++r) counts[r] = m->x_counts[r];
+  m->n_xlist = (long long)list.size();
+  m->x_list_host = list;
+  if (m->host_only) return FR_OK;
+  CK(cudaSetDevice(m->device));
+  CK(cudaStreamSynchronize(m->stream));
+  if (m->x_list) {
+    cudaFree(m->x_list);
+    m->x_list = nullptr;
+  }
+  if (!list.empty()) {
+    CK(cudaMalloc((void**)&m->x_list, list.size() * sizeof(int32_t)));
+    CK(cudaMemcpy(m->x_list, list.data(), list.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  }
+  if (m->xm) {
+    if (m->wsize == 8) {
+      CK(cudaMemcpy(m->xm, xm.data(), xm.size() * sizeof(double), cudaMemcpyHostToDevice));
+    } else {
+      std::vector<float> h(xm.begin(), xm.end());
+      CK(cudaMemcpy(m->xm, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
+  }
+  return FR_OK;
+}
+
+int fr_exchange_list(const fr_mesh* m, int32_t* points, int64_t* n) {
+  if (!m || !n) return fail(FR_EINVAL, "null argument");
+  *n = int64_t(m->x_list_host.size());
+  if (points) std::copy(m->x_list_host.begin(), m->x_list_host.end(), points);
+  return FR_OK;
+}
+
+int fr_exchange_pack(fr_mesh* m, int what, void* dev_buf) {
+  if (!m || (!dev_buf && m && m->n_xlist)) return fail(FR_EINVAL, "null argument");
+  if (m->host_only) return fail(FR_EINVAL, "host-only handle (device < 0)");
+  if (what != FR_XCH_SOLUTION && what != FR_XCH_GRADIENT) return fail(FR_EINVAL, "bad trace kind");
+  CK(cudaSetDevice(m->device));
+  return FR_PREC(m, exchange_pack, m, what, dev_buf);
+}
+
+int fr_exchange_unpack(fr_mesh* m, int what, const void* dev_buf) {
+  if (!m || (!dev_buf && m && m->n_xlist)) return fail(FR_EINVAL, "null argument");
+  if (m->host_only) return fail(FR_EINVAL, "host-only handle (device < 0)");
+  if (what != FR_XCH_SOLUTION && what != FR_XCH_GRADIENT) return fail(FR_EINVAL, "bad trace kind");
+  CK(cudaSetDevice(m->device));
+  return FR_PREC(m, exchange_unpack, m, what, dev_buf);
+}
+
+int fr_rk_stage(fr_mesh* m, int scheme, double dt, int stage, int phase, int part) {
+  if (!m) return fail(FR_EINVAL, "null mesh");
+  if (m->host_only) return fail(FR_EINVAL, "host-only handle (device < 0)");
+  if (m->in_group) return fail(FR_EINVAL, "the mesh belongs to a group");
+  if (m->filter_on) return fail(FR_EINVAL, "not with the entropy filter");
+  if (scheme != FR_RK4 && scheme != FR_RK45) return fail(FR_EINVAL, "unknown scheme");
+  const int nst = scheme == FR_RK4 ? 4 : 5;
+  if (stage < 0 || stage >= nst || (phase != 1 && phase != 2) || part < 0 || part > 2)
+    return fail(FR_EINVAL, "bad stage, phase or part");
+  if (m->has_exch && m->n_xlist == 0 && m->nb > m->nb_x0)
+    return fail(FR_EINVAL, "exchange points without fr_exchange_setup");
+  CK(cudaSetDevice(m->device));
+  int rc = FR_PREC(m, do_stage, m, scheme, dt, stage, phase, part);
+  if (rc) return rc;
+  if (phase == 2 && part != 1) ++m->n_stages;
+  if (stage == nst - 1 && phase == 2 && part != 1) ++m->n_steps;
   return FR_OK;
 }
 

@@ -198,6 +198,16 @@ struct fr_mesh {
   void* xu = nullptr;         // [nb][5] partner solution traces
   void* xg = nullptr;         // [nb][15] partner gradients (FP64) or [nb][5] q (FP32)
   void* xm = nullptr;         // [nb] partner |S^T n~|
+  // boundary points [nb_x0, nb) are the exchange points; elements [0,
+  // n_int[t]) of type t own none of them (the interior part of a stage)
+  long long nb_x0 = 0;
+  std::vector<long long> n_int;
+  // exchange with other processes (fr_exchange_setup): own exchange points
+  // (boundary-point indices) in message order, partners ascending
+  int32_t* x_list = nullptr;
+  long long n_xlist = 0;
+  std::vector<long long> x_counts;  // points exchanged with each rank
+  std::vector<int32_t> x_list_host;
   std::vector<double> periodic;  // [n][3] translation vectors
   bool err_on = false;        // stage epilogues accumulate the embedded error
   double* d_errpart = nullptr;  // per-block partial sums of the error norm
@@ -237,6 +247,7 @@ struct fr_mesh {
   size_t staging_bytes = 0;
 
   ~fr_mesh() {
+    if (x_list) cudaFree(x_list);
     for (cudaStream_t st : par_st)
       if (st) cudaStreamDestroy(st);
     for (cudaEvent_t ev : par_ev)
@@ -954,13 +965,44 @@ inline std::vector<int> tile_candidates(const fr_mesh* m, const DevType& D, bool
   return c;
 }
 
+// Elements [e0, e0 + n) of a type as a type of their own: every
+// per-element array shifted, flux-point regions included.  The kernels then
+// run on that range unchanged.
+inline DevType sub_view(const fr_mesh* m, const DevType& D, long long e0, long long n) {
+  DevType V = D;
+  V.ne = n;
+  const size_t w = m->wsize, r = m->rsize, nu = size_t(D.nu), nf = size_t(D.nf);
+  auto sh = [&](void* p, size_t per) -> void* {
+    return p ? static_cast<void*>(static_cast<char*>(p) + size_t(e0) * per) : nullptr;
+  };
+  V.X = sh(D.X, 5 * nu * r);
+  V.A = sh(D.A, 5 * nu * r);
+  V.E = sh(D.E, 5 * nu * r);
+  V.Xs = sh(D.Xs, 5 * nu * r);
+  V.Y = sh(D.Y, 5 * nu * w);
+  V.R = sh(D.R, 5 * nu * w);
+  V.smat = sh(D.smat, 9 * nu * w);
+  V.rcpdjac = sh(D.rcpdjac, nu * w);
+  V.grad = sh(D.grad, 15 * nu * w);
+  V.fnv = sh(D.fnv, 3 * nf * w);
+  V.fbc = static_cast<int8_t*>(sh(D.fbc, nf));
+  V.verts = sh(D.verts, 24 * w);
+  V.aasmq = sh(D.aasmq, 9 * size_t(D.aa_nq) * w);
+  V.tf = sh(D.tf, 15 * nu * w);
+  V.off_f = D.off_f + e0 * 5 * (long long)nf;
+  return V;
+}
+
 // Launch one RK stage (or a bare right-hand side when mode == 0).  phase
 // bit 1: the NS common solution and gradients; bit 2: the common fluxes and
 // the volume kernels.  A partitioned group exchanges the gradient traces
-// between the two (and the solution traces before bit 1).
+// between the two (and the solution traces before bit 1).  part 1: only the
+// interior pairs, the boundary points that are not exchange points and the
+// elements that own no exchange point; part 2: the rest (exchange points and
+// the elements [n_int, ne)); 0: everything.
 template <typename T, typename TR>
 void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
-                  Prof* prof = nullptr, int phase = 3) {
+                  Prof* prof = nullptr, int phase = 3, int part = 0) {
   const bool ns = m->physics == FR_NAVIER_STOKES;
   const Phys<T> ph = phys<T>(m);
   const BCTab<T>& bc = bctab<T>(m);
@@ -969,18 +1011,44 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
   // not while profiling) as parallel branches forked from and joined to s
   auto per_type = [&](auto&& fn) {
     const size_t nt = m->types.size();
-    if (!m->par_types || prof || nt < 2 || m->par_st.size() < nt) {
-      for (auto& D : m->types) fn(D, s);
+    std::vector<DevType> views;
+    std::vector<DevType*> ds;
+    if (part == 0) {
+      for (auto& D : m->types) ds.push_back(&D);
+    } else {
+      views.reserve(nt);
+      for (size_t t = 0; t < nt; ++t) {
+        const DevType& D = m->types[t];
+        const long long ni = t < m->n_int.size() ? m->n_int[t] : D.ne;
+        const long long e0 = part == 1 ? 0 : ni, n = part == 1 ? ni : D.ne - ni;
+        if (n <= 0) continue;
+        views.push_back(sub_view(m, D, e0, n));
+      }
+      for (auto& V : views) ds.push_back(&V);
+    }
+    if (!m->par_types || prof || ds.size() < 2 || m->par_st.size() < ds.size()) {
+      for (DevType* D : ds) fn(*D, s);
       return;
     }
     cudaEventRecord(m->par_ev[0], s);
-    for (size_t t = 0; t < nt; ++t) {
+    for (size_t t = 0; t < ds.size(); ++t) {
       cudaStreamWaitEvent(m->par_st[t], m->par_ev[0], 0);
-      fn(m->types[t], m->par_st[t]);
+      fn(*ds[t], m->par_st[t]);
       cudaEventRecord(m->par_ev[1 + t], m->par_st[t]);
     }
-    for (size_t t = 0; t < nt; ++t) cudaStreamWaitEvent(s, m->par_ev[1 + t], 0);
+    for (size_t t = 0; t < ds.size(); ++t) cudaStreamWaitEvent(s, m->par_ev[1 + t], 0);
   };
+  // boundary points of this part: [b0, b0 + nbp)
+  const long long b0 = part == 2 ? m->nb_x0 : 0;
+  const long long nbp = part == 0 ? m->nb : (part == 1 ? m->nb_x0 : m->nb - m->nb_x0);
+  const bool pairs = part != 2;
+  const int nvg = sizeof(T) == 4 ? 5 : 15;
+  const int32_t* bidx = m->bidx + b0;
+  const int32_t* bbc = m->bbc + b0;
+  const T* bnp = m->bn ? (const T*)m->bn + 4 * b0 : nullptr;
+  const T* xup = m->xu ? (const T*)m->xu + 5 * b0 : nullptr;
+  const T* xgp = m->xg ? (const T*)m->xg + nvg * b0 : nullptr;
+  const T* xmp = m->xm ? (const T*)m->xm + b0 : nullptr;
   // stage input: the solution register X for a bare RHS and the first
   // stage, the stage register Y afterwards
   const bool from_x = (mode == 0 || stage == 0);
@@ -992,17 +1060,16 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
     PROF_END(FR_KC_FILTER);
   }
   if (ns && (phase & 1)) {
-    if (m->np) {
+    if (m->np && pairs) {
       PROF_BEGIN(FR_KC_FACE_U);
       k_face_ucommon<T><<<nblk(m->np, tb), tb, 0, s>>>(
           m->np, m->pl, m->pr, (const T*)m->uf, (T*)m->du, m->tt, ph.beta);
       PROF_END(FR_KC_FACE_U);
     }
-    if (m->nb) {
+    if (nbp > 0) {
       PROF_BEGIN(FR_KC_BND_U);
-      k_bnd_ucommon<T><<<nblk(m->nb, tb), tb, 0, s>>>(
-          m->nb, m->bidx, m->bbc, (const T*)m->uf, (T*)m->du, m->tt, bc,
-          (const T*)m->xu, ph.beta);
+      k_bnd_ucommon<T><<<nblk(nbp, tb), tb, 0, s>>>(
+          int(nbp), bidx, bbc, (const T*)m->uf, (T*)m->du, m->tt, bc, xup, ph.beta);
       PROF_END(FR_KC_BND_U);
     }
     per_type([&](DevType& D, cudaStream_t s) {
@@ -1052,7 +1119,7 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
     });
   }
   if (!(phase & 2)) return;
-  if (m->np) {
+  if (m->np && pairs) {
     PROF_BEGIN(FR_KC_FACE_F);
     if (ns && sizeof(T) == 4)
       k_face_flux_ns<T><<<nblk(m->np, tb), tb, 0, s>>>(
@@ -1068,22 +1135,20 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
           (const T*)m->uf, nullptr, (T*)m->fc, m->tt, ph);
     PROF_END(FR_KC_FACE_F);
   }
-  if (m->nb) {
+  if (nbp > 0) {
     PROF_BEGIN(FR_KC_BND_F);
     if (ns && sizeof(T) == 4)
-      k_bnd_flux_ns<T><<<nblk(m->nb, tb), tb, 0, s>>>(
-          m->nb, m->bidx, m->bbc, (const T*)m->bn, (const T*)m->uf,
-          (const T*)m->gradf, (T*)m->fc, m->tt, ph, bc, (const T*)m->xu,
-          (const T*)m->xg, (const T*)m->xm);
+      k_bnd_flux_ns<T><<<nblk(nbp, tb), tb, 0, s>>>(
+          int(nbp), bidx, bbc, bnp, (const T*)m->uf, (const T*)m->gradf, (T*)m->fc,
+          m->tt, ph, bc, xup, xgp, xmp);
     else if (ns)
-      k_bnd_flux<T, true><<<nblk(m->nb, tb), tb, 0, s>>>(
-          m->nb, m->bidx, m->bbc, (const T*)m->bn, (const T*)m->uf,
-          (const T*)m->gradf, (T*)m->fc, m->tt, ph, bc, (const T*)m->xu,
-          (const T*)m->xg);
+      k_bnd_flux<T, true><<<nblk(nbp, tb), tb, 0, s>>>(
+          int(nbp), bidx, bbc, bnp, (const T*)m->uf, (const T*)m->gradf, (T*)m->fc,
+          m->tt, ph, bc, xup, xgp);
     else
-      k_bnd_flux<T, false><<<nblk(m->nb, tb), tb, 0, s>>>(
-          m->nb, m->bidx, m->bbc, (const T*)m->bn, (const T*)m->uf, nullptr,
-          (T*)m->fc, m->tt, ph, bc, (const T*)m->xu);
+      k_bnd_flux<T, false><<<nblk(nbp, tb), tb, 0, s>>>(
+          int(nbp), bidx, bbc, bnp, (const T*)m->uf, nullptr, (T*)m->fc, m->tt, ph,
+          bc, xup);
     PROF_END(FR_KC_BND_F);
   }
   const bool aa = m->aa_qdeg > 0;
@@ -2041,6 +2106,68 @@ int group_run(fr_group* g, int mode, double dt, int nsteps) {
   return FR_OK;
 }
 
+// ------------------------------------------------- exchange between processes
+// One phase of one RK stage of a part whose partners live in other
+// processes; the caller moves the traces between the phases
+// (exchange_pack / exchange_unpack around its transport).  phase 1: NS
+// common solution and gradients (nothing for Euler); phase 2: common
+// fluxes, volume kernels and the stage's RK update.  part: 0 all, 1
+// interior (no exchange point involved), 2 exchange-adjacent.
+template <typename T, typename TR>
+int do_stage(fr_mesh* m, int scheme, double dt, int stage, int phase, int part) {
+  const int mode = scheme == FR_RK4 ? 1 : 2, nst = scheme == FR_RK4 ? 4 : 5;
+  if (stage == 0 && phase == 1 && part <= 1) {
+    if (m->variant != FR_VARIANT_AUTO) {
+      int rv = resolve_variant<T, TR>(m, scheme, dt);
+      if (rv) return rv;
+    } else {
+      m->tuned = true;  // no tuning of a part: every rank runs the default family
+    }
+    m->h_dt = dt;
+    CK(cudaMemcpyAsync(m->d_dt, &m->h_dt, sizeof(double), cudaMemcpyHostToDevice, m->stream));
+    CK(cudaMemsetAsync(m->d_flag, 0, sizeof(int), m->stream));
+    int rc = ensure_uf<T, TR>(m);
+    if (rc) return rc;
+  }
+  launch_stage<T, TR>(m, m->stream, mode, stage, nullptr, phase, part);
+  CK(cudaGetLastError());
+  if (stage == nst - 1 && phase == 2 && part != 1) {
+    int flag = 0;
+    CK(cudaMemcpyAsync(&flag, m->d_flag, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+    if (flag & 2) return fail(FR_ETIMEOUT, "a tensor-core wait timed out");
+    if (flag) return fail(FR_ENONFINITE, "a stage of the part is not finite");
+  }
+  return FR_OK;
+}
+
+// what 0: solution traces (5 values per point); 1: gradient traces (15,
+// FP64 values) or viscous normal fluxes (5, FP32 values).
+template <typename T, typename TR>
+int exchange_pack(fr_mesh* m, int what, void* buf) {
+  if (what == 0) {
+    int rc = ensure_uf<T, TR>(m);
+    if (rc) return rc;
+  }
+  if (m->n_xlist == 0) return FR_OK;
+  const int nv = what == 0 ? 5 : (sizeof(T) == 4 ? 5 : 15);
+  k_exchange_gather<T><<<nblk(m->n_xlist, 256), 256, 0, m->stream>>>(
+      int(m->n_xlist), m->x_list, m->bidx, what == 0 ? (const T*)m->uf : (const T*)m->gradf,
+      nv, (T*)buf, m->tt);
+  CK(cudaGetLastError());
+  return FR_OK;
+}
+
+template <typename T, typename TR>
+int exchange_unpack(fr_mesh* m, int what, const void* buf) {
+  if (m->n_xlist == 0) return FR_OK;
+  const int nv = what == 0 ? 5 : (sizeof(T) == 4 ? 5 : 15);
+  k_exchange_scatter<T><<<nblk(m->n_xlist, 256), 256, 0, m->stream>>>(
+      int(m->n_xlist), m->x_list, (const T*)buf, nv, what == 0 ? (T*)m->xu : (T*)m->xg);
+  CK(cudaGetLastError());
+  return FR_OK;
+}
+
 // Match every member's exchange points with their partners; fills the push
 // lists and the partners' |S^T n~| (xm) of every member.
 template <typename T, typename TR>
@@ -2218,6 +2345,9 @@ struct PrecTable {
   int (*group_setup)(fr_group*);
   int (*group_run)(fr_group*, int, double, int);
   int (*filter_solution)(fr_mesh*, const double*);
+  int (*do_stage)(fr_mesh*, int, double, int, int, int);
+  int (*exchange_pack)(fr_mesh*, int, void*);
+  int (*exchange_unpack)(fr_mesh*, int, const void*);
 };
 
 extern const PrecTable kPrecF64, kPrecF32, kPrecMixed;
@@ -2234,6 +2364,8 @@ inline const PrecTable& prec_table(int precision) {
                           &do_rhs<T, TR>,         &do_rk<T, TR>,              \
                           &do_rk_adaptive<T, TR>, &do_profile<T, TR>,         \
                           &aa_setup<T, TR>,       &group_setup<T, TR>,        \
-                          &group_run<T, TR>,      &filter_solution<T, TR>};   \
+                          &group_run<T, TR>,      &filter_solution<T, TR>,    \
+                          &do_stage<T, TR>,       &exchange_pack<T, TR>,      \
+                          &exchange_unpack<T, TR>};                           \
   }
 

@@ -549,6 +549,32 @@ __global__ void k_exchange_push(int n, const int32_t* __restrict__ code,
   for (int c = 0; c < nv; ++c) d[c] = src[fp_index(tt, t, e, f, nv, c)];
 }
 
+// Exchange with other processes: gather the traces (nv values per point) at
+// the listed own exchange points into a message buffer [n][nv], and scatter
+// a received buffer into the receive slots of the same points.
+template <typename T>
+__global__ void k_exchange_gather(int n, const int32_t* __restrict__ list,
+                                  const int32_t* __restrict__ bidx,
+                                  const T* __restrict__ src, int nv,
+                                  T* __restrict__ dst, TypeTab tt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int t, f;
+  long long e;
+  decode_fp(bidx[list[i]], tt, &t, &e, &f);
+  for (int c = 0; c < nv; ++c) dst[(long long)i * nv + c] = src[fp_index(tt, t, e, f, nv, c)];
+}
+
+template <typename T>
+__global__ void k_exchange_scatter(int n, const int32_t* __restrict__ list,
+                                   const T* __restrict__ src, int nv,
+                                   T* __restrict__ dst) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const long long slot = list[i];
+  for (int c = 0; c < nv; ++c) dst[slot * nv + c] = src[(long long)i * nv + c];
+}
+
 // ---------------------------------------------------------------------------
 // Dense kernels (prisms, tetrahedra, and the dense hexahedron variant) are
 // persistent: each CTA copies the type's operators into shared memory once

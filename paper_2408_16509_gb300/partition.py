@@ -15,15 +15,27 @@ def _as_dict(spec):
     return spec.as_dict() if hasattr(spec, "as_dict") else dict(spec)
 
 
-def split(spec, nparts, mode="weighted", weights=None, order=1):
+def split(spec, nparts, mode="weighted", weights=None, order=1, halo_last=False):
     """Partition `spec` into nparts and return (sub_specs, element_ids):
     sub_specs[r] is a mesh description of part r (all nodes kept, its
     elements, the original boundary faces plus its exchange faces tagged
     EXCHANGE_TAG); element_ids[r][t] are the indices, within type t of the
-    full mesh, of part r's elements (for scattering solutions)."""
+    full mesh, of part r's elements (for scattering solutions).  halo_last:
+    each type's elements that border another part come after the others,
+    so that a stage's interior work (fr_rk_stage part 1) is one contiguous
+    range and can overlap the exchange."""
     d = _as_dict(spec)
     host = FRMesh(d, order, bcs={k: ("extrap",) for k in _tags(d)}, device=-1)
     part = host.partition(nparts, mode, weights)
+    halo = {}
+    if halo_last:
+        types0 = [t for t in ORDER if t in d["elements"] and len(d["elements"][t])]
+        offs0 = np.cumsum([0] + [len(d["elements"][t]) for t in types0])
+        for i, t in enumerate(types0):
+            nbr = host.adjacency(t)
+            mine = part[offs0[i]:offs0[i + 1]]
+            other = np.where(nbr >= 0, part[np.maximum(nbr, 0)], mine[:, None])
+            halo[t] = np.any(other != mine[:, None], axis=1)
     subs, ids = [], []
     types = [t for t in ORDER if t in d["elements"] and len(d["elements"][t])]
     offs = np.cumsum([0] + [len(d["elements"][t]) for t in types])
@@ -31,6 +43,8 @@ def split(spec, nparts, mode="weighted", weights=None, order=1):
         el, mp, idr = {}, {}, {}
         for i, t in enumerate(types):
             sel = np.nonzero(part[offs[i]:offs[i + 1]] == r)[0]
+            if halo_last:
+                sel = np.concatenate([sel[~halo[t][sel]], sel[halo[t][sel]]])
             idr[t] = sel
             if len(sel):
                 el[t] = np.asarray(d["elements"][t])[sel]
