@@ -6,5 +6,5 @@ points.  It contains none of the FR method's arithmetic: no point sets, no
 operators, no fluxes.  Both the oracle and the CUDA library consume its
 output; neither is imported here.
 """
-from .meshes import box_hex, curved_box_hex, mixed_box, MeshSpec  # noqa: F401
+from .meshes import box_hex, curved_box_hex, curved_mixed_box, mixed_box, MeshSpec  # noqa: F401
 from . import ics  # noqa: F401

@@ -10,9 +10,12 @@ Vertex order conventions (the library's documented input format):
 Boundary nodes of periodic directions are distinct nodes; periodic faces are
 paired by the translation vectors returned in ``periodic``.
 
-Curved (quadratic) hexahedra carry, besides their 8 corner ids, the ids of
-27 map nodes in tensor order: node a + 3 b + 9 c sits at reference point
-(-1 + a, -1 + b, -1 + c), a, b, c in {0, 1, 2} (``maps``).
+Curved (quadratic) elements carry, besides their corner ids, the ids of
+their map nodes (``maps``): hexahedra 27 nodes in tensor order (node
+a + 3 b + 9 c at reference point (-1 + a, -1 + b, -1 + c)); prisms 18 nodes,
+node = triangle node + 6 * layer with triangle nodes v0, v1, v2 and the
+midpoints of edges 01, 12, 02 and layers z = -1, 0, 1; tetrahedra 10 nodes,
+the vertices and then the midpoints of edges 01, 12, 02, 03, 13, 23.
 """
 from dataclasses import dataclass, field
 
@@ -269,3 +272,73 @@ def curved_box_hex(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), periodic=(0, 1, 2)
     bf = _boundary_faces(n, f2, set(periodic), tags)
     return MeshSpec(nodes, {"hex": corner.astype(np.int64)}, pv, bf,
                     {"hex": (2, hmap.astype(np.int64))})
+
+
+# reference coordinates of the quadratic map nodes of each element type, in
+# the library's node order (see the module docstring)
+_Q2_REF = {
+    "hex": np.array([[-1 + a, -1 + b, -1 + c] for c in range(3) for b in range(3)
+                     for a in range(3)], float),
+    "pri": np.array([[x, y, z] for z in (-1.0, 0.0, 1.0)
+                     for x, y in ((-1, -1), (1, -1), (-1, 1), (0, -1), (0, 0), (-1, 0))],
+                    float),
+    "tet": np.array([[-1, -1, -1], [1, -1, -1], [-1, 1, -1], [-1, -1, 1],
+                     [0, -1, -1], [0, 0, -1], [-1, 0, -1], [-1, -1, 0],
+                     [0, -1, 0], [-1, 0, 0]], float),
+}
+
+
+def _linear_shape(kind, x):
+    """Linear (vertex) shape functions of the reference element at x (n, 3)."""
+    if kind == "hex":
+        s = np.array([[-1, -1, -1], [1, -1, -1], [1, 1, -1], [-1, 1, -1],
+                      [-1, -1, 1], [1, -1, 1], [1, 1, 1], [-1, 1, 1]], float)
+        return np.prod(1 + x[:, None, :] * s[None], axis=2) / 8.0
+    if kind == "pri":
+        lam = np.stack([-(x[:, 0] + x[:, 1]) / 2, (1 + x[:, 0]) / 2, (1 + x[:, 1]) / 2], 1)
+        zl, zh = (1 - x[:, 2:3]) / 2, (1 + x[:, 2:3]) / 2
+        return np.concatenate([lam * zl, lam * zh], axis=1)
+    return np.stack([-(1 + x[:, 0] + x[:, 1] + x[:, 2]) / 2, (1 + x[:, 0]) / 2,
+                     (1 + x[:, 1]) / 2, (1 + x[:, 2]) / 2], axis=1)
+
+
+def curved_mixed_box(n=8, x_pri=0.34, x_tet=0.67, amp=0.05, periodic_x=False):
+    """The mixed_box layout (hexahedra, prisms, Kuhn tetrahedra; no vertex
+    jitter) with quadratic maps on every element: 27-node hexahedra, 18-node
+    prisms, 10-node tetrahedra.  All map nodes lie on the (2n+1)^3 lattice
+    of half-cell points (vertices, edge midpoints, face and cell centres),
+    displaced by the smooth field of curved_box_hex (corners stay on the
+    grid), so neighbouring elements share their face nodes."""
+    coarse = mixed_box(n=n, x_pri=x_pri, x_tet=x_tet, perturb=0.0,
+                       periodic_x=periodic_x)
+    N = (n, n, n)
+    m = (2 * n, 2 * n, 2 * n)
+    lat = _grid_nodes(m, (0, 0, 0), (1, 1, 1))
+    h = np.full(3, 1.0 / n)
+    X = lat
+    sn = [np.sin(np.pi * n * X[:, k]) for k in range(3)]
+    d = np.stack([h[k] * (sn[(k + 1) % 3] + sn[(k + 2) % 3])
+                  * (1.0 + 0.5 * np.cos(2.0 * np.pi * n * X[:, k]))
+                  for k in range(3)], axis=1)
+    nodes = lat + amp * d
+    g = _nid(m)
+    # lattice coordinates of the coarse grid's nodes
+    ci = np.arange((n + 1) ** 3)
+    cl = np.stack([2 * (ci % (n + 1)), 2 * ((ci // (n + 1)) % (n + 1)),
+                   2 * (ci // (n + 1) ** 2)], axis=1)
+
+    def lid(c):
+        return g(c[..., 0], c[..., 1], c[..., 2])
+    elements, maps = {}, {}
+    for kind, conn in coarse.elements.items():
+        if len(conn) == 0:
+            continue
+        Nl = _linear_shape(kind, _Q2_REF[kind])            # (n_map, n_vert)
+        vc = cl[conn]                                      # (ne, n_vert, 3)
+        q = np.einsum("mv,evk->emk", Nl, vc)
+        qi = np.rint(q).astype(np.int64)
+        assert np.abs(q - qi).max() < 1e-9
+        maps[kind] = (2, lid(qi))
+        elements[kind] = lid(vc)
+    bf = [(tuple(int(lid(cl[v])) for v in ids), tag) for ids, tag in coarse.bfaces]
+    return MeshSpec(nodes, elements, coarse.periodic, bf, maps)

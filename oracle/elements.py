@@ -256,6 +256,16 @@ class Hex(ElementType):
 
 
     # quadratic map (27 nodes, tensor order a + 3b + 9c at (-1+a, -1+b, -1+c))
+    def q2_nodes(self):
+        a = np.array([-1.0, 0.0, 1.0])
+        c, b, aa = np.meshgrid(a, a, a, indexing="ij")
+        return np.stack([aa.ravel(), b.ravel(), c.ravel()], axis=1)
+
+    def curl_nodes(self):
+        g = gauss_lobatto(self.p + 1)[0]
+        c, b, a = np.meshgrid(g, g, g, indexing="ij")
+        return np.stack([a.ravel(), b.ravel(), c.ravel()], axis=1)
+
     @staticmethod
     def _lag2(s):
         """Quadratic Lagrange polynomials on {-1, 0, 1} and their slopes."""
@@ -315,6 +325,55 @@ class Prism(ElementType):
         zl, zh = (1 - x[:, 2:3]) / 2, (1 + x[:, 2:3]) / 2
         return np.concatenate([lam * zl, lam * zh], axis=1)
 
+    # quadratic map (18 nodes): quadratic triangle (vertices 0, 1, 2, then the
+    # midpoints of edges 01, 12, 02) times the quadratic line (z = -1, 0, 1),
+    # node = triangle node + 6 * layer; the corners are nodes 0, 1, 2, 12, 13, 14
+    def q2_nodes(self):
+        tri = np.array([[-1, -1], [1, -1], [-1, 1], [0, -1], [0, 0], [-1, 0]], float)
+        return np.concatenate([np.column_stack([tri, np.full(6, z)])
+                               for z in (-1.0, 0.0, 1.0)])
+
+    @staticmethod
+    def _tri2(lam, dlam):
+        """Quadratic triangle basis and its gradients from barycentrics."""
+        l0, l1, l2 = lam[:, 0], lam[:, 1], lam[:, 2]
+        v = np.stack([l0 * (2 * l0 - 1), l1 * (2 * l1 - 1), l2 * (2 * l2 - 1),
+                      4 * l0 * l1, 4 * l1 * l2, 4 * l0 * l2], axis=1)
+        g = []
+        for j in range(2):
+            d0, d1, d2 = dlam[0][j], dlam[1][j], dlam[2][j]
+            g.append(np.stack([(4 * l0 - 1) * d0, (4 * l1 - 1) * d1, (4 * l2 - 1) * d2,
+                               4 * (d0 * l1 + l0 * d1), 4 * (d1 * l2 + l1 * d2),
+                               4 * (d0 * l2 + l0 * d2)], axis=1))
+        return v, g
+
+    def _q2_parts(self, x):
+        lam = self._bary(x)
+        dlam = [(-0.5, -0.5), (0.5, 0.0), (0.0, 0.5)]
+        tv, tg = self._tri2(lam, dlam)
+        t = x[:, 2]
+        lv = np.stack([0.5 * t * (t - 1), 1 - t * t, 0.5 * t * (t + 1)], axis=1)
+        ld = np.stack([t - 0.5, -2 * t, t + 0.5], axis=1)
+        return tv, tg, lv, ld
+
+    def q2_shape(self, x):
+        tv, _, lv, _ = self._q2_parts(x)
+        return np.einsum("pl,pa->pla", lv, tv).reshape(len(x), 18)
+
+    def q2_dshape(self, x):
+        tv, tg, lv, ld = self._q2_parts(x)
+        return np.stack([np.einsum("pl,pa->pla", lv, tg[0]).reshape(len(x), 18),
+                         np.einsum("pl,pa->pla", lv, tg[1]).reshape(len(x), 18),
+                         np.einsum("pl,pa->pla", ld, tv).reshape(len(x), 18)])
+
+    def curl_nodes(self):
+        """Nodes of the curl-form metric interpolant: the tetrahedron's face
+        node set on the triangle times Gauss-Lobatto points along z (nodes
+        on every face, shared with hexahedron and tetrahedron faces)."""
+        t = tri_face_points(self.p)
+        z = gauss_lobatto(self.p + 1)[0]
+        return np.concatenate([np.column_stack([t, np.full(len(t), zz)]) for zz in z])
+
     def dshape(self, x):
         lam = self._bary(x)
         zl, zh = (1 - x[:, 2:3]) / 2, (1 + x[:, 2:3]) / 2
@@ -361,6 +420,37 @@ class Tet(ElementType):
         base = np.array([[-0.5, 0.5, 0.0, 0.0], [-0.5, 0.0, 0.5, 0.0],
                          [-0.5, 0.0, 0.0, 0.5]])
         return np.stack([np.tile(base[j], (n, 1)) for j in range(3)])
+
+    # quadratic map (10 nodes): the vertices, then the midpoints of edges
+    # 01, 12, 02, 03, 13, 23
+    EDGES = ((0, 1), (1, 2), (0, 2), (0, 3), (1, 3), (2, 3))
+
+    def q2_nodes(self):
+        v = np.array([[-1, -1, -1], [1, -1, -1], [-1, 1, -1], [-1, -1, 1]], float)
+        return np.concatenate([v, [(v[a] + v[b]) / 2 for a, b in self.EDGES]])
+
+    def q2_shape(self, x):
+        lam = self.shape(x)                                  # barycentrics
+        return np.concatenate([lam * (2 * lam - 1),
+                               np.stack([4 * lam[:, a] * lam[:, b]
+                                         for a, b in self.EDGES], axis=1)], axis=1)
+
+    def q2_dshape(self, x):
+        lam = self.shape(x)
+        dl = self.dshape(x)                                  # (3, npts, 4)
+        out = []
+        for j in range(3):
+            d = dl[j]
+            out.append(np.concatenate(
+                [(4 * lam - 1) * d,
+                 np.stack([4 * (d[:, a] * lam[:, b] + lam[:, a] * d[:, b])
+                           for a, b in self.EDGES], axis=1)], axis=1))
+        return np.stack(out)
+
+    def curl_nodes(self):
+        """Nodes of the curl-form metric interpolant: the warp-and-blend
+        nodes (vertices, edges and faces included)."""
+        return tet_nodes(self.p) if self.p > 0 else self.upts
 
 
 ETYPES = {"hex": Hex, "pri": Prism, "tet": Tet}

@@ -8,11 +8,12 @@ partner with the same physical coordinates.
 
 * metrics: S = det(J) J^{-1} at solution and flux points, straight from the
   vertex map (linear elements, Section 3.4: metrics from the vertices);
-* curved elements (hexahedra with a quadratic 27-node map, "Curved
-  Elements" of Section 3.4): the conservative metric, i.e. the curl form
-  S[i][n] = -(curl_xi I(X_l grad_xi X_m))_i, (n, m, l) cyclic, with I the
-  order-p interpolation on the Gauss-Lobatto nodes, evaluated at the
-  solution and flux points; det J is the map's own;
+* curved elements (quadratic maps: 27-node hexahedra, 18-node prisms,
+  10-node tetrahedra, "Curved Elements" of Section 3.4): the conservative
+  metric, i.e. the curl form S[i][n] = -(curl_xi I(X_l grad_xi X_m))_i,
+  (n, m, l) cyclic, with I the order-p interpolation on a node set with
+  nodes on every face, evaluated at the solution and flux points; det J is
+  the map's own;
 * surface normal at a flux point: S^T n~ (Nanson), split into its magnitude
   and the physical unit normal;
 * faces are paired by their vertex sets; faces left over are paired
@@ -35,13 +36,30 @@ class MeshError(ValueError):
 
 
 def curl_metric(el, Xm, pts):
-    """Conservative (curl-form) metric of quadratic hexahedron maps at the
-    reference points pts.  Xm: (ne, 27, 3) map nodes.  The fields
+    """Conservative (curl-form) metric of quadratic maps at the reference
+    points pts.  Xm: (ne, n_map, 3) map nodes.  The fields
     w^n_j = X_l dX_m/dxi_j ((n, m, l) cyclic) are interpolated by the
-    order-p tensor Lagrange polynomial on the (p+1)^3 Gauss-Lobatto nodes
-    (nodes on every face: a face's normal component depends on that face
-    only, so neighbours agree), and S[i][n] = -(curl_xi of it)_i at pts.
-    Returns S[e, q, i, n] (= det J dxi_i/dx_n)."""
+    order-p polynomial of the element's solution space on a node set with
+    nodes on every face (a face's normal component depends on that face
+    only, so neighbours agree): the (p+1)^3 Gauss-Lobatto nodes on
+    hexahedra, el.curl_nodes() on prisms and tetrahedra; then
+    S[i][n] = -(curl_xi of it)_i at pts.  Returns S[e, q, i, n]
+    (= det J dxi_i/dx_n)."""
+    if el.name != "hex":
+        G = el.curl_nodes()
+        Vi = np.linalg.inv(el.basis(G))
+        dB = [gj @ Vi for gj in el.grad(pts)]                    # (npts, nG)
+        X = np.einsum("pv,evk->epk", el.q2_shape(G), Xm)
+        dX = np.einsum("jpv,evk->epjk", el.q2_dshape(G), Xm)
+        S = np.zeros((Xm.shape[0], len(pts), 3, 3))
+        for n in range(3):
+            m, l = (n + 1) % 3, (n + 2) % 3
+            w = X[:, :, l, None] * dX[:, :, :, m]
+            for i in range(3):
+                j, k = (i + 1) % 3, (i + 2) % 3
+                S[:, :, i, n] = -(np.einsum("pg,eg->ep", dB[j], w[:, :, k])
+                                  - np.einsum("pg,eg->ep", dB[k], w[:, :, j]))
+        return S
     g, _ = gauss_lobatto(el.p + 1)
     n1 = len(g)
     c, b, a = np.meshgrid(g, g, g, indexing="ij")
@@ -101,8 +119,6 @@ class FRMesh:
             morder, mconn = maps.get(t, (1, None))
             self.curved[t] = morder == 2
             if morder == 2:
-                if t != "hex":
-                    raise MeshError("quadratic maps are implemented for hexahedra")
                 Xm = nodes[np.asarray(mconn, np.int64)]
                 self._Xm[t] = Xm
                 self.upts_x[t] = np.einsum("pv,evk->epk", el.q2_shape(el.upts), Xm)

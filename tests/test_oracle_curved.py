@@ -1,11 +1,19 @@
-"""Pins for the oracle's curved (quadratic) hexahedra and their conservative
+"""Pins for the oracle's curved (quadratic) elements and their conservative
 metric ("Curved Elements", Section 3.4): the curl form keeps a uniform flow
-uniform on curved grids where the pointwise cross-product metric does not
-(the comparison the paper draws in its free-stream figure)."""
+uniform on curved grids, including where the pointwise cross-product metric
+does not (the comparison the paper draws in its free-stream figure); it is
+exact for straight elements written as quadratic maps, discretely
+divergence free, and conservative across curved faces.
+
+The pointwise metric is swapped in while the mesh is built, so that the
+interface normals come from it too.  So built, it keeps free stream on
+quadratic hexahedra for p >= 2 as well; it fails at p = 1 and, at p = 2, on
+prisms and tetrahedra -- those are the discriminating cases."""
 import numpy as np
 import pytest
 
-from frinputs import box_hex, curved_box_hex, ics
+import oracle.mesh as omesh
+from frinputs import box_hex, curved_box_hex, curved_mixed_box, ics, mixed_box
 from oracle.fr import FRSystem
 from oracle.mesh import FRMesh
 
@@ -20,21 +28,46 @@ def _uniform(m):
     return {"hex": u}
 
 
-def _cross_product_metric(m, spec):
-    """Replace the mesh's metric by the map's pointwise cross-product one."""
-    el = m.el["hex"]
-    Xm = spec.nodes[spec.maps["hex"][1]]
+def _pointwise_metric(el, Xm, pts):
+    """S = det J J^{-1} from the cross products of the map's columns."""
+    a = np.einsum("jpv,evk->epjk", el.q2_dshape(pts), Xm)
+    return np.stack([np.cross(a[:, :, 1], a[:, :, 2]),
+                     np.cross(a[:, :, 2], a[:, :, 0]),
+                     np.cross(a[:, :, 0], a[:, :, 1])], axis=2)
 
-    def cross(x):
-        a = np.einsum("jpv,evk->epjk", el.q2_dshape(x), Xm)
-        return np.stack([np.cross(a[:, :, 1], a[:, :, 2]),
-                         np.cross(a[:, :, 2], a[:, :, 0]),
-                         np.cross(a[:, :, 0], a[:, :, 1])], axis=2)
-    m.S_u["hex"] = cross(el.upts)
-    nv = np.einsum("epij,pi->epj", cross(el.fpts), el.fpts_norm)
-    mag = np.linalg.norm(nv, axis=2)
-    m.fmag["hex"] = mag
-    m.fnorm["hex"] = nv / mag[:, :, None]
+
+def _mesh(spec, p, pointwise=False):
+    if not pointwise:
+        return FRMesh(spec.as_dict(), p)
+    orig = omesh.curl_metric
+    omesh.curl_metric = _pointwise_metric
+    try:
+        return FRMesh(spec.as_dict(), p)
+    finally:
+        omesh.curl_metric = orig
+
+
+def _jittered(spec, n, frac=0.1, seed=3):
+    """Generic quadratic maps: the mid-edge, face and cell nodes strictly
+    inside the box moved by U(-a, a) per component, a = frac h / 2."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    m = 2 * n + 1
+    ids = np.arange(len(spec.nodes))
+    ijk = np.stack([ids % m, (ids // m) % m, ids // (m * m)], axis=1)
+    mv = np.all((ijk > 0) & (ijk < m - 1), axis=1) & np.any(ijk % 2 == 1, axis=1)
+    spec.nodes = spec.nodes.copy()
+    spec.nodes[mv] += rng.uniform(-1, 1, (mv.sum(), 3)) * frac / (2 * n)
+    return spec
+
+
+UNIFORM_BCS = {k: ("state", 1.0, 0.5, 0.3, 0.2, 1.0) for k in range(6)}
+
+
+def _free_stream_residual(m, physics="euler"):
+    u = {t: ics.uniform(m.upts_x[t].reshape(-1, 3), vel=(0.5, 0.3, 0.2)).reshape(m.ne[t], -1, 5)
+         for t in m.types}
+    r = FRSystem(m, physics, mu=0.01, bcs=UNIFORM_BCS).rhs(u)
+    return max(np.abs(v).max() for v in r.values())
 
 
 @pytest.mark.parametrize("p", [2, 3])
@@ -46,15 +79,31 @@ def test_curl_metric_is_discretely_divergence_free(p):
         assert np.abs(div).max() < 1e-12 * np.abs(S).max()
 
 
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_free_stream_kept_by_conservative_metric(p):
+    spec = _jittered(curved_box_hex((3, 3, 3)), 3)
+    assert _free_stream_residual(_mesh(spec, p)) < 1e-10     # residual scale ~1e2
+
+
+def test_pointwise_metric_loses_free_stream_where_curl_form_keeps_it():
+    """Quadratic hexahedra at p = 1 and curved prisms / tetrahedra at p = 2:
+    the pointwise metric leaves a residual of order one, the curl form
+    round-off."""
+    hexes = _jittered(curved_box_hex((3, 3, 3)), 3)
+    assert _free_stream_residual(_mesh(hexes, 1)) < 1e-11
+    assert _free_stream_residual(_mesh(hexes, 1, pointwise=True)) > 1e-2
+    mixed = _jittered(curved_mixed_box(n=3), 3)
+    assert _free_stream_residual(_mesh(mixed, 2)) < 1e-10
+    assert _free_stream_residual(_mesh(mixed, 2, pointwise=True)) > 1e-2
+
+
 @pytest.mark.parametrize("p", [2, 3])
-def test_free_stream_kept_by_conservative_metric_not_by_cross_product(p):
-    spec = curved_box_hex((3, 3, 3))
-    m = FRMesh(spec.as_dict(), p)
-    R = FRSystem(m, "euler").rhs(_uniform(m))["hex"]
-    assert np.abs(R).max() < 1e-10          # residual scale ~1e2
-    _cross_product_metric(m, spec)
-    Rx = FRSystem(m, "euler").rhs(_uniform(m))["hex"]
-    assert np.abs(Rx).max() > 1e-3
+@pytest.mark.parametrize("physics", ["euler", "ns"])
+def test_free_stream_on_curved_mixed_mesh(p, physics):
+    """Quadratic 27-node hexahedra, 18-node prisms and 10-node tetrahedra
+    with generic (jittered) maps."""
+    spec = _jittered(curved_mixed_box(n=3), 3)
+    assert _free_stream_residual(_mesh(spec, p), physics) < 1e-10
 
 
 @pytest.mark.parametrize("p", [2, 3])
@@ -92,4 +141,51 @@ def test_conservation_on_curved_periodic_mesh():
     R = sysm.rhs(u)["hex"]
     tot = np.einsum("q,eq,eqk->k", el.W, m.detJ["hex"], R)
     scale = np.einsum("q,eq,eqk->k", el.W, m.detJ["hex"], np.abs(R))
+    assert np.all(np.abs(tot) < 1e-13 * scale.max()), tot / scale.max()
+
+
+@pytest.mark.parametrize("kind", ["pri", "tet"])
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_curl_metric_equals_analytic_on_straight_simplices(kind, p):
+    """Straight prisms and tetrahedra written as quadratic maps: the curl form
+    equals the map's analytic metric at solution and flux points."""
+    lin = mixed_box(n=2, x_pri=0.0 if kind == "pri" else 1.0, x_tet=1.0 if kind == "pri" else 0.0,
+                    perturb=0.05)
+    ml = FRMesh(lin.as_dict(), p)
+    el = ml.el[kind]
+    V = lin.nodes[lin.elements[kind]]
+    Xq = el.map_points(V, el.q2_nodes())
+    nmap = Xq.shape[1]
+    nodes = np.concatenate([lin.nodes, Xq.reshape(-1, 3)])
+    mids = len(lin.nodes) + np.arange(Xq.shape[0] * nmap).reshape(-1, nmap)
+    spec = dict(lin.as_dict())
+    spec["nodes"] = nodes
+    spec["maps"] = {kind: (2, mids)}
+    mc = FRMesh(spec, p)
+    scale = np.abs(ml.S_u[kind]).max()
+    assert np.abs(mc.S_u[kind] - ml.S_u[kind]).max() < 1e-13 * scale
+    assert np.abs(mc.fmag[kind] - ml.fmag[kind]).max() < 1e-13 * scale
+    assert np.abs(mc.detJ[kind] - ml.detJ[kind]).max() < 1e-13 * np.abs(ml.detJ[kind]).max()
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_curl_metric_of_simplices_is_discretely_divergence_free(p):
+    m = FRMesh(_jittered(curved_mixed_box(n=3), 3).as_dict(), p)
+    for t in ("pri", "tet"):
+        el, S = m.el[t], m.S_u[t]
+        for n in range(3):
+            div = sum(np.einsum("pq,eq->ep", el.D[i], S[:, :, i, n]) for i in range(3))
+            assert np.abs(div).max() < 1e-12 * np.abs(S).max()
+
+
+@pytest.mark.parametrize("layout", [(0.0, 1.0), (0.0, 0.0), (0.5, 1.0)])
+def test_conservation_on_curved_periodic_mixed_meshes(layout):
+    """All prisms, all tetrahedra, hexahedra | prisms; curved and periodic."""
+    spec = _jittered(curved_mixed_box(n=3, x_pri=layout[0], x_tet=layout[1],
+                                      periodic_x=True), 3)
+    m = FRMesh(spec.as_dict(), 3)
+    u = {t: ics.flow3d(m.upts_x[t].reshape(-1, 3)).reshape(m.ne[t], -1, 5) for t in m.types}
+    R = FRSystem(m, "ns", mu=0.02).rhs(u)
+    tot = sum(np.einsum("q,eq,eqk->k", m.el[t].W, m.detJ[t], R[t]) for t in m.types)
+    scale = sum(np.einsum("q,eq,eqk->k", m.el[t].W, m.detJ[t], np.abs(R[t])) for t in m.types)
     assert np.all(np.abs(tot) < 1e-13 * scale.max()), tot / scale.max()
