@@ -65,15 +65,26 @@ typedef struct {
   const int64_t* conn;  /* [n_elem][n_vertices] node ids (face pairing; and
                            the map of straight elements) */
   int map_order;        /* 0 or 1: straight elements (vertex map); 2:
-                           quadratic map (hexahedra only, Section 3.4
-                           "Curved Elements") given by map_conn */
-  const int64_t* map_conn;  /* map_order 2: [n_elem][27] node ids, node
-                               a + 3b + 9c at reference point (-1+a, -1+b,
-                               -1+c); its corner nodes must be the vertices
-                               of conn.  Metrics of curved elements: the
-                               conservative curl form
-                               S[i][n] = -(curl I(X_l grad X_m))_i, I the
-                               order-p interpolant on Gauss-Lobatto nodes */
+                           quadratic map (Section 3.4 "Curved Elements")
+                           given by map_conn */
+  const int64_t* map_conn;  /* map_order 2: [n_elem][n_map] node ids of the
+                               quadratic map; its vertex nodes must be the
+                               vertices of conn.
+                               FR_HEX8, 27 nodes: node a + 3b + 9c at
+                               reference point (-1+a, -1+b, -1+c);
+                               FR_PRI6, 18 nodes: triangle node + 6 layer,
+                               triangle nodes v0, v1, v2 and the midpoints of
+                               edges 01, 12, 02, layers z = -1, 0, 1 (the
+                               vertices are nodes 0, 1, 2, 12, 13, 14);
+                               FR_TET4, 10 nodes: v0..v3, then the midpoints
+                               of edges 01, 12, 02, 03, 13, 23.
+                               Metrics of curved elements: the conservative
+                               curl form S[i][n] = -(curl I(X_l grad X_m))_i,
+                               I the order-p interpolant on nodes with nodes
+                               on every face (Gauss-Lobatto tensor nodes,
+                               warp-and-blend tetrahedron nodes, the
+                               tetrahedron's face nodes times Gauss-Lobatto
+                               points for prisms) */
 } fr_etype_desc;
 
 typedef struct {

@@ -55,8 +55,8 @@ int fr_mesh_create(const fr_mesh_desc* d, fr_mesh** out) {
     if (t.n_elem < 0 || (t.n_elem > 0 && !t.conn)) return fail(FR_EINVAL, "bad connectivity");
     if (t.map_order < 0 || t.map_order > 2)
       return fail(FR_EINVAL, "map order must be 0, 1 or 2");
-    if (t.map_order == 2 && (t.etype != FR_HEX8 || (t.n_elem > 0 && !t.map_conn)))
-      return fail(FR_EINVAL, "quadratic maps: hexahedra with map_conn only");
+    if (t.map_order == 2 && t.n_elem > 0 && !t.map_conn)
+      return fail(FR_EINVAL, "quadratic maps need map_conn");
     seen[t.etype] = true;
     if (t.etype == FR_PRI6 && t.n_elem > 0 && d->point_family == FR_POINTS_GLL)
       return fail(FR_EINVAL, "Gauss-Lobatto hexahedra cannot meet prisms (their quad faces carry Gauss-Legendre points)");

@@ -270,7 +270,182 @@ void parallel_elements(int64_t ne, F body) {
   for (auto& th : pool) th.join();
 }
 
+// Number of map nodes of a quadratic element and the map node of each vertex.
+int q2_nodes(int kind) { return kind == EK_HEX ? 27 : (kind == EK_PRI ? 18 : 10); }
+const int* q2_corners(int kind) {
+  static const int hexc[8] = {0, 2, 8, 6, 18, 20, 26, 24};
+  static const int pric[6] = {0, 1, 2, 12, 13, 14};
+  static const int tetc[4] = {0, 1, 2, 3};
+  return kind == EK_HEX ? hexc : (kind == EK_PRI ? pric : tetc);
+}
+
+// x_k(pt) and a[j][k] = d x_k / d xi_j of a quadratic prism (18 nodes:
+// triangle node + 6 layer, triangle nodes v0 v1 v2 and the midpoints of
+// edges 01, 12, 02, layers z = -1, 0, 1) or tetrahedron (10 nodes: the
+// vertices, then the midpoints of edges 01, 12, 02, 03, 13, 23).
+void q2s_eval(int kind, const double* X, const double* pt, double x[3], double a[3][3]) {
+  double N[18], dN[3][18];
+  int nn;
+  if (kind == EK_TET) {
+    nn = 10;
+    const double lam[4] = {-(1 + pt[0] + pt[1] + pt[2]) / 2, (1 + pt[0]) / 2,
+                           (1 + pt[1]) / 2, (1 + pt[2]) / 2};
+    const double dl[4][3] = {{-0.5, -0.5, -0.5}, {0.5, 0, 0}, {0, 0.5, 0}, {0, 0, 0.5}};
+    static const int E[6][2] = {{0, 1}, {1, 2}, {0, 2}, {0, 3}, {1, 3}, {2, 3}};
+    for (int v = 0; v < 4; ++v) {
+      N[v] = lam[v] * (2 * lam[v] - 1);
+      for (int j = 0; j < 3; ++j) dN[j][v] = (4 * lam[v] - 1) * dl[v][j];
+    }
+    for (int e = 0; e < 6; ++e) {
+      const int p0 = E[e][0], p1 = E[e][1];
+      N[4 + e] = 4 * lam[p0] * lam[p1];
+      for (int j = 0; j < 3; ++j) dN[j][4 + e] = 4 * (dl[p0][j] * lam[p1] + lam[p0] * dl[p1][j]);
+    }
+  } else {
+    nn = 18;
+    const double l0 = -(pt[0] + pt[1]) / 2, l1 = (1 + pt[0]) / 2, l2 = (1 + pt[1]) / 2;
+    const double d0[2] = {-0.5, -0.5}, d1[2] = {0.5, 0.0}, d2[2] = {0.0, 0.5};
+    double T[6], dT[2][6];
+    T[0] = l0 * (2 * l0 - 1);
+    T[1] = l1 * (2 * l1 - 1);
+    T[2] = l2 * (2 * l2 - 1);
+    T[3] = 4 * l0 * l1;
+    T[4] = 4 * l1 * l2;
+    T[5] = 4 * l0 * l2;
+    for (int j = 0; j < 2; ++j) {
+      dT[j][0] = (4 * l0 - 1) * d0[j];
+      dT[j][1] = (4 * l1 - 1) * d1[j];
+      dT[j][2] = (4 * l2 - 1) * d2[j];
+      dT[j][3] = 4 * (d0[j] * l1 + l0 * d1[j]);
+      dT[j][4] = 4 * (d1[j] * l2 + l1 * d2[j]);
+      dT[j][5] = 4 * (d0[j] * l2 + l0 * d2[j]);
+    }
+    const double t = pt[2];
+    const double L[3] = {0.5 * t * (t - 1), 1 - t * t, 0.5 * t * (t + 1)};
+    const double dL[3] = {t - 0.5, -2 * t, t + 0.5};
+    for (int l = 0; l < 3; ++l)
+      for (int q = 0; q < 6; ++q) {
+        N[q + 6 * l] = T[q] * L[l];
+        dN[0][q + 6 * l] = dT[0][q] * L[l];
+        dN[1][q + 6 * l] = dT[1][q] * L[l];
+        dN[2][q + 6 * l] = T[q] * dL[l];
+      }
+  }
+  for (int k = 0; k < 3; ++k) {
+    x[k] = 0.0;
+    for (int j = 0; j < 3; ++j) a[j][k] = 0.0;
+  }
+  for (int v = 0; v < nn; ++v)
+    for (int k = 0; k < 3; ++k) {
+      x[k] += N[v] * X[3 * v + k];
+      for (int j = 0; j < 3; ++j) a[j][k] += dN[j][v] * X[3 * v + k];
+    }
+}
+
+// Curl-form interpolant of a prism or tetrahedron through its modal basis:
+// the derivative d_i of the interpolant on the curl nodes, at np points,
+// dB[np][3][ng].
+struct CurlSimplex {
+  int ng = 0;
+  std::vector<double> G;     // [ng][3] curl nodes
+  std::vector<double> Vinv;  // [nm][ng] modal <- nodal on the curl nodes
+  explicit CurlSimplex(const RefElement& R) : G(curl_nodes(R)) {
+    ng = int(G.size() / 3);
+    std::vector<double> V(size_t(ng) * ng);
+    R.basis(ng, G.data(), V.data());
+    Vinv.resize(V.size());
+    invert(ng, V.data(), Vinv.data());
+  }
+  void deriv(const RefElement& R, int np, const double* pts, std::vector<double>& dB) const {
+    std::vector<double> g(size_t(3) * np * ng);
+    R.grad(np, pts, g.data());
+    dB.assign(size_t(np) * 3 * ng, 0.0);
+    for (int q = 0; q < np; ++q)
+      for (int i = 0; i < 3; ++i)
+        for (int m = 0; m < ng; ++m) {
+          const double gv = g[(size_t(i) * np + q) * ng + m];
+          if (gv == 0.0) continue;
+          for (int node = 0; node < ng; ++node)
+            dB[(size_t(q) * 3 + i) * ng + node] += gv * Vinv[size_t(m) * ng + node];
+        }
+  }
+  // w[n][j][node] = X_l d X_m / d xi_j ((n, m, l) cyclic) at the curl nodes
+  void fields(int kind, const double* X, double* w) const {
+    for (int node = 0; node < ng; ++node) {
+      double x[3], J[3][3];
+      q2s_eval(kind, X, &G[3 * node], x, J);
+      for (int n = 0; n < 3; ++n) {
+        const int m = (n + 1) % 3, l = (n + 2) % 3;
+        for (int j = 0; j < 3; ++j) w[(size_t(n) * 3 + j) * ng + node] = x[l] * J[j][m];
+      }
+    }
+  }
+  // S[i][n] = -(curl_xi I(w^n))_i at one point from its dB row [3][ng]
+  void eval(const double* dBq, const double* w, double S[3][3]) const {
+    double dw[3][3][3];
+    for (int n = 0; n < 3; ++n)
+      for (int j = 0; j < 3; ++j)
+        for (int i = 0; i < 3; ++i) {
+          double s = 0.0;
+          for (int node = 0; node < ng; ++node)
+            s += dBq[size_t(i) * ng + node] * w[(size_t(n) * 3 + j) * ng + node];
+          dw[n][j][i] = s;
+        }
+    for (int i = 0; i < 3; ++i) {
+      const int j = (i + 1) % 3, k = (i + 2) % 3;
+      for (int n = 0; n < 3; ++n) S[i][n] = dw[n][j][k] - dw[n][k][j];
+    }
+  }
+};
+
+void curved_geometry_simplex(HostType& T) {
+  const RefElement& R = T.ref;
+  const int nu = R.nupts, nf = R.nfpts, nmap = q2_nodes(T.kind);
+  const CurlSimplex C(R);
+  std::vector<double> dBu, dBf;
+  C.deriv(R, nu, R.upts.data(), dBu);
+  C.deriv(R, nf, R.fpts.data(), dBf);
+  T.upts_x.resize(size_t(T.ne) * nu * 3);
+  T.smat.resize(size_t(T.ne) * 9 * nu);
+  T.rcpdjac.resize(size_t(T.ne) * nu);
+  T.fpts_x.resize(size_t(T.ne) * nf * 3);
+  T.fnvec.resize(size_t(T.ne) * nf * 3);
+  parallel_elements(T.ne, [&](int64_t e0, int64_t e1) {
+    std::vector<double> w(size_t(9) * C.ng);
+    for (int64_t e = e0; e < e1; ++e) {
+      const double* X = &T.mapx[size_t(e) * nmap * 3];
+      C.fields(T.kind, X, w.data());
+      for (int q = 0; q < nu; ++q) {
+        double x[3], J[3][3], S[3][3];
+        q2s_eval(T.kind, X, &R.upts[3 * q], x, J);
+        for (int k = 0; k < 3; ++k) T.upts_x[(size_t(e) * nu + q) * 3 + k] = x[k];
+        const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                           J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                           J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+        C.eval(&dBu[size_t(q) * 3 * C.ng], w.data(), S);
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j) T.smat[(size_t(e) * 9 + i * 3 + j) * nu + q] = S[i][j];
+        T.rcpdjac[size_t(e) * nu + q] = det > 0 ? 1.0 / det : -1.0;
+      }
+      for (int q = 0; q < nf; ++q) {
+        double x[3], J[3][3], S[3][3];
+        q2s_eval(T.kind, X, &R.fpts[3 * q], x, J);
+        for (int k = 0; k < 3; ++k) T.fpts_x[(size_t(e) * nf + q) * 3 + k] = x[k];
+        C.eval(&dBf[size_t(q) * 3 * C.ng], w.data(), S);
+        const double* n = &R.fnorm[3 * q];
+        for (int j = 0; j < 3; ++j)
+          T.fnvec[(size_t(e) * nf + q) * 3 + j] =
+              S[0][j] * n[0] + S[1][j] * n[1] + S[2][j] * n[2];
+      }
+    }
+  });
+}
+
 void curved_geometry(HostType& T) {
+  if (T.kind != EK_HEX) {
+    curved_geometry_simplex(T);
+    return;
+  }
   const RefElement& R = T.ref;
   const int nu = R.nupts, nf = R.nfpts, n1 = R.p + 1, ng = n1 * n1 * n1;
   const std::vector<double> g = gll_nodes(n1);
@@ -319,6 +494,24 @@ void metric_points(const HostType& T, int np, const double* pts,
                    std::vector<double>& S) {
   const RefElement& R = T.ref;
   S.assign(size_t(T.ne) * 9 * np, 0.0);
+  if (T.map_order == 2 && T.kind != EK_HEX) {
+    const CurlSimplex C(R);
+    std::vector<double> dB;
+    C.deriv(R, np, pts, dB);
+    const int nmap = q2_nodes(T.kind);
+    parallel_elements(T.ne, [&](int64_t e0, int64_t e1) {
+      std::vector<double> w(size_t(9) * C.ng);
+      for (int64_t e = e0; e < e1; ++e) {
+        C.fields(T.kind, &T.mapx[size_t(e) * nmap * 3], w.data());
+        for (int q = 0; q < np; ++q) {
+          double M[3][3];
+          C.eval(&dB[size_t(q) * 3 * C.ng], w.data(), M);
+          for (int r = 0; r < 9; ++r) S[(size_t(e) * 9 + r) * np + q] = M[r / 3][r % 3];
+        }
+      }
+    });
+    return;
+  }
   if (T.map_order == 2) {
     const int n1 = R.p + 1, ng = n1 * n1 * n1;
     const std::vector<double> g = gll_nodes(n1);
@@ -379,28 +572,29 @@ std::string build_mesh(const MeshInput& in, std::vector<HostType>& types,
     if (span >= (int64_t(1) << 29)) return "too many elements of one type";
     const size_t ti = size_t(&t - in.types.data());
     if (ti < in.map_order.size() && in.map_order[ti] == 2) {
-      if (T.kind != EK_HEX) return "quadratic maps are supported on hexahedra only";
       T.map_order = 2;
-      T.map_conn.assign(in.map_conn[ti], in.map_conn[ti] + size_t(T.ne) * 27);
-      static const int corner[8] = {0, 2, 8, 6, 18, 20, 26, 24};
+      const int nmap = q2_nodes(T.kind);
+      const int* corner = q2_corners(T.kind);
+      T.map_conn.assign(in.map_conn[ti], in.map_conn[ti] + size_t(T.ne) * nmap);
       for (int64_t e = 0; e < T.ne; ++e) {
-        for (int v = 0; v < 27; ++v) {
-          const int64_t id = T.map_conn[size_t(e) * 27 + v];
+        for (int v = 0; v < nmap; ++v) {
+          const int64_t id = T.map_conn[size_t(e) * nmap + v];
           if (id < 0 || id >= in.n_nodes) return "map connectivity refers to a missing node";
         }
-        for (int v = 0; v < 8; ++v)
-          if (T.map_conn[size_t(e) * 27 + corner[v]] != T.conn[size_t(e) * 8 + v])
+        for (int v = 0; v < nv; ++v)
+          if (T.map_conn[size_t(e) * nmap + corner[v]] != T.conn[size_t(e) * nv + v])
             return "map corner nodes differ from the element vertices";
       }
-      T.mapx.resize(size_t(T.ne) * 81);
-      T.verts.resize(size_t(T.ne) * 24);
+      T.mapx.resize(size_t(T.ne) * nmap * 3);
+      T.verts.resize(size_t(T.ne) * nv * 3);
       for (int64_t e = 0; e < T.ne; ++e) {
-        for (int v = 0; v < 27; ++v)
+        for (int v = 0; v < nmap; ++v)
           for (int k = 0; k < 3; ++k)
-            T.mapx[(size_t(e) * 27 + v) * 3 + k] = in.nodes[T.map_conn[size_t(e) * 27 + v] * 3 + k];
-        for (int v = 0; v < 8; ++v)
+            T.mapx[(size_t(e) * nmap + v) * 3 + k] =
+                in.nodes[T.map_conn[size_t(e) * nmap + v] * 3 + k];
+        for (int v = 0; v < nv; ++v)
           for (int k = 0; k < 3; ++k)
-            T.verts[(size_t(e) * 8 + v) * 3 + k] = T.mapx[(size_t(e) * 27 + corner[v]) * 3 + k];
+            T.verts[(size_t(e) * nv + v) * 3 + k] = T.mapx[(size_t(e) * nmap + corner[v]) * 3 + k];
       }
       curved_geometry(T);
     } else {

@@ -21,7 +21,7 @@ struct HostType {
   std::vector<int64_t> conn;     // [ne][nv]
   int map_order = 1;             // 2: quadratic (27-node) hexahedron map
   std::vector<int64_t> map_conn; // [ne][27] (map_order 2)
-  std::vector<double> mapx;      // [ne][27][3] map node coordinates (map_order 2)
+  std::vector<double> mapx;      // [ne][n_map][3] map node coordinates (map_order 2)
   // anti-aliasing (Section 3.2): rule of degree aa_qdeg and its operators
   int aa_qdeg = 0;
   std::vector<double> aa_x, aa_w;  // [nq][3], [nq]

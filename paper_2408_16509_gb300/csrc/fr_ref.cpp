@@ -701,6 +701,26 @@ static void volume_rule(int kind, int n, std::vector<double>& xq,
       }
 }
 
+std::vector<double> curl_nodes(const RefElement& R) {
+  const int p = R.p;
+  std::vector<double> g(p + 1), out;
+  gauss_lobatto(p + 1, g.data());
+  if (R.kind == EK_HEX) {
+    for (int k = 0; k <= p; ++k)
+      for (int j = 0; j <= p; ++j)
+        for (int i = 0; i <= p; ++i) out.insert(out.end(), {g[i], g[j], g[k]});
+  } else if (R.kind == EK_TET) {
+    out = tet_nodes(p);
+  } else {
+    const double a = p <= 15 ? kAlpha3D[std::max(p, 1) - 1] : 1.0;
+    const std::vector<double> t = tri_nodes(p, a);
+    const int nt = int(t.size() / 2);
+    for (int k = 0; k <= p; ++k)
+      for (int m = 0; m < nt; ++m) out.insert(out.end(), {t[2 * m], t[2 * m + 1], g[k]});
+  }
+  return out;
+}
+
 RefElement make_ref(int kind, int p, int family) {
   if (p < 1 || p > 8) throw std::invalid_argument("order out of range");
   if (family != 0 && (family != 1 || kind != EK_HEX))

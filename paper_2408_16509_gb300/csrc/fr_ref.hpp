@@ -57,6 +57,13 @@ struct RefElement {
 // family 0: Gauss-Legendre line points; 1: Gauss-Lobatto (hexahedra only)
 RefElement make_ref(int kind, int p, int family = 0);
 
+// Nodes of the interpolant of the curl-form metric of curved elements
+// ([n][3], n = the element's number of modes, nodes on every face so that a
+// face's normal depends on that face alone): the Gauss-Lobatto tensor nodes
+// (hexahedra), the warp-and-blend nodes (tetrahedra), the tetrahedron's
+// face nodes times Gauss-Lobatto points along z (prisms).
+std::vector<double> curl_nodes(const RefElement& R);
+
 // 1D helpers (exposed for unit use)
 void gauss_legendre(int n, double* x, double* w);
 void gauss_lobatto(int n, double* x);

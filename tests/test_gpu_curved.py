@@ -1,4 +1,5 @@
-"""GPU parity on curved hexahedra ("Curved Elements", Section 3.4): the
+"""GPU parity on curved hexahedra, prisms and tetrahedra ("Curved Elements",
+Section 3.4): the
 library's quadratic-map geometry (conservative curl-form metric, exact
 det J) and every kernel family that can run on it, against the oracle.
 
@@ -122,3 +123,69 @@ def test_curved_free_stream_at_size(precision, oracle_free_stream_16):
     ratio = 1.0 if precision == "fp64" else 2.0 ** -24 / 2.0 ** -53
     assert 0 < oracle_free_stream_16 < 1e-9
     assert r <= 4 * ratio * oracle_free_stream_16, (r, oracle_free_stream_16)
+
+
+# ---------------------------------------------------------------- simplices
+MIXED_BCS = {0: ("state", 1.0, 0.4, 0.1, 0.0, 1.0 / 1.4 / 0.09), 1: ("extrap",),
+             2: ("state", 1.0, 0.4, 0.1, 0.0, 1.0 / 1.4 / 0.09), 3: ("extrap",)}
+
+
+def _curved_mixed(n=3, **kw):
+    from frinputs import curved_mixed_box
+    return curved_mixed_box(n=n, **kw)
+
+
+def _pair_mixed(spec, p, physics, precision="fp64", bcs=MIXED_BCS):
+    o = OracleMesh(spec.as_dict(), p)
+    osys = FRSystem(o, physics, gamma=1.4, mu=0.02, pr=0.71, bcs=bcs)
+    g = fr.FRMesh(spec, p, physics=physics, gamma=1.4, mu=0.02, prandtl=0.71,
+                  bcs=bcs, precision=precision)
+    for t in g.types:
+        assert np.abs(g.points(t) - o.upts_x[t]).max() < 1e-14
+    return o, osys, g
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+@pytest.mark.parametrize("physics", ["euler", "ns"])
+def test_curved_mixed_rhs_fp64(p, physics):
+    """Curved hexahedra, prisms (18-node maps) and tetrahedra (10-node maps)
+    against the oracle, FP64, 1e-12 per conserved variable."""
+    o, osys, g = _pair_mixed(_curved_mixed(), p, physics)
+    g.set_solution(lib_state(g, _tgv))
+    err = rel_l2_rhs(g.rhs(), osys.rhs(oracle_state(o, _tgv)))
+    assert err.max() < 1e-12, err
+
+
+def test_curved_prisms_and_tets_rhs_fp64():
+    spec = _curved_mixed(x_pri=0.0, x_tet=0.5, periodic_x=False)
+    o, osys, g = _pair_mixed(spec, 3, "ns")
+    g.set_solution(lib_state(g, _tgv))
+    err = rel_l2_rhs(g.rhs(), osys.rhs(oracle_state(o, _tgv)))
+    assert err.max() < 1e-12, err
+
+
+@pytest.mark.parametrize("precision,variant,tol", [("fp64", "sumfact", 1e-12),
+                                                   ("fp32", "sumfact", 1e-6),
+                                                   ("fp32", "tensor", 1e-6)])
+def test_curved_mixed_rk_steps(precision, variant, tol):
+    o, osys, g = _pair_mixed(_curved_mixed(), 3, "ns", precision=precision)
+    g.set_variant(variant)
+    g.set_solution(lib_state(g, _tgv))
+    u = oracle_state(o, _tgv)
+    for _ in range(2):
+        u = rk.step(osys.rhs, u, 2e-4, "rk45")
+    g.rk_step("rk45", 2e-4, 2)
+    err = rel_l2(g.get_solution(), u)
+    assert err.max() < tol, err
+
+
+def test_curved_mixed_free_stream_at_size():
+    """A uniform state on 16^3 cells of curved hexahedra, prisms and
+    tetrahedra (p = 3): right-hand side at round-off."""
+    spec = _curved_mixed(n=16)
+    far = ("state", 1.0, 0.5, 0.3, 0.2, 1.0)
+    g = fr.FRMesh(spec, 3, physics="ns", mu=1e-3, prandtl=0.71,
+                  bcs={k: far for k in range(4)})
+    g.set_solution(lib_state(g, lambda x: ics.uniform(x, vel=(0.5, 0.3, 0.2))))
+    r = g.rhs()
+    assert max(np.abs(v).max() for v in r.values()) < 1e-9

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import paper_2408_16509_gb300 as fr
-from frinputs import box_hex, curved_box_hex, mixed_box
+from frinputs import box_hex, curved_box_hex, curved_mixed_box, mixed_box
 from oracle.mesh import FRMesh as OracleMesh
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -61,6 +61,7 @@ SPECS = {
     "hex": lambda: box_hex((3, 2, 2), perturb=0.1),
     "hex-gll": lambda: box_hex((3, 2, 2), perturb=0.1),
     "curved-gll": lambda: curved_box_hex((3, 2, 2)),
+    "curved-mixed": lambda: curved_mixed_box(n=3),
     "mixed": lambda: mixed_box(n=3, x_pri=0.34, x_tet=0.67, perturb=0.05),
     "curved": lambda: curved_box_hex((3, 2, 2)),
 }
