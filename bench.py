@@ -265,7 +265,8 @@ def measure(fr, torch, precision, steps, warmup, device, dist, n=None,
             a[0] += t / reps
             a[1] = c
     return {"mesh": mesh, "u0": u0, "ms": ms, "clocks": clocks, "prof": prof,
-            "final": final, "tuning": tuning, "units": units}
+            "final": final, "tuning": tuning, "units": units,
+            "schedule": mesh.schedule()}
 
 
 def _rel_l2_arrays(a, b):
@@ -349,7 +350,8 @@ def run_ours(args):
         "gpu_launches": launches_per_step * args.steps,
         "kernel_ms_per_step": {k: v[0] for k, v in prof.items() if v[1]},
         "kernel_family": {"active": r["tuning"][0],
-                          "tuned_ms_per_step": r["tuning"][1]},
+                          "tuned_ms_per_step": r["tuning"][1],
+                          "schedule": r["schedule"]},
         "roofline": roof,
         "alu_probe": {"fp64_tflops": alu["fp64"][0], "fp32_tflops": alu["fp32"][0],
                       "clocks": probe_clocks},
@@ -375,7 +377,8 @@ def run_ours(args):
                     src, prec, alu),
                 "kernel_ms_per_step": {k: x[0] for k, x in v["prof"].items() if x[1]},
                 "kernel_family": {"active": v["tuning"][0],
-                                  "tuned_ms_per_step": v["tuning"][1]},
+                                  "tuned_ms_per_step": v["tuning"][1],
+                                  "schedule": v["schedule"]},
                 "clocks": v["clocks"]}
             v["mesh"].close()
         if ref_final is None and "fp64" in finals:
@@ -542,6 +545,7 @@ def config_mixed_elements(fr, torch, device, steps=20, cells=40, variant="auto",
     active, tuned = mesh.tuning()
     out = {"gdof_stage_s": _gdofs(mesh, 4, steps, ms), "ms_per_step": ms / steps,
            "elements": {t: mesh.info(t)[0] for t in mesh.types},
+           "schedule": mesh.schedule(),
            "kernel_ms_per_step": {k: v[0] for k, v in prof.items() if v[1]},
            "kernel_family": {"active": active, "tuned_ms_per_step": tuned}}
     mesh.close()

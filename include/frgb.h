@@ -51,7 +51,7 @@ enum { FR_EULER = 0, FR_NAVIER_STOKES = 1 };
  * FR_MIXED: traces, fluxes, operators and stage values in FP32, the RK
  * solution and accumulator registers in FP64 (hexahedral meshes). */
 enum { FR_FP64 = 0, FR_FP32 = 1, FR_MIXED = 2 };
-enum { FR_BC_STATE = 0, FR_BC_EXTRAPOLATE = 1, FR_BC_EXCHANGE = 2 };
+enum { FR_BC_STATE = 0, FR_BC_EXTRAPOLATE = 1, FR_BC_EXCHANGE = 2, FR_BC_PRESCRIBED = 3 };
 enum { FR_RK4 = 0, FR_RK45 = 1 };
 /* Line points of hexahedra (fr_mesh_desc.point_family). */
 enum { FR_POINTS_GL = 0, FR_POINTS_GLL = 1 };
@@ -89,7 +89,9 @@ typedef struct {
 
 typedef struct {
   int tag;              /* boundary-face tag this condition applies to */
-  int kind;             /* FR_BC_EXCHANGE: a face between parts of a
+  int kind;             /* FR_BC_PRESCRIBED: outside state given point by
+                           point by the caller (fr_set_bc_state; state[]
+                           unused); FR_BC_EXCHANGE: a face between parts of a
                            partitioned mesh, its outside state the partner
                            part's (meshes with such faces run only in a
                            group, fr_group_create); FR_BC_STATE: outside
@@ -183,6 +185,22 @@ enum { FR_DTYPE_F64 = 0, FR_DTYPE_F32 = 1 };
  * the stream reaches the copy (fr_sync).  FR_EINVAL for another dtype. */
 int fr_set_solution_device(fr_mesh* mesh, int etype, const void* dptr, int dtype);
 int fr_get_solution_device(const fr_mesh* mesh, int etype, void* dptr, int dtype);
+
+/* Outside state of an FR_BC_PRESCRIBED condition (the prescribed-state
+ * boundary of Section 2's problem statement: the outside state u+ of
+ * Eq. comm_flux comes from the boundary).  The library calls
+ *   fn(n, x, t, prim, ctx)
+ * once with the n boundary flux points of condition `tag` (x [n][3], in
+ * fr_get_boundary_points order) and time t; fn writes the primitive state
+ * prim [n][5] (rho, u, v, w, p) at each.  The states are kept on the device
+ * and used by every later right-hand side and RK stage until the next call
+ * (a time-dependent condition is updated by the caller, e.g. once per
+ * step).  With Navier-Stokes the outside gradient is the inside one, as for
+ * FR_BC_STATE.  Compute calls on a mesh with a prescribed condition that
+ * has no state yet return FR_EINVAL; so does a non-positive density or
+ * pressure.  Synchronous. */
+typedef void (*fr_bc_fn)(int64_t n, const double* x, double t, double* prim, void* ctx);
+int fr_set_bc_state(fr_mesh* mesh, int tag, fr_bc_fn fn, double t, void* ctx);
 
 /* One evaluation of the right-hand side du/dt = -J^{-1} div~ f~ (Section 2:
  * Eq. disu, interpolation to the flux points; Eq. comm_flux, the common

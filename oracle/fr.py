@@ -35,7 +35,10 @@ flux (1/2 + beta) F_v- + (1/2 - beta) F_v+ (biased the other way), and the
 common normal flux gains the penalty tau (u- - u+).  beta = tau = 0 is BR1.
 
 Boundary conditions (by tag): ('state', rho, u, v, w, p) -- outside state is
-the given constant state; ('extrap',) -- outside state = inside state.
+the given constant state; ('extrap',) -- outside state = inside state;
+('prescribed', fn) -- outside state given point by point, fn(x) returning
+the primitive state (rho, u, v, w, p) at the boundary flux points x (n, 3);
+the outside gradient is the inside one in every case.
 """
 import numpy as np
 
@@ -76,6 +79,10 @@ class FRSystem:
             bc = self.bcs[int(tag)]
             if bc[0] == "state":
                 out[sel] = self._ghost_state[int(tag)]
+            elif bc[0] == "prescribed":
+                x = self.m.flat(self.m.fpts_x)[self.m.bnd_g[sel]]
+                w = np.asarray(bc[1](x), float)
+                out[sel] = prim_to_cons(w[:, 0], w[:, 1:4], w[:, 4], self.gamma)
             elif bc[0] != "extrap":
                 raise ValueError(f"unknown boundary condition {bc[0]}")
         return out

@@ -20,7 +20,7 @@ PRECISION = {"fp64": 0, "fp32": 1, "mixed": 2}
 VARIANTS = {"auto": 0, "dense": 1, "sumfact": 2, "sumfact_vertex": 3,
             "tensor": 4}
 SCHEMES = {"rk4": 0, "rk45": 1}
-BC_KIND = {"state": 0, "extrap": 1, "exchange": 2}
+BC_KIND = {"state": 0, "extrap": 1, "exchange": 2, "prescribed": 3}
 VARIANT_NAMES = {v: k for k, v in VARIANTS.items()}
 FR_DTYPE_F64, FR_DTYPE_F32 = 0, 1
 FR_KC_COUNT = 8
@@ -94,6 +94,7 @@ def load():
         "fr_exchange_pack": (I, [P, I, P]),
         "fr_exchange_unpack": (I, [P, I, P]),
         "fr_rk_stage": (I, [P, I, D, I, I, I]),
+        "fr_set_bc_state": (I, [P, I, BC_FN, D, P]),
         "fr_probe_fma": (I, [I, I, C.c_int64, C.POINTER(D), C.POINTER(D)]),
         "fr_get_rhs": (I, [P, I, P]),
         "fr_rk_step": (I, [P, I, D, I]),
@@ -152,6 +153,10 @@ class Stats(C.Structure):
                 ("ms_kernel", C.c_double * FR_KC_COUNT),
                 ("launches", C.c_int * FR_KC_COUNT),
                 ("kernel_family", C.c_int), ("t_last", C.c_double)]
+
+
+BC_FN = C.CFUNCTYPE(None, C.c_int64, C.POINTER(C.c_double), C.c_double,
+                    C.POINTER(C.c_double), C.c_void_p)
 
 
 class Schedule(C.Structure):
@@ -216,8 +221,11 @@ class FRMesh:
         self._keep += [bnodes, btags]
         bcs = bcs or {}
         bc_list = []
+        presc = {}
         for tag, bc in bcs.items():
             st = (C.c_double * 5)(*(bc[1:6] if bc[0] == "state" else [0] * 5))
+            if bc[0] == "prescribed":
+                presc[int(tag)] = bc[1]
             bc_list.append(BCDesc(int(tag), BC_KIND[bc[0]], st))
         bc_arr = (BCDesc * max(len(bc_list), 1))(*bc_list)
         per = ((C.c_double * 3) * 3)()
@@ -249,6 +257,9 @@ class FRMesh:
         self._keep = None
         self.precision = precision
         self.physics = physics
+        for tag, fn in presc.items():
+            if device >= 0 and fn is not None:   # None: set later (set_bc_state)
+                self.set_bc_state(tag, fn)
         self.types = [t for t in ("hex", "pri", "tet") if self.info(t)[0] > 0]
 
     def close(self):
@@ -404,6 +415,28 @@ class FRMesh:
         names = {v: k for k, v in VARIANTS.items()}
         return names[a.value], {names[i]: float(ms[i]) for i in range(1, 5)
                                 if ms[i] > 0}
+
+    def set_bc_state(self, tag, fn, t=0.0):
+        """States of an FR_BC_PRESCRIBED condition (fr_set_bc_state):
+        fn(x (n, 3), t) or fn(x) returns the primitive state (n, 5)."""
+        err = []
+
+        def cb(n, x, tt, prim, ctx):
+            try:
+                xs = np.ctypeslib.as_array(x, shape=(n, 3))
+                try:
+                    w = fn(xs.copy(), tt)
+                except TypeError:
+                    w = fn(xs.copy())
+                np.ctypeslib.as_array(prim, shape=(n, 5))[:] = np.asarray(w, float)
+            except Exception as exc:  # noqa: BLE001 - reported after the call
+                err.append(exc)
+                np.ctypeslib.as_array(prim, shape=(n, 5))[:] = np.nan
+        cfun = BC_FN(cb)
+        rc = load().fr_set_bc_state(self._h, int(tag), cfun, float(t), None)
+        if err:
+            raise err[0]
+        _check(rc)
 
     def schedule(self):
         """Tiles and schedule of the kernels (fr_get_schedule): per element

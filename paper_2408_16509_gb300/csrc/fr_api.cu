@@ -77,9 +77,12 @@ int fr_mesh_create(const fr_mesh_desc* d, fr_mesh** out) {
     return fail(FR_EINVAL, "boundary faces without nodes or tags");
   for (int i = 0; i < d->n_bcs; ++i) {
     const fr_bc_desc& b = d->bcs[i];
-    if (b.kind != FR_BC_STATE && b.kind != FR_BC_EXTRAPOLATE && b.kind != FR_BC_EXCHANGE)
+    if (b.kind != FR_BC_STATE && b.kind != FR_BC_EXTRAPOLATE && b.kind != FR_BC_EXCHANGE &&
+        b.kind != FR_BC_PRESCRIBED)
       return fail(FR_EINVAL, "unknown boundary condition");
+    m->has_presc |= b.kind == FR_BC_PRESCRIBED;
     in.bc_tags.push_back(b.tag);
+    m->bc_tags.push_back(b.tag);
     double rho = b.state[0], u = b.state[1], v = b.state[2], w = b.state[3],
            p = b.state[4];
     double cons[5] = {rho, rho * u, rho * v, rho * w,
@@ -151,9 +154,12 @@ int fr_mesh_create(const fr_mesh_desc* d, fr_mesh** out) {
   if (rc) return rc;
   rc = FR_PREC(m, prepare_kernels, m.get());
   if (rc) return rc;
-  if (m->has_exch) {
+  if (m->has_exch || m->has_presc) {
     const size_t nb = m->conn.bidx.size();
     if ((rc = dev_zeros(m.get(), nb * 5 * m->wsize, &m->xu))) return rc;
+  }
+  if (m->has_exch) {
+    const size_t nb = m->conn.bidx.size();
     if ((rc = dev_zeros(m.get(), nb * 15 * m->wsize, &m->xg))) return rc;
     if ((rc = dev_zeros(m.get(), nb * m->wsize, &m->xm))) return rc;
   }
@@ -388,12 +394,22 @@ void stats_end(fr_mesh* m, int slot) {
 
 int stages_of(int scheme) { return scheme == FR_RK4 ? 4 : 5; }
 
+// Every FR_BC_PRESCRIBED condition must have its states (fr_set_bc_state).
+int bc_ready(const fr_mesh* m) {
+  if (!m->has_presc) return FR_OK;
+  for (size_t b = 0; b < m->bc_tags.size(); ++b)
+    if (m->bc64.kind[b] == FR_BC_PRESCRIBED && (b >= m->presc_set.size() || !m->presc_set[b]))
+      return fail(FR_EINVAL, "a prescribed boundary condition has no state: call fr_set_bc_state");
+  return FR_OK;
+}
+
 }  // namespace
 
 extern "C" {
 
 int fr_rhs(fr_mesh* m, double t, double* rhs_host, void* rhs_dev) {
   if (!m) return fail(FR_EINVAL, "null mesh");
+  if (int rb = bc_ready(m)) return rb;
   if (m->host_only) return fail(FR_EINVAL, "host-only handle (device < 0)");
   if (m->has_exch) return fail(FR_EINVAL, "mesh has exchange faces: run it in a group");
   if (!std::isfinite(t)) return fail(FR_EINVAL, "time is not finite");
@@ -436,6 +452,7 @@ int fr_rhs(fr_mesh* m, double t, double* rhs_host, void* rhs_dev) {
 
 int fr_rk_step(fr_mesh* m, int scheme, double dt, int nsteps) {
   if (!m) return fail(FR_EINVAL, "null mesh");
+  if (int rb = bc_ready(m)) return rb;
   if (m->host_only) return fail(FR_EINVAL, "host-only handle (device < 0)");
   if (scheme != FR_RK4 && scheme != FR_RK45) return fail(FR_EINVAL, "unknown scheme");
   if (nsteps < 0) return fail(FR_EINVAL, "negative step count");
@@ -454,6 +471,7 @@ int fr_rk_step(fr_mesh* m, int scheme, double dt, int nsteps) {
 int fr_rk_adaptive_step(fr_mesh* m, fr_adapt_t* ctl, double* dt, int* accepted,
                         double* err) {
   if (!m || !ctl || !dt || !accepted || !err) return fail(FR_EINVAL, "null argument");
+  if (int rb = bc_ready(m)) return rb;
   if (m->host_only) return fail(FR_EINVAL, "host-only handle (device < 0)");
   if (m->has_exch) return fail(FR_EINVAL, "mesh has exchange faces: run it in a group");
   CK(cudaSetDevice(m->device));
@@ -470,6 +488,7 @@ int fr_rk_adaptive_step(fr_mesh* m, fr_adapt_t* ctl, double* dt, int* accepted,
 int fr_profile_step(fr_mesh* m, int scheme, double dt, double* ms,
                     int* launches) {
   if (!m || !ms || !launches) return fail(FR_EINVAL, "null argument");
+  if (int rb = bc_ready(m)) return rb;
   if (m->host_only) return fail(FR_EINVAL, "host-only handle (device < 0)");
   if (m->has_exch) return fail(FR_EINVAL, "mesh has exchange faces: run it in a group");
   if (scheme != FR_RK4 && scheme != FR_RK45) return fail(FR_EINVAL, "unknown scheme");
@@ -593,6 +612,69 @@ const double* bpt_x(const fr_mesh* m, int32_t i) {
 }  // namespace
 
 extern "C" {
+
+int fr_set_bc_state(fr_mesh* m, int tag, fr_bc_fn fn, double t, void* ctx) {
+  if (!m || !fn) return fail(FR_EINVAL, "null argument");
+  if (m->host_only) return fail(FR_EINVAL, "host-only handle (device < 0)");
+  int b = -1;
+  for (size_t i = 0; i < m->bc_tags.size(); ++i)
+    if (m->bc_tags[i] == tag) b = int(i);
+  if (b < 0 || m->bc64.kind[b] != FR_BC_PRESCRIBED)
+    return fail(FR_EINVAL, "no prescribed boundary condition with this tag");
+  std::vector<int32_t> slot;
+  std::vector<double> x;
+  for (size_t i = 0; i < m->conn.bidx.size(); ++i) {
+    if (m->conn.bbc[i] != b) continue;
+    slot.push_back(int32_t(i));
+    const double* p = bpt_x(m, int32_t(i));
+    x.insert(x.end(), p, p + 3);
+  }
+  const size_t n = slot.size();
+  std::vector<double> prim(5 * n, 0.0), cons(5 * n);
+  if (n) fn(int64_t(n), x.data(), t, prim.data(), ctx);
+  for (size_t q = 0; q < n; ++q) {
+    const double* w = &prim[5 * q];
+    if (!(w[0] > 0.0) || !(w[4] > 0.0) || !std::isfinite(w[1]) || !std::isfinite(w[2]) ||
+        !std::isfinite(w[3]))
+      return fail(FR_EINVAL, "prescribed state with non-positive density or pressure");
+    cons[5 * q] = w[0];
+    for (int k = 0; k < 3; ++k) cons[5 * q + 1 + k] = w[0] * w[1 + k];
+    cons[5 * q + 4] = w[4] / (m->gamma - 1.0) +
+                      0.5 * w[0] * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]);
+  }
+  CK(cudaSetDevice(m->device));
+  if (n) {
+    void *dv = nullptr, *ds = nullptr;
+    CK(cudaMalloc(&dv, 5 * n * m->wsize));
+    cudaError_t e = cudaMalloc(&ds, n * sizeof(int32_t));
+    if (e == cudaSuccess) {
+      if (m->wsize == 8) {
+        e = cudaMemcpy(dv, cons.data(), 5 * n * 8, cudaMemcpyHostToDevice);
+      } else {
+        std::vector<float> c32(cons.begin(), cons.end());
+        e = cudaMemcpy(dv, c32.data(), 5 * n * 4, cudaMemcpyHostToDevice);
+      }
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(ds, slot.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+      CK(cudaStreamSynchronize(m->stream));
+      if (m->wsize == 8)
+        k_exchange_scatter<double><<<nblk((long long)n, 256), 256, 0, m->stream>>>(
+            int(n), (const int32_t*)ds, (const double*)dv, 5, (double*)m->xu);
+      else
+        k_exchange_scatter<float><<<nblk((long long)n, 256), 256, 0, m->stream>>>(
+            int(n), (const int32_t*)ds, (const float*)dv, 5, (float*)m->xu);
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    }
+    cudaFree(dv);
+    cudaFree(ds);
+    if (e != cudaSuccess) return fail(FR_ECUDA, std::string("fr_set_bc_state: ") + cudaGetErrorString(e));
+  }
+  if (m->presc_set.size() < m->bc_tags.size()) m->presc_set.resize(m->bc_tags.size(), 0);
+  m->presc_set[b] = 1;
+  return FR_OK;
+}
 
 int fr_exchange_faces(const fr_mesh* m, int64_t* n_faces, int64_t* n_points,
                       int32_t* face_npts, double* centroids, double* pt_x,
@@ -801,6 +883,7 @@ int fr_exchange_unpack(fr_mesh* m, int what, const void* dev_buf) {
 
 int fr_rk_stage(fr_mesh* m, int scheme, double dt, int stage, int phase, int part) {
   if (!m) return fail(FR_EINVAL, "null mesh");
+  if (int rb = bc_ready(m)) return rb;
   if (m->host_only) return fail(FR_EINVAL, "host-only handle (device < 0)");
   if (m->in_group) return fail(FR_EINVAL, "the mesh belongs to a group");
   if (m->filter_on) return fail(FR_EINVAL, "not with the entropy filter");

@@ -717,7 +717,7 @@ __global__ void __launch_bounds__(kTcThreads, MINB)
         for (int c = 0; c < 3; ++c)
 #pragma unroll
           for (int k = 0; k < 5; ++k) G[c][k] = gf[c][k][j];
-        visc_q_pre(bc, ph, ut[j], G, nv[j], fb[j], q);
+        visc_q_pre(bc, ph, ut[j], G, nv[j], fb[j], q, prescribed_at(va, e, rf, NF));
 #pragma unroll
         for (int k = 0; k < 5; ++k) va.q[(e * 5 + k) * NF + rf] = q[k];
       }

@@ -291,7 +291,8 @@ __global__ void __launch_bounds__(EPB* N* N* N)
 #pragma unroll
         for (int k = 0; k < 5; ++k) G[j][k] = g[j * 5 + k];
       }
-      visc_q_pre(bc, ph, u, G, nv, int(va.fbc[e * NF + f]), q);
+      visc_q_pre(bc, ph, u, G, nv, int(va.fbc[e * NF + f]), q,
+                 prescribed_at(va, e, f, NF));
 #pragma unroll
       for (int k = 0; k < 5; ++k) va.q[(e * 5 + k) * NF + f] = q[k];
     } else {
@@ -639,7 +640,13 @@ __global__ void __launch_bounds__(EPB* N* N* N)
     const int bb = va.fbc[e * NF + f];
     if (bb >= 0 && bc.kind[bb] != 2) {  // exchange points keep the inside q
       T ur[5], q2[5] = {0, 0, 0, 0, 0};
-      ghost_state(bc, bb, u, ur);
+      const T* pre = prescribed_at(va, e, f, NF);
+      if (bc.kind[bb] == 3 && pre) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) ur[k] = pre[k];
+      } else {
+        ghost_state(bc, bb, u, ur);
+      }
       viscous_normal_acc(ur, G, nv, ph, T(1), q2);
 #pragma unroll
       for (int k = 0; k < 5; ++k)

@@ -111,6 +111,7 @@ struct DevType {
   int tile_grad = 0, tile_vol = 0;
   void* fnv = nullptr;       // [ne][3][nf] S^T n~ at flux points (NS)
   int8_t* fbc = nullptr;     // [ne][nf] boundary-condition index or -1 (NS)
+  int32_t* fbi = nullptr;    // [ne][nf] boundary-point index or -1 (NS, prescribed states)
   void* verts = nullptr;     // [ne][8][3] vertices minus vertex 0 (hex, FP32)
   bool curved = false;       // quadratic map: metrics only from the tables
   // anti-aliasing (Section 3.2): operators, metric at the quadrature
@@ -194,6 +195,9 @@ struct fr_mesh {
   // exchange boundary points (partitioned meshes): receive buffers filled
   // by the group's push kernels, indexed by boundary point
   bool has_exch = false;
+  bool has_presc = false;          // a boundary condition FR_BC_PRESCRIBED
+  std::vector<int> bc_tags;        // tag of boundary condition i
+  std::vector<char> presc_set;     // per condition: fr_set_bc_state called
   bool in_group = false;
   void* xu = nullptr;         // [nb][5] partner solution traces
   void* xg = nullptr;         // [nb][15] partner gradients (FP64) or [nb][5] q (FP32)
@@ -516,6 +520,18 @@ int setup_device(fr_mesh* m) {
       m->allocs.push_back(p);
       CK(cudaMemcpy(p, fbc.data(), fbc.size(), cudaMemcpyHostToDevice));
       D.fbc = (int8_t*)p;
+      if (m->has_presc) {  // boundary-point index of every prescribed flux point
+        std::vector<int32_t> fbi(size_t(D.ne) * D.nf, -1);
+        for (size_t ib = 0; ib < m->conn.bidx.size(); ++ib) {
+          int32_t code = m->conn.bidx[ib];
+          if ((code >> 29) != int(t) || m->bc64.kind[m->conn.bbc[ib]] != FR_BC_PRESCRIBED) continue;
+          long long l = code & ((1 << 29) - 1);
+          long long e = l / (5 * D.nf);
+          int f = int(l - e * 5 * D.nf);
+          fbi[size_t(e) * D.nf + f] = int32_t(ib);
+        }
+        if ((rc = dev_upload_i32(m, fbi, &D.fbi))) return rc;
+      }
     }
     m->types.push_back(D);
   }
@@ -986,6 +1002,7 @@ inline DevType sub_view(const fr_mesh* m, const DevType& D, long long e0, long l
   V.grad = sh(D.grad, 15 * nu * w);
   V.fnv = sh(D.fnv, 3 * nf * w);
   V.fbc = static_cast<int8_t*>(sh(D.fbc, nf));
+  V.fbi = static_cast<int32_t*>(sh(D.fbi, nf * sizeof(int32_t)));
   V.verts = sh(D.verts, 24 * w);
   V.aasmq = sh(D.aasmq, 9 * size_t(D.aa_nq) * w);
   V.tf = sh(D.tf, 15 * nu * w);
@@ -1076,6 +1093,8 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
       const T* du = (const T*)m->du + D.off_f;
       ViscArgs<T> va{(const T*)m->uf + D.off_f, (const T*)D.fnv, D.fbc,
                      (T*)m->gradf + D.off_f * (sizeof(T) == 4 ? 1 : 3)};
+      va.fbi = D.fbi;
+      va.xp = (const T*)m->xu;
       PROF_BEGIN(FR_KC_GRAD);
       if (use_hex(m, D) && sizeof(T) == 4 && D.verts &&
           m->active == FR_VARIANT_SUMFACT_VERTEX) {

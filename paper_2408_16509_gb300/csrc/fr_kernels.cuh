@@ -28,8 +28,9 @@ struct TypeTab {
 
 template <typename T>
 struct BCTab {
-  int kind[kMaxBC];      // 0 = prescribed state, 1 = extrapolate,
-                         // 2 = exchange (outside state of a partner part)
+  int kind[kMaxBC];      // 0 = given state, 1 = extrapolate, 2 = exchange
+                         // (outside state of a partner part), 3 = state
+                         // prescribed per boundary point (in xu)
   T state[kMaxBC][5];    // conserved ghost state
 };
 
@@ -268,12 +269,13 @@ __device__ __forceinline__ void ghost_state(const BCTab<T>& bc, int b,
 }
 
 // Outside state of boundary point i: the condition's, or for an exchange
-// point the partner part's trace received in xu ([nb][5]).
+// point the partner part's trace and for a prescribed point the caller's
+// state, both in xu ([nb][5]).
 template <typename T>
 __device__ __forceinline__ void ghost_state_x(const BCTab<T>& bc, int b, int i,
                                               const T* __restrict__ xu,
                                               const T ul[5], T ur[5]) {
-  if (bc.kind[b] == 2) {
+  if (bc.kind[b] == 2 || bc.kind[b] == 3) {
 #pragma unroll
     for (int k = 0; k < 5; ++k) ur[k] = xu[5 * i + k];
   } else {
@@ -384,7 +386,19 @@ struct ViscArgs {
   const T* fnv;         // this type's [ne][3][nf] S^T n~ at flux points
   const int8_t* fbc;    // this type's [ne][nf]: -1 interior, else bc index
   T* q;                 // this type's [ne][5][nf] output
+  const int32_t* fbi = nullptr;  // [ne][nf] boundary-point index (prescribed states)
+  const T* xp = nullptr;         // [nb][5] per-point outside states
 };
+
+// Outside state of a prescribed boundary point seen from the element side
+// (flux point f of element e), or nullptr.
+template <typename T>
+__device__ __forceinline__ const T* prescribed_at(const ViscArgs<T>& va, long long e,
+                                                  int f, int nf) {
+  if (!va.fbi) return nullptr;
+  const int32_t i = va.fbi[e * nf + f];
+  return i >= 0 ? va.xp + 5 * (long long)i : nullptr;
+}
 
 template <typename T>
 __device__ __forceinline__ void write_visc_q(const ViscArgs<T>& va,
@@ -405,7 +419,11 @@ __device__ __forceinline__ void write_visc_q(const ViscArgs<T>& va,
   const int b = va.fbc[e * nf + f];
   if (b >= 0 && bc.kind[b] != 2) {  // exchange points keep the inside q
     T ur[5], q2[5] = {0, 0, 0, 0, 0};
-    if (bc.kind[b] == 0) {
+    const T* pre = prescribed_at(va, e, f, nf);
+    if (bc.kind[b] == 3 && pre) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) ur[k] = pre[k];
+    } else if (bc.kind[b] == 0) {
 #pragma unroll
       for (int k = 0; k < 5; ++k) ur[k] = bc.state[b][k];
     } else {
@@ -427,13 +445,17 @@ __device__ __forceinline__ void write_visc_q(const ViscArgs<T>& va,
 template <typename T>
 __device__ __forceinline__ void visc_q_pre(const BCTab<T>& bc, const Phys<T>& ph,
                                            const T u[5], const T G[3][5],
-                                           const T nv[3], int b, T q[5]) {
+                                           const T nv[3], int b, T q[5],
+                                           const T* pre = nullptr) {
 #pragma unroll
   for (int k = 0; k < 5; ++k) q[k] = T(0);
   viscous_normal_acc(u, G, nv, ph, T(1), q);
   if (b >= 0 && bc.kind[b] != 2) {  // exchange points keep the inside q
     T ur[5], q2[5] = {0, 0, 0, 0, 0};
-    if (bc.kind[b] == 0) {
+    if (bc.kind[b] == 3 && pre) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) ur[k] = pre[k];
+    } else if (bc.kind[b] == 0) {
 #pragma unroll
       for (int k = 0; k < 5; ++k) ur[k] = bc.state[b][k];
     } else {

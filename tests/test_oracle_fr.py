@@ -174,3 +174,30 @@ def test_isentropic_vortex_converges_at_order_p_plus_1(p):
     e2 = _vortex_error(32, p, 0.05, 0.005)
     order = np.log2(e1 / e2)
     assert order > p + 0.3, (e1, e2, order)
+
+
+@pytest.mark.parametrize("physics", ["euler", "ns"])
+def test_prescribed_boundary_state_keeps_exact_shear_steady(physics):
+    """The steady shear u = (y, 0, 0) with its own values prescribed point by
+    point on the y boundaries ('prescribed' condition): R = 0 (Euler) and
+    R = (0, 0, 0, 0, mu) (NS), as with the constant-state condition; and a
+    constant prescribed state equals the 'state' condition exactly."""
+    mu = 0.05
+    spec = box_hex((3, 2, 2), periodic=(0, 2))
+
+    def exact(x):
+        return np.column_stack([np.ones(len(x)), x[:, 1], 0 * x[:, 0], 0 * x[:, 0],
+                                np.ones(len(x))])
+    m = FRMesh(spec.as_dict(), 3)
+    s = FRSystem(m, physics, mu=mu, bcs={2: ("prescribed", exact), 3: ("prescribed", exact)})
+    r = s.rhs(_state(m, ics.shear))
+    expect = np.zeros(5)
+    if physics == "ns":
+        expect[4] = mu
+    assert np.abs(r["hex"] - expect).max() < 1e-11
+    const = (1.0, 0.3, 0.1, -0.2, 1.2)
+    a = FRSystem(m, physics, mu=mu, bcs={2: ("prescribed", lambda x: np.tile(const, (len(x), 1))),
+                                        3: ("state",) + const}).rhs(_state(m, ics.shear))
+    b = FRSystem(m, physics, mu=mu, bcs={2: ("state",) + const,
+                                        3: ("state",) + const}).rhs(_state(m, ics.shear))
+    assert np.array_equal(a["hex"], b["hex"])
