@@ -229,19 +229,22 @@ def _plane_faces(elements, plane_nodes, _unused, tag):
 
 
 def curved_box_hex(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), periodic=(0, 1, 2),
-                   amp=0.05, tags=None):
-    """Box of n[0] x n[1] x n[2] curved hexahedra with quadratic maps.
+                   amp=0.05, tags=None, order=2):
+    """Box of n[0] x n[1] x n[2] curved hexahedra with quadratic (order 2,
+    27 nodes) or cubic (order 3, 64 nodes: node a + 4b + 16c at reference
+    point (-1 + 2a/3, -1 + 2b/3, -1 + 2c/3)) maps.
 
-    The (2n+1)^3 lattice of corner, mid-edge, mid-face and centre nodes is
-    displaced by d_k = amp h_k (sin(pi n_{k+1} X_{k+1}) + sin(pi n_{k+2}
-    X_{k+2})) (1 + cos(2 pi n_k X_k) / 2) (X the box coordinates scaled to
-    [0, 1], indices cyclic).  Corners stay on the grid (the sines vanish
-    there), the field is the same on opposite box sides (faces pair by their
-    corner ids or periodic translation), and each component depends on all
-    three coordinates, so the map's cofactors are of high degree.
+    The (order n + 1)^3 lattice of map nodes is displaced by d_k = amp h_k
+    (sin(pi n_{k+1} X_{k+1}) + sin(pi n_{k+2} X_{k+2})) (1 + cos(2 pi n_k
+    X_k) / 2) (X the box coordinates scaled to [0, 1], indices cyclic).
+    Corners stay on the grid (the sines vanish there), the field is the same
+    on opposite box sides (faces pair by their corner ids or periodic
+    translation), and each component depends on all three coordinates, so
+    the map's cofactors are of high degree.
     """
     n = tuple(int(v) for v in n)
-    m = tuple(2 * v for v in n)
+    o = int(order)
+    m = tuple(o * v for v in n)
     lo_a, hi_a = np.asarray(lo, float), np.asarray(hi, float)
     nodes = _grid_nodes(m, lo, hi)
     L = hi_a - lo_a
@@ -254,12 +257,14 @@ def curved_box_hex(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), periodic=(0, 1, 2)
     nodes = nodes + amp * d
     g = _nid(m)
     I, J, K = _hex_cells(n)
-    a = np.arange(3)
+    a = np.arange(o + 1)
     A, B, C = np.meshgrid(a, a, a, indexing="ij")
     A, B, C = (v.transpose(2, 1, 0).ravel() for v in (A, B, C))   # a fastest
-    hmap = g(2 * I[:, None] + A[None, :], 2 * J[:, None] + B[None, :],
-             2 * K[:, None] + C[None, :])
-    corner = hmap[:, [0, 2, 8, 6, 18, 20, 26, 24]]
+    hmap = g(o * I[:, None] + A[None, :], o * J[:, None] + B[None, :],
+             o * K[:, None] + C[None, :])
+    q = o + 1
+    corner = hmap[:, [0, o, o + q * o, q * o, q * q * o, o + q * q * o,
+                      o + q * o + q * q * o, q * o + q * q * o]]
     pv = []
     for dd in periodic:
         T = np.zeros(3)
@@ -267,11 +272,11 @@ def curved_box_hex(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), periodic=(0, 1, 2)
         pv.append(T)
     if tags is None:
         tags = {(dd, s_): 2 * dd + s_ for dd in range(3) for s_ in (0, 1)}
-    # boundary faces on the half-spacing lattice: corner ids of each quad
-    f2 = lambda i, j, k: g(2 * i, 2 * j, 2 * k)  # noqa: E731
-    bf = _boundary_faces(n, f2, set(periodic), tags)
+    # boundary faces on the map lattice: corner ids of each quad
+    fo = lambda i, j, k: g(o * i, o * j, o * k)  # noqa: E731
+    bf = _boundary_faces(n, fo, set(periodic), tags)
     return MeshSpec(nodes, {"hex": corner.astype(np.int64)}, pv, bf,
-                    {"hex": (2, hmap.astype(np.int64))})
+                    {"hex": (o, hmap.astype(np.int64))})
 
 
 # reference coordinates of the quadratic map nodes of each element type, in

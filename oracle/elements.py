@@ -273,6 +273,38 @@ class Hex(ElementType):
         d = np.stack([s - 0.5, -2.0 * s, s + 0.5], axis=-1)
         return v, d
 
+    # cubic map (64 nodes, tensor order a + 4b + 16c at (-1 + 2a/3, ...))
+    @staticmethod
+    def _lag3(s):
+        """Cubic Lagrange polynomials on {-1, -1/3, 1/3, 1} and their slopes."""
+        nodes = (-1.0, -1.0 / 3.0, 1.0 / 3.0, 1.0)
+        v, d = [], []
+        for i, xi in enumerate(nodes):
+            others = [xj for j, xj in enumerate(nodes) if j != i]
+            den = np.prod([xi - xj for xj in others])
+            v.append(np.prod([s - xj for xj in others], axis=0) / den)
+            d.append(sum(np.prod([s - others[k] for k in range(3) if k != m], axis=0)
+                         for m in range(3)) / den)
+        return np.stack(v, axis=-1), np.stack(d, axis=-1)
+
+    def q3_nodes(self):
+        a = np.array([-1.0, -1.0 / 3.0, 1.0 / 3.0, 1.0])
+        c, b, aa = np.meshgrid(a, a, a, indexing="ij")
+        return np.stack([aa.ravel(), b.ravel(), c.ravel()], axis=1)
+
+    def q3_shape(self, x):
+        """(npts, 64) values of the cubic map's basis at points x."""
+        v = [self._lag3(x[:, i])[0] for i in range(3)]
+        return np.einsum("pa,pb,pc->pcba", v[0], v[1], v[2]).reshape(len(x), 64)
+
+    def q3_dshape(self, x):
+        vd = [self._lag3(x[:, i]) for i in range(3)]
+        out = []
+        for j in range(3):
+            f = [vd[i][1] if i == j else vd[i][0] for i in range(3)]
+            out.append(np.einsum("pa,pb,pc->pcba", f[0], f[1], f[2]).reshape(len(x), 64))
+        return np.stack(out)
+
     def q2_shape(self, x):
         """(npts, 27) values of the quadratic map's basis at points x."""
         v = [self._lag2(x[:, i])[0] for i in range(3)]

@@ -35,7 +35,14 @@ class MeshError(ValueError):
     pass
 
 
-def curl_metric(el, Xm, pts):
+def _map_fns(el, order):
+    """Shape functions (values, derivatives) of an element map of `order`."""
+    if order == 3:
+        return el.q3_shape, el.q3_dshape
+    return el.q2_shape, el.q2_dshape
+
+
+def curl_metric(el, Xm, pts, order=2):
     """Conservative (curl-form) metric of quadratic maps at the reference
     points pts.  Xm: (ne, n_map, 3) map nodes.  The fields
     w^n_j = X_l dX_m/dxi_j ((n, m, l) cyclic) are interpolated by the
@@ -44,13 +51,15 @@ def curl_metric(el, Xm, pts):
     only, so neighbours agree): the (p+1)^3 Gauss-Lobatto nodes on
     hexahedra, el.curl_nodes() on prisms and tetrahedra; then
     S[i][n] = -(curl_xi of it)_i at pts.  Returns S[e, q, i, n]
-    (= det J dxi_i/dx_n)."""
+    (= det J dxi_i/dx_n).  order: 2 (quadratic maps) or 3 (cubic
+    hexahedra, 64 nodes)."""
+    shape, dshape = _map_fns(el, order)
     if el.name != "hex":
         G = el.curl_nodes()
         Vi = np.linalg.inv(el.basis(G))
         dB = [gj @ Vi for gj in el.grad(pts)]                    # (npts, nG)
-        X = np.einsum("pv,evk->epk", el.q2_shape(G), Xm)
-        dX = np.einsum("jpv,evk->epjk", el.q2_dshape(G), Xm)
+        X = np.einsum("pv,evk->epk", shape(G), Xm)
+        dX = np.einsum("jpv,evk->epjk", dshape(G), Xm)
         S = np.zeros((Xm.shape[0], len(pts), 3, 3))
         for n in range(3):
             m, l = (n + 1) % 3, (n + 2) % 3
@@ -64,8 +73,8 @@ def curl_metric(el, Xm, pts):
     n1 = len(g)
     c, b, a = np.meshgrid(g, g, g, indexing="ij")
     G = np.stack([a.ravel(), b.ravel(), c.ravel()], axis=1)      # x~_0 fastest
-    X = np.einsum("pv,evk->epk", el.q2_shape(G), Xm)
-    dX = np.einsum("jpv,evk->epjk", el.q2_dshape(G), Xm)        # d x_k / d xi_j
+    X = np.einsum("pv,evk->epk", shape(G), Xm)
+    dX = np.einsum("jpv,evk->epjk", dshape(G), Xm)              # d x_k / d xi_j
     L = [lagrange_matrix(g, pts[:, i]) for i in range(3)]
     dL = [dlagrange_matrix(g, pts[:, i]) for i in range(3)]
 
@@ -114,19 +123,24 @@ class FRMesh:
         maps = spec.get("maps", {}) or {}
         self.curved = {}
         self._Xm = {}
+        self._morder = {}
         for t in self.types:
             el, V = self.el[t], self.verts[t]
             morder, mconn = maps.get(t, (1, None))
-            self.curved[t] = morder == 2
-            if morder == 2:
+            self.curved[t] = morder >= 2
+            if morder == 3 and t != "hex":
+                raise MeshError("cubic maps are implemented for hexahedra")
+            if morder in (2, 3):
+                shape, dshape = _map_fns(el, morder)
                 Xm = nodes[np.asarray(mconn, np.int64)]
                 self._Xm[t] = Xm
-                self.upts_x[t] = np.einsum("pv,evk->epk", el.q2_shape(el.upts), Xm)
-                self.S_u[t] = curl_metric(el, Xm, el.upts)
-                dX = np.einsum("jpv,evk->epjk", el.q2_dshape(el.upts), Xm)
+                self._morder[t] = morder
+                self.upts_x[t] = np.einsum("pv,evk->epk", shape(el.upts), Xm)
+                self.S_u[t] = curl_metric(el, Xm, el.upts, morder)
+                dX = np.einsum("jpv,evk->epjk", dshape(el.upts), Xm)
                 self.detJ[t] = np.linalg.det(dX)
-                self.fpts_x[t] = np.einsum("pv,evk->epk", el.q2_shape(el.fpts), Xm)
-                Sf = curl_metric(el, Xm, el.fpts)
+                self.fpts_x[t] = np.einsum("pv,evk->epk", shape(el.fpts), Xm)
+                Sf = curl_metric(el, Xm, el.fpts, morder)
             elif morder == 1:
                 self.upts_x[t] = el.map_points(V, el.upts)
                 self.S_u[t], self.detJ[t] = el.metrics(V, el.upts)
@@ -153,7 +167,7 @@ class FRMesh:
         pts, in the form the mesh uses (curl form on curved elements, the
         map's cross products otherwise).  Shape (ne, npts, 3, 3)."""
         if self.curved[t]:
-            return curl_metric(self.el[t], self._Xm[t], pts)
+            return curl_metric(self.el[t], self._Xm[t], pts, self._morder[t])
         return self.el[t].metrics(self.verts[t], pts)[0]
 
     def gidx(self, t, e, i):

@@ -28,7 +28,7 @@ def _uniform(m):
     return {"hex": u}
 
 
-def _pointwise_metric(el, Xm, pts):
+def _pointwise_metric(el, Xm, pts, order=2):
     """S = det J J^{-1} from the cross products of the map's columns."""
     a = np.einsum("jpv,evk->epjk", el.q2_dshape(pts), Xm)
     return np.stack([np.cross(a[:, :, 1], a[:, :, 2]),
@@ -47,16 +47,16 @@ def _mesh(spec, p, pointwise=False):
         omesh.curl_metric = orig
 
 
-def _jittered(spec, n, frac=0.1, seed=3):
-    """Generic quadratic maps: the mid-edge, face and cell nodes strictly
-    inside the box moved by U(-a, a) per component, a = frac h / 2."""
+def _jittered(spec, n, frac=0.1, seed=3, order=2):
+    """Generic maps: the map nodes strictly inside the box that are not cell
+    corners moved by U(-a, a) per component, a = frac h / order."""
     rng = np.random.Generator(np.random.PCG64(seed))
-    m = 2 * n + 1
+    m = order * n + 1
     ids = np.arange(len(spec.nodes))
     ijk = np.stack([ids % m, (ids // m) % m, ids // (m * m)], axis=1)
-    mv = np.all((ijk > 0) & (ijk < m - 1), axis=1) & np.any(ijk % 2 == 1, axis=1)
+    mv = np.all((ijk > 0) & (ijk < m - 1), axis=1) & np.any(ijk % order != 0, axis=1)
     spec.nodes = spec.nodes.copy()
-    spec.nodes[mv] += rng.uniform(-1, 1, (mv.sum(), 3)) * frac / (2 * n)
+    spec.nodes[mv] += rng.uniform(-1, 1, (mv.sum(), 3)) * frac / (order * n)
     return spec
 
 
@@ -189,3 +189,60 @@ def test_conservation_on_curved_periodic_mixed_meshes(layout):
     tot = sum(np.einsum("q,eq,eqk->k", m.el[t].W, m.detJ[t], R[t]) for t in m.types)
     scale = sum(np.einsum("q,eq,eqk->k", m.el[t].W, m.detJ[t], np.abs(R[t])) for t in m.types)
     assert np.all(np.abs(tot) < 1e-13 * scale.max()), tot / scale.max()
+
+
+# ---------------------------------------------------------------- cubic maps
+def _pointwise3(el, Xm, pts, order=3):
+    a = np.einsum("jpv,evk->epjk", el.q3_dshape(pts), Xm)
+    return np.stack([np.cross(a[:, :, 1], a[:, :, 2]),
+                     np.cross(a[:, :, 2], a[:, :, 0]),
+                     np.cross(a[:, :, 0], a[:, :, 1])], axis=2)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_cubic_hexahedra_free_stream_and_conservation(p):
+    spec = _jittered(curved_box_hex((3, 3, 3), order=3), 3, order=3)
+    m = FRMesh(spec.as_dict(), p)
+    assert _free_stream_residual(m) < 1e-10
+    u = {"hex": ics.flow3d(m.upts_x["hex"].reshape(-1, 3)).reshape(m.ne["hex"], -1, 5)}
+    R = FRSystem(m, "ns", mu=0.02).rhs(u)["hex"]
+    el = m.el["hex"]
+    tot = np.einsum("q,eq,eqk->k", el.W, m.detJ["hex"], R)
+    scale = np.einsum("q,eq,eqk->k", el.W, m.detJ["hex"], np.abs(R))
+    assert np.all(np.abs(tot) < 1e-13 * scale.max())
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_cubic_pointwise_metric_loses_free_stream(p):
+    """Generic (jittered) cubic maps: the pointwise metric loses free stream
+    by O(1) at p = 2 and 3, the curl form keeps it."""
+    spec = _jittered(curved_box_hex((3, 3, 3), order=3), 3, order=3)
+    orig = omesh.curl_metric
+    omesh.curl_metric = lambda el, Xm, pts, order=2: _pointwise3(el, Xm, pts)
+    try:
+        mx = FRMesh(spec.as_dict(), p)
+    finally:
+        omesh.curl_metric = orig
+    assert _free_stream_residual(mx) > 1e-2
+    assert _free_stream_residual(FRMesh(spec.as_dict(), p)) < 1e-10
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_quadratic_map_written_as_cubic_gives_the_same_metric(p):
+    """Cubic map nodes placed on a quadratic map: the same geometry, so the
+    same curl-form metric, det J and points."""
+    q = curved_box_hex((2, 2, 2))
+    m2 = FRMesh(q.as_dict(), p)
+    el = m2.el["hex"]
+    X2 = q.nodes[q.maps["hex"][1]]
+    X3 = np.einsum("pv,evk->epk", el.q2_shape(el.q3_nodes()), X2)   # (ne, 64, 3)
+    nodes = np.concatenate([q.nodes, X3.reshape(-1, 3)])
+    ids = len(q.nodes) + np.arange(X3.shape[0] * 64).reshape(-1, 64)
+    spec = dict(q.as_dict())
+    spec["nodes"] = nodes
+    spec["maps"] = {"hex": (3, ids)}
+    m3 = FRMesh(spec, p)
+    sc = np.abs(m2.S_u["hex"]).max()
+    assert np.abs(m3.S_u["hex"] - m2.S_u["hex"]).max() < 1e-13 * sc
+    assert np.abs(m3.detJ["hex"] - m2.detJ["hex"]).max() < 1e-13 * np.abs(m2.detJ["hex"]).max()
+    assert np.abs(m3.upts_x["hex"] - m2.upts_x["hex"]).max() < 1e-14
