@@ -65,13 +65,16 @@ typedef struct {
   const int64_t* conn;  /* [n_elem][n_vertices] node ids (face pairing; and
                            the map of straight elements) */
   int map_order;        /* 0 or 1: straight elements (vertex map); 2:
-                           quadratic map (Section 3.4 "Curved Elements")
-                           given by map_conn */
-  const int64_t* map_conn;  /* map_order 2: [n_elem][n_map] node ids of the
-                               quadratic map; its vertex nodes must be the
-                               vertices of conn.
-                               FR_HEX8, 27 nodes: node a + 3b + 9c at
-                               reference point (-1+a, -1+b, -1+c);
+                           quadratic map, 3: cubic map (hexahedra only)
+                           (Section 3.4 "Curved Elements") given by
+                           map_conn */
+  const int64_t* map_conn;  /* map_order 2 or 3: [n_elem][n_map] node ids of
+                               the map; its vertex nodes must be the vertices
+                               of conn.
+                               FR_HEX8, order 2, 27 nodes: node a + 3b + 9c at
+                               reference point (-1+a, -1+b, -1+c); order 3,
+                               64 nodes: node a + 4b + 16c at
+                               (-1+2a/3, -1+2b/3, -1+2c/3);
                                FR_PRI6, 18 nodes: triangle node + 6 layer,
                                triangle nodes v0, v1, v2 and the midpoints of
                                edges 01, 12, 02, layers z = -1, 0, 1 (the

@@ -204,7 +204,7 @@ class FRMesh:
             self._keep.append(conn)
             morder, mconn = maps.get(name, (1, None))
             mptr = None
-            if morder == 2:
+            if morder >= 2:
                 mconn = np.ascontiguousarray(mconn, np.int64)
                 self._keep.append(mconn)
                 mptr = mconn.ctypes.data_as(C.POINTER(C.c_int64))

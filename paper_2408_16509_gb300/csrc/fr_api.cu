@@ -53,10 +53,12 @@ int fr_mesh_create(const fr_mesh_desc* d, fr_mesh** out) {
     if (t.etype < 0 || t.etype > 2 || seen[t.etype])
       return fail(FR_EINVAL, "bad or repeated element type");
     if (t.n_elem < 0 || (t.n_elem > 0 && !t.conn)) return fail(FR_EINVAL, "bad connectivity");
-    if (t.map_order < 0 || t.map_order > 2)
-      return fail(FR_EINVAL, "map order must be 0, 1 or 2");
-    if (t.map_order == 2 && t.n_elem > 0 && !t.map_conn)
-      return fail(FR_EINVAL, "quadratic maps need map_conn");
+    if (t.map_order < 0 || t.map_order > 3)
+      return fail(FR_EINVAL, "map order must be 0, 1, 2 or 3");
+    if (t.map_order == 3 && t.etype != FR_HEX8)
+      return fail(FR_EINVAL, "cubic maps: hexahedra only");
+    if (t.map_order >= 2 && t.n_elem > 0 && !t.map_conn)
+      return fail(FR_EINVAL, "curved maps need map_conn");
     seen[t.etype] = true;
     if (t.etype == FR_PRI6 && t.n_elem > 0 && d->point_family == FR_POINTS_GLL)
       return fail(FR_EINVAL, "Gauss-Lobatto hexahedra cannot meet prisms (their quad faces carry Gauss-Legendre points)");
@@ -65,8 +67,8 @@ int fr_mesh_create(const fr_mesh_desc* d, fr_mesh** out) {
     for (int i = 0; i < d->n_etypes; ++i)
       if (d->etypes[i].etype == k) {
         in.types.push_back({k, {d->etypes[i].n_elem, d->etypes[i].conn}});
-        in.map_order.push_back(d->etypes[i].map_order == 2 ? 2 : 1);
-        in.map_conn.push_back(d->etypes[i].map_order == 2 ? d->etypes[i].map_conn : nullptr);
+        in.map_order.push_back(d->etypes[i].map_order >= 2 ? d->etypes[i].map_order : 1);
+        in.map_conn.push_back(d->etypes[i].map_order >= 2 ? d->etypes[i].map_conn : nullptr);
       }
   for (int i = 0; i < d->n_periodic; ++i)
     in.periodic.push_back({d->periodic[i][0], d->periodic[i][1], d->periodic[i][2]});

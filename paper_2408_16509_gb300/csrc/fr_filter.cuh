@@ -92,8 +92,10 @@ __device__ __forceinline__ double entropy_of(double r, double mx, double my,
 // (p the FP64 pressure of the same state): every operation of
 // p = (g-1)(E - (mx^2+my^2+mz^2)/(2 rho)) and the rounding of the inputs
 // contribute at most ~11 unit roundoffs (2^-24) of (g-1)(|E| + |k|); dp
-// takes 2e-6 ~ 34 of them.  __powf(rho, -g) is within ~2e-6 relative; the s
-// bounds widen it to 1e-5.  Points with rho <= 0 (or NaN) get no bounds.
+// takes 2e-6 ~ 34 of them.  __powf(rho, -g) = 2^(-g log2 rho) errs by
+// about ln 2 |g log2 rho| 2^-22 relative, under 2e-6 for rho in [2^-8, 2^8];
+// the s bounds widen it to 1e-5 there.  Points with rho outside that range
+// get no entropy bounds, points with rho <= 0 (or NaN) no bounds at all.
 struct PtScreen {
   float plo, phi, slo, shi;
   bool pos;  // rho > 0 in FP32 (bounds valid)
@@ -114,6 +116,14 @@ __device__ __forceinline__ PtScreen screen_point(float r, float mx, float my,
   const float dp = 2e-6f * gm1 * (fabsf(E) + fabsf(k));
   o.plo = p - dp;
   o.phi = p + dp;
+  if (!(r >= 0x1p-8f && r <= 0x1p8f)) {
+    // the intrinsic's error grows with |g log2 r|: outside this range the
+    // 1e-5 margin is not shown to hold, so no entropy bounds (the point's
+    // FP64 entropy is always evaluated)
+    o.slo = -INFINITY;
+    o.shi = INFINITY;
+    return o;
+  }
   const float rg = __powf(r, -g);
   o.slo = o.plo * rg * (o.plo >= 0.f ? 1.f - 1e-5f : 1.f + 1e-5f);
   o.shi = o.phi * rg * (o.phi >= 0.f ? 1.f + 1e-5f : 1.f - 1e-5f);

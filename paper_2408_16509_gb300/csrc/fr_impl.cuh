@@ -427,7 +427,7 @@ int setup_device(fr_mesh* m) {
     const HostType& H = m->host[t];
     DevType D;
     D.kind = H.kind;
-    D.curved = H.map_order == 2;
+    D.curved = H.map_order >= 2;
     D.nu = H.ref.nupts;
     D.nf = H.ref.nfpts;
     D.ne = H.ne;

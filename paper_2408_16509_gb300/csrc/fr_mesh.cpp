@@ -148,6 +148,35 @@ struct Quad1D {  // 1D quadratic Lagrange factors on {-1, 0, 1}
   }
 };
 
+// x_k(pt) and a[j][k] = d x_k / d xi_j of a tensor hexahedron map of
+// order k (nodes a + (k+1) b + (k+1)^2 c at equispaced reference points).
+void lagrange1d(int n, const double* g, double s, double* l, double* d);
+void hexk_eval(int order, const double* X, const double* pt, double x[3], double a[3][3]) {
+  const int n = order + 1;
+  double g[8], l[3][8], d[3][8];
+  for (int i = 0; i < n; ++i) g[i] = -1.0 + 2.0 * i / order;
+  for (int i = 0; i < 3; ++i) lagrange1d(n, g, pt[i], l[i], d[i]);
+  for (int k = 0; k < 3; ++k) {
+    x[k] = 0.0;
+    for (int j = 0; j < 3; ++j) a[j][k] = 0.0;
+  }
+  for (int c = 0; c < n; ++c)
+    for (int b = 0; b < n; ++b)
+      for (int aa = 0; aa < n; ++aa) {
+        const double* P = &X[(aa + n * (b + n * c)) * 3];
+        const double N = l[0][aa] * l[1][b] * l[2][c];
+        const double g0 = d[0][aa] * l[1][b] * l[2][c];
+        const double g1 = l[0][aa] * d[1][b] * l[2][c];
+        const double g2 = l[0][aa] * l[1][b] * d[2][c];
+        for (int k = 0; k < 3; ++k) {
+          x[k] += N * P[k];
+          a[0][k] += g0 * P[k];
+          a[1][k] += g1 * P[k];
+          a[2][k] += g2 * P[k];
+        }
+      }
+}
+
 // x_k(pt) and a[j][k] = d x_k / d xi_j of a 27-node map X[27][3].
 void q2_eval(const double* X, const double* pt, double x[3], double a[3][3]) {
   double l[3][3], d[3][3];
@@ -193,7 +222,7 @@ void lagrange1d(int n, const double* g, double s, double* l, double* d) {
 
 // Nodal fields w[n][j][node] = X_l d X_m / d xi_j ((n, m, l) cyclic) of a
 // 27-node map at the Gauss-Lobatto tensor nodes g (n1 per direction).
-void curl_fields(const double* X, const std::vector<double>& g, double* w) {
+void curl_fields(const double* X, const std::vector<double>& g, double* w, int order = 2) {
   const int n1 = int(g.size()), ng = n1 * n1 * n1;
   for (int c = 0; c < n1; ++c)
     for (int b = 0; b < n1; ++b)
@@ -201,7 +230,7 @@ void curl_fields(const double* X, const std::vector<double>& g, double* w) {
         const int node = a + n1 * (b + n1 * c);
         const double pt[3] = {g[a], g[b], g[c]};
         double x[3], J[3][3];
-        q2_eval(X, pt, x, J);
+        hexk_eval(order, X, pt, x, J);
         for (int n = 0; n < 3; ++n) {
           const int m = (n + 1) % 3, l = (n + 2) % 3;
           for (int j = 0; j < 3; ++j) w[(size_t(n) * 3 + j) * ng + node] = x[l] * J[j][m];
@@ -271,12 +300,17 @@ void parallel_elements(int64_t ne, F body) {
 }
 
 // Number of map nodes of a quadratic element and the map node of each vertex.
-int q2_nodes(int kind) { return kind == EK_HEX ? 27 : (kind == EK_PRI ? 18 : 10); }
-const int* q2_corners(int kind) {
+int q2_nodes(int kind, int order = 2) {
+  if (kind == EK_HEX) return (order + 1) * (order + 1) * (order + 1);
+  return kind == EK_PRI ? 18 : 10;
+}
+const int* q2_corners(int kind, int order = 2) {
   static const int hexc[8] = {0, 2, 8, 6, 18, 20, 26, 24};
+  static const int hex3[8] = {0, 3, 15, 12, 48, 51, 63, 60};
   static const int pric[6] = {0, 1, 2, 12, 13, 14};
   static const int tetc[4] = {0, 1, 2, 3};
-  return kind == EK_HEX ? hexc : (kind == EK_PRI ? pric : tetc);
+  if (kind == EK_HEX) return order == 3 ? hex3 : hexc;
+  return kind == EK_PRI ? pric : tetc;
 }
 
 // x_k(pt) and a[j][k] = d x_k / d xi_j of a quadratic prism (18 nodes:
@@ -459,12 +493,13 @@ void curved_geometry(HostType& T) {
   T.fnvec.resize(size_t(T.ne) * nf * 3);
   parallel_elements(T.ne, [&](int64_t e0, int64_t e1) {
     std::vector<double> w(size_t(9) * ng);
+    const int nmap = q2_nodes(EK_HEX, T.map_order);
     for (int64_t e = e0; e < e1; ++e) {
-      const double* X = &T.mapx[size_t(e) * 81];
-      curl_fields(X, g, w.data());
+      const double* X = &T.mapx[size_t(e) * nmap * 3];
+      curl_fields(X, g, w.data(), T.map_order);
       for (int q = 0; q < nu; ++q) {
         double x[3], J[3][3], S[3][3];
-        q2_eval(X, &R.upts[3 * q], x, J);
+        hexk_eval(T.map_order, X, &R.upts[3 * q], x, J);
         for (int k = 0; k < 3; ++k) T.upts_x[(size_t(e) * nu + q) * 3 + k] = x[k];
         const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
                            J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
@@ -476,7 +511,7 @@ void curved_geometry(HostType& T) {
       }
       for (int q = 0; q < nf; ++q) {
         double x[3], J[3][3], S[3][3];
-        q2_eval(X, &R.fpts[3 * q], x, J);
+        hexk_eval(T.map_order, X, &R.fpts[3 * q], x, J);
         for (int k = 0; k < 3; ++k) T.fpts_x[(size_t(e) * nf + q) * 3 + k] = x[k];
         curl_eval(n1, &Lf[size_t(q) * 3 * n1], &dLf[size_t(q) * 3 * n1], w.data(), S);
         const double* n = &R.fnorm[3 * q];
@@ -512,7 +547,7 @@ void metric_points(const HostType& T, int np, const double* pts,
     });
     return;
   }
-  if (T.map_order == 2) {
+  if (T.map_order >= 2) {
     const int n1 = R.p + 1, ng = n1 * n1 * n1;
     const std::vector<double> g = gll_nodes(n1);
     std::vector<double> L, dL;
@@ -520,7 +555,8 @@ void metric_points(const HostType& T, int np, const double* pts,
     parallel_elements(T.ne, [&](int64_t e0, int64_t e1) {
       std::vector<double> w(size_t(9) * ng);
       for (int64_t e = e0; e < e1; ++e) {
-        curl_fields(&T.mapx[size_t(e) * 81], g, w.data());
+        curl_fields(&T.mapx[size_t(e) * q2_nodes(EK_HEX, T.map_order) * 3], g, w.data(),
+                    T.map_order);
         for (int q = 0; q < np; ++q) {
           double M[3][3];
           curl_eval(n1, &L[size_t(q) * 3 * n1], &dL[size_t(q) * 3 * n1], w.data(), M);
@@ -571,10 +607,11 @@ std::string build_mesh(const MeshInput& in, std::vector<HostType>& types,
     int64_t span = T.ne * 5 * int64_t(T.ref.nfpts);
     if (span >= (int64_t(1) << 29)) return "too many elements of one type";
     const size_t ti = size_t(&t - in.types.data());
-    if (ti < in.map_order.size() && in.map_order[ti] == 2) {
-      T.map_order = 2;
-      const int nmap = q2_nodes(T.kind);
-      const int* corner = q2_corners(T.kind);
+    if (ti < in.map_order.size() && in.map_order[ti] >= 2) {
+      T.map_order = in.map_order[ti];
+      if (T.map_order == 3 && T.kind != EK_HEX) return "cubic maps are supported on hexahedra only";
+      const int nmap = q2_nodes(T.kind, T.map_order);
+      const int* corner = q2_corners(T.kind, T.map_order);
       T.map_conn.assign(in.map_conn[ti], in.map_conn[ti] + size_t(T.ne) * nmap);
       for (int64_t e = 0; e < T.ne; ++e) {
         for (int v = 0; v < nmap; ++v) {

@@ -194,3 +194,28 @@ def test_curved_mixed_free_stream_at_size(p):
     r = g.rhs()
     scale = 4.0 * (p + 1) ** 2 * n
     assert max(np.abs(v).max() for v in r.values()) < 1e-11 * scale
+
+
+# ---------------------------------------------------------------- cubic maps
+@pytest.mark.parametrize("p", [2, 3, 4])
+@pytest.mark.parametrize("physics", ["euler", "ns"])
+def test_cubic_hex_rhs_fp64(p, physics):
+    """64-node (cubic) hexahedron maps, FP64, against the oracle."""
+    spec = curved_box_hex((3, 3, 2), order=3)
+    o, osys, g = _pair(spec, p, physics)
+    g.set_solution(lib_state(g, _tgv))
+    err = rel_l2_rhs(g.rhs(), osys.rhs(oracle_state(o, _tgv)))
+    assert err.max() < (5e-12 if p == 4 else 1e-12), err
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-6)])
+def test_cubic_hex_rk_steps(precision, tol):
+    spec = curved_box_hex((3, 3, 2), order=3)
+    o, osys, g = _pair(spec, 3, "ns", precision=precision)
+    g.set_solution(lib_state(g, _tgv))
+    u = oracle_state(o, _tgv)
+    for _ in range(2):
+        u = rk.step(osys.rhs, u, 1e-3, "rk45")
+    g.rk_step("rk45", 1e-3, 2)
+    err = rel_l2(g.get_solution(), u)
+    assert err.max() < tol, err

@@ -16,6 +16,7 @@ import paper_2408_16509_gb300 as fr
 from frinputs import box_hex, ics
 from frtest import lib_state, oracle_state, rel_l2
 from oracle import entropy_filter as EF
+from oracle import rk
 from oracle import mlp
 from oracle.fr import FRSystem
 from oracle.mesh import FRMesh as OracleMesh
@@ -93,6 +94,46 @@ def test_filter_fp32_with_fp64_checks_against_oracle():
         u, _ = EF.rk4_step_filtered(s, u, dt, tau=2.0 ** -20)
     err = rel_l2(g.get_solution(), u)
     assert err[0] < 5e-3 and err[1:].max() < 1e-5, err
+
+
+def test_filter_fp32_single_application_same_elements_and_strengths():
+    """One filter application to the same FP32-representable state with the
+    same s_min on both sides (the oracle's, from the unperturbed state): FP32
+    values with FP64 checks against the FP64 oracle with the FP32 entropy
+    tolerance 2^-20.  Elements whose oracle margin at zeta = 0 is within
+    1e-5 of the threshold may flip with the FP32 rounding of the filtered
+    values; every other element is filtered on both sides or on neither, and
+    the strengths agree to 1e-3 relative (margins differ by FP32 rounding,
+    ~1e-7 of the state, divided by the margin's slope at the root)."""
+    o, s, g = _strip(64, precision="fp32")
+    u0 = oracle_state(o, ics.shu_osher)
+    smin = EF.element_smin(s, u0)
+    # a seeded 0.1 % point-wise perturbation: nearly every element violates
+    # the entropy bound of the unperturbed state by a little (moderate
+    # strengths rather than the zeta_max fallbacks of a shock)
+    rng = np.random.Generator(np.random.PCG64(9))
+    u = {t: v * (1 + 1e-3 * rng.uniform(-1, 1, v.shape)) for t, v in u0.items()}
+    u32 = {t: v.astype(np.float32).astype(np.float64) for t, v in u.items()}
+    g.set_solution(u32)
+    g.filter_enable(True)
+    g.filter_solution(smin)
+    zg, _ = g.filter_last()
+    _, zo, _, _ = EF.filter_state(s, u32, smin, tau=2.0 ** -20)
+    zo = zo["hex"]
+    op = EF.FilterOperators(o.el["hex"])
+    g0 = np.empty(len(zo))
+    for e in range(len(zo)):
+        uh = op.Vinv @ u32["hex"][e]
+        rho_m = max(np.dot(op.el.W, u32["hex"][e][:, 0]) / op.el.W.sum(), EF.EPS_POS)
+        p_m = max(np.dot(op.el.W, EF.primitives(u32["hex"][e], 1.4)[2]) / op.el.W.sum(),
+                  EF.EPS_POS)
+        vu, vf = op.evaluate(uh, 0.0)
+        g0[e] = EF.margin(vu, vf, smin["hex"][e], 1.4, rho_m, p_m, 2.0 ** -20)
+    clear = np.abs(g0) > 1e-5
+    assert np.sum((zo > 0) & (zo < 36)) > 40
+    assert np.array_equal((zg > 0)[clear], (zo > 0)[clear])
+    both = clear & (zo > 0) & (zg > 0)
+    assert np.all(np.abs(zg[both] - zo[both]) <= 1e-3 * zo[both])
 
 
 def test_unfiltered_run_blows_up_filtered_run_does_not():

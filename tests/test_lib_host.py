@@ -62,6 +62,7 @@ SPECS = {
     "hex-gll": lambda: box_hex((3, 2, 2), perturb=0.1),
     "curved-gll": lambda: curved_box_hex((3, 2, 2)),
     "curved-mixed": lambda: curved_mixed_box(n=3),
+    "curved-cubic": lambda: curved_box_hex((3, 2, 2), order=3),
     "mixed": lambda: mixed_box(n=3, x_pri=0.34, x_tet=0.67, perturb=0.05),
     "curved": lambda: curved_box_hex((3, 2, 2)),
 }

@@ -67,3 +67,28 @@ def test_static_upload_rejects_oversized_solutions():
     rc = _static(g, "hex", u)
     assert fr.ERRORS.get(rc) == "FR_EINVAL"
     assert b"static staging limit" in fr.load().fr_last_error()
+
+
+def test_static_upload_leaves_device_free_memory_unchanged():
+    """No device allocation: the device's free memory (cudaMemGetInfo) is the
+    same before and after repeated uploads on a fresh handle, while the
+    allocating fr_set_solution on another fresh handle does take memory for
+    its staging buffer (2.56 MB here), so the check can see an allocation."""
+    torch = pytest.importorskip("torch")
+    fr.build()
+    spec = box_hex((10, 10, 10))           # 1000 * 64 * 5 values: 2.56 MB FP64
+    g = fr.FRMesh(spec, 3)
+    u = np.ascontiguousarray(_state(g, np.random.default_rng(3), 0.01)["hex"])
+    assert _static(g, "hex", u) == 0       # first call: looks up the array's address
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        assert _static(g, "hex", u) == 0
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    h = fr.FRMesh(spec, 3)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    h.set_solution({"hex": u})
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] < free1
