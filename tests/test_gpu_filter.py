@@ -102,9 +102,15 @@ def test_filter_fp32_single_application_same_elements_and_strengths():
     values with FP64 checks against the FP64 oracle with the FP32 entropy
     tolerance 2^-20.  Elements whose oracle margin at zeta = 0 is within
     1e-5 of the threshold may flip with the FP32 rounding of the filtered
-    values; every other element is filtered on both sides or on neither, and
-    the strengths agree to 1e-3 relative (margins differ by FP32 rounding,
-    ~1e-7 of the state, divided by the margin's slope at the root)."""
+    values; every other element is filtered on both sides or on neither.
+    The GPU's strength must be the oracle's smallest feasible strength up to
+    the FP32 rounding of the margin: the oracle margin at the GPU's zeta is
+    within 4 * 2^-20 of zero.  The strengths themselves are compared where
+    the margin is steep (zeta* < 2: a 1 % change of zeta moves the margin by
+    1e-5 or more there) to 2e-3 relative.  Where it is flat (large zeta*:
+    sigma_k = exp(-zeta (d_k/p)^2) and so the filtered state barely depend
+    on zeta) FP32 rounding of ~1e-6 in the margin moves zeta* by a percent
+    or more, and only the margin check applies."""
     o, s, g = _strip(64, precision="fp32")
     u0 = oracle_state(o, ics.shu_osher)
     smin = EF.element_smin(s, u0)
@@ -121,19 +127,26 @@ def test_filter_fp32_single_application_same_elements_and_strengths():
     _, zo, _, _ = EF.filter_state(s, u32, smin, tau=2.0 ** -20)
     zo = zo["hex"]
     op = EF.FilterOperators(o.el["hex"])
-    g0 = np.empty(len(zo))
-    for e in range(len(zo)):
-        uh = op.Vinv @ u32["hex"][e]
-        rho_m = max(np.dot(op.el.W, u32["hex"][e][:, 0]) / op.el.W.sum(), EF.EPS_POS)
-        p_m = max(np.dot(op.el.W, EF.primitives(u32["hex"][e], 1.4)[2]) / op.el.W.sum(),
+
+    def margin_at(e, zeta):               # the oracle's margin of element e
+        ue = u32["hex"][e]
+        rho_m = max(np.dot(op.el.W, ue[:, 0]) / op.el.W.sum(), EF.EPS_POS)
+        p_m = max(np.dot(op.el.W, EF.primitives(ue, 1.4)[2]) / op.el.W.sum(),
                   EF.EPS_POS)
-        vu, vf = op.evaluate(uh, 0.0)
-        g0[e] = EF.margin(vu, vf, smin["hex"][e], 1.4, rho_m, p_m, 2.0 ** -20)
+        vu, vf = op.evaluate(op.Vinv @ ue, zeta)
+        return EF.margin(vu, vf, smin["hex"][e], 1.4, rho_m, p_m, 2.0 ** -20)
+
+    g0 = np.array([margin_at(e, 0.0) for e in range(len(zo))])
     clear = np.abs(g0) > 1e-5
     assert np.sum((zo > 0) & (zo < 36)) > 40
     assert np.array_equal((zg > 0)[clear], (zo > 0)[clear])
-    both = clear & (zo > 0) & (zg > 0)
-    assert np.all(np.abs(zg[both] - zo[both]) <= 1e-3 * zo[both])
+    both = clear & (zo > 0) & (zg > 0) & (zo < EF.ZETA_MAX)
+    steep = both & (zo < 2.0)
+    assert np.sum(steep) > 20
+    assert np.all(np.abs(zg[steep] - zo[steep]) <= 2e-3 * zo[steep])
+    for e in np.nonzero(both)[0]:
+        ge = margin_at(e, float(zg[e]))
+        assert abs(ge) <= 4 * 2.0 ** -20, (e, zg[e], zo[e], ge)
 
 
 def test_unfiltered_run_blows_up_filtered_run_does_not():
