@@ -21,9 +21,11 @@ paper gives no formulas; the reading used here:
   (s - s_min + tau |s_min|)/|s_min| with tau = 1e-8 (2^-20 when the
   state being compared is FP32, whose resolution is coarser than 1e-8);
   elements with g(0) >= 0 are left alone; otherwise zeta* is the root of g
-  found by the Illinois method on a bracket [lo, hi] with g(lo) < 0 <= g(hi),
-  stopped when hi - lo <= 1e-6 hi or after 24 evaluations; the result is
-  the feasible end hi.  The plain bracket is [0, zeta_max], zeta_max = 36
+  found by the Illinois method on a bracket [lo, hi] with g(lo) < 0 <=
+  g(hi), stopped when hi - lo <= 1e-6 hi, when g(hi) <= tau (the feasible
+  end meets the constraints with no more slack than the tolerance they
+  already carry, so further filtering could not be told from none) or
+  after 24 evaluations; the result is the feasible end hi.  The plain bracket is [0, zeta_max], zeta_max = 36
   (exp(-36) ~ 2e-16); with a start guess z0 the bracket is opened at z0,
   then z0 / r or r z0 (r = 1.25 unless given), then by halving / doubling.
   If g(zeta_max) < 0
@@ -31,7 +33,8 @@ paper gives no formulas; the reading used here:
 
 Parity: pinned by the tests in tests/test_oracle_filter.py (identity at
 zeta = 0, mean conservation, feasibility of the result, minimality
-(g(zeta* (1 - 2e-6)) < 0), agreement with a brute-force scan).
+(g(zeta* (1 - 2e-6)) < 0 or g(zeta*) <= tau), agreement with a brute-force
+scan).
 """
 import numpy as np
 
@@ -120,21 +123,25 @@ def margin(vals_u, vals_f, smin, gamma, rho_mean, p_mean, tau=TAU_S):
     return g if np.isfinite(g) or g == np.inf else -np.inf
 
 
-def find_zeta(gfun, guess=None, ratio=1.25):
+def find_zeta(gfun, guess=None, ratio=1.25, gtol=TAU_S):
     """Smallest feasible zeta by a bracketed Illinois iteration.
 
     g(0) is evaluated first in every case (it decides whether the element
     is filtered at all).  Without a guess the bracket is [0, zeta_max].
     With a guess z0 the bracket is opened around it: z0, then z0 / ratio
-    or ratio z0, then repeated halving / doubling.  Returns
-    (zeta, evaluations, fallback).  ratio: first bracket step around
-    a guess."""
+    or ratio z0, then repeated halving / doubling.  The search ends as soon
+    as a feasible point has margin <= gtol, when the bracket is within
+    1e-6 relative, or after 24 evaluations.  Returns (zeta, evaluations,
+    fallback).  ratio: first bracket step around a guess."""
     evals = 0
 
     def G(z):
         nonlocal evals
         evals += 1
         return gfun(z)
+
+    def close(gh):
+        return gtol is not None and gh <= gtol
 
     g0 = G(0.0)
     if g0 >= 0:
@@ -148,8 +155,8 @@ def find_zeta(gfun, guess=None, ratio=1.25):
         gz = G(guess)
         if gz >= 0:
             hi, ghi = guess, gz
-            z, f = guess / ratio, 1.0 / ratio
-            while True:
+            z = guess / ratio
+            while not close(ghi):
                 gz = G(z)
                 if gz < 0:
                     lo, glo = z, gz
@@ -157,7 +164,7 @@ def find_zeta(gfun, guess=None, ratio=1.25):
                 hi, ghi = z, gz
                 if z < 1e-6:
                     return hi, evals, False
-                z, f = z * 0.5, 0.5
+                z = z * 0.5
         else:
             lo, glo = guess, gz
             z = min(ratio * guess, ZETA_MAX)
@@ -171,13 +178,14 @@ def find_zeta(gfun, guess=None, ratio=1.25):
                     return ZETA_MAX, evals, True
                 z = min(2.0 * z, ZETA_MAX)
     side = 0
-    while hi - lo > REL_TOL * hi and evals < MAX_EVALS:
+    g_hi = ghi      # the margin at hi (ghi is halved by the Illinois rule)
+    while not close(g_hi) and hi - lo > REL_TOL * hi and evals < MAX_EVALS:
         z = (lo * ghi - hi * glo) / (ghi - glo)
         if not (lo < z < hi):
             z = 0.5 * (lo + hi)
         gz = G(z)
         if gz >= 0:
-            hi, ghi = z, gz
+            hi, ghi, g_hi = z, gz, gz
             if side == 1:
                 glo *= 0.5
             side = 1
@@ -250,7 +258,7 @@ def filter_state(system, u, smin, predictor=None, record=None, tau=TAU_S,
                         guess = float(predictor(feat))
                 else:
                     feat = None
-            z, n, fb = find_zeta(gfun, guess, ratio)
+            z, n, fb = find_zeta(gfun, guess, ratio, tau)
             zt[e], et[e], ft[e] = z, n, fb
             if z > 0:
                 ut[e] = op.evaluate(uhat, z)[0]

@@ -43,7 +43,7 @@ def test_zero_strength_is_identity_and_mean_is_kept(name):
     assert np.abs(vu - (el.W @ u) / el.W.sum()).max() < 1e-12
 
 
-def test_illinois_finds_minimal_feasible_strength():
+def test_root_find_returns_minimal_feasible_strength():
     """On a synthetic monotone margin the root-find returns the root to the
     stated tolerance, from the plain bracket and from guesses either side."""
     root = 2.7182818
@@ -51,9 +51,11 @@ def test_illinois_finds_minimal_feasible_strength():
     def g(z):
         return np.tanh(z - root)
     for guess in (None, 0.1, 2.0, 3.0, 30.0):
-        z, n, fb = EF.find_zeta(g, guess)
-        assert not fb and g(z) >= 0
-        assert abs(z - root) <= 2e-6 * root
+        for gtol in (EF.TAU_S, None):
+            z, n, fb = EF.find_zeta(g, guess, gtol=gtol)
+            assert not fb and g(z) >= 0
+            assert abs(z - root) <= 2e-6 * root
+            assert g(z) <= EF.TAU_S or g(z * (1 - 2e-6)) < 0
     z, n, fb = EF.find_zeta(lambda z: -1.0)
     assert fb and z == EF.ZETA_MAX
     z, n, fb = EF.find_zeta(lambda z: 1.0)
@@ -62,6 +64,19 @@ def test_illinois_finds_minimal_feasible_strength():
     n_plain = EF.find_zeta(g)[1]
     n_guess = EF.find_zeta(g, root * 1.05)[1]
     assert n_guess < n_plain
+
+
+def test_margin_stop_ends_at_the_first_feasible_point_within_tau():
+    """With gtol the search ends as soon as the feasible end's margin is at
+    most gtol, and never returns an infeasible strength."""
+    root = 0.37
+
+    def g(z):
+        return 1e-3 * (z - root)          # margin 1e-8 is 1e-5 past the root
+    z, n, fb = EF.find_zeta(g, gtol=1e-8)
+    assert 0.0 <= g(z) <= 1e-8
+    z2, n2, _ = EF.find_zeta(g, gtol=None)
+    assert n <= n2 and abs(z2 - root) <= 1e-6 * root
 
 
 def test_filtered_elements_are_feasible_minimal_and_match_a_scan():
@@ -87,7 +102,7 @@ def test_filtered_elements_are_feasible_minimal_and_match_a_scan():
             vu, vf = op.evaluate(uhat, zz)
             return EF.margin(vu, vf, smin["hex"][e], g, mr, mp)
         assert gfun(zt[e]) >= 0
-        assert gfun(zt[e] * (1 - 2e-6)) < 0
+        assert gfun(zt[e]) <= EF.TAU_S or gfun(zt[e] * (1 - 2e-6)) < 0
         scan = np.linspace(0, EF.ZETA_MAX, 3601)
         first = scan[np.argmax([gfun(q) >= 0 for q in scan])]
         assert first - 0.01 <= zt[e] <= first + 1e-9
