@@ -5,5 +5,5 @@ The compute path is the CUDA library ``lib/libfrgb.so`` (sources in
 arguments to it.
 """
 from ._binding import (ERRORS, ETYPES, AdaptCtl, FRError, FRGroup, FRMesh, load,  # noqa: F401
-                       mlp_loss_grad, mlp_train, probe_fma)
+                       check_conversions, mlp_loss_grad, mlp_train, probe_fma)
 from .build import build  # noqa: F401

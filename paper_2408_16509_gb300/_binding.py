@@ -96,6 +96,7 @@ def load():
         "fr_rk_stage": (I, [P, I, D, I, I, I]),
         "fr_set_bc_state": (I, [P, I, BC_FN, D, P]),
         "fr_probe_fma": (I, [I, I, C.c_int64, C.POINTER(D), C.POINTER(D)]),
+        "fr_check_conversions": (I, [I, C.c_uint64, C.c_int64, C.POINTER(C.c_int64)]),
         "fr_get_rhs": (I, [P, I, P]),
         "fr_rk_step": (I, [P, I, D, I]),
         "fr_rk_adaptive_step": (I, [P, C.POINTER(AdaptCtl), C.POINTER(D),
@@ -708,6 +709,14 @@ def probe_fma(dtype="fp64", iters=None, device=0):
     _check(load().fr_probe_fma(int(device), code, int(iters), C.byref(ms),
                                C.byref(fl)))
     return fl.value / (ms.value * 1e-3) / 1e12, ms.value, fl.value
+
+
+def check_conversions(n, seed=1, device=0):
+    """Number of the n seeded patterns on which the library's FP32 <-> FP64
+    conversions differ from the hardware's (fr_check_conversions)."""
+    bad = C.c_int64()
+    _check(load().fr_check_conversions(int(device), int(seed), int(n), C.byref(bad)))
+    return bad.value
 
 
 def mlp_train(x, zstar, params, epochs, lr, device=0):

@@ -66,6 +66,66 @@ __device__ __forceinline__ void hex_stage_needs(const HexStage<T, TR>& a, bool* 
   *na = a.mode == 1 && a.stage > 0;
 }
 
+// The mixed form's RK epilogue (FP32 stage values and right-hand side, FP64
+// registers): each increment c dt r is formed in FP32 (r carries FP32
+// rounding already) and added to the FP64 register exactly as a double, and
+// the next stage value is the register rounded to FP32 plus its FP32
+// increment.  One FP64 instruction per register write; the conversions run
+// on the integer pipe.  Modes 1 and 2 as in hex_stage_apply.
+template <typename T, typename TR>
+__device__ __forceinline__ void hex_stage_apply_mixed(const HexStage<T, TR>& a,
+                                                      long long i0, long long vstr,
+                                                      const T R[5], const TR x[5],
+                                                      const TR ac[5], T s[5]) {
+  const float dt = narrow_f64(*a.dt);
+  const int st = a.stage;
+  if (a.mode == 1) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const long long i = i0 + k * vstr;
+      const float r = R[k];
+      if (st == 0) {
+        a.A[i] = x[k] + widen_f32(dt * (1.0f / 6.0f) * r);
+        const float y = narrow_f64(x[k]) + dt * 0.5f * r;
+        a.Y[i] = y;
+        s[k] = y;
+      } else if (st < 3) {
+        a.A[i] = ac[k] + widen_f32(dt * (1.0f / 3.0f) * r);
+        const float y = narrow_f64(x[k]) + (st == 1 ? dt * 0.5f : dt) * r;
+        a.Y[i] = y;
+        s[k] = y;
+      } else {
+        const double xx = ac[k] + widen_f32(dt * (1.0f / 6.0f) * r);
+        a.X[i] = xx;
+        s[k] = narrow_f64(xx);
+      }
+    }
+    return;
+  }
+  const float bdt = c_rk45_bf[st] * dt;
+  const float adt = st < 4 ? (c_rk45_af[st] - c_rk45_bf[st]) * dt : 0.f;
+  const float edt = c_rk45_ef[st] * dt;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const long long i = i0 + k * vstr;
+    const float r = R[k];
+    const double xx = x[k] + widen_f32(bdt * r);
+    a.X[i] = xx;
+    if (a.E) {  // error estimate dt sum_i (b_i - bhat_i) R_i
+      const double ev = widen_f32(edt * r);
+      a.E[i] = st == 0 ? ev : a.E[i] + ev;
+    }
+    const float xf = narrow_f64(xx);
+    if (st < 4) {
+      const float y = xf + adt * r;
+      a.Y[i] = y;
+      s[k] = y;
+    } else {
+      s[k] = xf;
+    }
+  }
+}
+
 // RK epilogue for one point from the register values x (X) and ac (A) read
 // beforehand: R[5] -> registers; s receives the next stage value (u for a
 // bare right-hand side, mode 0).
@@ -85,6 +145,10 @@ __device__ __forceinline__ void hex_stage_apply(const HexStage<T, TR>& a,
       a.out[i0 + k * vstr] = R[k];
       s[k] = u[k];
     }
+    return;
+  }
+  if constexpr (sizeof(T) == 4 && sizeof(TR) == 8) {
+    hex_stage_apply_mixed(a, i0, vstr, R, x, ac, s);
     return;
   }
   const TR dt = TR(*a.dt);

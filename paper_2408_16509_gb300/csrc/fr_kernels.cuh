@@ -14,6 +14,7 @@
 #pragma once
 #include <cstdint>
 
+#include "fr_convert.cuh"
 #include "fr_phys.cuh"
 
 namespace frgb {
@@ -76,6 +77,22 @@ static __constant__ double c_rk45_e[5] = {
     -1672844663538.0 / 4480602732383.0 + 1563879915014.0 / 6823010717585.0,
     2114624349019.0 / 3568978502595.0 - 606302364029.0 / 971179775848.0,
     5198255086312.0 / 14908931495163.0 - 1097981568119.0 / 3980877426909.0};
+
+// The same coefficients rounded once to FP32, for the mixed form's FP32
+// increments (b dt r and friends are formed in FP32 there).
+static __constant__ float c_rk45_af[4] = {
+    float(970286171893.0 / 4311952581923.0), float(6584761158862.0 / 12103376702013.0),
+    float(2251764453980.0 / 15575788980749.0), float(26877169314380.0 / 34165994151039.0)};
+static __constant__ float c_rk45_bf[5] = {
+    float(1153189308089.0 / 22510343858157.0), float(1772645290293.0 / 4653164025191.0),
+    float(-1672844663538.0 / 4480602732383.0), float(2114624349019.0 / 3568978502595.0),
+    float(5198255086312.0 / 14908931495163.0)};
+static __constant__ float c_rk45_ef[5] = {
+    float(1153189308089.0 / 22510343858157.0 - 1016888040809.0 / 7410784769900.0),
+    float(1772645290293.0 / 4653164025191.0 - 11231460423587.0 / 58533540763752.0),
+    float(-1672844663538.0 / 4480602732383.0 + 1563879915014.0 / 6823010717585.0),
+    float(2114624349019.0 / 3568978502595.0 - 606302364029.0 / 971179775848.0),
+    float(5198255086312.0 / 14908931495163.0 - 1097981568119.0 / 3980877426909.0)};
 
 __device__ __forceinline__ void decode_fp(int32_t code, const TypeTab& tt,
                                           int* t, long long* e, int* f) {

@@ -6,6 +6,7 @@
 
 #include <string>
 
+#include "fr_convert.cuh"
 #include "fr_err.hpp"
 
 using namespace frgb;
@@ -62,7 +63,76 @@ int run_probe(int device, long long iters, double* ms, double* flops) {
   return FR_OK;
 }
 
+// splitmix64 (Steele, Lea & Flood 2014): the test patterns of the
+// conversion check, one counter per pattern.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z += 0x9e3779b97f4a7c15ull;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+// Pattern i: a random 32-bit float pattern for widening, and a 64-bit double
+// pattern for narrowing drawn from one of four classes: any bits, exponents
+// near the float range (with random sign and fraction), exact ties of the
+// dropped 29 bits, and all-ones fractions at the top and bottom exponents
+// (carries into the exponent and out of the range).
+__global__ void k_convert_check(unsigned long long seed, long long n,
+                                unsigned long long* bad) {
+  unsigned long long nb = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long r = mix64(seed ^ mix64((unsigned long long)i));
+    const unsigned long long q = mix64(r);
+    const float f = __uint_as_float(uint32_t(r));
+    const double w0 = double(f), w1 = widen_f32(f);
+    const bool wnan = w0 != w0;
+    if (wnan ? (w1 == w1) : (__double_as_longlong(w0) != __double_as_longlong(w1))) ++nb;
+    unsigned long long d = q;
+    const unsigned long long sign = q & 0x8000000000000000ull;
+    const unsigned long long frac = q & 0xfffffffffffffull;
+    switch (int(r >> 62)) {
+      case 0: break;
+      case 1: d = sign | ((unsigned long long)(860 + (r >> 32) % 330) << 52) | frac; break;
+      case 2:
+        d = sign | ((unsigned long long)(890 + (r >> 32) % 270) << 52) |
+            (frac & ~0x1fffffffull) | 0x10000000ull;
+        break;
+      default: {
+        const int k = int((r >> 32) % 6);  // exponents 895-897 and 1149-1151
+        d = sign | ((unsigned long long)(k < 3 ? 895 + k : 1146 + k) << 52) |
+            ((r >> 40) & 1 ? 0xfffffffffffffull : (frac | 0xfffffe0000000ull));
+      }
+    }
+    const double dv = __longlong_as_double((long long)d);
+    const float n0 = __double2float_rn(dv), n1 = narrow_f64(dv);
+    const bool nnan = n0 != n0;
+    if (nnan ? (n1 == n1) : (__float_as_uint(n0) != __float_as_uint(n1))) ++nb;
+  }
+  if (nb) atomicAdd(bad, nb);
+}
+
 }  // namespace
+
+extern "C" int fr_check_conversions(int device, uint64_t seed, int64_t n,
+                                    int64_t* mismatches) {
+  if (!mismatches) return fail(FR_EINVAL, "null argument");
+  if (n < 0) return fail(FR_EINVAL, "n must not be negative");
+  CK(cudaSetDevice(device));
+  unsigned long long* bad = nullptr;
+  CK(cudaMalloc(&bad, sizeof(unsigned long long)));
+  unsigned long long h = 0;
+  cudaError_t err = cudaMemset(bad, 0, sizeof(h));
+  if (err == cudaSuccess && n > 0) {
+    k_convert_check<<<1024, 256>>>(seed, n, bad);
+    err = cudaGetLastError();
+  }
+  if (err == cudaSuccess) err = cudaMemcpy(&h, bad, sizeof(h), cudaMemcpyDeviceToHost);
+  cudaFree(bad);
+  if (err != cudaSuccess) return fail(FR_ECUDA, std::string("conversion check: ") + cudaGetErrorString(err));
+  *mismatches = int64_t(h);
+  return FR_OK;
+}
 
 extern "C" int fr_probe_fma(int device, int dtype, int64_t iters, double* ms,
                             double* flops) {
