@@ -14,9 +14,11 @@
 //   margin g(zeta) = min((rho-1e-8)/rho_mean, (p-1e-8)/p_mean,
 //   (s - s_min + 1e-8 s_min)/s_min), evaluated in FP64;
 //   zeta* = the smallest feasible strength, by a bracketed Illinois
-//   iteration (relative tolerance 1e-6, at most 24 evaluations) started
-//   from [0, 36] or from a predicted guess z0 (bracket opened at z0, then
-//   z0 / r or r z0 with r = 1.25 by default, then halving / doubling).
+//   iteration (ended when the feasible end's margin is at most the entropy
+//   tolerance below, or at relative width 1e-6, or after 24 evaluations)
+//   started from [0, 36] or from a predicted guess z0 (bracket opened at
+//   z0, then z0 / r or r z0 with r = 1.25 by default, then halving /
+//   doubling).
 //   The entropy tolerance is 1e-8 for FP64 stage values and 2^-20 for FP32
 //   ones (1e-8 is below FP32 resolution, where the decision would be made
 //   by rounding noise).
@@ -500,7 +502,8 @@ __global__ void __launch_bounds__(kFilterThreads)
   enum { kPlainHi = 0, kGuess = 1, kDown = 2, kUp = 3, kIllinois = 4, kDone = 5 };
   __shared__ double s_next;
   __shared__ int s_go;
-  double lo = 0.0, glo = g0, hi = kZetaMax, ghi = 0.0, result = 0.0, zc = 0.0;
+  // ghr: the margin at hi (ghi is halved by the Illinois rule)
+  double lo = 0.0, glo = g0, hi = kZetaMax, ghi = 0.0, ghr = 0.0, result = 0.0, zc = 0.0;
   int evals = 1, state = kPlainHi, it = 0, side = 0;
   bool fallback = false, use_guess = false;
   if (fa.mlp) {
@@ -516,9 +519,10 @@ __global__ void __launch_bounds__(kFilterThreads)
     }
   }
   if (state == kPlainHi) zc = kZetaMax;
-  // next Illinois point, or kDone when the bracket is tight / evals spent
+  // next Illinois point, or kDone when the feasible end's margin is within
+  // tau, the bracket is tight or the evaluations are spent
   auto illinois_next = [&]() {
-    if (!(hi - lo > kRelTol * hi && evals < kMaxEvals)) {
+    if (!(ghr > fa.tau && hi - lo > kRelTol * hi && evals < kMaxEvals)) {
       state = kDone;
       result = hi;
       return;
@@ -541,7 +545,7 @@ __global__ void __launch_bounds__(kFilterThreads)
     ++evals;
     switch (state) {
       case kPlainHi:
-        ghi = gz;
+        ghi = ghr = gz;
         if (gz < 0.0) {
           state = kDone;
           fallback = true;
@@ -554,9 +558,13 @@ __global__ void __launch_bounds__(kFilterThreads)
       case kGuess:
         if (gz >= 0.0) {
           hi = z;
-          ghi = gz;
+          ghi = ghr = gz;
           state = kDown;
           zc = z / fa.ratio;
+          if (gz <= fa.tau) {
+            state = kDone;
+            result = hi;
+          }
         } else {
           lo = z;
           glo = gz;
@@ -573,8 +581,8 @@ __global__ void __launch_bounds__(kFilterThreads)
           illinois_next();
         } else {
           hi = z;
-          ghi = gz;
-          if (z < 1e-6) {
+          ghi = ghr = gz;
+          if (z < 1e-6 || gz <= fa.tau) {
             state = kDone;
             result = hi;
           } else {
@@ -590,7 +598,7 @@ __global__ void __launch_bounds__(kFilterThreads)
       case kUp:  // double until the margin is non-negative
         if (gz >= 0.0) {
           hi = z;
-          ghi = gz;
+          ghi = ghr = gz;
           state = kIllinois;
           illinois_next();
         } else {
@@ -613,7 +621,7 @@ __global__ void __launch_bounds__(kFilterThreads)
       case kIllinois:
         if (gz >= 0.0) {
           hi = z;
-          ghi = gz;
+          ghi = ghr = gz;
           if (side == 1) glo *= 0.5;
           side = 1;
         } else {

@@ -103,14 +103,16 @@ def test_filter_fp32_single_application_same_elements_and_strengths():
     tolerance 2^-20.  Elements whose oracle margin at zeta = 0 is within
     1e-5 of the threshold may flip with the FP32 rounding of the filtered
     values; every other element is filtered on both sides or on neither.
-    The GPU's strength must be the oracle's smallest feasible strength up to
-    the FP32 rounding of the margin: the oracle margin at the GPU's zeta is
-    within 4 * 2^-20 of zero.  The strengths themselves are compared where
-    the margin is steep (zeta* < 2: a 1 % change of zeta moves the margin by
-    1e-5 or more there) to 2e-3 relative.  Where it is flat (large zeta*:
-    sigma_k = exp(-zeta (d_k/p)^2) and so the filtered state barely depend
-    on zeta) FP32 rounding of ~1e-6 in the margin moves zeta* by a percent
-    or more, and only the margin check applies."""
+    Both searches end at a feasible strength whose margin is at most the
+    tolerance 2^-20 (or at a tight bracket); the GPU evaluates its margin
+    from FP32 filtered values, ~1e-6 of rounding.  So the oracle margin at
+    the GPU's zeta lies in [-4, 5] x 2^-20.  The strengths themselves are
+    compared where the margin is steep (zeta* < 2: a 1 % change of zeta
+    moves the margin by 1e-5 or more there, so 5 x 2^-20 is < 0.5 %) to
+    1e-2 relative.  Where it is flat (large zeta*: sigma_k = exp(-zeta
+    (d_k/p)^2) and so the filtered state barely depend on zeta) FP32
+    rounding of ~1e-6 in the margin moves zeta* by a percent or more, and
+    only the margin check applies."""
     o, s, g = _strip(64, precision="fp32")
     u0 = oracle_state(o, ics.shu_osher)
     smin = EF.element_smin(s, u0)
@@ -143,10 +145,10 @@ def test_filter_fp32_single_application_same_elements_and_strengths():
     both = clear & (zo > 0) & (zg > 0) & (zo < EF.ZETA_MAX)
     steep = both & (zo < 2.0)
     assert np.sum(steep) > 20
-    assert np.all(np.abs(zg[steep] - zo[steep]) <= 2e-3 * zo[steep])
+    assert np.all(np.abs(zg[steep] - zo[steep]) <= 1e-2 * zo[steep])
     for e in np.nonzero(both)[0]:
         ge = margin_at(e, float(zg[e]))
-        assert abs(ge) <= 4 * 2.0 ** -20, (e, zg[e], zo[e], ge)
+        assert -4 * 2.0 ** -20 <= ge <= 5 * 2.0 ** -20, (e, zg[e], zo[e], ge)
 
 
 def test_unfiltered_run_blows_up_filtered_run_does_not():
@@ -194,9 +196,11 @@ def _violating_state(g, dt, steps):
 def test_learned_start_guess_cuts_root_find_work():
     """Samples from plain root-finds train the predictor on the GPU (own
     forward / backward / Adam kernels); on the same violating states the
-    predicted start needs fewer margin evaluations and finds the same
-    strengths as the plain bracket, and the GPU agrees with the oracle
-    driven by the same BF16-rounded predictor."""
+    predicted start needs fewer margin evaluations, the two searches end at
+    strengths whose filtered states agree to 1e-5 (both stop where the
+    margin is within tau of the bound, not necessarily at the same zeta),
+    and the GPU agrees with the oracle driven by the same BF16-rounded
+    predictor."""
     o, s, g = _strip(128)
     dt = 1e-3
     g.set_solution(lib_state(g, ics.shu_osher))
@@ -220,7 +224,12 @@ def test_learned_start_guess_cuts_root_find_work():
     theta = np.concatenate([theta, [ratio]]).astype(np.float32)
     base = g.get_solution()
     smin = EF.element_smin(s, base)
-    tot_plain = tot_mlp = same = common = 0
+    op = EF.FilterOperators(o.el["hex"])
+
+    def state_at(state, e, zeta):
+        """The oracle's filtered state of element e at strength zeta."""
+        return op.evaluate(op.Vinv @ state["hex"][e], zeta)[0]
+    tot_plain = tot_mlp = same = common = n_filt = 0
     for k in range(5):
         g.set_solution(base)
         bad = _violating_state(g, dt, 1 + k)
@@ -236,16 +245,24 @@ def test_learned_start_guess_cuts_root_find_work():
         on = (z_plain > 0) & (z_mlp > 0)
         tot_plain += int(e_plain[z_plain > 0].sum())
         tot_mlp += int(e_mlp[z_mlp > 0].sum())
+        n_filt += int((z_mlp > 0).sum())
         common += int(on.sum())
-        same += int(np.sum(np.abs(z_mlp[on] - z_plain[on])
-                           <= 2e-6 * z_plain[on]))
+        for e in np.nonzero(on)[0]:
+            up = state_at(bad, e, float(z_plain[e]))
+            um = state_at(bad, e, float(z_mlp[e]))
+            same += int(np.linalg.norm(um - up) <= 1e-5 * np.linalg.norm(up))
         print("state", k, "filtered", int((z_plain > 0).sum()),
               "evals plain", int(e_plain[z_plain > 0].sum()),
               "with predictor", int(e_mlp[z_mlp > 0].sum()))
-    assert common > 0 and same >= 0.9 * common
-    # observed savings 11-21% over repeated runs (the samples, hence the
-    # trained predictor, change with the trajectory)
-    assert tot_mlp < 0.92 * tot_plain, (tot_plain, tot_mlp)
+    assert common > 0 and same == common
+    print("evaluations per filtered element: plain", tot_plain / n_filt,
+          "with predictor", tot_mlp / n_filt)
+    # A start guess with a log-normal error of about the predictor's rms
+    # (0.3) saves 20-30 % of the evaluations of the search from [0, 36] on
+    # recorded margins of this problem (the FP64 oracle search replayed on
+    # 1886 filtered elements); 6.4 against 8.75 per element observed.
+    assert tot_mlp < 0.85 * tot_plain, (tot_plain, tot_mlp)
+    assert tot_mlp <= 8 * n_filt, (tot_mlp, n_filt)
     # the oracle with the same BF16 predictor on the last violating state
     th = theta[:mlp.NPARAM].astype(np.float64).copy()
     th[:mlp.NTRAIN] = _bf16(theta[:mlp.NTRAIN])
@@ -256,5 +273,10 @@ def test_learned_start_guess_cuts_root_find_work():
                                   ratio=ratio)
     zo = zo["hex"]
     assert np.array_equal(zo > 0, z_mlp > 0)
-    on = zo > 0
-    assert np.sum(np.abs(z_mlp[on] - zo[on]) <= 2e-6 * zo[on]) >= 0.9 * on.sum()
+    # the GPU forms the guess in FP32, the oracle in FP64 from the same BF16
+    # weights: the searches can take different paths and stop at different
+    # points within tau of the bound; the filtered states agree
+    for e in np.nonzero(zo > 0)[0]:
+        ug = state_at(bad, e, float(z_mlp[e]))
+        uo = state_at(bad, e, float(zo[e]))
+        assert np.linalg.norm(ug - uo) <= 1e-5 * np.linalg.norm(uo), e
