@@ -223,9 +223,9 @@ __device__ __forceinline__ void hex_stage_update(const HexStage<T, TR>& a,
 }
 
 // interpolate smem field src[v][pt] to face point fp (5 variables)
-template <typename T, int N, int NV>
-__device__ __forceinline__ void face_interp(const T* src, int fp,
-                                            const HexOps<T>& op, T out[NV]) {
+template <typename T, int N, int NV, typename Ops>
+__device__ __forceinline__ void face_interp(const T* src, int fp, const Ops& op,
+                                            T out[NV]) {
   const int NF1 = N * N;
   int face = fp / NF1, r = fp - face * NF1;
   int i = r % N, j = r / N;
@@ -247,6 +247,38 @@ __device__ __forceinline__ void face_interp(const T* src, int fp,
   }
 }
 
+// Both faces of direction dir at face position (i, j): their flux points
+// lie on the same line of solution points, so one pass over the line's N
+// points (shared-memory reads) gives both values (o0: minus face, o1: plus
+// face) with the weights l_m(-1), l_m(+1).
+template <typename T, int N, int NV, typename Ops>
+__device__ __forceinline__ void face_interp_pair(const T* src, int dir, int i, int j,
+                                                 const Ops& op, T o0[NV], T o1[NV]) {
+  constexpr int NU = N * N * N;
+  if (op.gather) {  // Gauss-Lobatto: the line's end points
+    const int q0 = line_pt<N>(2 * dir, i, j, 0), q1 = line_pt<N>(2 * dir, i, j, N - 1);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      o0[k] = src[k * NU + q0];
+      o1[k] = src[k * NU + q1];
+    }
+    return;
+  }
+#pragma unroll
+  for (int k = 0; k < NV; ++k) o0[k] = o1[k] = T(0);
+#pragma unroll
+  for (int m = 0; m < N; ++m) {
+    const int q = line_pt<N>(2 * dir, i, j, m);
+    const T cm = op.lm[m], cp = op.lp[m];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      const T v = src[k * NU + q];
+      o0[k] += cm * v;
+      o1[k] += cp * v;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // NS gradients on hexahedra: corrected reference gradient, physical gradient
 // at solution points, and its value at the flux points.
@@ -260,8 +292,10 @@ __host__ __device__ constexpr int hex_grad_bytes_per_elem() {
   return ((20 * N * N * N + (QV ? 78 : 30) * N * N) * int(sizeof(T)) + 15) / 16 * 16;
 }
 
+// The q form (FP32 values) is bounded to 64 registers at 250 threads so that
+// four CTAs fit on an SM (a few bytes spill; measured faster than three).
 template <typename T, typename TR, int N, int EPB, bool QV>
-__global__ void __launch_bounds__(EPB* N* N* N)
+__global__ void __launch_bounds__(EPB* N* N* N, (QV && EPB * N * N * N >= 250 ? 4 : 1))
     k_hex_grad(long long ne, const T* __restrict__ uin, const TR* __restrict__ X,
                const T* __restrict__ du, const T* __restrict__ smat,
                const T* __restrict__ rcpdjac, HexOps<T> op,
@@ -342,9 +376,8 @@ __global__ void __launch_bounds__(EPB* N* N* N)
   }
   __syncthreads();
   if (e >= ne) return;
-  for (int f = z; f < NF; f += NU) {
-    T g[15];
-    face_interp<T, N, 15>(gs, f, op, g);
+  // flux point f with its interpolated gradient g: q (q form) or g itself
+  auto out = [&](int f, const T* g) {
     if (QV) {
       T u[5], G[3][5], nv[3], q[5];
 #pragma unroll
@@ -362,6 +395,23 @@ __global__ void __launch_bounds__(EPB* N* N* N)
     } else {
 #pragma unroll
       for (int k = 0; k < 15; ++k) va.q[(e * 15 + k) * NF + f] = g[k];
+    }
+  };
+  if constexpr (sizeof(T) == 4) {
+    // shared-memory bound: one thread per face pair (direction, position)
+    for (int t = z; t < 3 * N * N; t += NU) {
+      const int dir = t / (N * N), r = t - dir * N * N, i = r % N, j = r / N;
+      T g0[15], g1[15];
+      face_interp_pair<T, N, 15>(gs, dir, i, j, op, g0, g1);
+      out(fp_of<N>(2 * dir, i, j), g0);
+      out(fp_of<N>(2 * dir + 1, i, j), g1);
+    }
+  } else {
+    // FP64-pipe bound: one thread per flux point spreads the arithmetic
+    for (int f = z; f < NF; f += NU) {
+      T g[15];
+      face_interp<T, N, 15>(gs, f, op, g);
+      out(f, g);
     }
   }
 }
@@ -450,15 +500,31 @@ __global__ void __launch_bounds__(EPB* N* N* N)
   cp_async_wait_all();
   __syncthreads();
   if (e < ne) {
-    // jump at every flux point: F^C - n~ . M0 f~ (only the normal direction)
-    for (int f = z; f < NF; f += NU) {
-      int face = f / N2;
-      int dir = face >> 1;
-      T fn[5];
-      face_interp<T, N, 5>(ft + dir * 5 * NU, f, op, fn);
-      T sgn = (face & 1) ? T(1) : T(-1);
+    // jump at every flux point: F^C - n~ . M0 f~ (only the normal direction,
+    // -e_dir on the minus face, +e_dir on the plus face); FP32: per face
+    // pair (fewer shared reads), FP64: per flux point
+    if constexpr (sizeof(T) == 4) {
+      for (int t = z; t < 3 * N2; t += NU) {
+        const int dir = t / N2, r = t - dir * N2, i = r % N, j = r / N;
+        T f0[5], f1[5];
+        face_interp_pair<T, N, 5>(ft + dir * 5 * NU, dir, i, j, op, f0, f1);
+        const int fm = fp_of<N>(2 * dir, i, j), fp = fp_of<N>(2 * dir + 1, i, j);
 #pragma unroll
-      for (int k = 0; k < 5; ++k) jm[k * NF + f] = jm[k * NF + f] - sgn * fn[k];
+        for (int k = 0; k < 5; ++k) {
+          jm[k * NF + fm] = jm[k * NF + fm] + f0[k];
+          jm[k * NF + fp] = jm[k * NF + fp] - f1[k];
+        }
+      }
+    } else {
+      for (int f = z; f < NF; f += NU) {
+        int face = f / N2;
+        int dir = face >> 1;
+        T fn[5];
+        face_interp<T, N, 5>(ft + dir * 5 * NU, f, op, fn);
+        T sgn = (face & 1) ? T(1) : T(-1);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) jm[k * NF + f] = jm[k * NF + f] - sgn * fn[k];
+      }
     }
   }
   __syncthreads();
@@ -513,11 +579,25 @@ __global__ void __launch_bounds__(EPB* N* N* N)
   }
   __syncthreads();
   if (e >= ne) return;
-  for (int f = z; f < NF; f += NU) {
-    T v[5];
-    face_interp<T, N, 5>(ft, f, op, v);
+  if constexpr (sizeof(T) == 4) {
+    for (int t = z; t < 3 * N2; t += NU) {
+      const int dir = t / N2, r = t - dir * N2, i = r % N, j = r / N;
+      T v0[5], v1[5];
+      face_interp_pair<T, N, 5>(ft, dir, i, j, op, v0, v1);
+      const int fm = fp_of<N>(2 * dir, i, j), fp = fp_of<N>(2 * dir + 1, i, j);
 #pragma unroll
-    for (int k = 0; k < 5; ++k) sa.uf_next[(e * 5 + k) * NF + f] = v[k];
+      for (int k = 0; k < 5; ++k) {
+        sa.uf_next[(e * 5 + k) * NF + fm] = v0[k];
+        sa.uf_next[(e * 5 + k) * NF + fp] = v1[k];
+      }
+    }
+  } else {
+    for (int f = z; f < NF; f += NU) {
+      T v[5];
+      face_interp<T, N, 5>(ft, f, op, v);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) sa.uf_next[(e * 5 + k) * NF + f] = v[k];
+    }
   }
 }
 
@@ -608,10 +688,9 @@ __device__ __forceinline__ void hex_fpt_ref(const HexOps<T>& op, const T* x1,
 
 // corrected reference gradient at (a, b, c) from u (smem [5][NU]) and the
 // flux-point jumps du (smem [5][NF])
-template <typename T, int N>
-__device__ __forceinline__ void hex_ref_grad(const T* us, const T* ds,
-                                             const HexOps<T>& op, int a, int b,
-                                             int c, T gref[3][5]) {
+template <typename T, int N, typename Ops>
+__device__ __forceinline__ void hex_ref_grad(const T* us, const T* ds, const Ops& op,
+                                             int a, int b, int c, T gref[3][5]) {
   constexpr int NU = N * N * N, NF = 6 * N * N, N2 = N * N;
   T da[N], db[N], dc[N];
 #pragma unroll
@@ -640,32 +719,61 @@ __device__ __forceinline__ void hex_ref_grad(const T* us, const T* ds,
   }
 }
 
+// Shared memory per element of the vertex-metric kernels (16-byte padded).
+// Gradient: u [5][NU], du [5][NF], traces [5][NF], physical gradient
+// [15][NU], vertices [24].  Volume: f~ [3][5][NU], F^C / jump [5][NF],
+// u [5][NU], du [5][NF], vertices [24] (type T), then the
+// RK registers X, A [5][NU] (type TR).
+template <typename T, int N>
+__host__ __device__ constexpr int hexv_grad_bytes_per_elem() {
+  return ((20 * N * N * N + 60 * N * N + 24) * int(sizeof(T)) + 15) / 16 * 16;
+}
+
+template <typename T, int N>
+__host__ __device__ constexpr int hexv_vol_tbytes() {
+  return ((20 * N * N * N + 60 * N * N + 24) * int(sizeof(T)) + 15) / 16 * 16;
+}
+
+template <typename T, typename TR, int N>
+__host__ __device__ constexpr int hexv_vol_bytes_per_elem() {
+  return hexv_vol_tbytes<T, N>() + (10 * N * N * N * int(sizeof(TR)) + 15) / 16 * 16;
+}
+
 // NS gradients (FP32 values): vertex metrics, viscous flux at the flux
-// points; nothing is stored at the solution points.
+// points; nothing is stored at the solution points.  Every per-element
+// input arrives by cp.async (the boundary tags of the thread's flux points
+// and the vertices by plain loads).
 template <typename T, typename TR, int N, int EPB>
 __global__ void __launch_bounds__(EPB* N* N* N)
     k_hex_grad_v(long long ne, const T* __restrict__ uin, const TR* __restrict__ X,
                  const T* __restrict__ du, const T* __restrict__ verts,
                  HexOps<T> op, ViscArgs<T> va, BCTab<T> bc, Phys<T> ph) {
-  constexpr int NU = N * N * N, NF = 6 * N * N;
-  extern __shared__ unsigned char smem_raw[];
-  T* sm = reinterpret_cast<T*>(smem_raw);
+  constexpr int NU = N * N * N, NF = 6 * N * N, NFT = (NF + NU - 1) / NU;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int le = threadIdx.x / NU, z = threadIdx.x - le * NU;
   const long long e = (long long)blockIdx.x * (blockDim.x / NU) + le;
-  T* us = sm + le * (5 * NU + 5 * NF + 15 * NU + 24);
+  T* us = reinterpret_cast<T*>(smem_raw + le * hexv_grad_bytes_per_elem<T, N>());
   T* ds = us + 5 * NU;
-  T* gs = ds + 5 * NF;
-  T* xv = gs + 15 * NU;
+  T* ufs = ds + 5 * NF;
+  T* gs = ufs + 5 * NF;
+  T* xv = gs + 15 * NU;  // the 24 vertex coordinates (relative to vertex 0)
   const int a = z % N, b = (z / N) % N, c = z / (N * N);
+  int fb[NFT];
   if (e < ne) {
+    if (uin) {
+      async_copy(us, uin + e * 5 * NU, 5 * NU * int(sizeof(T)), z, NU);
+    } else {
 #pragma unroll
-    for (int k = 0; k < 5; ++k)
-      us[k * NU + z] = uin ? uin[(e * 5 + k) * NU + z] : T(X[(e * 5 + k) * NU + z]);
-    for (int f = z; f < NF; f += NU)
+      for (int k = 0; k < 5; ++k) us[k * NU + z] = T(X[(e * 5 + k) * NU + z]);
+    }
+    async_copy(ds, du + e * 5 * NF, 5 * NF * int(sizeof(T)), z, NU);
+    async_copy(ufs, va.uf + e * 5 * NF, 5 * NF * int(sizeof(T)), z, NU);
 #pragma unroll
-      for (int k = 0; k < 5; ++k) ds[k * NF + f] = du[(e * 5 + k) * NF + f];
+    for (int i = 0; i < NFT; ++i)
+      fb[i] = z + i * NU < NF ? int(va.fbc[e * NF + z + i * NU]) : -1;
     if (z < 24) xv[z] = verts[e * 24 + z];
   }
+  cp_async_wait_all();
   __syncthreads();
   if (e < ne) {
     T gref[3][5];
@@ -682,26 +790,31 @@ __global__ void __launch_bounds__(EPB* N* N* N)
   }
   __syncthreads();
   if (e >= ne) return;
-  for (int f = z; f < NF; f += NU) {
+#pragma unroll
+  for (int i = 0; i < NFT; ++i) {
+    const int f = z + i * NU;
+    if (f >= NF) break;
     T g[15];
     face_interp<T, N, 15>(gs, f, op, g);
     // S^T n~ at the flux point from the vertex map
-    T xr[3], nr[3], S[3][3], det;
+    T xr[3], nr[3], nv[3];
     hex_fpt_ref<T, N>(op, op.xg, f, xr, nr);
-    hex_metric_at(xv, xr[0], xr[1], xr[2], S, &det);
-    T nv[3];
+    {
+      T S[3][3], det;
+      hex_metric_at(xv, xr[0], xr[1], xr[2], S, &det);
 #pragma unroll
-    for (int j = 0; j < 3; ++j) nv[j] = S[0][j] * nr[0] + S[1][j] * nr[1] + S[2][j] * nr[2];
+      for (int j = 0; j < 3; ++j) nv[j] = S[0][j] * nr[0] + S[1][j] * nr[1] + S[2][j] * nr[2];
+    }
     T u[5], G[3][5];
 #pragma unroll
-    for (int k = 0; k < 5; ++k) u[k] = va.uf[(e * 5 + k) * NF + f];
+    for (int k = 0; k < 5; ++k) u[k] = ufs[k * NF + f];
 #pragma unroll
     for (int j = 0; j < 3; ++j)
 #pragma unroll
       for (int k = 0; k < 5; ++k) G[j][k] = g[j * 5 + k];
     T q[5] = {0, 0, 0, 0, 0};
     viscous_normal_acc(u, G, nv, ph, T(1), q);
-    const int bb = va.fbc[e * NF + f];
+    const int bb = fb[i];
     if (bb >= 0 && bc.kind[bb] != 2) {  // exchange points keep the inside q
       T ur[5], q2[5] = {0, 0, 0, 0, 0};
       const T* pre = prescribed_at(va, e, f, NF);
@@ -722,36 +835,42 @@ __global__ void __launch_bounds__(EPB* N* N* N)
 }
 
 // Volume kernel (FP32 values): vertex metrics; for NS the corrected
-// gradient is recomputed from u and du.
+// gradient is recomputed from u and du.  F^C, du and the RK registers
+// arrive by cp.async while u and the vertices are loaded.
 template <typename T, typename TR, int N, int EPB, bool NS>
 __global__ void __launch_bounds__(EPB* N* N* N)
     k_hex_vol_v(long long ne, const T* __restrict__ uin, const T* __restrict__ du,
                 const T* __restrict__ fc, const T* __restrict__ verts,
                 HexOps<T> op, Phys<T> ph, HexStage<T, TR> sa) {
   constexpr int NU = N * N * N, NF = 6 * N * N, N2 = N * N;
-  extern __shared__ unsigned char smem_raw[];
-  T* sm = reinterpret_cast<T*>(smem_raw);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int le = threadIdx.x / NU, z = threadIdx.x - le * NU;
   const long long e = (long long)blockIdx.x * (blockDim.x / NU) + le;
-  T* ft = sm + le * (15 * NU + 5 * NF + 5 * NU + 5 * NF + 24);
-  T* jm = ft + 15 * NU;
+  unsigned char* eb = smem_raw + le * hexv_vol_bytes_per_elem<T, TR, N>();
+  T* ft = reinterpret_cast<T*>(eb);  // [3][5][NU]
+  T* jm = ft + 15 * NU;              // [5][NF]: F^C, then the jump
   T* us = jm + 5 * NF;
   T* ds = us + 5 * NU;
-  T* xv = ds + 5 * NF;
+  T* xv = ds + 5 * NF;  // the 24 vertex coordinates (relative to vertex 0)
+  TR* xs = reinterpret_cast<TR*>(eb + hexv_vol_tbytes<T, N>());  // [5][NU]
+  TR* as = xs + 5 * NU;                                          // [5][NU]
   const int a = z % N, b = (z / N) % N, c = z / N2;
+  bool nx, na;
+  hex_stage_needs(sa, &nx, &na);
   T uz[5];
   if (e < ne) {
+    async_copy(jm, fc + e * 5 * NF, 5 * NF * int(sizeof(T)), z, NU);
+    if (NS) async_copy(ds, du + e * 5 * NF, 5 * NF * int(sizeof(T)), z, NU);
+    if (nx) async_copy(xs, sa.X + e * 5 * NU, 5 * NU * int(sizeof(TR)), z, NU);
+    if (na) async_copy(as, sa.A + e * 5 * NU, 5 * NU * int(sizeof(TR)), z, NU);
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
       uz[k] = uin ? uin[(e * 5 + k) * NU + z] : T(sa.X[(e * 5 + k) * NU + z]);
       us[k * NU + z] = uz[k];
     }
-    if (NS)
-      for (int f = z; f < NF; f += NU)
-#pragma unroll
-        for (int k = 0; k < 5; ++k) ds[k * NF + f] = du[(e * 5 + k) * NF + f];
     if (z < 24) xv[z] = verts[e * 24 + z];
   }
+  cp_async_wait_all();
   __syncthreads();
   T rj = T(0);
   if (e < ne) {
@@ -786,7 +905,7 @@ __global__ void __launch_bounds__(EPB* N* N* N)
       face_interp<T, N, 5>(ft + dir * 5 * NU, f, op, fn);
       T sgn = (face & 1) ? T(1) : T(-1);
 #pragma unroll
-      for (int k = 0; k < 5; ++k) jm[k * NF + f] = fc[(e * 5 + k) * NF + f] - sgn * fn[k];
+      for (int k = 0; k < 5; ++k) jm[k * NF + f] = jm[k * NF + f] - sgn * fn[k];
     }
   }
   __syncthreads();
@@ -820,7 +939,13 @@ __global__ void __launch_bounds__(EPB* N* N* N)
       dv += glc * jk[fp_of<N>(4, a, b)] + grc * jk[fp_of<N>(5, a, b)];
       R[k] = -dv * rj;
     }
-    hex_stage_update(sa, e * 5 * NU + z, NU, uz, R, s);
+    TR xr[5], ar[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      xr[k] = nx ? xs[k * NU + z] : TR(0);
+      ar[k] = na ? as[k * NU + z] : TR(0);
+    }
+    hex_stage_apply(sa, e * 5 * NU + z, NU, uz, R, xr, ar, s);
   }
   if (sa.uf_next == nullptr) return;
   __syncthreads();

@@ -70,13 +70,13 @@ constexpr int dense_epb() {
 template <typename T, int NU, int NF>
 constexpr size_t dense_grad_smem() {
   return (size_t(DenseLayout<T, NU, NF>::kStagedCount) +
-          size_t(dense_epb<NU>()) * (20 * NU + 5 * NF)) * sizeof(T);
+          size_t(dense_epb<NU>()) * size_t(DenseLayout<T, NU, NF>::kGradElem)) * sizeof(T);
 }
 
 template <typename T, int NU, int NF>
 constexpr size_t dense_vol_smem() {
   return (size_t(DenseLayout<T, NU, NF>::kStagedCount) +
-          size_t(dense_epb<NU>()) * (15 * NU + 5 * NF)) * sizeof(T);
+          size_t(dense_epb<NU>()) * size_t(DenseLayout<T, NU, NF>::kVolElem)) * sizeof(T);
 }
 
 struct DevType {
@@ -792,12 +792,12 @@ void launch_vol_tc(fr_mesh* m, const DevType& D, cudaStream_t s, bool from_x,
 // recomputed gradients)
 template <typename T, int N>
 constexpr size_t hexv_grad_smem() {
-  return size_t(hex_epb<N>()) * (20 * N * N * N + 30 * N * N + 24) * sizeof(T);
+  return size_t(hex_epb<N>()) * size_t(hexv_grad_bytes_per_elem<T, N>());
 }
 
-template <typename T, int N>
+template <typename T, typename TR, int N>
 constexpr size_t hexv_vol_smem() {
-  return size_t(hex_epb<N>()) * (20 * N * N * N + 60 * N * N + 24) * sizeof(T);
+  return size_t(hex_epb<N>()) * size_t(hexv_vol_bytes_per_elem<T, TR, N>());
 }
 
 // Opt in to > 48 KB of dynamic shared memory where a kernel needs it.  Runs
@@ -887,10 +887,10 @@ int prepare_kernels(fr_mesh* m) {
                            int(hexv_grad_smem<T, N>()));
       cudaFuncSetAttribute(k_hex_vol_v<T, TR, N, E, false>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           int(hexv_vol_smem<T, N>()));
+                           int(hexv_vol_smem<T, TR, N>()));
       cudaFuncSetAttribute(k_hex_vol_v<T, TR, N, E, true>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           int(hexv_vol_smem<T, N>()));
+                           int(hexv_vol_smem<T, TR, N>()));
     });
   }
   CK(cudaGetLastError());
@@ -1191,7 +1191,7 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
         const size_t sm = hex_vol_smem<T, TR, N>() / E * eb;
         const T* uin = from_x ? nullptr : (const T*)D.Y;
         if (sizeof(T) == 4 && D.verts && m->active == FR_VARIANT_SUMFACT_VERTEX) {
-          const size_t smv = hexv_vol_smem<T, N>() / E * eb;
+          const size_t smv = hexv_vol_smem<T, TR, N>() / E * eb;
           const T* dup = (const T*)m->du + D.off_f;
           if (ns)
             k_hex_vol_v<T, TR, N, E, true><<<nblk(D.ne, eb), eb * N * N * N, smv, s>>>(

@@ -619,12 +619,133 @@ __global__ void k_exchange_scatter(int n, const int32_t* __restrict__ list,
 // persistent: each CTA copies the type's operators into shared memory once
 // (when they fit) and then loops over groups of EPB elements.
 
+// one point's row of 5 / 15 values (16-byte aligned rows)
+template <typename T>
+__device__ __forceinline__ void lds_row5(const T* p, T v[5]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 a = *reinterpret_cast<const float4*>(p);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  } else {
+    const double2 a = *reinterpret_cast<const double2*>(p);
+    const double2 b = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  }
+  v[4] = p[4];
+}
+
+template <typename T>
+__device__ __forceinline__ void lds_row15(const T* p, T v[15]) {
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const float4 a = reinterpret_cast<const float4*>(p)[i];
+      v[4 * i] = a.x; v[4 * i + 1] = a.y; v[4 * i + 2] = a.z; v[4 * i + 3] = a.w;
+    }
+    const float4 a = reinterpret_cast<const float4*>(p)[3];
+    v[12] = a.x; v[13] = a.y; v[14] = a.z;
+  } else {
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+      const double2 a = reinterpret_cast<const double2*>(p)[i];
+      v[2 * i] = a.x; v[2 * i + 1] = a.y;
+    }
+    v[14] = p[14];
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void sts_row5(T* p, const T v[5]) {
+  if constexpr (sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+  }
+  p[4] = v[4];
+}
+
+template <typename T>
+__device__ __forceinline__ void sts_row15(T* p, const T v[15]) {
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      reinterpret_cast<float4*>(p)[i] =
+          make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+    reinterpret_cast<float4*>(p)[3] = make_float4(v[12], v[13], v[14], T(0));
+  } else {
+#pragma unroll
+    for (int i = 0; i < 7; ++i)
+      reinterpret_cast<double2*>(p)[i] = make_double2(v[2 * i], v[2 * i + 1]);
+    p[14] = v[14];
+  }
+}
+
+// Per-element working arrays of the dense kernels.  FP32 (kRows): one row
+// per point, the 5 variables of a point (row stride kP5 = 8) or its 15
+// transformed-flux / gradient components (stride 16); the inner loops read
+// a whole row with 128-bit shared loads (the same row for every thread of
+// the element: a broadcast) instead of one 32-bit load per component, which
+// relieves the shared-memory pipe that bounds the FP32 kernels.  FP64: one
+// column per component ([5][n], [15][n]); the FP64 kernels are bound by the
+// FP64 pipe and keep the skips of zero normal components.
 template <typename T, int NU, int NF>
 struct DenseLayout {
   static constexpr int kOps = 3 * NU * NU + 2 * NU * NF + 3 * NF;
   static constexpr bool kStaged = kOps * sizeof(T) <= 48 * 1024;
-  static constexpr int kStagedCount = kStaged ? kOps : 0;
+  static constexpr int kAlign = 16 / int(sizeof(T));
+  static constexpr int kStagedCount = kStaged ? (kOps + kAlign - 1) / kAlign * kAlign : 0;
+  static constexpr bool kRows = sizeof(T) == 4;
+  static constexpr int kP5 = 8;
+  static constexpr int kGradElem = kRows ? kP5 * NU + kP5 * NF + 16 * NU : 20 * NU + 5 * NF;
+  static constexpr int kVolElem = kRows ? 16 * NU + kP5 * NF : 15 * NU + 5 * NF;
+  // offsets of value (point q, component k) in a 5- / 15-component array
+  // over n points
+  template <int n>
+  __device__ static constexpr int at5(int q, int k) { return kRows ? q * kP5 + k : k * n + q; }
+  template <int n>
+  __device__ static constexpr int at15(int q, int c) { return kRows ? q * 16 + c : c * n + q; }
 };
+
+// the 5 / 15 values of point q (kRows: one row, vector loads)
+template <typename L, int n, typename T>
+__device__ __forceinline__ void get5(const T* a, int q, T v[5]) {
+  if constexpr (L::kRows) {
+    lds_row5(a + q * L::kP5, v);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) v[k] = a[k * n + q];
+  }
+}
+
+template <typename L, int n, typename T>
+__device__ __forceinline__ void put5(T* a, int q, const T v[5]) {
+  if constexpr (L::kRows) {
+    sts_row5(a + q * L::kP5, v);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) a[k * n + q] = v[k];
+  }
+}
+
+template <typename L, int n, typename T>
+__device__ __forceinline__ void get15(const T* a, int q, T v[15]) {
+  if constexpr (L::kRows) {
+    lds_row15(a + q * 16, v);
+  } else {
+#pragma unroll
+    for (int c = 0; c < 15; ++c) v[c] = a[c * n + q];
+  }
+}
+
+template <typename L, int n, typename T>
+__device__ __forceinline__ void put15(T* a, int q, const T v[15]) {
+  if constexpr (L::kRows) {
+    sts_row15(a + q * 16, v);
+  } else {
+#pragma unroll
+    for (int c = 0; c < 15; ++c) a[c * n + q] = v[c];
+  }
+}
 
 template <typename T, int NU, int NF>
 __device__ __forceinline__ DenseOps<T> stage_dense_ops(const DenseOps<T>& g,
@@ -654,24 +775,30 @@ __global__ void __launch_bounds__(EPB* NU)
                  const T* __restrict__ rcpdjac, DenseOps<T> gops,
                  T* __restrict__ grad, ViscArgs<T> va, BCTab<T> bc,
                  Phys<T> ph) {
-  extern __shared__ unsigned char smem_raw[];
+  using L = DenseLayout<T, NU, NF>;
+  constexpr int P5 = L::kP5;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   const DenseOps<T> ops = stage_dense_ops<T, NU, NF>(gops, sm);
-  T* buf = sm + DenseLayout<T, NU, NF>::kStagedCount;
+  T* buf = sm + L::kStagedCount;
   const int le = threadIdx.x / NU, z = threadIdx.x % NU;
-  T* us = buf + le * (5 * NU + 5 * NF + 15 * NU);
-  T* ds = us + 5 * NU;
-  T* gs = ds + 5 * NF;
+  T* us = buf + le * L::kGradElem;             // u at the solution points
+  T* ds = us + (L::kRows ? P5 * NU : 5 * NU);  // du at the flux points
+  T* gs = ds + (L::kRows ? P5 * NF : 5 * NF);  // physical gradient (15)
   const long long ngroups = (ne + EPB - 1) / EPB;
   for (long long grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
     const long long e = grp * EPB + le;
     const bool act = e < ne;
     if (act) {
+      T v[5];
 #pragma unroll
-      for (int k = 0; k < 5; ++k) us[k * NU + z] = u[(e * 5 + k) * NU + z];
-      for (int f = z; f < NF; f += NU)
+      for (int k = 0; k < 5; ++k) v[k] = u[(e * 5 + k) * NU + z];
+      put5<L, NU>(us, z, v);
+      for (int f = z; f < NF; f += NU) {
 #pragma unroll
-        for (int k = 0; k < 5; ++k) ds[k * NF + f] = du[(e * 5 + k) * NF + f];
+        for (int k = 0; k < 5; ++k) v[k] = du[(e * 5 + k) * NF + f];
+        put5<L, NF>(ds, f, v);
+      }
     }
     __syncthreads();
     if (act) {
@@ -681,21 +808,26 @@ __global__ void __launch_bounds__(EPB* NU)
 #pragma unroll
         for (int k = 0; k < 5; ++k) gref[d][k] = T(0);
       for (int q = 0; q < NU; ++q) {
+        T uq[5];
+        get5<L, NU>(us, q, uq);
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
           T w = ops.DT[(d * NU + q) * NU + z];
 #pragma unroll
-          for (int k = 0; k < 5; ++k) gref[d][k] += w * us[k * NU + q];
+          for (int k = 0; k < 5; ++k) gref[d][k] += w * uq[k];
         }
       }
       for (int f = 0; f < NF; ++f) {
-        T l = ops.LIFTT[f * NU + z];
+        const T l = ops.LIFTT[f * NU + z];
+        T dq[5];
+        get5<L, NF>(ds, f, dq);
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-          T w = l * ops.NREF[f * 3 + d];
-          if (w != T(0)) {
+          const T nd = ops.NREF[f * 3 + d];  // the same f on every thread
+          if (nd != T(0)) {
+            const T w = l * nd;
 #pragma unroll
-            for (int k = 0; k < 5; ++k) gref[d][k] += w * ds[k * NF + f];
+            for (int k = 0; k < 5; ++k) gref[d][k] += w * dq[k];
           }
         }
       }
@@ -703,15 +835,16 @@ __global__ void __launch_bounds__(EPB* NU)
 #pragma unroll
       for (int r = 0; r < 9; ++r) S[r / 3][r % 3] = smat[(e * 9 + r) * NU + z];
       T rj = rcpdjac[e * NU + z];
+      T gg[15];
 #pragma unroll
       for (int j = 0; j < 3; ++j)
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
-          T gg = rj * (S[0][j] * gref[0][k] + S[1][j] * gref[1][k] +
-                       S[2][j] * gref[2][k]);
-          grad[(e * 15 + j * 5 + k) * NU + z] = gg;
-          gs[(j * 5 + k) * NU + z] = gg;
+          gg[j * 5 + k] = rj * (S[0][j] * gref[0][k] + S[1][j] * gref[1][k] +
+                                S[2][j] * gref[2][k]);
+          grad[(e * 15 + j * 5 + k) * NU + z] = gg[j * 5 + k];
         }
+      put15<L, NU>(gs, z, gg);
     }
     __syncthreads();
     if (act) {
@@ -720,9 +853,11 @@ __global__ void __launch_bounds__(EPB* NU)
 #pragma unroll
         for (int c = 0; c < 15; ++c) acc[c] = T(0);
         for (int q = 0; q < NU; ++q) {
-          T m = ops.M0T[q * NF + f];
+          const T m = ops.M0T[q * NF + f];
+          T g[15];
+          get15<L, NU>(gs, q, g);
 #pragma unroll
-          for (int c = 0; c < 15; ++c) acc[c] += m * gs[c * NU + q];
+          for (int c = 0; c < 15; ++c) acc[c] += m * g[c];
         }
         if (QV) {
           write_visc_q(va, bc, ph, e, f, NF, acc);
@@ -749,13 +884,15 @@ __global__ void __launch_bounds__(EPB* NU)
                 const T* __restrict__ smat, const T* __restrict__ rcpdjac,
                 DenseOps<T> gops, Phys<T> ph, StageArgs<T> sa,
                 const T* __restrict__ tflux = nullptr) {
-  extern __shared__ unsigned char smem_raw[];
+  using L = DenseLayout<T, NU, NF>;
+  constexpr int P5 = L::kP5;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   const DenseOps<T> ops = stage_dense_ops<T, NU, NF>(gops, sm);
-  T* buf = sm + DenseLayout<T, NU, NF>::kStagedCount;
+  T* buf = sm + L::kStagedCount;
   const int le = threadIdx.x / NU, z = threadIdx.x % NU;
-  T* ft = buf + le * (15 * NU + 5 * NF);  // [3][5][NU]
-  T* jm = ft + 15 * NU;                   // [5][NF]
+  T* ft = buf + le * L::kVolElem;  // f~ (component d * 5 + k), then u_next
+  T* jm = ft + (L::kRows ? 16 * NU : 15 * NU);  // F^C - n~.f~ at the flux points
   const long long ngroups = (ne + EPB - 1) / EPB;
   for (long long grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
     const long long e = grp * EPB + le;
@@ -766,8 +903,10 @@ __global__ void __launch_bounds__(EPB* NU)
       for (int k = 0; k < 5; ++k) uz[k] = u[(e * 5 + k) * NU + z];
     }
     if (AA && act) {
+      T fv[15];
 #pragma unroll
-      for (int c = 0; c < 15; ++c) ft[c * NU + z] = tflux[(e * 15 + c) * NU + z];
+      for (int c = 0; c < 15; ++c) fv[c] = tflux[(e * 15 + c) * NU + z];
+      put15<L, NU>(ft, z, fv);
     } else if (act) {
       T F[3][5];
       euler_flux(uz, ph, F);
@@ -782,30 +921,42 @@ __global__ void __launch_bounds__(EPB* NU)
       T S[3][3];
 #pragma unroll
       for (int r = 0; r < 9; ++r) S[r / 3][r % 3] = smat[(e * 9 + r) * NU + z];
+      T fv[15];
 #pragma unroll
       for (int d = 0; d < 3; ++d)
 #pragma unroll
         for (int k = 0; k < 5; ++k)
-          ft[(d * 5 + k) * NU + z] =
-              S[d][0] * F[0][k] + S[d][1] * F[1][k] + S[d][2] * F[2][k];
+          fv[d * 5 + k] = S[d][0] * F[0][k] + S[d][1] * F[1][k] + S[d][2] * F[2][k];
+      put15<L, NU>(ft, z, fv);
     }
     __syncthreads();
     if (act) {
       for (int f = z; f < NF; f += NU) {
         T fn[5] = {0, 0, 0, 0, 0};
-        T nr[3] = {ops.NREF[f * 3], ops.NREF[f * 3 + 1], ops.NREF[f * 3 + 2]};
+        const T nr0 = ops.NREF[f * 3], nr1 = ops.NREF[f * 3 + 1], nr2 = ops.NREF[f * 3 + 2];
         for (int q = 0; q < NU; ++q) {
-          T m = ops.M0T[q * NF + f];
+          const T m = ops.M0T[q * NF + f];
+          if constexpr (L::kRows) {
+            T v[15];
+            lds_row15(ft + q * 16, v);
+            const T w0 = m * nr0, w1 = m * nr1, w2 = m * nr2;
 #pragma unroll
-          for (int d = 0; d < 3; ++d) {
-            if (nr[d] == T(0)) continue;
-            T w = m * nr[d];
+            for (int k = 0; k < 5; ++k) fn[k] += w0 * v[k] + w1 * v[5 + k] + w2 * v[10 + k];
+          } else {
+            const T nr[3] = {nr0, nr1, nr2};
 #pragma unroll
-            for (int k = 0; k < 5; ++k) fn[k] += w * ft[(d * 5 + k) * NU + q];
+            for (int d = 0; d < 3; ++d) {
+              if (nr[d] == T(0)) continue;
+              const T w = m * nr[d];
+#pragma unroll
+              for (int k = 0; k < 5; ++k) fn[k] += w * ft[(d * 5 + k) * NU + q];
+            }
           }
         }
+        T jv[5];
 #pragma unroll
-        for (int k = 0; k < 5; ++k) jm[k * NF + f] = fc[(e * 5 + k) * NF + f] - fn[k];
+        for (int k = 0; k < 5; ++k) jv[k] = fc[(e * 5 + k) * NF + f] - fn[k];
+        put5<L, NF>(jm, f, jv);
       }
     }
     __syncthreads();
@@ -813,17 +964,21 @@ __global__ void __launch_bounds__(EPB* NU)
     if (act) {
       T div[5] = {0, 0, 0, 0, 0};
       for (int q = 0; q < NU; ++q) {
+        T v[15];
+        get15<L, NU>(ft, q, v);
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-          T w = ops.DT[(d * NU + q) * NU + z];
+          const T w = ops.DT[(d * NU + q) * NU + z];
 #pragma unroll
-          for (int k = 0; k < 5; ++k) div[k] += w * ft[(d * 5 + k) * NU + q];
+          for (int k = 0; k < 5; ++k) div[k] += w * v[d * 5 + k];
         }
       }
       for (int f = 0; f < NF; ++f) {
-        T l = ops.LIFTT[f * NU + z];
+        const T l = ops.LIFTT[f * NU + z];
+        T jv[5];
+        get5<L, NF>(jm, f, jv);
 #pragma unroll
-        for (int k = 0; k < 5; ++k) div[k] += l * jm[k * NF + f];
+        for (int k = 0; k < 5; ++k) div[k] += l * jv[k];
       }
       T rj = rcpdjac[e * NU + z];
       T R[5];
@@ -833,18 +988,17 @@ __global__ void __launch_bounds__(EPB* NU)
     }
     if (sa.uf_next != nullptr) {
       __syncthreads();  // ft no longer read: reuse it for the next stage value
-      if (act) {
-#pragma unroll
-        for (int k = 0; k < 5; ++k) ft[k * NU + z] = s[k];
-      }
+      if (act) put5<L, NU>(ft, z, s);
       __syncthreads();
       if (act) {
         for (int f = z; f < NF; f += NU) {
           T acc[5] = {0, 0, 0, 0, 0};
           for (int q = 0; q < NU; ++q) {
-            T m = ops.M0T[q * NF + f];
+            const T m = ops.M0T[q * NF + f];
+            T v[5];
+            get5<L, NU>(ft, q, v);
 #pragma unroll
-            for (int k = 0; k < 5; ++k) acc[k] += m * ft[k * NU + q];
+            for (int k = 0; k < 5; ++k) acc[k] += m * v[k];
           }
 #pragma unroll
           for (int k = 0; k < 5; ++k) sa.uf_next[(e * 5 + k) * NF + f] = acc[k];
