@@ -324,7 +324,13 @@ int fr_get_tuning(const fr_mesh* mesh, int* active, float* ms_per_step);
  *     the sum-factorised hexahedron kernels (at most 256 threads per CTA),
  *     persistent CTAs per SM of the dense kernels; 0 = the largest (default),
  *     -1 = no such element in the mesh;
- *   tensor_grad, tensor_vol: 1 when that kernel runs on the tensor cores.
+ *   tensor_grad, tensor_vol: 1 when that kernel runs on the tensor cores;
+ *   structured: 1 when the CUDA-core kernels of that kind use the
+ *     structure of its operators (Section 3.1, "Matrix multiplications":
+ *     sum factorisation on hexahedra; on prisms the triangle x line
+ *     factorisation of the derivatives and the nonzeros of the
+ *     interpolation and lift; on tetrahedra the interpolation to the flux
+ *     points by its nonzeros, a gather), 0 for the dense operator products.
  * face_block: threads per CTA of the interface and boundary kernels (32..1024,
  * a multiple of 32); parallel_types: the per-type kernels of a phase run as
  * parallel branches of the step's graph (forked streams) instead of in
@@ -338,11 +344,12 @@ typedef struct {
   int face_block;
   int parallel_types;
   float ms_default, ms_tuned;
+  int structured[3];
 } fr_schedule_t;
 int fr_get_schedule(const fr_mesh* mesh, fr_schedule_t* out);
-/* Set the tiles and schedule (tensor_*, ms_* are ignored); FR_EINVAL for a
- * tile above the kernel's maximum, a bad block size, or a host-only handle.
- * Later steps rebuild their graphs. */
+/* Set the tiles and schedule (tensor_*, structured and ms_* are ignored);
+ * FR_EINVAL for a tile above the kernel's maximum, a bad block size, or a
+ * host-only handle.  Later steps rebuild their graphs. */
 int fr_set_schedule(fr_mesh* mesh, const fr_schedule_t* in);
 
 /* Kernels and copies of the handle run on this stream (cudaStream_t);

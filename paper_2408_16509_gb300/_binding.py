@@ -165,7 +165,8 @@ class Schedule(C.Structure):
     _fields_ = [("tile_grad", C.c_int * 3), ("tile_vol", C.c_int * 3),
                 ("tensor_grad", C.c_int * 3), ("tensor_vol", C.c_int * 3),
                 ("face_block", C.c_int), ("parallel_types", C.c_int),
-                ("ms_default", C.c_float), ("ms_tuned", C.c_float)]
+                ("ms_default", C.c_float), ("ms_tuned", C.c_float),
+                ("structured", C.c_int * 3)]
 
 
 class AdaptCtl(C.Structure):
@@ -442,8 +443,8 @@ class FRMesh:
     def schedule(self):
         """Tiles and schedule of the kernels (fr_get_schedule): per element
         type {'grad': tile, 'vol': tile, 'tensor_grad': bool, 'tensor_vol':
-        bool}, plus 'face_block', 'parallel_types', 'ms_default',
-        'ms_tuned'."""
+        bool, 'structured': bool}, plus 'face_block', 'parallel_types',
+        'ms_default', 'ms_tuned'."""
         sc = Schedule()
         _check(load().fr_get_schedule(self._h, C.byref(sc)))
         out = {"face_block": sc.face_block,
@@ -453,7 +454,8 @@ class FRMesh:
             if sc.tile_grad[k] >= 0:
                 out[name] = {"grad": sc.tile_grad[k], "vol": sc.tile_vol[k],
                              "tensor_grad": bool(sc.tensor_grad[k]),
-                             "tensor_vol": bool(sc.tensor_vol[k])}
+                             "tensor_vol": bool(sc.tensor_vol[k]),
+                             "structured": bool(sc.structured[k])}
         return out
 
     def set_schedule(self, tiles=None, face_block=256, parallel_types=False):

@@ -915,6 +915,7 @@ int fr_get_schedule(const fr_mesh* m, fr_schedule_t* out) {
     out->tile_vol[k] = D.tile_vol;
     out->tensor_grad[k] = use_tc_grad(m, D) ? 1 : 0;
     out->tensor_vol[k] = use_tc_vol(m, D) ? 1 : 0;
+    out->structured[k] = use_hex(m, D) || use_pri(m, D) || use_m0s(m, D) ? 1 : 0;
   }
   out->face_block = m->face_tb;
   out->parallel_types = m->par_types ? 1 : 0;
@@ -933,8 +934,9 @@ int fr_set_schedule(fr_mesh* m, const fr_schedule_t* in) {
     if (t < 0) continue;
     const DevType& D = m->types[t];
     const bool hexk = D.kind == EK_HEX && m->active != FR_VARIANT_DENSE;
-    const int mg = hexk ? hex_tile_max(m->order) : D.grad_ctas;
-    const int mv = hexk ? hex_tile_max(m->order) : D.vol_ctas;
+    const bool prik = use_pri(m, D);
+    const int mg = hexk ? hex_tile_max(m->order) : prik ? D.pri_grad_ctas : D.grad_ctas;
+    const int mv = hexk ? hex_tile_max(m->order) : prik ? D.pri_vol_ctas : D.vol_ctas;
     if (in->tile_grad[k] < 0 || in->tile_grad[k] > mg || in->tile_vol[k] < 0 ||
         in->tile_vol[k] > mv)
       return fail(FR_EINVAL, "tile out of range for this kernel");

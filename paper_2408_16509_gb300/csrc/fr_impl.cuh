@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <array>
 #include <memory>
 #include <unordered_map>
@@ -23,6 +24,7 @@
 #include "fr_filter.cuh"
 #include "fr_hex.cuh"
 #include "fr_kernels.cuh"
+#include "fr_prism.cuh"
 #include "fr_err.hpp"
 #include "fr_mesh.hpp"
 
@@ -106,6 +108,16 @@ struct DevType {
   float* zeta_last = nullptr;
   int* evals_last = nullptr;
   int grad_ctas = 1, vol_ctas = 1;  // resident CTAs per SM (dense kernels)
+  // prisms: operators in the structured form of fr_prism.cuh (device image
+  // of PriLayout: values, then the column indices)
+  bool pri_ok = false;
+  int pri_nm = 0, pri_nl = 0;
+  void* pri_img = nullptr;
+  int pri_grad_ctas = 1, pri_vol_ctas = 1;
+  // tetrahedra: M0 by its nonzeros (every flux point is a solution point)
+  int32_t* m0c = nullptr;
+  void* m0v = nullptr;
+  int m0_nm = 0;
   // tiles picked by the autotuner (0: the default, the largest): elements per
   // CTA of the hexahedron kernels, persistent CTAs per SM of the dense ones
   int tile_grad = 0, tile_vol = 0;
@@ -291,6 +303,112 @@ int dev_upload_i32(fr_mesh* m, const std::vector<int32_t>& h, int32_t** out) {
   return FR_OK;
 }
 
+// The prism's operators in the structured form of fr_prism.cuh, read out of
+// its dense operators: D_xi and D_eta must act within a level of the
+// triangle x line point set (identical blocks on every level) and D_zeta
+// along a line (the same 1D operator for every triangle point); M0 and LIFT
+// are stored by their nonzeros.  Entries below 1e-12 of an operator's
+// largest are structural zeros (the rounding of the dense construction).
+// Returns false (the dense kernels stay) when the structure does not hold
+// or a row has more nonzeros than the kernels are built for.
+inline bool build_prism_ops(const RefElement& R, std::vector<double>& tv,
+                            std::vector<int32_t>& ti, int* nm_out, int* nl_out) {
+  const int p = R.p, NT = (p + 1) * (p + 2) / 2, NL = p + 1;
+  const int NU = R.nupts, NF = R.nfpts;
+  if (R.kind != EK_PRI || NU != NT * NL || NF != 2 * NT + 3 * NL * NL) return false;
+  auto amax = [](const std::vector<double>& v) {
+    double a = 0.0;
+    for (double x : v) a = std::max(a, std::fabs(x));
+    return a;
+  };
+  const double td = 1e-12 * amax(R.D);
+  auto Dv = [&](int d, int r, int c) { return R.D[(size_t(d) * NU + r) * NU + c]; };
+  for (int r = 0; r < NU; ++r)
+    for (int c = 0; c < NU; ++c) {
+      const int zr = r / NT, tr = r % NT, zc = c / NT, tc = c % NT;
+      for (int d = 0; d < 2; ++d) {
+        const double ref = zr == zc ? Dv(d, tr, tc) : 0.0;
+        if (std::fabs(Dv(d, r, c) - ref) > td) return false;
+      }
+      const double rz = tr == tc ? Dv(2, zr * NT, zc * NT) : 0.0;
+      if (std::fabs(Dv(2, r, c) - rz) > td) return false;
+    }
+  const double tm = 1e-12 * amax(R.M0), tl = 1e-12 * amax(R.LIFT);
+  int nm = 0, nl = 0;
+  for (int f = 0; f < NF; ++f) {
+    int c = 0;
+    for (int q = 0; q < NU; ++q) c += std::fabs(R.M0[size_t(f) * NU + q]) > tm;
+    nm = std::max(nm, c);
+  }
+  for (int z = 0; z < NU; ++z) {
+    int c = 0;
+    for (int f = 0; f < NF; ++f) c += std::fabs(R.LIFT[size_t(z) * NF + f]) > tl;
+    nl = std::max(nl, c);
+  }
+  if (nm < 1 || nl < 1 || nm > kPriMaxM0 || nl > kPriMaxLift) return false;
+  tv.assign(size_t(2 * NT * NT + NL * NL + NF * nm + NU * nl + 3 * NF), 0.0);
+  ti.assign(size_t(NF * nm + NU * nl), 0);
+  double* axi = tv.data();
+  double* aeta = axi + NT * NT;
+  double* b = aeta + NT * NT;
+  double* mv = b + NL * NL;
+  double* lv = mv + NF * nm;
+  double* nr = lv + NU * nl;
+  int32_t* mc = ti.data();
+  int32_t* lc = mc + NF * nm;
+  for (int t = 0; t < NT; ++t)
+    for (int t2 = 0; t2 < NT; ++t2) {
+      axi[t * NT + t2] = Dv(0, t, t2);
+      aeta[t * NT + t2] = Dv(1, t, t2);
+    }
+  for (int z = 0; z < NL; ++z)
+    for (int z2 = 0; z2 < NL; ++z2) b[z * NL + z2] = Dv(2, z * NT, z2 * NT);
+  for (int f = 0; f < NF; ++f) {
+    int j = 0;
+    for (int q = 0; q < NU; ++q) {
+      const double v = R.M0[size_t(f) * NU + q];
+      if (std::fabs(v) > tm) {
+        mc[f * nm + j] = q;
+        mv[f * nm + j] = v;
+        ++j;
+      }
+    }
+  }
+  for (int z = 0; z < NU; ++z) {
+    int j = 0;
+    for (int f = 0; f < NF; ++f) {
+      const double v = R.LIFT[size_t(z) * NF + f];
+      if (std::fabs(v) > tl) {
+        lc[z * nl + j] = f;
+        lv[z * nl + j] = v;
+        ++j;
+      }
+    }
+  }
+  for (int i = 0; i < 3 * NF; ++i) nr[i] = R.fnorm[i];
+  *nm_out = nm;
+  *nl_out = nl;
+  return true;
+}
+
+// PriOps over the device image of a prism type (PriLayout order)
+template <typename T>
+PriOps<T> pri_ops_of(const fr_mesh* m, const DevType& D) {
+  const int p = m->order, NT = (p + 1) * (p + 2) / 2, NL = p + 1;
+  const int NU = D.nu, NF = D.nf, nm = D.pri_nm, nl = D.pri_nl;
+  const T* t = static_cast<const T*>(D.pri_img);
+  const T* axi = t;
+  const T* aeta = axi + NT * NT;
+  const T* b = aeta + NT * NT;
+  const T* mv = b + NL * NL;
+  const T* lv = mv + NF * nm;
+  const T* nr = lv + NU * nl;
+  const int tcount = 2 * NT * NT + NL * NL + NF * nm + NU * nl + 3 * NF;
+  const int* ib = reinterpret_cast<const int*>(
+      static_cast<const char*>(D.pri_img) + (size_t(tcount) * sizeof(T) + 15) / 16 * 16);
+  return PriOps<T>{axi, aeta, b, ib, mv, ib + NF * nm, lv, nr, nm, nl};
+}
+
 int dev_zeros(fr_mesh* m, size_t bytes, void** out) {
   *out = nullptr;
   if (!bytes) return FR_OK;
@@ -463,6 +581,56 @@ int setup_device(fr_mesh* m) {
     if ((rc = dev_upload<T>(m, dt, &D.DT))) return rc;
     if ((rc = dev_upload<T>(m, lt, &D.LIFTT))) return rc;
     if ((rc = dev_upload<T>(m, R.fnorm, &D.NREF))) return rc;
+    if (D.kind == EK_TET) {
+      // M0 rows with at most a quarter of the points nonzero: stored by
+      // their nonzeros (a gather when the flux points are solution points)
+      const int NU = D.nu, NF = D.nf;
+      double mx = 0.0;
+      for (double x : R.M0) mx = std::max(mx, std::fabs(x));
+      int nm = 0;
+      for (int f = 0; f < NF; ++f) {
+        int c = 0;
+        for (int q = 0; q < NU; ++q) c += std::fabs(R.M0[size_t(f) * NU + q]) > 1e-12 * mx;
+        nm = std::max(nm, c);
+      }
+      if (nm >= 1 && 4 * nm <= NU) {
+        std::vector<int32_t> mc(size_t(NF) * nm, 0);
+        std::vector<double> mv(size_t(NF) * nm, 0.0);
+        for (int f = 0; f < NF; ++f) {
+          int j = 0;
+          for (int q = 0; q < NU; ++q) {
+            const double v = R.M0[size_t(f) * NU + q];
+            if (std::fabs(v) > 1e-12 * mx) {
+              mc[size_t(f) * nm + j] = q;
+              mv[size_t(f) * nm + j] = v;
+              ++j;
+            }
+          }
+        }
+        if ((rc = dev_upload_i32(m, mc, &D.m0c))) return rc;
+        if ((rc = dev_upload<T>(m, mv, &D.m0v))) return rc;
+        D.m0_nm = nm;
+      }
+    }
+    if (D.kind == EK_PRI) {
+      std::vector<double> tv;
+      std::vector<int32_t> ti;
+      if (build_prism_ops(R, tv, ti, &D.pri_nm, &D.pri_nl)) {
+        // one device image: the values as T, padded to 16 bytes, then the
+        // column indices (the shared-memory layout of the kernels)
+        const size_t tb = (tv.size() * sizeof(T) + 15) / 16 * 16;
+        std::vector<unsigned char> img(tb + ti.size() * 4, 0);
+        for (size_t i = 0; i < tv.size(); ++i) {
+          const T v = T(tv[i]);
+          std::memcpy(img.data() + i * sizeof(T), &v, sizeof(T));
+        }
+        std::memcpy(img.data() + tb, ti.data(), ti.size() * 4);
+        CK(cudaMalloc(&D.pri_img, img.size()));
+        m->allocs.push_back(D.pri_img);
+        CK(cudaMemcpy(D.pri_img, img.data(), img.size(), cudaMemcpyHostToDevice));
+        D.pri_ok = true;
+      }
+    }
     if (sizeof(T) == 4 && D.kind != EK_HEX) {
       bool fits = false;
       int tca = 0;
@@ -603,6 +771,22 @@ DenseOps<T> ops_of(const DevType& D) {
                      (const T*)D.NREF};
 }
 
+// tetrahedra outside the DENSE family: M0 by its nonzeros
+bool use_m0s(const fr_mesh* m, const DevType& D) {
+  return D.kind == EK_TET && D.m0_nm > 0 && m->active != FR_VARIANT_DENSE;
+}
+
+template <typename T>
+DenseOps<T> stage_ops_of(const fr_mesh* m, const DevType& D) {
+  DenseOps<T> o = ops_of<T>(D);
+  if (use_m0s(m, D)) {
+    o.Mc = D.m0c;
+    o.Mv = (const T*)D.m0v;
+    o.nm = D.m0_nm;
+  }
+  return o;
+}
+
 inline unsigned nblk(long long n, int b) { return unsigned((n + b - 1) / b); }
 
 // hexahedron kernels: N = p + 1 solution points per line
@@ -642,6 +826,24 @@ bool use_tc_grad(const fr_mesh* m, const DevType& D) {
 
 bool use_tc_vol(const fr_mesh* m, const DevType& D) {
   return D.tc_ok && D.tc_vol_on && m->active == FR_VARIANT_TENSOR && m->aa_qdeg == 0;
+}
+
+// prisms on the structured kernels of fr_prism.cuh: every family but DENSE
+// (which keeps the dense operator products), no anti-aliasing
+bool use_pri(const fr_mesh* m, const DevType& D) {
+  return D.kind == EK_PRI && D.pri_ok && m->active != FR_VARIANT_DENSE && m->aa_qdeg == 0;
+}
+
+template <typename T, int NU, int NF>
+size_t pri_grad_smem(const DevType& D) {
+  return size_t(PriLayout<T, NU, NF>::bytes(D.pri_nm, D.pri_nl)) +
+         size_t(dense_epb<NU>()) * size_t(DenseLayout<T, NU, NF>::kGradElem) * sizeof(T);
+}
+
+template <typename T, int NU, int NF>
+size_t pri_vol_smem(const DevType& D) {
+  return size_t(PriLayout<T, NU, NF>::bytes(D.pri_nm, D.pri_nl)) +
+         size_t(dense_epb<NU>()) * size_t(DenseLayout<T, NU, NF>::kVolElem) * sizeof(T);
 }
 
 // Anti-aliased transformed flux of one element type (Section 3.2) into D.tf;
@@ -827,6 +1029,22 @@ int prepare_kernels(fr_mesh* m) {
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kv1, E * NU, sv);
       D.grad_ctas = a > 0 ? a : 1;
       D.vol_ctas = b > 0 ? b : 1;
+      if constexpr (pri_order(NU, NF) > 0) {
+        if (D.pri_ok) {
+          auto pg = k_grad_pri<T, NU, NF, E, sizeof(T) == 4>;
+          auto pv0 = k_vol_pri<T, NU, NF, E, false>;
+          auto pv1 = k_vol_pri<T, NU, NF, E, true>;
+          const int psg = int(pri_grad_smem<T, NU, NF>(D)), psv = int(pri_vol_smem<T, NU, NF>(D));
+          cudaFuncSetAttribute(pg, cudaFuncAttributeMaxDynamicSharedMemorySize, psg);
+          cudaFuncSetAttribute(pv0, cudaFuncAttributeMaxDynamicSharedMemorySize, psv);
+          cudaFuncSetAttribute(pv1, cudaFuncAttributeMaxDynamicSharedMemorySize, psv);
+          int pa = 0, pb = 0;
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pa, pg, E * NU, psg);
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pb, pv1, E * NU, psv);
+          D.pri_grad_ctas = pa > 0 ? pa : 1;
+          D.pri_vol_ctas = pb > 0 ? pb : 1;
+        }
+      }
       if constexpr (tc_types<T, TR>() && tc_supported<NU, NF>()) {
         if (D.tc_ok) {
           constexpr int EV = tc_vol_epb<NU, NF>(), EG = tc_grad_epb<NU, NF>();
@@ -975,7 +1193,8 @@ inline std::vector<int> tile_candidates(const fr_mesh* m, const DevType& D, bool
       if (k == 1) break;
     }
   } else {
-    const int mx = grad ? D.grad_ctas : D.vol_ctas;
+    const int mx = use_pri(m, D) ? (grad ? D.pri_grad_ctas : D.pri_vol_ctas)
+                                 : (grad ? D.grad_ctas : D.vol_ctas);
     for (int k = mx; k >= 1; k /= 2) c.push_back(k);
   }
   return c;
@@ -1120,6 +1339,20 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
         });
       } else if (use_tc_grad(m, D)) {
         launch_grad_tc<T, TR>(m, D, s, from_x, du, va, bc, ph);
+      } else if (use_pri(m, D)) {
+        dispatch(D.kind, m->order, [&](auto nu, auto nf) {
+          constexpr int NU = decltype(nu)::value, NF = decltype(nf)::value;
+          if constexpr (pri_order(NU, NF) > 0) {
+            constexpr int E = dense_epb<NU>();
+            const unsigned grid = unsigned(std::min<long long>(
+                (D.ne + E - 1) / E,
+                (long long)m->num_sms * (D.tile_grad > 0 ? D.tile_grad : D.pri_grad_ctas)));
+            k_grad_pri<T, NU, NF, E, sizeof(T) == 4>
+                <<<grid, E * NU, pri_grad_smem<T, NU, NF>(D), s>>>(
+                    D.ne, from_x ? (const T*)D.X : (const T*)D.Y, du, (const T*)D.smat,
+                    (const T*)D.rcpdjac, pri_ops_of<T>(m, D), (T*)D.grad, va, bc, ph);
+          }
+        });
       } else {
         dispatch(D.kind, m->order, [&](auto nu, auto nf) {
           constexpr int NU = decltype(nu)::value, NF = decltype(nf)::value;
@@ -1130,7 +1363,7 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
               (long long)m->num_sms * (D.tile_grad > 0 ? D.tile_grad : D.grad_ctas)));
           k_grad_dense<T, NU, NF, E, sizeof(T) == 4><<<grid, E * NU, sm, s>>>(
               D.ne, from_x ? (const T*)D.X : (const T*)D.Y, du,
-              (const T*)D.smat, (const T*)D.rcpdjac, ops_of<T>(D), (T*)D.grad,
+              (const T*)D.smat, (const T*)D.rcpdjac, stage_ops_of<T>(m, D), (T*)D.grad,
               va, bc, ph);
         });
       }
@@ -1236,6 +1469,26 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
       sa.uf_next = uf_next;
       sa.E = m->err_on ? (T*)D.E : nullptr;
       const T* uin = from_x ? (const T*)D.X : (const T*)D.Y;
+      if (use_pri(m, D)) {
+        dispatch(D.kind, m->order, [&](auto nu, auto nf) {
+          constexpr int NU = decltype(nu)::value, NF = decltype(nf)::value;
+          if constexpr (pri_order(NU, NF) > 0) {
+            constexpr int E = dense_epb<NU>();
+            const unsigned grid = unsigned(std::min<long long>(
+                (D.ne + E - 1) / E,
+                (long long)m->num_sms * (D.tile_vol > 0 ? D.tile_vol : D.pri_vol_ctas)));
+            const size_t sm = pri_vol_smem<T, NU, NF>(D);
+            if (ns)
+              k_vol_pri<T, NU, NF, E, true><<<grid, E * NU, sm, s>>>(
+                  D.ne, uin, (const T*)D.grad, fc, (const T*)D.smat, (const T*)D.rcpdjac,
+                  pri_ops_of<T>(m, D), ph, sa);
+            else
+              k_vol_pri<T, NU, NF, E, false><<<grid, E * NU, sm, s>>>(
+                  D.ne, uin, nullptr, fc, (const T*)D.smat, (const T*)D.rcpdjac,
+                  pri_ops_of<T>(m, D), ph, sa);
+          }
+        });
+      } else
       dispatch(D.kind, m->order, [&](auto nu, auto nf) {
         constexpr int NU = decltype(nu)::value, NF = decltype(nf)::value;
         constexpr int E = dense_epb<NU>();
@@ -1245,16 +1498,16 @@ void launch_stage(fr_mesh* m, cudaStream_t s, int mode, int stage,
             (long long)m->num_sms * (D.tile_vol > 0 ? D.tile_vol : D.vol_ctas)));
         if (aa)
           k_vol_dense<T, NU, NF, E, false, true><<<grid, E * NU, sm, s>>>(
-              D.ne, uin, nullptr, fc, nullptr, (const T*)D.rcpdjac, ops_of<T>(D),
-              ph, sa, (const T*)D.tf);
+              D.ne, uin, nullptr, fc, nullptr, (const T*)D.rcpdjac,
+              stage_ops_of<T>(m, D), ph, sa, (const T*)D.tf);
         else if (ns)
           k_vol_dense<T, NU, NF, E, true><<<grid, E * NU, sm, s>>>(
               D.ne, uin, (const T*)D.grad, fc, (const T*)D.smat,
-              (const T*)D.rcpdjac, ops_of<T>(D), ph, sa);
+              (const T*)D.rcpdjac, stage_ops_of<T>(m, D), ph, sa);
         else
           k_vol_dense<T, NU, NF, E, false><<<grid, E * NU, sm, s>>>(
               D.ne, uin, nullptr, fc, (const T*)D.smat, (const T*)D.rcpdjac,
-              ops_of<T>(D), ph, sa);
+              stage_ops_of<T>(m, D), ph, sa);
       });
     }
     PROF_END(FR_KC_VOL);

@@ -41,6 +41,11 @@ struct DenseOps {
   const T* DT;     // [3][nu][nu]
   const T* LIFTT;  // [nf][nu]
   const T* NREF;   // [nf][3]
+  // M0 by its nonzeros ([nf][nm] columns and values), nm = 0: dense M0.
+  // Tetrahedra: every flux point is a solution point (nm = 1, a gather).
+  const int* Mc = nullptr;
+  const T* Mv = nullptr;
+  int nm = 0;
 };
 
 // Time-integration epilogue of the volume kernel.
@@ -762,7 +767,7 @@ __device__ __forceinline__ DenseOps<T> stage_dense_ops(const DenseOps<T>& g,
   }
   for (int i = threadIdx.x; i < 3 * NF; i += blockDim.x) nr[i] = g.NREF[i];
   __syncthreads();
-  return DenseOps<T>{m0, dt, li, nr};
+  return DenseOps<T>{m0, dt, li, nr, g.Mc, g.Mv, g.nm};
 }
 
 // NS gradient path: corrected reference gradient D u + LIFT (n~ du), physical
@@ -852,12 +857,22 @@ __global__ void __launch_bounds__(EPB* NU)
         T acc[15];
 #pragma unroll
         for (int c = 0; c < 15; ++c) acc[c] = T(0);
-        for (int q = 0; q < NU; ++q) {
-          const T m = ops.M0T[q * NF + f];
-          T g[15];
-          get15<L, NU>(gs, q, g);
+        if (ops.nm > 0) {  // M0 by its nonzeros
+          for (int j = 0; j < ops.nm; ++j) {
+            const T m = ops.Mv[f * ops.nm + j];
+            T g[15];
+            get15<L, NU>(gs, ops.Mc[f * ops.nm + j], g);
 #pragma unroll
-          for (int c = 0; c < 15; ++c) acc[c] += m * g[c];
+            for (int c = 0; c < 15; ++c) acc[c] += m * g[c];
+          }
+        } else {
+          for (int q = 0; q < NU; ++q) {
+            const T m = ops.M0T[q * NF + f];
+            T g[15];
+            get15<L, NU>(gs, q, g);
+#pragma unroll
+            for (int c = 0; c < 15; ++c) acc[c] += m * g[c];
+          }
         }
         if (QV) {
           write_visc_q(va, bc, ph, e, f, NF, acc);
@@ -934,7 +949,15 @@ __global__ void __launch_bounds__(EPB* NU)
       for (int f = z; f < NF; f += NU) {
         T fn[5] = {0, 0, 0, 0, 0};
         const T nr0 = ops.NREF[f * 3], nr1 = ops.NREF[f * 3 + 1], nr2 = ops.NREF[f * 3 + 2];
-        for (int q = 0; q < NU; ++q) {
+        for (int j = 0; j < ops.nm; ++j) {  // M0 by its nonzeros
+          const T m = ops.Mv[f * ops.nm + j];
+          T v[15];
+          get15<L, NU>(ft, ops.Mc[f * ops.nm + j], v);
+          const T w0 = m * nr0, w1 = m * nr1, w2 = m * nr2;
+#pragma unroll
+          for (int k = 0; k < 5; ++k) fn[k] += w0 * v[k] + w1 * v[5 + k] + w2 * v[10 + k];
+        }
+        for (int q = 0; q < (ops.nm > 0 ? 0 : NU); ++q) {
           const T m = ops.M0T[q * NF + f];
           if constexpr (L::kRows) {
             T v[15];
@@ -993,7 +1016,14 @@ __global__ void __launch_bounds__(EPB* NU)
       if (act) {
         for (int f = z; f < NF; f += NU) {
           T acc[5] = {0, 0, 0, 0, 0};
-          for (int q = 0; q < NU; ++q) {
+          for (int j = 0; j < ops.nm; ++j) {  // M0 by its nonzeros
+            const T m = ops.Mv[f * ops.nm + j];
+            T v[5];
+            get5<L, NU>(ft, ops.Mc[f * ops.nm + j], v);
+#pragma unroll
+            for (int k = 0; k < 5; ++k) acc[k] += m * v[k];
+          }
+          for (int q = 0; q < (ops.nm > 0 ? 0 : NU); ++q) {
             const T m = ops.M0T[q * NF + f];
             T v[5];
             get5<L, NU>(ft, q, v);

@@ -216,3 +216,61 @@ def test_interface_orientation_matches_oracle(name):
     lib = sorted(zip(left.tolist(), right.tolist()))
     ora = sorted(zip(ol.tolist(), orr.tolist()))
     assert lib == ora
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_prism_operators_factor_into_triangle_and_line(p):
+    """The prism's operators as the library builds them have the structure
+    its structured kernels read: D_xi and D_eta act within a level of the
+    triangle x line points (the same block on every level), D_zeta along a
+    line (the same 1D operator for every triangle point), and M0 / LIFT rows
+    touch few points (the line through a triangle-face point, the edge of a
+    level for a quadrilateral face).  Checked here on the host from the
+    library's own dense operators, against the point order z * NT + t."""
+    bcs = {k: ("state", 1.0, 0.2, 0.0, 0.0, 5.0) for k in range(4)}
+    g = fr.FRMesh(mixed_box(n=2, x_pri=0.0, x_tet=1.1), p, bcs=bcs, device=-1)
+    D = g.operator("pri", "D")
+    M0 = g.operator("pri", "M0")
+    L = g.operator("pri", "LIFT")
+    nt, nl = (p + 1) * (p + 2) // 2, p + 1
+    nu = nt * nl
+    assert D.shape == (3, nu, nu)
+    tol = 1e-12 * np.abs(D).max()
+    lev = np.arange(nu) // nt
+    tri = np.arange(nu) % nt
+    same_level = lev[:, None] == lev[None, :]
+    same_line = tri[:, None] == tri[None, :]
+    for d in (0, 1):
+        assert np.abs(D[d][~same_level]).max() <= tol
+        blk = D[d][:nt, :nt]
+        for z in range(nl):
+            assert np.abs(D[d][z * nt:(z + 1) * nt, z * nt:(z + 1) * nt] - blk).max() <= tol
+    assert np.abs(D[2][~same_line]).max() <= tol
+    line = D[2][::nt, ::nt]
+    for t in range(nt):
+        assert np.abs(D[2][t::nt, t::nt] - line).max() <= tol
+    nz_m0 = (np.abs(M0) > 1e-12 * np.abs(M0).max()).sum(axis=1)
+    nz_l = (np.abs(L) > 1e-12 * np.abs(L).max()).sum(axis=1)
+    if p <= 3:
+        # the triangle-face flux points are the solution points' triangle
+        # points: every M0 row is the p + 1 points of a line or an edge,
+        # within the kernels' bounds (16 per M0 row, 64 per LIFT row)
+        assert nz_m0.max() == nl and nz_l.max() <= 64
+    else:
+        # at p = 4 the triangle-face points differ from the solution
+        # triangle points: those rows are dense (the library keeps the dense
+        # kernels for this order)
+        assert nz_m0.max() == nu
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_tetrahedron_flux_points_are_solution_points(p):
+    """Every flux point of the library's tetrahedron is one of its solution
+    points (its M0 row has a single nonzero, 1): the CUDA-core kernels take
+    the interpolation to the flux points as a gather."""
+    bcs = {k: ("state", 1.0, 0.2, 0.0, 0.0, 5.0) for k in range(4)}
+    g = fr.FRMesh(mixed_box(n=2, x_pri=0.34, x_tet=0.67), p, bcs=bcs, device=-1)
+    M0 = g.operator("tet", "M0")
+    nz = np.abs(M0) > 1e-12 * np.abs(M0).max()
+    assert np.all(nz.sum(axis=1) == 1)
+    assert np.allclose(M0[nz], 1.0, rtol=0, atol=1e-12)
