@@ -607,14 +607,17 @@ int fr_mlp_loss_grad(int device, const float* params, const float* x,
  * `device`; synchronous. */
 int fr_probe_fma(int device, int dtype, int64_t iters, double* ms, double* flops);
 
-/* Self-check of the mixed form's FP32 <-> FP64 conversions (the paper has no
- * counterpart): the library widens FP32 increments to FP64 and rounds its
- * FP64 registers to FP32 with integer instructions instead of the FP64
- * pipe.  Runs n seeded patterns of each (random bits, exponents around the
+/* Self-check of the arithmetic the library does off the FP64 pipe (the
+ * paper has no counterpart): the mixed form widens FP32 increments to FP64
+ * and rounds its FP64 registers to FP32 with integer instructions, and the
+ * entropy filter's FP64 checks take 1/rho and fifth roots by Newton steps
+ * from FP32 values.  Runs n seeded patterns (random bits, exponents around the
  * FP32 range, exact rounding ties, carries into and out of the exponent) on
- * `device` against the hardware conversions and writes the number of
- * results that differ in any bit (NaNs: that differ in NaN-ness) to
- * *mismatches.  Allocates and frees 8 bytes on `device`; synchronous. */
+ * `device` and writes to *mismatches the number of conversions that differ
+ * from the hardware conversions in any bit (NaNs: that differ in NaN-ness)
+ * plus the reciprocals more than 2 units in the last place from the FP64
+ * division and the fifth roots r with |r^5 - x| > 5e-15 x.
+ * Allocates and frees 8 bytes on `device`; synchronous. */
 int fr_check_conversions(int device, uint64_t seed, int64_t n, int64_t* mismatches);
 
 /* Message of the last failed call on this thread. */

@@ -80,13 +80,58 @@ struct FilterArgs {
   const float* mlp_norm;     // mean[4], std[4]
 };
 
-__device__ __forceinline__ double entropy_of(double r, double mx, double my,
-                                             double mz, double E, double g,
-                                             double* p_out) {
-  double p = (g - 1.0) * (E - 0.5 * (mx * mx + my * my + mz * mz) / r);
-  *p_out = p;
-  if (r > 0.0 && p > 0.0) return p * pow(r, -g);
-  return INFINITY;
+// Entropy minima without an FP64 pow per point (gamma = 7/5, the value
+// every workload here uses).  Then s^5 = p^5 rho^-7 exactly, and x -> x^5
+// is increasing on all reals, so the point of least s is the point of
+// least y = p^5 (1/rho)^7, formed with seven FP64 multiplications; s_min =
+// y_min^(1/5) is one fifth root per minimum (root5: Newton steps from the
+// FP32 root), and a sign test s >= b is y >= b^5.  Against p rho^-gamma
+// evaluated per point this differs only by rounding (about 1e-15
+// relative; FP64 1.4 itself is 7/5 to 6e-17).  y is formed only where it
+// stays a normal FP64 number (s5_in_range); other points take the
+// per-point pow.
+__device__ __forceinline__ bool entropy_by_s5(double g) { return g == 1.4; }
+
+// unbiased binary exponent of x from its bits (integer pipe)
+__device__ __forceinline__ int dexp2(double x) {
+  return int((__double_as_longlong(x) >> 52) & 0x7ff) - 1023;
+}
+
+// |p| in [2^-99, 2^100) or p = 0, 1/rho in [2^-69, 2^70): then p^5 (1/rho)^7
+// is a normal number (between 2^-978 and 2^985); tested on the exponent
+// bits, off the FP64 pipe
+__device__ __forceinline__ bool s5_in_range(double p, double rr) {
+  const long long pb = __double_as_longlong(p) & 0x7fffffffffffffffLL;
+  const int ep = dexp2(p), er = dexp2(rr);
+  return (pb == 0 || (ep >= -99 && ep <= 99)) && er >= -69 && er <= 69;
+}
+
+// minimum of two doubles by their order-preserving integer keys (defined
+// below for the block reductions), off the FP64 pipe
+__device__ __forceinline__ long long dkey(double x);
+__device__ __forceinline__ double dunkey(long long k);
+__device__ __forceinline__ double dmin_key(double a, double b) {
+  // like fmin: a NaN operand is ignored
+  const long long mag = __double_as_longlong(b) & 0x7fffffffffffffffLL;
+  if (mag > 0x7ff0000000000000LL) return a;
+  return dunkey(min(dkey(a), dkey(b)));
+}
+
+// FP64 copy of a stored value: FP32 values are widened on the integer pipe
+template <typename S>
+__device__ __forceinline__ double to_f64(S x) {
+  if constexpr (sizeof(S) == 4) return widen_f32(x);
+  else return double(x);
+}
+
+__device__ __forceinline__ double s5_of(double p, double rr) {
+  const double p2 = p * p, r2 = rr * rr, r4 = r2 * r2;
+  return (p2 * p2 * p) * (r4 * r2 * rr);
+}
+
+__device__ __forceinline__ double s_of_s5(double y) {
+  if (!(y == y) || y == INFINITY || y == -INFINITY) return y;
+  return root5(y);
 }
 
 // FP32 screen of a point for the exact FP64 minima of p and s = p rho^-g.
@@ -219,17 +264,47 @@ __global__ void k_entropy_min(long long ne, const T* __restrict__ uin,
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1)
     shi_min = fminf(shi_min, __shfl_xor_sync(0xffffffffu, shi_min, o));
-  double m = INFINITY;
+  const bool by5 = entropy_by_s5(gamma);
+  // the stored values as FP64: FP32 stage values widened exactly on the
+  // integer pipe (the FP64 pipe is this kernel's bound)
+  constexpr bool f32in = sizeof(T) == 4 && sizeof(TR) == 4;
+  double m = INFINITY, y = INFINITY;  // direct minimum, minimum of s^5
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
     if (!((cand >> q) & 1u) && !(slo[q] <= shi_min)) continue;
     double v[5];
-    if (!load(lane + 32 * q, v)) continue;
-    const double p = pressure64(v, gamma);
-    if (v[0] > 0.0 && p > 0.0) m = fmin(m, p * pow(v[0], -gamma));
+    float r32;
+    if constexpr (f32in) {
+      float vf[5];
+      if (!load(lane + 32 * q, vf)) continue;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) v[k] = widen_f32(vf[k]);
+      r32 = vf[0];
+    } else {
+      if (!load(lane + 32 * q, v)) continue;
+      r32 = narrow_f64(v[0]);
+    }
+    if (!(v[0] > 0.0)) continue;
+    const double rr = rcp64(v[0], r32);
+    const double p = (gamma - 1.0) * (v[4] - 0.5 * (v[1] * v[1] + v[2] * v[2] + v[3] * v[3]) * rr);
+    if (!(p > 0.0)) continue;
+    if (by5 && s5_in_range(p, rr))
+      y = dmin_key(y, s5_of(p, rr));
+    else
+      m = dmin_key(m, p * pow(v[0], -gamma));
   }
-  m = warp_min(m);
-  if (lane == 0) smin[e] = isfinite(m) ? m : 0.0;
+  long long km = dkey(m), ky = dkey(y);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    km = min(km, __shfl_xor_sync(0xffffffffu, km, o));
+    ky = min(ky, __shfl_xor_sync(0xffffffffu, ky, o));
+  }
+  m = dunkey(km);
+  y = dunkey(ky);
+  if (lane == 0) {
+    if (y < INFINITY) m = fmin(m, s_of_s5(y));
+    smin[e] = isfinite(m) ? m : 0.0;
+  }
 }
 
 // Block-wide reductions for the filter kernel.
@@ -283,6 +358,31 @@ __device__ __forceinline__ void block_min3_key(double& a, double& b, double& c,
   a = dunkey(ka);
   b = dunkey(kb);
   c = dunkey(kc);
+}
+
+// exact minima of four doubles over the block (one pair of barriers)
+__device__ __forceinline__ void block_min4_key(double& a, double& b, double& c, double& d,
+                                               long long* red) {
+  long long k[4] = {dkey(a), dkey(b), dkey(c), dkey(d)};
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) k[i] = min(k[i], __shfl_xor_sync(0xffffffffu, k[i], o));
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) red[4 * w + i] = k[i];
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 4; ++i) k[i] = 0x7fffffffffffffffLL;
+  for (int j = 0; j < kFilterThreads / 32; ++j)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) k[i] = min(k[i], red[4 * j + i]);
+  a = dunkey(k[0]);
+  b = dunkey(k[1]);
+  c = dunkey(k[2]);
+  d = dunkey(k[3]);
 }
 
 // minima of two floats over the block (one pair of barriers)
@@ -353,7 +453,7 @@ __global__ void __launch_bounds__(kFilterThreads)
   __shared__ T uh[5][NM];       // modal coefficients
   __shared__ T sg[NM];          // filtered weights sigma_k
   __shared__ double red[kFilterThreads / 32];
-  __shared__ long long redk[3 * (kFilterThreads / 32)];
+  __shared__ long long redk[4 * (kFilterThreads / 32)];
   __shared__ float redf[2 * (kFilterThreads / 32)];
   __shared__ double s_z;        // requested strength
   const long long e = blockIdx.x;
@@ -361,6 +461,7 @@ __global__ void __launch_bounds__(kFilterThreads)
   if (e >= ne) return;
   const double g = fa.gamma;
   const float gf = float(g);
+  const bool by5 = entropy_by_s5(g);
   // load the state into registers of a point-parallel layout, then modes
   __shared__ T us[5][NU];
   for (int z = tid; z < NU; z += kFilterThreads)
@@ -388,7 +489,12 @@ __global__ void __launch_bounds__(kFilterThreads)
   // pass over the same values.
   constexpr int NPT = (NP + kFilterThreads - 1) / kFilterThreads;
   struct Mins {
-    double r, p, s;
+    double r, p, s;  // s: minimum over the points that took the per-point pow
+    double ys;       // minimum of s^5 over the others (entropy_by_s5)
+  };
+  // the entropy minimum of an evaluation (one pow, by the thread that needs it)
+  auto smin_of = [](const Mins& q) -> double {
+    return q.ys < INFINITY ? fmin(q.s, s_of_s5(q.ys)) : q.s;
   };
   auto minima = [&](double z) -> Mins {
     for (int m = tid; m < NM; m += kFilterThreads) {
@@ -423,7 +529,7 @@ __global__ void __launch_bounds__(kFilterThreads)
       }
     }
     block_min2f(phi, shi, redf);
-    double rmin = double(rmin_t), mp = INFINITY, ms = INFINITY;
+    double rmin = double(rmin_t), mp = INFINITY, ms = INFINITY, ys = INFINITY;
 #pragma unroll
     for (int q = 0; q < NPT; ++q) {
       if (tid + q * kFilterThreads >= NP) continue;
@@ -432,19 +538,38 @@ __global__ void __launch_bounds__(kFilterThreads)
       if (!cp && !cs) continue;
       double w[5];
 #pragma unroll
-      for (int k = 0; k < 5; ++k) w[k] = double(v[q][k]);
-      const double p = pressure64(w, g);
-      if (cp) mp = fmin(mp, p);
-      if (cs) ms = fmin(ms, w[0] > 0.0 ? p * pow(w[0], -g) : -INFINITY);
+      for (int k = 0; k < 5; ++k) w[k] = to_f64(v[q][k]);
+      // one FP64 reciprocal per point (Newton steps from FP32, rcp64): 1/rho
+      // serves p and the s^5 key
+      const bool rpos = w[0] > 0.0;
+      const double rr =
+          rpos ? rcp64(w[0], sizeof(T) == 4 ? float(v[q][0]) : narrow_f64(w[0])) : 0.0;
+      const double p =
+          rpos ? (g - 1.0) * (w[4] - 0.5 * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]) * rr)
+               : pressure64(w, g);
+      if (cp) mp = dmin_key(mp, p);
+      if (cs) {
+        if (!rpos)
+          ms = -INFINITY;
+        else if (by5 && s5_in_range(p, rr))
+          ys = dmin_key(ys, s5_of(p, rr));
+        else
+          ms = dmin_key(ms, p * pow(w[0], -g));
+      }
     }
-    block_min3_key(rmin, mp, ms, redk);
-    return Mins{rmin, mp, ms};
+    block_min4_key(rmin, mp, ms, ys, redk);
+    return Mins{rmin, mp, ms, ys};
   };
-  const Mins m0 = minima(0.0);
+  Mins m0 = minima(0.0);
   // unfiltered state admissible (the sign of the margin below, which the
-  // positive means do not change): nothing to do (uniform across the block)
-  const double gm0 = fmin(m0.r - kEpsPos,
-                          fmin(m0.p - kEpsPos, smin > 0.0 ? m0.s - sb : INFINITY));
+  // positive means do not change): nothing to do (uniform across the block).
+  // The entropy term's sign without a pow: s >= sb <=> s^5 >= sb^5.
+  double s_term = INFINITY;
+  if (smin > 0.0) {
+    const double sb2 = sb * sb, sb5 = sb2 * sb2 * sb;
+    s_term = (m0.s >= sb && !(m0.ys < sb5)) ? 0.0 : -1.0;
+  }
+  const double gm0 = fmin(m0.r - kEpsPos, fmin(m0.p - kEpsPos, s_term));
   if (!isnan(gm0) && gm0 >= 0.0) {
     if (tid == 0 && fa.zeta_last) {
       fa.zeta_last[e] = 0.f;
@@ -452,12 +577,16 @@ __global__ void __launch_bounds__(kFilterThreads)
     }
     return;
   }
+  // a filtered element: its entropy minimum at z = 0 (one pow, warp 0:
+  // the predictor's features and thread 0's margin read it)
+  if (tid < 32) m0.s = smin_of(m0);
+  m0.ys = INFINITY;
   // element means of density and pressure (normalise the margin)
   double wr = 0.0, wp = 0.0, ws = 0.0;
   for (int z = tid; z < NU; z += kFilterThreads) {
-    double p;
-    entropy_of(double(us[0][z]), double(us[1][z]), double(us[2][z]),
-               double(us[3][z]), double(us[4][z]), g, &p);
+    const double w5[5] = {double(us[0][z]), double(us[1][z]), double(us[2][z]),
+                          double(us[3][z]), double(us[4][z])};
+    const double p = pressure64(w5, g);
     double w = double(op.W[z]);
     wr += w * double(us[0][z]);
     wp += w * p;
@@ -469,7 +598,7 @@ __global__ void __launch_bounds__(kFilterThreads)
   // margin g(z) = min((rho-eps)/rho_mean, (p-eps)/p_mean, (s-sb)/s_min)
   auto gval = [&](const Mins& q) -> double {
     const double gr = (q.r - kEpsPos) / rmean, gp = (q.p - kEpsPos) / pmean;
-    const double gs = smin > 0.0 ? (q.s - sb) / smin : INFINITY;
+    const double gs = smin > 0.0 ? (smin_of(q) - sb) / smin : INFINITY;
     double gm = fmin(gr, fmin(gp, gs));
     if (isnan(gm)) gm = -INFINITY;
     return gm;

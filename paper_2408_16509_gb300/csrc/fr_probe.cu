@@ -108,6 +108,21 @@ __global__ void k_convert_check(unsigned long long seed, long long n,
     const float n0 = __double2float_rn(dv), n1 = narrow_f64(dv);
     const bool nnan = n0 != n0;
     if (nnan ? (n1 == n1) : (__float_as_uint(n0) != __float_as_uint(n1))) ++nb;
+    // the FP64 reciprocal, positive x across and beyond its fast range:
+    // within 2 units in the last place of the division
+    const double x = fabs(dv);
+    if (x > 0.0 && x < INFINITY) {
+      const double r0 = 1.0 / x, r1 = rcp64(x, __double2float_rn(x));
+      const long long u = __double_as_longlong(r0) - __double_as_longlong(r1);
+      if (r0 > 0.0 && r0 < INFINITY && (u > 2 || u < -2)) ++nb;
+      // the fifth root: r^5 = x to 5e-15 relative (r within about 2 units
+      // in the last place; the FP64 fifth power adds ~4 roundings).  pow(x,
+      // 0.2) is no reference here: 0.2 is 1/5 only to 1e-17, which moves
+      // the result by 1e-17 |ln x| relative (8e-15 at x = 1e300)
+      const double q = root5(x);
+      const double q2 = q * q, q5 = q2 * q2 * q;
+      if (x >= 1e-290 && x <= 1e290 && !(fabs(q5 - x) <= 5e-15 * x)) ++nb;
+    }
   }
   if (nb) atomicAdd(bad, nb);
 }
