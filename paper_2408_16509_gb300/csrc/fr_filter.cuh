@@ -29,6 +29,7 @@
 
 #include <type_traits>
 
+#include "fr_dfloat.cuh"
 #include "fr_kernels.cuh"
 
 namespace frgb {
@@ -268,6 +269,93 @@ __global__ void k_entropy_min(long long ne, const T* __restrict__ uin,
   // the stored values as FP64: FP32 stage values widened exactly on the
   // integer pipe (the FP64 pipe is this kernel's bound)
   constexpr bool f32in = sizeof(T) == 4 && sizeof(TR) == 4;
+  if constexpr (f32in) {
+    if (by5) {
+      // FP32 values, gamma = 7/5: the point of least s^5 is selected in
+      // double-float arithmetic (FP64 where the pressure is too close to
+      // zero to sign), then s^5 is computed in FP64 at that point
+      const float gm1h = float(gamma - 1.0);
+      const dfl gm1d{gm1h, float((gamma - 1.0) - widen_f32(gm1h))};
+      double m = INFINITY;  // direct minimum (points outside the s^5 range)
+      long long ky = 0x7fffffffffffffffLL;
+      int qy = -1;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        if (!((cand >> q) & 1u) && !(slo[q] <= shi_min)) continue;
+        float vf[5];
+        if (!load(lane + 32 * q, vf)) continue;
+        if (!(vf[0] > 0.f)) continue;
+        bool amb = !(vf[0] >= 0x1p-100f && vf[0] <= 0x1p100f);
+        dfl rr{0.f, 0.f}, pd{0.f, 0.f};
+        if (!amb) {
+          rr = df_rcp(vf[0]);
+          pd = df_pressure(vf[1], vf[2], vf[3], vf[4], rr, gm1d, &amb);
+        }
+        double yk;
+        bool ykey = false;
+        if (amb) {
+          double v[5];
+#pragma unroll
+          for (int k = 0; k < 5; ++k) v[k] = widen_f32(vf[k]);
+          const double rr64 = rcp64(v[0], vf[0]);
+          const double p = (gamma - 1.0) * (v[4] - 0.5 * (v[1] * v[1] + v[2] * v[2] + v[3] * v[3]) * rr64);
+          if (!(p > 0.0)) continue;
+          if (s5_in_range(p, rr64)) {
+            yk = s5_of(p, rr64);
+            ykey = true;
+          } else {
+            m = dmin_key(m, p * pow(v[0], -gamma));
+          }
+        } else {
+          if (!(pd.hi > 0.f)) continue;
+          if (df_s5_key(pd, rr, &yk)) {
+            ykey = true;
+          } else {
+            double v[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) v[k] = widen_f32(vf[k]);
+            m = dmin_key(m, pressure64(v, gamma) * pow(v[0], -gamma));
+          }
+        }
+        if (ykey) {
+          const long long kt = (dkey(yk) & ~0x1fLL) | lane;
+          if (kt < ky) {
+            ky = kt;
+            qy = q;
+          }
+        }
+      }
+      long long km = dkey(m), kym = ky;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        km = min(km, __shfl_xor_sync(0xffffffffu, km, o));
+        kym = min(kym, __shfl_xor_sync(0xffffffffu, kym, o));
+      }
+      m = dunkey(km);
+      // the selected point's s^5 in FP64, on its lane, then to lane 0
+      double ysel = INFINITY, sdir = INFINITY;
+      if (qy >= 0 && ky == kym) {
+        float vf[5];
+        load(lane + 32 * qy, vf);
+        double v[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) v[k] = widen_f32(vf[k]);
+        const double rr64 = rcp64(v[0], vf[0]);
+        const double p = (gamma - 1.0) * (v[4] - 0.5 * (v[1] * v[1] + v[2] * v[2] + v[3] * v[3]) * rr64);
+        if (s5_in_range(p, rr64)) ysel = s5_of(p, rr64);
+        else sdir = p * pow(v[0], -gamma);
+      }
+      const int src = kym == 0x7fffffffffffffffLL ? 0 : int(kym & 0x1f);
+      ysel = __shfl_sync(0xffffffffu, ysel, src);
+      sdir = __shfl_sync(0xffffffffu, sdir, src);
+      if (lane == 0) {
+        m = fmin(m, sdir);
+        if (ysel < INFINITY) m = fmin(m, s_of_s5(ysel));
+        smin[e] = isfinite(m) ? m : 0.0;
+      }
+      return;
+    }
+  }
   double m = INFINITY, y = INFINITY;  // direct minimum, minimum of s^5
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
@@ -358,6 +446,31 @@ __device__ __forceinline__ void block_min3_key(double& a, double& b, double& c,
   a = dunkey(ka);
   b = dunkey(kb);
   c = dunkey(kc);
+}
+
+// minima of four integer keys over the block (one pair of barriers)
+__device__ __forceinline__ void block_min_ll4(long long& a, long long& b, long long& c,
+                                              long long& d, long long* red) {
+  long long k[4] = {a, b, c, d};
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) k[i] = min(k[i], __shfl_xor_sync(0xffffffffu, k[i], o));
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) red[4 * w + i] = k[i];
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 4; ++i) k[i] = 0x7fffffffffffffffLL;
+  for (int j = 0; j < kFilterThreads / 32; ++j)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) k[i] = min(k[i], red[4 * j + i]);
+  a = k[0];
+  b = k[1];
+  c = k[2];
+  d = k[3];
 }
 
 // exact minima of four doubles over the block (one pair of barriers)
@@ -462,23 +575,10 @@ __global__ void __launch_bounds__(kFilterThreads)
   const double g = fa.gamma;
   const float gf = float(g);
   const bool by5 = entropy_by_s5(g);
-  // load the state into registers of a point-parallel layout, then modes
+  const float gm1h = float(g - 1.0);
+  const dfl gm1d{gm1h, float((g - 1.0) - widen_f32(gm1h))};  // gamma - 1, double-float
+  __shared__ double s_sel[3];  // FP64 values at the selected points
   __shared__ T us[5][NU];
-  for (int z = tid; z < NU; z += kFilterThreads)
-#pragma unroll
-    for (int k = 0; k < 5; ++k)
-      us[k][z] = reg ? reg[(e * 5 + k) * NU + z] : T(regR[(e * 5 + k) * NU + z]);
-  __syncthreads();
-  for (int m = tid; m < NM; m += kFilterThreads) {
-    T acc[5] = {0, 0, 0, 0, 0};
-    for (int z = 0; z < NU; ++z) {
-      T w = op.VinvT[z * NM + m];
-#pragma unroll
-      for (int k = 0; k < 5; ++k) acc[k] += w * us[k][z];
-    }
-#pragma unroll
-    for (int k = 0; k < 5; ++k) uh[k][m] = acc[k];
-  }
   const double smin = fa.smin[e];
   const double sb = smin * (1.0 - fa.tau);
   // Exact minima of rho, p and s = p rho^-g (-inf where rho <= 0) of the
@@ -496,12 +596,17 @@ __global__ void __launch_bounds__(kFilterThreads)
   auto smin_of = [](const Mins& q) -> double {
     return q.ys < INFINITY ? fmin(q.s, s_of_s5(q.ys)) : q.s;
   };
-  auto minima = [&](double z) -> Mins {
-    for (int m = tid; m < NM; m += kFilterThreads) {
-      double d = double(op.deg[m]);
-      sg[m] = sizeof(T) == 4 ? T(__expf(-float(z * d * d))) : T(exp(-z * d * d));
+  // direct: the stage value itself at the solution points (reg) and its
+  // flux-point traces (uf, from the volume kernel) instead of the modal
+  // evaluation (the same polynomial, other rounding)
+  auto minima = [&](double z, bool direct) -> Mins {
+    if (!direct) {
+      for (int m = tid; m < NM; m += kFilterThreads) {
+        double d = double(op.deg[m]);
+        sg[m] = sizeof(T) == 4 ? T(__expf(-float(z * d * d))) : T(exp(-z * d * d));
+      }
+      __syncthreads();
     }
-    __syncthreads();
     T v[NPT][5];
     PtScreen sc[NPT];
     T rmin_t = T(INFINITY);
@@ -514,10 +619,17 @@ __global__ void __launch_bounds__(kFilterThreads)
       sc[q].pos = false;
       sc[q].plo = sc[q].slo = INFINITY;  // no point: never a candidate
       if (i >= NP) continue;
-      for (int m = 0; m < NM; ++m) {
-        T w = op.VT[m * NP + i] * sg[m];
+      if (direct) {
 #pragma unroll
-        for (int k = 0; k < 5; ++k) v[q][k] += w * uh[k][m];
+        for (int k = 0; k < 5; ++k)
+          v[q][k] = i < NU ? (reg ? reg[(e * 5 + k) * NU + i] : T(regR[(e * 5 + k) * NU + i]))
+                           : uf[(e * 5 + k) * NF + (i - NU)];
+      } else {
+        for (int m = 0; m < NM; ++m) {
+          T w = op.VT[m * NP + i] * sg[m];
+#pragma unroll
+          for (int k = 0; k < 5; ++k) v[q][k] += w * uh[k][m];
+        }
       }
       rmin_t = sizeof(T) == 4 ? T(fminf(float(rmin_t), float(v[q][0])))
                               : T(fmin(double(rmin_t), double(v[q][0])));
@@ -530,6 +642,105 @@ __global__ void __launch_bounds__(kFilterThreads)
     }
     block_min2f(phi, shi, redf);
     double rmin = double(rmin_t), mp = INFINITY, ms = INFINITY, ys = INFINITY;
+    if constexpr (sizeof(T) == 4) {
+      if (by5) {
+        // FP32 values, gamma = 7/5: the points of least p and of least s
+        // are selected in double-float arithmetic (~2^-43; FP64 only where
+        // its pressure is too close to zero to sign), then p and s^5 are
+        // computed in FP64 at the selected points.  Keys carry the thread
+        // in their low bits, so the selected point is unique.
+        long long kp = 0x7fffffffffffffffLL, ky = 0x7fffffffffffffffLL;
+        int qp = -1, qy = -1;
+#pragma unroll
+        for (int q = 0; q < NPT; ++q) {
+          if (tid + q * kFilterThreads >= NP) continue;
+          const bool cp = !sc[q].pos || sc[q].plo <= phi;
+          const bool cs = smin > 0.0 && (!sc[q].pos || sc[q].slo <= shi);
+          if (!cp && !cs) continue;
+          const float r = float(v[q][0]);
+          bool amb = !(r >= 0x1p-100f && r <= 0x1p100f);
+          dfl rr{0.f, 0.f}, pd{0.f, 0.f};
+          if (!amb) {
+            rr = df_rcp(r);
+            pd = df_pressure(float(v[q][1]), float(v[q][2]), float(v[q][3]),
+                             float(v[q][4]), rr, gm1d, &amb);
+          }
+          double pk, yk;
+          bool ykey = false;
+          if (amb) {  // FP64 at this point
+            double w[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) w[k] = to_f64(v[q][k]);
+            pk = pressure64(w, g);
+            if (cs) {
+              if (!(w[0] > 0.0)) {
+                ms = -INFINITY;
+              } else {
+                const double rr64 = rcp64(w[0], r);
+                if (s5_in_range(pk, rr64)) {
+                  yk = s5_of(pk, rr64);
+                  ykey = true;
+                } else {
+                  ms = dmin_key(ms, pk * pow(w[0], -g));
+                }
+              }
+            }
+          } else {
+            pk = df_to_f64(pd);
+            if (cs) {
+              if (df_s5_key(pd, rr, &yk)) {
+                ykey = true;
+              } else {
+                double w[5];
+#pragma unroll
+                for (int k = 0; k < 5; ++k) w[k] = to_f64(v[q][k]);
+                ms = dmin_key(ms, pressure64(w, g) * pow(w[0], -g));
+              }
+            }
+          }
+          const bool pnan = (__double_as_longlong(pk) & 0x7fffffffffffffffLL) >
+                            0x7ff0000000000000LL;  // ignored, like fmin
+          const long long kt = (dkey(pk) & ~0x7fLL) | tid;
+          if (cp && !pnan && kt < kp) {
+            kp = kt;
+            qp = q;
+          }
+          if (ykey) {
+            const long long kyt = (dkey(yk) & ~0x7fLL) | tid;
+            if (kyt < ky) {
+              ky = kyt;
+              qy = q;
+            }
+          }
+        }
+        long long kr = dkey(rmin), kms = dkey(ms), kpm = kp, kym = ky;
+        block_min_ll4(kr, kpm, kms, kym, redk);
+        rmin = dunkey(kr);
+        ms = dunkey(kms);
+        // the selected points' FP64 values (one writer each)
+        if (qp >= 0 && kp == kpm) {
+          double w[5];
+#pragma unroll
+          for (int k = 0; k < 5; ++k) w[k] = to_f64(v[qp][k]);
+          s_sel[0] = pressure64(w, g);
+        }
+        if (qy >= 0 && ky == kym) {
+          double w[5];
+#pragma unroll
+          for (int k = 0; k < 5; ++k) w[k] = to_f64(v[qy][k]);
+          const double rr64 = rcp64(w[0], float(v[qy][0]));
+          const double p64 = (g - 1.0) * (w[4] - 0.5 * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]) * rr64);
+          s_sel[1] = s5_in_range(p64, rr64) ? s5_of(p64, rr64) : INFINITY;
+          if (!s5_in_range(p64, rr64)) s_sel[2] = p64 * pow(w[0], -g);
+        }
+        __syncthreads();
+        mp = kpm == 0x7fffffffffffffffLL ? INFINITY : s_sel[0];
+        ys = kym == 0x7fffffffffffffffLL ? INFINITY : s_sel[1];
+        if (kym != 0x7fffffffffffffffLL && !(s_sel[1] < INFINITY)) ms = fmin(ms, s_sel[2]);
+        // (s_sel is written again only after the next evaluation's barriers)
+        return Mins{rmin, mp, ms, ys};
+      }
+    }
 #pragma unroll
     for (int q = 0; q < NPT; ++q) {
       if (tid + q * kFilterThreads >= NP) continue;
@@ -560,21 +771,50 @@ __global__ void __launch_bounds__(kFilterThreads)
     block_min4_key(rmin, mp, ms, ys, redk);
     return Mins{rmin, mp, ms, ys};
   };
-  Mins m0 = minima(0.0);
   // unfiltered state admissible (the sign of the margin below, which the
   // positive means do not change): nothing to do (uniform across the block).
   // The entropy term's sign without a pow: s >= sb <=> s^5 >= sb^5.
-  double s_term = INFINITY;
-  if (smin > 0.0) {
-    const double sb2 = sb * sb, sb5 = sb2 * sb2 * sb;
-    s_term = (m0.s >= sb && !(m0.ys < sb5)) ? 0.0 : -1.0;
-  }
-  const double gm0 = fmin(m0.r - kEpsPos, fmin(m0.p - kEpsPos, s_term));
-  if (!isnan(gm0) && gm0 >= 0.0) {
+  auto admissible = [&](const Mins& q) -> bool {
+    double s_term = INFINITY;
+    if (smin > 0.0) {
+      const double sb2 = sb * sb, sb5 = sb2 * sb2 * sb;
+      s_term = (q.s >= sb && !(q.ys < sb5)) ? 0.0 : -1.0;
+    }
+    const double gm = fmin(q.r - kEpsPos, fmin(q.p - kEpsPos, s_term));
+    return !isnan(gm) && gm >= 0.0;
+  };
+  auto leave_unfiltered = [&]() {
     if (tid == 0 && fa.zeta_last) {
       fa.zeta_last[e] = 0.f;
       fa.evals_last[e] = 1;
     }
+  };
+  // Most elements pass at zeta = 0: test the stage value and its traces
+  // directly, before any modal transform.
+  if (admissible(minima(0.0, true))) {
+    leave_unfiltered();
+    return;
+  }
+  // modal coefficients u^ = V^-1 u
+  for (int z = tid; z < NU; z += kFilterThreads)
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+      us[k][z] = reg ? reg[(e * 5 + k) * NU + z] : T(regR[(e * 5 + k) * NU + z]);
+  __syncthreads();
+  for (int m = tid; m < NM; m += kFilterThreads) {
+    T acc[5] = {0, 0, 0, 0, 0};
+    for (int z = 0; z < NU; ++z) {
+      T w = op.VinvT[z * NM + m];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) acc[k] += w * us[k][z];
+    }
+#pragma unroll
+    for (int k = 0; k < 5; ++k) uh[k][m] = acc[k];
+  }
+  // the same test on the modal evaluation (the oracle's form)
+  Mins m0 = minima(0.0, false);
+  if (admissible(m0)) {
+    leave_unfiltered();
     return;
   }
   // a filtered element: its entropy minimum at z = 0 (one pow, warp 0:
@@ -603,7 +843,7 @@ __global__ void __launch_bounds__(kFilterThreads)
     if (isnan(gm)) gm = -INFINITY;
     return gm;
   };
-  auto margin = [&](double z) -> double { return gval(minima(z)); };
+  auto margin = [&](double z) -> double { return gval(minima(z, false)); };
   // predictor inputs from the unfiltered state (z = 0)
   float feat[4] = {0.f, 0.f, 0.f, 0.f};
   if (fa.mlp || fa.samples) {
@@ -668,7 +908,7 @@ __global__ void __launch_bounds__(kFilterThreads)
     __syncthreads();
     if (!s_go) break;
     const double z = s_next;
-    const Mins mz = minima(z);  // ends with a barrier: s_next / s_go reusable
+    const Mins mz = minima(z, false);  // ends with a barrier: s_next / s_go reusable
     if (tid != 0) continue;
     const double gz = gval(mz);
     ++evals;
