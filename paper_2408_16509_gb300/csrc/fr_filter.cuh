@@ -555,13 +555,201 @@ static __device__ float mlp_guess(const float feat[4], const __nv_bfloat16* w,
   return o > 20.f ? o : log1pf(__expf(o));
 }
 
+// Minima of rho, p and s over a warp's element: slots lane + 32 q of v
+// (with their FP32 screens), FP64 values where the screen cannot decide; the
+// points of least p and least s^5 selected in double-float arithmetic for
+// FP32 values with gamma = 7/5 and computed in FP64 (as k_filter's minima).
+// Returns, on every lane, r (exact), p (FP64 at its point), s_dir (minimum
+// of s over the points that took the per-point pow) and ys (s^5 at its
+// point, FP64).
+template <typename T, int NQ, int NP>
+__device__ __forceinline__ void warp_minima(const T (&v)[NQ][5], const PtScreen (&sc)[NQ],
+                                            double smin, double g, bool by5, dfl gm1d,
+                                            double* r_out, double* p_out, double* s_out,
+                                            double* ys_out) {
+  const int lane = threadIdx.x & 31;
+  float phi = INFINITY, shi = INFINITY;
+  double rmin = INFINITY;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    if (lane + 32 * q >= NP) continue;
+    rmin = dmin_key(rmin, to_f64(v[q][0]));
+    if (sc[q].pos) {
+      phi = fminf(phi, sc[q].phi);
+      shi = fminf(shi, sc[q].shi);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    phi = fminf(phi, __shfl_xor_sync(0xffffffffu, phi, o));
+    shi = fminf(shi, __shfl_xor_sync(0xffffffffu, shi, o));
+  }
+  double ms = INFINITY;
+  long long kp = 0x7fffffffffffffffLL, ky = 0x7fffffffffffffffLL;
+  int qp = -1, qy = -1;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    if (lane + 32 * q >= NP) continue;
+    const bool cp = !sc[q].pos || sc[q].plo <= phi;
+    const bool cs = smin > 0.0 && (!sc[q].pos || sc[q].slo <= shi);
+    if (!cp && !cs) continue;
+    double pk = 0.0, yk = 0.0;
+    bool ykey = false, exact = true;
+    if constexpr (sizeof(T) == 4) {
+      const float r = v[q][0];
+      if (by5 && r >= 0x1p-100f && r <= 0x1p100f) {
+        bool amb;
+        const dfl rr = df_rcp(r);
+        const dfl pd = df_pressure(v[q][1], v[q][2], v[q][3], v[q][4], rr, gm1d, &amb);
+        if (!amb) {
+          exact = false;
+          pk = df_to_f64(pd);
+          if (cs) {
+            if (df_s5_key(pd, rr, &yk)) {
+              ykey = true;
+            } else {
+              double w[5];
+#pragma unroll
+              for (int k = 0; k < 5; ++k) w[k] = to_f64(v[q][k]);
+              ms = dmin_key(ms, pressure64(w, g) * pow(w[0], -g));
+            }
+          }
+        }
+      }
+    }
+    if (exact) {
+      double w[5];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) w[k] = to_f64(v[q][k]);
+      const bool rpos = w[0] > 0.0;
+      const double rr64 = rpos ? rcp64(w[0], sizeof(T) == 4 ? float(v[q][0]) : narrow_f64(w[0])) : 0.0;
+      pk = rpos ? (g - 1.0) * (w[4] - 0.5 * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]) * rr64)
+                : pressure64(w, g);
+      if (cs) {
+        if (!rpos) {
+          ms = -INFINITY;
+        } else if (by5 && s5_in_range(pk, rr64)) {
+          yk = s5_of(pk, rr64);
+          ykey = true;
+        } else {
+          ms = dmin_key(ms, pk * pow(w[0], -g));
+        }
+      }
+    }
+    const bool pnan = (__double_as_longlong(pk) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL;
+    const long long kt = (dkey(pk) & ~0x1fLL) | lane;
+    if (cp && !pnan && kt < kp) {
+      kp = kt;
+      qp = q;
+    }
+    if (ykey) {
+      const long long kyt = (dkey(yk) & ~0x1fLL) | lane;
+      if (kyt < ky) {
+        ky = kyt;
+        qy = q;
+      }
+    }
+  }
+  long long kr = dkey(rmin), kms = dkey(ms), kpm = kp, kym = ky;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    kr = min(kr, __shfl_xor_sync(0xffffffffu, kr, o));
+    kms = min(kms, __shfl_xor_sync(0xffffffffu, kms, o));
+    kpm = min(kpm, __shfl_xor_sync(0xffffffffu, kpm, o));
+    kym = min(kym, __shfl_xor_sync(0xffffffffu, kym, o));
+  }
+  // the selected points' FP64 values, from their lanes
+  double psel = INFINITY, ysel = INFINITY, sdir = INFINITY;
+  if (qp >= 0 && kp == kpm) {
+    double w[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) w[k] = to_f64(v[qp][k]);
+    psel = pressure64(w, g);
+  }
+  if (qy >= 0 && ky == kym) {
+    double w[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) w[k] = to_f64(v[qy][k]);
+    const double rr64 = rcp64(w[0], sizeof(T) == 4 ? float(v[qy][0]) : narrow_f64(w[0]));
+    const double p64 = (g - 1.0) * (w[4] - 0.5 * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]) * rr64);
+    if (s5_in_range(p64, rr64)) ysel = s5_of(p64, rr64);
+    else sdir = p64 * pow(w[0], -g);
+  }
+  const bool hp = kpm != 0x7fffffffffffffffLL, hy = kym != 0x7fffffffffffffffLL;
+  psel = __shfl_sync(0xffffffffu, psel, hp ? int(kpm & 0x1f) : 0);
+  ysel = __shfl_sync(0xffffffffu, ysel, hy ? int(kym & 0x1f) : 0);
+  sdir = __shfl_sync(0xffffffffu, sdir, hy ? int(kym & 0x1f) : 0);
+  *r_out = dunkey(kr);
+  *p_out = hp ? psel : INFINITY;
+  *s_out = fmin(dunkey(kms), hy ? sdir : INFINITY);
+  *ys_out = hy ? ysel : INFINITY;
+}
+
+// The zeta = 0 test of every element of a type, one warp per element, on
+// the stage value (reg / regR) at the solution points and its flux-point
+// traces (uf, from the volume kernel): elements that meet the constraints
+// are left alone (zeta 0, one evaluation); the others are listed for
+// k_filter, which takes the oracle's modal form from there.
+template <typename T, typename TR, int NU, int NF>
+__global__ void k_filter_check(long long ne, const T* __restrict__ reg,
+                               const TR* __restrict__ regR, const T* __restrict__ uf,
+                               FilterArgs fa, int32_t* __restrict__ list,
+                               int* __restrict__ count) {
+  constexpr int NP = NU + NF, NQ = (NP + 31) / 32;
+  const int lane = threadIdx.x & 31;
+  const long long e = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (e >= ne) return;  // whole warps
+  const double g = fa.gamma;
+  const float gf = float(g);
+  const bool by5 = entropy_by_s5(g);
+  const float gm1h = float(g - 1.0);
+  const dfl gm1d{gm1h, float((g - 1.0) - widen_f32(gm1h))};
+  const double smin = fa.smin[e];
+  const double sb = smin * (1.0 - fa.tau);
+  T v[NQ][5];
+  PtScreen sc[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int i = lane + 32 * q;
+    sc[q].pos = false;
+    sc[q].plo = sc[q].slo = INFINITY;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) v[q][k] = T(0);
+    if (i >= NP) continue;
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+      v[q][k] = i < NU ? (reg ? reg[(e * 5 + k) * NU + i] : T(regR[(e * 5 + k) * NU + i]))
+                       : uf[(e * 5 + k) * NF + (i - NU)];
+    sc[q] = screen_point(float(v[q][0]), float(v[q][1]), float(v[q][2]), float(v[q][3]),
+                         float(v[q][4]), gf);
+  }
+  double r, p, sdir, ys;
+  warp_minima<T, NQ, NP>(v, sc, smin, g, by5, gm1d, &r, &p, &sdir, &ys);
+  if (lane != 0) return;
+  double s_term = INFINITY;
+  if (smin > 0.0) {
+    const double sb2 = sb * sb, sb5 = sb2 * sb2 * sb;
+    s_term = (sdir >= sb && !(ys < sb5)) ? 0.0 : -1.0;
+  }
+  const double gm = fmin(r - kEpsPos, fmin(p - kEpsPos, s_term));
+  if (!isnan(gm) && gm >= 0.0) {
+    if (fa.zeta_last) {
+      fa.zeta_last[e] = 0.f;
+      fa.evals_last[e] = 1;
+    }
+  } else {
+    list[atomicAdd(count, 1)] = int32_t(e);
+  }
+}
+
 // Filter the stage value of each element that violates the constraints.
 // reg / regR: the register holding the new stage value (type T or TR, one
 // of them null); uf: this type's flux-point traces of that value.
 template <typename T, typename TR, int NU, int NF>
 __global__ void __launch_bounds__(kFilterThreads)
     k_filter(long long ne, T* __restrict__ reg, TR* __restrict__ regR,
-             T* __restrict__ uf, FilterOps<T> op, FilterArgs fa) {
+             T* __restrict__ uf, FilterOps<T> op, FilterArgs fa,
+             const int32_t* __restrict__ list, const int* __restrict__ count) {
   constexpr int NM = NU, NP = NU + NF;
   __shared__ T uh[5][NM];       // modal coefficients
   __shared__ T sg[NM];          // filtered weights sigma_k
@@ -569,7 +757,9 @@ __global__ void __launch_bounds__(kFilterThreads)
   __shared__ long long redk[4 * (kFilterThreads / 32)];
   __shared__ float redf[2 * (kFilterThreads / 32)];
   __shared__ double s_z;        // requested strength
-  const long long e = blockIdx.x;
+  // CTA b filters element list[b] of the k_filter_check list
+  if (int(blockIdx.x) >= *count) return;
+  const long long e = list[blockIdx.x];
   const int tid = threadIdx.x;
   if (e >= ne) return;
   const double g = fa.gamma;
@@ -596,17 +786,12 @@ __global__ void __launch_bounds__(kFilterThreads)
   auto smin_of = [](const Mins& q) -> double {
     return q.ys < INFINITY ? fmin(q.s, s_of_s5(q.ys)) : q.s;
   };
-  // direct: the stage value itself at the solution points (reg) and its
-  // flux-point traces (uf, from the volume kernel) instead of the modal
-  // evaluation (the same polynomial, other rounding)
-  auto minima = [&](double z, bool direct) -> Mins {
-    if (!direct) {
-      for (int m = tid; m < NM; m += kFilterThreads) {
-        double d = double(op.deg[m]);
-        sg[m] = sizeof(T) == 4 ? T(__expf(-float(z * d * d))) : T(exp(-z * d * d));
-      }
-      __syncthreads();
+  auto minima = [&](double z) -> Mins {
+    for (int m = tid; m < NM; m += kFilterThreads) {
+      double d = double(op.deg[m]);
+      sg[m] = sizeof(T) == 4 ? T(__expf(-float(z * d * d))) : T(exp(-z * d * d));
     }
+    __syncthreads();
     T v[NPT][5];
     PtScreen sc[NPT];
     T rmin_t = T(INFINITY);
@@ -619,17 +804,10 @@ __global__ void __launch_bounds__(kFilterThreads)
       sc[q].pos = false;
       sc[q].plo = sc[q].slo = INFINITY;  // no point: never a candidate
       if (i >= NP) continue;
-      if (direct) {
+      for (int m = 0; m < NM; ++m) {
+        T w = op.VT[m * NP + i] * sg[m];
 #pragma unroll
-        for (int k = 0; k < 5; ++k)
-          v[q][k] = i < NU ? (reg ? reg[(e * 5 + k) * NU + i] : T(regR[(e * 5 + k) * NU + i]))
-                           : uf[(e * 5 + k) * NF + (i - NU)];
-      } else {
-        for (int m = 0; m < NM; ++m) {
-          T w = op.VT[m * NP + i] * sg[m];
-#pragma unroll
-          for (int k = 0; k < 5; ++k) v[q][k] += w * uh[k][m];
-        }
+        for (int k = 0; k < 5; ++k) v[q][k] += w * uh[k][m];
       }
       rmin_t = sizeof(T) == 4 ? T(fminf(float(rmin_t), float(v[q][0])))
                               : T(fmin(double(rmin_t), double(v[q][0])));
@@ -789,12 +967,8 @@ __global__ void __launch_bounds__(kFilterThreads)
       fa.evals_last[e] = 1;
     }
   };
-  // Most elements pass at zeta = 0: test the stage value and its traces
-  // directly, before any modal transform.
-  if (admissible(minima(0.0, true))) {
-    leave_unfiltered();
-    return;
-  }
+  // (k_filter_check left the elements that pass at zeta = 0 on the stage
+  // value and its traces alone)
   // modal coefficients u^ = V^-1 u
   for (int z = tid; z < NU; z += kFilterThreads)
 #pragma unroll
@@ -812,7 +986,7 @@ __global__ void __launch_bounds__(kFilterThreads)
     for (int k = 0; k < 5; ++k) uh[k][m] = acc[k];
   }
   // the same test on the modal evaluation (the oracle's form)
-  Mins m0 = minima(0.0, false);
+  Mins m0 = minima(0.0);
   if (admissible(m0)) {
     leave_unfiltered();
     return;
@@ -843,7 +1017,7 @@ __global__ void __launch_bounds__(kFilterThreads)
     if (isnan(gm)) gm = -INFINITY;
     return gm;
   };
-  auto margin = [&](double z) -> double { return gval(minima(z, false)); };
+  auto margin = [&](double z) -> double { return gval(minima(z)); };
   // predictor inputs from the unfiltered state (z = 0)
   float feat[4] = {0.f, 0.f, 0.f, 0.f};
   if (fa.mlp || fa.samples) {
@@ -908,7 +1082,7 @@ __global__ void __launch_bounds__(kFilterThreads)
     __syncthreads();
     if (!s_go) break;
     const double z = s_next;
-    const Mins mz = minima(z, false);  // ends with a barrier: s_next / s_go reusable
+    const Mins mz = minima(z);  // ends with a barrier: s_next / s_go reusable
     if (tid != 0) continue;
     const double gz = gval(mz);
     ++evals;

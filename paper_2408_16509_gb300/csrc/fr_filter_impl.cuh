@@ -30,6 +30,8 @@ int setup_filter(fr_mesh* m) {
     if ((rc = dev_zeros(m, size_t(D.ne) * sizeof(double), (void**)&D.smin))) return rc;
     if ((rc = dev_zeros(m, size_t(D.ne) * sizeof(float), (void**)&D.zeta_last))) return rc;
     if ((rc = dev_zeros(m, size_t(D.ne) * sizeof(int), (void**)&D.evals_last))) return rc;
+    if ((rc = dev_zeros(m, size_t(D.ne) * sizeof(int32_t), (void**)&D.flist))) return rc;
+    if ((rc = dev_zeros(m, sizeof(int), (void**)&D.fcount))) return rc;
   }
   // partner flux point of every element flux point (-1 on boundaries)
   for (size_t t = 0; t < m->types.size(); ++t) {
@@ -94,10 +96,15 @@ void launch_filter(fr_mesh* m, cudaStream_t s, DevType& D, bool last_stage) {
   T* uf = (T*)m->uf + D.off_f;
   T* reg = last_stage ? nullptr : (T*)D.Y;
   TR* regR = last_stage ? (TR*)D.X : nullptr;
+  // the zeta = 0 test of every element (a warp each), then k_filter on the
+  // elements it lists (one CTA per element; CTAs past the count return)
+  cudaMemsetAsync(D.fcount, 0, sizeof(int), s);
   dispatch(D.kind, m->order, [&](auto nu, auto nf) {
     constexpr int NU = decltype(nu)::value, NF = decltype(nf)::value;
+    k_filter_check<T, TR, NU, NF><<<nblk(D.ne * 32, 256), 256, 0, s>>>(
+        D.ne, reg, regR, uf, fa, D.flist, D.fcount);
     k_filter<T, TR, NU, NF><<<unsigned(D.ne), kFilterThreads, 0, s>>>(
-        D.ne, reg, regR, uf, op, fa);
+        D.ne, reg, regR, uf, op, fa, D.flist, D.fcount);
   });
 }
 

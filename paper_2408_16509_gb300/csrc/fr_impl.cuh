@@ -104,6 +104,8 @@ struct DevType {
   void* fdeg = nullptr;
   void* fW = nullptr;
   int32_t* fpartner = nullptr;
+  int32_t* flist = nullptr;  // [ne] elements that fail the zeta = 0 test
+  int* fcount = nullptr;     // their number
   double* smin = nullptr;
   float* zeta_last = nullptr;
   int* evals_last = nullptr;
