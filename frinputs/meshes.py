@@ -293,6 +293,33 @@ _Q2_REF = {
 }
 
 
+def _simplex_cubic_ref(verts, edges, faces):
+    v = np.asarray(verts, float)
+    out = list(v)
+    for a, b in edges:
+        out += [(2 * v[a] + v[b]) / 3, (v[a] + 2 * v[b]) / 3]
+    out += [v[list(f)].mean(axis=0) for f in faces]
+    return np.array(out)
+
+
+# reference coordinates of the cubic map nodes, in the library's node order:
+# hexahedra a + 4b + 16c at (-1 + 2a/3, ...); prisms triangle node + 10 *
+# layer (triangle: vertices, two nodes on each of the edges 01, 12, 02 -- the
+# one nearer the edge's first vertex first -- and the centroid; layers z =
+# -1, -1/3, 1/3, 1); tetrahedra: vertices, two nodes on each of the edges
+# 01, 12, 02, 03, 13, 23, the centroids of the faces 012, 013, 023, 123
+_THIRDS = (-1.0, -1.0 / 3.0, 1.0 / 3.0, 1.0)
+_TRI3 = _simplex_cubic_ref([(-1, -1), (1, -1), (-1, 1)], [(0, 1), (1, 2), (0, 2)],
+                           [(0, 1, 2)])
+_Q3_REF = {
+    "hex": np.array([[a, b, c] for c in _THIRDS for b in _THIRDS for a in _THIRDS]),
+    "pri": np.array([[x, y, z] for z in _THIRDS for x, y in _TRI3]),
+    "tet": _simplex_cubic_ref([(-1, -1, -1), (1, -1, -1), (-1, 1, -1), (-1, -1, 1)],
+                              [(0, 1), (1, 2), (0, 2), (0, 3), (1, 3), (2, 3)],
+                              [(0, 1, 2), (0, 1, 3), (0, 2, 3), (1, 2, 3)]),
+}
+
+
 def _linear_shape(kind, x):
     """Linear (vertex) shape functions of the reference element at x (n, 3)."""
     if kind == "hex":
@@ -307,17 +334,19 @@ def _linear_shape(kind, x):
                      (1 + x[:, 1]) / 2, (1 + x[:, 2]) / 2], axis=1)
 
 
-def curved_mixed_box(n=8, x_pri=0.34, x_tet=0.67, amp=0.05, periodic_x=False):
+def curved_mixed_box(n=8, x_pri=0.34, x_tet=0.67, amp=0.05, periodic_x=False,
+                     order=2):
     """The mixed_box layout (hexahedra, prisms, Kuhn tetrahedra; no vertex
-    jitter) with quadratic maps on every element: 27-node hexahedra, 18-node
-    prisms, 10-node tetrahedra.  All map nodes lie on the (2n+1)^3 lattice
-    of half-cell points (vertices, edge midpoints, face and cell centres),
-    displaced by the smooth field of curved_box_hex (corners stay on the
-    grid), so neighbouring elements share their face nodes."""
+    jitter) with curved maps on every element: order 2, 27-node hexahedra,
+    18-node prisms, 10-node tetrahedra; order 3, 64-node hexahedra, 40-node
+    prisms, 20-node tetrahedra.  All map nodes lie on the (order n + 1)^3
+    lattice of the cells' 1/order points (vertices, edge, face and cell
+    points), displaced by the smooth field of curved_box_hex (corners stay on
+    the grid), so neighbouring elements share their face nodes."""
+    o = int(order)
     coarse = mixed_box(n=n, x_pri=x_pri, x_tet=x_tet, perturb=0.0,
                        periodic_x=periodic_x)
-    N = (n, n, n)
-    m = (2 * n, 2 * n, 2 * n)
+    m = (o * n, o * n, o * n)
     lat = _grid_nodes(m, (0, 0, 0), (1, 1, 1))
     h = np.full(3, 1.0 / n)
     X = lat
@@ -329,8 +358,8 @@ def curved_mixed_box(n=8, x_pri=0.34, x_tet=0.67, amp=0.05, periodic_x=False):
     g = _nid(m)
     # lattice coordinates of the coarse grid's nodes
     ci = np.arange((n + 1) ** 3)
-    cl = np.stack([2 * (ci % (n + 1)), 2 * ((ci // (n + 1)) % (n + 1)),
-                   2 * (ci // (n + 1) ** 2)], axis=1)
+    cl = o * np.stack([ci % (n + 1), (ci // (n + 1)) % (n + 1),
+                       ci // (n + 1) ** 2], axis=1)
 
     def lid(c):
         return g(c[..., 0], c[..., 1], c[..., 2])
@@ -338,12 +367,12 @@ def curved_mixed_box(n=8, x_pri=0.34, x_tet=0.67, amp=0.05, periodic_x=False):
     for kind, conn in coarse.elements.items():
         if len(conn) == 0:
             continue
-        Nl = _linear_shape(kind, _Q2_REF[kind])            # (n_map, n_vert)
+        Nl = _linear_shape(kind, (_Q2_REF if o == 2 else _Q3_REF)[kind])  # (n_map, n_vert)
         vc = cl[conn]                                      # (ne, n_vert, 3)
         q = np.einsum("mv,evk->emk", Nl, vc)
         qi = np.rint(q).astype(np.int64)
         assert np.abs(q - qi).max() < 1e-9
-        maps[kind] = (2, lid(qi))
+        maps[kind] = (o, lid(qi))
         elements[kind] = lid(vc)
     bf = [(tuple(int(lid(cl[v])) for v in ids), tag) for ids, tag in coarse.bfaces]
     return MeshSpec(nodes, elements, coarse.periodic, bf, maps)

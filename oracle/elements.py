@@ -82,6 +82,49 @@ def pri_rule(n):
     return pts, w
 
 
+def _cubic_simplex(lam, dlam, edges, faces):
+    """Cubic Lagrange basis on a simplex (a triangle or a tetrahedron) from
+    its barycentric coordinates lam (npts, n_vertices), whose gradients
+    dlam[v] are constant.  Nodes, in this order: the vertices; two per edge
+    (a, b), at barycentric (2/3, 1/3) then (1/3, 2/3) of its two vertices;
+    the centroid of each face (a, b, c).  Basis: 9/2 l (l - 1/3)(l - 2/3)
+    at a vertex, 27/2 l_a l_b (l_a - 1/3) at an edge node nearer a,
+    27 l_a l_b l_c at a face centroid.  Returns the values (npts, n) and the
+    derivatives (ndim, npts, n)."""
+    ndim = len(dlam[0])
+    vals, ders = [], [[] for _ in range(ndim)]
+
+    def push(v, grad_by_vertex):
+        vals.append(v)
+        for j in range(ndim):
+            ders[j].append(sum(g * dlam[w][j] for w, g in grad_by_vertex))
+
+    for v in range(lam.shape[1]):
+        lv = lam[:, v]
+        push(0.5 * lv * (3 * lv - 1) * (3 * lv - 2),
+             [(v, 0.5 * (27 * lv * lv - 18 * lv + 2))])
+    for a, b in edges:
+        for s, t in ((a, b), (b, a)):
+            ls, lt = lam[:, s], lam[:, t]
+            push(4.5 * ls * lt * (3 * ls - 1),
+                 [(s, 4.5 * lt * (6 * ls - 1)), (t, 4.5 * ls * (3 * ls - 1))])
+    for a, b, c in faces:
+        la, lb, lc = lam[:, a], lam[:, b], lam[:, c]
+        push(27 * la * lb * lc, [(a, 27 * lb * lc), (b, 27 * la * lc), (c, 27 * la * lb)])
+    return np.stack(vals, axis=1), np.stack([np.stack(d, axis=1) for d in ders])
+
+
+def _cubic_simplex_nodes(verts, edges, faces):
+    """Reference coordinates of the nodes of _cubic_simplex."""
+    v = np.asarray(verts, float)
+    out = list(v)
+    for a, b in edges:
+        out += [(2 * v[a] + v[b]) / 3, (v[a] + 2 * v[b]) / 3]
+    for f in faces:
+        out.append(v[list(f)].mean(axis=0))
+    return np.array(out)
+
+
 class Face:
     """One face of a reference element: 2D parameterisation -> 3D."""
 
@@ -398,6 +441,35 @@ class Prism(ElementType):
                          np.einsum("pl,pa->pla", lv, tg[1]).reshape(len(x), 18),
                          np.einsum("pl,pa->pla", ld, tv).reshape(len(x), 18)])
 
+    # cubic map (40 nodes): the cubic triangle of _cubic_simplex (vertices
+    # 0, 1, 2; edges 01, 12, 02; the centroid) times the cubic line
+    # (z = -1, -1/3, 1/3, 1), node = triangle node + 10 * layer; the corners
+    # are nodes 0, 1, 2, 30, 31, 32
+    TRI = ((-1.0, -1.0), (1.0, -1.0), (-1.0, 1.0))
+    TRI_EDGES = ((0, 1), (1, 2), (0, 2))
+
+    def q3_nodes(self):
+        tri = _cubic_simplex_nodes(self.TRI, self.TRI_EDGES, [(0, 1, 2)])
+        return np.concatenate([np.column_stack([tri, np.full(10, z)])
+                               for z in (-1.0, -1.0 / 3.0, 1.0 / 3.0, 1.0)])
+
+    def _q3_parts(self, x):
+        lam = self._bary(x)
+        dlam = [(-0.5, -0.5), (0.5, 0.0), (0.0, 0.5)]
+        tv, tg = _cubic_simplex(lam, dlam, self.TRI_EDGES, [(0, 1, 2)])
+        lv, ld = Hex._lag3(x[:, 2])
+        return tv, tg, lv, ld
+
+    def q3_shape(self, x):
+        tv, _, lv, _ = self._q3_parts(x)
+        return np.einsum("pl,pa->pla", lv, tv).reshape(len(x), 40)
+
+    def q3_dshape(self, x):
+        tv, tg, lv, ld = self._q3_parts(x)
+        return np.stack([np.einsum("pl,pa->pla", lv, tg[0]).reshape(len(x), 40),
+                         np.einsum("pl,pa->pla", lv, tg[1]).reshape(len(x), 40),
+                         np.einsum("pl,pa->pla", ld, tv).reshape(len(x), 40)])
+
     def curl_nodes(self):
         """Nodes of the curl-form metric interpolant: the tetrahedron's face
         node set on the triangle times Gauss-Lobatto points along z (nodes
@@ -478,6 +550,24 @@ class Tet(ElementType):
                  np.stack([4 * (d[:, a] * lam[:, b] + lam[:, a] * d[:, b])
                            for a, b in self.EDGES], axis=1)], axis=1))
         return np.stack(out)
+
+    # cubic map (20 nodes): _cubic_simplex on the vertices, the edges above
+    # (two nodes each) and the faces 012, 013, 023, 123 (their centroids)
+    FACES3 = ((0, 1, 2), (0, 1, 3), (0, 2, 3), (1, 2, 3))
+    VERTS = ((-1.0, -1.0, -1.0), (1.0, -1.0, -1.0), (-1.0, 1.0, -1.0), (-1.0, -1.0, 1.0))
+
+    def q3_nodes(self):
+        return _cubic_simplex_nodes(self.VERTS, self.EDGES, self.FACES3)
+
+    def _q3(self, x):
+        dlam = [(-0.5, -0.5, -0.5), (0.5, 0.0, 0.0), (0.0, 0.5, 0.0), (0.0, 0.0, 0.5)]
+        return _cubic_simplex(self.shape(x), dlam, self.EDGES, self.FACES3)
+
+    def q3_shape(self, x):
+        return self._q3(x)[0]
+
+    def q3_dshape(self, x):
+        return self._q3(x)[1]
 
     def curl_nodes(self):
         """Nodes of the curl-form metric interpolant: the warp-and-blend

@@ -51,8 +51,8 @@ def curl_metric(el, Xm, pts, order=2):
     only, so neighbours agree): the (p+1)^3 Gauss-Lobatto nodes on
     hexahedra, el.curl_nodes() on prisms and tetrahedra; then
     S[i][n] = -(curl_xi of it)_i at pts.  Returns S[e, q, i, n]
-    (= det J dxi_i/dx_n).  order: 2 (quadratic maps) or 3 (cubic
-    hexahedra, 64 nodes)."""
+    (= det J dxi_i/dx_n).  order: 2 (quadratic maps) or 3 (cubic maps:
+    64-node hexahedra, 40-node prisms, 20-node tetrahedra)."""
     shape, dshape = _map_fns(el, order)
     if el.name != "hex":
         G = el.curl_nodes()
@@ -128,8 +128,6 @@ class FRMesh:
             el, V = self.el[t], self.verts[t]
             morder, mconn = maps.get(t, (1, None))
             self.curved[t] = morder >= 2
-            if morder == 3 and t != "hex":
-                raise MeshError("cubic maps are implemented for hexahedra")
             if morder in (2, 3):
                 shape, dshape = _map_fns(el, morder)
                 Xm = nodes[np.asarray(mconn, np.int64)]
