@@ -65,9 +65,8 @@ typedef struct {
   const int64_t* conn;  /* [n_elem][n_vertices] node ids (face pairing; and
                            the map of straight elements) */
   int map_order;        /* 0 or 1: straight elements (vertex map); 2:
-                           quadratic map, 3: cubic map (hexahedra only)
-                           (Section 3.4 "Curved Elements") given by
-                           map_conn */
+                           quadratic map, 3: cubic map (Section 3.4
+                           "Curved Elements") given by map_conn */
   const int64_t* map_conn;  /* map_order 2 or 3: [n_elem][n_map] node ids of
                                the map; its vertex nodes must be the vertices
                                of conn.
@@ -81,6 +80,16 @@ typedef struct {
                                vertices are nodes 0, 1, 2, 12, 13, 14);
                                FR_TET4, 10 nodes: v0..v3, then the midpoints
                                of edges 01, 12, 02, 03, 13, 23.
+                               Order 3: FR_PRI6, 40 nodes: triangle node +
+                               10 layer, layers z = -1, -1/3, 1/3, 1,
+                               triangle nodes v0, v1, v2, two on each of the
+                               edges 01, 12, 02 (at 1/3 then 2/3 of the way
+                               from the edge's first vertex) and the
+                               centroid (the vertices are nodes 0, 1, 2, 30,
+                               31, 32); FR_TET4, 20 nodes: v0..v3, two on
+                               each of the edges 01, 12, 02, 03, 13, 23 (in
+                               the same way), the centroids of the faces 012,
+                               013, 023, 123.
                                Metrics of curved elements: the conservative
                                curl form S[i][n] = -(curl I(X_l grad X_m))_i,
                                I the order-p interpolant on nodes with nodes

@@ -15,6 +15,9 @@ FR_OK = 0
 ERRORS = {-1: "FR_EINVAL", -2: "FR_ENOMEM", -3: "FR_ECUDA", -4: "FR_EMESH",
           -5: "FR_ENONFINITE", -6: "FR_EFILTER", -7: "FR_ETIMEOUT"}
 ETYPES = {"hex": 0, "pri": 1, "tet": 2}
+# map nodes of curved elements per (type, map order)
+MAP_NODES = {("hex", 2): 27, ("hex", 3): 64, ("pri", 2): 18, ("pri", 3): 40,
+             ("tet", 2): 10, ("tet", 3): 20}
 PHYSICS = {"euler": 0, "ns": 1}
 PRECISION = {"fp64": 0, "fp32": 1, "mixed": 2}
 VARIANTS = {"auto": 0, "dense": 1, "sumfact": 2, "sumfact_vertex": 3,
@@ -208,6 +211,10 @@ class FRMesh:
             mptr = None
             if morder >= 2:
                 mconn = np.ascontiguousarray(mconn, np.int64)
+                nmap = MAP_NODES.get((name, int(morder)))
+                if nmap is None or mconn.shape != (len(conn), nmap):
+                    raise FRError(-1, f"{name} map of order {morder}: map connectivity "
+                                      f"of shape {mconn.shape}, expected ({len(conn)}, {nmap})")
                 self._keep.append(mconn)
                 mptr = mconn.ctypes.data_as(C.POINTER(C.c_int64))
             ets.append(EtypeDesc(ETYPES[name], len(conn),

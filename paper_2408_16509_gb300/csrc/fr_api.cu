@@ -55,8 +55,6 @@ int fr_mesh_create(const fr_mesh_desc* d, fr_mesh** out) {
     if (t.n_elem < 0 || (t.n_elem > 0 && !t.conn)) return fail(FR_EINVAL, "bad connectivity");
     if (t.map_order < 0 || t.map_order > 3)
       return fail(FR_EINVAL, "map order must be 0, 1, 2 or 3");
-    if (t.map_order == 3 && t.etype != FR_HEX8)
-      return fail(FR_EINVAL, "cubic maps: hexahedra only");
     if (t.map_order >= 2 && t.n_elem > 0 && !t.map_conn)
       return fail(FR_EINVAL, "curved maps need map_conn");
     seen[t.etype] = true;

@@ -299,70 +299,134 @@ void parallel_elements(int64_t ne, F body) {
   for (auto& th : pool) th.join();
 }
 
-// Number of map nodes of a quadratic element and the map node of each vertex.
-int q2_nodes(int kind, int order = 2) {
+// Number of map nodes of a curved element of map order 2 or 3 and the map
+// node of each vertex.
+int map_nodes(int kind, int order) {
   if (kind == EK_HEX) return (order + 1) * (order + 1) * (order + 1);
-  return kind == EK_PRI ? 18 : 10;
+  if (kind == EK_PRI) return order == 3 ? 40 : 18;
+  return order == 3 ? 20 : 10;
 }
-const int* q2_corners(int kind, int order = 2) {
+const int* map_corners(int kind, int order) {
   static const int hexc[8] = {0, 2, 8, 6, 18, 20, 26, 24};
   static const int hex3[8] = {0, 3, 15, 12, 48, 51, 63, 60};
   static const int pric[6] = {0, 1, 2, 12, 13, 14};
+  static const int pri3[6] = {0, 1, 2, 30, 31, 32};
   static const int tetc[4] = {0, 1, 2, 3};
   if (kind == EK_HEX) return order == 3 ? hex3 : hexc;
-  return kind == EK_PRI ? pric : tetc;
+  if (kind == EK_PRI) return order == 3 ? pri3 : pric;
+  return tetc;
 }
 
-// x_k(pt) and a[j][k] = d x_k / d xi_j of a quadratic prism (18 nodes:
-// triangle node + 6 layer, triangle nodes v0 v1 v2 and the midpoints of
-// edges 01, 12, 02, layers z = -1, 0, 1) or tetrahedron (10 nodes: the
-// vertices, then the midpoints of edges 01, 12, 02, 03, 13, 23).
-void q2s_eval(int kind, const double* X, const double* pt, double x[3], double a[3][3]) {
-  double N[18], dN[3][18];
+// Cubic Lagrange basis of a triangle (nv = 3) or tetrahedron (nv = 4) from
+// its barycentric coordinates lam[nv], whose gradients dl[nv][3] are
+// constant.  Nodes: the vertices; two per edge (a, b), at barycentric
+// (2/3, 1/3) then (1/3, 2/3) of a and b; the centroid of each face.  Basis:
+// l (3l - 1)(3l - 2) / 2 at a vertex, 9/2 l_a l_b (3 l_a - 1) at an edge
+// node nearer a, 27 l_a l_b l_c at a centroid.  N[n], dN[3][kMaxSimplexMap].
+constexpr int kMaxSimplexMap = 20;
+int cubic_simplex(int nv, const double* lam, const double (*dl)[3], int nedge,
+                  const int (*E)[2], int nface, const int (*F)[3], double* N,
+                  double (*dN)[kMaxSimplexMap]) {
+  int k = 0;
+  for (int v = 0; v < nv; ++v, ++k) {
+    const double l = lam[v], g = 0.5 * (27 * l * l - 18 * l + 2);
+    N[k] = 0.5 * l * (3 * l - 1) * (3 * l - 2);
+    for (int j = 0; j < 3; ++j) dN[j][k] = g * dl[v][j];
+  }
+  for (int e = 0; e < nedge; ++e)
+    for (int side = 0; side < 2; ++side, ++k) {
+      const int a = E[e][side], b = E[e][1 - side];
+      const double la = lam[a], lb = lam[b];
+      N[k] = 4.5 * la * lb * (3 * la - 1);
+      const double ga = 4.5 * lb * (6 * la - 1), gb = 4.5 * la * (3 * la - 1);
+      for (int j = 0; j < 3; ++j) dN[j][k] = ga * dl[a][j] + gb * dl[b][j];
+    }
+  for (int f = 0; f < nface; ++f, ++k) {
+    const int a = F[f][0], b = F[f][1], c = F[f][2];
+    const double la = lam[a], lb = lam[b], lc = lam[c];
+    N[k] = 27 * la * lb * lc;
+    for (int j = 0; j < 3; ++j)
+      dN[j][k] = 27 * (lb * lc * dl[a][j] + la * lc * dl[b][j] + la * lb * dl[c][j]);
+  }
+  return k;
+}
+
+// x_k(pt) and a[j][k] = d x_k / d xi_j of a curved prism or tetrahedron.
+// Quadratic prism (18 nodes): triangle node + 6 layer, triangle nodes v0 v1
+// v2 and the midpoints of edges 01, 12, 02, layers z = -1, 0, 1; quadratic
+// tetrahedron (10 nodes): the vertices, then the midpoints of edges 01, 12,
+// 02, 03, 13, 23.  Cubic prism (40 nodes): triangle node + 10 layer, the
+// cubic triangle of cubic_simplex on edges 01, 12, 02 and face 012, layers
+// z = -1, -1/3, 1/3, 1; cubic tetrahedron (20 nodes): cubic_simplex on
+// edges 01, 12, 02, 03, 13, 23 and faces 012, 013, 023, 123.
+void simplex_map_eval(int kind, int order, const double* X, const double* pt, double x[3],
+                      double a[3][3]) {
+  double N[40], dN[3][40];
   int nn;
+  static const int TE[6][2] = {{0, 1}, {1, 2}, {0, 2}, {0, 3}, {1, 3}, {2, 3}};
   if (kind == EK_TET) {
-    nn = 10;
     const double lam[4] = {-(1 + pt[0] + pt[1] + pt[2]) / 2, (1 + pt[0]) / 2,
                            (1 + pt[1]) / 2, (1 + pt[2]) / 2};
     const double dl[4][3] = {{-0.5, -0.5, -0.5}, {0.5, 0, 0}, {0, 0.5, 0}, {0, 0, 0.5}};
-    static const int E[6][2] = {{0, 1}, {1, 2}, {0, 2}, {0, 3}, {1, 3}, {2, 3}};
-    for (int v = 0; v < 4; ++v) {
-      N[v] = lam[v] * (2 * lam[v] - 1);
-      for (int j = 0; j < 3; ++j) dN[j][v] = (4 * lam[v] - 1) * dl[v][j];
-    }
-    for (int e = 0; e < 6; ++e) {
-      const int p0 = E[e][0], p1 = E[e][1];
-      N[4 + e] = 4 * lam[p0] * lam[p1];
-      for (int j = 0; j < 3; ++j) dN[j][4 + e] = 4 * (dl[p0][j] * lam[p1] + lam[p0] * dl[p1][j]);
+    if (order == 3) {
+      static const int TF[4][3] = {{0, 1, 2}, {0, 1, 3}, {0, 2, 3}, {1, 2, 3}};
+      double Nc[kMaxSimplexMap], dNc[3][kMaxSimplexMap];
+      nn = cubic_simplex(4, lam, dl, 6, TE, 4, TF, Nc, dNc);
+      for (int v = 0; v < nn; ++v) {
+        N[v] = Nc[v];
+        for (int j = 0; j < 3; ++j) dN[j][v] = dNc[j][v];
+      }
+    } else {
+      nn = 10;
+      for (int v = 0; v < 4; ++v) {
+        N[v] = lam[v] * (2 * lam[v] - 1);
+        for (int j = 0; j < 3; ++j) dN[j][v] = (4 * lam[v] - 1) * dl[v][j];
+      }
+      for (int e = 0; e < 6; ++e) {
+        const int p0 = TE[e][0], p1 = TE[e][1];
+        N[4 + e] = 4 * lam[p0] * lam[p1];
+        for (int j = 0; j < 3; ++j) dN[j][4 + e] = 4 * (dl[p0][j] * lam[p1] + lam[p0] * dl[p1][j]);
+      }
     }
   } else {
-    nn = 18;
-    const double l0 = -(pt[0] + pt[1]) / 2, l1 = (1 + pt[0]) / 2, l2 = (1 + pt[1]) / 2;
-    const double d0[2] = {-0.5, -0.5}, d1[2] = {0.5, 0.0}, d2[2] = {0.0, 0.5};
-    double T[6], dT[2][6];
-    T[0] = l0 * (2 * l0 - 1);
-    T[1] = l1 * (2 * l1 - 1);
-    T[2] = l2 * (2 * l2 - 1);
-    T[3] = 4 * l0 * l1;
-    T[4] = 4 * l1 * l2;
-    T[5] = 4 * l0 * l2;
-    for (int j = 0; j < 2; ++j) {
-      dT[j][0] = (4 * l0 - 1) * d0[j];
-      dT[j][1] = (4 * l1 - 1) * d1[j];
-      dT[j][2] = (4 * l2 - 1) * d2[j];
-      dT[j][3] = 4 * (d0[j] * l1 + l0 * d1[j]);
-      dT[j][4] = 4 * (d1[j] * l2 + l1 * d2[j]);
-      dT[j][5] = 4 * (d0[j] * l2 + l0 * d2[j]);
-    }
+    const double lam[3] = {-(pt[0] + pt[1]) / 2, (1 + pt[0]) / 2, (1 + pt[1]) / 2};
+    const double dl[3][3] = {{-0.5, -0.5, 0.0}, {0.5, 0.0, 0.0}, {0.0, 0.5, 0.0}};
+    double T[kMaxSimplexMap], dT[3][kMaxSimplexMap], L[4], dL[4];
+    int nt, nl;
     const double t = pt[2];
-    const double L[3] = {0.5 * t * (t - 1), 1 - t * t, 0.5 * t * (t + 1)};
-    const double dL[3] = {t - 0.5, -2 * t, t + 0.5};
-    for (int l = 0; l < 3; ++l)
-      for (int q = 0; q < 6; ++q) {
-        N[q + 6 * l] = T[q] * L[l];
-        dN[0][q + 6 * l] = dT[0][q] * L[l];
-        dN[1][q + 6 * l] = dT[1][q] * L[l];
-        dN[2][q + 6 * l] = T[q] * dL[l];
+    if (order == 3) {
+      static const int E[3][2] = {{0, 1}, {1, 2}, {0, 2}};
+      static const int F[1][3] = {{0, 1, 2}};
+      static const double g3[4] = {-1.0, -1.0 / 3.0, 1.0 / 3.0, 1.0};
+      nt = cubic_simplex(3, lam, dl, 3, E, 1, F, T, dT);
+      nl = 4;
+      lagrange1d(4, g3, t, L, dL);
+    } else {
+      nt = 6;
+      nl = 3;
+      for (int v = 0; v < 3; ++v) {
+        T[v] = lam[v] * (2 * lam[v] - 1);
+        for (int j = 0; j < 2; ++j) dT[j][v] = (4 * lam[v] - 1) * dl[v][j];
+      }
+      for (int e = 0; e < 3; ++e) {
+        const int p0 = TE[e][0], p1 = TE[e][1];  // edges 01, 12, 02
+        T[3 + e] = 4 * lam[p0] * lam[p1];
+        for (int j = 0; j < 2; ++j) dT[j][3 + e] = 4 * (dl[p0][j] * lam[p1] + lam[p0] * dl[p1][j]);
+      }
+      L[0] = 0.5 * t * (t - 1);
+      L[1] = 1 - t * t;
+      L[2] = 0.5 * t * (t + 1);
+      dL[0] = t - 0.5;
+      dL[1] = -2 * t;
+      dL[2] = t + 0.5;
+    }
+    nn = nt * nl;
+    for (int l = 0; l < nl; ++l)
+      for (int q = 0; q < nt; ++q) {
+        N[q + nt * l] = T[q] * L[l];
+        dN[0][q + nt * l] = dT[0][q] * L[l];
+        dN[1][q + nt * l] = dT[1][q] * L[l];
+        dN[2][q + nt * l] = T[q] * dL[l];
       }
   }
   for (int k = 0; k < 3; ++k) {
@@ -404,10 +468,10 @@ struct CurlSimplex {
         }
   }
   // w[n][j][node] = X_l d X_m / d xi_j ((n, m, l) cyclic) at the curl nodes
-  void fields(int kind, const double* X, double* w) const {
+  void fields(int kind, int order, const double* X, double* w) const {
     for (int node = 0; node < ng; ++node) {
       double x[3], J[3][3];
-      q2s_eval(kind, X, &G[3 * node], x, J);
+      simplex_map_eval(kind, order, X, &G[3 * node], x, J);
       for (int n = 0; n < 3; ++n) {
         const int m = (n + 1) % 3, l = (n + 2) % 3;
         for (int j = 0; j < 3; ++j) w[(size_t(n) * 3 + j) * ng + node] = x[l] * J[j][m];
@@ -434,7 +498,7 @@ struct CurlSimplex {
 
 void curved_geometry_simplex(HostType& T) {
   const RefElement& R = T.ref;
-  const int nu = R.nupts, nf = R.nfpts, nmap = q2_nodes(T.kind);
+  const int nu = R.nupts, nf = R.nfpts, nmap = map_nodes(T.kind, T.map_order);
   const CurlSimplex C(R);
   std::vector<double> dBu, dBf;
   C.deriv(R, nu, R.upts.data(), dBu);
@@ -448,10 +512,10 @@ void curved_geometry_simplex(HostType& T) {
     std::vector<double> w(size_t(9) * C.ng);
     for (int64_t e = e0; e < e1; ++e) {
       const double* X = &T.mapx[size_t(e) * nmap * 3];
-      C.fields(T.kind, X, w.data());
+      C.fields(T.kind, T.map_order, X, w.data());
       for (int q = 0; q < nu; ++q) {
         double x[3], J[3][3], S[3][3];
-        q2s_eval(T.kind, X, &R.upts[3 * q], x, J);
+        simplex_map_eval(T.kind, T.map_order, X, &R.upts[3 * q], x, J);
         for (int k = 0; k < 3; ++k) T.upts_x[(size_t(e) * nu + q) * 3 + k] = x[k];
         const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
                            J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
@@ -463,7 +527,7 @@ void curved_geometry_simplex(HostType& T) {
       }
       for (int q = 0; q < nf; ++q) {
         double x[3], J[3][3], S[3][3];
-        q2s_eval(T.kind, X, &R.fpts[3 * q], x, J);
+        simplex_map_eval(T.kind, T.map_order, X, &R.fpts[3 * q], x, J);
         for (int k = 0; k < 3; ++k) T.fpts_x[(size_t(e) * nf + q) * 3 + k] = x[k];
         C.eval(&dBf[size_t(q) * 3 * C.ng], w.data(), S);
         const double* n = &R.fnorm[3 * q];
@@ -493,7 +557,7 @@ void curved_geometry(HostType& T) {
   T.fnvec.resize(size_t(T.ne) * nf * 3);
   parallel_elements(T.ne, [&](int64_t e0, int64_t e1) {
     std::vector<double> w(size_t(9) * ng);
-    const int nmap = q2_nodes(EK_HEX, T.map_order);
+    const int nmap = map_nodes(EK_HEX, T.map_order);
     for (int64_t e = e0; e < e1; ++e) {
       const double* X = &T.mapx[size_t(e) * nmap * 3];
       curl_fields(X, g, w.data(), T.map_order);
@@ -529,15 +593,15 @@ void metric_points(const HostType& T, int np, const double* pts,
                    std::vector<double>& S) {
   const RefElement& R = T.ref;
   S.assign(size_t(T.ne) * 9 * np, 0.0);
-  if (T.map_order == 2 && T.kind != EK_HEX) {
+  if (T.map_order >= 2 && T.kind != EK_HEX) {
     const CurlSimplex C(R);
     std::vector<double> dB;
     C.deriv(R, np, pts, dB);
-    const int nmap = q2_nodes(T.kind);
+    const int nmap = map_nodes(T.kind, T.map_order);
     parallel_elements(T.ne, [&](int64_t e0, int64_t e1) {
       std::vector<double> w(size_t(9) * C.ng);
       for (int64_t e = e0; e < e1; ++e) {
-        C.fields(T.kind, &T.mapx[size_t(e) * nmap * 3], w.data());
+        C.fields(T.kind, T.map_order, &T.mapx[size_t(e) * nmap * 3], w.data());
         for (int q = 0; q < np; ++q) {
           double M[3][3];
           C.eval(&dB[size_t(q) * 3 * C.ng], w.data(), M);
@@ -555,7 +619,7 @@ void metric_points(const HostType& T, int np, const double* pts,
     parallel_elements(T.ne, [&](int64_t e0, int64_t e1) {
       std::vector<double> w(size_t(9) * ng);
       for (int64_t e = e0; e < e1; ++e) {
-        curl_fields(&T.mapx[size_t(e) * q2_nodes(EK_HEX, T.map_order) * 3], g, w.data(),
+        curl_fields(&T.mapx[size_t(e) * map_nodes(EK_HEX, T.map_order) * 3], g, w.data(),
                     T.map_order);
         for (int q = 0; q < np; ++q) {
           double M[3][3];
@@ -609,9 +673,8 @@ std::string build_mesh(const MeshInput& in, std::vector<HostType>& types,
     const size_t ti = size_t(&t - in.types.data());
     if (ti < in.map_order.size() && in.map_order[ti] >= 2) {
       T.map_order = in.map_order[ti];
-      if (T.map_order == 3 && T.kind != EK_HEX) return "cubic maps are supported on hexahedra only";
-      const int nmap = q2_nodes(T.kind, T.map_order);
-      const int* corner = q2_corners(T.kind, T.map_order);
+      const int nmap = map_nodes(T.kind, T.map_order);
+      const int* corner = map_corners(T.kind, T.map_order);
       T.map_conn.assign(in.map_conn[ti], in.map_conn[ti] + size_t(T.ne) * nmap);
       for (int64_t e = 0; e < T.ne; ++e) {
         for (int v = 0; v < nmap; ++v) {

@@ -19,9 +19,9 @@ struct HostType {
   int64_t ne = 0;
   RefElement ref;
   std::vector<int64_t> conn;     // [ne][nv]
-  int map_order = 1;             // 2: quadratic (27-node) hexahedron map
-  std::vector<int64_t> map_conn; // [ne][27] (map_order 2)
-  std::vector<double> mapx;      // [ne][n_map][3] map node coordinates (map_order 2)
+  int map_order = 1;             // 2: quadratic, 3: cubic map
+  std::vector<int64_t> map_conn; // [ne][n_map] (map_order 2 or 3)
+  std::vector<double> mapx;      // [ne][n_map][3] map node coordinates (map_order 2 or 3)
   // anti-aliasing (Section 3.2): rule of degree aa_qdeg and its operators
   int aa_qdeg = 0;
   std::vector<double> aa_x, aa_w;  // [nq][3], [nq]
@@ -59,8 +59,8 @@ struct MeshInput {
   int order = 0;
   int family = 0;                       // hexahedron line points: 0 GL, 1 GLL
   std::vector<std::pair<int, std::pair<int64_t, const int64_t*>>> types;
-  std::vector<int> map_order;               // per entry of types: 1 or 2
-  std::vector<const int64_t*> map_conn;     // per entry: [ne][27] or null
+  std::vector<int> map_order;               // per entry of types: 1, 2 or 3
+  std::vector<const int64_t*> map_conn;     // per entry: [ne][n_map] or null
   std::vector<std::array<double, 3>> periodic;
   int64_t n_bfaces = 0;
   const int64_t* bface_nodes = nullptr;  // [n][4], -1 pads triangles

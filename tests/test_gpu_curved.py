@@ -219,3 +219,29 @@ def test_cubic_hex_rk_steps(precision, tol):
     g.rk_step("rk45", 1e-3, 2)
     err = rel_l2(g.get_solution(), u)
     assert err.max() < tol, err
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+@pytest.mark.parametrize("physics", ["euler", "ns"])
+def test_cubic_mixed_rhs_fp64(p, physics):
+    """Cubic maps on every type (64-node hexahedra, 40-node prisms, 20-node
+    tetrahedra) against the oracle, FP64, per conserved variable."""
+    o, osys, g = _pair_mixed(_curved_mixed(order=3), p, physics)
+    g.set_solution(lib_state(g, _tgv))
+    err = rel_l2_rhs(g.rhs(), osys.rhs(oracle_state(o, _tgv)))
+    assert err.max() < (5e-12 if p == 4 else 1e-12), err
+
+
+@pytest.mark.parametrize("precision,variant,tol", [("fp64", "sumfact", 1e-12),
+                                                   ("fp32", "sumfact", 1e-6),
+                                                   ("fp32", "tensor", 1e-6)])
+def test_cubic_mixed_rk_steps(precision, variant, tol):
+    o, osys, g = _pair_mixed(_curved_mixed(order=3), 3, "ns", precision=precision)
+    g.set_variant(variant)
+    g.set_solution(lib_state(g, _tgv))
+    u = oracle_state(o, _tgv)
+    for _ in range(2):
+        u = rk.step(osys.rhs, u, 2e-4, "rk45")
+    g.rk_step("rk45", 2e-4, 2)
+    err = rel_l2(g.get_solution(), u)
+    assert err.max() < tol, err

@@ -63,6 +63,7 @@ SPECS = {
     "curved-gll": lambda: curved_box_hex((3, 2, 2)),
     "curved-mixed": lambda: curved_mixed_box(n=3),
     "curved-cubic": lambda: curved_box_hex((3, 2, 2), order=3),
+    "curved-mixed-cubic": lambda: curved_mixed_box(n=3, order=3),
     "mixed": lambda: mixed_box(n=3, x_pri=0.34, x_tet=0.67, perturb=0.05),
     "curved": lambda: curved_box_hex((3, 2, 2)),
 }
@@ -89,7 +90,12 @@ def test_host_setup_matches_oracle(name, p):
         assert np.abs(g.points(t) - o.upts_x[t]).max() < 1e-14
         S, rj = g.metrics(t)
         So = o.S_u[t].reshape(o.ne[t], -1, 9).transpose(0, 2, 1)
-        assert np.abs(S - So).max() < 1e-14
+        # the host library and the oracle sum in different orders: 1e-13 of
+        # the metric's scale; 5e-13 for cubic simplex maps, whose curl form
+        # cancels terms X_l dX_m some 10x larger than S, built from basis
+        # coefficients up to 27
+        tol = 5e-13 if name == "curved-mixed-cubic" else 1e-13
+        assert np.abs(S - So).max() < tol * np.abs(So).max()
         assert np.abs(rj * o.detJ[t] - 1).max() < 1e-13
     npair, nb = g.pair_counts()
     assert npair == len(o.pair_l) and nb == len(o.bnd_g)
