@@ -96,7 +96,8 @@ def test_filter_fp32_with_fp64_checks_against_oracle():
     assert err[0] < 5e-3 and err[1:].max() < 1e-5, err
 
 
-def test_filter_fp32_single_application_same_elements_and_strengths():
+@pytest.mark.parametrize("scale", [1.0, 1e-6, 1e6])
+def test_filter_fp32_single_application_same_elements_and_strengths(scale):
     """One filter application to the same FP32-representable state with the
     same s_min on both sides (the oracle's, from the unperturbed state): FP32
     values with FP64 checks against the FP64 oracle with the FP32 entropy
@@ -112,9 +113,16 @@ def test_filter_fp32_single_application_same_elements_and_strengths():
     1e-2 relative.  Where it is flat (large zeta*: sigma_k = exp(-zeta
     (d_k/p)^2) and so the filtered state barely depend on zeta) FP32
     rounding of ~1e-6 in the margin moves zeta* by a percent or more, and
-    only the margin check applies."""
+    only the margin check applies.
+
+    scale multiplies the whole state (density, momentum and energy; the
+    velocities stay): the entropy margin is relative to s_min and the
+    density and pressure margins to the element means, so the decisions
+    are those of the unscaled state, while the FP32 pressures, entropies
+    and their ordering keys run through exponents far from those of
+    order-one values (s scales by scale^(1 - gamma))."""
     o, s, g = _strip(64, precision="fp32")
-    u0 = oracle_state(o, ics.shu_osher)
+    u0 = {t: scale * v for t, v in oracle_state(o, ics.shu_osher).items()}
     smin = EF.element_smin(s, u0)
     # a seeded 0.1 % point-wise perturbation: nearly every element violates
     # the entropy bound of the unperturbed state by a little (moderate
