@@ -48,7 +48,9 @@ constexpr double kZetaMax = 36.0;
 constexpr double kEpsPos = 1e-8;
 constexpr double kRelTol = 1e-6;
 constexpr int kMaxEvals = 24;
-constexpr int kFilterThreads = 128;
+// threads of a k_filter CTA: one point per thread for p = 3 hexahedra (64
+// solution + 96 flux points), two for p = 4
+constexpr int kFilterThreads = 160;
 
 struct FilterStats {
   unsigned long long filtered;    // element-stages filtered (zeta > 0)
@@ -742,6 +744,26 @@ __global__ void k_filter_check(long long ne, const T* __restrict__ reg,
   }
 }
 
+// the five values of one mode of ush (a 16-byte aligned row of 8): one
+// 128-bit and one 32-bit shared load in FP32
+__device__ __forceinline__ void get_modes5(const float (&r)[8], float (&a)[5]) {
+  const float4 x = *reinterpret_cast<const float4*>(&r[0]);
+  a[0] = x.x;
+  a[1] = x.y;
+  a[2] = x.z;
+  a[3] = x.w;
+  a[4] = r[4];
+}
+__device__ __forceinline__ void get_modes5(const double (&r)[8], double (&a)[5]) {
+  const double2 x = *reinterpret_cast<const double2*>(&r[0]);
+  const double2 y = *reinterpret_cast<const double2*>(&r[2]);
+  a[0] = x.x;
+  a[1] = x.y;
+  a[2] = y.x;
+  a[3] = y.y;
+  a[4] = r[4];
+}
+
 // Filter the stage value of each element that violates the constraints.
 // reg / regR: the register holding the new stage value (type T or TR, one
 // of them null); uf: this type's flux-point traces of that value.
@@ -752,7 +774,7 @@ __global__ void __launch_bounds__(kFilterThreads)
              const int32_t* __restrict__ list, const int* __restrict__ count) {
   constexpr int NM = NU, NP = NU + NF;
   __shared__ T uh[5][NM];       // modal coefficients
-  __shared__ T sg[NM];          // filtered weights sigma_k
+  __shared__ __align__(16) T ush[NM][8];  // sigma_k u^_k of an evaluation (5 used)
   __shared__ double red[kFilterThreads / 32];
   __shared__ long long redk[4 * (kFilterThreads / 32)];
   __shared__ float redf[2 * (kFilterThreads / 32)];
@@ -789,7 +811,9 @@ __global__ void __launch_bounds__(kFilterThreads)
   auto minima = [&](double z) -> Mins {
     for (int m = tid; m < NM; m += kFilterThreads) {
       double d = double(op.deg[m]);
-      sg[m] = sizeof(T) == 4 ? T(__expf(-float(z * d * d))) : T(exp(-z * d * d));
+      const T sk = sizeof(T) == 4 ? T(__expf(-float(z * d * d))) : T(exp(-z * d * d));
+#pragma unroll
+      for (int k = 0; k < 5; ++k) ush[m][k] = sk * uh[k][m];
     }
     __syncthreads();
     T v[NPT][5];
@@ -805,9 +829,11 @@ __global__ void __launch_bounds__(kFilterThreads)
       sc[q].plo = sc[q].slo = INFINITY;  // no point: never a candidate
       if (i >= NP) continue;
       for (int m = 0; m < NM; ++m) {
-        T w = op.VT[m * NP + i] * sg[m];
+        const T w = op.VT[m * NP + i];
+        T a[5];
+        get_modes5(ush[m], a);
 #pragma unroll
-        for (int k = 0; k < 5; ++k) v[q][k] += w * uh[k][m];
+        for (int k = 0; k < 5; ++k) v[q][k] += w * a[k];
       }
       rmin_t = sizeof(T) == 4 ? T(fminf(float(rmin_t), float(v[q][0])))
                               : T(fmin(double(rmin_t), double(v[q][0])));
@@ -878,13 +904,13 @@ __global__ void __launch_bounds__(kFilterThreads)
           }
           const bool pnan = (__double_as_longlong(pk) & 0x7fffffffffffffffLL) >
                             0x7ff0000000000000LL;  // ignored, like fmin
-          const long long kt = (dkey(pk) & ~0x7fLL) | tid;
+          const long long kt = (dkey(pk) & ~0xffLL) | tid;
           if (cp && !pnan && kt < kp) {
             kp = kt;
             qp = q;
           }
           if (ykey) {
-            const long long kyt = (dkey(yk) & ~0x7fLL) | tid;
+            const long long kyt = (dkey(yk) & ~0xffLL) | tid;
             if (kyt < ky) {
               ky = kyt;
               qy = q;
@@ -1182,15 +1208,20 @@ __global__ void __launch_bounds__(kFilterThreads)
   // every thread: the strength found by thread 0
   result = s_next;
   // write the filtered state and its flux-point values
-  for (int m = tid; m < NM; m += kFilterThreads)
-    sg[m] = T(exp(-result * double(op.deg[m]) * double(op.deg[m])));
+  for (int m = tid; m < NM; m += kFilterThreads) {
+    const T sk = T(exp(-result * double(op.deg[m]) * double(op.deg[m])));
+#pragma unroll
+    for (int k = 0; k < 5; ++k) ush[m][k] = sk * uh[k][m];
+  }
   __syncthreads();
   for (int i = tid; i < NP; i += kFilterThreads) {
     T v[5] = {0, 0, 0, 0, 0};
     for (int m = 0; m < NM; ++m) {
-      T w = op.VT[m * NP + i] * sg[m];
+      const T w = op.VT[m * NP + i];
+      T a[5];
+      get_modes5(ush[m], a);
 #pragma unroll
-      for (int k = 0; k < 5; ++k) v[k] += w * uh[k][m];
+      for (int k = 0; k < 5; ++k) v[k] += w * a[k];
     }
     if (i < NU) {
 #pragma unroll

@@ -4,8 +4,9 @@ inputs (Section 2 right-hand side; Section 2/3.5 time stepping).
 Tolerances (relative L2 per conserved variable):
 * FP64 mode, solutions (after RK steps): 1e-12, normalised as
   ||u - u_ref|| / max(||u_ref||, ||rho_ref||) per variable.
-* FP64 mode, bare right-hand sides: normalised by the largest per-variable
-  RHS norm.  The RHS is a small difference of large terms: the energy flux
+* FP64 mode, bare right-hand sides: each variable normalised by its own
+  RHS norm (floored at 1e-3 of the largest, for components that vanish in
+  exact arithmetic).  The RHS is a small difference of large terms: the energy flux
   (E + p) v is ~p0 gamma/(gamma-1) = 250 at Ma 0.1 while |R| ~ 1, and the
   derivative operators add a factor ~(p+1)^2 / h.  Rounding of order
   eps * 250 * (p+1)^2 / h therefore reaches 1e-10 of |R| at p=3 on 32^3
