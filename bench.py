@@ -164,7 +164,45 @@ def kernel_models(nu, nf, ne, w, wr, npair):
     return bytes_, flops
 
 
-def roofline(prof, models, peaks, src, precision, alu):
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of a dominant
+# kernel per element and launch, from one ncu capture on a smaller case of the
+# same kernel (inputs well above L2, so traffic grows with the elements) and
+# scaled by the elements of a launch.  Keyed by (kernel class, precision,
+# order); each entry records the sha256 of the library's CUDA sources the
+# capture ran, and the bench reports it only while they are unchanged (a
+# changed kernel reports null), with the profile that holds the capture.
+TRAFFIC = {
+    # k_hex_vol<double, double, 5, 2, NS>: 32^3 elements, p = 4, two launches
+    ("volume", "fp64", 4): (53324.6,
+                           "686cfcca827c9ddaf043d9eaa9600573a3627d36daac1e196544fe4da21f742b",
+                           "profiles/k_hex_vol_fp64_tgv32_p4_traffic.md"),
+}
+
+
+def _sources_sha():
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2408_16509_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".inc")):
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(f.encode())
+                h.update(fh.read())
+    return h.hexdigest()
+
+
+def traffic_of(kernel, precision, p, ne):
+    """(bytes per launch, profile) of a recorded capture, or (None, why)."""
+    rec = TRAFFIC.get((kernel, precision, p))
+    if rec is None:
+        return None, "no capture recorded for this kernel"
+    per_elem, sha, prof = rec
+    if sha != _sources_sha():
+        return None, "kernel sources changed since " + prof
+    return per_elem * ne, prof
+
+
+def roofline(prof, models, peaks, src, precision, alu, order=None, ne=None):
     """Roofline record of the dominant kernel class: the bound is whichever
     of DRAM bytes / HBM peak and flops / arithmetic peak takes longer.
     alu: {"fp64": (TFLOP/s, source), "fp32": (...)} measured in this run."""
@@ -185,8 +223,8 @@ def roofline(prof, models, peaks, src, precision, alu):
                "peak": peaks["hbm_gbs"], "unit": "GB/s",
                "frac": bw / peaks["hbm_gbs"],
                "peak_source": src + " hbm_gbs (MEASURED_PEAKS.json), burst copy"}
-    # DRAM traffic needs an ncu capture (profiles/); not measured in a bench run
-    out["traffic"] = None
+    out["traffic"], out["traffic_source"] = (
+        traffic_of(dom, precision, order, ne) if ne else (None, "not recorded"))
     out.update({"launches_per_step": prof[dom][1], "kernel_ms": t * 1e3,
                 "algorithmic_bytes": b, "algorithmic_flops": f,
                 "achieved_gbs": bw, "achieved_tflops": fl,
@@ -287,6 +325,13 @@ def _e2e(fr, torch, mesh, u0, steps, world, dist):
     hin, hout = host_in.numpy(), host_out.numpy()
     ne, nu, _ = mesh.info("hex")
     e2e_steps = max(3, min(steps, 10))
+    # one untimed pass: the first copies through freshly pinned buffers pay
+    # a one-time cost (about 27 ms for the 553 MB input at 48^3, p = 4)
+    rc = lib.fr_set_solution(mesh._h, 0, hin.ctypes.data_as(ctypes.c_void_p))
+    rc |= lib.fr_rk_step(mesh._h, 1, DT, 1)
+    rc |= lib.fr_get_solution(mesh._h, 0, hout.ctypes.data_as(ctypes.c_void_p))
+    if rc:
+        raise RuntimeError(lib.fr_last_error().decode())
     torch.cuda.synchronize()
     w0 = time.perf_counter()
     for _ in range(e2e_steps):
@@ -333,8 +378,9 @@ def run_ours(args):
     def widths(prec):
         return (8 if prec == "fp64" else 4), (4 if prec == "fp32" else 8)
     w, wr = widths(args.precision)
+    order = round(nu ** (1.0 / 3.0)) - 1
     roof = roofline(prof, kernel_models(nu, nf, ne, w, wr, npair), peaks, src,
-                    args.precision, alu)
+                    args.precision, alu, order, ne)
     line = {
         "metric": METRIC,
         "value": value, "unit": "GDOF-stage/s", "n_gpus": world,
@@ -374,7 +420,7 @@ def run_ours(args):
                 "ms_per_step": v["ms"] / args.steps,
                 "roofline": roofline(
                     v["prof"], kernel_models(nu, nf, ne, w2, wr2, npair), peaks,
-                    src, prec, alu),
+                    src, prec, alu, order, ne),
                 "kernel_ms_per_step": {k: x[0] for k, x in v["prof"].items() if x[1]},
                 "kernel_family": {"active": v["tuning"][0],
                                   "tuned_ms_per_step": v["tuning"][1],
