@@ -280,3 +280,20 @@ def test_tetrahedron_flux_points_are_solution_points(p):
     nz = np.abs(M0) > 1e-12 * np.abs(M0).max()
     assert np.all(nz.sum(axis=1) == 1)
     assert np.allclose(M0[nz], 1.0, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("order", [2, 3])
+@pytest.mark.parametrize("p", [2, 3])
+def test_library_curl_metrics_are_discretely_divergence_free(order, p):
+    """The library's own curved metrics, with its own derivative operators
+    (no oracle): sum_i D_i S[i][n] = 0 at the solution points of every type,
+    for quadratic and cubic maps (S in the element's solution space)."""
+    g = fr.FRMesh(curved_mixed_box(n=3, order=order), p, device=-1,
+                  bcs={k: ("state", 1.0, 0.0, 0.0, 0.0, 1.0) for k in range(6)})
+    for t in g.types:
+        S, _ = g.metrics(t)                    # (ne, 9, nu), row i*3 + n
+        D = g.operator(t, "D")                 # (3, nu, nu)
+        scale = np.abs(S).max()
+        for n in range(3):
+            div = sum(np.einsum("pq,eq->ep", D[i], S[:, 3 * i + n, :]) for i in range(3))
+            assert np.abs(div).max() < 1e-12 * scale, (t, n, np.abs(div).max() / scale)
